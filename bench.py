@@ -1,0 +1,329 @@
+"""Benchmark: TDSE coefficient-updates/s of the batched Crank-Nicolson propagator on B300.
+
+Workload (N=1): the batched 1-D position-dependent-mass double-quantum-well scan -
+256 GaAs/Al0.3Ga0.7As geometries (barrier 1-6 nm, wells 10 nm, 0.24 eV offset,
+m* 0.067/0.092, 800-3000 order-6 B-splines with knots on every interface) x 4 mid-IR
+intensities (lambda = 10 um, Keldysh gamma 2.3/1.5/1.0/0.5) = 1024 uneven runs in one
+persistent launch, dt = 0.5 a.u., mixed precision (FP32 factors + double-float
+refinement). A step = one CN step of every run incl. the per-step observables.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line. With torchrun (N > 1) each rank propagates its own full batch (weak
+scaling, no data-path collective); rank 0 prints the line with the max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+# the CPU-baseline leg times the oracle single-threaded: pin BLAS/OpenMP pools before numpy loads
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as wl  # noqa: E402
+
+METRIC = "TDSE coefficient-updates/s: batched mixed vs plain FP64 at stated HHG/norm error"
+UNIT = "coefficient-updates/s"
+
+
+def flops_per_dof_step(p: int) -> int:
+    """Algorithmic flops of one CN step per coefficient (complex MAC = 8 flops): band LDL^T
+    (p(p+1)/2 MACs + p scalings + reciprocal), rhs (2p+1 MACs), forward/back substitution
+    (2p MACs + D^-1), and the four quadratic forms S, D, G, K of the observables."""
+    factor = 8 * p * (p + 1) // 2 + 6 * p + 10
+    rhs = 8 * (2 * p + 1)
+    subst = 16 * p + 6
+    obs = 3 * (p + 1) + 8 * (p + 1)
+    return factor + rhs + subst + obs
+
+
+def build_batch_inputs(n_geom, fields_per_geom, nsteps, seed=wl.SEED):
+    wk = wl.dqw_batch(n_geometries=n_geom, fields_per_geometry=fields_per_geom, nsteps=nsteps, seed=seed)
+    return wk
+
+
+def initial_state(run: wl.Run1D, med) -> np.ndarray:
+    """Synthetic initial state: Gaussian wavepacket centred in the left well (Greville samples)."""
+    b = med["mass"]["bounds"]
+    x0 = 0.5 * (b[1] + b[2])
+    sigma = 0.25 * (b[2] - b[1])
+    c = wl.gaussian_coeffs(run.knots, run.degree, x0, sigma)
+    return c / np.sqrt(np.sum(np.abs(c) ** 2))
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+# ----------------------------------------------------------------------------- CPU baseline (oracle)
+def cpu_oracle_leg(wk, c0s, nruns_sample, nsteps_sample, ops_mats=None):
+    """Time the CPU oracle (as it stands) on a bounded sample: the first `nruns_sample` runs for
+    `nsteps_sample` steps. Returns (value, details, final states, observables)."""
+    from oracle import assemble, propagate
+    mats = {}
+    finals, obs = [], []
+    if True:
+        t_asm = 0.0
+        for i in range(nruns_sample):
+            r = wk.runs[i]
+            if r.geometry not in mats:
+                t0 = time.perf_counter()
+                mats[r.geometry] = assemble.assemble_1d(r.knots, r.degree, r.nquad, r.medium)
+                t_asm += time.perf_counter() - t0
+        t0 = time.perf_counter()
+        dof = 0
+        for i in range(nruns_sample):
+            r = wk.runs[i]
+            c, o = propagate.cn_propagate(mats[r.geometry], c0s[i], r.field, wk.dt, nsteps_sample)
+            finals.append(c)
+            obs.append(o)
+            dof += len(c)
+        t = time.perf_counter() - t0
+    return dof * nsteps_sample / t, {"seconds": t, "dof": dof, "assembly_s": t_asm}, finals, obs
+
+
+def reference_arm(args):
+    """--impl reference: the CPU oracle (the stated reference for this build) on host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    nsample = 8
+    wk = build_batch_inputs(args.n_geom, 4, args.warmup + args.steps + 1)
+    c0s = [initial_state(wk.runs[i], wk.runs[i].medium) for i in range(nsample)]
+    # warm-up: W steps on one run (imports, caches)
+    cpu_oracle_leg(wk, c0s, 1, max(1, args.warmup))
+    value, det, _, _ = cpu_oracle_leg(wk, c0s, nsample, args.steps)
+    sample = f"first {nsample} runs of the batch for {args.steps} steps ({det['dof']} coefficients/step)"
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * det["seconds"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": "dqw_batch_1d", "runs": len(wk.runs), "sample_runs": nsample, "degree": 6},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n-geom", type=int, default=256)
+    ap.add_argument("--fp64-steps", type=int, default=10)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import paper_2608_18472_b300 as tdz
+
+    nsteps_total = args.warmup + args.steps
+    # every rank builds its own shard: the full scan with a rank-dependent seed (weak scaling)
+    wk = build_batch_inputs(args.n_geom, 4, nsteps_total + args.fp64_steps + 1, seed=wl.SEED + rank)
+    runs = wk.runs
+    geoms = {}
+    for r in runs:
+        if r.geometry not in geoms:
+            geoms[r.geometry] = tdz.assemble_1d(r.knots, r.degree, r.medium, r.nquad)
+    ops = [geoms[g] for g in sorted(geoms)]
+    run_ops = [r.geometry for r in runs]
+    c0 = [initial_state(r, r.medium) for r in runs]
+    p = runs[0].degree
+    field_all = np.ascontiguousarray(np.stack([r.field for r in runs]))  # [runs, steps+1, 1]
+    nruns = len(runs)
+    dof = sum(ops[g].n for g in run_ops)
+    stream = torch.cuda.current_stream()
+
+    def make_batch(prec):
+        b = tdz.Batch(ops, run_ops, prec, stream=stream.cuda_stream)
+        for i in range(nruns):
+            b.set_state(i, c0[i])
+        return b
+
+    def dev_field(k0, k):
+        return torch.from_numpy(np.ascontiguousarray(field_all[:, k0:k0 + k + 1, :])).cuda()
+
+    # ---------------- mixed (headline): warm-up then K timed steps, inputs resident on device
+    bm = make_batch(tdz.MIXED)
+    fw, ft = dev_field(0, args.warmup), dev_field(args.warmup, args.steps)
+    bm.propagate(fw, wk.dt, 0, args.warmup)
+    norm0 = np.array([bm.observe(i)[0][-1, 4] for i in range(nruns)])
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        bm.propagate(ft, wk.dt, args.warmup, args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    drift = 0.0
+    statuses = []
+    for i in range(nruns):
+        o, st = bm.observe(i)
+        statuses.append(st)
+        drift = max(drift, float(np.max(np.abs(o[:, 4] - norm0[i]) / norm0[i])))
+    max_rel, nsolve = bm.refine_stats()
+    solves_per_step = nsolve / (nruns * (args.warmup + args.steps))
+
+    # ---------------- plain FP64 on the same batch (comparison leg)
+    bf = make_batch(tdz.FP64)
+    ff = dev_field(0, args.fp64_steps)
+    bf.propagate(dev_field(0, 2), wk.dt, 0, 2)  # warm-up
+    for i in range(nruns):
+        bf.set_state(i, c0[i])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    bf.propagate(ff, wk.dt, 0, args.fp64_steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = e0.elapsed_time(e1)
+    del bf
+
+    # ---------------- end to end through the public API with host buffers
+    pinned_field = torch.from_numpy(np.ascontiguousarray(field_all[:, args.warmup:args.warmup + args.steps + 1, :])).pin_memory()
+    obs_host = torch.empty((args.steps, 5), dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(nruns):
+        bm.set_state(i, c0[i])
+    bm.propagate(pinned_field, wk.dt, args.warmup, args.steps)
+    for i in range(nruns):
+        bm.observe(i, out=obs_host)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    h2d = (nruns * (args.steps + 1) * 8 + dof * 16) / args.steps
+    d2h = nruns * 5 * 8
+
+    value = world * dof * args.steps / (ms * 1e-3)
+    value64 = dof * args.fp64_steps / (ms64 * 1e-3)
+    flops = flops_per_dof_step(p) * dof * args.steps
+    peak_fp32 = 148 * 128 * 2 * 2.032e9 / 1e12  # TFLOP/s, unit counts x max clock
+    achieved = flops / (ms * 1e-3) / 1e12
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+ff", "data": "synthetic",
+            "config": {"workload": "dqw_batch_1d", "runs": nruns, "geometries": len(ops), "coefficients": dof,
+                       "degree": p, "dt": wk.dt, "precision": "mixed", "l2": "working set > L2 (126 MB): no flush",
+                       "parallelism": f"replicas x{world}"},
+            "gpu_launches": 1,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
+                         "frac": achieved / peak_fp32, "traffic": None,
+                         "note": "algorithmic flops per coefficient-step x coefficients / event time; peak = 148 SM x 128 FP32 FMA x 2 x 2.032 GHz"},
+            "plain_fp64": {"value": value64, "unit": UNIT, "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps,
+                           "speedup_mixed": value / world / value64},
+            "accuracy": {"norm_drift_max": drift, "refine_max_rel_residual": max_rel,
+                         "solves_per_step": solves_per_step, "runs_not_ok": int(sum(s != 0 for s in statuses))},
+            "e2e": {"value": world * dof * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "clocks": clk.summary()}
+    if rank == 0 and not args.no_cpu:
+        # bounded oracle sample sized to ~cpu_seconds; GPU mixed path compared on the same sample
+        ns_probe = 20
+        v_probe, det, _, _ = cpu_oracle_leg(wk, c0, 1, ns_probe)
+        per_run_step = det["seconds"] / ns_probe
+        nsample = 8
+        nsteps_s = max(20, min(2000, int(args.cpu_seconds / (per_run_step * nsample))))
+        v, det, finals, oobs = cpu_oracle_leg(wk, c0, nsample, nsteps_s)
+        bs = tdz.Batch(ops, run_ops[:nsample], tdz.MIXED)
+        for i in range(nsample):
+            bs.set_state(i, c0[i])
+        bs.propagate(np.ascontiguousarray(field_all[:nsample, :nsteps_s + 1]), wk.dt, 0, nsteps_s)
+        rel = max(np.linalg.norm(bs.get_state(i) - finals[i]) / np.linalg.norm(finals[i]) for i in range(nsample))
+        dmax = max(np.max(np.abs(bs.observe(i)[0][:, 2] - oobs[i][:, 2])) / max(1e-30, np.max(np.abs(oobs[i][:, 2])))
+                   for i in range(nsample))
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"first {nsample} runs x {nsteps_s} steps ({det['dof']} coefficients), "
+                                          f"{det['seconds']:.1f} s single-threaded"}
+        line["accuracy"]["sample_vs_oracle"] = {"runs": nsample, "steps": nsteps_s, "max_rel_l2": rel,
+                                                "max_dipole_rel_err": dmax}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

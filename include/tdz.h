@@ -1,0 +1,177 @@
+/*
+ * tdz.h - C ABI of the B300 Crank-Nicolson propagator for the B-spline Galerkin
+ * time-dependent Schrodinger equation with a BenDaniel-Duke (position-dependent
+ * mass) kinetic operator, after TDSE-Z (arXiv 2608.18472).
+ *
+ * Conventions shared by every entry point
+ *   - Status: every function returns int; TDZ_OK (0) on success, a negative
+ *     TDZ_E* code otherwise. No call aborts or exits the process.
+ *   - Ownership: the caller owns every array it passes; the library copies
+ *     what it keeps. Opaque handles are library-owned and freed by their
+ *     *_destroy function (NULL is accepted and ignored).
+ *   - Complex vectors are interleaved (re, im) doubles: element j at [2j], [2j+1].
+ *   - Coefficient order: B-spline index with the two Dirichlet end functions
+ *     removed (Sec. "Weak form"): DoF j <-> B-spline j+1. In 2-D/3-D the linear
+ *     index is x fastest: I = i_x + n_x (i_y + n_y i_z).
+ *   - Pointers documented "host or device" may be either; the library tells
+ *     them apart with cudaPointerGetAttributes.
+ *   - Units are atomic units throughout.
+ */
+#ifndef TDZ_H
+#define TDZ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+#define TDZ_OK            0
+#define TDZ_EINVAL       -1   /* bad argument: null pointer, size, range, knot vector */
+#define TDZ_ENOMEM       -2   /* host or device allocation failed                      */
+#define TDZ_ECUDA        -3   /* a CUDA runtime call failed (message: tdz_last_error)  */
+#define TDZ_ENOCONV      -4   /* an iteration reached its cap before its tolerance     */
+#define TDZ_ENONFINITE   -5   /* a NaN/Inf appeared in the state or the field          */
+#define TDZ_EUNSUPPORTED -6   /* valid request outside what this build implements      */
+
+/* Human-readable description of the last error raised on the calling thread. */
+const char* tdz_last_error(void);
+
+/* ------------------------------------------------------------------ precision */
+#define TDZ_FP64   0  /* binary64 everywhere: factors, solves, residuals, state              */
+#define TDZ_MIXED  1  /* FP32 factors and solves; residual, correction, state and observable
+                         products in double-float (hi+lo FP32 pair, 48-bit significand);
+                         reductions accumulated in binary64                                   */
+
+/* ------------------------------------------------------------------ basis
+ * tdz_basis_create: B-spline basis of degree `degree` on an open knot vector
+ * (Sec. "Weak form": ends repeated degree+1 times; Eq. tensor3d gives the
+ * tensor product of such 1-D bases), with an `nquad`-point Gauss-Legendre
+ * rule on every non-empty knot span (Sec. "Parallel assembly").
+ *   knots  : host, nknots non-decreasing values, first and last repeated
+ *            degree+1 times, at least one non-empty span.
+ *   degree : 1..8.   nquad: 1..16.
+ * Errors: TDZ_EINVAL for a malformed knot vector or out-of-range sizes.
+ */
+typedef struct tdz_basis tdz_basis;
+int  tdz_basis_create(const double* knots, int64_t nknots, int degree, int nquad, tdz_basis** out);
+/* nfun = number of B-splines (Dirichlet ends included), nelem = non-empty spans. */
+int  tdz_basis_info(const tdz_basis* b, int64_t* nfun, int64_t* nelem, int* degree, int* nquad);
+/* Values and first derivatives of all nfun B-splines at npts host points,
+ * written to host arrays val[nfun*npts], der[nfun*npts] (function-major). */
+int  tdz_basis_eval(const tdz_basis* b, const double* x, int64_t npts, double* val, double* der);
+void tdz_basis_destroy(tdz_basis* b);
+
+/* ------------------------------------------------------------------ medium */
+#define TDZ_MASS_CONST    0  /* m(r) = mass_par[0]                                              */
+#define TDZ_MASS_QUESNE   1  /* m(x) = (1 + x/a)^-1, a = mass_par[0] (Eq. mass)                  */
+#define TDZ_MASS_LAYERS   2  /* 1-D piecewise constant: layer_mass[r] on [bounds[r], bounds[r+1]) */
+#define TDZ_MASS_ELLIPSE  3  /* 2-D dot: m_in inside x^2/a^2+y^2/b^2<1, m_out outside;
+                                mass_par = {a, b, m_in, m_out}                                  */
+#define TDZ_POT_ZERO      0
+#define TDZ_POT_SOFTCORE  1  /* V = -z / sqrt(|r|^2 + eps), pot_par = {z, eps}                   */
+#define TDZ_POT_HO        2  /* V = 1/2 sum_a w_a^2 x_a^2, pot_par = {w_x, w_y, w_z}              */
+#define TDZ_POT_QUESNE    3  /* V = a w^2 x^2 / (8 (x + a)) (Eq. rescaling), pot_par = {a, w}      */
+#define TDZ_POT_LAYERS    4  /* 1-D piecewise constant layer_pot[r]                               */
+#define TDZ_POT_ELLIPSE   5  /* 2-D dot, pot_par = {a, b, v_in, v_out}                            */
+#define TDZ_POT_H2P       6  /* 1-D two-centre soft core, pot_par = {R, eps} (Sec. Molecular HHG) */
+
+typedef struct tdz_medium {
+  int mass_kind;
+  int pot_kind;
+  double mass_par[4];
+  double pot_par[4];
+  int nlayers;                 /* TDZ_*_LAYERS only                      */
+  const double* layer_bounds;  /* host, nlayers+1 increasing points      */
+  const double* layer_mass;    /* host, nlayers                          */
+  const double* layer_pot;     /* host, nlayers                          */
+} tdz_medium;
+
+/* ------------------------------------------------------------------ assembly
+ * tdz_assemble: Galerkin matrices of Sec. "Parallel assembly" by Gauss
+ * quadrature on every element, all in one pass over the elements:
+ *   S = <B|B> (Eq. mass_elem), T = 1/2 <dB| m^-1 |dB> (Eq. bdd_elem),
+ *   V = <B|V|B>, D_a = <B|x_a|B> (potential/dipole element formulas),
+ *   G_a = <B| m^-1 dV/dx_a |B>, K = <B| m^-1 |B>  (acceleration, Eq. pdm_acceleration),
+ * with the Dirichlet end functions removed. 1-D results are symmetric band
+ * matrices, half bandwidth = degree. dim = 1 only in this build (2-D/3-D
+ * return TDZ_EUNSUPPORTED).
+ */
+typedef struct tdz_ops tdz_ops;
+#define TDZ_MAT_S  0
+#define TDZ_MAT_T  1
+#define TDZ_MAT_V  2
+#define TDZ_MAT_H0 3   /* T + V */
+#define TDZ_MAT_D  4
+#define TDZ_MAT_G  5
+#define TDZ_MAT_K  6
+int  tdz_assemble(const tdz_basis* const* axes, int dim, const tdz_medium* medium, tdz_ops** out);
+/* n = DoF per axis (shape[0..dim-1]); degree per axis. */
+int  tdz_ops_info(const tdz_ops* ops, int* dim, int64_t* shape, int* degree);
+/* Copy a 1-D band matrix to host out[n*(degree+1)]: out[i*(degree+1)+d] = M(i, i-d). */
+int  tdz_ops_band(const tdz_ops* ops, int which, int axis, double* out);
+void tdz_ops_destroy(tdz_ops* ops);
+
+/* Ground state of H0 c = eps S c (Eq. gen_ev) by shifted inverse iteration on
+ * the host (1-D). Output: *energy and c[2n] (interleaved complex, real-valued,
+ * S-normalised, largest component positive: Sec. "Wavefunction realignment").
+ * TDZ_ENOCONV if the Rayleigh quotient has not settled within the cap.       */
+int  tdz_ground_state(const tdz_ops* ops, double* energy, double* c);
+
+/* ------------------------------------------------------------------ batch
+ * A batch is a set of independent runs propagated together on one GPU (one
+ * persistent launch per tdz_propagate call). Run r uses ops[ops_index[r]];
+ * runs may have different sizes. precision is TDZ_FP64 or TDZ_MIXED.
+ * cuda_stream: a cudaStream_t (NULL = the legacy default stream); every GPU
+ * operation of the batch is enqueued on it. The batch owns its device memory
+ * (allocated here with cudaMalloc, freed by tdz_batch_destroy).
+ */
+typedef struct tdz_batch tdz_batch;
+int  tdz_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* ops_index,
+                      int precision, void* cuda_stream, tdz_batch** out);
+/* Device bytes held by the batch (for capacity planning). */
+int  tdz_batch_info(const tdz_batch* b, int* nruns, int64_t* total_dof, size_t* device_bytes);
+/* Set the state of one run: c[2n], host or device. Resets that run's
+ * extrapolation history (the next mixed step refines without a predictor). */
+int  tdz_set_state(tdz_batch* b, int run, const double* c);
+/* Copy the state of one run to c[2n], host or device. */
+int  tdz_get_state(const tdz_batch* b, int run, double* c);
+
+/* Mixed-precision refinement control: after each FP32 solve the step is accepted when
+ * ||B_n c^n - A_n c^{n+1}|| <= tol ||S c^n||; at most max_solves FP32 solves per step
+ * (then the run's status becomes TDZ_ENOCONV and propagation continues). Defaults:
+ * tol = 1e-11, max_solves = 6. Ignored by TDZ_FP64 batches (one exact solve per step). */
+int  tdz_batch_set_refinement(tdz_batch* b, double tol, int max_solves);
+
+/* tdz_propagate: nsteps Crank-Nicolson steps of every run (Sec. "Time
+ * propagation", Eq. cn_system), from absolute step index step0:
+ *   (S + i dt/2 H_n) c^{n+1} = (S - i dt/2 H_n) c^n,  H_n = H0 + Ebar_n D,
+ *   Ebar_n = (E(t_n) + E(t_{n+1}))/2,  t_n = n dt.
+ * field: host or device, field[(r*(nsteps+1) + k)*dim + a] = E_a(t_{step0+k}),
+ *   k = 0..nsteps, for every run r.
+ * After every step the observables of Sec. "Dipoles" are recorded (see
+ * tdz_observe). The call is asynchronous with respect to the host when the
+ * field is a device pointer; it synchronises the stream otherwise.
+ * Errors: TDZ_EINVAL (sizes), TDZ_ECUDA. Per-run numerical failures
+ * (non-finite state, refinement cap) are reported by tdz_observe's status. */
+int  tdz_propagate(tdz_batch* b, const double* field, double dt, int64_t step0, int64_t nsteps);
+
+/* tdz_observe: observables of run `run` for the steps of the last
+ * tdz_propagate call, out[nsteps][2+3*dim] (host or device):
+ *   [t_{n+1}, E_a(t_{n+1}), d_a = c^H D_a c, a_a = -c^H G_a c - E_a c^H K c, c^H S c]
+ * (raw, not divided by the norm). *status (host, may be NULL) receives the
+ * run's status: TDZ_OK, TDZ_ENONFINITE or TDZ_ENOCONV (first failure wins).
+ * Synchronises the batch stream. */
+int  tdz_observe(const tdz_batch* b, int run, double* out, int* status);
+/* Largest relative residual ||b - A c||/||b|| seen by the refinement of any run
+ * in the last call (mixed precision; 0 for TDZ_FP64) and the mean number of
+ * FP32 solves per step. Synchronises the batch stream. */
+int  tdz_refine_stats(const tdz_batch* b, double* max_rel_residual, double* mean_solves);
+void tdz_batch_destroy(tdz_batch* b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TDZ_H */

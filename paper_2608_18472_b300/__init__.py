@@ -1,0 +1,273 @@
+"""Python binding of the TDSE-Z B300 propagator library (libtdz.so, C ABI in include/tdz.h).
+
+Argument marshalling only: every step of the propagation runs in the library's CUDA
+kernels. Importing this package loads the in-tree ``libtdz.so``; if it is missing the
+import fails loudly (build it with ``python paper_2608_18472_b300/build.py``). There is
+no CPU fallback.
+
+Names follow the paper (arXiv 2608.18472): S (overlap, M in the paper), T (BenDaniel-Duke
+kinetic), V, D (dipole), G/K (acceleration matrices), Crank-Nicolson propagation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtdz.so")
+
+TDZ_OK, TDZ_EINVAL, TDZ_ENOMEM, TDZ_ECUDA, TDZ_ENOCONV, TDZ_ENONFINITE, TDZ_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+FP64, MIXED = 0, 1
+MAT = {"S": 0, "T": 1, "V": 2, "H0": 3, "D": 4, "G": 5, "K": 6}
+_MASS = {"const": 0, "quesne": 1, "layers": 2, "ellipse": 3}
+_POT = {"zero": 0, "softcore": 1, "ho": 2, "quesne": 3, "layers": 4, "ellipse": 5, "h2p_softcore": 6}
+
+
+class TDZError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what} failed with status {code}: {last_error()}")
+        self.code = code
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} not found: build the CUDA library with `python paper_2608_18472_b300/build.py`")
+_lib = C.CDLL(LIB_PATH)
+
+
+class _Medium(C.Structure):
+    _fields_ = [("mass_kind", C.c_int), ("pot_kind", C.c_int), ("mass_par", C.c_double * 4),
+                ("pot_par", C.c_double * 4), ("nlayers", C.c_int), ("layer_bounds", C.POINTER(C.c_double)),
+                ("layer_mass", C.POINTER(C.c_double)), ("layer_pot", C.POINTER(C.c_double))]
+
+
+_dp = C.POINTER(C.c_double)
+_vp = C.c_void_p
+_sig = {
+    "tdz_last_error": (C.c_char_p, []),
+    "tdz_basis_create": (C.c_int, [_dp, C.c_int64, C.c_int, C.c_int, C.POINTER(_vp)]),
+    "tdz_basis_info": (C.c_int, [_vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "tdz_basis_eval": (C.c_int, [_vp, _dp, C.c_int64, _dp, _dp]),
+    "tdz_basis_destroy": (None, [_vp]),
+    "tdz_assemble": (C.c_int, [C.POINTER(_vp), C.c_int, C.POINTER(_Medium), C.POINTER(_vp)]),
+    "tdz_ops_info": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int64), C.POINTER(C.c_int)]),
+    "tdz_ops_band": (C.c_int, [_vp, C.c_int, C.c_int, _dp]),
+    "tdz_ops_destroy": (None, [_vp]),
+    "tdz_ground_state": (C.c_int, [_vp, _dp, _dp]),
+    "tdz_batch_create": (C.c_int, [C.POINTER(_vp), C.c_int, C.c_int, C.POINTER(C.c_int), C.c_int, _vp, C.POINTER(_vp)]),
+    "tdz_batch_set_refinement": (C.c_int, [_vp, C.c_double, C.c_int]),
+    "tdz_batch_info": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int64), C.POINTER(C.c_size_t)]),
+    "tdz_set_state": (C.c_int, [_vp, C.c_int, _vp]),
+    "tdz_get_state": (C.c_int, [_vp, C.c_int, _vp]),
+    "tdz_propagate": (C.c_int, [_vp, _vp, C.c_double, C.c_int64, C.c_int64]),
+    "tdz_observe": (C.c_int, [_vp, C.c_int, _vp, C.POINTER(C.c_int)]),
+    "tdz_refine_stats": (C.c_int, [_vp, _dp, _dp]),
+    "tdz_batch_destroy": (None, [_vp]),
+}
+for _name, (_res, _args) in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+def last_error() -> str:
+    s = _lib.tdz_last_error()
+    return s.decode() if s else ""
+
+
+def _check(code: int, what: str):
+    if code != TDZ_OK:
+        raise TDZError(code, what)
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+def _ptr(x) -> int:
+    """Address of a numpy array (host) or a torch tensor (host or device)."""
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return int(x.data_ptr())
+
+
+class Basis:
+    """B-spline basis on an open knot vector with an nquad-point Gauss rule per span."""
+
+    def __init__(self, knots: Sequence[float], degree: int, nquad: Optional[int] = None):
+        k = np.ascontiguousarray(knots, dtype=np.float64)
+        h = _vp()
+        _check(_lib.tdz_basis_create(_dptr(k), len(k), int(degree), int(nquad or degree + 1), C.byref(h)),
+               "tdz_basis_create")
+        self._h = h
+        nf, ne, p, nq = C.c_int64(), C.c_int64(), C.c_int(), C.c_int()
+        _check(_lib.tdz_basis_info(h, C.byref(nf), C.byref(ne), C.byref(p), C.byref(nq)), "tdz_basis_info")
+        self.nfun, self.nelem, self.degree, self.nquad = nf.value, ne.value, p.value, nq.value
+
+    def eval(self, x):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        val = np.zeros((self.nfun, len(x)))
+        der = np.zeros((self.nfun, len(x)))
+        _check(_lib.tdz_basis_eval(self._h, _dptr(x), len(x), _dptr(val), _dptr(der)), "tdz_basis_eval")
+        return val, der
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            _lib.tdz_basis_destroy(self._h)
+            self._h = None
+
+
+def _medium_struct(med: Dict):
+    m, v = med["mass"], med["potential"]
+    s = _Medium()
+    s.mass_kind = _MASS[m["kind"]]
+    s.pot_kind = _POT[v["kind"]]
+    keep = []
+    mk, vk = m["kind"], v["kind"]
+    if mk == "const":
+        s.mass_par[0] = m["m"]
+    elif mk == "quesne":
+        s.mass_par[0] = m["a"]
+    elif mk == "ellipse":
+        for i, key in enumerate(("a", "b", "m_in", "m_out")):
+            s.mass_par[i] = m[key]
+    if vk == "softcore":
+        s.pot_par[0], s.pot_par[1] = v.get("z", 1.0), v["eps"]
+    elif vk == "ho":
+        for i, w in enumerate(v["omega"]):
+            s.pot_par[i] = w
+    elif vk == "quesne":
+        s.pot_par[0], s.pot_par[1] = v["a"], v["omega"]
+    elif vk == "ellipse":
+        for i, key in enumerate(("a", "b", "v_in", "v_out")):
+            s.pot_par[i] = v[key]
+    elif vk == "h2p_softcore":
+        s.pot_par[0], s.pot_par[1] = v["R"], v["eps"]
+    if mk == "layers" or vk == "layers":
+        b = np.ascontiguousarray(m.get("bounds", v.get("bounds")), dtype=np.float64)
+        s.nlayers = len(b) - 1
+        s.layer_bounds = _dptr(b)
+        keep.append(b)
+        if mk == "layers":
+            lm = np.ascontiguousarray(m["m"], dtype=np.float64)
+            s.layer_mass = _dptr(lm)
+            keep.append(lm)
+        if vk == "layers":
+            lv = np.ascontiguousarray(v["V"], dtype=np.float64)
+            s.layer_pot = _dptr(lv)
+            keep.append(lv)
+    return s, keep
+
+
+class Ops:
+    """Assembled Galerkin operators (S, T_BDD, V, H0, D, G, K) of one geometry."""
+
+    def __init__(self, axes: Sequence[Basis], medium: Dict):
+        arr = (_vp * len(axes))(*[a._h for a in axes])
+        ms, keep = _medium_struct(medium)
+        h = _vp()
+        _check(_lib.tdz_assemble(arr, len(axes), C.byref(ms), C.byref(h)), "tdz_assemble")
+        del keep
+        self._h = h
+        self._axes = list(axes)
+        dim, shape, deg = C.c_int(), (C.c_int64 * 3)(), (C.c_int * 3)()
+        _check(_lib.tdz_ops_info(h, C.byref(dim), shape, deg), "tdz_ops_info")
+        self.dim = dim.value
+        self.shape = [shape[i] for i in range(self.dim)]
+        self.degree = [deg[i] for i in range(self.dim)]
+
+    @property
+    def n(self) -> int:
+        return int(np.prod(self.shape))
+
+    def band(self, which: str, axis: int = 0) -> np.ndarray:
+        out = np.zeros((self.shape[axis], self.degree[axis] + 1))
+        _check(_lib.tdz_ops_band(self._h, MAT[which], axis, _dptr(out)), "tdz_ops_band")
+        return out
+
+    def ground_state(self):
+        e = C.c_double()
+        c = np.zeros(2 * self.n)
+        _check(_lib.tdz_ground_state(self._h, C.byref(e), _dptr(c)), "tdz_ground_state")
+        return e.value, c[0::2] + 1j * c[1::2]
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            _lib.tdz_ops_destroy(self._h)
+            self._h = None
+
+
+def assemble_1d(knots, degree: int, medium: Dict, nquad: Optional[int] = None) -> Ops:
+    return Ops([Basis(knots, degree, nquad)], medium)
+
+
+class Batch:
+    """Independent runs propagated together on the current CUDA device, one persistent launch
+    per propagate() call. `stream` is a raw cudaStream_t handle (int) or None."""
+
+    def __init__(self, ops: Sequence[Ops], run_ops: Sequence[int], precision: int = FP64, stream: Optional[int] = None):
+        arr = (_vp * len(ops))(*[o._h for o in ops])
+        idx = (C.c_int * len(run_ops))(*[int(i) for i in run_ops])
+        h = _vp()
+        _check(_lib.tdz_batch_create(arr, len(ops), len(run_ops), idx, int(precision), _vp(stream or 0), C.byref(h)),
+               "tdz_batch_create")
+        self._h = h
+        self._ops = list(ops)
+        self.run_ops = list(run_ops)
+        self.nruns = len(run_ops)
+        self.precision = precision
+        self.dim = ops[0].dim
+        self._last_nsteps = 0
+        n, dof, nb = C.c_int(), C.c_int64(), C.c_size_t()
+        _check(_lib.tdz_batch_info(h, C.byref(n), C.byref(dof), C.byref(nb)), "tdz_batch_info")
+        self.total_dof, self.device_bytes = dof.value, nb.value
+
+    def set_refinement(self, tol: float, max_solves: int = 6):
+        _check(_lib.tdz_batch_set_refinement(self._h, float(tol), int(max_solves)), "tdz_batch_set_refinement")
+
+    def n_of(self, run: int) -> int:
+        return self._ops[self.run_ops[run]].n
+
+    def set_state(self, run: int, c):
+        """c: complex numpy array (host) or an interleaved float64 torch tensor (host or device)."""
+        if isinstance(c, np.ndarray) and np.iscomplexobj(c):
+            buf = np.ascontiguousarray(np.stack([c.real, c.imag], axis=1).reshape(-1), dtype=np.float64)
+            _check(_lib.tdz_set_state(self._h, run, _vp(_ptr(buf))), "tdz_set_state")
+        else:
+            _check(_lib.tdz_set_state(self._h, run, _vp(_ptr(c))), "tdz_set_state")
+
+    def get_state(self, run: int, out=None):
+        if out is None:
+            buf = np.zeros(2 * self.n_of(run))
+            _check(_lib.tdz_get_state(self._h, run, _vp(_ptr(buf))), "tdz_get_state")
+            return buf[0::2] + 1j * buf[1::2]
+        _check(_lib.tdz_get_state(self._h, run, _vp(_ptr(out))), "tdz_get_state")
+        return out
+
+    def propagate(self, field, dt: float, step0: int, nsteps: int):
+        """field: float64 [nruns, nsteps+1, dim] (numpy host array or torch tensor, host or device)."""
+        if isinstance(field, np.ndarray):
+            field = np.ascontiguousarray(field, dtype=np.float64)
+            assert field.size == self.nruns * (nsteps + 1) * self.dim
+        _check(_lib.tdz_propagate(self._h, _vp(_ptr(field)), float(dt), int(step0), int(nsteps)), "tdz_propagate")
+        self._last_nsteps = nsteps
+
+    def observe(self, run: int, out=None):
+        """Observables [nsteps, 2+3dim]: t, E, d, a, norm. Returns (array, status)."""
+        st = C.c_int()
+        if out is None:
+            out = np.zeros((self._last_nsteps, 2 + 3 * self.dim))
+        _check(_lib.tdz_observe(self._h, run, _vp(_ptr(out)), C.byref(st)), "tdz_observe")
+        return out, st.value
+
+    def refine_stats(self):
+        mx, ns = C.c_double(), C.c_double()
+        _check(_lib.tdz_refine_stats(self._h, C.byref(mx), C.byref(ns)), "tdz_refine_stats")
+        return mx.value, ns.value
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            _lib.tdz_batch_destroy(self._h)
+            self._h = None

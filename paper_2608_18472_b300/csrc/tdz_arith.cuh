@@ -1,0 +1,114 @@
+// Device arithmetic helpers: complex numbers over float/double and double-float ("ff")
+// numbers (an unevaluated sum hi + lo of two FP32 values, 48-bit significand).
+//
+// The ff operations follow the classical error-free transformations:
+//   Knuth's TwoSum (exact a + b = s + e), Dekker's FastTwoSum (|a| >= |b|) and the
+//   FMA-based TwoProduct (exact a * b = p + e with e = fma(a, b, -p)).
+// They are used because the binary64 pipe of sm_103a runs at ~1/70 of the FP32 rate,
+// so per-coefficient residual, correction and quadratic-form arithmetic is done in ff.
+// This file must be compiled without fast-math (IEEE FP32 semantics are required).
+#pragma once
+#include <cuda_runtime.h>
+
+namespace tdz {
+
+#define TDZ_DEV __device__ __forceinline__
+
+// ---------------------------------------------------------------------------- complex
+template <class T>
+struct cx {
+  T r, i;
+};
+template <class T> TDZ_DEV cx<T> mk(T r, T i) { return cx<T>{r, i}; }
+template <class T> TDZ_DEV cx<T> operator+(cx<T> a, cx<T> b) { return {a.r + b.r, a.i + b.i}; }
+template <class T> TDZ_DEV cx<T> operator-(cx<T> a, cx<T> b) { return {a.r - b.r, a.i - b.i}; }
+template <class T> TDZ_DEV cx<T> cmul(cx<T> a, cx<T> b) { return {a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r}; }
+// a - b*c
+template <class T> TDZ_DEV cx<T> cmsub(cx<T> a, cx<T> b, cx<T> c) {
+  return {a.r - b.r * c.r + b.i * c.i, a.i - b.r * c.i - b.i * c.r};
+}
+// a + b*c
+template <class T> TDZ_DEV cx<T> cmadd(cx<T> a, cx<T> b, cx<T> c) {
+  return {a.r + b.r * c.r - b.i * c.i, a.i + b.r * c.i + b.i * c.r};
+}
+template <class T> TDZ_DEV cx<T> crecip(cx<T> a) {
+  T d = a.r * a.r + a.i * a.i;
+  T s = T(1) / d;
+  return {a.r * s, -a.i * s};
+}
+template <class T> TDZ_DEV cx<T> czero() { return {T(0), T(0)}; }
+template <class T> TDZ_DEV T cnorm2(cx<T> a) { return a.r * a.r + a.i * a.i; }
+
+// ---------------------------------------------------------------------------- double-float
+struct ff {
+  float h, l;
+};
+TDZ_DEV ff two_sum(float a, float b) {
+  float s = a + b;
+  float bb = s - a;
+  float e = (a - (s - bb)) + (b - bb);
+  return {s, e};
+}
+TDZ_DEV ff fast_two_sum(float a, float b) {
+  float s = a + b;
+  float e = b - (s - a);
+  return {s, e};
+}
+TDZ_DEV ff ff_add(ff a, ff b) {
+  ff s = two_sum(a.h, b.h);
+  float e = s.l + (a.l + b.l);
+  return fast_two_sum(s.h, e);
+}
+TDZ_DEV ff ff_neg(ff a) { return {-a.h, -a.l}; }
+TDZ_DEV ff ff_sub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
+TDZ_DEV ff ff_mul(ff a, ff b) {
+  float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  return fast_two_sum(p, e);
+}
+TDZ_DEV ff ff_mulf(ff a, float b) {
+  float p = a.h * b;
+  float e = fmaf(a.h, b, -p);
+  e = fmaf(a.l, b, e);
+  return fast_two_sum(p, e);
+}
+TDZ_DEV ff ff_addf(ff a, float b) {
+  ff s = two_sum(a.h, b);
+  float e = s.l + a.l;
+  return fast_two_sum(s.h, e);
+}
+TDZ_DEV float ff_f(ff a) { return a.h + a.l; }
+
+// Dot2-style accumulator (Ogita, Rump, Oishi 2005): the running sum s is kept with a
+// compensation c; each product is added as an exact TwoProduct pair.
+struct ffacc {
+  float s, c;
+};
+TDZ_DEV void acc_zero(ffacc& a) { a.s = 0.f; a.c = 0.f; }
+// a += x * y  with x, y double-float numbers (lo*lo neglected)
+TDZ_DEV void acc_mul(ffacc& a, ff x, ff y) {
+  float p = x.h * y.h;
+  float e = fmaf(x.h, y.h, -p);
+  e = fmaf(x.h, y.l, e);
+  e = fmaf(x.l, y.h, e);
+  ff t = two_sum(a.s, p);
+  a.s = t.h;
+  a.c += t.l + e;
+}
+TDZ_DEV void acc_add(ffacc& a, ff x) {
+  ff t = two_sum(a.s, x.h);
+  a.s = t.h;
+  a.c += t.l + x.l;
+}
+TDZ_DEV ff acc_get(const ffacc& a) { return fast_two_sum(a.s, a.c); }
+
+// complex double-float
+struct cff {
+  ff r, i;
+};
+TDZ_DEV cff cff_add(cff a, cff b) { return {ff_add(a.r, b.r), ff_add(a.i, b.i)}; }
+TDZ_DEV cff cff_addc(cff a, cx<float> b) { return {ff_addf(a.r, b.r), ff_addf(a.i, b.i)}; }
+
+}  // namespace tdz

@@ -1,0 +1,1339 @@
+// Batched 1-D Crank-Nicolson propagation on sm_103a.
+//
+// Method (arXiv 2608.18472, Sec. "Time propagation", Eq. cn_system): per step
+//     (S + i tau H_n) c^{n+1} = (S - i tau H_n) c^n,  tau = dt/2,  H_n = H0 + Ebar_n D,
+// solved here in correction form: c^{n+1} = y0 + delta with
+//     A_n delta = r,  r = B_n c^n - A_n y0 = -S w - i tau H_n (2 c^n + w),  w = y0 - c^n,
+// where A_n = S + i tau H_n is complex symmetric with positive definite Hermitian part S,
+// so an unpivoted LDL^T factorisation is stable. y0 = c^n (binary64 path) or a quadratic
+// extrapolation from the last two steps (mixed path). Observables of Sec. "Dipoles" are
+// reduced after every step.
+//
+// GPU organisation (one warp per run, the whole time loop inside one persistent launch):
+//   * the n rows of a run are split into K <= 32 chunks of m rows, one per lane; the last
+//     P rows of every chunk but the last are a separator ("Sep_k"), the rest its interior;
+//   * sweep 1 (top-down): each lane eliminates its interior with a register-window band
+//     LDL^T, carrying the coupling to the separator above (the "spike") and the right-hand
+//     side; it stores L and D^-1 and leaves the Schur complement of its lower separator;
+//   * sweep 2 (bottom-up): each lane eliminates its interior from the bottom to obtain the
+//     Schur complement of the separator above it (no storage);
+//   * the separators form a block-tridiagonal system (K-1 blocks of P x P), factored and
+//     solved by the whole warp in shared memory (block LDL^T with explicit pivot inverses);
+//   * forward/back substitution of every interior with the separator values;
+//   * state update and observables.
+// All arrays of a run are interleaved [row][lane] so that every warp access is coalesced.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "tdz_arith.cuh"
+#include "tdz_internal.h"
+
+namespace tdz {
+
+constexpr int LANES = 32;
+constexpr int MAXP = 8;
+
+struct GeomDev {
+  int n, m, K, pad;
+  const void* S;   // band arrays [m][P+1][32]: double (binary64 path) or float2 hi/lo (mixed)
+  const void* H;   // H0 = T + V
+  const void* D;
+  const void* G;
+  const void* Km;  // <m^-1> matrix
+};
+
+struct RunDev {
+  int geom;
+  int status;
+  int hist;        // steps of valid difference history (mixed)
+  int pad;
+  void* state;     // binary64: double2 [m][32]; mixed: float4 {hr, hi, lr, li} [m][32]
+  float2* d1;      // mixed: c^n - c^{n-1}
+  float2* d2;      // mixed: c^{n-1} - c^{n-2}
+  float4* W;       // mixed: correction w (double-float complex)
+  void* rhs;       // cx<T> [m][32]
+  void* Lc;        // cx<T> [m][P][32]
+  void* Dv;        // cx<T> [m][32]
+  void* gd;        // cx<T> [m][32]
+  void* dl;        // cx<T> [m][32]
+  double max_rel;  // largest final relative residual (mixed)
+  long long nsolve;
+};
+
+struct StepArgs {
+  const GeomDev* geoms;
+  RunDev* runs;
+  const int* order;
+  int nruns;
+  int* counter;
+  const double* field;  // [run][nsteps+1]
+  double* obs;          // [run][nsteps][5]
+  long long nsteps;
+  long long step0;
+  double dt;
+  double tol;
+  int max_it;
+};
+
+// ============================================================================ band access
+template <int P>
+TDZ_DEV int bidx(int i, int d, int k) { return (i * (P + 1) + d) * LANES + k; }
+TDZ_DEV int ridx(int i, int k) { return i * LANES + k; }
+
+// A(i, i-d) entry for the factorisation, in the solve precision T.
+template <int P, class T, bool MIXED>
+TDZ_DEV cx<T> a_entry(const GeomDev& g, int idx, T tau, T ebar) {
+  if constexpr (MIXED) {
+    float2 s = static_cast<const float2*>(g.S)[idx];
+    float2 h = static_cast<const float2*>(g.H)[idx];
+    float2 d = static_cast<const float2*>(g.D)[idx];
+    return cx<T>{s.x, tau * fmaf(ebar, d.x, h.x)};
+  } else {
+    double s = static_cast<const double*>(g.S)[idx];
+    double h = static_cast<const double*>(g.H)[idx];
+    double d = static_cast<const double*>(g.D)[idx];
+    return cx<T>{s, tau * fma(ebar, d, h)};
+  }
+}
+
+// ============================================================================ per-lane context
+struct Lane {
+  int k, K, m, mI;
+  bool active, up, dn;
+};
+
+template <class T>
+struct Red {  // reduced system in shared memory (one warp)
+  cx<T>* Dg;  // [31][P*P]  diagonal blocks -> pivot inverses
+  cx<T>* E;   // [31][P*P]  sub-diagonal blocks Ŝ(s, s-1) -> F_s
+  cx<T>* rb;  // [31][P]    rhs -> separator solution
+  cx<T>* Wt;  // [P*P]      scratch tile
+};
+
+// ============================================================================ sweep 1 (top-down)
+// Eliminates the interior rows 0..mI-1 of the lane's chunk. Stores L (column-wise: Lc[i][d-1]
+// = L(i+d, i)) and D^-1, and returns in registers the Schur complement of the rows mI..mI+P-1
+// (the lane's separator), their coupling to the separator above and their reduced rhs.
+template <int P, class T, bool MIXED>
+TDZ_DEV void sweep1(const GeomDev& g, const RunDev& run, const Lane& L, T tau, T ebar, Red<T>& red) {
+  cx<T> w[P + 1][P + 1];
+  cx<T> cw[P + 1][P];
+  cx<T> rw[P + 1];
+  const cx<T>* rhs = static_cast<const cx<T>*>(run.rhs);
+  cx<T>* Lc = static_cast<cx<T>*>(run.Lc);
+  cx<T>* Dv = static_cast<cx<T>*>(run.Dv);
+  const int k = L.k;
+#pragma unroll
+  for (int a = 0; a < P; ++a) {
+#pragma unroll
+    for (int b = 0; b <= a; ++b) w[a][b] = a_entry<P, T, MIXED>(g, bidx<P>(a, a - b, k), tau, ebar);
+#pragma unroll
+    for (int j = 0; j < P; ++j)
+      cw[a][j] = (L.up && a <= j) ? a_entry<P, T, MIXED>(g, bidx<P>(a, a + P - j, k), tau, ebar) : czero<T>();
+    rw[a] = rhs[ridx(a, k)];
+  }
+  for (int i = 0; i < L.mI; ++i) {
+    const int r = i + P;  // row entering the window
+    if (r < L.m) {
+#pragma unroll
+      for (int b = 0; b <= P; ++b) w[P][b] = a_entry<P, T, MIXED>(g, bidx<P>(r, P - b, k), tau, ebar);
+      rw[P] = rhs[ridx(r, k)];
+    } else {
+#pragma unroll
+      for (int b = 0; b <= P; ++b) w[P][b] = czero<T>();
+      rw[P] = czero<T>();
+    }
+#pragma unroll
+    for (int j = 0; j < P; ++j) cw[P][j] = czero<T>();
+    const cx<T> dinv = crecip(w[0][0]);
+    cx<T> l[P + 1];
+#pragma unroll
+    for (int a = 1; a <= P; ++a) {
+      l[a] = cmul(w[a][0], dinv);
+      Lc[(i * P + a - 1) * LANES + k] = l[a];
+    }
+    Dv[ridx(i, k)] = dinv;
+#pragma unroll
+    for (int a = 1; a <= P; ++a) {
+#pragma unroll
+      for (int b = 1; b <= a; ++b) w[a][b] = cmsub(w[a][b], l[a], w[b][0]);
+#pragma unroll
+      for (int j = 0; j < P; ++j) cw[a][j] = cmsub(cw[a][j], l[a], cw[0][j]);
+      rw[a] = cmsub(rw[a], l[a], rw[0]);
+    }
+#pragma unroll
+    for (int a = 0; a < P; ++a) {
+#pragma unroll
+      for (int b = 0; b <= a; ++b) w[a][b] = w[a + 1][b + 1];
+#pragma unroll
+      for (int j = 0; j < P; ++j) cw[a][j] = cw[a + 1][j];
+      rw[a] = rw[a + 1];
+    }
+  }
+  if (L.dn) {
+    cx<T>* Dg = red.Dg + k * P * P;
+    cx<T>* E = red.E + k * P * P;
+#pragma unroll
+    for (int a = 0; a < P; ++a) {
+#pragma unroll
+      for (int b = 0; b <= a; ++b) {
+        Dg[a * P + b] = w[a][b];
+        Dg[b * P + a] = w[a][b];
+      }
+#pragma unroll
+      for (int j = 0; j < P; ++j) E[a * P + j] = cw[a][j];
+      red.rb[k * P + a] = rw[a];
+    }
+  }
+}
+
+// ============================================================================ sweep 2 (bottom-up)
+// Eliminates the interior from its last row upwards with the separator above (rows -P..-1)
+// entering with zero self block and zero rhs: what remains is -C^T A_II^-1 C and -C^T A_II^-1 b
+// for that separator; added into the shared reduced system.
+template <int P, class T, bool MIXED>
+TDZ_DEV void sweep2(const GeomDev& g, const RunDev& run, const Lane& L, T tau, T ebar, Red<T>& red) {
+  cx<T> w[P + 1][P + 1];  // w[a][b] = A(r-a, r-b), b <= a, r = current pivot row
+  cx<T> rw[P + 1];
+  const cx<T>* rhs = static_cast<const cx<T>*>(run.rhs);
+  const int k = L.k;
+  const int r0 = L.mI - 1;
+#pragma unroll
+  for (int a = 0; a < P; ++a) {
+#pragma unroll
+    for (int b = 0; b <= a; ++b) w[a][b] = a_entry<P, T, MIXED>(g, bidx<P>(r0 - b, a - b, k), tau, ebar);
+    rw[a] = rhs[ridx(r0 - a, k)];
+  }
+  for (int t = 0; t < L.mI; ++t) {
+    const int r = r0 - t;
+    const int q = r - P;  // row entering the window
+#pragma unroll
+    for (int b = 0; b <= P; ++b) {
+      const int rb = r - b;  // A(q, rb) stored at row rb (rb >= q), diagonal P - b
+      w[P][b] = (rb >= 0) ? a_entry<P, T, MIXED>(g, bidx<P>(rb, P - b, k), tau, ebar) : czero<T>();
+    }
+    rw[P] = (q >= 0) ? rhs[ridx(q, k)] : czero<T>();
+    const cx<T> dinv = crecip(w[0][0]);
+    cx<T> l[P + 1];
+#pragma unroll
+    for (int a = 1; a <= P; ++a) l[a] = cmul(w[a][0], dinv);
+#pragma unroll
+    for (int a = 1; a <= P; ++a) {
+#pragma unroll
+      for (int b = 1; b <= a; ++b) w[a][b] = cmsub(w[a][b], l[a], w[b][0]);
+      rw[a] = cmsub(rw[a], l[a], rw[0]);
+    }
+#pragma unroll
+    for (int a = 0; a < P; ++a) {
+#pragma unroll
+      for (int b = 0; b <= a; ++b) w[a][b] = w[a + 1][b + 1];
+      rw[a] = rw[a + 1];
+    }
+  }
+  // window rows -1..-P  <->  separator (k-1) local index j = P-1-a
+  cx<T>* Dg = red.Dg + (k - 1) * P * P;
+#pragma unroll
+  for (int a = 0; a < P; ++a) {
+    const int ja = P - 1 - a;
+#pragma unroll
+    for (int b = 0; b <= a; ++b) {
+      const int jb = P - 1 - b;
+      Dg[ja * P + jb] = Dg[ja * P + jb] + w[a][b];
+      if (ja != jb) Dg[jb * P + ja] = Dg[jb * P + ja] + w[a][b];
+    }
+    red.rb[(k - 1) * P + ja] = red.rb[(k - 1) * P + ja] + rw[a];
+  }
+}
+
+// ============================================================================ reduced system
+template <int P, class T>
+TDZ_DEV void red_invert(cx<T>* M, int lane) {
+  // in-place Gauss-Jordan inversion (no pivoting) of a P x P complex symmetric block
+  for (int q = 0; q < P; ++q) {
+    cx<T> piv = crecip(M[q * P + q]);
+    cx<T> nv[2];
+    int cnt = 0;
+    for (int t = lane; t < P * P; t += LANES, ++cnt) {
+      int r = t / P, c = t % P;
+      cx<T> v;
+      if (r == q && c == q) v = piv;
+      else if (r == q) v = cmul(M[q * P + c], piv);
+      else if (c == q) v = czero<T>() - cmul(M[r * P + q], piv);
+      else v = cmsub(M[r * P + c], cmul(M[r * P + q], piv), M[q * P + c]);
+      nv[cnt] = v;
+    }
+    __syncwarp();
+    cnt = 0;
+    for (int t = lane; t < P * P; t += LANES, ++cnt) M[t] = nv[cnt];
+    __syncwarp();
+  }
+}
+
+template <int P, class T>
+TDZ_DEV void red_factor(Red<T>& red, int nsep, int lane) {
+  for (int s = 0; s < nsep; ++s) {
+    cx<T>* D = red.Dg + s * P * P;
+    if (s > 0) {
+      const cx<T>* Pinv = red.Dg + (s - 1) * P * P;
+      cx<T>* E = red.E + s * P * P;
+      // F = E * Pinv
+      for (int t = lane; t < P * P; t += LANES) {
+        int r = t / P, c = t % P;
+        cx<T> acc = czero<T>();
+#pragma unroll
+        for (int q = 0; q < P; ++q) acc = cmadd(acc, E[r * P + q], Pinv[q * P + c]);
+        red.Wt[t] = acc;
+      }
+      __syncwarp();
+      // D -= F * E^T ; E <- F
+      cx<T> nv[2];
+      int cnt = 0;
+      for (int t = lane; t < P * P; t += LANES, ++cnt) {
+        int r = t / P, c = t % P;
+        cx<T> acc = D[t];
+#pragma unroll
+        for (int q = 0; q < P; ++q) acc = cmsub(acc, red.Wt[r * P + q], E[c * P + q]);
+        nv[cnt] = acc;
+      }
+      __syncwarp();
+      cnt = 0;
+      for (int t = lane; t < P * P; t += LANES, ++cnt) {
+        D[t] = nv[cnt];
+        E[t] = red.Wt[t];
+      }
+      __syncwarp();
+    }
+    red_invert<P, T>(D, lane);
+  }
+}
+
+// in-place: rb (rhs) -> separator solution
+template <int P, class T>
+TDZ_DEV void red_solve(Red<T>& red, int nsep, int lane) {
+  for (int s = 1; s < nsep; ++s) {  // y_s = b_s - F_s y_{s-1}
+    cx<T> v = czero<T>();
+    if (lane < P) {
+      const cx<T>* F = red.E + s * P * P;
+      v = red.rb[s * P + lane];
+#pragma unroll
+      for (int q = 0; q < P; ++q) v = cmsub(v, F[lane * P + q], red.rb[(s - 1) * P + q]);
+    }
+    __syncwarp();
+    if (lane < P) red.rb[s * P + lane] = v;
+    __syncwarp();
+  }
+  for (int s = nsep - 1; s >= 0; --s) {  // x_s = Pinv_s y_s - F_{s+1}^T x_{s+1}
+    cx<T> v = czero<T>();
+    if (lane < P) {
+      const cx<T>* Pi = red.Dg + s * P * P;
+#pragma unroll
+      for (int q = 0; q < P; ++q) v = cmadd(v, Pi[lane * P + q], red.rb[s * P + q]);
+      if (s + 1 < nsep) {
+        const cx<T>* F = red.E + (s + 1) * P * P;
+#pragma unroll
+        for (int q = 0; q < P; ++q) v = cmsub(v, F[q * P + lane], red.rb[(s + 1) * P + q]);
+      }
+    }
+    __syncwarp();
+    if (lane < P) red.rb[s * P + lane] = v;
+    __syncwarp();
+  }
+}
+
+// ============================================================================ substitution
+// Forward: g = L^-1 b' with b' = rhs - A(I, Sep_{k-1}) x_up, store g D^-1.
+// Backward: x = L^-T (g D^-1) - (L_SI)^T x_dn, where L_SI are the multipliers sweep 1 stored for
+// the lower separator rows (A_II^-1 A_IS = L^-T L_SI^T), so the lower coupling enters only here.
+// Writes the interior and the lane's own separator solution to dl.
+template <int P, class T, bool MIXED>
+TDZ_DEV void substitute(const GeomDev& g, const RunDev& run, const Lane& L, T tau, T ebar, const Red<T>& red) {
+  const int k = L.k;
+  const cx<T>* rhs = static_cast<const cx<T>*>(run.rhs);
+  const cx<T>* Lc = static_cast<const cx<T>*>(run.Lc);
+  const cx<T>* Dv = static_cast<const cx<T>*>(run.Dv);
+  cx<T>* gd = static_cast<cx<T>*>(run.gd);
+  cx<T>* dl = static_cast<cx<T>*>(run.dl);
+  cx<T> xup[P], xdn[P];
+#pragma unroll
+  for (int j = 0; j < P; ++j) {
+    xup[j] = L.up ? red.rb[(k - 1) * P + j] : czero<T>();
+    xdn[j] = L.dn ? red.rb[k * P + j] : czero<T>();
+  }
+  cx<T> gw[P + 1];  // gw[d] = g_{i-d}
+#pragma unroll
+  for (int d = 0; d <= P; ++d) gw[d] = czero<T>();
+  for (int i = 0; i < L.mI; ++i) {
+    cx<T> b = rhs[ridx(i, k)];
+    if (L.up && i < P) {
+#pragma unroll
+      for (int j = 0; j < P; ++j)
+        if (j >= i) b = cmsub(b, a_entry<P, T, MIXED>(g, bidx<P>(i, i + P - j, k), tau, ebar), xup[j]);
+    }
+#pragma unroll
+    for (int d = 1; d <= P; ++d)
+      if (i - d >= 0) b = cmsub(b, Lc[((i - d) * P + d - 1) * LANES + k], gw[d]);
+#pragma unroll
+    for (int d = P; d >= 2; --d) gw[d] = gw[d - 1];
+    gw[1] = b;
+    gd[ridx(i, k)] = cmul(b, Dv[ridx(i, k)]);
+  }
+  cx<T> xw[P + 1];  // xw[d] = x_{i+d}
+#pragma unroll
+  for (int d = 1; d <= P; ++d) xw[d] = xdn[d - 1];
+  for (int i = L.mI - 1; i >= 0; --i) {
+    cx<T> x = gd[ridx(i, k)];
+#pragma unroll
+    for (int d = 1; d <= P; ++d) x = cmsub(x, Lc[(i * P + d - 1) * LANES + k], xw[d]);
+#pragma unroll
+    for (int d = P; d >= 2; --d) xw[d] = xw[d - 1];
+    xw[1] = x;
+    dl[ridx(i, k)] = x;
+  }
+  if (L.dn) {
+#pragma unroll
+    for (int j = 0; j < P; ++j) dl[ridx(L.mI + j, k)] = xdn[j];
+  }
+}
+
+template <int P, class T, bool MIXED>
+TDZ_DEV void solve(const GeomDev& g, const RunDev& run, const Lane& L, T tau, T ebar, Red<T>& red, int lane) {
+  if (L.active) sweep1<P, T, MIXED>(g, run, L, tau, ebar, red);
+  __syncwarp();
+  if (L.active && L.up) sweep2<P, T, MIXED>(g, run, L, tau, ebar, red);
+  __syncwarp();
+  const int nsep = L.K - 1;
+  if (nsep > 0) {
+    red_factor<P, T>(red, nsep, lane);
+    red_solve<P, T>(red, nsep, lane);
+  }
+  __syncwarp();
+  if (L.active) substitute<P, T, MIXED>(g, run, L, tau, ebar, red);
+  __syncwarp();
+}
+
+// ============================================================================ row helpers
+// Location of local row j of lane k's chunk, possibly in a neighbouring chunk; false if none.
+TDZ_DEV bool locate(const Lane& L, int j, int& row, int& chunk) {
+  chunk = L.k;
+  row = j;
+  if (j < 0) {
+    chunk = L.k - 1;
+    row = j + L.m;
+  } else if (j >= L.m) {
+    chunk = L.k + 1;
+    row = j - L.m;
+  }
+  return chunk >= 0 && chunk < L.K;
+}
+
+// ============================================================================ binary64 rhs
+// r = -i tau H_n (2 c), scatter form over rows -P..m+P-1 with pending sums for P+1 rows.
+template <int P>
+TDZ_DEV void rhs_fp64(const GeomDev& g, const RunDev& run, const Lane& L, double tau, double ebar) {
+  const double2* c = static_cast<const double2*>(run.state);
+  cx<double>* rhs = static_cast<cx<double>*>(run.rhs);
+  cx<double> uw[P + 1];   // uw[d] = u_{j-d}
+  cx<double> acc[P + 1];  // acc[d] = pending H u for row j-d
+#pragma unroll
+  for (int d = 0; d <= P; ++d) {
+    uw[d] = czero<double>();
+    acc[d] = czero<double>();
+  }
+  for (int j = -P; j < L.m + P; ++j) {
+    int row, chunk;
+    const bool ok = locate(L, j, row, chunk);
+    cx<double> u = czero<double>();
+    double h[P + 1];
+#pragma unroll
+    for (int d = 0; d <= P; ++d) h[d] = 0.0;
+    if (ok) {
+      double2 cc = c[ridx(row, chunk)];
+      u = cx<double>{2.0 * cc.x, 2.0 * cc.y};
+      if (j >= 0) {
+#pragma unroll
+        for (int d = 0; d <= P; ++d) {
+          const int idx = bidx<P>(row, d, chunk);
+          h[d] = tau * fma(ebar, static_cast<const double*>(g.D)[idx], static_cast<const double*>(g.H)[idx]);
+        }
+      }
+    }
+    // shift pending sums: acc[d] now refers to row j-d
+#pragma unroll
+    for (int d = P; d >= 1; --d) {
+      acc[d] = acc[d - 1];
+      uw[d] = uw[d - 1];
+    }
+    uw[0] = u;
+    acc[0] = czero<double>();
+    if (j >= 0 && j < L.m) {  // row j's own sum: lower part
+#pragma unroll
+      for (int d = 0; d <= P; ++d) {
+        acc[0].r += h[d] * uw[d].r;
+        acc[0].i += h[d] * uw[d].i;
+      }
+    }
+    // upper contributions of row j to rows j-d
+#pragma unroll
+    for (int d = 1; d <= P; ++d) {
+      if (j - d >= 0 && j - d < L.m) {
+        acc[d].r += h[d] * u.r;
+        acc[d].i += h[d] * u.i;
+      }
+    }
+    const int jf = j - P;  // row complete
+    if (jf >= 0 && jf < L.m) {
+      // r = -i * acc  ->  (acc.i, -acc.r)
+      rhs[ridx(jf, L.k)] = cx<double>{acc[P].i, -acc[P].r};
+    }
+  }
+}
+
+// ============================================================================ double-float rhs
+// r = -S w - i (tau H_n) u,  u = 2c + w, all products in double-float. Also accumulates
+// ||r||^2 and ||S c||^2 (FP32 scale) for the relative residual.
+template <int P>
+TDZ_DEV void rhs_mixed(const GeomDev& g, const RunDev& run, const Lane& L, ff tau, ff ebar, float& rr, float& bb) {
+  const float4* c = static_cast<const float4*>(run.state);
+  const float4* W = run.W;
+  cx<float>* rhs = static_cast<cx<float>*>(run.rhs);
+  cff uw[P + 1], ww[P + 1];
+  float2 cw[P + 1];          // FP32 copy of c for the scale
+  ffacc ar[P + 1], ai[P + 1];
+  cx<float> sc[P + 1];
+#pragma unroll
+  for (int d = 0; d <= P; ++d) {
+    uw[d] = cff{{0.f, 0.f}, {0.f, 0.f}};
+    ww[d] = uw[d];
+    cw[d] = make_float2(0.f, 0.f);
+    acc_zero(ar[d]);
+    acc_zero(ai[d]);
+    sc[d] = czero<float>();
+  }
+  rr = 0.f;
+  bb = 0.f;
+  for (int j = -P; j < L.m + P; ++j) {
+    int row, chunk;
+    const bool ok = locate(L, j, row, chunk);
+    cff u = cff{{0.f, 0.f}, {0.f, 0.f}}, w = u;
+    float2 chi = make_float2(0.f, 0.f);
+    ff s[P + 1], h[P + 1];
+#pragma unroll
+    for (int d = 0; d <= P; ++d) s[d] = h[d] = ff{0.f, 0.f};
+    if (ok) {
+      const float4 cc = c[ridx(row, chunk)];
+      const float4 wq = W[ridx(row, chunk)];
+      w = cff{{wq.x, wq.z}, {wq.y, wq.w}};
+      const cff c2 = cff{{2.f * cc.x, 2.f * cc.z}, {2.f * cc.y, 2.f * cc.w}};
+      u = cff_add(c2, w);
+      chi = make_float2(cc.x, cc.y);
+      if (j >= 0) {
+#pragma unroll
+        for (int d = 0; d <= P; ++d) {
+          const int idx = bidx<P>(row, d, chunk);
+          const float2 sv = static_cast<const float2*>(g.S)[idx];
+          const float2 hv = static_cast<const float2*>(g.H)[idx];
+          const float2 dv = static_cast<const float2*>(g.D)[idx];
+          s[d] = ff{sv.x, sv.y};
+          // tau * (H0 + Ebar D)
+          h[d] = ff_mul(tau, ff_add(ff{hv.x, hv.y}, ff_mul(ebar, ff{dv.x, dv.y})));
+        }
+      }
+    }
+#pragma unroll
+    for (int d = P; d >= 1; --d) {
+      ar[d] = ar[d - 1];
+      ai[d] = ai[d - 1];
+      sc[d] = sc[d - 1];
+      uw[d] = uw[d - 1];
+      ww[d] = ww[d - 1];
+      cw[d] = cw[d - 1];
+    }
+    uw[0] = u;
+    ww[0] = w;
+    cw[0] = chi;
+    acc_zero(ar[0]);
+    acc_zero(ai[0]);
+    sc[0] = czero<float>();
+    // r.re = -S w.re + (tau H) u.im ;  r.im = -S w.im - (tau H) u.re
+    if (j >= 0 && j < L.m) {
+#pragma unroll
+      for (int d = 0; d <= P; ++d) {
+        acc_mul(ar[0], ff_neg(s[d]), ww[d].r);
+        acc_mul(ar[0], h[d], uw[d].i);
+        acc_mul(ai[0], ff_neg(s[d]), ww[d].i);
+        acc_mul(ai[0], ff_neg(h[d]), uw[d].r);
+        sc[0].r = fmaf(s[d].h, cw[d].x, sc[0].r);
+        sc[0].i = fmaf(s[d].h, cw[d].y, sc[0].i);
+      }
+    }
+#pragma unroll
+    for (int d = 1; d <= P; ++d) {
+      if (j - d >= 0 && j - d < L.m) {
+        acc_mul(ar[d], ff_neg(s[d]), w.r);
+        acc_mul(ar[d], h[d], u.i);
+        acc_mul(ai[d], ff_neg(s[d]), w.i);
+        acc_mul(ai[d], ff_neg(h[d]), u.r);
+        sc[d].r = fmaf(s[d].h, chi.x, sc[d].r);
+        sc[d].i = fmaf(s[d].h, chi.y, sc[d].i);
+      }
+    }
+    const int jf = j - P;
+    if (jf >= 0 && jf < L.m) {
+      const cx<float> r = cx<float>{ff_f(acc_get(ar[P])), ff_f(acc_get(ai[P]))};
+      rhs[ridx(jf, L.k)] = r;
+      rr = fmaf(r.r, r.r, fmaf(r.i, r.i, rr));
+      bb = fmaf(sc[P].r, sc[P].r, fmaf(sc[P].i, sc[P].i, bb));
+    }
+  }
+}
+
+// ============================================================================ FP32 residual check
+// r1 = rhs - A delta in FP32 (valid as a convergence measure when |delta| << |c|).
+template <int P>
+TDZ_DEV float resid_fp32(const GeomDev& g, const RunDev& run, const Lane& L, float tau, float ebar) {
+  const cx<float>* dl = static_cast<const cx<float>*>(run.dl);
+  const cx<float>* rhs = static_cast<const cx<float>*>(run.rhs);
+  cx<float> xw[P + 1], acc[P + 1];
+#pragma unroll
+  for (int d = 0; d <= P; ++d) xw[d] = acc[d] = czero<float>();
+  float rr = 0.f;
+  for (int j = -P; j < L.m + P; ++j) {
+    int row, chunk;
+    const bool ok = locate(L, j, row, chunk);
+    cx<float> x = czero<float>();
+    cx<float> a[P + 1];
+#pragma unroll
+    for (int d = 0; d <= P; ++d) a[d] = czero<float>();
+    if (ok) {
+      x = dl[ridx(row, chunk)];
+      if (j >= 0) {
+#pragma unroll
+        for (int d = 0; d <= P; ++d) a[d] = a_entry<P, float, true>(g, bidx<P>(row, d, chunk), tau, ebar);
+      }
+    }
+#pragma unroll
+    for (int d = P; d >= 1; --d) {
+      acc[d] = acc[d - 1];
+      xw[d] = xw[d - 1];
+    }
+    xw[0] = x;
+    acc[0] = czero<float>();
+    if (j >= 0 && j < L.m) {
+#pragma unroll
+      for (int d = 0; d <= P; ++d) acc[0] = cmadd(acc[0], a[d], xw[d]);
+    }
+#pragma unroll
+    for (int d = 1; d <= P; ++d)
+      if (j - d >= 0 && j - d < L.m) acc[d] = cmadd(acc[d], a[d], x);
+    const int jf = j - P;
+    if (jf >= 0 && jf < L.m) {
+      const cx<float> r = rhs[ridx(jf, L.k)] - acc[P];
+      rr = fmaf(r.r, r.r, fmaf(r.i, r.i, rr));
+    }
+  }
+  return rr;
+}
+
+// ============================================================================ observables
+// c^H M c = sum_j M_jj |c_j|^2 + 2 sum_{d>=1} M(j, j-d) Re(conj(c_j) c_{j-d}) for M = S, D, G, K.
+template <int P>
+TDZ_DEV void observe_fp64(const GeomDev& g, const RunDev& run, const Lane& L, double out[4]) {
+  const double2* c = static_cast<const double2*>(run.state);
+  double2 cwin[P + 1];
+#pragma unroll
+  for (int d = 0; d <= P; ++d) cwin[d] = make_double2(0.0, 0.0);
+  double s = 0, dd = 0, gg = 0, kk = 0;
+  for (int j = -P; j < L.m; ++j) {
+    int row, chunk;
+    const bool ok = locate(L, j, row, chunk);
+    const double2 cj = ok ? c[ridx(row, chunk)] : make_double2(0.0, 0.0);
+#pragma unroll
+    for (int d = P; d >= 1; --d) cwin[d] = cwin[d - 1];
+    cwin[0] = cj;
+    if (j >= 0) {
+#pragma unroll
+      for (int d = 0; d <= P; ++d) {
+        const double u = (d == 0 ? 1.0 : 2.0) * (cj.x * cwin[d].x + cj.y * cwin[d].y);
+        const int idx = bidx<P>(row, d, chunk);
+        s = fma(static_cast<const double*>(g.S)[idx], u, s);
+        dd = fma(static_cast<const double*>(g.D)[idx], u, dd);
+        gg = fma(static_cast<const double*>(g.G)[idx], u, gg);
+        kk = fma(static_cast<const double*>(g.Km)[idx], u, kk);
+      }
+    }
+  }
+  out[0] = s;
+  out[1] = dd;
+  out[2] = gg;
+  out[3] = kk;
+}
+
+template <int P>
+TDZ_DEV void observe_mixed(const GeomDev& g, const RunDev& run, const Lane& L, double out[4]) {
+  const float4* c = static_cast<const float4*>(run.state);
+  cff cwin[P + 1];
+#pragma unroll
+  for (int d = 0; d <= P; ++d) cwin[d] = cff{{0.f, 0.f}, {0.f, 0.f}};
+  ffacc s, dd, gg, kk;
+  acc_zero(s);
+  acc_zero(dd);
+  acc_zero(gg);
+  acc_zero(kk);
+  for (int j = -P; j < L.m; ++j) {
+    int row, chunk;
+    const bool ok = locate(L, j, row, chunk);
+    cff cj = cff{{0.f, 0.f}, {0.f, 0.f}};
+    if (ok) {
+      const float4 q = c[ridx(row, chunk)];
+      cj = cff{{q.x, q.z}, {q.y, q.w}};
+    }
+#pragma unroll
+    for (int d = P; d >= 1; --d) cwin[d] = cwin[d - 1];
+    cwin[0] = cj;
+    if (j >= 0) {
+#pragma unroll
+      for (int d = 0; d <= P; ++d) {
+        ffacc ua;
+        acc_zero(ua);
+        acc_mul(ua, cj.r, cwin[d].r);
+        acc_mul(ua, cj.i, cwin[d].i);
+        ff u = acc_get(ua);
+        if (d > 0) u = ff{2.f * u.h, 2.f * u.l};
+        const int idx = bidx<P>(row, d, chunk);
+        const float2 sv = static_cast<const float2*>(g.S)[idx];
+        const float2 dv = static_cast<const float2*>(g.D)[idx];
+        const float2 gv = static_cast<const float2*>(g.G)[idx];
+        const float2 kv = static_cast<const float2*>(g.Km)[idx];
+        acc_mul(s, ff{sv.x, sv.y}, u);
+        acc_mul(dd, ff{dv.x, dv.y}, u);
+        acc_mul(gg, ff{gv.x, gv.y}, u);
+        acc_mul(kk, ff{kv.x, kv.y}, u);
+      }
+    }
+  }
+  ff fs = acc_get(s), fd = acc_get(dd), fg = acc_get(gg), fk = acc_get(kk);
+  out[0] = (double)fs.h + (double)fs.l;
+  out[1] = (double)fd.h + (double)fd.l;
+  out[2] = (double)fg.h + (double)fg.l;
+  out[3] = (double)fk.h + (double)fk.l;
+}
+
+TDZ_DEV double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ============================================================================ the kernel
+template <int P, bool MIXED>
+__global__ void __launch_bounds__(256) cn1d_kernel(StepArgs A) {
+  using T = typename std::conditional<MIXED, float, double>::type;
+  extern __shared__ unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const size_t per_warp = (size_t)(2 * 31 * P * P + 31 * P + P * P) * sizeof(cx<T>);
+  cx<T>* base = reinterpret_cast<cx<T>*>(smem_raw + wib * per_warp);
+  Red<T> red;
+  red.Dg = base;
+  red.E = base + 31 * P * P;
+  red.rb = base + 2 * 31 * P * P;
+  red.Wt = base + 2 * 31 * P * P + 31 * P;
+
+  while (true) {
+    int item = 0;
+    if (lane == 0) item = atomicAdd(A.counter, 1);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= A.nruns) break;
+    const int rid = A.order[item];
+    RunDev run = A.runs[rid];
+    const GeomDev g = A.geoms[run.geom];
+    Lane L;
+    L.k = lane;
+    L.K = g.K;
+    L.m = g.m;
+    L.active = lane < g.K;
+    L.up = L.active && lane >= 1;
+    L.dn = L.active && lane < g.K - 1;
+    L.mI = L.dn ? g.m - P : g.m;
+    const double* E = A.field + (size_t)rid * (A.nsteps + 1);
+    double* obs = A.obs + (size_t)rid * A.nsteps * 5;
+    int status = run.status;
+    double max_rel = 0.0;
+    long long nsolve = 0;
+    int hist = run.hist;
+    for (long long s = 0; s < A.nsteps && status == TDZ_OK; ++s) {
+      const double ebar_d = 0.5 * (E[s] + E[s + 1]);
+      const double tau_d = 0.5 * A.dt;
+      if constexpr (!MIXED) {
+        if (L.active) rhs_fp64<P>(g, run, L, tau_d, ebar_d);
+        __syncwarp();
+        solve<P, double, false>(g, run, L, tau_d, ebar_d, red, lane);
+        nsolve++;
+        if (L.active) {  // c += delta
+          double2* c = static_cast<double2*>(run.state);
+          const cx<double>* dl = static_cast<const cx<double>*>(run.dl);
+          for (int i = 0; i < L.m; ++i) {
+            double2 v = c[ridx(i, lane)];
+            const cx<double> x = dl[ridx(i, lane)];
+            c[ridx(i, lane)] = make_double2(v.x + x.r, v.y + x.i);
+          }
+        }
+      } else {
+        const float tau_f = (float)tau_d, ebar_f = (float)ebar_d;
+        const ff tau_ff = ff{tau_f, (float)(tau_d - (double)tau_f)};
+        const ff ebar_ff = ff{ebar_f, (float)(ebar_d - (double)ebar_f)};
+        bool ok = false;
+        double rel = 0.0;
+        for (int it = 0; it <= A.max_it; ++it) {
+          float rr = 0.f, bb = 0.f;
+          if (L.active) rhs_mixed<P>(g, run, L, tau_ff, ebar_ff, rr, bb);
+          const double rrs = warp_sum((double)rr), bbs = warp_sum((double)bb);
+          rel = sqrt(rrs / fmax(bbs, 1e-300));
+          if (it > 0 && rel <= A.tol) {
+            ok = true;
+            break;
+          }
+          if (it == A.max_it) break;
+          __syncwarp();
+          solve<P, float, true>(g, run, L, tau_f, ebar_f, red, lane);
+          nsolve++;
+          if (L.active) {  // w += delta (double-float)
+            const cx<float>* dl = static_cast<const cx<float>*>(run.dl);
+            for (int i = 0; i < L.m; ++i) {
+              const float4 q = run.W[ridx(i, lane)];
+              const cx<float> x = dl[ridx(i, lane)];
+              const ff wr = ff_addf(ff{q.x, q.z}, x.r), wi = ff_addf(ff{q.y, q.w}, x.i);
+              run.W[ridx(i, lane)] = make_float4(wr.h, wi.h, wr.l, wi.l);
+            }
+          }
+          __syncwarp();
+          if (it == 0 && hist >= 2) {
+            float r1 = 0.f;
+            if (L.active) r1 = resid_fp32<P>(g, run, L, tau_f, ebar_f);
+            const double r1s = warp_sum((double)r1);
+            rel = sqrt(r1s / fmax(bbs, 1e-300));
+            if (rel <= A.tol) {
+              ok = true;
+              break;
+            }
+          }
+          __syncwarp();
+        }
+        max_rel = fmax(max_rel, rel);
+        if (!ok && status == TDZ_OK) status = TDZ_ENOCONV;
+        // c += w; history; next predictor
+        hist = hist + 1;
+        if (L.active) {
+          float4* c = static_cast<float4*>(run.state);
+          for (int i = 0; i < L.m; ++i) {
+            const float4 q = c[ridx(i, lane)];
+            const float4 wq = run.W[ridx(i, lane)];
+            const ff cr = ff_add(ff{q.x, q.z}, ff{wq.x, wq.z});
+            const ff ci = ff_add(ff{q.y, q.w}, ff{wq.y, wq.w});
+            c[ridx(i, lane)] = make_float4(cr.h, ci.h, cr.l, ci.l);
+            const float2 n1 = make_float2(wq.x + wq.z, wq.y + wq.w);
+            const float2 o1 = run.d1[ridx(i, lane)];
+            run.d2[ridx(i, lane)] = o1;
+            run.d1[ridx(i, lane)] = n1;
+            float2 e = make_float2(0.f, 0.f);
+            if (hist >= 2) e = make_float2(2.f * n1.x - o1.x, 2.f * n1.y - o1.y);
+            run.W[ridx(i, lane)] = make_float4(e.x, e.y, 0.f, 0.f);
+          }
+        }
+      }
+      __syncwarp();
+      double o[4] = {0, 0, 0, 0};
+      if (L.active) {
+        if constexpr (MIXED) observe_mixed<P>(g, run, L, o);
+        else observe_fp64<P>(g, run, L, o);
+      }
+      const double ns = warp_sum(o[0]), ds = warp_sum(o[1]), gs = warp_sum(o[2]), ks = warp_sum(o[3]);
+      const double Et = E[s + 1];
+      if (lane == 0) {
+        double* row = obs + s * 5;
+        row[0] = (double)(A.step0 + s + 1) * A.dt;
+        row[1] = Et;
+        row[2] = ds;
+        row[3] = -gs - Et * ks;
+        row[4] = ns;
+      }
+      if (!isfinite(ns) || !isfinite(ds)) status = TDZ_ENONFINITE;
+      __syncwarp();
+    }
+    if (lane == 0) {
+      A.runs[rid].status = status;
+      A.runs[rid].hist = hist;
+      A.runs[rid].max_rel = fmax(run.max_rel, max_rel);
+      A.runs[rid].nsolve = run.nsolve + nsolve;
+    }
+    __syncwarp();
+  }
+}
+
+}  // namespace tdz
+
+// ============================================================================ host side
+using namespace tdz;
+
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+int cuda_fail(cudaError_t e, const char* what) {
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return TDZ_ECUDA;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+size_t smem_per_warp(int P, bool mixed) {
+  const size_t cxsz = mixed ? 8 : 16;
+  return (size_t)(2 * 31 * P * P + 31 * P + P * P) * cxsz;
+}
+
+}  // namespace
+
+struct tdz_batch {
+  int prec = TDZ_FP64;
+  int P = 0;
+  int nruns = 0;
+  cudaStream_t stream = nullptr;
+  struct G {
+    int n, m, K;
+  };
+  std::vector<G> geo;
+  std::vector<int> run_geom;
+  std::vector<DevBuf> bufs;  // everything allocated, freed in destroy
+  GeomDev* d_geoms = nullptr;
+  RunDev* d_runs = nullptr;
+  std::vector<RunDev> h_runs;
+  int* d_order = nullptr;
+  int* d_counter = nullptr;
+  double* d_obs = nullptr;
+  size_t obs_steps = 0;
+  double* d_field = nullptr;
+  size_t field_len = 0;
+  long long last_nsteps = 0;
+  int64_t total_dof = 0;
+  size_t dev_bytes = 0;
+  int warps_per_block = 4;
+  int blocks = 0;
+  double tol = 1e-11;
+  int max_it = 6;
+
+  void* alloc(size_t bytes) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+    cudaMemsetAsync(p, 0, bytes, stream);
+    bufs.push_back({p, bytes});
+    dev_bytes += bytes;
+    return p;
+  }
+  ~tdz_batch() {
+    for (auto& b : bufs) cudaFree(b.p);
+    if (d_obs) cudaFree(d_obs);
+    if (d_field) cudaFree(d_field);
+  }
+};
+
+namespace {
+
+template <int P, bool M>
+cudaError_t launch_p(tdz_batch* b, const StepArgs& a) {
+  const size_t sm = smem_per_warp(P, M) * b->warps_per_block;
+  cudaError_t e = cudaFuncSetAttribute(cn1d_kernel<P, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  cn1d_kernel<P, M><<<b->blocks, 32 * b->warps_per_block, sm, b->stream>>>(a);
+  return cudaGetLastError();
+}
+
+template <bool M>
+cudaError_t launch(tdz_batch* b, const StepArgs& a) {
+  switch (b->P) {
+    case 1: return launch_p<1, M>(b, a);
+    case 2: return launch_p<2, M>(b, a);
+    case 3: return launch_p<3, M>(b, a);
+    case 4: return launch_p<4, M>(b, a);
+    case 5: return launch_p<5, M>(b, a);
+    case 6: return launch_p<6, M>(b, a);
+    case 7: return launch_p<7, M>(b, a);
+    case 8: return launch_p<8, M>(b, a);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tdz_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* ops_index, int precision,
+                     void* cuda_stream, tdz_batch** out) {
+  if (!ops || nops < 1 || nruns < 1 || !ops_index || !out) return TDZ_EINVAL;
+  if (precision != TDZ_FP64 && precision != TDZ_MIXED) return TDZ_EINVAL;
+  for (int g = 0; g < nops; ++g) {
+    if (!ops[g]) return TDZ_EINVAL;
+    if (ops[g]->o.dim != 1) {
+      set_error("tdz_batch_create: only 1-D operators are supported by this build");
+      return TDZ_EUNSUPPORTED;
+    }
+    if (ops[g]->o.n[0] < ops[g]->o.p[0] + 1) {
+      set_error("tdz_batch_create: a run needs at least degree+1 coefficients");
+      return TDZ_EINVAL;
+    }
+    if (ops[g]->o.p[0] != ops[0]->o.p[0]) {
+      set_error("tdz_batch_create: all operators of a batch must have the same degree");
+      return TDZ_EUNSUPPORTED;
+    }
+  }
+  for (int r = 0; r < nruns; ++r)
+    if (ops_index[r] < 0 || ops_index[r] >= nops) return TDZ_EINVAL;
+  const int P = ops[0]->o.p[0];
+  if (P < 1 || P > MAXP) return TDZ_EUNSUPPORTED;
+  tdz_batch* b = new (std::nothrow) tdz_batch;
+  if (!b) return TDZ_ENOMEM;
+  b->prec = precision;
+  b->P = P;
+  b->nruns = nruns;
+  b->stream = static_cast<cudaStream_t>(cuda_stream);
+  const bool mixed = precision == TDZ_MIXED;
+  const int P1 = P + 1;
+  const size_t Tsz = mixed ? 8 : 16;  // complex element of the solve precision
+  // ---------------------------------------------------------------- geometries
+  std::vector<GeomDev> hg(nops);
+  b->geo.resize(nops);
+  for (int gi = 0; gi < nops; ++gi) {
+    const Ops& o = ops[gi]->o;
+    const int n = (int)o.n[0];
+    int K = std::max(1, std::min(32, n / (3 * P)));
+    int m = (n + K - 1) / K;
+    while (K > 1 && m - P < P + 1) {
+      --K;
+      m = (n + K - 1) / K;
+    }
+    b->geo[gi] = {n, m, K};
+    const size_t nb = (size_t)m * P1 * LANES;
+    const Band* src[5] = {&o.S, &o.H0, &o.D, &o.G, &o.K};
+    void* dst[5];
+    for (int q = 0; q < 5; ++q) {
+      std::vector<double> hd;
+      std::vector<float> hf;
+      if (mixed) hf.assign(nb * 2, 0.f);
+      else hd.assign(nb, 0.0);
+      for (int k = 0; k < K; ++k)
+        for (int i = 0; i < m; ++i) {
+          const int64_t gr = (int64_t)k * m + i;
+          for (int d = 0; d <= P; ++d) {
+            double v = 0.0;
+            if (gr < n) {
+              if (gr - d >= 0) v = src[q]->at(gr, d);
+            } else if (d == 0 && q == 0) {
+              v = 1.0;  // padding rows: identity in S
+            }
+            const size_t idx = ((size_t)i * P1 + d) * LANES + k;
+            if (mixed) {
+              float hi = (float)v;
+              hf[2 * idx] = hi;
+              hf[2 * idx + 1] = (float)(v - (double)hi);
+            } else {
+              hd[idx] = v;
+            }
+          }
+        }
+      void* p = b->alloc(nb * (mixed ? 8 : 8));
+      if (!p) {
+        delete b;
+        return TDZ_ENOMEM;
+      }
+      cudaError_t e = cudaMemcpyAsync(p, mixed ? (const void*)hf.data() : (const void*)hd.data(), nb * 8,
+                                      cudaMemcpyHostToDevice, b->stream);
+      if (e != cudaSuccess) {
+        delete b;
+        return cuda_fail(e, "tdz_batch_create: upload");
+      }
+      cudaStreamSynchronize(b->stream);
+      dst[q] = p;
+    }
+    hg[gi] = GeomDev{n, m, K, 0, dst[0], dst[1], dst[2], dst[3], dst[4]};
+  }
+  // ---------------------------------------------------------------- runs
+  b->h_runs.resize(nruns);
+  b->run_geom.assign(ops_index, ops_index + nruns);
+  for (int r = 0; r < nruns; ++r) {
+    const auto& G = b->geo[ops_index[r]];
+    const size_t rows = (size_t)G.m * LANES;
+    RunDev R{};
+    R.geom = ops_index[r];
+    R.status = TDZ_OK;
+    R.hist = 0;
+    R.state = b->alloc(rows * 16);
+    R.rhs = b->alloc(rows * Tsz);
+    R.Lc = b->alloc(rows * P * Tsz);
+    R.Dv = b->alloc(rows * Tsz);
+    R.gd = b->alloc(rows * Tsz);
+    R.dl = b->alloc(rows * Tsz);
+    if (mixed) {
+      R.d1 = static_cast<float2*>(b->alloc(rows * 8));
+      R.d2 = static_cast<float2*>(b->alloc(rows * 8));
+      R.W = static_cast<float4*>(b->alloc(rows * 16));
+    }
+    if (!R.state || !R.rhs || !R.Lc || !R.Dv || !R.gd || !R.dl || (mixed && (!R.d1 || !R.d2 || !R.W))) {
+      delete b;
+      return TDZ_ENOMEM;
+    }
+    b->h_runs[r] = R;
+    b->total_dof += G.n;
+  }
+  b->d_geoms = static_cast<GeomDev*>(b->alloc(sizeof(GeomDev) * nops));
+  b->d_runs = static_cast<RunDev*>(b->alloc(sizeof(RunDev) * nruns));
+  b->d_order = static_cast<int*>(b->alloc(sizeof(int) * nruns));
+  b->d_counter = static_cast<int*>(b->alloc(sizeof(int)));
+  if (!b->d_geoms || !b->d_runs || !b->d_order || !b->d_counter) {
+    delete b;
+    return TDZ_ENOMEM;
+  }
+  // longest-processing-time order: largest runs first
+  std::vector<int> order(nruns);
+  for (int r = 0; r < nruns; ++r) order[r] = r;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int x, int y) { return b->geo[ops_index[x]].n > b->geo[ops_index[y]].n; });
+  cudaMemcpyAsync(b->d_geoms, hg.data(), sizeof(GeomDev) * nops, cudaMemcpyHostToDevice, b->stream);
+  cudaMemcpyAsync(b->d_runs, b->h_runs.data(), sizeof(RunDev) * nruns, cudaMemcpyHostToDevice, b->stream);
+  cudaMemcpyAsync(b->d_order, order.data(), sizeof(int) * nruns, cudaMemcpyHostToDevice, b->stream);
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) {
+    delete b;
+    return cuda_fail(e, "tdz_batch_create");
+  }
+  // launch shape: warps per block limited by shared memory; one warp per run at most
+  int dev = 0, sms = 148, maxsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const size_t spw = smem_per_warp(P, mixed);
+  int wpb = (int)std::min<size_t>(8, std::max<size_t>(1, (size_t)maxsm / spw));
+  b->warps_per_block = wpb;
+  int per_sm = std::max(1, (int)((size_t)228 * 1024 / (spw * wpb + 1024)));
+  b->blocks = std::max(1, std::min((nruns + wpb - 1) / wpb, sms * per_sm));
+  *out = b;
+  return TDZ_OK;
+}
+
+int tdz_batch_set_refinement(tdz_batch* b, double tol, int max_solves) {
+  if (!b || !(tol > 0) || max_solves < 1 || max_solves > 64) return TDZ_EINVAL;
+  b->tol = tol;
+  b->max_it = max_solves;
+  return TDZ_OK;
+}
+
+int tdz_batch_info(const tdz_batch* b, int* nruns, int64_t* total_dof, size_t* device_bytes) {
+  if (!b) return TDZ_EINVAL;
+  if (nruns) *nruns = b->nruns;
+  if (total_dof) *total_dof = b->total_dof;
+  if (device_bytes) *device_bytes = b->dev_bytes;
+  return TDZ_OK;
+}
+
+int tdz_set_state(tdz_batch* b, int run, const double* c) {
+  if (!b || !c || run < 0 || run >= b->nruns) return TDZ_EINVAL;
+  const auto& G = b->geo[b->run_geom[run]];
+  const int n = G.n, m = G.m;
+  std::vector<double> hc((size_t)2 * n);
+  cudaError_t e;
+  if (is_device_ptr(c)) {
+    e = cudaMemcpyAsync(hc.data(), c, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "tdz_set_state");
+  } else {
+    std::memcpy(hc.data(), c, sizeof(double) * 2 * n);
+  }
+  for (int i = 0; i < 2 * n; ++i)
+    if (!std::isfinite(hc[i])) {
+      set_error("tdz_set_state: non-finite coefficient");
+      return TDZ_ENONFINITE;
+    }
+  const size_t rows = (size_t)m * LANES;
+  RunDev& R = b->h_runs[run];
+  if (b->prec == TDZ_MIXED) {
+    std::vector<float> s(rows * 4, 0.f);
+    for (int g = 0; g < n; ++g) {
+      const size_t idx = (size_t)(g % m) * LANES + g / m;
+      const double re = hc[2 * g], im = hc[2 * g + 1];
+      const float rh = (float)re, ih = (float)im;
+      s[4 * idx + 0] = rh;
+      s[4 * idx + 1] = ih;
+      s[4 * idx + 2] = (float)(re - (double)rh);
+      s[4 * idx + 3] = (float)(im - (double)ih);
+    }
+    e = cudaMemcpyAsync(R.state, s.data(), rows * 16, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(R.d1, 0, rows * 8, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(R.d2, 0, rows * 8, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(R.W, 0, rows * 16, b->stream);
+  } else {
+    std::vector<double> s(rows * 2, 0.0);
+    for (int g = 0; g < n; ++g) {
+      const size_t idx = (size_t)(g % m) * LANES + g / m;
+      s[2 * idx] = hc[2 * g];
+      s[2 * idx + 1] = hc[2 * g + 1];
+    }
+    e = cudaMemcpyAsync(R.state, s.data(), rows * 16, cudaMemcpyHostToDevice, b->stream);
+  }
+  // reset history and status of this run
+  if (e == cudaSuccess) {
+    RunDev upd = R;
+    upd.hist = 0;
+    upd.status = TDZ_OK;
+    e = cudaMemcpyAsync(&b->d_runs[run].status, &upd.status, sizeof(int) * 2, cudaMemcpyHostToDevice, b->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "tdz_set_state");
+  return TDZ_OK;
+}
+
+int tdz_get_state(const tdz_batch* b, int run, double* c) {
+  if (!b || !c || run < 0 || run >= b->nruns) return TDZ_EINVAL;
+  const auto& G = b->geo[b->run_geom[run]];
+  const int n = G.n, m = G.m;
+  const size_t rows = (size_t)m * LANES;
+  const RunDev& R = b->h_runs[run];
+  std::vector<double> hc((size_t)2 * n);
+  cudaError_t e;
+  if (b->prec == TDZ_MIXED) {
+    std::vector<float> s(rows * 4);
+    e = cudaMemcpyAsync(s.data(), R.state, rows * 16, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "tdz_get_state");
+    for (int g = 0; g < n; ++g) {
+      const size_t idx = (size_t)(g % m) * LANES + g / m;
+      hc[2 * g] = (double)s[4 * idx] + (double)s[4 * idx + 2];
+      hc[2 * g + 1] = (double)s[4 * idx + 1] + (double)s[4 * idx + 3];
+    }
+  } else {
+    std::vector<double> s(rows * 2);
+    e = cudaMemcpyAsync(s.data(), R.state, rows * 16, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "tdz_get_state");
+    for (int g = 0; g < n; ++g) {
+      const size_t idx = (size_t)(g % m) * LANES + g / m;
+      hc[2 * g] = s[2 * idx];
+      hc[2 * g + 1] = s[2 * idx + 1];
+    }
+  }
+  if (is_device_ptr(c)) {
+    e = cudaMemcpyAsync(c, hc.data(), sizeof(double) * 2 * n, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "tdz_get_state");
+  } else {
+    std::memcpy(c, hc.data(), sizeof(double) * 2 * n);
+  }
+  return TDZ_OK;
+}
+
+int tdz_propagate(tdz_batch* b, const double* field, double dt, int64_t step0, int64_t nsteps) {
+  if (!b || !field || nsteps < 1 || step0 < 0 || !(dt > 0) || !std::isfinite(dt)) return TDZ_EINVAL;
+  const size_t need = (size_t)b->nruns * (nsteps + 1);
+  const double* dfield = field;
+  cudaError_t e;
+  if (!is_device_ptr(field)) {
+    if (b->field_len < need) {
+      if (b->d_field) cudaFree(b->d_field);
+      b->d_field = nullptr;
+      e = cudaMalloc(&b->d_field, need * sizeof(double));
+      if (e != cudaSuccess) return cuda_fail(e, "tdz_propagate: field buffer");
+      b->field_len = need;
+    }
+    e = cudaMemcpyAsync(b->d_field, field, need * sizeof(double), cudaMemcpyHostToDevice, b->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "tdz_propagate: field upload");
+    dfield = b->d_field;
+  }
+  const size_t obs_need = (size_t)b->nruns * nsteps * 5;
+  if (b->obs_steps < obs_need) {
+    if (b->d_obs) cudaFree(b->d_obs);
+    b->d_obs = nullptr;
+    e = cudaMalloc(&b->d_obs, obs_need * sizeof(double));
+    if (e != cudaSuccess) return cuda_fail(e, "tdz_propagate: observable buffer");
+    b->obs_steps = obs_need;
+  }
+  e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "tdz_propagate");
+  StepArgs a;
+  a.geoms = b->d_geoms;
+  a.runs = b->d_runs;
+  a.order = b->d_order;
+  a.nruns = b->nruns;
+  a.counter = b->d_counter;
+  a.field = dfield;
+  a.obs = b->d_obs;
+  a.nsteps = nsteps;
+  a.step0 = step0;
+  a.dt = dt;
+  a.tol = b->tol;
+  a.max_it = b->max_it;
+  e = (b->prec == TDZ_MIXED) ? launch<true>(b, a) : launch<false>(b, a);
+  if (e != cudaSuccess) return cuda_fail(e, "tdz_propagate: launch");
+  b->last_nsteps = nsteps;
+  if (dfield != field) {
+    e = cudaStreamSynchronize(b->stream);  // the host field buffer may be reused by the caller
+    if (e != cudaSuccess) return cuda_fail(e, "tdz_propagate");
+  }
+  return TDZ_OK;
+}
+
+int tdz_observe(const tdz_batch* b, int run, double* out, int* status) {
+  if (!b || run < 0 || run >= b->nruns) return TDZ_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "tdz_observe");
+  if (out && b->last_nsteps > 0) {
+    const size_t cnt = (size_t)b->last_nsteps * 5;
+    e = cudaMemcpy(out, b->d_obs + (size_t)run * cnt, cnt * sizeof(double), cudaMemcpyDefault);
+    if (e != cudaSuccess) return cuda_fail(e, "tdz_observe");
+  }
+  if (status) {
+    int st = 0;
+    e = cudaMemcpy(&st, &b->d_runs[run].status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "tdz_observe");
+    *status = st;
+  }
+  return TDZ_OK;
+}
+
+int tdz_refine_stats(const tdz_batch* b, double* max_rel_residual, double* mean_solves) {
+  if (!b) return TDZ_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "tdz_refine_stats");
+  std::vector<RunDev> r(b->nruns);
+  e = cudaMemcpy(r.data(), b->d_runs, sizeof(RunDev) * b->nruns, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "tdz_refine_stats");
+  double mx = 0.0, ns = 0.0;
+  for (auto& x : r) {
+    mx = std::max(mx, x.max_rel);
+    ns += (double)x.nsolve;
+  }
+  if (max_rel_residual) *max_rel_residual = mx;
+  if (mean_solves) *mean_solves = ns;
+  return TDZ_OK;
+}
+
+void tdz_batch_destroy(tdz_batch* b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  delete b;
+}
+
+}  // extern "C"

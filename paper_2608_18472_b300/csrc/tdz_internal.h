@@ -1,0 +1,55 @@
+// Internal declarations shared by the host (C++) and device (CUDA) translation units.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "tdz.h"
+
+namespace tdz {
+
+void set_error(const std::string& msg);
+
+struct Basis {
+  std::vector<double> knots;
+  int p = 0;        // degree
+  int nq = 0;       // Gauss points per element
+  int64_t nfun = 0; // B-splines incl. Dirichlet ends
+  // per element e: span index, quadrature points, weights (w*J), values and derivatives
+  std::vector<int64_t> span;           // nelem
+  std::vector<double> xq, wq;          // nelem*nq
+  std::vector<double> val, der;        // nelem*nq*(p+1), column r <-> function span-p+r
+  int64_t nelem() const { return (int64_t)span.size(); }
+};
+
+struct Medium {
+  int mass_kind = TDZ_MASS_CONST, pot_kind = TDZ_POT_ZERO;
+  double mass_par[4] = {1, 0, 0, 0};
+  double pot_par[4] = {0, 0, 0, 0};
+  std::vector<double> bounds, lmass, lpot;
+  double inv_mass(const double* r, int dim) const;
+  double potential(const double* r, int dim) const;
+  double dpotential(const double* r, int dim, int axis) const;
+};
+
+// symmetric lower band: band[i*(p+1)+d] = M(i, i-d)
+struct Band {
+  int64_t n = 0;
+  int p = 0;
+  std::vector<double> a;
+  double at(int64_t i, int d) const { return a[(size_t)i * (p + 1) + d]; }
+};
+
+struct Ops {
+  int dim = 1;
+  int64_t n[3] = {0, 0, 0};
+  int p[3] = {0, 0, 0};
+  Medium med;
+  // 1-D matrices
+  Band S, T, V, H0, D, G, K;
+};
+
+}  // namespace tdz
+
+struct tdz_basis { tdz::Basis b; };
+struct tdz_ops { tdz::Ops o; };

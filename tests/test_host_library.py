@@ -1,0 +1,99 @@
+"""Host-side parts of the library (no GPU needed): exported C ABI, basis tables, one-pass band
+assembly and the host ground state, each compared with the independent CPU oracle."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import assemble, bspline, eigen
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def tdz():
+    import paper_2608_18472_b300 as m
+    return m
+
+
+def test_library_exports_every_declared_symbol(tdz):
+    import ctypes
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            names |= set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(tdz_\w+)\s*\(", txt, flags=re.M))
+    assert len(names) >= 15
+    lib = ctypes.CDLL(tdz.LIB_PATH)
+    missing = [n for n in sorted(names) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+@pytest.mark.parametrize("p", [1, 3, 6, 8])
+def test_basis_tables_match_oracle(tdz, p):
+    rng = np.random.default_rng(7)
+    inner = np.sort(rng.uniform(-5, 5, 13))
+    knots = np.concatenate([np.full(p + 1, -5.0), inner, np.full(p + 1, 5.0)])
+    b = tdz.Basis(knots, p, p + 1)
+    x = rng.uniform(-5, 5, 300)
+    v, d = b.eval(x)
+    vo, do = bspline.eval_all(knots, p, x)
+    assert np.max(np.abs(v - vo)) < 1e-13
+    assert np.max(np.abs(d - do)) < 1e-10 * max(1, np.max(np.abs(do)))
+
+
+def _lower_band(A, p):
+    A = A.toarray()
+    n = A.shape[0]
+    out = np.zeros((n, p + 1))
+    for d in range(p + 1):
+        out[d:, d] = np.diagonal(A, -d)
+    return out
+
+
+MEDIA = [
+    ("softcore", lambda: (wl.knots_for_nsplines(-40, 40, 90, 5), 5, 6, wl.softcore_medium(2.0))),
+    ("quesne", lambda: (wl.open_uniform_knots(-2.0, 50.0, 120, 7), 7, 10, wl.quesne_medium())),
+    ("dqw", lambda: (wl.dqw_knots(wl.dqw_medium(10.0, 3.0, 0.24), 400, 6), 6, 7, wl.dqw_medium(10.0, 3.0, 0.24))),
+    ("ho", lambda: (wl.knots_for_nsplines(-10, 10, 60, 4), 4, 5, wl.ho_medium([1.0]))),
+    ("h2p", lambda: (wl.knots_for_nsplines(-60, 60, 150, 7), 7, 8,
+                     wl.medium({"kind": "const", "m": 1.0}, {"kind": "h2p_softcore", "R": 2.0, "eps": 1.472}))),
+]
+
+
+@pytest.mark.parametrize("name,make", MEDIA, ids=[m[0] for m in MEDIA])
+def test_band_assembly_matches_oracle(tdz, name, make):
+    knots, p, nq, med = make()
+    ops = tdz.assemble_1d(knots, p, med, nq)
+    ref = assemble.assemble_1d(knots, p, nq, med)
+    for key in ("S", "T", "V", "H0", "K"):
+        a, b = ops.band(key), _lower_band(ref[key], p)
+        assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(b)) + 1e-300, key
+    for key in ("D", "G"):
+        a, b = ops.band(key), _lower_band(ref[key][0], p)
+        assert np.max(np.abs(a - b)) <= 1e-12 * max(np.max(np.abs(b)), 1e-300) + 1e-300, key
+
+
+def test_host_ground_state_matches_oracle(tdz):
+    knots = wl.knots_for_nsplines(-60, 60, 200, 6)
+    med = wl.softcore_medium(2.0)
+    e, c = tdz.assemble_1d(knots, 6, med).ground_state()
+    m = assemble.assemble_1d(knots, 6, 7, med)
+    eo, co = eigen.ground_state(m)
+    assert abs(e - eo) < 1e-12
+    assert np.linalg.norm(c - co) < 1e-8
+
+
+def test_errors_are_status_codes(tdz):
+    with pytest.raises(tdz.TDZError) as ei:
+        tdz.Basis([0.0, 1.0, 0.5, 2.0], 1)
+    assert ei.value.code == tdz.TDZ_EINVAL
+    with pytest.raises(tdz.TDZError) as ei:
+        tdz.Basis(wl.open_uniform_knots(0, 1, 4, 3)[1:], 3)   # not open
+    assert ei.value.code == tdz.TDZ_EINVAL
+    b = tdz.Basis(wl.open_uniform_knots(0, 1, 6, 3), 3)
+    with pytest.raises(tdz.TDZError) as ei:
+        tdz.Ops([b, b], wl.ho_medium([1.0, 1.0]))
+    assert ei.value.code == tdz.TDZ_EUNSUPPORTED
