@@ -36,6 +36,7 @@ sys.path.insert(0, ROOT)
 
 import workloads as wl  # noqa: E402
 
+CPU_MAX_STEPS = 2000
 METRIC = "TDSE coefficient-updates/s: batched mixed vs plain FP64 at stated HHG/norm error"
 UNIT = "coefficient-updates/s"
 
@@ -121,23 +122,24 @@ def cpu_oracle_leg(wk, c0s, nruns_sample, nsteps_sample, ops_mats=None):
     from oracle import assemble, propagate
     mats = {}
     finals, obs = [], []
-    if True:
-        t_asm = 0.0
-        for i in range(nruns_sample):
-            r = wk.runs[i]
-            if r.geometry not in mats:
-                t0 = time.perf_counter()
-                mats[r.geometry] = assemble.assemble_1d(r.knots, r.degree, r.nquad, r.medium)
-                t_asm += time.perf_counter() - t0
-        t0 = time.perf_counter()
-        dof = 0
-        for i in range(nruns_sample):
-            r = wk.runs[i]
-            c, o = propagate.cn_propagate(mats[r.geometry], c0s[i], r.field, wk.dt, nsteps_sample)
-            finals.append(c)
-            obs.append(o)
-            dof += len(c)
-        t = time.perf_counter() - t0
+    t_asm = 0.0
+    if nsteps_sample + 1 > len(wk.runs[0].field):
+        raise ValueError("field shorter than the requested oracle sample")
+    for i in range(nruns_sample):
+        r = wk.runs[i]
+        if r.geometry not in mats:
+            t0 = time.perf_counter()
+            mats[r.geometry] = assemble.assemble_1d(r.knots, r.degree, r.nquad, r.medium)
+            t_asm += time.perf_counter() - t0
+    t0 = time.perf_counter()
+    dof = 0
+    for i in range(nruns_sample):
+        r = wk.runs[i]
+        c, o = propagate.cn_propagate(mats[r.geometry], c0s[i], r.field, wk.dt, nsteps_sample)
+        finals.append(c)
+        obs.append(o)
+        dof += len(c)
+    t = time.perf_counter() - t0
     return dof * nsteps_sample / t, {"seconds": t, "dof": dof, "assembly_s": t_asm}, finals, obs
 
 
@@ -192,7 +194,8 @@ def main():
 
     nsteps_total = args.warmup + args.steps
     # every rank builds its own shard: the full scan with a rank-dependent seed (weak scaling)
-    wk = build_batch_inputs(args.n_geom, 4, nsteps_total + args.fp64_steps + 1, seed=wl.SEED + rank)
+    # field samples long enough for the timed window, the FP64 leg and the oracle sample (<= 2000 steps)
+    wk = build_batch_inputs(args.n_geom, 4, max(nsteps_total, args.fp64_steps, CPU_MAX_STEPS) + 1, seed=wl.SEED + rank)
     runs = wk.runs
     geoms = {}
     for r in runs:
@@ -305,7 +308,7 @@ def main():
         v_probe, det, _, _ = cpu_oracle_leg(wk, c0, 1, ns_probe)
         per_run_step = det["seconds"] / ns_probe
         nsample = 8
-        nsteps_s = max(20, min(2000, int(args.cpu_seconds / (per_run_step * nsample))))
+        nsteps_s = max(20, min(CPU_MAX_STEPS, int(args.cpu_seconds / (per_run_step * nsample))))
         v, det, finals, oobs = cpu_oracle_leg(wk, c0, nsample, nsteps_s)
         bs = tdz.Batch(ops, run_ops[:nsample], tdz.MIXED)
         for i in range(nsample):
