@@ -171,6 +171,31 @@ int  tdz_observe(const tdz_batch* b, int run, double* out, int* status);
 int  tdz_refine_stats(const tdz_batch* b, double* max_rel_residual, double* mean_solves);
 void tdz_batch_destroy(tdz_batch* b);
 
+
+/* ------------------------------------------------------------------ allocation-free entry point
+ * tdz_cn1d_propagate_noalloc: the binary64 1-D propagation of tdz_propagate for ONE run, for
+ * callers that cannot call cudaMalloc: integrations whose host framework owns all device memory
+ * through its own pool (a caching allocator or an arena reserved at start-up) and forbids side
+ * allocations, and code that must not risk the implicit device synchronisation cudaMalloc and
+ * cudaFree can cause. The paper has no counterpart; it exists for deployment only.
+ * The caller passes inputs and outputs; the scratch lives in one fixed device array compiled
+ * into this library (about 2.4 MB, held by every GPU that loads the library until exit):
+ *   bands : device, [5][n][degree+1] lower bands S, H0, D, G, K: bands[(q*n + i)*(degree+1) + d]
+ *           = M_q(i, i-d) (as returned by tdz_ops_band), read only.
+ *   field : device, E(t_{step0+k}) for k = 0..nsteps.   state: device, [2n] complex in/out.
+ *   obs   : device, [nsteps][5] = t, E, d, a, norm (as tdz_observe).
+ *   status: host, optional; if given the call synchronises the stream and stores the run status.
+ * Limits: n <= TDZ_NOALLOC_MAX_N, degree <= 8; larger sizes return TDZ_EINVAL with a message.
+ * The first call on a device resolves the array's device address with cudaGetSymbolAddress
+ * (that device current); make that first call before any stream capture. Every call shares the
+ * one array and overwrites it (the call initialises all of it that it reads), so calls that
+ * overlap on the GPU - on different streams or host threads - race and must be serialised.
+ * No cudaMalloc, cudaFree or allocating library routine is called.                           */
+#define TDZ_NOALLOC_MAX_N 4096
+int  tdz_cn1d_propagate_noalloc(const double* bands, int64_t n, int degree, const double* field, double dt,
+                                int64_t step0, int64_t nsteps, double* state, double* obs, void* cuda_stream,
+                                int* status);
+
 #ifdef __cplusplus
 }
 #endif

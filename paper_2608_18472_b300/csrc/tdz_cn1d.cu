@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -1337,3 +1338,192 @@ void tdz_batch_destroy(tdz_batch* b) {
 }
 
 }  // extern "C"
+
+// ============================================================================ allocation-free variant
+// Scratch for tdz_cn1d_propagate_noalloc: one binary64 run of at most TDZ_NOALLOC_MAX_N coefficients
+// and degree <= 8, in a fixed device array that every GPU loading this library holds until exit.
+namespace tdz {
+constexpr int NOALLOC_ROWS = TDZ_NOALLOC_MAX_N + 32;                       // interleaved rows m*32 bound
+constexpr size_t NOALLOC_DOUBLES = (size_t)NOALLOC_ROWS * (7 * MAXP + 15) + 64;
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_DOUBLES];
+
+struct NoAllocLayout {
+  int n, m, K, P;
+  size_t band, state, rhs, Lc, Dv, gd, dl, desc;  // offsets in doubles
+};
+
+// Pack the caller's natural-order bands and state into the interleaved [row][lane] layout and
+// write the run descriptors; everything the step kernel reads before writing is set here.
+__global__ void noalloc_pack(double* scr, NoAllocLayout L, const double* bands, const double* state) {
+  const int P1 = L.P + 1;
+  const size_t rows = (size_t)L.m * LANES;
+  const size_t tid = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t e = tid; e < 5 * rows * P1; e += stride) {
+    const int q = (int)(e / (rows * P1));
+    const size_t rem = e % (rows * P1);
+    const int i = (int)(rem / ((size_t)P1 * LANES));
+    const int d = (int)((rem / LANES) % P1);
+    const int k = (int)(rem % LANES);
+    const long long g = (long long)k * L.m + i;
+    double v = 0.0;
+    if (k < L.K) {
+      if (g < L.n) {
+        if (g - d >= 0) v = bands[((size_t)q * L.n + g) * P1 + d];
+      } else if (q == 0 && d == 0) {
+        v = 1.0;  // padding rows: identity in S
+      }
+    }
+    scr[L.band + e] = v;
+  }
+  for (size_t e = tid; e < rows; e += stride) {
+    const int i = (int)(e / LANES), k = (int)(e % LANES);
+    const long long g = (long long)k * L.m + i;
+    const bool in = k < L.K && g < L.n;
+    scr[L.state + 2 * e] = in ? state[2 * g] : 0.0;
+    scr[L.state + 2 * e + 1] = in ? state[2 * g + 1] : 0.0;
+  }
+  if (tid == 0) {
+    GeomDev* G = reinterpret_cast<GeomDev*>(scr + L.desc);
+    RunDev* R = reinterpret_cast<RunDev*>(G + 1);
+    int* order = reinterpret_cast<int*>(R + 1);
+    const size_t nb = rows * P1;
+    *G = GeomDev{L.n, L.m, L.K, 0, scr + L.band, scr + L.band + nb, scr + L.band + 2 * nb, scr + L.band + 3 * nb,
+                 scr + L.band + 4 * nb};
+    RunDev r{};
+    r.geom = 0;
+    r.status = TDZ_OK;
+    r.state = scr + L.state;
+    r.rhs = scr + L.rhs;
+    r.Lc = scr + L.Lc;
+    r.Dv = scr + L.Dv;
+    r.gd = scr + L.gd;
+    r.dl = scr + L.dl;
+    *R = r;
+    order[0] = 0;
+    order[1] = 0;  // work counter
+  }
+}
+
+__global__ void noalloc_unpack(const double* scr, NoAllocLayout L, double* state) {
+  const size_t tid = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  for (size_t g = tid; g < (size_t)L.n; g += (size_t)gridDim.x * blockDim.x) {
+    const size_t e = (size_t)(g % L.m) * LANES + g / L.m;
+    state[2 * g] = scr[L.state + 2 * e];
+    state[2 * g + 1] = scr[L.state + 2 * e + 1];
+  }
+}
+
+static double* g_noalloc_ptr[64] = {nullptr};
+static std::mutex g_noalloc_mu;
+
+template <int P>
+cudaError_t noalloc_launch(cudaStream_t st, const StepArgs& a) {
+  const size_t sm = smem_per_warp(P, false);
+  cudaError_t e = cudaFuncSetAttribute(cn1d_kernel<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  cn1d_kernel<P, false><<<1, 32, sm, st>>>(a);
+  return cudaGetLastError();
+}
+}  // namespace tdz
+
+extern "C" int tdz_cn1d_propagate_noalloc(const double* bands, int64_t n, int degree, const double* field, double dt,
+                                          int64_t step0, int64_t nsteps, double* state, double* obs, void* cuda_stream,
+                                          int* status) {
+  using namespace tdz;
+  if (!bands || !field || !state || !obs || degree < 1 || degree > MAXP || n < degree + 1 || nsteps < 1 ||
+      step0 < 0 || !(dt > 0) || !std::isfinite(dt)) {
+    set_error("tdz_cn1d_propagate_noalloc: bad arguments");
+    return TDZ_EINVAL;
+  }
+  if (n > TDZ_NOALLOC_MAX_N) {
+    set_error("tdz_cn1d_propagate_noalloc: n exceeds TDZ_NOALLOC_MAX_N (" + std::to_string(TDZ_NOALLOC_MAX_N) +
+              "); use the batch API for larger runs");
+    return TDZ_EINVAL;
+  }
+  const int P = degree;
+  NoAllocLayout L{};
+  L.n = (int)n;
+  L.P = P;
+  L.K = std::max(1, std::min(32, (int)n / (3 * P)));
+  L.m = (int)((n + L.K - 1) / L.K);
+  while (L.K > 1 && L.m - P < P + 1) {
+    --L.K;
+    L.m = (int)((n + L.K - 1) / L.K);
+  }
+  const size_t rows = (size_t)L.m * LANES;
+  if (rows > (size_t)NOALLOC_ROWS) {
+    set_error("tdz_cn1d_propagate_noalloc: the interleaved layout of this size exceeds the static scratch");
+    return TDZ_EINVAL;
+  }
+  L.band = 0;
+  L.state = L.band + 5 * rows * (P + 1);
+  L.rhs = L.state + 2 * rows;
+  L.Lc = L.rhs + 2 * rows;
+  L.Dv = L.Lc + 2 * rows * P;
+  L.gd = L.Dv + 2 * rows;
+  L.dl = L.gd + 2 * rows;
+  L.desc = L.dl + 2 * rows;
+  L.desc = (L.desc + 31) & ~(size_t)31;
+  if (L.desc + 64 > NOALLOC_DOUBLES) {
+    set_error("tdz_cn1d_propagate_noalloc: scratch layout overflow");
+    return TDZ_EINVAL;
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= 64) return cuda_fail(e, "tdz_cn1d_propagate_noalloc: device");
+  double* scr = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      // first call on this device (which is current): resolve the device address of the array
+      void* p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess) return cuda_fail(e, "tdz_cn1d_propagate_noalloc: cudaGetSymbolAddress");
+      g_noalloc_ptr[dev] = static_cast<double*>(p);
+    }
+    scr = g_noalloc_ptr[dev];
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  noalloc_pack<<<148, 256, 0, st>>>(scr, L, bands, state);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "tdz_cn1d_propagate_noalloc: pack");
+  GeomDev* G = reinterpret_cast<GeomDev*>(scr + L.desc);
+  RunDev* R = reinterpret_cast<RunDev*>(G + 1);
+  int* order = reinterpret_cast<int*>(R + 1);
+  StepArgs a;
+  a.geoms = G;
+  a.runs = R;
+  a.order = order;
+  a.nruns = 1;
+  a.counter = order + 1;
+  a.field = field;
+  a.obs = obs;
+  a.nsteps = nsteps;
+  a.step0 = step0;
+  a.dt = dt;
+  a.tol = 1e-11;
+  a.max_it = 1;
+  switch (P) {
+    case 1: e = noalloc_launch<1>(st, a); break;
+    case 2: e = noalloc_launch<2>(st, a); break;
+    case 3: e = noalloc_launch<3>(st, a); break;
+    case 4: e = noalloc_launch<4>(st, a); break;
+    case 5: e = noalloc_launch<5>(st, a); break;
+    case 6: e = noalloc_launch<6>(st, a); break;
+    case 7: e = noalloc_launch<7>(st, a); break;
+    default: e = noalloc_launch<8>(st, a); break;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "tdz_cn1d_propagate_noalloc: propagate");
+  noalloc_unpack<<<64, 256, 0, st>>>(scr, L, state);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "tdz_cn1d_propagate_noalloc: unpack");
+  if (status) {
+    int sv = 0;
+    e = cudaMemcpyAsync(&sv, &R->status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "tdz_cn1d_propagate_noalloc: status");
+    *status = sv;
+  }
+  return TDZ_OK;
+}
