@@ -43,11 +43,16 @@ constexpr int MAXP = 8;
 
 struct GeomDev {
   int n, m, K, pad;
-  const void* S;   // band arrays [m][P+1][32]: double (binary64 path) or float2 hi/lo (mixed)
-  const void* H;   // H0 = T + V
+  // Band arrays, [m][P+1][32] each.
+  //   binary64 path: S, H (= H0 = T + V), D, G, Km (<m^-1>) as double.
+  //   mixed path:    S  = float4 {S.hi, H0.hi, D.hi, S.lo}   (one 16-byte load per entry in the sweeps)
+  //                  H  = float2 {H0.lo, D.lo}
+  //                  G  = float4 {G.hi, G.lo, K.hi, K.lo};  D and Km unused.
+  const void* S;
+  const void* H;
   const void* D;
   const void* G;
-  const void* Km;  // <m^-1> matrix
+  const void* Km;
 };
 
 struct RunDev {
@@ -92,14 +97,12 @@ TDZ_DEV int ridx(int i, int k) { return i * LANES + k; }
 template <int P, class T, bool MIXED>
 TDZ_DEV cx<T> a_entry(const GeomDev& g, int idx, T tau, T ebar) {
   if constexpr (MIXED) {
-    float2 s = static_cast<const float2*>(g.S)[idx];
-    float2 h = static_cast<const float2*>(g.H)[idx];
-    float2 d = static_cast<const float2*>(g.D)[idx];
-    return cx<T>{s.x, tau * fmaf(ebar, d.x, h.x)};
+    const float4 v = __ldg(static_cast<const float4*>(g.S) + idx);
+    return cx<T>{v.x, tau * fmaf(ebar, v.z, v.y)};
   } else {
-    double s = static_cast<const double*>(g.S)[idx];
-    double h = static_cast<const double*>(g.H)[idx];
-    double d = static_cast<const double*>(g.D)[idx];
+    const double s = __ldg(static_cast<const double*>(g.S) + idx);
+    const double h = __ldg(static_cast<const double*>(g.H) + idx);
+    const double d = __ldg(static_cast<const double*>(g.D) + idx);
     return cx<T>{s, tau * fma(ebar, d, h)};
   }
 }
@@ -352,15 +355,29 @@ TDZ_DEV void red_solve(Red<T>& red, int nsep, int lane) {
 // Forward: g = L^-1 b' with b' = rhs - A(I, Sep_{k-1}) x_up, store g D^-1.
 // Backward: x = L^-T (g D^-1) - (L_SI)^T x_dn, where L_SI are the multipliers sweep 1 stored for
 // the lower separator rows (A_II^-1 A_IS = L^-T L_SI^T), so the lower coupling enters only here.
-// Writes the interior and the lane's own separator solution to dl.
+// The solution is accumulated in place: into the binary64 state (binary64 path) or into the
+// double-float correction W (mixed path), for the interior and the lane's own separator rows.
+template <class T, bool MIXED>
+TDZ_DEV void accumulate(const RunDev& run, int idx, cx<T> x) {
+  if constexpr (MIXED) {
+    float4* W = run.W;
+    const float4 q = W[idx];
+    const ff wr = ff_addf(ff{q.x, q.z}, x.r), wi = ff_addf(ff{q.y, q.w}, x.i);
+    W[idx] = make_float4(wr.h, wi.h, wr.l, wi.l);
+  } else {
+    double2* c = static_cast<double2*>(run.state);
+    const double2 v = c[idx];
+    c[idx] = make_double2(v.x + x.r, v.y + x.i);
+  }
+}
+
 template <int P, class T, bool MIXED>
 TDZ_DEV void substitute(const GeomDev& g, const RunDev& run, const Lane& L, T tau, T ebar, const Red<T>& red) {
   const int k = L.k;
-  const cx<T>* rhs = static_cast<const cx<T>*>(run.rhs);
-  const cx<T>* Lc = static_cast<const cx<T>*>(run.Lc);
-  const cx<T>* Dv = static_cast<const cx<T>*>(run.Dv);
-  cx<T>* gd = static_cast<cx<T>*>(run.gd);
-  cx<T>* dl = static_cast<cx<T>*>(run.dl);
+  const cx<T>* __restrict__ rhs = static_cast<const cx<T>*>(run.rhs);
+  const cx<T>* __restrict__ Lc = static_cast<const cx<T>*>(run.Lc);
+  const cx<T>* __restrict__ Dv = static_cast<const cx<T>*>(run.Dv);
+  cx<T>* __restrict__ gd = static_cast<cx<T>*>(run.gd);
   cx<T> xup[P], xdn[P];
 #pragma unroll
   for (int j = 0; j < P; ++j) {
@@ -395,11 +412,11 @@ TDZ_DEV void substitute(const GeomDev& g, const RunDev& run, const Lane& L, T ta
 #pragma unroll
     for (int d = P; d >= 2; --d) xw[d] = xw[d - 1];
     xw[1] = x;
-    dl[ridx(i, k)] = x;
+    accumulate<T, MIXED>(run, ridx(i, k), x);
   }
   if (L.dn) {
 #pragma unroll
-    for (int j = 0; j < P; ++j) dl[ridx(L.mI + j, k)] = xdn[j];
+    for (int j = 0; j < P; ++j) accumulate<T, MIXED>(run, ridx(L.mI + j, k), xdn[j]);
   }
 }
 
@@ -414,6 +431,79 @@ TDZ_DEV void solve(const GeomDev& g, const RunDev& run, const Lane& L, T tau, T 
     red_factor<P, T>(red, nsep, lane);
     red_solve<P, T>(red, nsep, lane);
   }
+  __syncwarp();
+  if (L.active) substitute<P, T, MIXED>(g, run, L, tau, ebar, red);
+  __syncwarp();
+}
+
+// Second solve with the factors of the last solve(): forward substitution with the stored L that
+// also eliminates into the lower separator rows (their multipliers are stored too), a backward
+// pass for the top of A_II^-1 r (the upper separator's term -C^T z_T), the reduced solve with the
+// stored block factors, then the substitution. No refactorisation.
+template <int P, class T, bool MIXED>
+TDZ_DEV void resolve(const GeomDev& g, const RunDev& run, const Lane& L, T tau, T ebar, Red<T>& red, int lane) {
+  const int k = L.k;
+  if (L.active) {
+    const cx<T>* __restrict__ rhs = static_cast<const cx<T>*>(run.rhs);
+    const cx<T>* __restrict__ Lc = static_cast<const cx<T>*>(run.Lc);
+    const cx<T>* __restrict__ Dv = static_cast<const cx<T>*>(run.Dv);
+    cx<T>* __restrict__ gd = static_cast<cx<T>*>(run.gd);
+    cx<T> sep[P];
+#pragma unroll
+    for (int j = 0; j < P; ++j) sep[j] = L.dn ? rhs[ridx(L.mI + j, k)] : czero<T>();
+    cx<T> gw[P + 1];
+#pragma unroll
+    for (int d = 0; d <= P; ++d) gw[d] = czero<T>();
+    for (int i = 0; i < L.mI; ++i) {
+      cx<T> b = rhs[ridx(i, k)];
+#pragma unroll
+      for (int d = 1; d <= P; ++d)
+        if (i - d >= 0) b = cmsub(b, Lc[((i - d) * P + d - 1) * LANES + k], gw[d]);
+#pragma unroll
+      for (int d = P; d >= 2; --d) gw[d] = gw[d - 1];
+      gw[1] = b;
+      gd[ridx(i, k)] = cmul(b, Dv[ridx(i, k)]);
+      if (L.dn && i >= L.mI - P) {
+#pragma unroll
+        for (int a = 1; a <= P; ++a) {
+          const int j = i + a - L.mI;  // separator row index of row i+a
+          if (j >= 0) sep[j] = cmsub(sep[j], Lc[(i * P + a - 1) * LANES + k], b);
+        }
+      }
+    }
+    if (L.dn) {
+#pragma unroll
+      for (int j = 0; j < P; ++j) red.rb[k * P + j] = sep[j];
+    }
+  }
+  __syncwarp();
+  if (L.active && L.up) {
+    const cx<T>* __restrict__ Lc = static_cast<const cx<T>*>(run.Lc);
+    const cx<T>* __restrict__ gd = static_cast<const cx<T>*>(run.gd);
+    cx<T> zw[P + 1];  // zw[d] = z_{i+d}; the top P values end up in zw[1..P] reversed
+#pragma unroll
+    for (int d = 0; d <= P; ++d) zw[d] = czero<T>();
+    for (int i = L.mI - 1; i >= 0; --i) {
+      cx<T> z = gd[ridx(i, k)];
+#pragma unroll
+      for (int d = 1; d <= P; ++d) z = cmsub(z, Lc[(i * P + d - 1) * LANES + k], zw[d]);
+#pragma unroll
+      for (int d = P; d >= 2; --d) zw[d] = zw[d - 1];
+      zw[1] = z;
+    }
+    // zw[1 + i] = z_i for i = 0..P-1
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+      cx<T> acc = czero<T>();
+#pragma unroll
+      for (int i = 0; i <= j; ++i)
+        if (i < L.mI) acc = cmadd(acc, a_entry<P, T, MIXED>(g, bidx<P>(i, i + P - j, k), tau, ebar), zw[1 + i]);
+      red.rb[(k - 1) * P + j] = red.rb[(k - 1) * P + j] - acc;
+    }
+  }
+  __syncwarp();
+  const int nsep = L.K - 1;
+  if (nsep > 0) red_solve<P, T>(red, nsep, lane);
   __syncwarp();
   if (L.active) substitute<P, T, MIXED>(g, run, L, tau, ebar, red);
   __syncwarp();
@@ -497,15 +587,18 @@ TDZ_DEV void rhs_fp64(const GeomDev& g, const RunDev& run, const Lane& L, double
 }
 
 // ============================================================================ double-float rhs
-// r = -S w - i (tau H_n) u,  u = 2c + w, all products in double-float. Also accumulates
-// ||r||^2 and ||S c||^2 (FP32 scale) for the relative residual.
-template <int P>
+// r = -S w - i (tau H_n) u,  u = 2c + w, all products in double-float (Dot2 accumulation), scatter
+// form with pending sums for P+1 rows. Accumulates ||r||^2 and, when SCALE, ||S c||^2 (FP32) as the
+// reference for the relative residual.
+template <int P, bool SCALE>
 TDZ_DEV void rhs_mixed(const GeomDev& g, const RunDev& run, const Lane& L, ff tau, ff ebar, float& rr, float& bb) {
-  const float4* c = static_cast<const float4*>(run.state);
-  const float4* W = run.W;
-  cx<float>* rhs = static_cast<cx<float>*>(run.rhs);
+  const float4* __restrict__ c = static_cast<const float4*>(run.state);
+  const float4* __restrict__ W = run.W;
+  const float4* __restrict__ A4 = static_cast<const float4*>(g.S);
+  const float2* __restrict__ HD = static_cast<const float2*>(g.H);
+  cx<float>* __restrict__ rhs = static_cast<cx<float>*>(run.rhs);
   cff uw[P + 1], ww[P + 1];
-  float2 cw[P + 1];          // FP32 copy of c for the scale
+  float2 cw[P + 1];
   ffacc ar[P + 1], ai[P + 1];
   cx<float> sc[P + 1];
 #pragma unroll
@@ -531,19 +624,16 @@ TDZ_DEV void rhs_mixed(const GeomDev& g, const RunDev& run, const Lane& L, ff ta
       const float4 cc = c[ridx(row, chunk)];
       const float4 wq = W[ridx(row, chunk)];
       w = cff{{wq.x, wq.z}, {wq.y, wq.w}};
-      const cff c2 = cff{{2.f * cc.x, 2.f * cc.z}, {2.f * cc.y, 2.f * cc.w}};
-      u = cff_add(c2, w);
+      u = cff_add(cff{{2.f * cc.x, 2.f * cc.z}, {2.f * cc.y, 2.f * cc.w}}, w);
       chi = make_float2(cc.x, cc.y);
       if (j >= 0) {
 #pragma unroll
         for (int d = 0; d <= P; ++d) {
           const int idx = bidx<P>(row, d, chunk);
-          const float2 sv = static_cast<const float2*>(g.S)[idx];
-          const float2 hv = static_cast<const float2*>(g.H)[idx];
-          const float2 dv = static_cast<const float2*>(g.D)[idx];
-          s[d] = ff{sv.x, sv.y};
-          // tau * (H0 + Ebar D)
-          h[d] = ff_mul(tau, ff_add(ff{hv.x, hv.y}, ff_mul(ebar, ff{dv.x, dv.y})));
+          const float4 v = __ldg(A4 + idx);
+          const float2 lo = __ldg(HD + idx);
+          s[d] = ff{v.x, v.w};
+          h[d] = ff_mul(tau, ff_add(ff{v.y, lo.x}, ff_mul(ebar, ff{v.z, lo.y})));  // tau (H0 + Ebar D)
         }
       }
     }
@@ -551,10 +641,12 @@ TDZ_DEV void rhs_mixed(const GeomDev& g, const RunDev& run, const Lane& L, ff ta
     for (int d = P; d >= 1; --d) {
       ar[d] = ar[d - 1];
       ai[d] = ai[d - 1];
-      sc[d] = sc[d - 1];
       uw[d] = uw[d - 1];
       ww[d] = ww[d - 1];
-      cw[d] = cw[d - 1];
+      if (SCALE) {
+        sc[d] = sc[d - 1];
+        cw[d] = cw[d - 1];
+      }
     }
     uw[0] = u;
     ww[0] = w;
@@ -563,16 +655,31 @@ TDZ_DEV void rhs_mixed(const GeomDev& g, const RunDev& run, const Lane& L, ff ta
     acc_zero(ai[0]);
     sc[0] = czero<float>();
     // r.re = -S w.re + (tau H) u.im ;  r.im = -S w.im - (tau H) u.re
+    // own row: four independent compensated partial sums per component (short dependency chains)
     if (j >= 0 && j < L.m) {
+      ffacc pr[4], pi[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        acc_zero(pr[q]);
+        acc_zero(pi[q]);
+      }
 #pragma unroll
       for (int d = 0; d <= P; ++d) {
-        acc_mul(ar[0], ff_neg(s[d]), ww[d].r);
-        acc_mul(ar[0], h[d], uw[d].i);
-        acc_mul(ai[0], ff_neg(s[d]), ww[d].i);
-        acc_mul(ai[0], ff_neg(h[d]), uw[d].r);
-        sc[0].r = fmaf(s[d].h, cw[d].x, sc[0].r);
-        sc[0].i = fmaf(s[d].h, cw[d].y, sc[0].i);
+        acc_mul(pr[(d & 1)], ff_neg(s[d]), ww[d].r);
+        acc_mul(pr[2 + (d & 1)], h[d], uw[d].i);
+        acc_mul(pi[(d & 1)], ff_neg(s[d]), ww[d].i);
+        acc_mul(pi[2 + (d & 1)], ff_neg(h[d]), uw[d].r);
+        if (SCALE) {
+          sc[0].r = fmaf(s[d].h, cw[d].x, sc[0].r);
+          sc[0].i = fmaf(s[d].h, cw[d].y, sc[0].i);
+        }
       }
+      ff tr = ff_add(ff_add(acc_get(pr[0]), acc_get(pr[1])), ff_add(acc_get(pr[2]), acc_get(pr[3])));
+      ff ti = ff_add(ff_add(acc_get(pi[0]), acc_get(pi[1])), ff_add(acc_get(pi[2]), acc_get(pi[3])));
+      ar[0].s = tr.h;
+      ar[0].c = tr.l;
+      ai[0].s = ti.h;
+      ai[0].c = ti.l;
     }
 #pragma unroll
     for (int d = 1; d <= P; ++d) {
@@ -581,8 +688,10 @@ TDZ_DEV void rhs_mixed(const GeomDev& g, const RunDev& run, const Lane& L, ff ta
         acc_mul(ar[d], h[d], u.i);
         acc_mul(ai[d], ff_neg(s[d]), w.i);
         acc_mul(ai[d], ff_neg(h[d]), u.r);
-        sc[d].r = fmaf(s[d].h, chi.x, sc[d].r);
-        sc[d].i = fmaf(s[d].h, chi.y, sc[d].i);
+        if (SCALE) {
+          sc[d].r = fmaf(s[d].h, chi.x, sc[d].r);
+          sc[d].i = fmaf(s[d].h, chi.y, sc[d].i);
+        }
       }
     }
     const int jf = j - P;
@@ -590,56 +699,9 @@ TDZ_DEV void rhs_mixed(const GeomDev& g, const RunDev& run, const Lane& L, ff ta
       const cx<float> r = cx<float>{ff_f(acc_get(ar[P])), ff_f(acc_get(ai[P]))};
       rhs[ridx(jf, L.k)] = r;
       rr = fmaf(r.r, r.r, fmaf(r.i, r.i, rr));
-      bb = fmaf(sc[P].r, sc[P].r, fmaf(sc[P].i, sc[P].i, bb));
+      if (SCALE) bb = fmaf(sc[P].r, sc[P].r, fmaf(sc[P].i, sc[P].i, bb));
     }
   }
-}
-
-// ============================================================================ FP32 residual check
-// r1 = rhs - A delta in FP32 (valid as a convergence measure when |delta| << |c|).
-template <int P>
-TDZ_DEV float resid_fp32(const GeomDev& g, const RunDev& run, const Lane& L, float tau, float ebar) {
-  const cx<float>* dl = static_cast<const cx<float>*>(run.dl);
-  const cx<float>* rhs = static_cast<const cx<float>*>(run.rhs);
-  cx<float> xw[P + 1], acc[P + 1];
-#pragma unroll
-  for (int d = 0; d <= P; ++d) xw[d] = acc[d] = czero<float>();
-  float rr = 0.f;
-  for (int j = -P; j < L.m + P; ++j) {
-    int row, chunk;
-    const bool ok = locate(L, j, row, chunk);
-    cx<float> x = czero<float>();
-    cx<float> a[P + 1];
-#pragma unroll
-    for (int d = 0; d <= P; ++d) a[d] = czero<float>();
-    if (ok) {
-      x = dl[ridx(row, chunk)];
-      if (j >= 0) {
-#pragma unroll
-        for (int d = 0; d <= P; ++d) a[d] = a_entry<P, float, true>(g, bidx<P>(row, d, chunk), tau, ebar);
-      }
-    }
-#pragma unroll
-    for (int d = P; d >= 1; --d) {
-      acc[d] = acc[d - 1];
-      xw[d] = xw[d - 1];
-    }
-    xw[0] = x;
-    acc[0] = czero<float>();
-    if (j >= 0 && j < L.m) {
-#pragma unroll
-      for (int d = 0; d <= P; ++d) acc[0] = cmadd(acc[0], a[d], xw[d]);
-    }
-#pragma unroll
-    for (int d = 1; d <= P; ++d)
-      if (j - d >= 0 && j - d < L.m) acc[d] = cmadd(acc[d], a[d], x);
-    const int jf = j - P;
-    if (jf >= 0 && jf < L.m) {
-      const cx<float> r = rhs[ridx(jf, L.k)] - acc[P];
-      rr = fmaf(r.r, r.r, fmaf(r.i, r.i, rr));
-    }
-  }
-  return rr;
 }
 
 // ============================================================================ observables
@@ -676,29 +738,58 @@ TDZ_DEV void observe_fp64(const GeomDev& g, const RunDev& run, const Lane& L, do
   out[3] = kk;
 }
 
+// Mixed path: c <- c + w (double-float), difference history d2 <- d1, d1 <- w, next predictor
+// w <- 2 d1 - d2 (quadratic extrapolation, once two differences exist), and the observables of
+// the new state, in one pass. The new values of the P rows above the chunk (the previous lane's
+// separator) are formed from that lane's c and w before anyone overwrites them.
 template <int P>
-TDZ_DEV void observe_mixed(const GeomDev& g, const RunDev& run, const Lane& L, double out[4]) {
-  const float4* c = static_cast<const float4*>(run.state);
+TDZ_DEV void update_observe_mixed(const GeomDev& g, const RunDev& run, const Lane& L, int hist_new, double out[4]) {
+  float4* __restrict__ c = static_cast<float4*>(run.state);
+  float4* __restrict__ W = run.W;
+  const float4* __restrict__ A4 = static_cast<const float4*>(g.S);
+  const float2* __restrict__ HD = static_cast<const float2*>(g.H);
+  const float4* __restrict__ GK = static_cast<const float4*>(g.G);
   cff cwin[P + 1];
 #pragma unroll
   for (int d = 0; d <= P; ++d) cwin[d] = cff{{0.f, 0.f}, {0.f, 0.f}};
+  if (L.active && L.up) {
+#pragma unroll
+    for (int q = 0; q < P; ++q) {  // row -P+q of chunk k-1 -> cwin[P-1-q] (the loop shifts before use)
+      const int idx = ridx(L.m - P + q, L.k - 1);
+      const float4 cq = c[idx], wq = W[idx];
+      cwin[P - 1 - q] = cff{ff_add(ff{cq.x, cq.z}, ff{wq.x, wq.z}), ff_add(ff{cq.y, cq.w}, ff{wq.y, wq.w})};
+    }
+  }
+  __syncwarp();
   ffacc s, dd, gg, kk;
   acc_zero(s);
   acc_zero(dd);
   acc_zero(gg);
   acc_zero(kk);
-  for (int j = -P; j < L.m; ++j) {
-    int row, chunk;
-    const bool ok = locate(L, j, row, chunk);
-    cff cj = cff{{0.f, 0.f}, {0.f, 0.f}};
-    if (ok) {
-      const float4 q = c[ridx(row, chunk)];
-      cj = cff{{q.x, q.z}, {q.y, q.w}};
-    }
+  if (L.active) {
+    for (int j = 0; j < L.m; ++j) {
+      const int idx = ridx(j, L.k);
+      const float4 cq = c[idx], wq = W[idx];
+      const cff cj = cff{ff_add(ff{cq.x, cq.z}, ff{wq.x, wq.z}), ff_add(ff{cq.y, cq.w}, ff{wq.y, wq.w})};
+      c[idx] = make_float4(cj.r.h, cj.i.h, cj.r.l, cj.i.l);
+      const float2 n1 = make_float2(wq.x + wq.z, wq.y + wq.w);
+      const float2 o1 = run.d1[idx];
+      run.d2[idx] = o1;
+      run.d1[idx] = n1;
+      const float2 e = (hist_new >= 2) ? make_float2(2.f * n1.x - o1.x, 2.f * n1.y - o1.y) : make_float2(0.f, 0.f);
+      W[idx] = make_float4(e.x, e.y, 0.f, 0.f);
 #pragma unroll
-    for (int d = P; d >= 1; --d) cwin[d] = cwin[d - 1];
-    cwin[0] = cj;
-    if (j >= 0) {
+      for (int d = P; d >= 1; --d) cwin[d] = cwin[d - 1];
+      cwin[0] = cj;
+      // per-row partial sums, two independent chains per matrix, folded into the lane totals once
+      ffacc ps[2], pd[2], pg[2], pk[2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        acc_zero(ps[q]);
+        acc_zero(pd[q]);
+        acc_zero(pg[q]);
+        acc_zero(pk[q]);
+      }
 #pragma unroll
       for (int d = 0; d <= P; ++d) {
         ffacc ua;
@@ -707,19 +798,22 @@ TDZ_DEV void observe_mixed(const GeomDev& g, const RunDev& run, const Lane& L, d
         acc_mul(ua, cj.i, cwin[d].i);
         ff u = acc_get(ua);
         if (d > 0) u = ff{2.f * u.h, 2.f * u.l};
-        const int idx = bidx<P>(row, d, chunk);
-        const float2 sv = static_cast<const float2*>(g.S)[idx];
-        const float2 dv = static_cast<const float2*>(g.D)[idx];
-        const float2 gv = static_cast<const float2*>(g.G)[idx];
-        const float2 kv = static_cast<const float2*>(g.Km)[idx];
-        acc_mul(s, ff{sv.x, sv.y}, u);
-        acc_mul(dd, ff{dv.x, dv.y}, u);
-        acc_mul(gg, ff{gv.x, gv.y}, u);
-        acc_mul(kk, ff{kv.x, kv.y}, u);
+        const int bi = bidx<P>(j, d, L.k);
+        const float4 v = __ldg(A4 + bi);
+        const float2 lo = __ldg(HD + bi);
+        const float4 gk = __ldg(GK + bi);
+        acc_mul(ps[d & 1], ff{v.x, v.w}, u);
+        acc_mul(pd[d & 1], ff{v.z, lo.y}, u);
+        acc_mul(pg[d & 1], ff{gk.x, gk.y}, u);
+        acc_mul(pk[d & 1], ff{gk.z, gk.w}, u);
       }
+      acc_add(s, ff_add(acc_get(ps[0]), acc_get(ps[1])));
+      acc_add(dd, ff_add(acc_get(pd[0]), acc_get(pd[1])));
+      acc_add(gg, ff_add(acc_get(pg[0]), acc_get(pg[1])));
+      acc_add(kk, ff_add(acc_get(pk[0]), acc_get(pk[1])));
     }
   }
-  ff fs = acc_get(s), fd = acc_get(dd), fg = acc_get(gg), fk = acc_get(kk);
+  const ff fs = acc_get(s), fd = acc_get(dd), fg = acc_get(gg), fk = acc_get(kk);
   out[0] = (double)fs.h + (double)fs.l;
   out[1] = (double)fd.h + (double)fd.l;
   out[2] = (double)fg.h + (double)fg.l;
@@ -733,12 +827,19 @@ TDZ_DEV double warp_sum(double v) {
 }
 
 // ============================================================================ the kernel
+// One block = `warps per block` runs of neighbouring size (the run order is longest first) that
+// advance in lock step: every warp owns one run, and the block crosses each phase of a step
+// together (block barriers), so all warps of an SM execute the same code region at a time. The
+// adaptive refinement decides collectively how many extra solves the block makes; warps whose
+// run is already converged skip the work of those rounds.
 template <int P, bool MIXED>
 __global__ void __launch_bounds__(256) cn1d_kernel(StepArgs A) {
   using T = typename std::conditional<MIXED, float, double>::type;
   extern __shared__ unsigned char smem_raw[];
+  __shared__ int s_base;
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
+  const int wpb = blockDim.x >> 5;
   const size_t per_warp = (size_t)(2 * 31 * P * P + 31 * P + P * P) * sizeof(cx<T>);
   cx<T>* base = reinterpret_cast<cx<T>*>(smem_raw + wib * per_warp);
   Red<T> red;
@@ -748,133 +849,134 @@ __global__ void __launch_bounds__(256) cn1d_kernel(StepArgs A) {
   red.Wt = base + 2 * 31 * P * P + 31 * P;
 
   while (true) {
-    int item = 0;
-    if (lane == 0) item = atomicAdd(A.counter, 1);
-    item = __shfl_sync(0xffffffffu, item, 0);
-    if (item >= A.nruns) break;
-    const int rid = A.order[item];
+    if (threadIdx.x == 0) s_base = atomicAdd(A.counter, wpb);
+    __syncthreads();
+    const int item = s_base + wib;
+    const bool done = s_base >= A.nruns;
+    __syncthreads();
+    if (done) break;
+    const bool has = item < A.nruns;
+    const int rid = has ? A.order[item] : 0;
     RunDev run = A.runs[rid];
     const GeomDev g = A.geoms[run.geom];
     Lane L;
     L.k = lane;
-    L.K = g.K;
+    L.K = has ? g.K : 1;
     L.m = g.m;
-    L.active = lane < g.K;
+    L.active = has && lane < g.K;
     L.up = L.active && lane >= 1;
     L.dn = L.active && lane < g.K - 1;
     L.mI = L.dn ? g.m - P : g.m;
     const double* E = A.field + (size_t)rid * (A.nsteps + 1);
     double* obs = A.obs + (size_t)rid * A.nsteps * 5;
-    int status = run.status;
+    int status = has ? run.status : TDZ_OK;
     double max_rel = 0.0;
     long long nsolve = 0;
     int hist = run.hist;
-    for (long long s = 0; s < A.nsteps && status == TDZ_OK; ++s) {
+    for (long long s = 0; s < A.nsteps; ++s) {
+      const bool work = has && status == TDZ_OK;
+      Lane W = L;  // lanes of a warp whose run is finished or failed do no work this step
+      W.active = L.active && work;
+      W.up = W.active && L.up;
+      W.dn = W.active && L.dn;
+      const int nsep = work ? L.K - 1 : 0;
       const double ebar_d = 0.5 * (E[s] + E[s + 1]);
       const double tau_d = 0.5 * A.dt;
+      double o[4] = {0, 0, 0, 0};
       if constexpr (!MIXED) {
-        if (L.active) rhs_fp64<P>(g, run, L, tau_d, ebar_d);
-        __syncwarp();
-        solve<P, double, false>(g, run, L, tau_d, ebar_d, red, lane);
-        nsolve++;
-        if (L.active) {  // c += delta
-          double2* c = static_cast<double2*>(run.state);
-          const cx<double>* dl = static_cast<const cx<double>*>(run.dl);
-          for (int i = 0; i < L.m; ++i) {
-            double2 v = c[ridx(i, lane)];
-            const cx<double> x = dl[ridx(i, lane)];
-            c[ridx(i, lane)] = make_double2(v.x + x.r, v.y + x.i);
-          }
+        if (W.active) rhs_fp64<P>(g, run, W, tau_d, ebar_d);
+        __syncthreads();
+        if (W.active) sweep1<P, double, false>(g, run, W, tau_d, ebar_d, red);
+        __syncthreads();
+        if (W.up) sweep2<P, double, false>(g, run, W, tau_d, ebar_d, red);
+        __syncthreads();
+        if (nsep > 0) {
+          red_factor<P, double>(red, nsep, lane);
+          red_solve<P, double>(red, nsep, lane);
         }
+        __syncthreads();
+        if (W.active) substitute<P, double, false>(g, run, W, tau_d, ebar_d, red);  // c += delta
+        __syncthreads();
+        nsolve += work;
+        if (W.active) observe_fp64<P>(g, run, W, o);
       } else {
         const float tau_f = (float)tau_d, ebar_f = (float)ebar_d;
         const ff tau_ff = ff{tau_f, (float)(tau_d - (double)tau_f)};
         const ff ebar_ff = ff{ebar_f, (float)(ebar_d - (double)ebar_f)};
-        bool ok = false;
-        double rel = 0.0;
-        for (int it = 0; it <= A.max_it; ++it) {
-          float rr = 0.f, bb = 0.f;
-          if (L.active) rhs_mixed<P>(g, run, L, tau_ff, ebar_ff, rr, bb);
-          const double rrs = warp_sum((double)rr), bbs = warp_sum((double)bb);
-          rel = sqrt(rrs / fmax(bbs, 1e-300));
-          if (it > 0 && rel <= A.tol) {
-            ok = true;
-            break;
-          }
-          if (it == A.max_it) break;
-          __syncwarp();
-          solve<P, float, true>(g, run, L, tau_f, ebar_f, red, lane);
-          nsolve++;
-          if (L.active) {  // w += delta (double-float)
-            const cx<float>* dl = static_cast<const cx<float>*>(run.dl);
-            for (int i = 0; i < L.m; ++i) {
-              const float4 q = run.W[ridx(i, lane)];
-              const cx<float> x = dl[ridx(i, lane)];
-              const ff wr = ff_addf(ff{q.x, q.z}, x.r), wi = ff_addf(ff{q.y, q.w}, x.i);
-              run.W[ridx(i, lane)] = make_float4(wr.h, wi.h, wr.l, wi.l);
-            }
-          }
-          __syncwarp();
-          if (it == 0 && hist >= 2) {
-            float r1 = 0.f;
-            if (L.active) r1 = resid_fp32<P>(g, run, L, tau_f, ebar_f);
-            const double r1s = warp_sum((double)r1);
-            rel = sqrt(r1s / fmax(bbs, 1e-300));
-            if (rel <= A.tol) {
+        // residual of the predictor y0 = c + w, then one factorising FP32 solve
+        float rr = 0.f, bb = 0.f;
+        if (W.active) rhs_mixed<P, true>(g, run, W, tau_ff, ebar_ff, rr, bb);
+        const double bbs = fmax(warp_sum((double)bb), 1e-300);
+        const double rel0 = sqrt(warp_sum((double)rr) / bbs);
+        __syncthreads();
+        if (W.active) sweep1<P, float, true>(g, run, W, tau_f, ebar_f, red);
+        __syncthreads();
+        if (W.up) sweep2<P, float, true>(g, run, W, tau_f, ebar_f, red);
+        __syncthreads();
+        if (nsep > 0) {
+          red_factor<P, float>(red, nsep, lane);
+          red_solve<P, float>(red, nsep, lane);
+        }
+        __syncthreads();
+        if (W.active) substitute<P, float, true>(g, run, W, tau_f, ebar_f, red);  // w += delta
+        __syncthreads();
+        nsolve += work;
+        // residual after the solve; refine with the stored factors while above tolerance
+        if (W.active) rhs_mixed<P, false>(g, run, W, tau_ff, ebar_ff, rr, bb);
+        double rel = sqrt(warp_sum((double)rr) / bbs);
+        const double rho = fmin(rel / fmax(rel0, 1e-300), 1.0);  // contraction of one FP32 solve
+        int it = 1;
+        bool ok = !work || rel <= A.tol;
+        bool need = !ok && it < A.max_it;
+        while (__syncthreads_or(need)) {
+          if (need) {
+            resolve<P, float, true>(g, run, W, tau_f, ebar_f, red, lane);
+            nsolve++;
+            ++it;
+            const double predicted = rho * rel;
+            if (predicted <= 0.1 * A.tol && rho < 1e-2) {  // contraction certain: accept unchecked
+              rel = predicted;
               ok = true;
-              break;
             }
           }
-          __syncwarp();
-        }
-        max_rel = fmax(max_rel, rel);
-        if (!ok && status == TDZ_OK) status = TDZ_ENOCONV;
-        // c += w; history; next predictor
-        hist = hist + 1;
-        if (L.active) {
-          float4* c = static_cast<float4*>(run.state);
-          for (int i = 0; i < L.m; ++i) {
-            const float4 q = c[ridx(i, lane)];
-            const float4 wq = run.W[ridx(i, lane)];
-            const ff cr = ff_add(ff{q.x, q.z}, ff{wq.x, wq.z});
-            const ff ci = ff_add(ff{q.y, q.w}, ff{wq.y, wq.w});
-            c[ridx(i, lane)] = make_float4(cr.h, ci.h, cr.l, ci.l);
-            const float2 n1 = make_float2(wq.x + wq.z, wq.y + wq.w);
-            const float2 o1 = run.d1[ridx(i, lane)];
-            run.d2[ridx(i, lane)] = o1;
-            run.d1[ridx(i, lane)] = n1;
-            float2 e = make_float2(0.f, 0.f);
-            if (hist >= 2) e = make_float2(2.f * n1.x - o1.x, 2.f * n1.y - o1.y);
-            run.W[ridx(i, lane)] = make_float4(e.x, e.y, 0.f, 0.f);
+          const bool check = need && !ok;
+          if (check && W.active) rhs_mixed<P, false>(g, run, W, tau_ff, ebar_ff, rr, bb);
+          if (check) {
+            rel = sqrt(warp_sum((double)rr) / bbs);
+            ok = rel <= A.tol;
           }
+          need = need && !ok && it < A.max_it;
         }
-      }
-      __syncwarp();
-      double o[4] = {0, 0, 0, 0};
-      if (L.active) {
-        if constexpr (MIXED) observe_mixed<P>(g, run, L, o);
-        else observe_fp64<P>(g, run, L, o);
+        if (work) {
+          max_rel = fmax(max_rel, rel);
+          if (!ok && status == TDZ_OK) status = TDZ_ENOCONV;
+          hist = hist + 1;
+        }
+        __syncthreads();
+        update_observe_mixed<P>(g, run, W, hist, o);
       }
       const double ns = warp_sum(o[0]), ds = warp_sum(o[1]), gs = warp_sum(o[2]), ks = warp_sum(o[3]);
-      const double Et = E[s + 1];
-      if (lane == 0) {
-        double* row = obs + s * 5;
-        row[0] = (double)(A.step0 + s + 1) * A.dt;
-        row[1] = Et;
-        row[2] = ds;
-        row[3] = -gs - Et * ks;
-        row[4] = ns;
+      if (work) {
+        const double Et = E[s + 1];
+        if (lane == 0) {
+          double* row = obs + s * 5;
+          row[0] = (double)(A.step0 + s + 1) * A.dt;
+          row[1] = Et;
+          row[2] = ds;
+          row[3] = -gs - Et * ks;
+          row[4] = ns;
+        }
+        if (!isfinite(ns) || !isfinite(ds)) status = TDZ_ENONFINITE;
       }
-      if (!isfinite(ns) || !isfinite(ds)) status = TDZ_ENONFINITE;
-      __syncwarp();
+      __syncthreads();
     }
-    if (lane == 0) {
+    if (has && lane == 0) {
       A.runs[rid].status = status;
       A.runs[rid].hist = hist;
       A.runs[rid].max_rel = fmax(run.max_rel, max_rel);
       A.runs[rid].nsolve = run.nsolve + nsolve;
     }
-    __syncwarp();
+    __syncthreads();
   }
 }
 
@@ -1031,45 +1133,63 @@ int tdz_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* 
     b->geo[gi] = {n, m, K};
     const size_t nb = (size_t)m * P1 * LANES;
     const Band* src[5] = {&o.S, &o.H0, &o.D, &o.G, &o.K};
-    void* dst[5];
-    for (int q = 0; q < 5; ++q) {
-      std::vector<double> hd;
-      std::vector<float> hf;
-      if (mixed) hf.assign(nb * 2, 0.f);
-      else hd.assign(nb, 0.0);
-      for (int k = 0; k < K; ++k)
-        for (int i = 0; i < m; ++i) {
-          const int64_t gr = (int64_t)k * m + i;
+    // value of matrix q at interleaved position (i, d, k); padding rows are identity in S
+    auto val = [&](int q, int i, int d, int k) -> double {
+      const int64_t gr = (int64_t)k * m + i;
+      if (k >= K) return 0.0;
+      if (gr < n) return (gr - d >= 0) ? src[q]->at(gr, d) : 0.0;
+      return (q == 0 && d == 0) ? 1.0 : 0.0;
+    };
+    auto hi = [](double v) { return (float)v; };
+    auto lo = [](double v) { return (float)(v - (double)(float)v); };
+    void* dst[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    auto upload = [&](const void* h, size_t bytes) -> void* {
+      void* p = b->alloc(bytes);
+      if (!p) return nullptr;
+      if (cudaMemcpyAsync(p, h, bytes, cudaMemcpyHostToDevice, b->stream) != cudaSuccess) return nullptr;
+      if (cudaStreamSynchronize(b->stream) != cudaSuccess) return nullptr;
+      return p;
+    };
+    if (mixed) {
+      std::vector<float> a4(nb * 4), hd(nb * 2), gk(nb * 4);
+      for (int k = 0; k < LANES; ++k)
+        for (int i = 0; i < m; ++i)
           for (int d = 0; d <= P; ++d) {
-            double v = 0.0;
-            if (gr < n) {
-              if (gr - d >= 0) v = src[q]->at(gr, d);
-            } else if (d == 0 && q == 0) {
-              v = 1.0;  // padding rows: identity in S
-            }
             const size_t idx = ((size_t)i * P1 + d) * LANES + k;
-            if (mixed) {
-              float hi = (float)v;
-              hf[2 * idx] = hi;
-              hf[2 * idx + 1] = (float)(v - (double)hi);
-            } else {
-              hd[idx] = v;
-            }
+            const double S = val(0, i, d, k), H = val(1, i, d, k), D = val(2, i, d, k), Gv = val(3, i, d, k),
+                         Kv = val(4, i, d, k);
+            a4[4 * idx + 0] = hi(S);
+            a4[4 * idx + 1] = hi(H);
+            a4[4 * idx + 2] = hi(D);
+            a4[4 * idx + 3] = lo(S);
+            hd[2 * idx + 0] = lo(H);
+            hd[2 * idx + 1] = lo(D);
+            gk[4 * idx + 0] = hi(Gv);
+            gk[4 * idx + 1] = lo(Gv);
+            gk[4 * idx + 2] = hi(Kv);
+            gk[4 * idx + 3] = lo(Kv);
           }
-        }
-      void* p = b->alloc(nb * (mixed ? 8 : 8));
-      if (!p) {
+      dst[0] = upload(a4.data(), nb * 16);
+      dst[1] = upload(hd.data(), nb * 8);
+      dst[3] = upload(gk.data(), nb * 16);
+      if (!dst[0] || !dst[1] || !dst[3]) {
         delete b;
+        set_error("tdz_batch_create: band upload failed");
         return TDZ_ENOMEM;
       }
-      cudaError_t e = cudaMemcpyAsync(p, mixed ? (const void*)hf.data() : (const void*)hd.data(), nb * 8,
-                                      cudaMemcpyHostToDevice, b->stream);
-      if (e != cudaSuccess) {
-        delete b;
-        return cuda_fail(e, "tdz_batch_create: upload");
+    } else {
+      std::vector<double> hd(nb);
+      for (int q = 0; q < 5; ++q) {
+        for (int k = 0; k < LANES; ++k)
+          for (int i = 0; i < m; ++i)
+            for (int d = 0; d <= P; ++d) hd[((size_t)i * P1 + d) * LANES + k] = val(q, i, d, k);
+        dst[q] = upload(hd.data(), nb * 8);
+        if (!dst[q]) {
+          delete b;
+          set_error("tdz_batch_create: band upload failed");
+          return TDZ_ENOMEM;
+        }
       }
-      cudaStreamSynchronize(b->stream);
-      dst[q] = p;
     }
     hg[gi] = GeomDev{n, m, K, 0, dst[0], dst[1], dst[2], dst[3], dst[4]};
   }
