@@ -92,6 +92,9 @@ struct StepArgs {
 template <int P>
 TDZ_DEV int bidx(int i, int d, int k) { return (i * (P + 1) + d) * LANES + k; }
 TDZ_DEV int ridx(int i, int k) { return i * LANES + k; }
+// L1 prefetch of the line holding p: rows ahead of a lane's sequential row loop are requested
+// early, so the loop does not pay a full memory round trip per row (no registers needed).
+TDZ_DEV void pf(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
 
 // A(i, i-d) entry for the factorisation, in the solve precision T.
 template <int P, class T, bool MIXED>
@@ -145,6 +148,11 @@ TDZ_DEV void sweep1(const GeomDev& g, const RunDev& run, const Lane& L, T tau, T
   }
   for (int i = 0; i < L.mI; ++i) {
     const int r = i + P;  // row entering the window
+    if (r + 2 < L.m) {
+#pragma unroll
+      for (int b = 0; b <= P; ++b) pf(static_cast<const char*>(g.S) + (size_t)bidx<P>(r + 2, b, k) * (MIXED ? 16 : 8));
+      pf(rhs + ridx(r + 2, k));
+    }
     if (r < L.m) {
 #pragma unroll
       for (int b = 0; b <= P; ++b) w[P][b] = a_entry<P, T, MIXED>(g, bidx<P>(r, P - b, k), tau, ebar);
@@ -218,6 +226,11 @@ TDZ_DEV void sweep2(const GeomDev& g, const RunDev& run, const Lane& L, T tau, T
   for (int t = 0; t < L.mI; ++t) {
     const int r = r0 - t;
     const int q = r - P;  // row entering the window
+    if (q - 2 >= 0) {
+#pragma unroll
+      for (int b = 0; b <= P; ++b) pf(static_cast<const char*>(g.S) + (size_t)bidx<P>(q - 2, b, k) * (MIXED ? 16 : 8));
+      pf(rhs + ridx(q - 2, k));
+    }
 #pragma unroll
     for (int b = 0; b <= P; ++b) {
       const int rb = r - b;  // A(q, rb) stored at row rb (rb >= q), diagonal P - b
@@ -388,6 +401,12 @@ TDZ_DEV void substitute(const GeomDev& g, const RunDev& run, const Lane& L, T ta
 #pragma unroll
   for (int d = 0; d <= P; ++d) gw[d] = czero<T>();
   for (int i = 0; i < L.mI; ++i) {
+    if (i + 4 < L.mI) {
+      pf(rhs + ridx(i + 4, k));
+      pf(Dv + ridx(i + 4, k));
+#pragma unroll
+      for (int d = 0; d < P; ++d) pf(Lc + ((i + 4) * P + d) * LANES + k);
+    }
     cx<T> b = rhs[ridx(i, k)];
     if (L.up && i < P) {
 #pragma unroll
@@ -406,6 +425,13 @@ TDZ_DEV void substitute(const GeomDev& g, const RunDev& run, const Lane& L, T ta
 #pragma unroll
   for (int d = 1; d <= P; ++d) xw[d] = xdn[d - 1];
   for (int i = L.mI - 1; i >= 0; --i) {
+    if (i - 4 >= 0) {
+      pf(gd + ridx(i - 4, k));
+      if constexpr (MIXED) pf(run.W + ridx(i - 4, k));
+      else pf(static_cast<const double2*>(run.state) + ridx(i - 4, k));
+#pragma unroll
+      for (int d = 0; d < P; ++d) pf(Lc + ((i - 4) * P + d) * LANES + k);
+    }
     cx<T> x = gd[ridx(i, k)];
 #pragma unroll
     for (int d = 1; d <= P; ++d) x = cmsub(x, Lc[(i * P + d - 1) * LANES + k], xw[d]);
@@ -455,6 +481,12 @@ TDZ_DEV void resolve(const GeomDev& g, const RunDev& run, const Lane& L, T tau, 
 #pragma unroll
     for (int d = 0; d <= P; ++d) gw[d] = czero<T>();
     for (int i = 0; i < L.mI; ++i) {
+      if (i + 4 < L.mI) {
+        pf(rhs + ridx(i + 4, k));
+        pf(Dv + ridx(i + 4, k));
+#pragma unroll
+        for (int d = 0; d < P; ++d) pf(Lc + ((i + 4) * P + d) * LANES + k);
+      }
       cx<T> b = rhs[ridx(i, k)];
 #pragma unroll
       for (int d = 1; d <= P; ++d)
@@ -484,6 +516,11 @@ TDZ_DEV void resolve(const GeomDev& g, const RunDev& run, const Lane& L, T tau, 
 #pragma unroll
     for (int d = 0; d <= P; ++d) zw[d] = czero<T>();
     for (int i = L.mI - 1; i >= 0; --i) {
+      if (i - 4 >= 0) {
+        pf(gd + ridx(i - 4, k));
+#pragma unroll
+        for (int d = 0; d < P; ++d) pf(Lc + ((i - 4) * P + d) * LANES + k);
+      }
       cx<T> z = gd[ridx(i, k)];
 #pragma unroll
       for (int d = 1; d <= P; ++d) z = cmsub(z, Lc[(i * P + d - 1) * LANES + k], zw[d]);
@@ -615,6 +652,20 @@ TDZ_DEV void rhs_mixed(const GeomDev& g, const RunDev& run, const Lane& L, ff ta
   for (int j = -P; j < L.m + P; ++j) {
     int row, chunk;
     const bool ok = locate(L, j, row, chunk);
+    {
+      int r2, c2;
+      if (j + 2 < L.m + P && locate(L, j + 2, r2, c2)) {
+        pf(c + ridx(r2, c2));
+        pf(W + ridx(r2, c2));
+        if (j + 2 >= 0) {
+#pragma unroll
+          for (int d = 0; d <= P; ++d) {
+            pf(A4 + bidx<P>(r2, d, c2));
+            pf(HD + bidx<P>(r2, d, c2));
+          }
+        }
+      }
+    }
     cff u = cff{{0.f, 0.f}, {0.f, 0.f}}, w = u;
     float2 chi = make_float2(0.f, 0.f);
     ff s[P + 1], h[P + 1];
@@ -769,6 +820,18 @@ TDZ_DEV void update_observe_mixed(const GeomDev& g, const RunDev& run, const Lan
   if (L.active) {
     for (int j = 0; j < L.m; ++j) {
       const int idx = ridx(j, L.k);
+      if (j + 2 < L.m) {
+        const int i2 = ridx(j + 2, L.k);
+        pf(c + i2);
+        pf(W + i2);
+        pf(run.d1 + i2);
+#pragma unroll
+        for (int d = 0; d <= P; ++d) {
+          pf(A4 + bidx<P>(j + 2, d, L.k));
+          pf(HD + bidx<P>(j + 2, d, L.k));
+          pf(GK + bidx<P>(j + 2, d, L.k));
+        }
+      }
       const float4 cq = c[idx], wq = W[idx];
       const cff cj = cff{ff_add(ff{cq.x, cq.z}, ff{wq.x, wq.z}), ff_add(ff{cq.y, cq.w}, ff{wq.y, wq.w})};
       c[idx] = make_float4(cj.r.h, cj.i.h, cj.r.l, cj.i.l);
