@@ -1077,6 +1077,7 @@ size_t smem_per_warp(int P, bool mixed) {
 }  // namespace
 
 struct tdz_batch {
+  tdz::NdBatch* nd = nullptr;  // 2-D / 3-D batches are served by tdz_nd.cu
   int prec = TDZ_FP64;
   int P = 0;
   int nruns = 0;
@@ -1113,6 +1114,7 @@ struct tdz_batch {
     return p;
   }
   ~tdz_batch() {
+    if (nd) tdz::nd_batch_destroy(nd);
     for (auto& b : bufs) cudaFree(b.p);
     if (d_obs) cudaFree(d_obs);
     if (d_field) cudaFree(d_field);
@@ -1153,10 +1155,28 @@ int tdz_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* 
                      void* cuda_stream, tdz_batch** out) {
   if (!ops || nops < 1 || nruns < 1 || !ops_index || !out) return TDZ_EINVAL;
   if (precision != TDZ_FP64 && precision != TDZ_MIXED) return TDZ_EINVAL;
-  for (int g = 0; g < nops; ++g) {
+  for (int g = 0; g < nops; ++g)
     if (!ops[g]) return TDZ_EINVAL;
+  for (int r = 0; r < nruns; ++r)
+    if (ops_index[r] < 0 || ops_index[r] >= nops) return TDZ_EINVAL;
+  if (ops[0]->o.dim > 1) {
+    tdz_batch* b = new (std::nothrow) tdz_batch;
+    if (!b) return TDZ_ENOMEM;
+    b->prec = precision;
+    b->nruns = nruns;
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+    const int rc = tdz::nd_batch_create(ops, nops, nruns, ops_index, precision, cuda_stream, &b->nd);
+    if (rc != TDZ_OK) {
+      delete b;
+      return rc;
+    }
+    for (int r = 0; r < nruns; ++r) b->total_dof += tdz::nd_run_size(b->nd, r);
+    *out = b;
+    return TDZ_OK;
+  }
+  for (int g = 0; g < nops; ++g) {
     if (ops[g]->o.dim != 1) {
-      set_error("tdz_batch_create: only 1-D operators are supported by this build");
+      set_error("tdz_batch_create: all operators of a batch must have the same dimension");
       return TDZ_EUNSUPPORTED;
     }
     if (ops[g]->o.n[0] < ops[g]->o.p[0] + 1) {
@@ -1321,6 +1341,7 @@ int tdz_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* 
 
 int tdz_batch_set_refinement(tdz_batch* b, double tol, int max_solves) {
   if (!b || !(tol > 0) || max_solves < 1 || max_solves > 64) return TDZ_EINVAL;
+  if (b->nd) tdz::nd_set_refinement(b->nd, tol, max_solves);
   b->tol = tol;
   b->max_it = max_solves;
   return TDZ_OK;
@@ -1336,6 +1357,7 @@ int tdz_batch_info(const tdz_batch* b, int* nruns, int64_t* total_dof, size_t* d
 
 int tdz_set_state(tdz_batch* b, int run, const double* c) {
   if (!b || !c || run < 0 || run >= b->nruns) return TDZ_EINVAL;
+  if (b->nd) return tdz::nd_set_state(b->nd, run, c, is_device_ptr(c));
   const auto& G = b->geo[b->run_geom[run]];
   const int n = G.n, m = G.m;
   std::vector<double> hc((size_t)2 * n);
@@ -1392,6 +1414,7 @@ int tdz_set_state(tdz_batch* b, int run, const double* c) {
 
 int tdz_get_state(const tdz_batch* b, int run, double* c) {
   if (!b || !c || run < 0 || run >= b->nruns) return TDZ_EINVAL;
+  if (b->nd) return tdz::nd_get_state(b->nd, run, c, is_device_ptr(c));
   const auto& G = b->geo[b->run_geom[run]];
   const int n = G.n, m = G.m;
   const size_t rows = (size_t)m * LANES;
@@ -1431,6 +1454,27 @@ int tdz_get_state(const tdz_batch* b, int run, double* c) {
 
 int tdz_propagate(tdz_batch* b, const double* field, double dt, int64_t step0, int64_t nsteps) {
   if (!b || !field || nsteps < 1 || step0 < 0 || !(dt > 0) || !std::isfinite(dt)) return TDZ_EINVAL;
+  if (b->nd) {
+    // the 2-D/3-D driver reads the field samples on the host
+    const size_t cnt = (size_t)b->nruns * (nsteps + 1);
+    std::vector<double> hf;
+    const double* fh = field;
+    const int D = tdz::nd_dim(b->nd);
+    if (is_device_ptr(field)) {
+      hf.resize(cnt * D);
+      cudaError_t e = cudaMemcpy(hf.data(), field, sizeof(double) * cnt * D, cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) return cuda_fail(e, "tdz_propagate: field download");
+      fh = hf.data();
+    }
+    for (size_t k = 0; k < cnt * D; ++k)
+      if (!std::isfinite(fh[k])) {
+        set_error("tdz_propagate: non-finite field sample");
+        return TDZ_ENONFINITE;
+      }
+    const int rc = tdz::nd_propagate(b->nd, fh, dt, step0, nsteps);
+    b->last_nsteps = nsteps;
+    return rc;
+  }
   const size_t need = (size_t)b->nruns * (nsteps + 1);
   const double* dfield = field;
   cudaError_t e;
@@ -1481,6 +1525,7 @@ int tdz_propagate(tdz_batch* b, const double* field, double dt, int64_t step0, i
 
 int tdz_observe(const tdz_batch* b, int run, double* out, int* status) {
   if (!b || run < 0 || run >= b->nruns) return TDZ_EINVAL;
+  if (b->nd) return tdz::nd_observe(b->nd, run, out, status, out ? is_device_ptr(out) : false);
   cudaError_t e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return cuda_fail(e, "tdz_observe");
   if (out && b->last_nsteps > 0) {
@@ -1499,6 +1544,7 @@ int tdz_observe(const tdz_batch* b, int run, double* out, int* status) {
 
 int tdz_refine_stats(const tdz_batch* b, double* max_rel_residual, double* mean_solves) {
   if (!b) return TDZ_EINVAL;
+  if (b->nd) return tdz::nd_stats(b->nd, max_rel_residual, mean_solves, nullptr);
   cudaError_t e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return cuda_fail(e, "tdz_refine_stats");
   std::vector<RunDev> r(b->nruns);

@@ -212,6 +212,41 @@ static void assemble_1d(const Basis& B, const Medium& med, Ops& o) {
   for (size_t k = 0; k < o.H0.a.size(); ++k) o.H0.a[k] = o.T.a[k] + o.V.a[k];
 }
 
+// ----------------------------------------------------------------------------- 2-D / 3-D factors
+// Per-axis 1-D bands of the tensor-product basis (Eq. tensor3d): S_a, the unit-mass kinetic factor
+// T1_a = 1/2 <N'|N'> and the dipole factor D_a, by the same element quadrature as in 1-D. The
+// non-separable potential and mass are applied on the GPU at the Gauss points of the same tables.
+static void assemble_axis(const Basis& B, Band& S, Band& T1, Band& D) {
+  const int p = B.p, nq = B.nq, P1 = p + 1;
+  const int64_t n = B.nfun - 2;
+  for (Band* m : {&S, &T1, &D}) {
+    m->n = n;
+    m->p = p;
+    m->a.assign((size_t)n * P1, 0.0);
+  }
+  for (int64_t e = 0; e < B.nelem(); ++e) {
+    const int64_t first = B.span[e] - p;
+    for (int a = 0; a < P1; ++a)
+      for (int c = 0; c <= a; ++c) {
+        const int64_t fi = first + a, fj = first + c;
+        if (fj < 1 || fi > B.nfun - 2) continue;
+        double s = 0, t = 0, d = 0;
+        for (int q = 0; q < nq; ++q) {
+          const double w = B.wq[e * nq + q], x = B.xq[e * nq + q];
+          const double* N = &B.val[(e * nq + q) * P1];
+          const double* dN = &B.der[(e * nq + q) * P1];
+          s += w * N[a] * N[c];
+          t += 0.5 * w * dN[a] * dN[c];
+          d += w * x * N[a] * N[c];
+        }
+        const size_t k = (size_t)(fi - 1) * P1 + (fi - fj);
+        S.a[k] += s;
+        T1.a[k] += t;
+        D.a[k] += d;
+      }
+  }
+}
+
 // ----------------------------------------------------------------------------- ground state
 // Real symmetric band LDL^T (no pivoting; used for H0 - sigma S with sigma below the spectrum,
 // which is positive definite) and the matching solve.
@@ -357,12 +392,22 @@ void tdz_basis_destroy(tdz_basis* b) { delete b; }
 
 int tdz_assemble(const tdz_basis* const* axes, int dim, const tdz_medium* medium, tdz_ops** out) {
   if (!axes || !medium || !out || dim < 1 || dim > 3) return TDZ_EINVAL;
-  if (dim != 1) {
-    set_error("tdz_assemble: only dim = 1 is built in this version");
-    return TDZ_EUNSUPPORTED;
-  }
   for (int a = 0; a < dim; ++a)
     if (!axes[a]) return TDZ_EINVAL;
+  if (dim > 1) {
+    for (int a = 0; a < dim; ++a) {
+      const Basis& B = axes[a]->b;
+      if (B.p != axes[0]->b.p) {
+        set_error("tdz_assemble: all axes must have the same degree");
+        return TDZ_EUNSUPPORTED;
+      }
+      for (int64_t e = 0; e < B.nelem(); ++e)
+        if (B.span[e] != e + B.p) {
+          set_error("tdz_assemble: 2-D/3-D needs distinct interior knots (one element per span)");
+          return TDZ_EUNSUPPORTED;
+        }
+    }
+  }
   Medium med;
   med.mass_kind = medium->mass_kind;
   med.pot_kind = medium->pot_kind;
@@ -387,15 +432,29 @@ int tdz_assemble(const tdz_basis* const* axes, int dim, const tdz_medium* medium
     }
   }
   if (med.mass_kind == TDZ_MASS_CONST && !(med.mass_par[0] > 0)) return TDZ_EINVAL;
+  if (dim > 1 && (med.mass_kind == TDZ_MASS_LAYERS || med.mass_kind == TDZ_MASS_QUESNE ||
+                  med.pot_kind == TDZ_POT_LAYERS || med.pot_kind == TDZ_POT_QUESNE || med.pot_kind == TDZ_POT_H2P)) {
+    set_error("tdz_assemble: 1-D-only medium kind in a 2-D/3-D assembly");
+    return TDZ_EINVAL;
+  }
   tdz_ops* h = new (std::nothrow) tdz_ops;
   if (!h) return TDZ_ENOMEM;
   Ops& o = h->o;
   o.dim = dim;
   o.med = med;
-  o.n[0] = axes[0]->b.nfun - 2;
-  o.p[0] = axes[0]->b.p;
   try {
-    assemble_1d(axes[0]->b, med, o);
+    for (int a = 0; a < dim; ++a) {
+      o.n[a] = axes[a]->b.nfun - 2;
+      o.p[a] = axes[a]->b.p;
+    }
+    if (dim == 1) {
+      assemble_1d(axes[0]->b, med, o);
+    } else {
+      for (int a = 0; a < dim; ++a) {
+        o.axis[a] = axes[a]->b;
+        assemble_axis(o.axis[a], o.Sa[a], o.T1a[a], o.Da[a]);
+      }
+    }
   } catch (const std::bad_alloc&) {
     delete h;
     return TDZ_ENOMEM;
@@ -415,8 +474,20 @@ int tdz_ops_info(const tdz_ops* ops, int* dim, int64_t* shape, int* degree) {
 }
 
 int tdz_ops_band(const tdz_ops* ops, int which, int axis, double* out) {
-  if (!ops || !out || axis != 0 || ops->o.dim != 1) return TDZ_EINVAL;
+  if (!ops || !out || axis < 0 || axis >= ops->o.dim) return TDZ_EINVAL;
   const Band* m = nullptr;
+  if (ops->o.dim > 1) {
+    switch (which) {
+      case TDZ_MAT_S: m = &ops->o.Sa[axis]; break;
+      case TDZ_MAT_T: m = &ops->o.T1a[axis]; break;
+      case TDZ_MAT_D: m = &ops->o.Da[axis]; break;
+      default:
+        set_error("tdz_ops_band: 2-D/3-D operators expose the per-axis S, T (unit mass) and D factors");
+        return TDZ_EINVAL;
+    }
+    std::memcpy(out, m->a.data(), sizeof(double) * m->a.size());
+    return TDZ_OK;
+  }
   switch (which) {
     case TDZ_MAT_S: m = &ops->o.S; break;
     case TDZ_MAT_T: m = &ops->o.T; break;

@@ -47,7 +47,24 @@ struct Ops {
   Medium med;
   // 1-D matrices
   Band S, T, V, H0, D, G, K;
+  // 2-D / 3-D: per-axis 1-D factors (unit-mass kinetic T1 = 1/2 <N'|N'>) and quadrature tables
+  Band Sa[3], T1a[3], Da[3];
+  Basis axis[3];
 };
+
+// 2-D / 3-D batches (tdz_nd.cu), reached through the public tdz_batch_* entry points
+struct NdBatch;
+int nd_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* ops_index, int precision, void* stream,
+                    NdBatch** out);
+void nd_batch_destroy(NdBatch* b);
+long long nd_run_size(const NdBatch* b, int run);
+int nd_set_state(NdBatch* b, int run, const double* c, bool device);
+int nd_get_state(const NdBatch* b, int run, double* c, bool device);
+int nd_propagate(NdBatch* b, const double* field_host, double dt, long long step0, long long nsteps);
+int nd_observe(const NdBatch* b, int run, double* out, int* status, bool device);
+int nd_stats(const NdBatch* b, double* max_rel, double* solves, double* iters);
+void nd_set_refinement(NdBatch* b, double tol, int max_it);
+int nd_dim(const NdBatch* b);
 
 }  // namespace tdz
 

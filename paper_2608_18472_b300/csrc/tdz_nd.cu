@@ -1,0 +1,1116 @@
+// 2-D / 3-D Crank-Nicolson propagation on sm_103a (tensor-product B-spline basis, Eq. tensor3d).
+//
+// Per step (Sec. "Time propagation", Eq. cn_system) the system A_n c^{n+1} = B_n c^n with
+//   A_n = S + i tau (T + V + sum_a Ebar_a D_a),  B_n = 2S - A_n,
+// is solved in correction form c^{n+1} = c^n + delta, A_n delta = r0 = 2 (S c - A_n c), by
+// preconditioned COCG (conjugate orthogonal CG for complex symmetric A; bilinear products x^T y).
+//
+// Operator application (no global matrix is ever formed):
+//   * separable terms (S, constant-mass kinetic T, dipoles D_a) are Kronecker products of the
+//     per-axis 1-D bands, applied one axis at a time;
+//   * the potential V (and, for a position-dependent mass, the kinetic term
+//     1/2 sum_a <d_a B| m^-1 |d_a B>, Eq. bdd_elem) by sum factorisation at the Gauss points:
+//     interpolate axis by axis to the points, multiply by w_q f(r_q) with f evaluated on the fly
+//     from the medium, project back axis by axis (Sec. "Parallel assembly" quadrature).
+// Preconditioner: M = (x)_a P_a, P_a = S_a + i tau mbar T1_a (field free, factored once per call),
+// applied as independent banded line solves along each axis.
+// Precision: binary64 throughout (TDZ_FP64), or FP32 COCG inside an outer binary64 residual
+// refinement (TDZ_MIXED). Reductions accumulate in binary64.
+// Observables (Sec. "Dipoles"): norm = c^H S c and d_a = c^H D_a c as Kronecker quadratic forms;
+// c^H G_a c (G_a = <m^-1 d_a V>) and c^H K c (K = <m^-1>) as reductions over the Gauss points.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "tdz_arith.cuh"
+#include "tdz_internal.h"
+
+namespace tdz {
+namespace nd {
+
+constexpr int TPB = 256;
+
+struct AxisDev {
+  int n, E, nq, Q;
+  const double* B;   // [Q][P+1] basis values at point q (element q/nq), column r <-> DoF e + r - 1
+  const double* dB;  // [Q][P+1] first derivatives
+  const double* x;   // [Q] point coordinates
+  const double* w;   // [Q] weights (incl. Jacobian)
+  const double* S;   // [n][P+1] lower bands
+  const double* T1;
+  const double* D;
+};
+
+struct MediumDev {
+  int mass_kind, pot_kind;
+  double mp[4], vp[4];
+};
+
+// f(r) at a Gauss point. kind: 0 = V, 1 = 1/2 m^-1 (kinetic weight), 2 = m^-1 dV/dx_axis, 3 = m^-1
+__device__ __forceinline__ double medium_f(const MediumDev& M, int kind, int axis, const double* r, int dim) {
+  double minv = 1.0;
+  if (M.mass_kind == TDZ_MASS_CONST) {
+    minv = 1.0 / M.mp[0];
+  } else if (M.mass_kind == TDZ_MASS_ELLIPSE) {
+    const double u = r[0] / M.mp[0], v = dim > 1 ? r[1] / M.mp[1] : 0.0;
+    minv = (u * u + v * v < 1.0) ? 1.0 / M.mp[2] : 1.0 / M.mp[3];
+  }
+  if (kind == 1) return 0.5 * minv;
+  if (kind == 3) return minv;
+  double r2 = 0.0;
+  for (int a = 0; a < dim; ++a) r2 += r[a] * r[a];
+  if (kind == 0) {
+    switch (M.pot_kind) {
+      case TDZ_POT_SOFTCORE: return -M.vp[0] / sqrt(r2 + M.vp[1]);
+      case TDZ_POT_HO: {
+        double s = 0.0;
+        for (int a = 0; a < dim; ++a) s += M.vp[a] * M.vp[a] * r[a] * r[a];
+        return 0.5 * s;
+      }
+      case TDZ_POT_ELLIPSE: {
+        const double u = r[0] / M.vp[0], v = dim > 1 ? r[1] / M.vp[1] : 0.0;
+        return (u * u + v * v < 1.0) ? M.vp[2] : M.vp[3];
+      }
+      default: return 0.0;
+    }
+  }
+  // kind 2: m^-1 dV/dx_axis
+  switch (M.pot_kind) {
+    case TDZ_POT_SOFTCORE: {
+      const double q = r2 + M.vp[1];
+      return minv * M.vp[0] * r[axis] / (q * sqrt(q));
+    }
+    case TDZ_POT_HO: return minv * M.vp[axis] * M.vp[axis] * r[axis];
+    default: return 0.0;
+  }
+}
+
+template <class T>
+using C = cx<T>;
+
+// ------------------------------------------------------------------------------- axis band terms
+// out[o][j][i] (+)= sum_t coef_t * sum_d R_t(j, j+d) in_{sel_t}[o][j+d][i]   (R_t real symmetric bands)
+struct BandTerms {
+  int nt;
+  const double* R[4];
+  double cr[4], ci[4];
+  int sel[4];
+};
+
+template <class T, int P>
+__global__ void k_axis_band(BandTerms bt, const C<T>* __restrict__ in0, const C<T>* __restrict__ in1,
+                            C<T>* __restrict__ out, long long outer, int L, long long inner, int accumulate) {
+  const long long total = outer * L * inner;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long i = idx % inner;
+    const long long oj = idx / inner;
+    const int j = (int)(oj % L);
+    const long long o = oj / L;
+    T ar = 0, ai = 0;
+    for (int t = 0; t < bt.nt; ++t) {
+      const C<T>* in = bt.sel[t] ? in1 : in0;
+      const double* R = bt.R[t];
+      T sr = 0, si = 0;
+#pragma unroll
+      for (int d = -P; d <= P; ++d) {
+        const int jj = j + d;
+        if (jj < 0 || jj >= L) continue;
+        const int hi = jj > j ? jj : j;
+        const T m = (T)R[(size_t)hi * (P + 1) + (d < 0 ? -d : d)];
+        const C<T> v = in[(o * L + jj) * inner + i];
+        sr += m * v.r;
+        si += m * v.i;
+      }
+      const T cr = (T)bt.cr[t], ci = (T)bt.ci[t];
+      ar += cr * sr - ci * si;
+      ai += cr * si + ci * sr;
+    }
+    if (accumulate) {
+      C<T> v = out[idx];
+      out[idx] = C<T>{v.r + ar, v.i + ai};
+    } else {
+      out[idx] = C<T>{ar, ai};
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------- Gauss point passes
+// interpolation: out[o][q][i] = sum_r Btab[q][r] in[o][e+r-1][i],  e = q / nq
+template <class T, int P>
+__global__ void k_interp(const double* __restrict__ Btab, int nq, int n, int Q, const C<T>* __restrict__ in,
+                         C<T>* __restrict__ out, long long outer, long long inner) {
+  const long long total = outer * Q * inner;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long i = idx % inner;
+    const long long oq = idx / inner;
+    const int q = (int)(oq % Q);
+    const long long o = oq / Q;
+    const int e = q / nq;
+    T sr = 0, si = 0;
+#pragma unroll
+    for (int r = 0; r <= P; ++r) {
+      const int j = e + r - 1;
+      if (j < 0 || j >= n) continue;
+      const T b = (T)Btab[(size_t)q * (P + 1) + r];
+      const C<T> v = in[(o * n + j) * inner + i];
+      sr += b * v.r;
+      si += b * v.i;
+    }
+    out[idx] = C<T>{sr, si};
+  }
+}
+
+// projection: out[o][j][i] = sum_{r, qq} Btab[(e nq + qq)][r] in[o][e nq + qq][i],  e = j + 1 - r
+template <class T, int P>
+__global__ void k_project(const double* __restrict__ Btab, int nq, int n, int E, const C<T>* __restrict__ in,
+                          C<T>* __restrict__ out, long long outer, long long inner, int accumulate) {
+  const int Q = E * nq;
+  const long long total = outer * n * inner;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long i = idx % inner;
+    const long long oj = idx / inner;
+    const int j = (int)(oj % n);
+    const long long o = oj / n;
+    T sr = 0, si = 0;
+#pragma unroll
+    for (int r = 0; r <= P; ++r) {
+      const int e = j + 1 - r;
+      if (e < 0 || e >= E) continue;
+      for (int qq = 0; qq < nq; ++qq) {
+        const int q = e * nq + qq;
+        const T b = (T)Btab[(size_t)q * (P + 1) + r];
+        const C<T> v = in[(o * Q + q) * inner + i];
+        sr += b * v.r;
+        si += b * v.i;
+      }
+    }
+    if (accumulate) {
+      C<T> v = out[idx];
+      out[idx] = C<T>{v.r + sr, v.i + si};
+    } else {
+      out[idx] = C<T>{sr, si};
+    }
+  }
+}
+
+struct QGrid {
+  int dim;
+  int Q[3];
+  const double* x[3];
+  const double* w[3];
+};
+
+// X[q] *= (cr + i ci) w(q) f(r_q)
+template <class T>
+__global__ void k_qmult(C<T>* __restrict__ X, QGrid g, MediumDev M, int kind, int axis, double cr, double ci) {
+  const long long total = (long long)g.Q[0] * g.Q[1] * (g.dim > 2 ? g.Q[2] : 1);
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    long long t = idx;
+    double r[3];
+    double w = 1.0;
+    for (int a = 0; a < g.dim; ++a) {
+      const int q = (int)(t % g.Q[a]);
+      t /= g.Q[a];
+      r[a] = g.x[a][q];
+      w *= g.w[a][q];
+    }
+    const double f = w * medium_f(M, kind, axis, r, g.dim);
+    const T fr = (T)(f * cr), fi = (T)(f * ci);
+    const C<T> v = X[idx];
+    X[idx] = C<T>{fr * v.r - fi * v.i, fr * v.i + fi * v.r};
+  }
+}
+
+// ------------------------------------------------------------------------------- reductions
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  v = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+  if (w == 0) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  }
+  return v;
+}
+
+// sum_q w f |X_q|^2 for kinds 2 (per axis) and 3, into res[slot]
+template <class T>
+__global__ void k_qreduce(const C<T>* __restrict__ X, QGrid g, MediumDev M, int kind, int axis, double* res) {
+  __shared__ double sh[32];
+  const long long total = (long long)g.Q[0] * g.Q[1] * (g.dim > 2 ? g.Q[2] : 1);
+  double acc = 0.0;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    long long t = idx;
+    double r[3];
+    double w = 1.0;
+    for (int a = 0; a < g.dim; ++a) {
+      const int q = (int)(t % g.Q[a]);
+      t /= g.Q[a];
+      r[a] = g.x[a][q];
+      w *= g.w[a][q];
+    }
+    const C<T> v = X[idx];
+    acc += w * medium_f(M, kind, axis, r, g.dim) * ((double)v.r * v.r + (double)v.i * v.i);
+  }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) atomicAdd(res, acc);
+}
+
+// res[0] += Re sum conj(a) b ; res[1] += Im   (Hermitian product, for observables)
+template <class T>
+__global__ void k_hdot(const C<T>* __restrict__ a, const C<T>* __restrict__ b, long long n, double* res) {
+  __shared__ double sh[32];
+  double re = 0.0, im = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const C<T> x = a[i], y = b[i];
+    re += (double)x.r * y.r + (double)x.i * y.i;
+    im += (double)x.r * y.i - (double)x.i * y.r;
+  }
+  re = block_sum(re, sh);
+  im = block_sum(im, sh);
+  if (threadIdx.x == 0) {
+    atomicAdd(res, re);
+    atomicAdd(res + 1, im);
+  }
+}
+
+// res[0..1] += sum a b (bilinear, no conjugation: COCG); res[2] += ||b||^2 if nrm
+template <class T>
+__global__ void k_bdot(const C<T>* __restrict__ a, const C<T>* __restrict__ b, long long n, double* res) {
+  __shared__ double sh[32];
+  double re = 0.0, im = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const C<T> x = a[i], y = b[i];
+    re += (double)x.r * y.r - (double)x.i * y.i;
+    im += (double)x.r * y.i + (double)x.i * y.r;
+  }
+  re = block_sum(re, sh);
+  im = block_sum(im, sh);
+  if (threadIdx.x == 0) {
+    atomicAdd(res, re);
+    atomicAdd(res + 1, im);
+  }
+}
+
+// COCG update: x += alpha p; r -= alpha q; res[0] += ||r||^2
+template <class T>
+__global__ void k_cocg_update(C<T>* __restrict__ x, C<T>* __restrict__ r, const C<T>* __restrict__ p,
+                              const C<T>* __restrict__ q, long long n, double ar, double ai, double* res) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  const T a_r = (T)ar, a_i = (T)ai;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const C<T> pv = p[i], qv = q[i];
+    C<T> xv = x[i], rv = r[i];
+    xv.r += a_r * pv.r - a_i * pv.i;
+    xv.i += a_r * pv.i + a_i * pv.r;
+    rv.r -= a_r * qv.r - a_i * qv.i;
+    rv.i -= a_r * qv.i + a_i * qv.r;
+    x[i] = xv;
+    r[i] = rv;
+    acc += (double)rv.r * rv.r + (double)rv.i * rv.i;
+  }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) atomicAdd(res, acc);
+}
+
+// p = z + beta p
+template <class T>
+__global__ void k_xpby(C<T>* __restrict__ p, const C<T>* __restrict__ z, long long n, double br, double bi) {
+  const T b_r = (T)br, b_i = (T)bi;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const C<T> pv = p[i], zv = z[i];
+    p[i] = C<T>{zv.r + b_r * pv.r - b_i * pv.i, zv.i + b_r * pv.i + b_i * pv.r};
+  }
+}
+
+// y = a*x + b*y  (real scalars), mixed types (Tx -> Ty)
+template <class Tx, class Ty>
+__global__ void k_axby(const C<Tx>* __restrict__ x, C<Ty>* __restrict__ y, long long n, double a, double b) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const C<Tx> xv = x[i];
+    const C<Ty> yv = y[i];
+    y[i] = C<Ty>{(Ty)(a * (double)xv.r + b * (double)yv.r), (Ty)(a * (double)xv.i + b * (double)yv.i)};
+  }
+}
+
+template <class T>
+__global__ void k_nrm(const C<T>* __restrict__ a, long long n, double* res) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const C<T> x = a[i];
+    acc += (double)x.r * x.r + (double)x.i * x.i;
+  }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) atomicAdd(res, acc);
+}
+
+// ------------------------------------------------------------------------------- preconditioner
+// per line along an axis: solve P u = v in place, P = L D L^T with Lc[j][d-1] = L(j+d, j), Dv = D^-1
+template <class T, int P>
+__global__ void k_line_solve(C<T>* __restrict__ v, const C<T>* __restrict__ Lc, const C<T>* __restrict__ Dv,
+                             long long outer, int n, long long inner) {
+  const long long lines = outer * inner;
+  for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < lines;
+       l += (long long)gridDim.x * blockDim.x) {
+    const long long i = l % inner, o = l / inner;
+    C<T>* base = v + o * n * inner + i;
+    C<T> win[P + 1];
+#pragma unroll
+    for (int d = 0; d <= P; ++d) win[d] = czero<T>();
+    for (int j = 0; j < n; ++j) {  // forward: y_j = v_j - sum_d L(j, j-d) y_{j-d}
+      C<T> y = base[(long long)j * inner];
+#pragma unroll
+      for (int d = 1; d <= P; ++d)
+        if (j - d >= 0) y = cmsub(y, Lc[(size_t)(j - d) * P + d - 1], win[d]);
+#pragma unroll
+      for (int d = P; d >= 2; --d) win[d] = win[d - 1];
+      win[1] = y;
+      base[(long long)j * inner] = cmul(y, Dv[j]);
+    }
+#pragma unroll
+    for (int d = 0; d <= P; ++d) win[d] = czero<T>();
+    for (int j = n - 1; j >= 0; --j) {  // backward: x_j = z_j - sum_d L(j+d, j) x_{j+d}
+      C<T> x = base[(long long)j * inner];
+#pragma unroll
+      for (int d = 1; d <= P; ++d)
+        if (j + d < n) x = cmsub(x, Lc[(size_t)j * P + d - 1], win[d]);
+#pragma unroll
+      for (int d = P; d >= 2; --d) win[d] = win[d - 1];
+      win[1] = x;
+      base[(long long)j * inner] = x;
+    }
+  }
+}
+
+}  // namespace nd
+}  // namespace tdz
+
+// ================================================================================= host driver
+using namespace tdz;
+using namespace tdz::nd;
+
+namespace {
+
+int nd_cuda_fail(cudaError_t e, const char* what) {
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return TDZ_ECUDA;
+}
+
+inline int grid_for(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + TPB - 1) / TPB, 148 * 16)); }
+
+struct NdRun {
+  int ops = 0;
+  int dim = 0, P = 0;
+  long long N = 0;
+  int n[3] = {0, 0, 0}, E[3] = {0, 0, 0}, nq[3] = {0, 0, 0}, Q[3] = {0, 0, 0};
+  AxisDev ax[3];
+  MediumDev med;
+  bool const_mass = true;
+  double cm = 1.0;      // m^-1 for constant mass
+  double mbar = 1.0;    // mean m^-1 for the preconditioner
+  double2* c = nullptr;  // state, binary64
+  int status = TDZ_OK;
+  double max_rel = 0.0;
+  long long nsolve = 0;
+  long long iters = 0;
+};
+
+}  // namespace
+
+namespace tdz {
+
+struct NdBatch {
+  int prec = TDZ_FP64;
+  int dim = 0;
+  int P = 0;
+  int nruns = 0;
+  cudaStream_t st = nullptr;
+  std::vector<NdRun> runs;
+  std::vector<Ops> ops;  // copies of the operators (per-axis factors for the preconditioner)
+  std::vector<void*> bufs;
+  // work vectors sized for the largest run: binary64 and solve precision
+  size_t maxN = 0, maxQ = 0;
+  double2 *d_r0 = nullptr, *d_y = nullptr, *d_t1 = nullptr, *d_t2 = nullptr, *d_t3 = nullptr, *d_t4 = nullptr;
+  double2 *d_qa = nullptr, *d_qb = nullptr;
+  double2 *d_z = nullptr, *d_p = nullptr, *d_q = nullptr, *d_rc = nullptr;  // COCG / residual vectors
+  void *w_x = nullptr, *w_r = nullptr, *w_z = nullptr, *w_p = nullptr, *w_q = nullptr, *w_t1 = nullptr, *w_t2 = nullptr,
+       *w_t3 = nullptr, *w_t4 = nullptr, *w_qa = nullptr, *w_qb = nullptr;
+  void* pre_L[3] = {nullptr, nullptr, nullptr};  // per run would be needed for different sizes; refreshed per run
+  void* pre_D[3] = {nullptr, nullptr, nullptr};
+  double* d_red = nullptr;  // reduction scratch (16 doubles)
+  std::vector<double> obs;  // host copy [run][nsteps][2+3dim]
+  long long last_nsteps = 0;
+  double tol = 1e-12;
+  int max_it = 400;
+  double inner_tol = 1e-6;
+  size_t dev_bytes = 0;
+
+  void* alloc(size_t bytes) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+    cudaMemsetAsync(p, 0, bytes, st);
+    bufs.push_back(p);
+    dev_bytes += bytes;
+    return p;
+  }
+  ~NdBatch() {
+    for (void* p : bufs) cudaFree(p);
+  }
+};
+
+}  // namespace tdz
+
+namespace {
+
+// ---------------------------------------------------------------- operator application (templated)
+template <class T, int P>
+struct Apply {
+  NdBatch* b;
+  NdRun* r;
+  C<T>* t1;
+  C<T>* t2;
+  C<T>* t3;
+  C<T>* t4;
+  C<T>* qa;
+  C<T>* qb;
+
+  // shape helpers: lengths of axes with the first `k` axes already in quadrature space
+  void shape(int axis, const int* len, long long& outer, long long& inner) const {
+    inner = 1;
+    outer = 1;
+    for (int a = 0; a < axis; ++a) inner *= len[a];
+    for (int a = axis + 1; a < r->dim; ++a) outer *= len[a];
+  }
+
+  // out = sum over Kronecker terms: factors per axis f[a] applied to input; generic two-stream scheme
+  // out = [S_z] [S_y] (S_x + i tau K_x) x + i tau [S_z] K_y S_x x + i tau K_z S_y S_x x   (3-D)
+  // with K_a = cm T1_a + Ebar_a D_a. Mode "S only": out = (x)S x. Mode "D_a": D_a on axis a, S elsewhere.
+  void kron(const C<T>* x, C<T>* out, int mode, double tau, const double* ebar, int daxis = 0) {
+    const int D = r->dim;
+    int len[3] = {r->n[0], r->n[1], r->n[2]};
+    // streams: a = S-product so far, bsum = accumulated operator
+    const C<T>* a_in = x;
+    const C<T>* b_in = x;
+    C<T>* bufs[4] = {t1, t2, t3, t4};
+    int nb = 0;
+    for (int ax = 0; ax < D; ++ax) {
+      long long outer, inner;
+      shape(ax, len, outer, inner);
+      const AxisDev& A = r->ax[ax];
+      const bool last = ax == D - 1;
+      C<T>* a_out = last ? nullptr : bufs[nb++ % 4];
+      C<T>* b_out = last ? out : bufs[nb++ % 4];
+      BandTerms ta{}, tb{};
+      if (mode == 0) {  // A_sep
+        // a stream: S_ax a
+        ta.nt = 1;
+        ta.R[0] = A.S;
+        ta.cr[0] = 1;
+        ta.ci[0] = 0;
+        ta.sel[0] = 0;
+        // b stream: S_ax b + i tau K_ax a  (for the first axis a == b == x)
+        tb.nt = 3;
+        tb.R[0] = A.S;
+        tb.cr[0] = 1;
+        tb.ci[0] = 0;
+        tb.sel[0] = 1;
+        tb.R[1] = A.T1;
+        tb.cr[1] = 0;
+        tb.ci[1] = tau * (r->const_mass ? r->cm : 0.0);
+        tb.sel[1] = 0;
+        tb.R[2] = A.D;
+        tb.cr[2] = 0;
+        tb.ci[2] = tau * ebar[ax];
+        tb.sel[2] = 0;
+      } else if (mode == 1) {  // S only
+        ta.nt = 1;
+        ta.R[0] = A.S;
+        ta.cr[0] = 1;
+        ta.sel[0] = 0;
+        tb = ta;
+      } else {  // D on daxis, S elsewhere
+        ta.nt = 1;
+        ta.R[0] = ax == daxis ? A.D : A.S;
+        ta.cr[0] = 1;
+        ta.sel[0] = 0;
+        tb = ta;
+      }
+      const long long tot = outer * len[ax] * inner;
+      if (!last && mode == 0)
+        k_axis_band<T, P><<<grid_for(tot), TPB, 0, b->st>>>(ta, a_in, b_in, a_out, outer, len[ax], inner, 0);
+      if (mode == 0) {
+        k_axis_band<T, P><<<grid_for(tot), TPB, 0, b->st>>>(tb, a_in, b_in, b_out, outer, len[ax], inner, 0);
+      } else {
+        k_axis_band<T, P><<<grid_for(tot), TPB, 0, b->st>>>(tb, b_in, b_in, b_out, outer, len[ax], inner, 0);
+      }
+      if (!last && mode == 0) a_in = a_out;
+      b_in = b_out;
+    }
+  }
+
+  // interpolate x to the Gauss grid (derivative on axis `dax`, or none if dax < 0); result in qa
+  C<T>* to_points(const C<T>* x, int dax) {
+    const int D = r->dim;
+    int len[3] = {r->n[0], r->n[1], r->n[2]};
+    const C<T>* in = x;
+    C<T>* out = nullptr;
+    for (int ax = 0; ax < D; ++ax) {
+      long long outer, inner;
+      shape(ax, len, outer, inner);
+      const AxisDev& A = r->ax[ax];
+      out = (ax % 2 == 0) ? qa : qb;
+      const long long tot = outer * A.Q * inner;
+      k_interp<T, P><<<grid_for(tot), TPB, 0, b->st>>>(ax == dax ? A.dB : A.B, A.nq, A.n, A.Q, in, out, outer, inner);
+      len[ax] = A.Q;
+      in = out;
+    }
+    return out;
+  }
+
+  // project a Gauss-grid array back to coefficients, adding into y
+  void from_points(C<T>* X, int dax, C<T>* y) {
+    const int D = r->dim;
+    int len[3] = {r->Q[0], r->Q[1], r->Q[2]};
+    C<T>* in = X;
+    for (int ax = D - 1; ax >= 0; --ax) {
+      long long outer, inner;
+      shape(ax, len, outer, inner);
+      const AxisDev& A = r->ax[ax];
+      const bool last = ax == 0;
+      C<T>* out = last ? y : ((in == qa) ? qb : qa);
+      const long long tot = outer * A.n * inner;
+      k_project<T, P><<<grid_for(tot), TPB, 0, b->st>>>(ax == dax ? A.dB : A.B, A.nq, A.n, A.E, in, out, outer, inner,
+                                                         last ? 1 : 0);
+      len[ax] = A.n;
+      in = out;
+    }
+  }
+
+  QGrid grid() const {
+    QGrid g{};
+    g.dim = r->dim;
+    for (int a = 0; a < r->dim; ++a) {
+      g.Q[a] = r->Q[a];
+      g.x[a] = r->ax[a].x;
+      g.w[a] = r->ax[a].w;
+    }
+    return g;
+  }
+
+  // y = A_n x
+  void apply(const C<T>* x, C<T>* y, double tau, const double* ebar) {
+    kron(x, y, 0, tau, ebar);
+    const QGrid g = grid();
+    const long long NQ = (long long)r->Q[0] * r->Q[1] * (r->dim > 2 ? r->Q[2] : 1);
+    if (r->med.pot_kind != TDZ_POT_ZERO) {
+      C<T>* X = to_points(x, -1);
+      k_qmult<T><<<grid_for(NQ), TPB, 0, b->st>>>(X, g, r->med, 0, 0, 0.0, tau);  // i tau V
+      from_points(X, -1, y);
+    }
+    if (!r->const_mass) {
+      for (int a = 0; a < r->dim; ++a) {
+        C<T>* X = to_points(x, a);
+        k_qmult<T><<<grid_for(NQ), TPB, 0, b->st>>>(X, g, r->med, 1, a, 0.0, tau);  // i tau (1/2 m^-1)
+        from_points(X, a, y);
+      }
+    }
+  }
+};
+
+template <class T, int P>
+void line_precond(NdBatch* b, NdRun* r, C<T>* v) {
+  int len[3] = {r->n[0], r->n[1], r->n[2]};
+  for (int ax = 0; ax < r->dim; ++ax) {
+    long long inner = 1, outer = 1;
+    for (int a = 0; a < ax; ++a) inner *= len[a];
+    for (int a = ax + 1; a < r->dim; ++a) outer *= len[a];
+    k_line_solve<T, P><<<grid_for(outer * inner), 128, 0, b->st>>>(v, static_cast<const C<T>*>(b->pre_L[ax]),
+                                                                    static_cast<const C<T>*>(b->pre_D[ax]), outer,
+                                                                    len[ax], inner);
+  }
+}
+
+double* red_get(NdBatch* b, int k, double* host) {
+  cudaMemcpyAsync(host, b->d_red, sizeof(double) * k, cudaMemcpyDeviceToHost, b->st);
+  cudaStreamSynchronize(b->st);
+  return host;
+}
+
+void red_zero(NdBatch* b, int k) { cudaMemsetAsync(b->d_red, 0, sizeof(double) * k, b->st); }
+
+// Preconditioned COCG on A x = r (x starts at 0). Returns iterations; final ||r||^2 in *rr.
+template <class T, int P>
+int cocg(NdBatch* b, NdRun* r, Apply<T, P>& op, C<T>* x, C<T>* res, C<T>* z, C<T>* p, C<T>* q, double tau,
+         const double* ebar, double tol_abs2, int maxit, double* rr_out) {
+  const long long N = r->N;
+  double h[4];
+  cudaMemsetAsync(x, 0, sizeof(C<T>) * N, b->st);
+  cudaMemcpyAsync(z, res, sizeof(C<T>) * N, cudaMemcpyDeviceToDevice, b->st);
+  line_precond<T, P>(b, r, z);
+  cudaMemcpyAsync(p, z, sizeof(C<T>) * N, cudaMemcpyDeviceToDevice, b->st);
+  red_zero(b, 2);
+  k_bdot<T><<<grid_for(N), TPB, 0, b->st>>>(res, z, N, b->d_red);
+  red_get(b, 2, h);
+  std::complex<double> rho(h[0], h[1]);
+  red_zero(b, 1);
+  k_nrm<T><<<grid_for(N), TPB, 0, b->st>>>(res, N, b->d_red);
+  double rr = red_get(b, 1, h)[0];
+  int it = 0;
+  while (rr > tol_abs2 && it < maxit) {
+    op.apply(p, q, tau, ebar);
+    red_zero(b, 2);
+    k_bdot<T><<<grid_for(N), TPB, 0, b->st>>>(p, q, N, b->d_red);
+    red_get(b, 2, h);
+    const std::complex<double> pq(h[0], h[1]);
+    if (std::abs(pq) == 0.0) break;
+    const std::complex<double> alpha = rho / pq;
+    red_zero(b, 1);
+    k_cocg_update<T><<<grid_for(N), TPB, 0, b->st>>>(x, res, p, q, N, alpha.real(), alpha.imag(), b->d_red);
+    rr = red_get(b, 1, h)[0];
+    ++it;
+    if (!(rr > tol_abs2)) break;
+    cudaMemcpyAsync(z, res, sizeof(C<T>) * N, cudaMemcpyDeviceToDevice, b->st);
+    line_precond<T, P>(b, r, z);
+    red_zero(b, 2);
+    k_bdot<T><<<grid_for(N), TPB, 0, b->st>>>(res, z, N, b->d_red);
+    red_get(b, 2, h);
+    const std::complex<double> rho_new(h[0], h[1]);
+    if (std::abs(rho) == 0.0) break;
+    const std::complex<double> beta = rho_new / rho;
+    rho = rho_new;
+    k_xpby<T><<<grid_for(N), TPB, 0, b->st>>>(p, z, N, beta.real(), beta.imag());
+  }
+  *rr_out = rr;
+  return it;
+}
+
+// complex symmetric band LDL^T (host, binary64) of P_a = S_a + i tau mbar T1_a; upload in T
+template <class T>
+int factor_precond(NdBatch* b, NdRun* r, const tdz::Ops& o, double tau) {
+  for (int ax = 0; ax < r->dim; ++ax) {
+    const int n = r->n[ax], P = r->P, P1 = P + 1;
+    std::vector<std::complex<double>> a((size_t)n * P1);
+    for (size_t k = 0; k < a.size(); ++k) a[k] = {o.Sa[ax].a[k], tau * r->mbar * o.T1a[ax].a[k]};
+    std::vector<std::complex<double>> L((size_t)n * P), Dv(n);
+    std::vector<std::complex<double>> l(P1);
+    for (int j = 0; j < n; ++j) {
+      const std::complex<double> dj = a[(size_t)j * P1];
+      const std::complex<double> di = 1.0 / dj;
+      Dv[j] = di;
+      const int rmax = std::min(P, n - 1 - j);
+      for (int q = 1; q <= rmax; ++q) l[q] = a[(size_t)(j + q) * P1 + q] * di;
+      for (int q = 1; q <= rmax; ++q) {
+        for (int c = 1; c <= q; ++c) a[(size_t)(j + q) * P1 + (q - c)] -= l[q] * l[c] * dj;
+        L[(size_t)j * P + q - 1] = l[q];
+      }
+    }
+    std::vector<C<T>> hL(L.size()), hD(n);
+    for (size_t k = 0; k < L.size(); ++k) hL[k] = C<T>{(T)L[k].real(), (T)L[k].imag()};
+    for (int j = 0; j < n; ++j) hD[j] = C<T>{(T)Dv[j].real(), (T)Dv[j].imag()};
+    cudaMemcpyAsync(b->pre_L[ax], hL.data(), sizeof(C<T>) * hL.size(), cudaMemcpyHostToDevice, b->st);
+    cudaMemcpyAsync(b->pre_D[ax], hD.data(), sizeof(C<T>) * n, cudaMemcpyHostToDevice, b->st);
+    cudaStreamSynchronize(b->st);
+  }
+  return TDZ_OK;
+}
+
+// observables of the binary64 state: [d_a, a_a, norm]
+template <int P>
+void observe(NdBatch* b, NdRun* r, Apply<double, P>& op, const double* Et, double* out) {
+  const long long N = r->N;
+  double h[4];
+  const C<double>* c = reinterpret_cast<const C<double>*>(r->c);
+  C<double>* y = reinterpret_cast<C<double>*>(b->d_y);
+  double zero3[3] = {0, 0, 0};
+  op.kron(c, y, 1, 0.0, zero3);
+  red_zero(b, 2);
+  k_hdot<double><<<grid_for(N), TPB, 0, b->st>>>(c, y, N, b->d_red);
+  const double norm = red_get(b, 2, h)[0];
+  double dvals[3], gvals[3];
+  for (int a = 0; a < r->dim; ++a) {
+    op.kron(c, y, 2, 0.0, zero3, a);
+    red_zero(b, 2);
+    k_hdot<double><<<grid_for(N), TPB, 0, b->st>>>(c, y, N, b->d_red);
+    dvals[a] = red_get(b, 2, h)[0];
+  }
+  const QGrid g = op.grid();
+  C<double>* X = op.to_points(c, -1);
+  double kq;
+  if (r->const_mass) {
+    kq = r->cm * norm;
+  } else {
+    red_zero(b, 1);
+    k_qreduce<double><<<grid_for((long long)g.Q[0] * g.Q[1] * (g.dim > 2 ? g.Q[2] : 1)), TPB, 0, b->st>>>(X, g, r->med, 3,
+                                                                                                        0, b->d_red);
+    kq = red_get(b, 1, h)[0];
+  }
+  for (int a = 0; a < r->dim; ++a) {
+    red_zero(b, 1);
+    k_qreduce<double><<<grid_for((long long)g.Q[0] * g.Q[1] * (g.dim > 2 ? g.Q[2] : 1)), TPB, 0, b->st>>>(X, g, r->med, 2,
+                                                                                                        a, b->d_red);
+    gvals[a] = red_get(b, 1, h)[0];
+  }
+  const int D = r->dim;
+  for (int a = 0; a < D; ++a) {
+    out[a] = dvals[a];
+    out[D + a] = -gvals[a] - Et[a] * kq;
+  }
+  out[2 * D] = norm;
+}
+
+template <int P>
+int propagate_run(NdBatch* b, NdRun* r, const tdz::Ops& o, const double* field, double dt, long long step0,
+                  long long nsteps, double* obs_out) {
+  const long long N = r->N;
+  const double tau = 0.5 * dt;
+  const int D = r->dim;
+  // binary64 operator and buffers
+  Apply<double, P> op64{b, r, reinterpret_cast<C<double>*>(b->d_t1), reinterpret_cast<C<double>*>(b->d_t2),
+                        reinterpret_cast<C<double>*>(b->d_t3), reinterpret_cast<C<double>*>(b->d_t4),
+                        reinterpret_cast<C<double>*>(b->d_qa), reinterpret_cast<C<double>*>(b->d_qb)};
+  Apply<float, P> op32{b, r, static_cast<C<float>*>(b->w_t1), static_cast<C<float>*>(b->w_t2),
+                       static_cast<C<float>*>(b->w_t3), static_cast<C<float>*>(b->w_t4),
+                       static_cast<C<float>*>(b->w_qa), static_cast<C<float>*>(b->w_qb)};
+  const bool mixed = b->prec == TDZ_MIXED;
+  if (mixed) factor_precond<float>(b, r, o, tau);
+  else factor_precond<double>(b, r, o, tau);
+  C<double>* c = reinterpret_cast<C<double>*>(r->c);
+  C<double>* r0 = reinterpret_cast<C<double>*>(b->d_r0);
+  C<double>* y = reinterpret_cast<C<double>*>(b->d_y);
+  double h[4];
+  for (long long s = 0; s < nsteps && r->status == TDZ_OK; ++s) {
+    double ebar[3] = {0, 0, 0}, Et[3] = {0, 0, 0};
+    for (int a = 0; a < D; ++a) {
+      ebar[a] = 0.5 * (field[s * D + a] + field[(s + 1) * D + a]);
+      Et[a] = field[(s + 1) * D + a];
+    }
+    // r0 = 2 (S c - A c): y = A c, r0 = S c, r0 = 2 r0 - 2 y
+    op64.apply(c, y, tau, ebar);
+    double zero3[3] = {0, 0, 0};
+    op64.kron(c, r0, 1, 0.0, zero3);
+    red_zero(b, 1);
+    k_nrm<double><<<grid_for(N), TPB, 0, b->st>>>(r0, N, b->d_red);
+    const double bb = red_get(b, 1, h)[0];
+    k_axby<double, double><<<grid_for(N), TPB, 0, b->st>>>(y, r0, N, -2.0, 2.0);
+    const double tol2 = b->tol * b->tol * bb;
+    double rel = 0.0;
+    bool ok = false;
+    if (!mixed) {
+      C<double>* x = reinterpret_cast<C<double>*>(b->d_y);
+      double rr = 0;
+      const int its = cocg<double, P>(b, r, op64, x, r0, reinterpret_cast<C<double>*>(b->d_z),
+                                      reinterpret_cast<C<double>*>(b->d_p), reinterpret_cast<C<double>*>(b->d_q), tau,
+                                      ebar, tol2, b->max_it, &rr);
+      (void)its;
+      r->iters += its;
+      rel = std::sqrt(rr / std::max(bb, 1e-300));
+      ok = rel <= b->tol;
+      k_axby<double, double><<<grid_for(N), TPB, 0, b->st>>>(x, c, N, 1.0, 1.0);  // c += delta
+      r->nsolve++;
+    } else {
+      // outer refinement: r = r0 - A delta (binary64), inner FP32 COCG
+      C<double>* delta = y;
+      cudaMemsetAsync(delta, 0, sizeof(C<double>) * N, b->st);
+      C<double>* rcur = reinterpret_cast<C<double>*>(b->d_rc);  // binary64 residual
+      cudaMemcpyAsync(rcur, r0, sizeof(C<double>) * N, cudaMemcpyDeviceToDevice, b->st);
+      double rr = bb * 1e300;
+      red_zero(b, 1);
+      k_nrm<double><<<grid_for(N), TPB, 0, b->st>>>(rcur, N, b->d_red);
+      rr = red_get(b, 1, h)[0];
+      for (int outer = 0; outer < 8 && rr > tol2; ++outer) {
+        C<float>* rf = static_cast<C<float>*>(b->w_r);
+        C<float>* xf = static_cast<C<float>*>(b->w_x);
+        k_axby<double, float><<<grid_for(N), TPB, 0, b->st>>>(rcur, rf, N, 1.0, 0.0);
+        double rri = 0;
+        const int its = cocg<float, P>(b, r, op32, xf, rf, static_cast<C<float>*>(b->w_z),
+                                       static_cast<C<float>*>(b->w_p), static_cast<C<float>*>(b->w_q), tau, ebar,
+                                       rr * b->inner_tol * b->inner_tol, b->max_it, &rri);
+        r->iters += its;
+        r->nsolve++;
+        k_axby<float, double><<<grid_for(N), TPB, 0, b->st>>>(xf, delta, N, 1.0, 1.0);
+        // rcur = r0 - A delta
+        op64.apply(delta, rcur, tau, ebar);
+        k_axby<double, double><<<grid_for(N), TPB, 0, b->st>>>(r0, rcur, N, 1.0, -1.0);
+        red_zero(b, 1);
+        k_nrm<double><<<grid_for(N), TPB, 0, b->st>>>(rcur, N, b->d_red);
+        rr = red_get(b, 1, h)[0];
+      }
+      rel = std::sqrt(rr / std::max(bb, 1e-300));
+      ok = rel <= b->tol;
+      k_axby<double, double><<<grid_for(N), TPB, 0, b->st>>>(delta, c, N, 1.0, 1.0);
+    }
+    r->max_rel = std::max(r->max_rel, rel);
+    if (!ok && r->status == TDZ_OK) r->status = TDZ_ENOCONV;
+    double* row = obs_out + s * (2 + 3 * D);
+    row[0] = (double)(step0 + s + 1) * dt;
+    for (int a = 0; a < D; ++a) row[1 + a] = Et[a];
+    observe<P>(b, r, op64, Et, row + 1 + D);
+    if (!std::isfinite(row[1 + 3 * D]) || !std::isfinite(row[1 + D])) r->status = TDZ_ENONFINITE;
+  }
+  cudaError_t e = cudaStreamSynchronize(b->st);
+  if (e != cudaSuccess) return nd_cuda_fail(e, "tdz_propagate (2-D/3-D)");
+  return TDZ_OK;
+}
+
+}  // namespace
+
+namespace tdz {
+
+int nd_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* ops_index, int precision, void* stream,
+                    NdBatch** out) {
+  const int dim = ops[0]->o.dim;
+  const int P = ops[0]->o.p[0];
+  for (int g = 0; g < nops; ++g)
+    if (ops[g]->o.dim != dim || ops[g]->o.p[0] != P) {
+      set_error("tdz_batch_create: all 2-D/3-D operators of a batch need the same dimension and degree");
+      return TDZ_EUNSUPPORTED;
+    }
+  if (P < 1 || P > 8) return TDZ_EUNSUPPORTED;
+  NdBatch* b = new (std::nothrow) NdBatch;
+  if (!b) return TDZ_ENOMEM;
+  b->prec = precision;
+  b->dim = dim;
+  b->P = P;
+  b->nruns = nruns;
+  b->st = static_cast<cudaStream_t>(stream);
+  for (int g = 0; g < nops; ++g) b->ops.push_back(ops[g]->o);
+  // per-geometry device tables
+  struct GeoDev {
+    AxisDev ax[3];
+    int n[3], E[3], nq[3], Q[3];
+  };
+  std::vector<GeoDev> geo(nops);
+  for (int g = 0; g < nops; ++g) {
+    const Ops& o = ops[g]->o;
+    for (int a = 0; a < dim; ++a) {
+      const Basis& B = o.axis[a];
+      AxisDev A{};
+      A.n = (int)o.n[a];
+      A.E = (int)B.nelem();
+      A.nq = B.nq;
+      A.Q = A.E * A.nq;
+      auto up = [&](const std::vector<double>& v) -> double* {
+        void* p = b->alloc(sizeof(double) * v.size());
+        if (!p) return nullptr;
+        cudaMemcpyAsync(p, v.data(), sizeof(double) * v.size(), cudaMemcpyHostToDevice, b->st);
+        cudaStreamSynchronize(b->st);
+        return static_cast<double*>(p);
+      };
+      A.B = up(B.val);
+      A.dB = up(B.der);
+      A.x = up(B.xq);
+      A.w = up(B.wq);
+      A.S = up(o.Sa[a].a);
+      A.T1 = up(o.T1a[a].a);
+      A.D = up(o.Da[a].a);
+      if (!A.B || !A.dB || !A.x || !A.w || !A.S || !A.T1 || !A.D) {
+        delete b;
+        return TDZ_ENOMEM;
+      }
+      geo[g].ax[a] = A;
+      geo[g].n[a] = A.n;
+      geo[g].E[a] = A.E;
+      geo[g].nq[a] = A.nq;
+      geo[g].Q[a] = A.Q;
+    }
+  }
+  b->runs.resize(nruns);
+  size_t maxN = 0, maxQ = 0;
+  int maxn = 0;
+  for (int r = 0; r < nruns; ++r) {
+    const Ops& o = ops[ops_index[r]]->o;
+    NdRun& R = b->runs[r];
+    R.ops = ops_index[r];
+    R.dim = dim;
+    R.P = P;
+    R.N = 1;
+    long long NQ = 1;
+    for (int a = 0; a < dim; ++a) {
+      R.ax[a] = geo[R.ops].ax[a];
+      R.n[a] = geo[R.ops].n[a];
+      R.E[a] = geo[R.ops].E[a];
+      R.nq[a] = geo[R.ops].nq[a];
+      R.Q[a] = geo[R.ops].Q[a];
+      R.N *= R.n[a];
+      NQ *= R.Q[a];
+      maxn = std::max(maxn, R.n[a]);
+    }
+    R.med.mass_kind = o.med.mass_kind;
+    R.med.pot_kind = o.med.pot_kind;
+    std::memcpy(R.med.mp, o.med.mass_par, sizeof(R.med.mp));
+    std::memcpy(R.med.vp, o.med.pot_par, sizeof(R.med.vp));
+    R.const_mass = o.med.mass_kind == TDZ_MASS_CONST;
+    R.cm = R.const_mass ? 1.0 / o.med.mass_par[0] : 0.0;
+    R.mbar = R.const_mass ? R.cm : 0.5 * (1.0 / o.med.mass_par[2] + 1.0 / o.med.mass_par[3]);
+    R.c = static_cast<double2*>(b->alloc(sizeof(double2) * R.N));
+    if (!R.c) {
+      delete b;
+      return TDZ_ENOMEM;
+    }
+    maxN = std::max(maxN, (size_t)R.N);
+    // the largest intermediate of a Gauss-point pass: product of max(n, Q) over axes
+    size_t mq = 1;
+    for (int a = 0; a < dim; ++a) mq *= (size_t)std::max(R.n[a], R.Q[a]);
+    maxQ = std::max(maxQ, mq);
+    (void)NQ;
+  }
+  b->maxN = maxN;
+  b->maxQ = maxQ;
+  const size_t z64 = sizeof(double2);
+  b->d_r0 = static_cast<double2*>(b->alloc(z64 * maxN));
+  b->d_y = static_cast<double2*>(b->alloc(z64 * maxN));
+  b->d_t1 = static_cast<double2*>(b->alloc(z64 * maxQ));
+  b->d_t2 = static_cast<double2*>(b->alloc(z64 * maxQ));
+  b->d_t3 = static_cast<double2*>(b->alloc(z64 * maxQ));
+  b->d_t4 = static_cast<double2*>(b->alloc(z64 * maxQ));
+  b->d_qa = static_cast<double2*>(b->alloc(z64 * maxQ));
+  b->d_qb = static_cast<double2*>(b->alloc(z64 * maxQ));
+  b->d_red = static_cast<double*>(b->alloc(sizeof(double) * 16));
+  b->d_z = static_cast<double2*>(b->alloc(z64 * maxN));
+  b->d_p = static_cast<double2*>(b->alloc(z64 * maxN));
+  b->d_q = static_cast<double2*>(b->alloc(z64 * maxN));
+  b->d_rc = static_cast<double2*>(b->alloc(z64 * maxN));
+  if (!b->d_z || !b->d_p || !b->d_q || !b->d_rc) {
+    delete b;
+    return TDZ_ENOMEM;
+  }
+  const size_t zs = precision == TDZ_MIXED ? sizeof(float2) : sizeof(double2);
+  for (int a = 0; a < 3; ++a) {
+    b->pre_L[a] = b->alloc(zs * (size_t)std::max(maxn, 1) * P);
+    b->pre_D[a] = b->alloc(zs * (size_t)std::max(maxn, 1));
+  }
+  if (precision == TDZ_MIXED) {
+    const size_t f = sizeof(float2);
+    b->w_x = b->alloc(f * maxN);
+    b->w_r = b->alloc(f * maxN);
+    b->w_z = b->alloc(f * maxN);
+    b->w_p = b->alloc(f * maxN);
+    b->w_q = b->alloc(f * maxN);
+    b->w_t1 = b->alloc(f * maxQ);
+    b->w_t2 = b->alloc(f * maxQ);
+    b->w_t3 = b->alloc(f * maxQ);
+    b->w_t4 = b->alloc(f * maxQ);
+    b->w_qa = b->alloc(f * maxQ);
+    b->w_qb = b->alloc(f * maxQ);
+    if (!b->w_qb) {
+      delete b;
+      return TDZ_ENOMEM;
+    }
+  }
+  if (!b->d_qb || !b->d_red) {
+    delete b;
+    set_error("tdz_batch_create: device allocation for 2-D/3-D work buffers failed");
+    return TDZ_ENOMEM;
+  }
+  cudaError_t e = cudaStreamSynchronize(b->st);
+  if (e != cudaSuccess) {
+    delete b;
+    return nd_cuda_fail(e, "tdz_batch_create (2-D/3-D)");
+  }
+  *out = b;
+  return TDZ_OK;
+}
+
+void nd_batch_destroy(NdBatch* b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->st);
+  delete b;
+}
+
+long long nd_run_size(const NdBatch* b, int run) { return b->runs[run].N; }
+
+int nd_set_state(NdBatch* b, int run, const double* c, bool device) {
+  NdRun& R = b->runs[run];
+  cudaError_t e = cudaMemcpyAsync(R.c, c, sizeof(double2) * R.N, device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                  b->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+  if (e != cudaSuccess) return nd_cuda_fail(e, "tdz_set_state");
+  R.status = TDZ_OK;
+  return TDZ_OK;
+}
+
+int nd_get_state(const NdBatch* b, int run, double* c, bool device) {
+  const NdRun& R = b->runs[run];
+  cudaError_t e = cudaMemcpyAsync(c, R.c, sizeof(double2) * R.N, device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                  b->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+  if (e != cudaSuccess) return nd_cuda_fail(e, "tdz_get_state");
+  return TDZ_OK;
+}
+
+int nd_propagate(NdBatch* b, const double* field_host, double dt, long long step0, long long nsteps) {
+  const int D = b->dim;
+  const int cols = 2 + 3 * D;
+  b->obs.assign((size_t)b->nruns * nsteps * cols, 0.0);
+  for (int r = 0; r < b->nruns; ++r) {
+    NdRun& R = b->runs[r];
+    const double* f = field_host + (size_t)r * (nsteps + 1) * D;
+    int rc = TDZ_OK;
+    switch (b->P) {
+      case 1: rc = propagate_run<1>(b, &R, b->ops[R.ops], f, dt, step0, nsteps, &b->obs[(size_t)r * nsteps * cols]); break;
+      case 2: rc = propagate_run<2>(b, &R, b->ops[R.ops], f, dt, step0, nsteps, &b->obs[(size_t)r * nsteps * cols]); break;
+      case 3: rc = propagate_run<3>(b, &R, b->ops[R.ops], f, dt, step0, nsteps, &b->obs[(size_t)r * nsteps * cols]); break;
+      case 4: rc = propagate_run<4>(b, &R, b->ops[R.ops], f, dt, step0, nsteps, &b->obs[(size_t)r * nsteps * cols]); break;
+      case 5: rc = propagate_run<5>(b, &R, b->ops[R.ops], f, dt, step0, nsteps, &b->obs[(size_t)r * nsteps * cols]); break;
+      case 6: rc = propagate_run<6>(b, &R, b->ops[R.ops], f, dt, step0, nsteps, &b->obs[(size_t)r * nsteps * cols]); break;
+      case 7: rc = propagate_run<7>(b, &R, b->ops[R.ops], f, dt, step0, nsteps, &b->obs[(size_t)r * nsteps * cols]); break;
+      default: rc = propagate_run<8>(b, &R, b->ops[R.ops], f, dt, step0, nsteps, &b->obs[(size_t)r * nsteps * cols]); break;
+    }
+    if (rc != TDZ_OK) return rc;
+  }
+  b->last_nsteps = nsteps;
+  return TDZ_OK;
+}
+
+int nd_observe(const NdBatch* b, int run, double* out, int* status, bool device) {
+  const int cols = 2 + 3 * b->dim;
+  const size_t cnt = (size_t)b->last_nsteps * cols;
+  if (out && cnt) {
+    cudaError_t e = cudaMemcpy(out, &b->obs[(size_t)run * cnt], sizeof(double) * cnt,
+                               device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost);
+    if (e != cudaSuccess) return nd_cuda_fail(e, "tdz_observe");
+  }
+  if (status) *status = b->runs[run].status;
+  return TDZ_OK;
+}
+
+int nd_stats(const NdBatch* b, double* max_rel, double* solves, double* iters) {
+  double mx = 0, ns = 0, it = 0;
+  for (const auto& r : b->runs) {
+    mx = std::max(mx, r.max_rel);
+    ns += (double)r.nsolve;
+    it += (double)r.iters;
+  }
+  if (max_rel) *max_rel = mx;
+  if (solves) *solves = ns;
+  if (iters) *iters = it;
+  return TDZ_OK;
+}
+
+void nd_set_refinement(NdBatch* b, double tol, int max_it) {
+  b->tol = tol;
+  b->max_it = std::max(max_it, 50);
+}
+
+}  // namespace tdz
+
+namespace tdz {
+int nd_dim(const NdBatch* b) { return b->dim; }
+}  // namespace tdz

@@ -95,5 +95,22 @@ def test_errors_are_status_codes(tdz):
     assert ei.value.code == tdz.TDZ_EINVAL
     b = tdz.Basis(wl.open_uniform_knots(0, 1, 6, 3), 3)
     with pytest.raises(tdz.TDZError) as ei:
-        tdz.Ops([b, b], wl.ho_medium([1.0, 1.0]))
+        tdz.Ops([b, b], wl.dqw_medium(8.0, 4.0, 0.2))      # layered media are 1-D only
+    assert ei.value.code == tdz.TDZ_EINVAL
+    b2 = tdz.Basis(wl.open_uniform_knots(0, 1, 6, 2), 2)
+    with pytest.raises(tdz.TDZError) as ei:
+        tdz.Ops([b, b2], wl.ho_medium([1.0, 1.0]))          # mixed degrees across axes
     assert ei.value.code == tdz.TDZ_EUNSUPPORTED
+
+
+def test_axis_factors_for_tensor_bases_match_oracle(tdz):
+    """2-D/3-D assembly keeps the per-axis 1-D factors S, T1 = 1/2 <N'|N'> and D (Eq. tensor3d)."""
+    tx = wl.knots_for_nsplines(-5, 5, 20, 4)
+    ty = wl.knots_for_nsplines(-3, 4, 14, 4)
+    ops = tdz.Ops([tdz.Basis(tx, 4, 5), tdz.Basis(ty, 4, 5)], wl.softcore_medium(0.5))
+    assert ops.dim == 2 and ops.shape == [18, 12]
+    for a, t in enumerate((tx, ty)):
+        ref = assemble.assemble_1d(t, 4, 5, wl.medium({"kind": "const", "m": 1.0}, {"kind": "zero"}))
+        assert np.max(np.abs(ops.band("S", a) - _lower_band(ref["S"], 4))) < 1e-13
+        assert np.max(np.abs(ops.band("T", a) - _lower_band(ref["T"], 4))) < 1e-12
+        assert np.max(np.abs(ops.band("D", a) - _lower_band(ref["D"][0], 4))) < 1e-13
