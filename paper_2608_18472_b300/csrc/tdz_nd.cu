@@ -45,7 +45,17 @@ struct AxisDev {
   const double* S;   // [n][P+1] lower bands
   const double* T1;
   const double* D;
+  // FP32 copies for the single-precision inner solver (no binary64 loads or conversions there)
+  const float *fB, *fdB, *fx, *fw, *fS, *fT1, *fD;
 };
+template <class T> __host__ __device__ inline const T* tab(const AxisDev& A, int which);
+template <> __host__ __device__ inline const double* tab<double>(const AxisDev& A, int which) {
+  switch (which) { case 0: return A.B; case 1: return A.dB; case 2: return A.x; case 3: return A.w; case 4: return A.S; case 5: return A.T1; default: return A.D; }
+}
+template <> __host__ __device__ inline const float* tab<float>(const AxisDev& A, int which) {
+  switch (which) { case 0: return A.fB; case 1: return A.fdB; case 2: return A.fx; case 3: return A.fw; case 4: return A.fS; case 5: return A.fT1; default: return A.fD; }
+}
+enum { TB = 0, TDB = 1, TX = 2, TW = 3, TS = 4, TT1 = 5, TD = 6 };
 
 struct MediumDev {
   int mass_kind, pot_kind;
@@ -53,41 +63,42 @@ struct MediumDev {
 };
 
 // f(r) at a Gauss point. kind: 0 = V, 1 = 1/2 m^-1 (kinetic weight), 2 = m^-1 dV/dx_axis, 3 = m^-1
-__device__ __forceinline__ double medium_f(const MediumDev& M, int kind, int axis, const double* r, int dim) {
-  double minv = 1.0;
+template <class T>
+__device__ __forceinline__ T medium_f(const MediumDev& M, int kind, int axis, const T* r, int dim) {
+  T minv = 1;
   if (M.mass_kind == TDZ_MASS_CONST) {
-    minv = 1.0 / M.mp[0];
+    minv = (T)(1.0 / M.mp[0]);
   } else if (M.mass_kind == TDZ_MASS_ELLIPSE) {
-    const double u = r[0] / M.mp[0], v = dim > 1 ? r[1] / M.mp[1] : 0.0;
-    minv = (u * u + v * v < 1.0) ? 1.0 / M.mp[2] : 1.0 / M.mp[3];
+    const T u = r[0] / (T)M.mp[0], v = dim > 1 ? r[1] / (T)M.mp[1] : (T)0;
+    minv = (u * u + v * v < (T)1) ? (T)(1.0 / M.mp[2]) : (T)(1.0 / M.mp[3]);
   }
-  if (kind == 1) return 0.5 * minv;
+  if (kind == 1) return (T)0.5 * minv;
   if (kind == 3) return minv;
-  double r2 = 0.0;
+  T r2 = 0;
   for (int a = 0; a < dim; ++a) r2 += r[a] * r[a];
   if (kind == 0) {
     switch (M.pot_kind) {
-      case TDZ_POT_SOFTCORE: return -M.vp[0] / sqrt(r2 + M.vp[1]);
+      case TDZ_POT_SOFTCORE: return -(T)M.vp[0] / sqrt(r2 + (T)M.vp[1]);
       case TDZ_POT_HO: {
-        double s = 0.0;
-        for (int a = 0; a < dim; ++a) s += M.vp[a] * M.vp[a] * r[a] * r[a];
-        return 0.5 * s;
+        T s = 0;
+        for (int a = 0; a < dim; ++a) s += (T)(M.vp[a] * M.vp[a]) * r[a] * r[a];
+        return (T)0.5 * s;
       }
       case TDZ_POT_ELLIPSE: {
-        const double u = r[0] / M.vp[0], v = dim > 1 ? r[1] / M.vp[1] : 0.0;
-        return (u * u + v * v < 1.0) ? M.vp[2] : M.vp[3];
+        const T u = r[0] / (T)M.vp[0], v = dim > 1 ? r[1] / (T)M.vp[1] : (T)0;
+        return (u * u + v * v < (T)1) ? (T)M.vp[2] : (T)M.vp[3];
       }
-      default: return 0.0;
+      default: return 0;
     }
   }
   // kind 2: m^-1 dV/dx_axis
   switch (M.pot_kind) {
     case TDZ_POT_SOFTCORE: {
-      const double q = r2 + M.vp[1];
-      return minv * M.vp[0] * r[axis] / (q * sqrt(q));
+      const T q = r2 + (T)M.vp[1];
+      return minv * (T)M.vp[0] * r[axis] / (q * sqrt(q));
     }
-    case TDZ_POT_HO: return minv * M.vp[axis] * M.vp[axis] * r[axis];
-    default: return 0.0;
+    case TDZ_POT_HO: return minv * (T)(M.vp[axis] * M.vp[axis]) * r[axis];
+    default: return 0;
   }
 }
 
@@ -98,7 +109,7 @@ using C = cx<T>;
 // out[o][j][i] (+)= sum_t coef_t * sum_d R_t(j, j+d) in_{sel_t}[o][j+d][i]   (R_t real symmetric bands)
 struct BandTerms {
   int nt;
-  const double* R[4];
+  const void* R[4];
   double cr[4], ci[4];
   int sel[4];
 };
@@ -116,14 +127,14 @@ __global__ void k_axis_band(BandTerms bt, const C<T>* __restrict__ in0, const C<
     T ar = 0, ai = 0;
     for (int t = 0; t < bt.nt; ++t) {
       const C<T>* in = bt.sel[t] ? in1 : in0;
-      const double* R = bt.R[t];
+      const T* R = static_cast<const T*>(bt.R[t]);
       T sr = 0, si = 0;
 #pragma unroll
       for (int d = -P; d <= P; ++d) {
         const int jj = j + d;
         if (jj < 0 || jj >= L) continue;
         const int hi = jj > j ? jj : j;
-        const T m = (T)R[(size_t)hi * (P + 1) + (d < 0 ? -d : d)];
+        const T m = R[(size_t)hi * (P + 1) + (d < 0 ? -d : d)];
         const C<T> v = in[(o * L + jj) * inner + i];
         sr += m * v.r;
         si += m * v.i;
@@ -144,7 +155,7 @@ __global__ void k_axis_band(BandTerms bt, const C<T>* __restrict__ in0, const C<
 // ------------------------------------------------------------------------------- Gauss point passes
 // interpolation: out[o][q][i] = sum_r Btab[q][r] in[o][e+r-1][i],  e = q / nq
 template <class T, int P>
-__global__ void k_interp(const double* __restrict__ Btab, int nq, int n, int Q, const C<T>* __restrict__ in,
+__global__ void k_interp(const T* __restrict__ Btab, int nq, int n, int Q, const C<T>* __restrict__ in,
                          C<T>* __restrict__ out, long long outer, long long inner) {
   const long long total = outer * Q * inner;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
@@ -159,7 +170,7 @@ __global__ void k_interp(const double* __restrict__ Btab, int nq, int n, int Q, 
     for (int r = 0; r <= P; ++r) {
       const int j = e + r - 1;
       if (j < 0 || j >= n) continue;
-      const T b = (T)Btab[(size_t)q * (P + 1) + r];
+      const T b = Btab[(size_t)q * (P + 1) + r];
       const C<T> v = in[(o * n + j) * inner + i];
       sr += b * v.r;
       si += b * v.i;
@@ -170,7 +181,7 @@ __global__ void k_interp(const double* __restrict__ Btab, int nq, int n, int Q, 
 
 // projection: out[o][j][i] = sum_{r, qq} Btab[(e nq + qq)][r] in[o][e nq + qq][i],  e = j + 1 - r
 template <class T, int P>
-__global__ void k_project(const double* __restrict__ Btab, int nq, int n, int E, const C<T>* __restrict__ in,
+__global__ void k_project(const T* __restrict__ Btab, int nq, int n, int E, const C<T>* __restrict__ in,
                           C<T>* __restrict__ out, long long outer, long long inner, int accumulate) {
   const int Q = E * nq;
   const long long total = outer * n * inner;
@@ -187,7 +198,7 @@ __global__ void k_project(const double* __restrict__ Btab, int nq, int n, int E,
       if (e < 0 || e >= E) continue;
       for (int qq = 0; qq < nq; ++qq) {
         const int q = e * nq + qq;
-        const T b = (T)Btab[(size_t)q * (P + 1) + r];
+        const T b = Btab[(size_t)q * (P + 1) + r];
         const C<T> v = in[(o * Q + q) * inner + i];
         sr += b * v.r;
         si += b * v.i;
@@ -202,32 +213,132 @@ __global__ void k_project(const double* __restrict__ Btab, int nq, int n, int E,
   }
 }
 
+template <class T>
 struct QGrid {
   int dim;
   int Q[3];
-  const double* x[3];
-  const double* w[3];
+  const T* x[3];
+  const T* w[3];
 };
 
 // X[q] *= (cr + i ci) w(q) f(r_q)
 template <class T>
-__global__ void k_qmult(C<T>* __restrict__ X, QGrid g, MediumDev M, int kind, int axis, double cr, double ci) {
+__global__ void k_qmult(C<T>* __restrict__ X, QGrid<T> g, MediumDev M, int kind, int axis, double cr, double ci) {
   const long long total = (long long)g.Q[0] * g.Q[1] * (g.dim > 2 ? g.Q[2] : 1);
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
     long long t = idx;
-    double r[3];
-    double w = 1.0;
+    T r[3];
+    T w = 1;
     for (int a = 0; a < g.dim; ++a) {
       const int q = (int)(t % g.Q[a]);
       t /= g.Q[a];
       r[a] = g.x[a][q];
       w *= g.w[a][q];
     }
-    const double f = w * medium_f(M, kind, axis, r, g.dim);
-    const T fr = (T)(f * cr), fi = (T)(f * ci);
+    const T f = w * medium_f<T>(M, kind, axis, r, g.dim);
+    const T fr = f * (T)cr, fi = f * (T)ci;
     const C<T> v = X[idx];
     X[idx] = C<T>{fr * v.r - fi * v.i, fr * v.i + fi * v.r};
+  }
+}
+
+
+// ------------------------------------------------------------------------------- fused last axis
+// Along the last (slowest) axis L: for every pencil (one point of the faster axes, already
+// interpolated) and chunk of elements, walk the elements with a sliding window of P+1
+// coefficients: interpolate to the nq points (table Bl), multiply by coef * w(q) * f(r_q), and
+// project back with the same table, accumulating into out (shape [n_L][inner]). Coefficients
+// touched by two chunks are accumulated atomically, the others by their single owner.
+template <class T, int P>
+__global__ void k_fused_last(const C<T>* __restrict__ in, C<T>* __restrict__ out, const T* __restrict__ Bl, int nq,
+                             int nL, int EL, long long inner, int echunk, QGrid<T> g, MediumDev M, int kind, int axis,
+                             double cr, double ci) {
+  const int nchunks = (EL + echunk - 1) / echunk;
+  const long long total = inner * nchunks;
+  const int L = g.dim - 1;
+  const T tcr = (T)cr, tci = (T)ci;
+  for (long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x; tid < total;
+       tid += (long long)gridDim.x * blockDim.x) {
+    const long long i = tid % inner;
+    const int ch = (int)(tid / inner);
+    const int e0 = ch * echunk, e1 = min(EL, e0 + echunk);
+    // coordinates and weight of the pencil on the faster axes
+    T r[3];
+    T wp = 1;
+    long long t = i;
+    for (int a = 0; a < L; ++a) {
+      const int q = (int)(t % g.Q[a]);
+      t /= g.Q[a];
+      r[a] = g.x[a][q];
+      wp *= g.w[a][q];
+    }
+    C<T> win[P + 1];   // win[r] = coefficient e + r - 1 of the current element
+    C<T> acc[P + 1];   // acc[r] = partial projection onto coefficient e + r - 1
+#pragma unroll
+    for (int k = 0; k <= P; ++k) {
+      const int j = e0 + k - 1;
+      win[k] = (j >= 0 && j < nL) ? in[(long long)j * inner + i] : czero<T>();
+      acc[k] = czero<T>();
+    }
+    for (int e = e0; e < e1; ++e) {
+      for (int qq = 0; qq < nq; ++qq) {
+        const int q = e * nq + qq;
+        const T* b = Bl + (size_t)q * (P + 1);
+        T pr = 0, pi = 0;
+#pragma unroll
+        for (int k = 0; k <= P; ++k) {
+          pr += b[k] * win[k].r;
+          pi += b[k] * win[k].i;
+        }
+        r[L] = g.x[L][q];
+        const T f = wp * g.w[L][q] * medium_f<T>(M, kind, axis, r, g.dim);
+        const T fr = f * tcr, fi = f * tci;
+        const T gr = fr * pr - fi * pi, gi = fr * pi + fi * pr;
+#pragma unroll
+        for (int k = 0; k <= P; ++k) {
+          acc[k].r += b[k] * gr;
+          acc[k].i += b[k] * gi;
+        }
+      }
+      // coefficient e - 1 is complete: emit; shift both windows by one
+      {
+        const int j = e - 1;
+        if (j >= 0 && j < nL) {
+          C<T>* o = out + (long long)j * inner + i;
+          if (e - e0 < P && e0 > 0) {
+            atomicAdd(&o->r, acc[0].r);
+            atomicAdd(&o->i, acc[0].i);
+          } else {
+            const C<T> v = *o;
+            *o = C<T>{v.r + acc[0].r, v.i + acc[0].i};
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < P; ++k) {
+        win[k] = win[k + 1];
+        acc[k] = acc[k + 1];
+      }
+      const int jn = e + P;  // coefficient entering the window for element e + 1
+      win[P] = (jn >= 0 && jn < nL && e + 1 < e1) ? in[(long long)jn * inner + i] : czero<T>();
+      acc[P] = czero<T>();
+    }
+    // remaining partial sums: coefficients e1 - 1 .. e1 + P - 2 (shared with the next chunk)
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+      const int j = e1 - 1 + k;
+      if (j >= 0 && j < nL) {
+        C<T>* o = out + (long long)j * inner + i;
+        if (e1 < EL || (e1 - e0 < P + 1 - k && e0 > 0)) {
+          atomicAdd(&o->r, acc[k].r);
+          atomicAdd(&o->i, acc[k].i);
+        } else {
+          const C<T> v = *o;
+          *o = C<T>{v.r + acc[k].r, v.i + acc[k].i};
+        }
+      }
+    }
   }
 }
 
@@ -249,15 +360,15 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 
 // sum_q w f |X_q|^2 for kinds 2 (per axis) and 3, into res[slot]
 template <class T>
-__global__ void k_qreduce(const C<T>* __restrict__ X, QGrid g, MediumDev M, int kind, int axis, double* res) {
+__global__ void k_qreduce(const C<T>* __restrict__ X, QGrid<T> g, MediumDev M, int kind, int axis, double* res) {
   __shared__ double sh[32];
   const long long total = (long long)g.Q[0] * g.Q[1] * (g.dim > 2 ? g.Q[2] : 1);
   double acc = 0.0;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
     long long t = idx;
-    double r[3];
-    double w = 1.0;
+    T r[3];
+    T w = 1;
     for (int a = 0; a < g.dim; ++a) {
       const int q = (int)(t % g.Q[a]);
       t /= g.Q[a];
@@ -265,7 +376,7 @@ __global__ void k_qreduce(const C<T>* __restrict__ X, QGrid g, MediumDev M, int 
       w *= g.w[a][q];
     }
     const C<T> v = X[idx];
-    acc += w * medium_f(M, kind, axis, r, g.dim) * ((double)v.r * v.r + (double)v.i * v.i);
+    acc += (double)(w * medium_f<T>(M, kind, axis, r, g.dim)) * ((double)v.r * v.r + (double)v.i * v.i);
   }
   acc = block_sum(acc, sh);
   if (threadIdx.x == 0) atomicAdd(res, acc);
@@ -521,33 +632,33 @@ struct Apply {
       if (mode == 0) {  // A_sep
         // a stream: S_ax a
         ta.nt = 1;
-        ta.R[0] = A.S;
+        ta.R[0] = tab<T>(A, TS);
         ta.cr[0] = 1;
         ta.ci[0] = 0;
         ta.sel[0] = 0;
         // b stream: S_ax b + i tau K_ax a  (for the first axis a == b == x)
         tb.nt = 3;
-        tb.R[0] = A.S;
+        tb.R[0] = tab<T>(A, TS);
         tb.cr[0] = 1;
         tb.ci[0] = 0;
         tb.sel[0] = 1;
-        tb.R[1] = A.T1;
+        tb.R[1] = tab<T>(A, TT1);
         tb.cr[1] = 0;
         tb.ci[1] = tau * (r->const_mass ? r->cm : 0.0);
         tb.sel[1] = 0;
-        tb.R[2] = A.D;
+        tb.R[2] = tab<T>(A, TD);
         tb.cr[2] = 0;
         tb.ci[2] = tau * ebar[ax];
         tb.sel[2] = 0;
       } else if (mode == 1) {  // S only
         ta.nt = 1;
-        ta.R[0] = A.S;
+        ta.R[0] = tab<T>(A, TS);
         ta.cr[0] = 1;
         ta.sel[0] = 0;
         tb = ta;
       } else {  // D on daxis, S elsewhere
         ta.nt = 1;
-        ta.R[0] = ax == daxis ? A.D : A.S;
+        ta.R[0] = ax == daxis ? tab<T>(A, TD) : tab<T>(A, TS);
         ta.cr[0] = 1;
         ta.sel[0] = 0;
         tb = ta;
@@ -577,7 +688,8 @@ struct Apply {
       const AxisDev& A = r->ax[ax];
       out = (ax % 2 == 0) ? qa : qb;
       const long long tot = outer * A.Q * inner;
-      k_interp<T, P><<<grid_for(tot), TPB, 0, b->st>>>(ax == dax ? A.dB : A.B, A.nq, A.n, A.Q, in, out, outer, inner);
+      k_interp<T, P><<<grid_for(tot), TPB, 0, b->st>>>(tab<T>(A, ax == dax ? TDB : TB), A.nq, A.n, A.Q, in, out, outer,
+                                                        inner);
       len[ax] = A.Q;
       in = out;
     }
@@ -596,41 +708,76 @@ struct Apply {
       const bool last = ax == 0;
       C<T>* out = last ? y : ((in == qa) ? qb : qa);
       const long long tot = outer * A.n * inner;
-      k_project<T, P><<<grid_for(tot), TPB, 0, b->st>>>(ax == dax ? A.dB : A.B, A.nq, A.n, A.E, in, out, outer, inner,
-                                                         last ? 1 : 0);
+      k_project<T, P><<<grid_for(tot), TPB, 0, b->st>>>(tab<T>(A, ax == dax ? TDB : TB), A.nq, A.n, A.E, in, out,
+                                                         outer, inner, last ? 1 : 0);
       len[ax] = A.n;
       in = out;
     }
   }
 
-  QGrid grid() const {
-    QGrid g{};
+  QGrid<T> grid() const {
+    QGrid<T> g{};
     g.dim = r->dim;
     for (int a = 0; a < r->dim; ++a) {
       g.Q[a] = r->Q[a];
-      g.x[a] = r->ax[a].x;
-      g.w[a] = r->ax[a].w;
+      g.x[a] = tab<T>(r->ax[a], TX);
+      g.w[a] = tab<T>(r->ax[a], TW);
     }
     return g;
+  }
+
+  // y += coef * (Gauss-point operator of kind `kind`) x, derivative on axis dax (or none if dax < 0):
+  // interpolate along the faster axes, fused interpolate/multiply/project along the last axis,
+  // project back along the faster axes.
+  void quad(const C<T>* x, C<T>* y, int dax, int kind, int faxis, double cr, double ci) {
+    const int D = r->dim, L = D - 1;
+    int len[3] = {r->n[0], r->n[1], r->n[2]};
+    const C<T>* in = x;
+    C<T>* X = nullptr;
+    for (int ax = 0; ax < L; ++ax) {
+      long long outer, inner;
+      shape(ax, len, outer, inner);
+      const AxisDev& A = r->ax[ax];
+      X = (ax % 2 == 0) ? qa : qb;
+      const long long tot = outer * A.Q * inner;
+      k_interp<T, P><<<grid_for(tot), TPB, 0, b->st>>>(tab<T>(A, ax == dax ? TDB : TB), A.nq, A.n, A.Q, in, X, outer,
+                                                        inner);
+      len[ax] = A.Q;
+      in = X;
+    }
+    C<T>* U = (X == qa) ? qb : qa;
+    long long inner = 1;
+    for (int a = 0; a < L; ++a) inner *= len[a];
+    const AxisDev& AL = r->ax[L];
+    cudaMemsetAsync(U, 0, sizeof(C<T>) * (size_t)AL.n * inner, b->st);
+    long long nch = std::max<long long>(1, std::min<long long>(AL.E / (2 * P + 2), (150000 + inner - 1) / inner));
+    const int echunk = (int)((AL.E + nch - 1) / nch);
+    nch = (AL.E + echunk - 1) / echunk;
+    k_fused_last<T, P><<<grid_for(inner * nch), TPB, 0, b->st>>>(in, U, tab<T>(AL, L == dax ? TDB : TB), AL.nq, AL.n,
+                                                                 AL.E, inner, echunk, grid(), r->med, kind, faxis, cr,
+                                                                 ci);
+    len[L] = AL.n;
+    C<T>* cur = U;
+    for (int ax = L - 1; ax >= 0; --ax) {
+      long long outer2, inner2;
+      shape(ax, len, outer2, inner2);
+      const AxisDev& A = r->ax[ax];
+      const bool last = ax == 0;
+      C<T>* out = last ? y : ((cur == qa) ? qb : qa);
+      const long long tot = outer2 * A.n * inner2;
+      k_project<T, P><<<grid_for(tot), TPB, 0, b->st>>>(tab<T>(A, ax == dax ? TDB : TB), A.nq, A.n, A.E, cur, out,
+                                                         outer2, inner2, last ? 1 : 0);
+      len[ax] = A.n;
+      cur = out;
+    }
   }
 
   // y = A_n x
   void apply(const C<T>* x, C<T>* y, double tau, const double* ebar) {
     kron(x, y, 0, tau, ebar);
-    const QGrid g = grid();
-    const long long NQ = (long long)r->Q[0] * r->Q[1] * (r->dim > 2 ? r->Q[2] : 1);
-    if (r->med.pot_kind != TDZ_POT_ZERO) {
-      C<T>* X = to_points(x, -1);
-      k_qmult<T><<<grid_for(NQ), TPB, 0, b->st>>>(X, g, r->med, 0, 0, 0.0, tau);  // i tau V
-      from_points(X, -1, y);
-    }
-    if (!r->const_mass) {
-      for (int a = 0; a < r->dim; ++a) {
-        C<T>* X = to_points(x, a);
-        k_qmult<T><<<grid_for(NQ), TPB, 0, b->st>>>(X, g, r->med, 1, a, 0.0, tau);  // i tau (1/2 m^-1)
-        from_points(X, a, y);
-      }
-    }
+    if (r->med.pot_kind != TDZ_POT_ZERO) quad(x, y, -1, 0, 0, 0.0, tau);  // i tau V
+    if (!r->const_mass)
+      for (int a = 0; a < r->dim; ++a) quad(x, y, a, 1, a, 0.0, tau);     // i tau 1/2 <d_a| m^-1 |d_a>
   }
 };
 
@@ -750,7 +897,7 @@ void observe(NdBatch* b, NdRun* r, Apply<double, P>& op, const double* Et, doubl
     k_hdot<double><<<grid_for(N), TPB, 0, b->st>>>(c, y, N, b->d_red);
     dvals[a] = red_get(b, 2, h)[0];
   }
-  const QGrid g = op.grid();
+  const QGrid<double> g = op.grid();
   C<double>* X = op.to_points(c, -1);
   double kq;
   if (r->const_mass) {
@@ -913,6 +1060,14 @@ int nd_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* o
         cudaStreamSynchronize(b->st);
         return static_cast<double*>(p);
       };
+      auto upf = [&](const std::vector<double>& v) -> float* {
+        std::vector<float> f(v.begin(), v.end());
+        void* p = b->alloc(sizeof(float) * f.size());
+        if (!p) return nullptr;
+        cudaMemcpyAsync(p, f.data(), sizeof(float) * f.size(), cudaMemcpyHostToDevice, b->st);
+        cudaStreamSynchronize(b->st);
+        return static_cast<float*>(p);
+      };
       A.B = up(B.val);
       A.dB = up(B.der);
       A.x = up(B.xq);
@@ -920,7 +1075,15 @@ int nd_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* o
       A.S = up(o.Sa[a].a);
       A.T1 = up(o.T1a[a].a);
       A.D = up(o.Da[a].a);
-      if (!A.B || !A.dB || !A.x || !A.w || !A.S || !A.T1 || !A.D) {
+      A.fB = upf(B.val);
+      A.fdB = upf(B.der);
+      A.fx = upf(B.xq);
+      A.fw = upf(B.wq);
+      A.fS = upf(o.Sa[a].a);
+      A.fT1 = upf(o.T1a[a].a);
+      A.fD = upf(o.Da[a].a);
+      if (!A.B || !A.dB || !A.x || !A.w || !A.S || !A.T1 || !A.D || !A.fB || !A.fdB || !A.fx || !A.fw || !A.fS ||
+          !A.fT1 || !A.fD) {
         delete b;
         return TDZ_ENOMEM;
       }
@@ -976,10 +1139,10 @@ int nd_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* o
   const size_t z64 = sizeof(double2);
   b->d_r0 = static_cast<double2*>(b->alloc(z64 * maxN));
   b->d_y = static_cast<double2*>(b->alloc(z64 * maxN));
-  b->d_t1 = static_cast<double2*>(b->alloc(z64 * maxQ));
-  b->d_t2 = static_cast<double2*>(b->alloc(z64 * maxQ));
-  b->d_t3 = static_cast<double2*>(b->alloc(z64 * maxQ));
-  b->d_t4 = static_cast<double2*>(b->alloc(z64 * maxQ));
+  b->d_t1 = static_cast<double2*>(b->alloc(z64 * maxN));
+  b->d_t2 = static_cast<double2*>(b->alloc(z64 * maxN));
+  b->d_t3 = static_cast<double2*>(b->alloc(z64 * maxN));
+  b->d_t4 = static_cast<double2*>(b->alloc(z64 * maxN));
   b->d_qa = static_cast<double2*>(b->alloc(z64 * maxQ));
   b->d_qb = static_cast<double2*>(b->alloc(z64 * maxQ));
   b->d_red = static_cast<double*>(b->alloc(sizeof(double) * 16));
@@ -1003,10 +1166,10 @@ int nd_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* o
     b->w_z = b->alloc(f * maxN);
     b->w_p = b->alloc(f * maxN);
     b->w_q = b->alloc(f * maxN);
-    b->w_t1 = b->alloc(f * maxQ);
-    b->w_t2 = b->alloc(f * maxQ);
-    b->w_t3 = b->alloc(f * maxQ);
-    b->w_t4 = b->alloc(f * maxQ);
+    b->w_t1 = b->alloc(f * maxN);
+    b->w_t2 = b->alloc(f * maxN);
+    b->w_t3 = b->alloc(f * maxN);
+    b->w_t4 = b->alloc(f * maxN);
     b->w_qa = b->alloc(f * maxQ);
     b->w_qb = b->alloc(f * maxQ);
     if (!b->w_qb) {
