@@ -164,6 +164,44 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def nd_leg(tdz, nsteps):
+    """2-D soft-core atom V = -1/sqrt(x^2+y^2+0.5) on [-150,150]^2, 1024 order-7 splines per axis
+    (1.04 M coefficients), 800 nm 1e14 W/cm^2 sin^2 pulse, dt = 0.05: ms/step in both precisions."""
+    import torch
+    p, nsp, L = 7, 1024, 150.0
+    t = wl.knots_for_nsplines(-L, L, nsp, p)
+    ops = tdz.Ops([tdz.Basis(t, p, p + 1) for _ in range(2)], wl.softcore_medium(0.5))
+    g = wl.greville(t, p)
+    psi = np.exp(-0.5 * g ** 2)
+    c0 = np.kron(psi, psi).astype(complex)
+    c0 /= np.linalg.norm(c0)
+    dt = 0.05
+    field = wl.sin2_pulse(wl.time_grid(dt, nsteps + 1), wl.e0_from_intensity(1e14), wl.omega_from_nm(800.0), 4.0,
+                          dim=2)
+    res = {"workload": "softcore_atom_2d", "coefficients": ops.n, "steps": nsteps}
+    states = {}
+    for name, prec in (("mixed", tdz.MIXED), ("fp64", tdz.FP64)):
+        b = tdz.Batch([ops], [0], prec)
+        b.set_state(0, c0)
+        b.propagate(np.ascontiguousarray(field[:2].reshape(1, 2, 2)), dt, 0, 1)   # warm-up step
+        b.set_state(0, c0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.propagate(np.ascontiguousarray(field[:nsteps + 1].reshape(1, nsteps + 1, 2)), dt, 0, nsteps)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / nsteps
+        o, st = b.observe(0)
+        res[name] = {"value": ops.n / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "status": st,
+                     "norm_drift": float(np.max(np.abs(o[:, -1] - o[0, -1])))}
+        states[name] = b.get_state(0)
+        del b
+    res["mixed_vs_fp64_rel_l2"] = float(np.linalg.norm(states["mixed"] - states["fp64"]) / np.linalg.norm(states["fp64"]))
+    res["speedup_mixed"] = res["fp64"]["ms_per_step"] / res["mixed"]["ms_per_step"]
+    return res
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -175,6 +213,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--nd-steps", type=int, default=2)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -302,6 +341,10 @@ def main():
             "e2e": {"value": world * dof * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "clocks": clk.summary()}
+    # ---------------- 2-D leg: the soft-core atom of the 2-D configuration (1024 x 1024 order-7 splines),
+    # a few steps in both precisions (Kronecker + Gauss-point operator, preconditioned COCG)
+    if rank == 0 and args.nd_steps > 0:
+        line["config_2d"] = nd_leg(tdz, args.nd_steps)
     if rank == 0 and not args.no_cpu:
         # bounded oracle sample sized to ~cpu_seconds; GPU mixed path compared on the same sample
         ns_probe = 20
