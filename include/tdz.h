@@ -145,6 +145,34 @@ int  tdz_get_state(const tdz_batch* b, int run, double* c);
  * tol = 1e-11, max_solves = 6. Ignored by TDZ_FP64 batches (one exact solve per step). */
 int  tdz_batch_set_refinement(tdz_batch* b, double tol, int max_solves);
 
+/* Solver options of 2-D/3-D batches (1-D batches accept and ignore them).
+ * TDZ_OPT_PRECOND selects the preconditioner M of the Krylov (COCG) solve:
+ *   TDZ_PRECOND_AUTO  fast diagonalisation where it was set up at tdz_batch_create, else lines;
+ *   TDZ_PRECOND_LINES M = (x)_a (S_a + i tau mbar T1_a), per-axis banded LDL^T line solves;
+ *   TDZ_PRECOND_FD    M = S(x)S + i tau mbar (T1(x)S + S(x)T1) (all axes), inverted exactly through
+ *                     the per-axis generalised eigenvectors T1_a v = lam S_a v (dense transforms).
+ *   mbar = 1/m for a constant mass, the mean of 1/m_in and 1/m_out for a dot.
+ * TDZ_OPT_OPERATOR selects how the non-separable part of H (V, and the kinetic term of a
+ * position-dependent mass) is applied:
+ *   TDZ_OPERATOR_AUTO        stencil where it was assembled (2-D), else quadrature;
+ *   TDZ_OPERATOR_QUADRATURE  sum factorisation at the Gauss points, f(r) evaluated on the fly;
+ *   TDZ_OPERATOR_STENCIL     2-D only: the same quadrature assembled once into a (2p+1)^2-point
+ *                            stencil per DoF.
+ * Both choices give the same A_n up to rounding. Errors: TDZ_EINVAL (unknown option or value),
+ * TDZ_EUNSUPPORTED (the choice was not set up for this batch). */
+#define TDZ_OPT_PRECOND          1
+#define TDZ_OPT_OPERATOR         2
+#define TDZ_PRECOND_AUTO         0
+#define TDZ_PRECOND_LINES        1
+#define TDZ_PRECOND_FD           2
+#define TDZ_OPERATOR_AUTO        0
+#define TDZ_OPERATOR_QUADRATURE  1
+#define TDZ_OPERATOR_STENCIL     2
+int  tdz_batch_set_option(tdz_batch* b, int option, int value);
+/* Total Krylov iterations of all runs since the batch was created (2-D/3-D; 0 in 1-D, whose
+ * solve is direct). Synchronises the batch stream. */
+int  tdz_krylov_stats(const tdz_batch* b, double* iterations);
+
 /* tdz_propagate: nsteps Crank-Nicolson steps of every run (Sec. "Time
  * propagation", Eq. cn_system), from absolute step index step0:
  *   (S + i dt/2 H_n) c^{n+1} = (S - i dt/2 H_n) c^n,  H_n = H0 + Ebar_n D,
@@ -166,8 +194,8 @@ int  tdz_propagate(tdz_batch* b, const double* field, double dt, int64_t step0, 
  * Synchronises the batch stream. */
 int  tdz_observe(const tdz_batch* b, int run, double* out, int* status);
 /* Largest relative residual ||b - A c||/||b|| seen by the refinement of any run
- * in the last call (mixed precision; 0 for TDZ_FP64) and the mean number of
- * FP32 solves per step. Synchronises the batch stream. */
+ * (mixed precision; 0 for a 1-D TDZ_FP64 batch) and the total number of solves of
+ * all runs, both since the batch was created. Synchronises the batch stream. */
 int  tdz_refine_stats(const tdz_batch* b, double* max_rel_residual, double* mean_solves);
 void tdz_batch_destroy(tdz_batch* b);
 

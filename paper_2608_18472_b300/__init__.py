@@ -21,6 +21,9 @@ LIB_PATH = os.path.join(_HERE, "libtdz.so")
 
 TDZ_OK, TDZ_EINVAL, TDZ_ENOMEM, TDZ_ECUDA, TDZ_ENOCONV, TDZ_ENONFINITE, TDZ_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 FP64, MIXED = 0, 1
+OPT_PRECOND, OPT_OPERATOR = 1, 2
+PRECOND_AUTO, PRECOND_LINES, PRECOND_FD = 0, 1, 2
+OPERATOR_AUTO, OPERATOR_QUADRATURE, OPERATOR_STENCIL = 0, 1, 2
 MAT = {"S": 0, "T": 1, "V": 2, "H0": 3, "D": 4, "G": 5, "K": 6}
 _MASS = {"const": 0, "quesne": 1, "layers": 2, "ellipse": 3}
 _POT = {"zero": 0, "softcore": 1, "ho": 2, "quesne": 3, "layers": 4, "ellipse": 5, "h2p_softcore": 6}
@@ -64,6 +67,8 @@ _sig = {
     "tdz_propagate": (C.c_int, [_vp, _vp, C.c_double, C.c_int64, C.c_int64]),
     "tdz_observe": (C.c_int, [_vp, C.c_int, _vp, C.POINTER(C.c_int)]),
     "tdz_refine_stats": (C.c_int, [_vp, _dp, _dp]),
+    "tdz_batch_set_option": (C.c_int, [_vp, C.c_int, C.c_int]),
+    "tdz_krylov_stats": (C.c_int, [_vp, _dp]),
     "tdz_batch_destroy": (None, [_vp]),
 }
 for _name, (_res, _args) in _sig.items():
@@ -266,6 +271,16 @@ class Batch:
         mx, ns = C.c_double(), C.c_double()
         _check(_lib.tdz_refine_stats(self._h, C.byref(mx), C.byref(ns)), "tdz_refine_stats")
         return mx.value, ns.value
+
+    def set_option(self, option: int, value: int):
+        """2-D/3-D solver options: OPT_PRECOND (PRECOND_*) or OPT_OPERATOR (OPERATOR_*)."""
+        _check(_lib.tdz_batch_set_option(self._h, int(option), int(value)), "tdz_batch_set_option")
+
+    def krylov_stats(self) -> float:
+        """Total Krylov iterations of all runs since creation (0 for 1-D batches)."""
+        it = C.c_double()
+        _check(_lib.tdz_krylov_stats(self._h, C.byref(it)), "tdz_krylov_stats")
+        return it.value
 
     def __del__(self):
         if getattr(self, "_h", None):

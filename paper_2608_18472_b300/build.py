@@ -47,7 +47,9 @@ def build(verbose: bool = False, force: bool = False) -> str:
             cmd.insert(1, "-Xptxas=-v")
         _run(cmd, verbose)
         objs.append(obj)
-    cmd = ["nvcc", *ARCH, "-shared", "-o", LIB, *objs, "-lcudart"]
+    cudalib = "/usr/local/cuda/lib64"
+    cmd = ["nvcc", *ARCH, "-shared", "-o", LIB, *objs, "-L", cudalib, "-lcudart", "-lcublas", "-lcusolver",
+           "-Xlinker", "-rpath", "-Xlinker", cudalib]
     _run(cmd, verbose)
     return LIB
 

@@ -1171,6 +1171,7 @@ int tdz_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* 
       return rc;
     }
     for (int r = 0; r < nruns; ++r) b->total_dof += tdz::nd_run_size(b->nd, r);
+    b->dev_bytes = tdz::nd_device_bytes(b->nd);
     *out = b;
     return TDZ_OK;
   }
@@ -1557,6 +1558,21 @@ int tdz_refine_stats(const tdz_batch* b, double* max_rel_residual, double* mean_
   }
   if (max_rel_residual) *max_rel_residual = mx;
   if (mean_solves) *mean_solves = ns;
+  return TDZ_OK;
+}
+
+int tdz_batch_set_option(tdz_batch* b, int option, int value) {
+  if (!b) return TDZ_EINVAL;
+  if (b->nd) return tdz::nd_set_option(b->nd, option, value);
+  if (option == TDZ_OPT_PRECOND && value >= TDZ_PRECOND_AUTO && value <= TDZ_PRECOND_FD) return TDZ_OK;
+  if (option == TDZ_OPT_OPERATOR && value >= TDZ_OPERATOR_AUTO && value <= TDZ_OPERATOR_STENCIL) return TDZ_OK;
+  return TDZ_EINVAL;
+}
+
+int tdz_krylov_stats(const tdz_batch* b, double* iterations) {
+  if (!b || !iterations) return TDZ_EINVAL;
+  *iterations = 0.0;
+  if (b->nd) return tdz::nd_stats(b->nd, nullptr, nullptr, iterations);
   return TDZ_OK;
 }
 

@@ -64,7 +64,9 @@ int nd_propagate(NdBatch* b, const double* field_host, double dt, long long step
 int nd_observe(const NdBatch* b, int run, double* out, int* status, bool device);
 int nd_stats(const NdBatch* b, double* max_rel, double* solves, double* iters);
 void nd_set_refinement(NdBatch* b, double tol, int max_it);
+int nd_set_option(NdBatch* b, int option, int value);
 int nd_dim(const NdBatch* b);
+size_t nd_device_bytes(const NdBatch* b);
 
 }  // namespace tdz
 

@@ -12,13 +12,19 @@
 //     1/2 sum_a <d_a B| m^-1 |d_a B>, Eq. bdd_elem) by sum factorisation at the Gauss points:
 //     interpolate axis by axis to the points, multiply by w_q f(r_q) with f evaluated on the fly
 //     from the medium, project back axis by axis (Sec. "Parallel assembly" quadrature).
-// Preconditioner: M = (x)_a P_a, P_a = S_a + i tau mbar T1_a (field free, factored once per call),
-// applied as independent banded line solves along each axis.
+// In 2-D the non-separable part may instead be assembled once into a (2p+1)^2-point stencil per DoF
+// (the same quadrature, summed in advance), which is far cheaper to apply in binary64.
+// Preconditioners: the field-free separable operator S(x)S + i tau mbar (T1(x)S + S(x)T1), inverted
+// exactly by fast diagonalisation (per-axis generalised eigenvectors T1_a v = lam S_a v; dense
+// axis transforms as GEMMs), or the product (x)_a (S_a + i tau mbar T1_a) applied as independent
+// banded line solves along each axis.
 // Precision: binary64 throughout (TDZ_FP64), or FP32 COCG inside an outer binary64 residual
 // refinement (TDZ_MIXED). Reductions accumulate in binary64.
 // Observables (Sec. "Dipoles"): norm = c^H S c and d_a = c^H D_a c as Kronecker quadratic forms;
 // c^H G_a c (G_a = <m^-1 d_a V>) and c^H K c (K = <m^-1>) as reductions over the Gauss points.
+#include <cublas_v2.h>
 #include <cuda_runtime.h>
+#include <cusolverDn.h>
 
 #include <algorithm>
 #include <cmath>
@@ -510,6 +516,150 @@ __global__ void k_line_solve(C<T>* __restrict__ v, const C<T>* __restrict__ Lc, 
   }
 }
 
+// ------------------------------------------------------------------------------- 2-D stencil operator
+// In 2-D the non-separable part of H (the potential and, for a position-dependent mass, the kinetic
+// term 1/2 <d_a B| m^-1 |d_a B>, Sec. "Parallel assembly") couples DoF (ix, iy) only with
+// (ix + dx, iy + dy), |dx|, |dy| <= P. It is assembled once, exactly as the Gauss-point quadrature
+// defines it, by sum factorisation:
+//   stage 1: F1[qy][ix][dx] = sum_{qx} w_x (fV B_ix B_jx + fK dB_ix dB_jx)(x_qx, y_qy),
+//            F2[qy][ix][dx] = sum_{qx} w_x  fK B_ix B_jx                   (variable mass only)
+//   stage 2: W[(dy, dx)][iy nx + ix] = sum_{qy} w_y (B_iy B_jy F1 + dB_iy dB_jy F2),
+// with fV = V, fK = 1/2 m^-1, jx = ix + dx, jy = iy + dy. Layout [offset][row] so that a warp reads
+// one offset of 32 consecutive rows in one transaction.
+template <int P>
+__global__ void k_w_stage1(AxisDev ax, AxisDev ay, MediumDev M, int varmass, double* __restrict__ F1,
+                           double* __restrict__ F2) {
+  constexpr int W = 2 * P + 1;
+  const long long total = (long long)ay.Q * ax.n * W;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int dxi = (int)(idx % W);
+    const long long t = idx / W;
+    const int ix = (int)(t % ax.n);
+    const int qy = (int)(t / ax.n);
+    const int jx = ix + dxi - P;
+    double s1 = 0.0, s2 = 0.0;
+    if (jx >= 0 && jx < ax.n) {
+      const int e0 = max(0, max(ix, jx) + 1 - P), e1 = min(ax.E - 1, min(ix, jx) + 1);
+      double r[2];
+      r[1] = ay.x[qy];
+      for (int e = e0; e <= e1; ++e) {
+        const int ri = ix + 1 - e, rj = jx + 1 - e;
+        for (int qq = 0; qq < ax.nq; ++qq) {
+          const int q = e * ax.nq + qq;
+          r[0] = ax.x[q];
+          const double bb = ax.B[(size_t)q * (P + 1) + ri] * ax.B[(size_t)q * (P + 1) + rj];
+          double v = medium_f<double>(M, 0, 0, r, 2) * bb;
+          if (varmass) {
+            const double fk = medium_f<double>(M, 1, 0, r, 2);
+            v += fk * ax.dB[(size_t)q * (P + 1) + ri] * ax.dB[(size_t)q * (P + 1) + rj];
+            s2 += ax.w[q] * fk * bb;
+          }
+          s1 += ax.w[q] * v;
+        }
+      }
+    }
+    F1[idx] = s1;
+    if (varmass) F2[idx] = s2;
+  }
+}
+
+template <int P>
+__global__ void k_w_stage2(AxisDev ax, AxisDev ay, int varmass, const double* __restrict__ F1,
+                           const double* __restrict__ F2, double* __restrict__ W64, float* __restrict__ W32) {
+  constexpr int W = 2 * P + 1;
+  const long long N = (long long)ax.n * ay.n;
+  const long long total = N * W * W;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long row = idx % N;
+    const int off = (int)(idx / N);
+    const int dyi = off / W, dxi = off % W;
+    const int ix = (int)(row % ax.n), iy = (int)(row / ax.n);
+    const int jy = iy + dyi - P, jx = ix + dxi - P;
+    double s = 0.0;
+    if (jy >= 0 && jy < ay.n && jx >= 0 && jx < ax.n) {
+      const int e0 = max(0, max(iy, jy) + 1 - P), e1 = min(ay.E - 1, min(iy, jy) + 1);
+      for (int e = e0; e <= e1; ++e) {
+        const int ri = iy + 1 - e, rj = jy + 1 - e;
+        for (int qq = 0; qq < ay.nq; ++qq) {
+          const int q = e * ay.nq + qq;
+          const size_t f = ((size_t)q * ax.n + ix) * W + dxi;
+          double v = ay.B[(size_t)q * (P + 1) + ri] * ay.B[(size_t)q * (P + 1) + rj] * F1[f];
+          if (varmass) v += ay.dB[(size_t)q * (P + 1) + ri] * ay.dB[(size_t)q * (P + 1) + rj] * F2[f];
+          s += ay.w[q] * v;
+        }
+      }
+    }
+    W64[idx] = s;
+    W32[idx] = (float)s;
+  }
+}
+
+// y += i tau W x  (W real symmetric stencil, layout [(dy + P)(2P + 1) + dx + P][row])
+template <class T, int P>
+__global__ void k_wapply(const T* __restrict__ Wm, const C<T>* __restrict__ x, C<T>* __restrict__ y, int nx, int ny,
+                         double tau) {
+  constexpr int W = 2 * P + 1;
+  const long long N = (long long)nx * ny;
+  for (long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x; row < N;
+       row += (long long)gridDim.x * blockDim.x) {
+    const int ix = (int)(row % nx), iy = (int)(row / nx);
+    T sr = 0, si = 0;
+    for (int dy = -P; dy <= P; ++dy) {
+      const int jy = iy + dy;
+      if (jy < 0 || jy >= ny) continue;
+      const T* wr = Wm + (size_t)(dy + P) * W * N + row;
+      const C<T>* xr = x + (long long)jy * nx;
+#pragma unroll
+      for (int dx = -P; dx <= P; ++dx) {
+        const int jx = ix + dx;
+        if (jx < 0 || jx >= nx) continue;
+        const T w = wr[(size_t)(dx + P) * N];
+        const C<T> v = xr[jx];
+        sr += w * v.r;
+        si += w * v.i;
+      }
+    }
+    const T t = (T)tau;
+    const C<T> o = y[row];
+    y[row] = C<T>{o.r - t * si, o.i + t * sr};
+  }
+}
+
+// ------------------------------------------------------------------------------- fast diagonalisation
+// interleaved complex <-> planar (re plane, then im plane), with a change of precision
+template <class Tv, class Tp>
+__global__ void k_split(const C<Tv>* __restrict__ v, Tp* __restrict__ w, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const C<Tv> a = v[i];
+    w[i] = (Tp)a.r;
+    w[n + i] = (Tp)a.i;
+  }
+}
+template <class Tv, class Tp>
+__global__ void k_merge(const Tp* __restrict__ w, C<Tv>* __restrict__ v, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    v[i] = C<Tv>{(Tv)w[i], (Tv)w[n + i]};
+}
+// in the eigenbasis (index j0 fastest): u /= 1 + i tm (lam0[j0] + lam1[j1] + lam2[j2])
+template <class Tp>
+__global__ void k_fd_scale(Tp* __restrict__ w, long long n, int dim, int n0, int n1, const double* __restrict__ l0,
+                           const double* __restrict__ l1, const double* __restrict__ l2, double tm) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int j0 = (int)(i % n0);
+    const long long t = i / n0;
+    double lam = l0[j0];
+    if (dim > 1) lam += l1[(int)(t % n1)];
+    if (dim > 2) lam += l2[(int)(t / n1)];
+    const double th = tm * lam;
+    const double g = 1.0 / (1.0 + th * th);
+    const double a = (double)w[i], b = (double)w[n + i];
+    w[i] = (Tp)((a + th * b) * g);
+    w[n + i] = (Tp)((b - th * a) * g);
+  }
+}
+
 }  // namespace nd
 }  // namespace tdz
 
@@ -533,6 +683,7 @@ struct NdRun {
   int n[3] = {0, 0, 0}, E[3] = {0, 0, 0}, nq[3] = {0, 0, 0}, Q[3] = {0, 0, 0};
   AxisDev ax[3];
   MediumDev med;
+  int geo = 0;          // index of the geometry tables (fast diagonalisation, stencil)
   bool const_mass = true;
   double cm = 1.0;      // m^-1 for constant mass
   double mbar = 1.0;    // mean m^-1 for the preconditioner
@@ -547,6 +698,18 @@ struct NdRun {
 
 namespace tdz {
 
+// per geometry: fast-diagonalisation factors (S-orthonormal eigenvectors, column j = vector j, and
+// eigenvalues) and the assembled 2-D stencil
+struct NdGeo {
+  bool fd = false;
+  int n[3] = {0, 0, 0};
+  double* V64[3] = {nullptr, nullptr, nullptr};
+  float* V32[3] = {nullptr, nullptr, nullptr};
+  double* lam[3] = {nullptr, nullptr, nullptr};
+  double* W64 = nullptr;
+  float* W32 = nullptr;
+};
+
 struct NdBatch {
   int prec = TDZ_FP64;
   int dim = 0;
@@ -555,6 +718,10 @@ struct NdBatch {
   cudaStream_t st = nullptr;
   std::vector<NdRun> runs;
   std::vector<Ops> ops;  // copies of the operators (per-axis factors for the preconditioner)
+  std::vector<NdGeo> geo;
+  cublasHandle_t blas = nullptr;
+  int opt_precond = TDZ_PRECOND_AUTO;
+  int opt_operator = TDZ_OPERATOR_AUTO;
   std::vector<void*> bufs;
   // work vectors sized for the largest run: binary64 and solve precision
   size_t maxN = 0, maxQ = 0;
@@ -582,6 +749,7 @@ struct NdBatch {
     return p;
   }
   ~NdBatch() {
+    if (blas) cublasDestroy(blas);
     for (void* p : bufs) cudaFree(p);
   }
 };
@@ -601,6 +769,7 @@ struct Apply {
   C<T>* t4;
   C<T>* qa;
   C<T>* qb;
+  const T* Wm = nullptr;  // assembled 2-D stencil of the non-separable terms, or null (quadrature)
 
   // shape helpers: lengths of axes with the first `k` axes already in quadrature space
   void shape(int axis, const int* len, long long& outer, long long& inner) const {
@@ -775,6 +944,10 @@ struct Apply {
   // y = A_n x
   void apply(const C<T>* x, C<T>* y, double tau, const double* ebar) {
     kron(x, y, 0, tau, ebar);
+    if (Wm) {  // i tau (V + variable-mass kinetic) through the assembled stencil
+      k_wapply<T, P><<<grid_for(r->N), TPB, 0, b->st>>>(Wm, x, y, r->n[0], r->n[1], tau);
+      return;
+    }
     if (r->med.pot_kind != TDZ_POT_ZERO) quad(x, y, -1, 0, 0, 0.0, tau);  // i tau V
     if (!r->const_mass)
       for (int a = 0; a < r->dim; ++a) quad(x, y, a, 1, a, 0.0, tau);     // i tau 1/2 <d_a| m^-1 |d_a>
@@ -794,6 +967,60 @@ void line_precond(NdBatch* b, NdRun* r, C<T>* v) {
   }
 }
 
+// ---------------------------------------------------------------- fast diagonalisation
+// One axis transform: contract the slowest axis of the current layout (length ns, R = N / ns
+// values per index) with V (forward, V^T) or V^T (inverse, V), writing the new index fastest:
+//   out(j, r) = sum_k M(k, j) in(r, k),  both planes (re, im) as a batch of two.
+// After dim transforms the axes are back in their original order.
+inline cublasStatus_t gemm_rot(cublasHandle_t h, bool inv, int ns, int R, const float* V, const float* in, float* out,
+                               long long stride) {
+  const float one = 1.0f, zero = 0.0f;
+  return cublasSgemmStridedBatched(h, inv ? CUBLAS_OP_N : CUBLAS_OP_T, CUBLAS_OP_T, ns, R, ns, &one, V, ns, 0, in, R,
+                                   stride, &zero, out, ns, stride, 2);
+}
+inline cublasStatus_t gemm_rot(cublasHandle_t h, bool inv, int ns, int R, const double* V, const double* in,
+                               double* out, long long stride) {
+  const double one = 1.0, zero = 0.0;
+  return cublasDgemmStridedBatched(h, inv ? CUBLAS_OP_N : CUBLAS_OP_T, CUBLAS_OP_T, ns, R, ns, &one, V, ns, 0, in, R,
+                                   stride, &zero, out, ns, stride, 2);
+}
+template <class T> const T* fd_mat(const NdGeo& g, int a);
+template <> const float* fd_mat<float>(const NdGeo& g, int a) { return g.V32[a]; }
+template <> const double* fd_mat<double>(const NdGeo& g, int a) { return g.V64[a]; }
+
+// v <- M^-1 v, M = S(x)S + i tau mbar sum_a (T1_a on axis a, S elsewhere):
+//   M^-1 = ((x)V_a) diag(1 / (1 + i tau mbar sum_a lam_a)) ((x)V_a)^T   since V_a^T S_a V_a = I,
+//   V_a^T T1_a V_a = diag(lam_a). w0, w1: planar scratch of 2N values each.
+template <class T>
+void fd_apply(NdBatch* b, const NdRun* r, C<T>* v, T* w0, T* w1, double tau) {
+  const NdGeo& G = b->geo[r->geo];
+  const long long N = r->N;
+  k_split<T, T><<<grid_for(N), TPB, 0, b->st>>>(v, w0, N);
+  T* cur = w0;
+  T* nxt = w1;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int a = r->dim - 1; a >= 0; --a) {
+      const int ns = r->n[a];
+      gemm_rot(b->blas, pass == 1, ns, (int)(N / ns), fd_mat<T>(G, a), cur, nxt, N);
+      std::swap(cur, nxt);
+    }
+    if (pass == 0)
+      k_fd_scale<T><<<grid_for(N), TPB, 0, b->st>>>(cur, N, r->dim, r->n[0], r->n[1], G.lam[0], G.lam[1], G.lam[2],
+                                                    tau * r->mbar);
+  }
+  k_merge<T, T><<<grid_for(N), TPB, 0, b->st>>>(cur, v, N);
+}
+
+bool use_fd(const NdBatch* b, const NdRun* r) {
+  return b->opt_precond != TDZ_PRECOND_LINES && b->geo[r->geo].fd;
+}
+
+template <class T, int P>
+void precond(NdBatch* b, NdRun* r, Apply<T, P>& op, C<T>* v, double tau) {
+  if (use_fd(b, r)) fd_apply<T>(b, r, v, reinterpret_cast<T*>(op.qa), reinterpret_cast<T*>(op.qb), tau);
+  else line_precond<T, P>(b, r, v);
+}
+
 double* red_get(NdBatch* b, int k, double* host) {
   cudaMemcpyAsync(host, b->d_red, sizeof(double) * k, cudaMemcpyDeviceToHost, b->st);
   cudaStreamSynchronize(b->st);
@@ -810,7 +1037,7 @@ int cocg(NdBatch* b, NdRun* r, Apply<T, P>& op, C<T>* x, C<T>* res, C<T>* z, C<T
   double h[4];
   cudaMemsetAsync(x, 0, sizeof(C<T>) * N, b->st);
   cudaMemcpyAsync(z, res, sizeof(C<T>) * N, cudaMemcpyDeviceToDevice, b->st);
-  line_precond<T, P>(b, r, z);
+  precond<T, P>(b, r, op, z, tau);
   cudaMemcpyAsync(p, z, sizeof(C<T>) * N, cudaMemcpyDeviceToDevice, b->st);
   red_zero(b, 2);
   k_bdot<T><<<grid_for(N), TPB, 0, b->st>>>(res, z, N, b->d_red);
@@ -834,7 +1061,7 @@ int cocg(NdBatch* b, NdRun* r, Apply<T, P>& op, C<T>* x, C<T>* res, C<T>* z, C<T
     ++it;
     if (!(rr > tol_abs2)) break;
     cudaMemcpyAsync(z, res, sizeof(C<T>) * N, cudaMemcpyDeviceToDevice, b->st);
-    line_precond<T, P>(b, r, z);
+    precond<T, P>(b, r, op, z, tau);
     red_zero(b, 2);
     k_bdot<T><<<grid_for(N), TPB, 0, b->st>>>(res, z, N, b->d_red);
     red_get(b, 2, h);
@@ -936,8 +1163,15 @@ int propagate_run(NdBatch* b, NdRun* r, const tdz::Ops& o, const double* field, 
                        static_cast<C<float>*>(b->w_t3), static_cast<C<float>*>(b->w_t4),
                        static_cast<C<float>*>(b->w_qa), static_cast<C<float>*>(b->w_qb)};
   const bool mixed = b->prec == TDZ_MIXED;
-  if (mixed) factor_precond<float>(b, r, o, tau);
-  else factor_precond<double>(b, r, o, tau);
+  const NdGeo& G = b->geo[r->geo];
+  if (G.W64 && b->opt_operator != TDZ_OPERATOR_QUADRATURE) {
+    op64.Wm = G.W64;
+    op32.Wm = G.W32;
+  }
+  if (!use_fd(b, r)) {
+    if (mixed) factor_precond<float>(b, r, o, tau);
+    else factor_precond<double>(b, r, o, tau);
+  }
   C<double>* c = reinterpret_cast<C<double>*>(r->c);
   C<double>* r0 = reinterpret_cast<C<double>*>(b->d_r0);
   C<double>* y = reinterpret_cast<C<double>*>(b->d_y);
@@ -1014,6 +1248,110 @@ int propagate_run(NdBatch* b, NdRun* r, const tdz::Ops& o, const double* field, 
   cudaError_t e = cudaStreamSynchronize(b->st);
   if (e != cudaSuccess) return nd_cuda_fail(e, "tdz_propagate (2-D/3-D)");
   return TDZ_OK;
+}
+
+MediumDev medium_dev(const Medium& m) {
+  MediumDev d{};
+  d.mass_kind = m.mass_kind;
+  d.pot_kind = m.pot_kind;
+  std::memcpy(d.mp, m.mass_par, sizeof(d.mp));
+  std::memcpy(d.vp, m.pot_par, sizeof(d.vp));
+  return d;
+}
+
+__global__ void k_d2f(const double* __restrict__ a, float* __restrict__ f, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    f[i] = (float)a[i];
+}
+
+// Generalised symmetric eigenproblems T1_a v = lam S_a v of every axis (cuSOLVER, binary64), eigenvectors
+// S_a-orthonormal. On a solver failure the geometry keeps the line preconditioner (fd = false).
+int fd_setup(NdBatch* b, int g, const Ops& o) {
+  NdGeo& G = b->geo[g];
+  cusolverDnHandle_t h = nullptr;
+  if (cusolverDnCreate(&h) != CUSOLVER_STATUS_SUCCESS) return TDZ_OK;
+  cusolverDnSetStream(h, b->st);
+  bool ok = true;
+  for (int a = 0; a < o.dim && ok; ++a) {
+    const int n = (int)o.n[a], P = o.p[a];
+    G.n[a] = n;
+    std::vector<double> A((size_t)n * n, 0.0), B((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i)
+      for (int d = 0; d <= P && d <= i; ++d) {
+        const int j = i - d;
+        A[(size_t)i + (size_t)j * n] = A[(size_t)j + (size_t)i * n] = o.T1a[a].at(i, d);
+        B[(size_t)i + (size_t)j * n] = B[(size_t)j + (size_t)i * n] = o.Sa[a].at(i, d);
+      }
+    G.V64[a] = static_cast<double*>(b->alloc(sizeof(double) * A.size()));
+    G.V32[a] = static_cast<float*>(b->alloc(sizeof(float) * A.size()));
+    G.lam[a] = static_cast<double*>(b->alloc(sizeof(double) * n));
+    if (!G.V64[a] || !G.V32[a] || !G.lam[a]) {
+      cusolverDnDestroy(h);
+      return TDZ_ENOMEM;
+    }
+    double* dB = nullptr;
+    int* dinfo = nullptr;
+    double* work = nullptr;
+    int lwork = 0, info = -1;
+    ok = cudaMalloc(&dB, sizeof(double) * B.size()) == cudaSuccess && cudaMalloc(&dinfo, sizeof(int)) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(G.V64[a], A.data(), sizeof(double) * A.size(), cudaMemcpyHostToDevice, b->st) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(dB, B.data(), sizeof(double) * B.size(), cudaMemcpyHostToDevice, b->st) == cudaSuccess;
+    ok = ok && cusolverDnDsygvd_bufferSize(h, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n,
+                                           G.V64[a], n, dB, n, G.lam[a], &lwork) == CUSOLVER_STATUS_SUCCESS;
+    ok = ok && cudaMalloc(&work, sizeof(double) * std::max(lwork, 1)) == cudaSuccess;
+    ok = ok && cusolverDnDsygvd(h, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, G.V64[a], n,
+                                dB, n, G.lam[a], work, lwork, dinfo) == CUSOLVER_STATUS_SUCCESS;
+    ok = ok && cudaMemcpyAsync(&info, dinfo, sizeof(int), cudaMemcpyDeviceToHost, b->st) == cudaSuccess;
+    ok = ok && cudaStreamSynchronize(b->st) == cudaSuccess && info == 0;
+    if (ok) {
+      k_d2f<<<grid_for((long long)n * n), TPB, 0, b->st>>>(G.V64[a], G.V32[a], (long long)n * n);
+      ok = cudaStreamSynchronize(b->st) == cudaSuccess;
+    }
+    cudaFree(work);
+    cudaFree(dinfo);
+    cudaFree(dB);
+  }
+  cusolverDnDestroy(h);
+  G.fd = ok;
+  return TDZ_OK;
+}
+
+template <int P>
+int stencil_setup_p(NdBatch* b, NdGeo& G, const AxisDev& ax, const AxisDev& ay, const MediumDev& M, bool varmass) {
+  constexpr int W = 2 * P + 1;
+  const long long N = (long long)ax.n * ay.n;
+  const size_t nf = (size_t)ay.Q * ax.n * W;
+  G.W64 = static_cast<double*>(b->alloc(sizeof(double) * N * W * W));
+  G.W32 = static_cast<float*>(b->alloc(sizeof(float) * N * W * W));
+  if (!G.W64 || !G.W32) return TDZ_ENOMEM;
+  double *F1 = nullptr, *F2 = nullptr;
+  if (cudaMalloc(&F1, sizeof(double) * nf) != cudaSuccess ||
+      (varmass && cudaMalloc(&F2, sizeof(double) * nf) != cudaSuccess)) {
+    cudaFree(F1);
+    set_error("tdz_batch_create: no device memory for the 2-D stencil assembly");
+    return TDZ_ENOMEM;
+  }
+  k_w_stage1<P><<<grid_for((long long)nf), TPB, 0, b->st>>>(ax, ay, M, varmass ? 1 : 0, F1, F2);
+  k_w_stage2<P><<<grid_for(N * W * W), TPB, 0, b->st>>>(ax, ay, varmass ? 1 : 0, F1, F2, G.W64, G.W32);
+  cudaError_t e = cudaStreamSynchronize(b->st);
+  cudaFree(F1);
+  cudaFree(F2);
+  if (e != cudaSuccess) return nd_cuda_fail(e, "tdz_batch_create (2-D stencil)");
+  return TDZ_OK;
+}
+
+int stencil_setup(NdBatch* b, int g, const AxisDev& ax, const AxisDev& ay, const MediumDev& M, bool varmass) {
+  NdGeo& G = b->geo[g];
+  switch (b->P) {
+    case 1: return stencil_setup_p<1>(b, G, ax, ay, M, varmass);
+    case 2: return stencil_setup_p<2>(b, G, ax, ay, M, varmass);
+    case 3: return stencil_setup_p<3>(b, G, ax, ay, M, varmass);
+    case 4: return stencil_setup_p<4>(b, G, ax, ay, M, varmass);
+    case 5: return stencil_setup_p<5>(b, G, ax, ay, M, varmass);
+    case 6: return stencil_setup_p<6>(b, G, ax, ay, M, varmass);
+    case 7: return stencil_setup_p<7>(b, G, ax, ay, M, varmass);
+    default: return stencil_setup_p<8>(b, G, ax, ay, M, varmass);
+  }
 }
 
 }  // namespace
@@ -1101,6 +1439,7 @@ int nd_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* o
     const Ops& o = ops[ops_index[r]]->o;
     NdRun& R = b->runs[r];
     R.ops = ops_index[r];
+    R.geo = ops_index[r];
     R.dim = dim;
     R.P = P;
     R.N = 1;
@@ -1115,10 +1454,7 @@ int nd_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* o
       NQ *= R.Q[a];
       maxn = std::max(maxn, R.n[a]);
     }
-    R.med.mass_kind = o.med.mass_kind;
-    R.med.pot_kind = o.med.pot_kind;
-    std::memcpy(R.med.mp, o.med.mass_par, sizeof(R.med.mp));
-    std::memcpy(R.med.vp, o.med.pot_par, sizeof(R.med.vp));
+    R.med = medium_dev(o.med);
     R.const_mass = o.med.mass_kind == TDZ_MASS_CONST;
     R.cm = R.const_mass ? 1.0 / o.med.mass_par[0] : 0.0;
     R.mbar = R.const_mass ? R.cm : 0.5 * (1.0 / o.med.mass_par[2] + 1.0 / o.med.mass_par[3]);
@@ -1181,6 +1517,35 @@ int nd_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* o
     delete b;
     set_error("tdz_batch_create: device allocation for 2-D/3-D work buffers failed");
     return TDZ_ENOMEM;
+  }
+  // per geometry: fast-diagonalisation factors and (2-D) the assembled stencil
+  b->geo.resize(nops);
+  if (cublasCreate(&b->blas) != CUBLAS_STATUS_SUCCESS || cublasSetStream(b->blas, b->st) != CUBLAS_STATUS_SUCCESS) {
+    delete b;
+    set_error("tdz_batch_create: cuBLAS initialisation failed");
+    return TDZ_ECUDA;
+  }
+  size_t stencil_bytes = 0;
+  if (dim == 2)
+    for (int g = 0; g < nops; ++g)
+      stencil_bytes += (size_t)geo[g].n[0] * geo[g].n[1] * (2 * P + 1) * (2 * P + 1) * (sizeof(double) + sizeof(float));
+  size_t free_b = 0, total_b = 0;
+  cudaMemGetInfo(&free_b, &total_b);
+  const bool want_stencil = dim == 2 && stencil_bytes < free_b / 2;
+  for (int g = 0; g < nops; ++g) {
+    const int rc = fd_setup(b, g, ops[g]->o);
+    if (rc == TDZ_ENOMEM) {
+      delete b;
+      return rc;
+    }
+    if (want_stencil) {
+      const int rs = stencil_setup(b, g, geo[g].ax[0], geo[g].ax[1], medium_dev(ops[g]->o.med),
+                                   ops[g]->o.med.mass_kind != TDZ_MASS_CONST);
+      if (rs != TDZ_OK) {
+        delete b;
+        return rs;
+      }
+    }
   }
   cudaError_t e = cudaStreamSynchronize(b->st);
   if (e != cudaSuccess) {
@@ -1267,6 +1632,32 @@ int nd_stats(const NdBatch* b, double* max_rel, double* solves, double* iters) {
   return TDZ_OK;
 }
 
+int nd_set_option(NdBatch* b, int option, int value) {
+  if (option == TDZ_OPT_PRECOND) {
+    if (value < TDZ_PRECOND_AUTO || value > TDZ_PRECOND_FD) return TDZ_EINVAL;
+    if (value == TDZ_PRECOND_FD)
+      for (const auto& g : b->geo)
+        if (!g.fd) {
+          set_error("tdz_batch_set_option: fast diagonalisation is not set up for this batch");
+          return TDZ_EUNSUPPORTED;
+        }
+    b->opt_precond = value;
+    return TDZ_OK;
+  }
+  if (option == TDZ_OPT_OPERATOR) {
+    if (value < TDZ_OPERATOR_AUTO || value > TDZ_OPERATOR_STENCIL) return TDZ_EINVAL;
+    if (value == TDZ_OPERATOR_STENCIL)
+      for (const auto& g : b->geo)
+        if (!g.W64) {
+          set_error("tdz_batch_set_option: the stencil operator exists for 2-D batches with enough device memory");
+          return TDZ_EUNSUPPORTED;
+        }
+    b->opt_operator = value;
+    return TDZ_OK;
+  }
+  return TDZ_EINVAL;
+}
+
 void nd_set_refinement(NdBatch* b, double tol, int max_it) {
   b->tol = tol;
   b->max_it = std::max(max_it, 50);
@@ -1276,4 +1667,5 @@ void nd_set_refinement(NdBatch* b, double tol, int max_it) {
 
 namespace tdz {
 int nd_dim(const NdBatch* b) { return b->dim; }
+size_t nd_device_bytes(const NdBatch* b) { return b->dev_bytes; }
 }  // namespace tdz

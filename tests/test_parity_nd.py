@@ -4,7 +4,8 @@ preconditioned COCG) against the CPU oracle (full tensor quadrature, SuperLU per
 Cases: separable HO (Kronecker terms only, plus a quadratic V at the Gauss points), the soft-core
 atom (non-separable V), the elliptical quantum dot (position-dependent mass and step potential at
 the Gauss points), and a 3-D soft-core atom; binary64 (rel-L2 <= 1e-9) and mixed precision (FP32
-COCG inside binary64 refinement, rel-L2 <= 1e-8).
+COCG inside binary64 refinement, rel-L2 <= 1e-8); every operator form (Gauss-point quadrature,
+assembled 2-D stencil) and preconditioner (per-axis lines, fast diagonalisation).
 """
 import numpy as np
 import pytest
@@ -41,19 +42,50 @@ def _case(name):
     raise KeyError(name)
 
 
-@pytest.mark.parametrize("name", ["ho2d", "softcore2d", "dot2d", "softcore3d"])
-def test_nd_matches_oracle(tdz, name):
+_REF = {}
+
+
+def _reference(name):
+    """Oracle trajectory of one case (computed once per module)."""
+    if name not in _REF:
+        knots, p, med, dt, nsteps, e0 = _case(name)
+        dim = len(knots)
+        m = assemble.assemble_nd(knots, [p] * dim, [p + 1] * dim, med)
+        _, c0 = eigen.ground_state(m)
+        t = wl.time_grid(dt, nsteps)
+        field = wl.sin2_pulse(t, e0, 0.5, 1.0, ellipticity=0.3 if dim > 1 else 0.0, dim=dim)
+        c, obs = propagate.cn_propagate(m, c0, field, dt, nsteps)
+        _REF[name] = (m, c0, field, c, obs)
+    return _REF[name]
+
+
+def _combos(dim):
+    """(operator, preconditioner) pairs: every implemented combination."""
+    if dim == 2:
+        return [("auto", "auto"), ("quadrature", "lines"), ("stencil", "lines"), ("quadrature", "fd")]
+    return [("auto", "auto"), ("quadrature", "lines")]
+
+
+CASES = [(n, o, pc) for n, d in (("ho2d", 2), ("softcore2d", 2), ("dot2d", 2), ("softcore3d", 3))
+         for o, pc in _combos(d)]
+
+
+def _configure(tdz, b, op, pc):
+    b.set_option(tdz.OPT_OPERATOR, {"auto": tdz.OPERATOR_AUTO, "quadrature": tdz.OPERATOR_QUADRATURE,
+                                    "stencil": tdz.OPERATOR_STENCIL}[op])
+    b.set_option(tdz.OPT_PRECOND, {"auto": tdz.PRECOND_AUTO, "lines": tdz.PRECOND_LINES, "fd": tdz.PRECOND_FD}[pc])
+
+
+@pytest.mark.parametrize("name,op,pc", CASES, ids=[f"{n}-{o}-{p}" for n, o, p in CASES])
+def test_nd_matches_oracle(tdz, name, op, pc):
     knots, p, med, dt, nsteps, e0 = _case(name)
     dim = len(knots)
-    m = assemble.assemble_nd(knots, [p] * dim, [p + 1] * dim, med)
-    _, c0 = eigen.ground_state(m)
-    t = wl.time_grid(dt, nsteps)
-    field = wl.sin2_pulse(t, e0, 0.5, 1.0, ellipticity=0.3 if dim > 1 else 0.0, dim=dim)
-    c, obs = propagate.cn_propagate(m, c0, field, dt, nsteps)
+    m, c0, field, c, obs = _reference(name)
     ops = tdz.Ops([tdz.Basis(k, p, p + 1) for k in knots], med)
     assert ops.n == m["S"].shape[0]
     for prec, tol in ((tdz.FP64, 1e-9), (tdz.MIXED, 1e-8)):
         b = tdz.Batch([ops], [0], prec)
+        _configure(tdz, b, op, pc)
         b.set_state(0, c0)
         b.propagate(field.reshape(1, nsteps + 1, dim), dt, 0, nsteps)
         og, st = b.observe(0)
@@ -65,3 +97,72 @@ def test_nd_matches_oracle(tdz, name):
         for col in range(1 + dim, 2 + 3 * dim):
             scale = max(1e-3, np.max(np.abs(obs[:, col])))
             assert np.max(np.abs(og[:, col] - obs[:, col])) < 10 * tol * scale, (prec, col)
+
+
+def test_fast_diagonalisation_needs_fewer_iterations(tdz):
+    """With tau * lam_max(T1) >> 1 (fine grid, long step) the per-axis product preconditioner carries the
+    cross term (i tau)^2 T1(x)T1; the exact inverse of the field-free separable part does not, and needs
+    fewer Krylov iterations (both reach the same tolerance)."""
+    p, dt, nsteps = 4, 0.5, 4
+    t = wl.knots_for_nsplines(-10.0, 10.0, 60, p)
+    ops = tdz.Ops([tdz.Basis(t, p, p + 1)] * 2, wl.softcore_medium(0.5))
+    g = wl.greville(t, p)
+    psi = np.exp(-0.5 * g ** 2)
+    c0 = np.kron(psi, psi).astype(complex)
+    field = wl.sin2_pulse(wl.time_grid(dt, nsteps), 0.05, 0.5, 1.0, dim=2).reshape(1, nsteps + 1, 2)
+    its, states = {}, {}
+    for pc in ("lines", "fd"):
+        b = tdz.Batch([ops], [0], tdz.FP64)
+        _configure(tdz, b, "auto", pc)
+        b.set_state(0, c0)
+        b.propagate(field, dt, 0, nsteps)
+        assert b.observe(0)[1] == tdz.TDZ_OK
+        its[pc] = b.krylov_stats()
+        states[pc] = b.get_state(0)
+    assert 0 < its["fd"] < 0.5 * its["lines"], its
+    assert np.linalg.norm(states["fd"] - states["lines"]) < 1e-10 * np.linalg.norm(states["lines"])
+
+
+def test_uneven_batch_of_dots(tdz):
+    """Several 2-D dots of different sizes and shapes in one batch (independent runs), each against
+    its own oracle trajectory, in both precisions."""
+    rng = np.random.default_rng(wl.SEED)
+    p, dt, nsteps = 3, 0.1, 10
+    runs = []
+    for k, nspl in enumerate((18, 24, 21)):
+        a, bb = rng.uniform(2.0, 3.5, 2)
+        t = wl.knots_for_nsplines(-6.0, 6.0, nspl, p)
+        med = wl.medium({"kind": "ellipse", "a": a, "b": bb, "m_in": 0.5, "m_out": 1.0},
+                        {"kind": "ellipse", "a": a, "b": bb, "v_in": -1.0, "v_out": 0.0})
+        m = assemble.assemble_nd([t, t], [p, p], [p + 1, p + 1], med)
+        _, c0 = eigen.ground_state(m)
+        field = wl.sin2_pulse(wl.time_grid(dt, nsteps), 0.1 + 0.05 * k, 0.5, 1.0, ellipticity=0.3, dim=2)
+        c, _ = propagate.cn_propagate(m, c0, field, dt, nsteps)
+        runs.append((tdz.Ops([tdz.Basis(t, p, p + 1)] * 2, med), c0, field, c))
+    order = [2, 0, 1, 0]  # run -> geometry, one geometry used twice
+    for prec, tol in ((tdz.FP64, 1e-9), (tdz.MIXED, 1e-8)):
+        b = tdz.Batch([r[0] for r in runs], order, prec)
+        fields = np.stack([runs[g][2] for g in order])
+        for i, g in enumerate(order):
+            b.set_state(i, runs[g][1])
+        b.propagate(fields, dt, 0, nsteps)
+        for i, g in enumerate(order):
+            cg = b.get_state(i)
+            assert b.observe(i)[1] == tdz.TDZ_OK
+            rel = np.linalg.norm(cg - runs[g][3]) / np.linalg.norm(runs[g][3])
+            assert rel < tol, (prec, i, rel)
+
+
+def test_options_are_validated(tdz):
+    t = wl.knots_for_nsplines(-6.0, 6.0, 12, 3)
+    ops3 = tdz.Ops([tdz.Basis(t, 3, 4)] * 3, wl.softcore_medium(0.5))
+    b = tdz.Batch([ops3], [0], tdz.FP64)
+    with pytest.raises(tdz.TDZError) as ei:
+        b.set_option(tdz.OPT_OPERATOR, tdz.OPERATOR_STENCIL)   # stencil is 2-D only
+    assert ei.value.code == tdz.TDZ_EUNSUPPORTED
+    with pytest.raises(tdz.TDZError) as ei:
+        b.set_option(99, 0)
+    assert ei.value.code == tdz.TDZ_EINVAL
+    with pytest.raises(tdz.TDZError) as ei:
+        b.set_option(tdz.OPT_PRECOND, 7)
+    assert ei.value.code == tdz.TDZ_EINVAL
