@@ -42,7 +42,8 @@ constexpr int LANES = 32;
 constexpr int MAXP = 8;
 
 struct GeomDev {
-  int n, m, K, pad;
+  int n, m, K;
+  int ks;  // interleave stride of the per-row arrays: 32 x (warps per run)
   // Band arrays, [m][P+1][32] each.
   //   binary64 path: S, H (= H0 = T + V), D, G, Km (<m^-1>) as double.
   //   mixed path:    S  = float4 {S.hi, H0.hi, D.hi, S.lo}   (one 16-byte load per entry in the sweeps)
@@ -90,8 +91,8 @@ struct StepArgs {
 
 // ============================================================================ band access
 template <int P>
-TDZ_DEV int bidx(int i, int d, int k) { return (i * (P + 1) + d) * LANES + k; }
-TDZ_DEV int ridx(int i, int k) { return i * LANES + k; }
+TDZ_DEV int bidx(int i, int d, int k, int ks) { return (i * (P + 1) + d) * ks + k; }
+TDZ_DEV int ridx(int i, int k, int ks) { return i * ks + k; }
 // L1 prefetch of the line holding p: rows ahead of a lane's sequential row loop are requested
 // early, so the loop does not pay a full memory round trip per row (no registers needed).
 TDZ_DEV void pf(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
@@ -112,12 +113,17 @@ TDZ_DEV cx<T> a_entry(const GeomDev& g, int idx, T tau, T ebar) {
 
 // ============================================================================ per-lane context
 struct Lane {
-  int k, K, m, mI;
+  int k, K, m, mI, ks;  // chunk index, chunks, rows per chunk, interior rows, interleave stride
   bool active, up, dn;
 };
 
+// Shared-memory elements per warp slot for the reduced system. A run of w warps has up to 32w - 1
+// separators and uses the areas of its w slots: Dg and E (cap P x P blocks each), rb (cap x P) and
+// one P x P scratch tile, cap = 32w - 1; 2 * 32 P^2 + 32 P + P^2 per slot covers w = 1 and w = 2.
+__host__ __device__ constexpr int red_elems(int P) { return 2 * 32 * P * P + 32 * P + P * P; }
+
 template <class T>
-struct Red {  // reduced system in shared memory (one warp)
+struct Red {  // reduced system of one run in shared memory
   cx<T>* Dg;  // [31][P*P]  diagonal blocks -> pivot inverses
   cx<T>* E;   // [31][P*P]  sub-diagonal blocks Ŝ(s, s-1) -> F_s
   cx<T>* rb;  // [31][P]    rhs -> separator solution
@@ -130,6 +136,7 @@ struct Red {  // reduced system in shared memory (one warp)
 // (the lane's separator), their coupling to the separator above and their reduced rhs.
 template <int P, class T, bool MIXED>
 TDZ_DEV void sweep1(const GeomDev& g, const RunDev& run, const Lane& L, T tau, T ebar, Red<T>& red) {
+  const int ks = L.ks;
   cx<T> w[P + 1][P + 1];
   cx<T> cw[P + 1][P];
   cx<T> rw[P + 1];
@@ -140,23 +147,23 @@ TDZ_DEV void sweep1(const GeomDev& g, const RunDev& run, const Lane& L, T tau, T
 #pragma unroll
   for (int a = 0; a < P; ++a) {
 #pragma unroll
-    for (int b = 0; b <= a; ++b) w[a][b] = a_entry<P, T, MIXED>(g, bidx<P>(a, a - b, k), tau, ebar);
+    for (int b = 0; b <= a; ++b) w[a][b] = a_entry<P, T, MIXED>(g, bidx<P>(a, a - b, k, ks), tau, ebar);
 #pragma unroll
     for (int j = 0; j < P; ++j)
-      cw[a][j] = (L.up && a <= j) ? a_entry<P, T, MIXED>(g, bidx<P>(a, a + P - j, k), tau, ebar) : czero<T>();
-    rw[a] = rhs[ridx(a, k)];
+      cw[a][j] = (L.up && a <= j) ? a_entry<P, T, MIXED>(g, bidx<P>(a, a + P - j, k, ks), tau, ebar) : czero<T>();
+    rw[a] = rhs[ridx(a, k, ks)];
   }
   for (int i = 0; i < L.mI; ++i) {
     const int r = i + P;  // row entering the window
     if (r + 2 < L.m) {
 #pragma unroll
-      for (int b = 0; b <= P; ++b) pf(static_cast<const char*>(g.S) + (size_t)bidx<P>(r + 2, b, k) * (MIXED ? 16 : 8));
-      pf(rhs + ridx(r + 2, k));
+      for (int b = 0; b <= P; ++b) pf(static_cast<const char*>(g.S) + (size_t)bidx<P>(r + 2, b, k, ks) * (MIXED ? 16 : 8));
+      pf(rhs + ridx(r + 2, k, ks));
     }
     if (r < L.m) {
 #pragma unroll
-      for (int b = 0; b <= P; ++b) w[P][b] = a_entry<P, T, MIXED>(g, bidx<P>(r, P - b, k), tau, ebar);
-      rw[P] = rhs[ridx(r, k)];
+      for (int b = 0; b <= P; ++b) w[P][b] = a_entry<P, T, MIXED>(g, bidx<P>(r, P - b, k, ks), tau, ebar);
+      rw[P] = rhs[ridx(r, k, ks)];
     } else {
 #pragma unroll
       for (int b = 0; b <= P; ++b) w[P][b] = czero<T>();
@@ -169,9 +176,9 @@ TDZ_DEV void sweep1(const GeomDev& g, const RunDev& run, const Lane& L, T tau, T
 #pragma unroll
     for (int a = 1; a <= P; ++a) {
       l[a] = cmul(w[a][0], dinv);
-      Lc[(i * P + a - 1) * LANES + k] = l[a];
+      Lc[(i * P + a - 1) * ks + k] = l[a];
     }
-    Dv[ridx(i, k)] = dinv;
+    Dv[ridx(i, k, ks)] = dinv;
 #pragma unroll
     for (int a = 1; a <= P; ++a) {
 #pragma unroll
@@ -212,6 +219,7 @@ TDZ_DEV void sweep1(const GeomDev& g, const RunDev& run, const Lane& L, T tau, T
 // for that separator; added into the shared reduced system.
 template <int P, class T, bool MIXED>
 TDZ_DEV void sweep2(const GeomDev& g, const RunDev& run, const Lane& L, T tau, T ebar, Red<T>& red) {
+  const int ks = L.ks;
   cx<T> w[P + 1][P + 1];  // w[a][b] = A(r-a, r-b), b <= a, r = current pivot row
   cx<T> rw[P + 1];
   const cx<T>* rhs = static_cast<const cx<T>*>(run.rhs);
@@ -220,23 +228,23 @@ TDZ_DEV void sweep2(const GeomDev& g, const RunDev& run, const Lane& L, T tau, T
 #pragma unroll
   for (int a = 0; a < P; ++a) {
 #pragma unroll
-    for (int b = 0; b <= a; ++b) w[a][b] = a_entry<P, T, MIXED>(g, bidx<P>(r0 - b, a - b, k), tau, ebar);
-    rw[a] = rhs[ridx(r0 - a, k)];
+    for (int b = 0; b <= a; ++b) w[a][b] = a_entry<P, T, MIXED>(g, bidx<P>(r0 - b, a - b, k, ks), tau, ebar);
+    rw[a] = rhs[ridx(r0 - a, k, ks)];
   }
   for (int t = 0; t < L.mI; ++t) {
     const int r = r0 - t;
     const int q = r - P;  // row entering the window
     if (q - 2 >= 0) {
 #pragma unroll
-      for (int b = 0; b <= P; ++b) pf(static_cast<const char*>(g.S) + (size_t)bidx<P>(q - 2, b, k) * (MIXED ? 16 : 8));
-      pf(rhs + ridx(q - 2, k));
+      for (int b = 0; b <= P; ++b) pf(static_cast<const char*>(g.S) + (size_t)bidx<P>(q - 2, b, k, ks) * (MIXED ? 16 : 8));
+      pf(rhs + ridx(q - 2, k, ks));
     }
 #pragma unroll
     for (int b = 0; b <= P; ++b) {
       const int rb = r - b;  // A(q, rb) stored at row rb (rb >= q), diagonal P - b
-      w[P][b] = (rb >= 0) ? a_entry<P, T, MIXED>(g, bidx<P>(rb, P - b, k), tau, ebar) : czero<T>();
+      w[P][b] = (rb >= 0) ? a_entry<P, T, MIXED>(g, bidx<P>(rb, P - b, k, ks), tau, ebar) : czero<T>();
     }
-    rw[P] = (q >= 0) ? rhs[ridx(q, k)] : czero<T>();
+    rw[P] = (q >= 0) ? rhs[ridx(q, k, ks)] : czero<T>();
     const cx<T> dinv = crecip(w[0][0]);
     cx<T> l[P + 1];
 #pragma unroll
@@ -386,6 +394,7 @@ TDZ_DEV void accumulate(const RunDev& run, int idx, cx<T> x) {
 
 template <int P, class T, bool MIXED>
 TDZ_DEV void substitute(const GeomDev& g, const RunDev& run, const Lane& L, T tau, T ebar, const Red<T>& red) {
+  const int ks = L.ks;
   const int k = L.k;
   const cx<T>* __restrict__ rhs = static_cast<const cx<T>*>(run.rhs);
   const cx<T>* __restrict__ Lc = static_cast<const cx<T>*>(run.Lc);
@@ -402,148 +411,131 @@ TDZ_DEV void substitute(const GeomDev& g, const RunDev& run, const Lane& L, T ta
   for (int d = 0; d <= P; ++d) gw[d] = czero<T>();
   for (int i = 0; i < L.mI; ++i) {
     if (i + 4 < L.mI) {
-      pf(rhs + ridx(i + 4, k));
-      pf(Dv + ridx(i + 4, k));
+      pf(rhs + ridx(i + 4, k, ks));
+      pf(Dv + ridx(i + 4, k, ks));
 #pragma unroll
-      for (int d = 0; d < P; ++d) pf(Lc + ((i + 4) * P + d) * LANES + k);
+      for (int d = 0; d < P; ++d) pf(Lc + ((i + 4) * P + d) * ks + k);
     }
-    cx<T> b = rhs[ridx(i, k)];
+    cx<T> b = rhs[ridx(i, k, ks)];
     if (L.up && i < P) {
 #pragma unroll
       for (int j = 0; j < P; ++j)
-        if (j >= i) b = cmsub(b, a_entry<P, T, MIXED>(g, bidx<P>(i, i + P - j, k), tau, ebar), xup[j]);
+        if (j >= i) b = cmsub(b, a_entry<P, T, MIXED>(g, bidx<P>(i, i + P - j, k, ks), tau, ebar), xup[j]);
     }
 #pragma unroll
     for (int d = 1; d <= P; ++d)
-      if (i - d >= 0) b = cmsub(b, Lc[((i - d) * P + d - 1) * LANES + k], gw[d]);
+      if (i - d >= 0) b = cmsub(b, Lc[((i - d) * P + d - 1) * ks + k], gw[d]);
 #pragma unroll
     for (int d = P; d >= 2; --d) gw[d] = gw[d - 1];
     gw[1] = b;
-    gd[ridx(i, k)] = cmul(b, Dv[ridx(i, k)]);
+    gd[ridx(i, k, ks)] = cmul(b, Dv[ridx(i, k, ks)]);
   }
   cx<T> xw[P + 1];  // xw[d] = x_{i+d}
 #pragma unroll
   for (int d = 1; d <= P; ++d) xw[d] = xdn[d - 1];
   for (int i = L.mI - 1; i >= 0; --i) {
     if (i - 4 >= 0) {
-      pf(gd + ridx(i - 4, k));
-      if constexpr (MIXED) pf(run.W + ridx(i - 4, k));
-      else pf(static_cast<const double2*>(run.state) + ridx(i - 4, k));
+      pf(gd + ridx(i - 4, k, ks));
+      if constexpr (MIXED) pf(run.W + ridx(i - 4, k, ks));
+      else pf(static_cast<const double2*>(run.state) + ridx(i - 4, k, ks));
 #pragma unroll
-      for (int d = 0; d < P; ++d) pf(Lc + ((i - 4) * P + d) * LANES + k);
+      for (int d = 0; d < P; ++d) pf(Lc + ((i - 4) * P + d) * ks + k);
     }
-    cx<T> x = gd[ridx(i, k)];
+    cx<T> x = gd[ridx(i, k, ks)];
 #pragma unroll
-    for (int d = 1; d <= P; ++d) x = cmsub(x, Lc[(i * P + d - 1) * LANES + k], xw[d]);
+    for (int d = 1; d <= P; ++d) x = cmsub(x, Lc[(i * P + d - 1) * ks + k], xw[d]);
 #pragma unroll
     for (int d = P; d >= 2; --d) xw[d] = xw[d - 1];
     xw[1] = x;
-    accumulate<T, MIXED>(run, ridx(i, k), x);
+    accumulate<T, MIXED>(run, ridx(i, k, ks), x);
   }
   if (L.dn) {
 #pragma unroll
-    for (int j = 0; j < P; ++j) accumulate<T, MIXED>(run, ridx(L.mI + j, k), xdn[j]);
+    for (int j = 0; j < P; ++j) accumulate<T, MIXED>(run, ridx(L.mI + j, k, ks), xdn[j]);
   }
 }
 
+// Second solve with the factors of the last factorisation (no refactorisation), in two lane phases
+// that the caller separates with block barriers (neighbouring chunks may sit in different warps):
+//   resolve_fwd: forward substitution with the stored L, which also eliminates into the lower
+//                separator rows (their multipliers are stored too), giving that separator's rhs;
+//   resolve_bwd: backward pass for the top of A_II^-1 r, whose product with the upper coupling
+//                (-C^T z_T) is the upper separator's remaining rhs term;
+// then the reduced solve with the stored block factors (red_solve) and substitute().
 template <int P, class T, bool MIXED>
-TDZ_DEV void solve(const GeomDev& g, const RunDev& run, const Lane& L, T tau, T ebar, Red<T>& red, int lane) {
-  if (L.active) sweep1<P, T, MIXED>(g, run, L, tau, ebar, red);
-  __syncwarp();
-  if (L.active && L.up) sweep2<P, T, MIXED>(g, run, L, tau, ebar, red);
-  __syncwarp();
-  const int nsep = L.K - 1;
-  if (nsep > 0) {
-    red_factor<P, T>(red, nsep, lane);
-    red_solve<P, T>(red, nsep, lane);
-  }
-  __syncwarp();
-  if (L.active) substitute<P, T, MIXED>(g, run, L, tau, ebar, red);
-  __syncwarp();
-}
-
-// Second solve with the factors of the last solve(): forward substitution with the stored L that
-// also eliminates into the lower separator rows (their multipliers are stored too), a backward
-// pass for the top of A_II^-1 r (the upper separator's term -C^T z_T), the reduced solve with the
-// stored block factors, then the substitution. No refactorisation.
-template <int P, class T, bool MIXED>
-TDZ_DEV void resolve(const GeomDev& g, const RunDev& run, const Lane& L, T tau, T ebar, Red<T>& red, int lane) {
+TDZ_DEV void resolve_fwd(const GeomDev& g, const RunDev& run, const Lane& L, Red<T>& red) {
+  const int ks = L.ks;
   const int k = L.k;
-  if (L.active) {
-    const cx<T>* __restrict__ rhs = static_cast<const cx<T>*>(run.rhs);
-    const cx<T>* __restrict__ Lc = static_cast<const cx<T>*>(run.Lc);
-    const cx<T>* __restrict__ Dv = static_cast<const cx<T>*>(run.Dv);
-    cx<T>* __restrict__ gd = static_cast<cx<T>*>(run.gd);
-    cx<T> sep[P];
+  const cx<T>* __restrict__ rhs = static_cast<const cx<T>*>(run.rhs);
+  const cx<T>* __restrict__ Lc = static_cast<const cx<T>*>(run.Lc);
+  const cx<T>* __restrict__ Dv = static_cast<const cx<T>*>(run.Dv);
+  cx<T>* __restrict__ gd = static_cast<cx<T>*>(run.gd);
+  cx<T> sep[P];
 #pragma unroll
-    for (int j = 0; j < P; ++j) sep[j] = L.dn ? rhs[ridx(L.mI + j, k)] : czero<T>();
-    cx<T> gw[P + 1];
+  for (int j = 0; j < P; ++j) sep[j] = L.dn ? rhs[ridx(L.mI + j, k, ks)] : czero<T>();
+  cx<T> gw[P + 1];
 #pragma unroll
-    for (int d = 0; d <= P; ++d) gw[d] = czero<T>();
-    for (int i = 0; i < L.mI; ++i) {
-      if (i + 4 < L.mI) {
-        pf(rhs + ridx(i + 4, k));
-        pf(Dv + ridx(i + 4, k));
+  for (int d = 0; d <= P; ++d) gw[d] = czero<T>();
+  for (int i = 0; i < L.mI; ++i) {
+    if (i + 4 < L.mI) {
+      pf(rhs + ridx(i + 4, k, ks));
+      pf(Dv + ridx(i + 4, k, ks));
 #pragma unroll
-        for (int d = 0; d < P; ++d) pf(Lc + ((i + 4) * P + d) * LANES + k);
-      }
-      cx<T> b = rhs[ridx(i, k)];
-#pragma unroll
-      for (int d = 1; d <= P; ++d)
-        if (i - d >= 0) b = cmsub(b, Lc[((i - d) * P + d - 1) * LANES + k], gw[d]);
-#pragma unroll
-      for (int d = P; d >= 2; --d) gw[d] = gw[d - 1];
-      gw[1] = b;
-      gd[ridx(i, k)] = cmul(b, Dv[ridx(i, k)]);
-      if (L.dn && i >= L.mI - P) {
-#pragma unroll
-        for (int a = 1; a <= P; ++a) {
-          const int j = i + a - L.mI;  // separator row index of row i+a
-          if (j >= 0) sep[j] = cmsub(sep[j], Lc[(i * P + a - 1) * LANES + k], b);
-        }
-      }
+      for (int d = 0; d < P; ++d) pf(Lc + ((i + 4) * P + d) * ks + k);
     }
-    if (L.dn) {
+    cx<T> b = rhs[ridx(i, k, ks)];
 #pragma unroll
-      for (int j = 0; j < P; ++j) red.rb[k * P + j] = sep[j];
+    for (int d = 1; d <= P; ++d)
+      if (i - d >= 0) b = cmsub(b, Lc[((i - d) * P + d - 1) * ks + k], gw[d]);
+#pragma unroll
+    for (int d = P; d >= 2; --d) gw[d] = gw[d - 1];
+    gw[1] = b;
+    gd[ridx(i, k, ks)] = cmul(b, Dv[ridx(i, k, ks)]);
+    if (L.dn && i >= L.mI - P) {
+#pragma unroll
+      for (int a = 1; a <= P; ++a) {
+        const int j = i + a - L.mI;  // separator row index of row i+a
+        if (j >= 0) sep[j] = cmsub(sep[j], Lc[(i * P + a - 1) * ks + k], b);
+      }
     }
   }
-  __syncwarp();
-  if (L.active && L.up) {
-    const cx<T>* __restrict__ Lc = static_cast<const cx<T>*>(run.Lc);
-    const cx<T>* __restrict__ gd = static_cast<const cx<T>*>(run.gd);
-    cx<T> zw[P + 1];  // zw[d] = z_{i+d}; the top P values end up in zw[1..P] reversed
+  if (L.dn) {
 #pragma unroll
-    for (int d = 0; d <= P; ++d) zw[d] = czero<T>();
-    for (int i = L.mI - 1; i >= 0; --i) {
-      if (i - 4 >= 0) {
-        pf(gd + ridx(i - 4, k));
-#pragma unroll
-        for (int d = 0; d < P; ++d) pf(Lc + ((i - 4) * P + d) * LANES + k);
-      }
-      cx<T> z = gd[ridx(i, k)];
-#pragma unroll
-      for (int d = 1; d <= P; ++d) z = cmsub(z, Lc[(i * P + d - 1) * LANES + k], zw[d]);
-#pragma unroll
-      for (int d = P; d >= 2; --d) zw[d] = zw[d - 1];
-      zw[1] = z;
-    }
-    // zw[1 + i] = z_i for i = 0..P-1
-#pragma unroll
-    for (int j = 0; j < P; ++j) {
-      cx<T> acc = czero<T>();
-#pragma unroll
-      for (int i = 0; i <= j; ++i)
-        if (i < L.mI) acc = cmadd(acc, a_entry<P, T, MIXED>(g, bidx<P>(i, i + P - j, k), tau, ebar), zw[1 + i]);
-      red.rb[(k - 1) * P + j] = red.rb[(k - 1) * P + j] - acc;
-    }
+    for (int j = 0; j < P; ++j) red.rb[k * P + j] = sep[j];
   }
-  __syncwarp();
-  const int nsep = L.K - 1;
-  if (nsep > 0) red_solve<P, T>(red, nsep, lane);
-  __syncwarp();
-  if (L.active) substitute<P, T, MIXED>(g, run, L, tau, ebar, red);
-  __syncwarp();
+}
+
+template <int P, class T, bool MIXED>
+TDZ_DEV void resolve_bwd(const GeomDev& g, const RunDev& run, const Lane& L, T tau, T ebar, Red<T>& red) {
+  const int ks = L.ks;
+  const int k = L.k;
+  const cx<T>* __restrict__ Lc = static_cast<const cx<T>*>(run.Lc);
+  const cx<T>* __restrict__ gd = static_cast<const cx<T>*>(run.gd);
+  cx<T> zw[P + 1];  // zw[d] = z_{i+d}; the top P values end up in zw[1..P] reversed
+#pragma unroll
+  for (int d = 0; d <= P; ++d) zw[d] = czero<T>();
+  for (int i = L.mI - 1; i >= 0; --i) {
+    if (i - 4 >= 0) {
+      pf(gd + ridx(i - 4, k, ks));
+#pragma unroll
+      for (int d = 0; d < P; ++d) pf(Lc + ((i - 4) * P + d) * ks + k);
+    }
+    cx<T> z = gd[ridx(i, k, ks)];
+#pragma unroll
+    for (int d = 1; d <= P; ++d) z = cmsub(z, Lc[(i * P + d - 1) * ks + k], zw[d]);
+#pragma unroll
+    for (int d = P; d >= 2; --d) zw[d] = zw[d - 1];
+    zw[1] = z;
+  }
+  // zw[1 + i] = z_i for i = 0..P-1
+#pragma unroll
+  for (int j = 0; j < P; ++j) {
+    cx<T> acc = czero<T>();
+#pragma unroll
+    for (int i = 0; i <= j; ++i)
+      if (i < L.mI) acc = cmadd(acc, a_entry<P, T, MIXED>(g, bidx<P>(i, i + P - j, k, ks), tau, ebar), zw[1 + i]);
+    red.rb[(k - 1) * P + j] = red.rb[(k - 1) * P + j] - acc;
+  }
 }
 
 // ============================================================================ row helpers
@@ -565,6 +557,7 @@ TDZ_DEV bool locate(const Lane& L, int j, int& row, int& chunk) {
 // r = -i tau H_n (2 c), scatter form over rows -P..m+P-1 with pending sums for P+1 rows.
 template <int P>
 TDZ_DEV void rhs_fp64(const GeomDev& g, const RunDev& run, const Lane& L, double tau, double ebar) {
+  const int ks = L.ks;
   const double2* c = static_cast<const double2*>(run.state);
   cx<double>* rhs = static_cast<cx<double>*>(run.rhs);
   cx<double> uw[P + 1];   // uw[d] = u_{j-d}
@@ -582,12 +575,12 @@ TDZ_DEV void rhs_fp64(const GeomDev& g, const RunDev& run, const Lane& L, double
 #pragma unroll
     for (int d = 0; d <= P; ++d) h[d] = 0.0;
     if (ok) {
-      double2 cc = c[ridx(row, chunk)];
+      double2 cc = c[ridx(row, chunk, ks)];
       u = cx<double>{2.0 * cc.x, 2.0 * cc.y};
       if (j >= 0) {
 #pragma unroll
         for (int d = 0; d <= P; ++d) {
-          const int idx = bidx<P>(row, d, chunk);
+          const int idx = bidx<P>(row, d, chunk, ks);
           h[d] = tau * fma(ebar, static_cast<const double*>(g.D)[idx], static_cast<const double*>(g.H)[idx]);
         }
       }
@@ -618,7 +611,7 @@ TDZ_DEV void rhs_fp64(const GeomDev& g, const RunDev& run, const Lane& L, double
     const int jf = j - P;  // row complete
     if (jf >= 0 && jf < L.m) {
       // r = -i * acc  ->  (acc.i, -acc.r)
-      rhs[ridx(jf, L.k)] = cx<double>{acc[P].i, -acc[P].r};
+      rhs[ridx(jf, L.k, ks)] = cx<double>{acc[P].i, -acc[P].r};
     }
   }
 }
@@ -629,6 +622,7 @@ TDZ_DEV void rhs_fp64(const GeomDev& g, const RunDev& run, const Lane& L, double
 // reference for the relative residual.
 template <int P, bool SCALE>
 TDZ_DEV void rhs_mixed(const GeomDev& g, const RunDev& run, const Lane& L, ff tau, ff ebar, float& rr, float& bb) {
+  const int ks = L.ks;
   const float4* __restrict__ c = static_cast<const float4*>(run.state);
   const float4* __restrict__ W = run.W;
   const float4* __restrict__ A4 = static_cast<const float4*>(g.S);
@@ -655,13 +649,13 @@ TDZ_DEV void rhs_mixed(const GeomDev& g, const RunDev& run, const Lane& L, ff ta
     {
       int r2, c2;
       if (j + 2 < L.m + P && locate(L, j + 2, r2, c2)) {
-        pf(c + ridx(r2, c2));
-        pf(W + ridx(r2, c2));
+        pf(c + ridx(r2, c2, ks));
+        pf(W + ridx(r2, c2, ks));
         if (j + 2 >= 0) {
 #pragma unroll
           for (int d = 0; d <= P; ++d) {
-            pf(A4 + bidx<P>(r2, d, c2));
-            pf(HD + bidx<P>(r2, d, c2));
+            pf(A4 + bidx<P>(r2, d, c2, ks));
+            pf(HD + bidx<P>(r2, d, c2, ks));
           }
         }
       }
@@ -672,15 +666,15 @@ TDZ_DEV void rhs_mixed(const GeomDev& g, const RunDev& run, const Lane& L, ff ta
 #pragma unroll
     for (int d = 0; d <= P; ++d) s[d] = h[d] = ff{0.f, 0.f};
     if (ok) {
-      const float4 cc = c[ridx(row, chunk)];
-      const float4 wq = W[ridx(row, chunk)];
+      const float4 cc = c[ridx(row, chunk, ks)];
+      const float4 wq = W[ridx(row, chunk, ks)];
       w = cff{{wq.x, wq.z}, {wq.y, wq.w}};
       u = cff_add(cff{{2.f * cc.x, 2.f * cc.z}, {2.f * cc.y, 2.f * cc.w}}, w);
       chi = make_float2(cc.x, cc.y);
       if (j >= 0) {
 #pragma unroll
         for (int d = 0; d <= P; ++d) {
-          const int idx = bidx<P>(row, d, chunk);
+          const int idx = bidx<P>(row, d, chunk, ks);
           const float4 v = __ldg(A4 + idx);
           const float2 lo = __ldg(HD + idx);
           s[d] = ff{v.x, v.w};
@@ -748,7 +742,7 @@ TDZ_DEV void rhs_mixed(const GeomDev& g, const RunDev& run, const Lane& L, ff ta
     const int jf = j - P;
     if (jf >= 0 && jf < L.m) {
       const cx<float> r = cx<float>{ff_f(acc_get(ar[P])), ff_f(acc_get(ai[P]))};
-      rhs[ridx(jf, L.k)] = r;
+      rhs[ridx(jf, L.k, ks)] = r;
       rr = fmaf(r.r, r.r, fmaf(r.i, r.i, rr));
       if (SCALE) bb = fmaf(sc[P].r, sc[P].r, fmaf(sc[P].i, sc[P].i, bb));
     }
@@ -759,6 +753,7 @@ TDZ_DEV void rhs_mixed(const GeomDev& g, const RunDev& run, const Lane& L, ff ta
 // c^H M c = sum_j M_jj |c_j|^2 + 2 sum_{d>=1} M(j, j-d) Re(conj(c_j) c_{j-d}) for M = S, D, G, K.
 template <int P>
 TDZ_DEV void observe_fp64(const GeomDev& g, const RunDev& run, const Lane& L, double out[4]) {
+  const int ks = L.ks;
   const double2* c = static_cast<const double2*>(run.state);
   double2 cwin[P + 1];
 #pragma unroll
@@ -767,7 +762,7 @@ TDZ_DEV void observe_fp64(const GeomDev& g, const RunDev& run, const Lane& L, do
   for (int j = -P; j < L.m; ++j) {
     int row, chunk;
     const bool ok = locate(L, j, row, chunk);
-    const double2 cj = ok ? c[ridx(row, chunk)] : make_double2(0.0, 0.0);
+    const double2 cj = ok ? c[ridx(row, chunk, ks)] : make_double2(0.0, 0.0);
 #pragma unroll
     for (int d = P; d >= 1; --d) cwin[d] = cwin[d - 1];
     cwin[0] = cj;
@@ -775,7 +770,7 @@ TDZ_DEV void observe_fp64(const GeomDev& g, const RunDev& run, const Lane& L, do
 #pragma unroll
       for (int d = 0; d <= P; ++d) {
         const double u = (d == 0 ? 1.0 : 2.0) * (cj.x * cwin[d].x + cj.y * cwin[d].y);
-        const int idx = bidx<P>(row, d, chunk);
+        const int idx = bidx<P>(row, d, chunk, ks);
         s = fma(static_cast<const double*>(g.S)[idx], u, s);
         dd = fma(static_cast<const double*>(g.D)[idx], u, dd);
         gg = fma(static_cast<const double*>(g.G)[idx], u, gg);
@@ -795,6 +790,7 @@ TDZ_DEV void observe_fp64(const GeomDev& g, const RunDev& run, const Lane& L, do
 // separator) are formed from that lane's c and w before anyone overwrites them.
 template <int P>
 TDZ_DEV void update_observe_mixed(const GeomDev& g, const RunDev& run, const Lane& L, int hist_new, double out[4]) {
+  const int ks = L.ks;
   float4* __restrict__ c = static_cast<float4*>(run.state);
   float4* __restrict__ W = run.W;
   const float4* __restrict__ A4 = static_cast<const float4*>(g.S);
@@ -806,12 +802,12 @@ TDZ_DEV void update_observe_mixed(const GeomDev& g, const RunDev& run, const Lan
   if (L.active && L.up) {
 #pragma unroll
     for (int q = 0; q < P; ++q) {  // row -P+q of chunk k-1 -> cwin[P-1-q] (the loop shifts before use)
-      const int idx = ridx(L.m - P + q, L.k - 1);
+      const int idx = ridx(L.m - P + q, L.k - 1, ks);
       const float4 cq = c[idx], wq = W[idx];
       cwin[P - 1 - q] = cff{ff_add(ff{cq.x, cq.z}, ff{wq.x, wq.z}), ff_add(ff{cq.y, cq.w}, ff{wq.y, wq.w})};
     }
   }
-  __syncwarp();
+  __syncthreads();  // the previous chunk may belong to the other warp of this run: every thread calls this
   ffacc s, dd, gg, kk;
   acc_zero(s);
   acc_zero(dd);
@@ -819,17 +815,17 @@ TDZ_DEV void update_observe_mixed(const GeomDev& g, const RunDev& run, const Lan
   acc_zero(kk);
   if (L.active) {
     for (int j = 0; j < L.m; ++j) {
-      const int idx = ridx(j, L.k);
+      const int idx = ridx(j, L.k, ks);
       if (j + 2 < L.m) {
-        const int i2 = ridx(j + 2, L.k);
+        const int i2 = ridx(j + 2, L.k, ks);
         pf(c + i2);
         pf(W + i2);
         pf(run.d1 + i2);
 #pragma unroll
         for (int d = 0; d <= P; ++d) {
-          pf(A4 + bidx<P>(j + 2, d, L.k));
-          pf(HD + bidx<P>(j + 2, d, L.k));
-          pf(GK + bidx<P>(j + 2, d, L.k));
+          pf(A4 + bidx<P>(j + 2, d, L.k, ks));
+          pf(HD + bidx<P>(j + 2, d, L.k, ks));
+          pf(GK + bidx<P>(j + 2, d, L.k, ks));
         }
       }
       const float4 cq = c[idx], wq = W[idx];
@@ -861,7 +857,7 @@ TDZ_DEV void update_observe_mixed(const GeomDev& g, const RunDev& run, const Lan
         acc_mul(ua, cj.i, cwin[d].i);
         ff u = acc_get(ua);
         if (d > 0) u = ff{2.f * u.h, 2.f * u.l};
-        const int bi = bidx<P>(j, d, L.k);
+        const int bi = bidx<P>(j, d, L.k, ks);
         const float4 v = __ldg(A4 + bi);
         const float2 lo = __ldg(HD + bi);
         const float4 gk = __ldg(GK + bi);
@@ -889,27 +885,40 @@ TDZ_DEV double warp_sum(double v) {
   return v;
 }
 
+// Sums over all lanes of a run (one or two warps), identical in every lane of the run. Called by
+// every thread of the block (it contains block barriers); idle warps pass zeros.
+template <int NV>
+TDZ_DEV void run_sum(double (&v)[NV], double (*sh)[4], int wib, int sub, int nw) {
+#pragma unroll
+  for (int q = 0; q < NV; ++q) v[q] = warp_sum(v[q]);
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int q = 0; q < NV; ++q) sh[wib][q] = v[q];
+  __syncthreads();
+  const int first = wib - sub;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) v[q] = sh[first][q] + (nw == 2 ? sh[first + 1][q] : 0.0);
+  __syncthreads();
+}
+
 // ============================================================================ the kernel
-// One block = `warps per block` runs of neighbouring size (the run order is longest first) that
-// advance in lock step: every warp owns one run, and the block crosses each phase of a step
-// together (block barriers), so all warps of an SM execute the same code region at a time. The
-// adaptive refinement decides collectively how many extra solves the block makes; warps whose
-// run is already converged skip the work of those rounds.
+// The block's warps are slots of a schedule built on the host: a slot holds one run (run * 2 + 0)
+// or one half of a two-warp run (run * 2 + sub), or nothing (-1); the two warps of a run are
+// adjacent in one block. The block advances its runs in lock step: it crosses each phase of a step
+// together (block barriers), so all warps of an SM execute the same code region at a time and the
+// two warps of a run see each other's chunk boundaries and shared reduced system. The adaptive
+// refinement decides collectively how many extra solves the block makes; warps whose run is
+// already converged skip the work of those rounds.
 template <int P, bool MIXED>
 __global__ void __launch_bounds__(256) cn1d_kernel(StepArgs A) {
   using T = typename std::conditional<MIXED, float, double>::type;
   extern __shared__ unsigned char smem_raw[];
   __shared__ int s_base;
+  __shared__ double s_sum[8][4];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int wpb = blockDim.x >> 5;
-  const size_t per_warp = (size_t)(2 * 31 * P * P + 31 * P + P * P) * sizeof(cx<T>);
-  cx<T>* base = reinterpret_cast<cx<T>*>(smem_raw + wib * per_warp);
-  Red<T> red;
-  red.Dg = base;
-  red.E = base + 31 * P * P;
-  red.rb = base + 2 * 31 * P * P;
-  red.Wt = base + 2 * 31 * P * P + 31 * P;
+  const size_t per_warp = (size_t)red_elems(P) * sizeof(cx<T>);
 
   while (true) {
     if (threadIdx.x == 0) s_base = atomicAdd(A.counter, wpb);
@@ -918,18 +927,33 @@ __global__ void __launch_bounds__(256) cn1d_kernel(StepArgs A) {
     const bool done = s_base >= A.nruns;
     __syncthreads();
     if (done) break;
-    const bool has = item < A.nruns;
-    const int rid = has ? A.order[item] : 0;
+    const int slot = item < A.nruns ? A.order[item] : -1;
+    const bool has = slot >= 0;
+    const int rid = has ? slot >> 1 : 0;
+    const int sub = has ? slot & 1 : 0;
     RunDev run = A.runs[rid];
     const GeomDev g = A.geoms[run.geom];
+    const int nw = has ? g.ks / LANES : 1;  // warps of this run
+    // reduced system of the run, in the shared memory of its first warp (and the second's)
+    Red<T> red;
+    {
+      const int cap = 32 * nw - 1;
+      cx<T>* base = reinterpret_cast<cx<T>*>(smem_raw + (wib - sub) * per_warp);
+      red.Dg = base;
+      red.E = base + cap * P * P;
+      red.rb = base + 2 * cap * P * P;
+      red.Wt = base + 2 * cap * P * P + cap * P;
+    }
     Lane L;
-    L.k = lane;
+    L.k = sub * LANES + lane;
     L.K = has ? g.K : 1;
     L.m = g.m;
-    L.active = has && lane < g.K;
-    L.up = L.active && lane >= 1;
-    L.dn = L.active && lane < g.K - 1;
+    L.ks = g.ks;
+    L.active = has && L.k < g.K;
+    L.up = L.active && L.k >= 1;
+    L.dn = L.active && L.k < g.K - 1;
     L.mI = L.dn ? g.m - P : g.m;
+    const bool lead = has && sub == 0;  // solves the reduced system and writes the run's results
     const double* E = A.field + (size_t)rid * (A.nsteps + 1);
     double* obs = A.obs + (size_t)rid * A.nsteps * 5;
     int status = has ? run.status : TDZ_OK;
@@ -953,7 +977,7 @@ __global__ void __launch_bounds__(256) cn1d_kernel(StepArgs A) {
         __syncthreads();
         if (W.up) sweep2<P, double, false>(g, run, W, tau_d, ebar_d, red);
         __syncthreads();
-        if (nsep > 0) {
+        if (lead && nsep > 0) {
           red_factor<P, double>(red, nsep, lane);
           red_solve<P, double>(red, nsep, lane);
         }
@@ -969,14 +993,15 @@ __global__ void __launch_bounds__(256) cn1d_kernel(StepArgs A) {
         // residual of the predictor y0 = c + w, then one factorising FP32 solve
         float rr = 0.f, bb = 0.f;
         if (W.active) rhs_mixed<P, true>(g, run, W, tau_ff, ebar_ff, rr, bb);
-        const double bbs = fmax(warp_sum((double)bb), 1e-300);
-        const double rel0 = sqrt(warp_sum((double)rr) / bbs);
-        __syncthreads();
+        double sums[2] = {(double)rr, (double)bb};
+        run_sum(sums, s_sum, wib, sub, nw);
+        const double bbs = fmax(sums[1], 1e-300);
+        const double rel0 = sqrt(sums[0] / bbs);
         if (W.active) sweep1<P, float, true>(g, run, W, tau_f, ebar_f, red);
         __syncthreads();
         if (W.up) sweep2<P, float, true>(g, run, W, tau_f, ebar_f, red);
         __syncthreads();
-        if (nsep > 0) {
+        if (lead && nsep > 0) {
           red_factor<P, float>(red, nsep, lane);
           red_solve<P, float>(red, nsep, lane);
         }
@@ -986,14 +1011,23 @@ __global__ void __launch_bounds__(256) cn1d_kernel(StepArgs A) {
         nsolve += work;
         // residual after the solve; refine with the stored factors while above tolerance
         if (W.active) rhs_mixed<P, false>(g, run, W, tau_ff, ebar_ff, rr, bb);
-        double rel = sqrt(warp_sum((double)rr) / bbs);
+        double r1[1] = {W.active ? (double)rr : 0.0};
+        run_sum(r1, s_sum, wib, sub, nw);
+        double rel = sqrt(r1[0] / bbs);
         const double rho = fmin(rel / fmax(rel0, 1e-300), 1.0);  // contraction of one FP32 solve
         int it = 1;
         bool ok = !work || rel <= A.tol;
         bool need = !ok && it < A.max_it;
         while (__syncthreads_or(need)) {
+          if (need && W.active) resolve_fwd<P, float, true>(g, run, W, red);
+          __syncthreads();
+          if (need && W.up) resolve_bwd<P, float, true>(g, run, W, tau_f, ebar_f, red);
+          __syncthreads();
+          if (need && lead && nsep > 0) red_solve<P, float>(red, nsep, lane);
+          __syncthreads();
+          if (need && W.active) substitute<P, float, true>(g, run, W, tau_f, ebar_f, red);
+          __syncthreads();
           if (need) {
-            resolve<P, float, true>(g, run, W, tau_f, ebar_f, red, lane);
             nsolve++;
             ++it;
             const double predicted = rho * rel;
@@ -1004,8 +1038,10 @@ __global__ void __launch_bounds__(256) cn1d_kernel(StepArgs A) {
           }
           const bool check = need && !ok;
           if (check && W.active) rhs_mixed<P, false>(g, run, W, tau_ff, ebar_ff, rr, bb);
+          double rc[1] = {(check && W.active) ? (double)rr : 0.0};
+          run_sum(rc, s_sum, wib, sub, nw);
           if (check) {
-            rel = sqrt(warp_sum((double)rr) / bbs);
+            rel = sqrt(rc[0] / bbs);
             ok = rel <= A.tol;
           }
           need = need && !ok && it < A.max_it;
@@ -1018,22 +1054,22 @@ __global__ void __launch_bounds__(256) cn1d_kernel(StepArgs A) {
         __syncthreads();
         update_observe_mixed<P>(g, run, W, hist, o);
       }
-      const double ns = warp_sum(o[0]), ds = warp_sum(o[1]), gs = warp_sum(o[2]), ks = warp_sum(o[3]);
+      run_sum(o, s_sum, wib, sub, nw);
       if (work) {
         const double Et = E[s + 1];
-        if (lane == 0) {
+        if (lead && lane == 0) {
           double* row = obs + s * 5;
           row[0] = (double)(A.step0 + s + 1) * A.dt;
           row[1] = Et;
-          row[2] = ds;
-          row[3] = -gs - Et * ks;
-          row[4] = ns;
+          row[2] = o[1];
+          row[3] = -o[2] - Et * o[3];
+          row[4] = o[0];
         }
-        if (!isfinite(ns) || !isfinite(ds)) status = TDZ_ENONFINITE;
+        if (!isfinite(o[0]) || !isfinite(o[1])) status = TDZ_ENONFINITE;
       }
       __syncthreads();
     }
-    if (has && lane == 0) {
+    if (lead && lane == 0) {
       A.runs[rid].status = status;
       A.runs[rid].hist = hist;
       A.runs[rid].max_rel = fmax(run.max_rel, max_rel);
@@ -1071,7 +1107,117 @@ bool is_device_ptr(const void* p) {
 
 size_t smem_per_warp(int P, bool mixed) {
   const size_t cxsz = mixed ? 8 : 16;
-  return (size_t)(2 * 31 * P * P + 31 * P + P * P) * cxsz;
+  return (size_t)red_elems(P) * cxsz;
+}
+
+}  // namespace
+
+namespace {
+
+// Chunking of a run of n rows over the lanes of `warps` warps: K <= 32 warps chunks of m rows, each
+// interior at least P + 1 rows long (the separator of a chunk is its last P rows).
+struct Chunking {
+  int K, m, ks;
+};
+Chunking chunking(int n, int P, int warps) {
+  int K = std::max(1, std::min(LANES * warps, n / (3 * P)));
+  int m = (n + K - 1) / K;
+  while (K > 1 && m - P < P + 1) {
+    --K;
+    m = (n + K - 1) / K;
+  }
+  return {K, m, LANES * warps};
+}
+
+// Schedule of the persistent launch. A block holds `wpb` warp slots and keeps them until all their
+// runs are done, so its duration is that of its longest run; `resident` blocks run at a time and
+// the next group of slots goes to the first block that finishes. With allow_pairs, runs longer than
+// a threshold get two warps (64 chunks, half the rows per lane); the threshold is chosen by
+// simulating this list schedule (cost of a run per step ~ rows per lane + a small term per
+// separator) and keeping the shortest makespan. (The binary64 kernel is bound by the FP64 pipe, so
+// the extra separator work of a second warp does not pay there; it keeps one warp per run.) Slots are run * 2 + sub (sub = warp of a two-warp run), -1 when empty; the two
+// warps of a run are adjacent in one block. Returns the slots (a multiple of wpb) and, per
+// geometry, the warps per run.
+std::vector<int> schedule_runs(const std::vector<int>& gsize, const int* ops_index, int nruns, int P, int wpb,
+                               int resident, bool allow_pairs, std::vector<int>& gwarps) {
+  const int nops = (int)gsize.size();
+  std::vector<int> cand = {INT32_MAX};
+  if (wpb >= 2 && allow_pairs)
+    for (int gi = 0; gi < nops; ++gi) cand.push_back(gsize[gi]);
+  std::sort(cand.begin(), cand.end());
+  cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+  double best = 1e300;
+  std::vector<int> best_slots;
+  std::vector<int> best_w(nops, 1);
+  std::vector<int> w(nops);
+  std::vector<double> cost(nops);
+  std::vector<int> order(nruns);
+  for (int thr : cand) {
+    for (int gi = 0; gi < nops; ++gi) {
+      w[gi] = (gsize[gi] > thr && wpb >= 2) ? 2 : 1;
+      const Chunking c = chunking(gsize[gi], P, w[gi]);
+      cost[gi] = c.m + 0.05 * c.K;
+    }
+    for (int r = 0; r < nruns; ++r) order[r] = r;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return cost[ops_index[x]] > cost[ops_index[y]]; });
+    // pack into blocks in that order; a two-warp run that does not fit in the current block's
+    // remaining slot is preceded by the next one-warp run (or an empty slot)
+    std::vector<int> slots;
+    std::vector<double> btime;
+    std::vector<char> used(nruns, 0);
+    size_t next = 0;
+    int fill = 0;
+    double bt = 0.0;
+    auto close_block = [&]() {
+      while (fill < wpb) {
+        slots.push_back(-1);
+        ++fill;
+      }
+      btime.push_back(bt);
+      fill = 0;
+      bt = 0.0;
+    };
+    for (;;) {
+      while (next < order.size() && used[order[next]]) ++next;
+      if (next >= order.size()) break;
+      const int r = order[next];
+      const int rw = w[ops_index[r]];
+      if (rw > wpb - fill) {  // fill the last slot with a one-warp run if one is left
+        size_t j = next + 1;
+        while (j < order.size() && (used[order[j]] || w[ops_index[order[j]]] != 1)) ++j;
+        if (j < order.size()) {
+          const int r1 = order[j];
+          used[r1] = 1;
+          slots.push_back(2 * r1);
+          bt = std::max(bt, cost[ops_index[r1]]);
+          ++fill;
+        }
+        close_block();
+        continue;
+      }
+      used[r] = 1;
+      for (int q = 0; q < rw; ++q) slots.push_back(2 * r + q);
+      bt = std::max(bt, cost[ops_index[r]]);
+      fill += rw;
+      if (fill == wpb) close_block();
+    }
+    if (fill > 0) close_block();
+    // list schedule of the blocks over the resident block slots
+    std::vector<double> fin(std::min<size_t>(std::max(1, resident), btime.size()), 0.0);
+    for (size_t q = 0; q < btime.size(); ++q) {
+      auto it = std::min_element(fin.begin(), fin.end());
+      *it += btime[q];
+    }
+    const double mk = fin.empty() ? 0.0 : *std::max_element(fin.begin(), fin.end());
+    if (mk < best * (1.0 - 1e-9)) {
+      best = mk;
+      best_slots = slots;
+      best_w = w;
+    }
+  }
+  gwarps = best_w;
+  return best_slots;
 }
 
 }  // namespace
@@ -1083,7 +1229,7 @@ struct tdz_batch {
   int nruns = 0;
   cudaStream_t stream = nullptr;
   struct G {
-    int n, m, K;
+    int n, m, K, ks;  // size, rows per chunk, chunks, interleave stride (32 x warps per run)
   };
   std::vector<G> geo;
   std::vector<int> run_geom;
@@ -1091,7 +1237,8 @@ struct tdz_batch {
   GeomDev* d_geoms = nullptr;
   RunDev* d_runs = nullptr;
   std::vector<RunDev> h_runs;
-  int* d_order = nullptr;
+  int* d_order = nullptr;  // schedule slots: run * 2 + sub, or -1
+  int nslots = 0;
   int* d_counter = nullptr;
   double* d_obs = nullptr;
   size_t obs_steps = 0;
@@ -1202,20 +1349,28 @@ int tdz_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* 
   const bool mixed = precision == TDZ_MIXED;
   const int P1 = P + 1;
   const size_t Tsz = mixed ? 8 : 16;  // complex element of the solve precision
+  // ---------------------------------------------------------------- launch shape and schedule
+  int dev = 0, sms = 148, maxsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const size_t spw = smem_per_warp(P, mixed);
+  const int wpb = (int)std::min<size_t>(8, std::max<size_t>(1, (size_t)maxsm / spw));
+  const int per_sm = std::max(1, (int)((size_t)228 * 1024 / (spw * wpb + 1024)));
+  std::vector<int> gsize(nops);
+  for (int gi = 0; gi < nops; ++gi) gsize[gi] = (int)ops[gi]->o.n[0];
+  std::vector<int> gwarps;
+  std::vector<int> slots = schedule_runs(gsize, ops_index, nruns, P, wpb, sms * per_sm, mixed, gwarps);
   // ---------------------------------------------------------------- geometries
   std::vector<GeomDev> hg(nops);
   b->geo.resize(nops);
   for (int gi = 0; gi < nops; ++gi) {
     const Ops& o = ops[gi]->o;
     const int n = (int)o.n[0];
-    int K = std::max(1, std::min(32, n / (3 * P)));
-    int m = (n + K - 1) / K;
-    while (K > 1 && m - P < P + 1) {
-      --K;
-      m = (n + K - 1) / K;
-    }
-    b->geo[gi] = {n, m, K};
-    const size_t nb = (size_t)m * P1 * LANES;
+    const Chunking ch = chunking(n, P, gwarps[gi]);
+    const int K = ch.K, m = ch.m, LS = ch.ks;
+    b->geo[gi] = {n, m, K, LS};
+    const size_t nb = (size_t)m * P1 * LS;
     const Band* src[5] = {&o.S, &o.H0, &o.D, &o.G, &o.K};
     // value of matrix q at interleaved position (i, d, k); padding rows are identity in S
     auto val = [&](int q, int i, int d, int k) -> double {
@@ -1236,10 +1391,10 @@ int tdz_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* 
     };
     if (mixed) {
       std::vector<float> a4(nb * 4), hd(nb * 2), gk(nb * 4);
-      for (int k = 0; k < LANES; ++k)
+      for (int k = 0; k < LS; ++k)
         for (int i = 0; i < m; ++i)
           for (int d = 0; d <= P; ++d) {
-            const size_t idx = ((size_t)i * P1 + d) * LANES + k;
+            const size_t idx = ((size_t)i * P1 + d) * LS + k;
             const double S = val(0, i, d, k), H = val(1, i, d, k), D = val(2, i, d, k), Gv = val(3, i, d, k),
                          Kv = val(4, i, d, k);
             a4[4 * idx + 0] = hi(S);
@@ -1264,9 +1419,9 @@ int tdz_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* 
     } else {
       std::vector<double> hd(nb);
       for (int q = 0; q < 5; ++q) {
-        for (int k = 0; k < LANES; ++k)
+        for (int k = 0; k < LS; ++k)
           for (int i = 0; i < m; ++i)
-            for (int d = 0; d <= P; ++d) hd[((size_t)i * P1 + d) * LANES + k] = val(q, i, d, k);
+            for (int d = 0; d <= P; ++d) hd[((size_t)i * P1 + d) * LS + k] = val(q, i, d, k);
         dst[q] = upload(hd.data(), nb * 8);
         if (!dst[q]) {
           delete b;
@@ -1275,14 +1430,14 @@ int tdz_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* 
         }
       }
     }
-    hg[gi] = GeomDev{n, m, K, 0, dst[0], dst[1], dst[2], dst[3], dst[4]};
+    hg[gi] = GeomDev{n, m, K, LS, dst[0], dst[1], dst[2], dst[3], dst[4]};
   }
   // ---------------------------------------------------------------- runs
   b->h_runs.resize(nruns);
   b->run_geom.assign(ops_index, ops_index + nruns);
   for (int r = 0; r < nruns; ++r) {
     const auto& G = b->geo[ops_index[r]];
-    const size_t rows = (size_t)G.m * LANES;
+    const size_t rows = (size_t)G.m * G.ks;
     RunDev R{};
     R.geom = ops_index[r];
     R.status = TDZ_OK;
@@ -1307,35 +1462,23 @@ int tdz_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* 
   }
   b->d_geoms = static_cast<GeomDev*>(b->alloc(sizeof(GeomDev) * nops));
   b->d_runs = static_cast<RunDev*>(b->alloc(sizeof(RunDev) * nruns));
-  b->d_order = static_cast<int*>(b->alloc(sizeof(int) * nruns));
+  b->nslots = (int)slots.size();
+  b->d_order = static_cast<int*>(b->alloc(sizeof(int) * slots.size()));
   b->d_counter = static_cast<int*>(b->alloc(sizeof(int)));
   if (!b->d_geoms || !b->d_runs || !b->d_order || !b->d_counter) {
     delete b;
     return TDZ_ENOMEM;
   }
-  // longest-processing-time order: largest runs first
-  std::vector<int> order(nruns);
-  for (int r = 0; r < nruns; ++r) order[r] = r;
-  std::stable_sort(order.begin(), order.end(),
-                   [&](int x, int y) { return b->geo[ops_index[x]].n > b->geo[ops_index[y]].n; });
   cudaMemcpyAsync(b->d_geoms, hg.data(), sizeof(GeomDev) * nops, cudaMemcpyHostToDevice, b->stream);
   cudaMemcpyAsync(b->d_runs, b->h_runs.data(), sizeof(RunDev) * nruns, cudaMemcpyHostToDevice, b->stream);
-  cudaMemcpyAsync(b->d_order, order.data(), sizeof(int) * nruns, cudaMemcpyHostToDevice, b->stream);
+  cudaMemcpyAsync(b->d_order, slots.data(), sizeof(int) * slots.size(), cudaMemcpyHostToDevice, b->stream);
   cudaError_t e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) {
     delete b;
     return cuda_fail(e, "tdz_batch_create");
   }
-  // launch shape: warps per block limited by shared memory; one warp per run at most
-  int dev = 0, sms = 148, maxsm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  const size_t spw = smem_per_warp(P, mixed);
-  int wpb = (int)std::min<size_t>(8, std::max<size_t>(1, (size_t)maxsm / spw));
   b->warps_per_block = wpb;
-  int per_sm = std::max(1, (int)((size_t)228 * 1024 / (spw * wpb + 1024)));
-  b->blocks = std::max(1, std::min((nruns + wpb - 1) / wpb, sms * per_sm));
+  b->blocks = std::max(1, std::min(b->nslots / wpb, sms * per_sm));
   *out = b;
   return TDZ_OK;
 }
@@ -1360,7 +1503,7 @@ int tdz_set_state(tdz_batch* b, int run, const double* c) {
   if (!b || !c || run < 0 || run >= b->nruns) return TDZ_EINVAL;
   if (b->nd) return tdz::nd_set_state(b->nd, run, c, is_device_ptr(c));
   const auto& G = b->geo[b->run_geom[run]];
-  const int n = G.n, m = G.m;
+  const int n = G.n, m = G.m, LS = G.ks;
   std::vector<double> hc((size_t)2 * n);
   cudaError_t e;
   if (is_device_ptr(c)) {
@@ -1375,12 +1518,12 @@ int tdz_set_state(tdz_batch* b, int run, const double* c) {
       set_error("tdz_set_state: non-finite coefficient");
       return TDZ_ENONFINITE;
     }
-  const size_t rows = (size_t)m * LANES;
+  const size_t rows = (size_t)m * LS;
   RunDev& R = b->h_runs[run];
   if (b->prec == TDZ_MIXED) {
     std::vector<float> s(rows * 4, 0.f);
     for (int g = 0; g < n; ++g) {
-      const size_t idx = (size_t)(g % m) * LANES + g / m;
+      const size_t idx = (size_t)(g % m) * LS + g / m;
       const double re = hc[2 * g], im = hc[2 * g + 1];
       const float rh = (float)re, ih = (float)im;
       s[4 * idx + 0] = rh;
@@ -1395,7 +1538,7 @@ int tdz_set_state(tdz_batch* b, int run, const double* c) {
   } else {
     std::vector<double> s(rows * 2, 0.0);
     for (int g = 0; g < n; ++g) {
-      const size_t idx = (size_t)(g % m) * LANES + g / m;
+      const size_t idx = (size_t)(g % m) * LS + g / m;
       s[2 * idx] = hc[2 * g];
       s[2 * idx + 1] = hc[2 * g + 1];
     }
@@ -1417,8 +1560,8 @@ int tdz_get_state(const tdz_batch* b, int run, double* c) {
   if (!b || !c || run < 0 || run >= b->nruns) return TDZ_EINVAL;
   if (b->nd) return tdz::nd_get_state(b->nd, run, c, is_device_ptr(c));
   const auto& G = b->geo[b->run_geom[run]];
-  const int n = G.n, m = G.m;
-  const size_t rows = (size_t)m * LANES;
+  const int n = G.n, m = G.m, LS = G.ks;
+  const size_t rows = (size_t)m * LS;
   const RunDev& R = b->h_runs[run];
   std::vector<double> hc((size_t)2 * n);
   cudaError_t e;
@@ -1428,7 +1571,7 @@ int tdz_get_state(const tdz_batch* b, int run, double* c) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return cuda_fail(e, "tdz_get_state");
     for (int g = 0; g < n; ++g) {
-      const size_t idx = (size_t)(g % m) * LANES + g / m;
+      const size_t idx = (size_t)(g % m) * LS + g / m;
       hc[2 * g] = (double)s[4 * idx] + (double)s[4 * idx + 2];
       hc[2 * g + 1] = (double)s[4 * idx + 1] + (double)s[4 * idx + 3];
     }
@@ -1438,7 +1581,7 @@ int tdz_get_state(const tdz_batch* b, int run, double* c) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return cuda_fail(e, "tdz_get_state");
     for (int g = 0; g < n; ++g) {
-      const size_t idx = (size_t)(g % m) * LANES + g / m;
+      const size_t idx = (size_t)(g % m) * LS + g / m;
       hc[2 * g] = s[2 * idx];
       hc[2 * g + 1] = s[2 * idx + 1];
     }
@@ -1481,9 +1624,9 @@ int tdz_propagate(tdz_batch* b, const double* field, double dt, int64_t step0, i
   cudaError_t e;
   if (!is_device_ptr(field)) {
     if (b->field_len < need) {
-      if (b->d_field) cudaFree(b->d_field);
+      if (b->d_field) cudaFreeAsync(b->d_field, b->stream);
       b->d_field = nullptr;
-      e = cudaMalloc(&b->d_field, need * sizeof(double));
+      e = cudaMallocAsync(reinterpret_cast<void**>(&b->d_field), need * sizeof(double), b->stream);
       if (e != cudaSuccess) return cuda_fail(e, "tdz_propagate: field buffer");
       b->field_len = need;
     }
@@ -1493,9 +1636,9 @@ int tdz_propagate(tdz_batch* b, const double* field, double dt, int64_t step0, i
   }
   const size_t obs_need = (size_t)b->nruns * nsteps * 5;
   if (b->obs_steps < obs_need) {
-    if (b->d_obs) cudaFree(b->d_obs);
+    if (b->d_obs) cudaFreeAsync(b->d_obs, b->stream);
     b->d_obs = nullptr;
-    e = cudaMalloc(&b->d_obs, obs_need * sizeof(double));
+    e = cudaMallocAsync(reinterpret_cast<void**>(&b->d_obs), obs_need * sizeof(double), b->stream);
     if (e != cudaSuccess) return cuda_fail(e, "tdz_propagate: observable buffer");
     b->obs_steps = obs_need;
   }
@@ -1505,7 +1648,7 @@ int tdz_propagate(tdz_batch* b, const double* field, double dt, int64_t step0, i
   a.geoms = b->d_geoms;
   a.runs = b->d_runs;
   a.order = b->d_order;
-  a.nruns = b->nruns;
+  a.nruns = b->nslots;
   a.counter = b->d_counter;
   a.field = dfield;
   a.obs = b->d_obs;
@@ -1633,7 +1776,7 @@ __global__ void noalloc_pack(double* scr, NoAllocLayout L, const double* bands, 
     RunDev* R = reinterpret_cast<RunDev*>(G + 1);
     int* order = reinterpret_cast<int*>(R + 1);
     const size_t nb = rows * P1;
-    *G = GeomDev{L.n, L.m, L.K, 0, scr + L.band, scr + L.band + nb, scr + L.band + 2 * nb, scr + L.band + 3 * nb,
+    *G = GeomDev{L.n, L.m, L.K, LANES, scr + L.band, scr + L.band + nb, scr + L.band + 2 * nb, scr + L.band + 3 * nb,
                  scr + L.band + 4 * nb};
     RunDev r{};
     r.geom = 0;
