@@ -164,46 +164,96 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
-def nd_leg(tdz, nsteps):
-    """2-D soft-core atom V = -1/sqrt(x^2+y^2+0.5) on [-150,150]^2, 1024 order-7 splines per axis
-    (1.04 M coefficients), 800 nm 1e14 W/cm^2 sin^2 pulse, dt = 0.05: ms/step in both precisions."""
+def _nd_time(tdz, name, ops, run_ops, c0s, fields, dt, nsteps, extra):
+    """Time `nsteps` steps of a 2-D/3-D batch in both precisions after one warm-up step."""
     import torch
-    p, nsp, L = 7, 1024, 150.0
-    t = wl.knots_for_nsplines(-L, L, nsp, p)
-    ops = tdz.Ops([tdz.Basis(t, p, p + 1) for _ in range(2)], wl.softcore_medium(0.5))
-    g = wl.greville(t, p)
-    psi = np.exp(-0.5 * g ** 2)
-    c0 = np.kron(psi, psi).astype(complex)
-    c0 /= np.linalg.norm(c0)
-    dt = 0.05
-    field = wl.sin2_pulse(wl.time_grid(dt, nsteps + 1), wl.e0_from_intensity(1e14), wl.omega_from_nm(800.0), 4.0,
-                          dim=2)
-    res = {"workload": "softcore_atom_2d", "coefficients": ops.n, "steps": nsteps,
-           "operator": "assembled (2p+1)^2 stencil", "preconditioner": "fast diagonalisation (cuBLAS axis GEMMs)"}
+    res = {"workload": name, "runs": len(run_ops), "coefficients": int(sum(ops[g].n for g in run_ops)),
+           "steps": nsteps}
+    res.update(extra)
+    dim = fields.shape[2]
     states = {}
-    for name, prec in (("mixed", tdz.MIXED), ("fp64", tdz.FP64)):
-        b = tdz.Batch([ops], [0], prec)
-        b.set_state(0, c0)
-        b.propagate(np.ascontiguousarray(field[:2].reshape(1, 2, 2)), dt, 0, 1)   # warm-up step
-        b.set_state(0, c0)
+    for label, prec in (("mixed", tdz.MIXED), ("fp64", tdz.FP64)):
+        t0 = time.perf_counter()
+        b = tdz.Batch(ops, run_ops, prec)
+        t_create = time.perf_counter() - t0
+        for i, c in enumerate(c0s):
+            b.set_state(i, c)
+        b.propagate(np.ascontiguousarray(fields[:, :2]), dt, 0, 1)   # warm-up step
+        for i, c in enumerate(c0s):
+            b.set_state(i, c)
+        _, solves0 = b.refine_stats()
+        it0 = b.krylov_stats()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        b.propagate(np.ascontiguousarray(field[:nsteps + 1].reshape(1, nsteps + 1, 2)), dt, 0, nsteps)
+        b.propagate(np.ascontiguousarray(fields[:, :nsteps + 1]), dt, 0, nsteps)
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / nsteps
-        o, st = b.observe(0)
+        drift, st_bad = 0.0, 0
+        for i in range(len(run_ops)):
+            o, st = b.observe(i)
+            drift = max(drift, float(np.max(np.abs(o[:, -1] - o[0, -1]))))
+            st_bad += int(st != 0)
         _, solves = b.refine_stats()
-        res[name] = {"value": ops.n / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "status": st,
-                     "norm_drift": float(np.max(np.abs(o[:, -1] - o[0, -1]))),
-                     "krylov_iterations_per_step": b.krylov_stats() / (nsteps + 1),
-                     "solves_per_step": solves / (nsteps + 1), "device_gb": b.device_bytes / 1e9}
-        states[name] = b.get_state(0)
+        nsteps_runs = nsteps * len(run_ops)
+        res[label] = {"value": res["coefficients"] / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                      "runs_not_ok": st_bad, "norm_drift": drift,
+                      "krylov_iterations_per_run_step": (b.krylov_stats() - it0) / nsteps_runs,
+                      "solves_per_run_step": (solves - solves0) / nsteps_runs, "device_gb": b.device_bytes / 1e9,
+                      "create_s": t_create}
+        states[label] = [b.get_state(i) for i in range(len(run_ops))]
         del b
-    res["mixed_vs_fp64_rel_l2"] = float(np.linalg.norm(states["mixed"] - states["fp64"]) / np.linalg.norm(states["fp64"]))
+    num = sum(np.linalg.norm(x - y) ** 2 for x, y in zip(states["mixed"], states["fp64"]))
+    den = sum(np.linalg.norm(y) ** 2 for y in states["fp64"])
+    res["mixed_vs_fp64_rel_l2"] = float(np.sqrt(num / den))
     res["speedup_mixed"] = res["fp64"]["ms_per_step"] / res["mixed"]["ms_per_step"]
     return res
+
+
+def _gauss_state(knots, p, dim):
+    g = wl.greville(knots, p)
+    psi = np.exp(-0.5 * (g / (0.05 * (g[-1] - g[0]))) ** 2)
+    c = psi
+    for _ in range(dim - 1):
+        c = np.kron(psi, c)
+    return (c / np.linalg.norm(c)).astype(complex)
+
+
+def nd_legs(tdz, nsteps, which):
+    """2-D/3-D workloads beside the 1-D batch:
+    softcore_atom_2d: V = -1/sqrt(r^2+0.5) on [-150,150]^2, 1024 order-7 splines per axis (1.04 M
+      coefficients), 800 nm 1e14 W/cm^2 sin^2 pulse, dt = 0.05;
+    dot_batch_2d: 64 elliptical GaAs dots (16 M coefficients), 10 um, 8 intensities x 8 CEPs, dt = 0.5;
+    softcore_atom_3d: [-100,100]^3, 256 order-6 splines per axis (16.4 M coefficients), elliptical
+      (0.3) 800 nm pulse, dt = 0.05."""
+    out = {}
+    if "2d" in which:
+        p, t = 7, wl.knots_for_nsplines(-150.0, 150.0, 1024, 7)
+        ops = tdz.Ops([tdz.Basis(t, p, p + 1) for _ in range(2)], wl.softcore_medium(0.5))
+        dt = 0.05
+        f = wl.sin2_pulse(wl.time_grid(dt, nsteps + 1), wl.e0_from_intensity(1e14), wl.omega_from_nm(800.0), 4.0,
+                          dim=2)
+        out["config_2d"] = _nd_time(tdz, "softcore_atom_2d", [ops], [0], [_gauss_state(t, p, 2)], f[None], dt, nsteps,
+                                    {"operator": "assembled (2p+1)^2 stencil",
+                                     "preconditioner": "fast diagonalisation (cuBLAS axis GEMMs)"})
+    if "dots" in which:
+        wk = wl.dot_batch(nsteps=nsteps + 1)
+        ops = [tdz.Ops([tdz.Basis(k, r.degree, r.nquad) for k in r.knots], r.medium) for r in wk.runs]
+        c0s = [_gauss_state(r.knots[0], r.degree, 2) for r in wk.runs]
+        fields = np.stack([r.field for r in wk.runs])
+        out["config_dots_2d"] = _nd_time(tdz, "dot_batch_2d", ops, list(range(len(ops))), c0s, fields, wk.dt, nsteps,
+                                         {"operator": "assembled stencil (variable mass + step potential)",
+                                          "preconditioner": "fast diagonalisation, mean 1/m"})
+    if "3d" in which:
+        p, t = 6, wl.knots_for_nsplines(-100.0, 100.0, 256, 6)
+        ops = tdz.Ops([tdz.Basis(t, p, p + 1) for _ in range(3)], wl.softcore_medium(0.5))
+        dt = 0.05
+        f = wl.sin2_pulse(wl.time_grid(dt, nsteps + 1), 0.05, wl.omega_from_nm(800.0), 4.0, ellipticity=0.3, dim=3)
+        out["config_3d"] = _nd_time(tdz, "softcore_atom_3d", [ops], [0], [_gauss_state(t, p, 3)], f[None], dt, nsteps,
+                                    {"operator": "Gauss-point sum factorisation",
+                                     "preconditioner": "fast diagonalisation (cuBLAS axis GEMMs)"})
+    return out
 
 
 # ----------------------------------------------------------------------------- GPU arm
@@ -217,7 +267,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--nd-steps", type=int, default=3)
+    ap.add_argument("--nd-steps", type=int, default=2)
+    ap.add_argument("--nd-legs", default="2d,dots,3d", help="comma list of 2d, dots, 3d (empty: none)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -347,8 +398,8 @@ def main():
             "clocks": clk.summary()}
     # ---------------- 2-D leg: the soft-core atom of the 2-D configuration (1024 x 1024 order-7 splines),
     # a few steps in both precisions (Kronecker + Gauss-point operator, preconditioned COCG)
-    if rank == 0 and args.nd_steps > 0:
-        line["config_2d"] = nd_leg(tdz, args.nd_steps)
+    if rank == 0 and args.nd_steps > 0 and args.nd_legs:
+        line.update(nd_legs(tdz, args.nd_steps, args.nd_legs.split(",")))
     if rank == 0 and not args.no_cpu:
         # bounded oracle sample sized to ~cpu_seconds; GPU mixed path compared on the same sample
         ns_probe = 20

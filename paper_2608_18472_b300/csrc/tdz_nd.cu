@@ -364,28 +364,65 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return v;
 }
 
-// sum_q w f |X_q|^2 for kinds 2 (per axis) and 3, into res[slot]
-template <class T>
-__global__ void k_qreduce(const C<T>* __restrict__ X, QGrid<T> g, MediumDev M, int kind, int axis, double* res) {
+// Gauss-point reductions of the observables, fused along the last axis: for every pencil (a point
+// of the faster axes, already interpolated) and chunk of elements, interpolate psi to the nq
+// points of each element with a sliding window of P+1 coefficients and accumulate
+//   res[a] += w f_a |psi|^2,  f_a = m^-1 dV/dx_a  (a < dim),   res[dim] += w m^-1 |psi|^2 (if kmass),
+// i.e. c^H G_a c and c^H K c of Eq. pdm_acceleration, without forming the full point grid.
+template <int P>
+__global__ void k_fused_last_reduce(const C<double>* __restrict__ in, const double* __restrict__ Bl, int nq, int nL,
+                                    int EL, long long inner, int echunk, QGrid<double> g, MediumDev M, int kmass,
+                                    double* res) {
   __shared__ double sh[32];
-  const long long total = (long long)g.Q[0] * g.Q[1] * (g.dim > 2 ? g.Q[2] : 1);
-  double acc = 0.0;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    long long t = idx;
-    T r[3];
-    T w = 1;
-    for (int a = 0; a < g.dim; ++a) {
+  const int nchunks = (EL + echunk - 1) / echunk;
+  const long long total = inner * nchunks;
+  const int L = g.dim - 1;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x; tid < total;
+       tid += (long long)gridDim.x * blockDim.x) {
+    const long long i = tid % inner;
+    const int ch = (int)(tid / inner);
+    const int e0 = ch * echunk, e1 = min(EL, e0 + echunk);
+    double r[3];
+    double wp = 1;
+    long long t = i;
+    for (int a = 0; a < L; ++a) {
       const int q = (int)(t % g.Q[a]);
       t /= g.Q[a];
       r[a] = g.x[a][q];
-      w *= g.w[a][q];
+      wp *= g.w[a][q];
     }
-    const C<T> v = X[idx];
-    acc += (double)(w * medium_f<T>(M, kind, axis, r, g.dim)) * ((double)v.r * v.r + (double)v.i * v.i);
+    C<double> win[P + 1];  // win[k] = coefficient e + k - 1 of the current element
+#pragma unroll
+    for (int k = 0; k <= P; ++k) {
+      const int j = e0 + k - 1;
+      win[k] = (j >= 0 && j < nL) ? in[(long long)j * inner + i] : czero<double>();
+    }
+    for (int e = e0; e < e1; ++e) {
+      for (int qq = 0; qq < nq; ++qq) {
+        const int q = e * nq + qq;
+        const double* bq = Bl + (size_t)q * (P + 1);
+        double pr = 0, pi = 0;
+#pragma unroll
+        for (int k = 0; k <= P; ++k) {
+          pr += bq[k] * win[k].r;
+          pi += bq[k] * win[k].i;
+        }
+        r[L] = g.x[L][q];
+        const double wq = wp * g.w[L][q] * (pr * pr + pi * pi);
+        for (int a = 0; a < g.dim; ++a) acc[a] += wq * medium_f<double>(M, 2, a, r, g.dim);
+        if (kmass) acc[3] += wq * medium_f<double>(M, 3, 0, r, g.dim);
+      }
+#pragma unroll
+      for (int k = 0; k < P; ++k) win[k] = win[k + 1];
+      const int jn = e + P;
+      win[P] = (jn >= 0 && jn < nL && e + 1 < e1) ? in[(long long)jn * inner + i] : czero<double>();
+    }
   }
-  acc = block_sum(acc, sh);
-  if (threadIdx.x == 0) atomicAdd(res, acc);
+  for (int a = 0; a < 4; ++a) {
+    const double v = block_sum(acc[a], sh);
+    if (threadIdx.x == 0) atomicAdd(res + a, v);
+  }
 }
 
 // res[0] += Re sum conj(a) b ; res[1] += Im   (Hermitian product, for observables)
@@ -521,78 +558,112 @@ __global__ void k_line_solve(C<T>* __restrict__ v, const C<T>* __restrict__ Lc, 
 // term 1/2 <d_a B| m^-1 |d_a B>, Sec. "Parallel assembly") couples DoF (ix, iy) only with
 // (ix + dx, iy + dy), |dx|, |dy| <= P. It is assembled once, exactly as the Gauss-point quadrature
 // defines it, by sum factorisation:
-//   stage 1: F1[qy][ix][dx] = sum_{qx} w_x (fV B_ix B_jx + fK dB_ix dB_jx)(x_qx, y_qy),
-//            F2[qy][ix][dx] = sum_{qx} w_x  fK B_ix B_jx                   (variable mass only)
+//   table:   fV(x_qx, y_qy) = V, fK = 1/2 m^-1 at every Gauss point
+//   stage 1: F1[qy][dx][ix] = sum_{qx} w_x (fV B_ix B_jx + fK dB_ix dB_jx),
+//            F2[qy][dx][ix] = sum_{qx} w_x  fK B_ix B_jx                   (variable mass only)
 //   stage 2: W[(dy, dx)][iy nx + ix] = sum_{qy} w_y (B_iy B_jy F1 + dB_iy dB_jy F2),
-// with fV = V, fK = 1/2 m^-1, jx = ix + dx, jy = iy + dy. Layout [offset][row] so that a warp reads
-// one offset of 32 consecutive rows in one transaction.
-template <int P>
-__global__ void k_w_stage1(AxisDev ax, AxisDev ay, MediumDev M, int varmass, double* __restrict__ F1,
-                           double* __restrict__ F2) {
-  constexpr int W = 2 * P + 1;
-  const long long total = (long long)ay.Q * ax.n * W;
+// with jx = ix + dx, jy = iy + dy. Layout [offset][row] so that a warp reads one offset of 32
+// consecutive rows in one transaction.
+__global__ void k_w_ftab(AxisDev ax, AxisDev ay, MediumDev M, int varmass, double* __restrict__ fV,
+                         double* __restrict__ fK) {
+  const long long total = (long long)ax.Q * ay.Q;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
-    const int dxi = (int)(idx % W);
-    const long long t = idx / W;
-    const int ix = (int)(t % ax.n);
-    const int qy = (int)(t / ax.n);
-    const int jx = ix + dxi - P;
-    double s1 = 0.0, s2 = 0.0;
-    if (jx >= 0 && jx < ax.n) {
-      const int e0 = max(0, max(ix, jx) + 1 - P), e1 = min(ax.E - 1, min(ix, jx) + 1);
-      double r[2];
-      r[1] = ay.x[qy];
-      for (int e = e0; e <= e1; ++e) {
-        const int ri = ix + 1 - e, rj = jx + 1 - e;
-        for (int qq = 0; qq < ax.nq; ++qq) {
-          const int q = e * ax.nq + qq;
-          r[0] = ax.x[q];
-          const double bb = ax.B[(size_t)q * (P + 1) + ri] * ax.B[(size_t)q * (P + 1) + rj];
-          double v = medium_f<double>(M, 0, 0, r, 2) * bb;
-          if (varmass) {
-            const double fk = medium_f<double>(M, 1, 0, r, 2);
-            v += fk * ax.dB[(size_t)q * (P + 1) + ri] * ax.dB[(size_t)q * (P + 1) + rj];
-            s2 += ax.w[q] * fk * bb;
-          }
-          s1 += ax.w[q] * v;
-        }
-      }
-    }
-    F1[idx] = s1;
-    if (varmass) F2[idx] = s2;
+    double r[2];
+    r[0] = ax.x[idx % ax.Q];
+    r[1] = ay.x[idx / ax.Q];
+    fV[idx] = medium_f<double>(M, 0, 0, r, 2);
+    if (varmass) fK[idx] = medium_f<double>(M, 1, 0, r, 2);
   }
 }
 
+// one thread per (qy, ix): the 2P+1 offsets dx from the elements of ix (local index ri) and their
+// functions jx = e + rj - 1
+template <int P>
+__global__ void k_w_stage1(AxisDev ax, AxisDev ay, int varmass, const double* __restrict__ fV,
+                           const double* __restrict__ fK, double* __restrict__ F1, double* __restrict__ F2) {
+  constexpr int W = 2 * P + 1;
+  const long long total = (long long)ay.Q * ax.n;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int ix = (int)(idx % ax.n);
+    const int qy = (int)(idx / ax.n);
+    double s1[W], s2[W];
+#pragma unroll
+    for (int t = 0; t < W; ++t) s1[t] = s2[t] = 0.0;
+    const int e0 = max(0, ix + 1 - P), e1 = min(ax.E - 1, ix + 1);
+    for (int e = e0; e <= e1; ++e) {
+      const int ri = ix + 1 - e;
+      for (int qq = 0; qq < ax.nq; ++qq) {
+        const int q = e * ax.nq + qq;
+        const double* Bq = ax.B + (size_t)q * (P + 1);
+        const double* dBq = ax.dB + (size_t)q * (P + 1);
+        const double wv = ax.w[q] * fV[(size_t)qy * ax.Q + q];
+        const double wk = varmass ? ax.w[q] * fK[(size_t)qy * ax.Q + q] : 0.0;
+        const double bi = Bq[ri], dbi = dBq[ri];
+#pragma unroll
+        for (int rj = 0; rj <= P; ++rj) {
+          const int dxi = e + rj - 1 - ix + P;  // in [0, 2P] since both functions live on element e
+          const double bb = bi * Bq[rj];
+          s1[dxi] += wv * bb + (varmass ? wk * dbi * dBq[rj] : 0.0);
+          if (varmass) s2[dxi] += wk * bb;
+        }
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < W; ++t) {
+      const int jx = ix + t - P;
+      const bool in = jx >= 0 && jx < ax.n;  // Dirichlet-trimmed functions do not couple
+      const size_t o = ((size_t)qy * W + t) * ax.n + ix;
+      F1[o] = in ? s1[t] : 0.0;
+      if (varmass) F2[o] = in ? s2[t] : 0.0;
+    }
+  }
+}
+
+// one thread per (iy, dx, ix): the 2P+1 offsets dy
 template <int P>
 __global__ void k_w_stage2(AxisDev ax, AxisDev ay, int varmass, const double* __restrict__ F1,
                            const double* __restrict__ F2, double* __restrict__ W64, float* __restrict__ W32) {
   constexpr int W = 2 * P + 1;
   const long long N = (long long)ax.n * ay.n;
-  const long long total = N * W * W;
+  const long long total = N * W;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
-    const long long row = idx % N;
-    const int off = (int)(idx / N);
-    const int dyi = off / W, dxi = off % W;
-    const int ix = (int)(row % ax.n), iy = (int)(row / ax.n);
-    const int jy = iy + dyi - P, jx = ix + dxi - P;
-    double s = 0.0;
-    if (jy >= 0 && jy < ay.n && jx >= 0 && jx < ax.n) {
-      const int e0 = max(0, max(iy, jy) + 1 - P), e1 = min(ay.E - 1, min(iy, jy) + 1);
-      for (int e = e0; e <= e1; ++e) {
-        const int ri = iy + 1 - e, rj = jy + 1 - e;
-        for (int qq = 0; qq < ay.nq; ++qq) {
-          const int q = e * ay.nq + qq;
-          const size_t f = ((size_t)q * ax.n + ix) * W + dxi;
-          double v = ay.B[(size_t)q * (P + 1) + ri] * ay.B[(size_t)q * (P + 1) + rj] * F1[f];
-          if (varmass) v += ay.dB[(size_t)q * (P + 1) + ri] * ay.dB[(size_t)q * (P + 1) + rj] * F2[f];
-          s += ay.w[q] * v;
+    const int ix = (int)(idx % ax.n);
+    const long long t = idx / ax.n;
+    const int dxi = (int)(t % W);
+    const int iy = (int)(t / W);
+    double s[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) s[k] = 0.0;
+    const int e0 = max(0, iy + 1 - P), e1 = min(ay.E - 1, iy + 1);
+    for (int e = e0; e <= e1; ++e) {
+      const int ri = iy + 1 - e;
+      for (int qq = 0; qq < ay.nq; ++qq) {
+        const int q = e * ay.nq + qq;
+        const double* Bq = ay.B + (size_t)q * (P + 1);
+        const double* dBq = ay.dB + (size_t)q * (P + 1);
+        const size_t f = ((size_t)q * W + dxi) * ax.n + ix;
+        const double a1 = ay.w[q] * Bq[ri] * F1[f];
+        const double a2 = varmass ? ay.w[q] * dBq[ri] * F2[f] : 0.0;
+#pragma unroll
+        for (int rj = 0; rj <= P; ++rj) {
+          const int dyi = e + rj - 1 - iy + P;
+          s[dyi] += a1 * Bq[rj] + (varmass ? a2 * dBq[rj] : 0.0);
         }
       }
     }
-    W64[idx] = s;
-    W32[idx] = (float)s;
+    const long long row = (long long)iy * ax.n + ix;
+    const int jx = ix + dxi - P;
+#pragma unroll
+    for (int dyi = 0; dyi < W; ++dyi) {
+      const int jy = iy + dyi - P;
+      const bool in = jx >= 0 && jx < ax.n && jy >= 0 && jy < ay.n;
+      const size_t o = (size_t)(dyi * W + dxi) * N + row;
+      W64[o] = in ? s[dyi] : 0.0;
+      W32[o] = in ? (float)s[dyi] : 0.0f;
+    }
   }
 }
 
@@ -845,45 +916,6 @@ struct Apply {
     }
   }
 
-  // interpolate x to the Gauss grid (derivative on axis `dax`, or none if dax < 0); result in qa
-  C<T>* to_points(const C<T>* x, int dax) {
-    const int D = r->dim;
-    int len[3] = {r->n[0], r->n[1], r->n[2]};
-    const C<T>* in = x;
-    C<T>* out = nullptr;
-    for (int ax = 0; ax < D; ++ax) {
-      long long outer, inner;
-      shape(ax, len, outer, inner);
-      const AxisDev& A = r->ax[ax];
-      out = (ax % 2 == 0) ? qa : qb;
-      const long long tot = outer * A.Q * inner;
-      k_interp<T, P><<<grid_for(tot), TPB, 0, b->st>>>(tab<T>(A, ax == dax ? TDB : TB), A.nq, A.n, A.Q, in, out, outer,
-                                                        inner);
-      len[ax] = A.Q;
-      in = out;
-    }
-    return out;
-  }
-
-  // project a Gauss-grid array back to coefficients, adding into y
-  void from_points(C<T>* X, int dax, C<T>* y) {
-    const int D = r->dim;
-    int len[3] = {r->Q[0], r->Q[1], r->Q[2]};
-    C<T>* in = X;
-    for (int ax = D - 1; ax >= 0; --ax) {
-      long long outer, inner;
-      shape(ax, len, outer, inner);
-      const AxisDev& A = r->ax[ax];
-      const bool last = ax == 0;
-      C<T>* out = last ? y : ((in == qa) ? qb : qa);
-      const long long tot = outer * A.n * inner;
-      k_project<T, P><<<grid_for(tot), TPB, 0, b->st>>>(tab<T>(A, ax == dax ? TDB : TB), A.nq, A.n, A.E, in, out,
-                                                         outer, inner, last ? 1 : 0);
-      len[ax] = A.n;
-      in = out;
-    }
-  }
-
   QGrid<T> grid() const {
     QGrid<T> g{};
     g.dim = r->dim;
@@ -893,6 +925,26 @@ struct Apply {
       g.w[a] = tab<T>(r->ax[a], TW);
     }
     return g;
+  }
+
+  // interpolate x along the faster axes 0..dim-2 (derivative on axis dax if dax < dim - 1); returns the
+  // result (shape [n_last][Q_0..Q_{dim-2}]) in qa or qb
+  const C<T>* to_pencils(const C<T>* x, int dax) {
+    const int D = r->dim, L = D - 1;
+    int len[3] = {r->n[0], r->n[1], r->n[2]};
+    const C<T>* in = x;
+    for (int ax = 0; ax < L; ++ax) {
+      long long outer, inner;
+      shape(ax, len, outer, inner);
+      const AxisDev& A = r->ax[ax];
+      C<T>* X = (ax % 2 == 0) ? qa : qb;
+      const long long tot = outer * A.Q * inner;
+      k_interp<T, P><<<grid_for(tot), TPB, 0, b->st>>>(tab<T>(A, ax == dax ? TDB : TB), A.nq, A.n, A.Q, in, X, outer,
+                                                        inner);
+      len[ax] = A.Q;
+      in = X;
+    }
+    return in;
   }
 
   // y += coef * (Gauss-point operator of kind `kind`) x, derivative on axis dax (or none if dax < 0):
@@ -1124,23 +1176,23 @@ void observe(NdBatch* b, NdRun* r, Apply<double, P>& op, const double* Et, doubl
     k_hdot<double><<<grid_for(N), TPB, 0, b->st>>>(c, y, N, b->d_red);
     dvals[a] = red_get(b, 2, h)[0];
   }
+  // c^H G_a c and (variable mass) c^H K c at the Gauss points, fused along the last axis
   const QGrid<double> g = op.grid();
-  C<double>* X = op.to_points(c, -1);
-  double kq;
-  if (r->const_mass) {
-    kq = r->cm * norm;
-  } else {
-    red_zero(b, 1);
-    k_qreduce<double><<<grid_for((long long)g.Q[0] * g.Q[1] * (g.dim > 2 ? g.Q[2] : 1)), TPB, 0, b->st>>>(X, g, r->med, 3,
-                                                                                                        0, b->d_red);
-    kq = red_get(b, 1, h)[0];
-  }
-  for (int a = 0; a < r->dim; ++a) {
-    red_zero(b, 1);
-    k_qreduce<double><<<grid_for((long long)g.Q[0] * g.Q[1] * (g.dim > 2 ? g.Q[2] : 1)), TPB, 0, b->st>>>(X, g, r->med, 2,
-                                                                                                        a, b->d_red);
-    gvals[a] = red_get(b, 1, h)[0];
-  }
+  const C<double>* X = op.to_pencils(c, -1);
+  const int L = r->dim - 1;
+  long long inner = 1;
+  for (int a = 0; a < L; ++a) inner *= r->Q[a];
+  const AxisDev& AL = r->ax[L];
+  long long nch = std::max<long long>(1, std::min<long long>(AL.E / (2 * P + 2), (150000 + inner - 1) / inner));
+  const int echunk = (int)((AL.E + nch - 1) / nch);
+  nch = (AL.E + echunk - 1) / echunk;
+  red_zero(b, 4);
+  k_fused_last_reduce<P><<<grid_for(inner * nch), TPB, 0, b->st>>>(X, AL.B, AL.nq, AL.n, AL.E, inner, echunk, g, r->med,
+                                                                   r->const_mass ? 0 : 1, b->d_red);
+  double q4[4];
+  red_get(b, 4, q4);
+  const double kq = r->const_mass ? r->cm * norm : q4[3];
+  for (int a = 0; a < r->dim; ++a) gvals[a] = q4[a];
   const int D = r->dim;
   for (int a = 0; a < D; ++a) {
     out[a] = dvals[a];
@@ -1321,21 +1373,30 @@ int stencil_setup_p(NdBatch* b, NdGeo& G, const AxisDev& ax, const AxisDev& ay, 
   constexpr int W = 2 * P + 1;
   const long long N = (long long)ax.n * ay.n;
   const size_t nf = (size_t)ay.Q * ax.n * W;
+  const size_t nt = (size_t)ax.Q * ay.Q;
   G.W64 = static_cast<double*>(b->alloc(sizeof(double) * N * W * W));
   G.W32 = static_cast<float*>(b->alloc(sizeof(float) * N * W * W));
   if (!G.W64 || !G.W32) return TDZ_ENOMEM;
-  double *F1 = nullptr, *F2 = nullptr;
-  if (cudaMalloc(&F1, sizeof(double) * nf) != cudaSuccess ||
-      (varmass && cudaMalloc(&F2, sizeof(double) * nf) != cudaSuccess)) {
+  double *F1 = nullptr, *F2 = nullptr, *fV = nullptr, *fK = nullptr;
+  if (cudaMalloc(&F1, sizeof(double) * nf) != cudaSuccess || cudaMalloc(&fV, sizeof(double) * nt) != cudaSuccess ||
+      (varmass && (cudaMalloc(&F2, sizeof(double) * nf) != cudaSuccess ||
+                   cudaMalloc(&fK, sizeof(double) * nt) != cudaSuccess))) {
     cudaFree(F1);
+    cudaFree(F2);
+    cudaFree(fV);
+    cudaFree(fK);
     set_error("tdz_batch_create: no device memory for the 2-D stencil assembly");
     return TDZ_ENOMEM;
   }
-  k_w_stage1<P><<<grid_for((long long)nf), TPB, 0, b->st>>>(ax, ay, M, varmass ? 1 : 0, F1, F2);
-  k_w_stage2<P><<<grid_for(N * W * W), TPB, 0, b->st>>>(ax, ay, varmass ? 1 : 0, F1, F2, G.W64, G.W32);
+  const int vm = varmass ? 1 : 0;
+  k_w_ftab<<<grid_for((long long)nt), TPB, 0, b->st>>>(ax, ay, M, vm, fV, fK);
+  k_w_stage1<P><<<grid_for((long long)ay.Q * ax.n), TPB, 0, b->st>>>(ax, ay, vm, fV, fK, F1, F2);
+  k_w_stage2<P><<<grid_for(N * W), TPB, 0, b->st>>>(ax, ay, vm, F1, F2, G.W64, G.W32);
   cudaError_t e = cudaStreamSynchronize(b->st);
   cudaFree(F1);
   cudaFree(F2);
+  cudaFree(fV);
+  cudaFree(fK);
   if (e != cudaSuccess) return nd_cuda_fail(e, "tdz_batch_create (2-D stencil)");
   return TDZ_OK;
 }
@@ -1464,9 +1525,14 @@ int nd_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* o
       return TDZ_ENOMEM;
     }
     maxN = std::max(maxN, (size_t)R.N);
-    // the largest intermediate of a Gauss-point pass: product of max(n, Q) over axes
-    size_t mq = 1;
-    for (int a = 0; a < dim; ++a) mq *= (size_t)std::max(R.n[a], R.Q[a]);
+    // the largest intermediate of a Gauss-point pass: axes 0..k at the points, the others at the
+    // coefficients (k <= dim - 2; the last axis is always fused), or the state itself
+    size_t mq = (size_t)R.N;
+    for (int k = 0; k + 1 < dim; ++k) {
+      size_t part = 1;
+      for (int a = 0; a < dim; ++a) part *= (size_t)(a <= k ? R.Q[a] : R.n[a]);
+      mq = std::max(mq, part);
+    }
     maxQ = std::max(maxQ, mq);
     (void)NQ;
   }

@@ -241,6 +241,49 @@ def dqw_batch(n_geometries: int = 256, fields_per_geometry: int = 4, p: int = 6,
                      "omega": omega, "T": T, "wb_nm": wbs.tolist(), "nsplines": ns.tolist()})
 
 
+@dataclass
+class RunND:
+    knots: List[np.ndarray]    # per axis
+    degree: int
+    nquad: int
+    medium: Dict
+    field: np.ndarray          # (nsteps+1, dim)
+    dt: float
+
+
+def dot_batch(n_dots: int = 64, p: int = 6, nsplines_range=(256, 768), semi_axes_nm=(5.0, 20.0),
+              margin_nm: float = 20.0, lam_nm: float = 10000.0, ncycles: float = 4.0, dt: float = 0.5,
+              nsteps: Optional[int] = None, gammas: Optional[Sequence[float]] = None, n_cep: int = 8,
+              seed: int = SEED) -> Workload:
+    """Batch of 2-D elliptical quantum dots (position-dependent mass 0.067/0.092, 0.24 eV step):
+    N/axis ~ U{nsplines_range}, semi-axes ~ U[semi_axes_nm], square domain of half-width
+    max(a, b) + margin; run k is driven by intensity k // n_cep (Keldysh gamma, log-spaced 2.3 .. 0.5)
+    and carrier-envelope phase 2 pi (k % n_cep) / n_cep, 10 um, sin^2, polarised along x."""
+    rng = np.random.default_rng(seed)
+    omega = omega_from_nm(lam_nm)
+    T = ncycles * 2 * math.pi / omega
+    if nsteps is None:
+        nsteps = int(math.ceil(T / dt - 1e-9))
+    t = time_grid(dt, nsteps)
+    n_int = max(1, n_dots // n_cep)
+    if gammas is None:
+        gammas = np.geomspace(2.3, 0.5, n_int)
+    ab = rng.uniform(semi_axes_nm[0], semi_axes_nm[1], size=(n_dots, 2))
+    ns = rng.integers(nsplines_range[0], nsplines_range[1] + 1, size=n_dots)
+    runs: List[RunND] = []
+    for k in range(n_dots):
+        a, b = float(ab[k, 0]), float(ab[k, 1])
+        half = (max(a, b) + margin_nm) * NM
+        kn = knots_for_nsplines(-half, half, int(ns[k]), p)
+        e0 = keldysh_e0(float(gammas[(k // n_cep) % len(gammas)]), omega)
+        cep = 2 * math.pi * (k % n_cep) / n_cep
+        runs.append(RunND([kn, kn], p, p + 1, ellipse_dot_medium(a, b), sin2_pulse(t, e0, omega, ncycles, cep=cep,
+                                                                                     dim=2), dt))
+    return Workload("dot_batch_2d", runs, nsteps, dt,
+                    {"n_dots": n_dots, "p": p, "omega": omega, "T": T, "semi_axes_nm": ab.tolist(),
+                     "nsplines": ns.tolist()})
+
+
 def driven_ho_1d(e0: float = 0.1, dt: float = 0.01, t_end: float = 10.0, L: float = 20.0,
                  nsplines: int = 200, p: int = 5) -> Workload:
     """1-D analogue of Appendix A: HO (omega=1) driven by E0 sin t."""
