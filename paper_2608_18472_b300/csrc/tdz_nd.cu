@@ -53,6 +53,8 @@ struct AxisDev {
   const double* D;
   // FP32 copies for the single-precision inner solver (no binary64 loads or conversions there)
   const float *fB, *fdB, *fx, *fw, *fS, *fT1, *fD;
+  // low parts of B, x, w (value - (double)(float)value): with fB, fx, fw the double-float tables
+  const float *lB, *lx, *lw;
 };
 template <class T> __host__ __device__ inline const T* tab(const AxisDev& A, int which);
 template <> __host__ __device__ inline const double* tab<double>(const AxisDev& A, int which) {
@@ -364,63 +366,127 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return v;
 }
 
-// Gauss-point reductions of the observables, fused along the last axis: for every pencil (a point
-// of the faster axes, already interpolated) and chunk of elements, interpolate psi to the nq
-// points of each element with a sliding window of P+1 coefficients and accumulate
-//   res[a] += w f_a |psi|^2,  f_a = m^-1 dV/dx_a  (a < dim),   res[dim] += w m^-1 |psi|^2 (if kmass),
-// i.e. c^H G_a c and c^H K c of Eq. pdm_acceleration, without forming the full point grid.
+// Medium constants as double-float numbers (prepared on the host once per launch).
+struct MediumFF {
+  int mass_kind, pot_kind;
+  ff m0;                 // 1/m, constant mass
+  ff ia, ib, min_, mout; // mass ellipse: 1/a, 1/b, 1/m_in, 1/m_out
+  ff z, eps;             // soft core -z / sqrt(r^2 + eps)
+  ff w2[3];              // harmonic oscillator w_a^2
+};
+
+TDZ_DEV ff ff_sq(ff a) { return ff_mul(a, a); }
+// q^(-1/2) for q > 0: FP32 seed refined by one Newton step y + y (1 - q y^2) / 2 with the residual
+// in double-float (the seed's ~2^-23 relative error becomes ~2^-46)
+TDZ_DEV ff ff_rsqrt(ff q) {
+  const float y = rsqrtf(q.h);
+  const float p = y * y;
+  const ff y2 = ff{p, fmaf(y, y, -p)};
+  const ff e = ff_sub(ff{1.0f, 0.0f}, ff_mul(q, y2));
+  return ff_add(ff{y, 0.0f}, ff_mulf(e, 0.5f * y));
+}
+
+// g[a] = m^-1 dV/dx_a (a < dim) and m^-1 at a Gauss point r, in double-float
+TDZ_DEV void medium_grad_ff(const MediumFF& M, const ff* r, int dim, ff* g, ff& minv) {
+  minv = M.m0;
+  if (M.mass_kind == TDZ_MASS_ELLIPSE) {
+    const ff u = ff_mul(r[0], M.ia), v = dim > 1 ? ff_mul(r[1], M.ib) : ff{0.f, 0.f};
+    const ff t = ff_add(ff_sq(u), ff_sq(v));
+    const bool inside = t.h < 1.0f || (t.h == 1.0f && t.l < 0.0f);
+    minv = inside ? M.min_ : M.mout;
+  }
+  for (int a = 0; a < dim; ++a) g[a] = ff{0.f, 0.f};
+  if (M.pot_kind == TDZ_POT_SOFTCORE) {
+    ff q = M.eps;
+    for (int a = 0; a < dim; ++a) q = ff_add(q, ff_sq(r[a]));
+    const ff s = ff_rsqrt(q);
+    const ff c = ff_mul(ff_mul(M.z, minv), ff_mul(s, ff_sq(s)));  // z m^-1 q^(-3/2)
+    for (int a = 0; a < dim; ++a) g[a] = ff_mul(c, r[a]);
+  } else if (M.pot_kind == TDZ_POT_HO) {
+    for (int a = 0; a < dim; ++a) g[a] = ff_mul(ff_mul(M.w2[a], r[a]), minv);
+  }
+}
+
+// Observable reductions at the Gauss points in double-float, fused along the last axis: for every
+// pencil (a point of the faster axes, already interpolated) and chunk of elements, psi is
+// interpolated to the nq points of each element with a sliding window of P+1 coefficients and
+//   res[a] += sum w m^-1 dV/dx_a |psi|^2 (a < dim),  res[3] += sum w m^-1 |psi|^2 (if kmass)
+// are accumulated, i.e. c^H G_a c and c^H K c of Eq. pdm_acceleration, without forming the full
+// point grid and without binary64 arithmetic per point:
+//   res[a] += sum w m^-1 dV/dx_a |psi|^2 (a < dim),  res[3] += sum w m^-1 |psi|^2 (if kmass).
+// `in` holds psi interpolated along the faster axes (binary64, shape [nL][inner]).
 template <int P>
-__global__ void k_fused_last_reduce(const C<double>* __restrict__ in, const double* __restrict__ Bl, int nq, int nL,
-                                    int EL, long long inner, int echunk, QGrid<double> g, MediumDev M, int kmass,
-                                    double* res) {
+__global__ void k_fused_last_reduce_ff(const C<double>* __restrict__ in, AxisDev A0, AxisDev A1, AxisDev AL, int dim,
+                                       long long inner, int echunk, MediumFF M, int kmass, double* res) {
   __shared__ double sh[32];
+  const int nL = AL.n, EL = AL.E, nq = AL.nq;
   const int nchunks = (EL + echunk - 1) / echunk;
   const long long total = inner * nchunks;
-  const int L = g.dim - 1;
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  const int L = dim - 1;
+  ffacc acc[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) acc_zero(acc[a]);
   for (long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x; tid < total;
        tid += (long long)gridDim.x * blockDim.x) {
     const long long i = tid % inner;
     const int ch = (int)(tid / inner);
     const int e0 = ch * echunk, e1 = min(EL, e0 + echunk);
-    double r[3];
-    double wp = 1;
-    long long t = i;
-    for (int a = 0; a < L; ++a) {
-      const int q = (int)(t % g.Q[a]);
-      t /= g.Q[a];
-      r[a] = g.x[a][q];
-      wp *= g.w[a][q];
+    ff r[3];
+    ff wp = ff{1.f, 0.f};
+    {
+      long long t = i;
+      const AxisDev* F[2] = {&A0, &A1};
+      for (int a = 0; a < L; ++a) {
+        const AxisDev& A = *F[a];
+        const int q = (int)(t % A.Q);
+        t /= A.Q;
+        r[a] = ff{A.fx[q], A.lx[q]};
+        wp = ff_mul(wp, ff{A.fw[q], A.lw[q]});
+      }
     }
-    C<double> win[P + 1];  // win[k] = coefficient e + k - 1 of the current element
+    cff win[P + 1];  // coefficient e + k - 1 of the current element
 #pragma unroll
     for (int k = 0; k <= P; ++k) {
       const int j = e0 + k - 1;
-      win[k] = (j >= 0 && j < nL) ? in[(long long)j * inner + i] : czero<double>();
+      const C<double> v = (j >= 0 && j < nL) ? in[(long long)j * inner + i] : czero<double>();
+      win[k] = cff{ff{(float)v.r, (float)(v.r - (double)(float)v.r)}, ff{(float)v.i, (float)(v.i - (double)(float)v.i)}};
     }
     for (int e = e0; e < e1; ++e) {
       for (int qq = 0; qq < nq; ++qq) {
         const int q = e * nq + qq;
-        const double* bq = Bl + (size_t)q * (P + 1);
-        double pr = 0, pi = 0;
+        const float* bh = AL.fB + (size_t)q * (P + 1);
+        const float* bl = AL.lB + (size_t)q * (P + 1);
+        ffacc pr, pi;
+        acc_zero(pr);
+        acc_zero(pi);
 #pragma unroll
         for (int k = 0; k <= P; ++k) {
-          pr += bq[k] * win[k].r;
-          pi += bq[k] * win[k].i;
+          const ff bk = ff{bh[k], bl[k]};
+          acc_mul(pr, bk, win[k].r);
+          acc_mul(pi, bk, win[k].i);
         }
-        r[L] = g.x[L][q];
-        const double wq = wp * g.w[L][q] * (pr * pr + pi * pi);
-        for (int a = 0; a < g.dim; ++a) acc[a] += wq * medium_f<double>(M, 2, a, r, g.dim);
-        if (kmass) acc[3] += wq * medium_f<double>(M, 3, 0, r, g.dim);
+        const ff psr = acc_get(pr), psi = acc_get(pi);
+        ffacc m2;
+        acc_zero(m2);
+        acc_mul(m2, psr, psr);
+        acc_mul(m2, psi, psi);
+        r[L] = ff{AL.fx[q], AL.lx[q]};
+        const ff wq = ff_mul(ff_mul(wp, ff{AL.fw[q], AL.lw[q]}), acc_get(m2));
+        ff g[3], minv;
+        medium_grad_ff(M, r, dim, g, minv);
+        for (int a = 0; a < dim; ++a) acc_mul(acc[a], wq, g[a]);
+        if (kmass) acc_mul(acc[3], wq, minv);
       }
 #pragma unroll
       for (int k = 0; k < P; ++k) win[k] = win[k + 1];
       const int jn = e + P;
-      win[P] = (jn >= 0 && jn < nL && e + 1 < e1) ? in[(long long)jn * inner + i] : czero<double>();
+      const C<double> v = (jn >= 0 && jn < nL && e + 1 < e1) ? in[(long long)jn * inner + i] : czero<double>();
+      win[P] = cff{ff{(float)v.r, (float)(v.r - (double)(float)v.r)}, ff{(float)v.i, (float)(v.i - (double)(float)v.i)}};
     }
   }
   for (int a = 0; a < 4; ++a) {
-    const double v = block_sum(acc[a], sh);
+    const ff t = acc_get(acc[a]);
+    const double v = block_sum((double)t.h + (double)t.l, sh);
     if (threadIdx.x == 0) atomicAdd(res + a, v);
   }
 }
@@ -1157,6 +1223,27 @@ int factor_precond(NdBatch* b, NdRun* r, const tdz::Ops& o, double tau) {
   return TDZ_OK;
 }
 
+inline ff ff_of(double v) {
+  const float h = (float)v;
+  return ff{h, (float)(v - (double)h)};
+}
+MediumFF medium_ff(const MediumDev& d) {
+  MediumFF m{};
+  m.mass_kind = d.mass_kind;
+  m.pot_kind = d.pot_kind;
+  m.m0 = ff_of(1.0 / d.mp[0]);
+  if (d.mass_kind == TDZ_MASS_ELLIPSE) {
+    m.ia = ff_of(1.0 / d.mp[0]);
+    m.ib = ff_of(1.0 / d.mp[1]);
+    m.min_ = ff_of(1.0 / d.mp[2]);
+    m.mout = ff_of(1.0 / d.mp[3]);
+  }
+  m.z = ff_of(d.vp[0]);
+  m.eps = ff_of(d.vp[1]);
+  for (int a = 0; a < 3; ++a) m.w2[a] = ff_of(d.vp[a] * d.vp[a]);
+  return m;
+}
+
 // observables of the binary64 state: [d_a, a_a, norm]
 template <int P>
 void observe(NdBatch* b, NdRun* r, Apply<double, P>& op, const double* Et, double* out) {
@@ -1177,7 +1264,6 @@ void observe(NdBatch* b, NdRun* r, Apply<double, P>& op, const double* Et, doubl
     dvals[a] = red_get(b, 2, h)[0];
   }
   // c^H G_a c and (variable mass) c^H K c at the Gauss points, fused along the last axis
-  const QGrid<double> g = op.grid();
   const C<double>* X = op.to_pencils(c, -1);
   const int L = r->dim - 1;
   long long inner = 1;
@@ -1187,8 +1273,9 @@ void observe(NdBatch* b, NdRun* r, Apply<double, P>& op, const double* Et, doubl
   const int echunk = (int)((AL.E + nch - 1) / nch);
   nch = (AL.E + echunk - 1) / echunk;
   red_zero(b, 4);
-  k_fused_last_reduce<P><<<grid_for(inner * nch), TPB, 0, b->st>>>(X, AL.B, AL.nq, AL.n, AL.E, inner, echunk, g, r->med,
-                                                                   r->const_mass ? 0 : 1, b->d_red);
+  k_fused_last_reduce_ff<P><<<grid_for(inner * nch), TPB, 0, b->st>>>(X, r->ax[0], r->ax[1], AL, r->dim, inner, echunk,
+                                                                      medium_ff(r->med), r->const_mass ? 0 : 1,
+                                                                      b->d_red);
   double q4[4];
   red_get(b, 4, q4);
   const double kq = r->const_mass ? r->cm * norm : q4[3];
@@ -1481,8 +1568,16 @@ int nd_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* o
       A.fS = upf(o.Sa[a].a);
       A.fT1 = upf(o.T1a[a].a);
       A.fD = upf(o.Da[a].a);
+      auto upl = [&](const std::vector<double>& v) -> float* {
+        std::vector<double> lo(v.size());
+        for (size_t k = 0; k < v.size(); ++k) lo[k] = v[k] - (double)(float)v[k];
+        return upf(lo);
+      };
+      A.lB = upl(B.val);
+      A.lx = upl(B.xq);
+      A.lw = upl(B.wq);
       if (!A.B || !A.dB || !A.x || !A.w || !A.S || !A.T1 || !A.D || !A.fB || !A.fdB || !A.fx || !A.fw || !A.fS ||
-          !A.fT1 || !A.fD) {
+          !A.fT1 || !A.fD || !A.lB || !A.lx || !A.lw) {
         delete b;
         return TDZ_ENOMEM;
       }
