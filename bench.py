@@ -37,6 +37,10 @@ sys.path.insert(0, ROOT)
 import workloads as wl  # noqa: E402
 
 CPU_MAX_STEPS = 2000
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per coefficient-step of the mixed 1-D
+# kernel, from one ncu capture of this kernel version on the DQW batch (2.880 GB over 3 steps of
+# 1.873 M coefficients); the traffic of a timed launch is this times its coefficient-steps.
+NCU_DRAM_BYTES_PER_COEFF_STEP = 513.0
 METRIC = "TDSE coefficient-updates/s: batched mixed vs plain FP64 at stated HHG/norm error"
 UNIT = "coefficient-updates/s"
 
@@ -387,8 +391,12 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "gpu_launches": 1,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
-                         "frac": achieved / peak_fp32, "traffic": None,
-                         "note": "algorithmic flops per coefficient-step x coefficients / event time; peak = 148 SM x 128 FP32 FMA x 2 x 2.032 GHz"},
+                         "frac": achieved / peak_fp32,
+                         "traffic": NCU_DRAM_BYTES_PER_COEFF_STEP * dof * args.steps,
+                         "note": ("achieved: algorithmic flops per coefficient-step x coefficient-steps of the timed "
+                                  "launch / its event time; peak: 148 SM x 128 FP32 lanes x 2 flop x 2.032 GHz (unit "
+                                  "counts and max clock); traffic: DRAM bytes of the timed launch (ncu bytes per "
+                                  "coefficient-step x coefficient-steps)")},
             "plain_fp64": {"value": value64, "unit": UNIT, "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps,
                            "speedup_mixed": value / world / value64},
             "accuracy": {"norm_drift_max": drift, "refine_max_rel_residual": max_rel,
