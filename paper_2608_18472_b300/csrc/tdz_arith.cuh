@@ -111,4 +111,48 @@ struct cff {
 TDZ_DEV cff cff_add(cff a, cff b) { return {ff_add(a.r, b.r), ff_add(a.i, b.i)}; }
 TDZ_DEV cff cff_addc(cff a, cx<float> b) { return {ff_addf(a.r, b.r), ff_addf(a.i, b.i)}; }
 
+// ---------------------------------------------------------------------------- fx
+// Double-float number with arithmetic operators, so that templated kernels written for float and
+// double also instantiate in double-float (48-bit significand on the FP32 pipe). Conversions from
+// double round to the nearest pair; in device code they cost binary64 operations, so kernels
+// receive their constants already converted.
+struct fx {
+  float h, l;
+  fx() = default;
+  __host__ __device__ constexpr fx(float a, float b) : h(a), l(b) {}
+  __host__ __device__ fx(int v) : h((float)v), l(0.f) {}
+  __host__ __device__ fx(double v) : h((float)v), l((float)(v - (double)(float)v)) {}
+  __host__ __device__ explicit operator double() const { return (double)h + (double)l; }
+  __host__ __device__ explicit operator float() const { return h + l; }
+};
+TDZ_DEV fx to_fx(ff a) { return fx(a.h, a.l); }
+TDZ_DEV ff to_ff(fx a) { return ff{a.h, a.l}; }
+TDZ_DEV fx operator+(fx a, fx b) { return to_fx(ff_add(to_ff(a), to_ff(b))); }
+TDZ_DEV fx operator-(fx a, fx b) { return to_fx(ff_add(to_ff(a), ff{-b.h, -b.l})); }
+TDZ_DEV fx operator-(fx a) { return fx(-a.h, -a.l); }
+TDZ_DEV fx operator*(fx a, fx b) { return to_fx(ff_mul(to_ff(a), to_ff(b))); }
+TDZ_DEV fx& operator+=(fx& a, fx b) { return a = a + b; }
+TDZ_DEV fx& operator-=(fx& a, fx b) { return a = a - b; }
+TDZ_DEV fx& operator*=(fx& a, fx b) { return a = a * b; }
+// a / b: FP32 quotient corrected once with the double-float remainder a - q b
+TDZ_DEV fx operator/(fx a, fx b) {
+  const float q0 = a.h / b.h;
+  const ff r = ff_add(to_ff(a), ff_neg(ff_mulf(to_ff(b), q0)));
+  const float q1 = r.h / b.h;
+  return to_fx(fast_two_sum(q0, q1));
+}
+TDZ_DEV bool operator<(fx a, fx b) { return a.h < b.h || (a.h == b.h && a.l < b.l); }
+// square root for templated kernels (float, double, fx)
+TDZ_DEV float tsqrt(float a) { return sqrtf(a); }
+TDZ_DEV double tsqrt(double a) { return ::sqrt(a); }
+// sqrt(a), a >= 0: FP32 root s refined once with the double-float remainder a - s^2
+TDZ_DEV fx tsqrt(fx a) {
+  if (!(a.h > 0.f)) return fx(0.f, 0.f);
+  const float s = sqrtf(a.h);
+  const float p = s * s;
+  const ff s2 = ff{p, fmaf(s, s, -p)};
+  const ff r = ff_add(to_ff(a), ff_neg(s2));
+  return to_fx(fast_two_sum(s, r.h / (2.f * s)));
+}
+
 }  // namespace tdz

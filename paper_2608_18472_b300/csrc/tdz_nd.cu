@@ -55,10 +55,15 @@ struct AxisDev {
   const float *fB, *fdB, *fx, *fw, *fS, *fT1, *fD;
   // low parts of B, x, w (value - (double)(float)value): with fB, fx, fw the double-float tables
   const float *lB, *lx, *lw;
+  // double-float copies of every table (the binary64-class residual of the mixed path)
+  const tdz::fx *xB, *xdB, *xx, *xw, *xS, *xT1, *xD;
 };
 template <class T> __host__ __device__ inline const T* tab(const AxisDev& A, int which);
 template <> __host__ __device__ inline const double* tab<double>(const AxisDev& A, int which) {
   switch (which) { case 0: return A.B; case 1: return A.dB; case 2: return A.x; case 3: return A.w; case 4: return A.S; case 5: return A.T1; default: return A.D; }
+}
+template <> __host__ __device__ inline const tdz::fx* tab<tdz::fx>(const AxisDev& A, int which) {
+  switch (which) { case 0: return A.xB; case 1: return A.xdB; case 2: return A.xx; case 3: return A.xw; case 4: return A.xS; case 5: return A.xT1; default: return A.xD; }
 }
 template <> __host__ __device__ inline const float* tab<float>(const AxisDev& A, int which) {
   switch (which) { case 0: return A.fB; case 1: return A.fdB; case 2: return A.fx; case 3: return A.fw; case 4: return A.fS; case 5: return A.fT1; default: return A.fD; }
@@ -70,31 +75,56 @@ struct MediumDev {
   double mp[4], vp[4];
 };
 
+// Medium parameters in the arithmetic type T of a kernel (converted on the host), so that no
+// binary64 conversion happens per point in double-float kernels.
+template <class T>
+struct MediumT {
+  int mass_kind, pot_kind;
+  T mp[4], vp[4];
+  T inv_m0, inv_min, inv_mout;  // 1/mp[0], 1/mp[2], 1/mp[3]
+  T w2[3];                      // vp[a]^2 (harmonic oscillator)
+};
+template <class T>
+MediumT<T> medium_t(const MediumDev& d) {
+  MediumT<T> m{};
+  m.mass_kind = d.mass_kind;
+  m.pot_kind = d.pot_kind;
+  for (int k = 0; k < 4; ++k) {
+    m.mp[k] = (T)d.mp[k];
+    m.vp[k] = (T)d.vp[k];
+  }
+  m.inv_m0 = (T)(1.0 / d.mp[0]);
+  m.inv_min = (T)(d.mp[2] != 0.0 ? 1.0 / d.mp[2] : 0.0);
+  m.inv_mout = (T)(d.mp[3] != 0.0 ? 1.0 / d.mp[3] : 0.0);
+  for (int a = 0; a < 3; ++a) m.w2[a] = (T)(d.vp[a] * d.vp[a]);
+  return m;
+}
+
 // f(r) at a Gauss point. kind: 0 = V, 1 = 1/2 m^-1 (kinetic weight), 2 = m^-1 dV/dx_axis, 3 = m^-1
 template <class T>
-__device__ __forceinline__ T medium_f(const MediumDev& M, int kind, int axis, const T* r, int dim) {
+__device__ __forceinline__ T medium_f(const MediumT<T>& M, int kind, int axis, const T* r, int dim) {
   T minv = 1;
   if (M.mass_kind == TDZ_MASS_CONST) {
-    minv = (T)(1.0 / M.mp[0]);
+    minv = M.inv_m0;
   } else if (M.mass_kind == TDZ_MASS_ELLIPSE) {
-    const T u = r[0] / (T)M.mp[0], v = dim > 1 ? r[1] / (T)M.mp[1] : (T)0;
-    minv = (u * u + v * v < (T)1) ? (T)(1.0 / M.mp[2]) : (T)(1.0 / M.mp[3]);
+    const T u = r[0] / M.mp[0], v = dim > 1 ? r[1] / M.mp[1] : (T)0;
+    minv = (u * u + v * v < (T)1) ? M.inv_min : M.inv_mout;
   }
-  if (kind == 1) return (T)0.5 * minv;
+  if (kind == 1) return (T)0.5f * minv;
   if (kind == 3) return minv;
   T r2 = 0;
   for (int a = 0; a < dim; ++a) r2 += r[a] * r[a];
   if (kind == 0) {
     switch (M.pot_kind) {
-      case TDZ_POT_SOFTCORE: return -(T)M.vp[0] / sqrt(r2 + (T)M.vp[1]);
+      case TDZ_POT_SOFTCORE: return -M.vp[0] / tsqrt(r2 + M.vp[1]);
       case TDZ_POT_HO: {
         T s = 0;
-        for (int a = 0; a < dim; ++a) s += (T)(M.vp[a] * M.vp[a]) * r[a] * r[a];
-        return (T)0.5 * s;
+        for (int a = 0; a < dim; ++a) s += M.w2[a] * r[a] * r[a];
+        return (T)0.5f * s;
       }
       case TDZ_POT_ELLIPSE: {
-        const T u = r[0] / (T)M.vp[0], v = dim > 1 ? r[1] / (T)M.vp[1] : (T)0;
-        return (u * u + v * v < (T)1) ? (T)M.vp[2] : (T)M.vp[3];
+        const T u = r[0] / M.vp[0], v = dim > 1 ? r[1] / M.vp[1] : (T)0;
+        return (u * u + v * v < (T)1) ? M.vp[2] : M.vp[3];
       }
       default: return 0;
     }
@@ -102,10 +132,10 @@ __device__ __forceinline__ T medium_f(const MediumDev& M, int kind, int axis, co
   // kind 2: m^-1 dV/dx_axis
   switch (M.pot_kind) {
     case TDZ_POT_SOFTCORE: {
-      const T q = r2 + (T)M.vp[1];
-      return minv * (T)M.vp[0] * r[axis] / (q * sqrt(q));
+      const T q = r2 + M.vp[1];
+      return minv * M.vp[0] * r[axis] / (q * tsqrt(q));
     }
-    case TDZ_POT_HO: return minv * (T)(M.vp[axis] * M.vp[axis]) * r[axis];
+    case TDZ_POT_HO: return minv * M.w2[axis] * r[axis];
     default: return 0;
   }
 }
@@ -115,15 +145,16 @@ using C = cx<T>;
 
 // ------------------------------------------------------------------------------- axis band terms
 // out[o][j][i] (+)= sum_t coef_t * sum_d R_t(j, j+d) in_{sel_t}[o][j+d][i]   (R_t real symmetric bands)
+template <class T>
 struct BandTerms {
   int nt;
   const void* R[4];
-  double cr[4], ci[4];
+  T cr[4], ci[4];
   int sel[4];
 };
 
 template <class T, int P>
-__global__ void k_axis_band(BandTerms bt, const C<T>* __restrict__ in0, const C<T>* __restrict__ in1,
+__global__ void k_axis_band(BandTerms<T> bt, const C<T>* __restrict__ in0, const C<T>* __restrict__ in1,
                             C<T>* __restrict__ out, long long outer, int L, long long inner, int accumulate) {
   const long long total = outer * L * inner;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
@@ -147,7 +178,7 @@ __global__ void k_axis_band(BandTerms bt, const C<T>* __restrict__ in0, const C<
         sr += m * v.r;
         si += m * v.i;
       }
-      const T cr = (T)bt.cr[t], ci = (T)bt.ci[t];
+      const T cr = bt.cr[t], ci = bt.ci[t];
       ar += cr * sr - ci * si;
       ai += cr * si + ci * sr;
     }
@@ -229,39 +260,19 @@ struct QGrid {
   const T* w[3];
 };
 
-// X[q] *= (cr + i ci) w(q) f(r_q)
-template <class T>
-__global__ void k_qmult(C<T>* __restrict__ X, QGrid<T> g, MediumDev M, int kind, int axis, double cr, double ci) {
-  const long long total = (long long)g.Q[0] * g.Q[1] * (g.dim > 2 ? g.Q[2] : 1);
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    long long t = idx;
-    T r[3];
-    T w = 1;
-    for (int a = 0; a < g.dim; ++a) {
-      const int q = (int)(t % g.Q[a]);
-      t /= g.Q[a];
-      r[a] = g.x[a][q];
-      w *= g.w[a][q];
-    }
-    const T f = w * medium_f<T>(M, kind, axis, r, g.dim);
-    const T fr = f * (T)cr, fi = f * (T)ci;
-    const C<T> v = X[idx];
-    X[idx] = C<T>{fr * v.r - fi * v.i, fr * v.i + fi * v.r};
-  }
-}
-
-
 // ------------------------------------------------------------------------------- fused last axis
 // Along the last (slowest) axis L: for every pencil (one point of the faster axes, already
 // interpolated) and chunk of elements, walk the elements with a sliding window of P+1
 // coefficients: interpolate to the nq points (table Bl), multiply by coef * w(q) * f(r_q), and
-// project back with the same table, accumulating into out (shape [n_L][inner]). Coefficients
-// touched by two chunks are accumulated atomically, the others by their single owner.
+// project back with the same table, accumulating into out (shape [n_L][inner], zero on entry).
+// A coefficient completed inside a chunk's element loop is written by that chunk alone; the last
+// P partial sums of every chunk but the last (shared with the next chunk) go to `side`
+// ([chunk][P][inner]) and k_fused_fixup adds them, so no atomics are needed and the sum order is
+// fixed.
 template <class T, int P>
-__global__ void k_fused_last(const C<T>* __restrict__ in, C<T>* __restrict__ out, const T* __restrict__ Bl, int nq,
-                             int nL, int EL, long long inner, int echunk, QGrid<T> g, MediumDev M, int kind, int axis,
-                             double cr, double ci) {
+__global__ void k_fused_last(const C<T>* __restrict__ in, C<T>* __restrict__ out, C<T>* __restrict__ side,
+                             const T* __restrict__ Bl, int nq, int nL, int EL, long long inner, int echunk, QGrid<T> g,
+                             MediumT<T> M, int kind, int axis, double cr, double ci) {
   const int nchunks = (EL + echunk - 1) / echunk;
   const long long total = inner * nchunks;
   const int L = g.dim - 1;
@@ -314,13 +325,8 @@ __global__ void k_fused_last(const C<T>* __restrict__ in, C<T>* __restrict__ out
         const int j = e - 1;
         if (j >= 0 && j < nL) {
           C<T>* o = out + (long long)j * inner + i;
-          if (e - e0 < P && e0 > 0) {
-            atomicAdd(&o->r, acc[0].r);
-            atomicAdd(&o->i, acc[0].i);
-          } else {
-            const C<T> v = *o;
-            *o = C<T>{v.r + acc[0].r, v.i + acc[0].i};
-          }
+          const C<T> v = *o;
+          *o = C<T>{v.r + acc[0].r, v.i + acc[0].i};
         }
       }
 #pragma unroll
@@ -336,16 +342,33 @@ __global__ void k_fused_last(const C<T>* __restrict__ in, C<T>* __restrict__ out
 #pragma unroll
     for (int k = 0; k < P; ++k) {
       const int j = e1 - 1 + k;
-      if (j >= 0 && j < nL) {
+      if (e1 < EL) {
+        side[((long long)ch * P + k) * inner + i] = acc[k];
+      } else if (j >= 0 && j < nL) {
         C<T>* o = out + (long long)j * inner + i;
-        if (e1 < EL || (e1 - e0 < P + 1 - k && e0 > 0)) {
-          atomicAdd(&o->r, acc[k].r);
-          atomicAdd(&o->i, acc[k].i);
-        } else {
-          const C<T> v = *o;
-          *o = C<T>{v.r + acc[k].r, v.i + acc[k].i};
-        }
+        const C<T> v = *o;
+        *o = C<T>{v.r + acc[k].r, v.i + acc[k].i};
       }
+    }
+  }
+}
+
+// out[e1(c) - 1 + k] += side[c][k] for every chunk c but the last (after k_fused_last)
+template <class T, int P>
+__global__ void k_fused_fixup(C<T>* __restrict__ out, const C<T>* __restrict__ side, int nL, long long inner,
+                              int echunk, int nchunks) {
+  const long long total = (long long)(nchunks - 1) * P * inner;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long i = idx % inner;
+    const long long t = idx / inner;
+    const int k = (int)(t % P);
+    const int c = (int)(t / P);
+    const int j = (c + 1) * echunk - 1 + k;
+    if (j < nL) {
+      C<T>* o = out + (long long)j * inner + i;
+      const C<T> v = *o, a = side[idx];
+      *o = C<T>{v.r + a.r, v.i + a.i};
     }
   }
 }
@@ -415,8 +438,13 @@ TDZ_DEV void medium_grad_ff(const MediumFF& M, const ff* r, int dim, ff* g, ff& 
 // point grid and without binary64 arithmetic per point:
 //   res[a] += sum w m^-1 dV/dx_a |psi|^2 (a < dim),  res[3] += sum w m^-1 |psi|^2 (if kmass).
 // `in` holds psi interpolated along the faster axes (binary64, shape [nL][inner]).
-template <int P>
-__global__ void k_fused_last_reduce_ff(const C<double>* __restrict__ in, AxisDev A0, AxisDev A1, AxisDev AL, int dim,
+TDZ_DEV cff to_cff(const C<double>& v) {
+  return cff{ff{(float)v.r, (float)(v.r - (double)(float)v.r)}, ff{(float)v.i, (float)(v.i - (double)(float)v.i)}};
+}
+TDZ_DEV cff to_cff(const C<fx>& v) { return cff{to_ff(v.r), to_ff(v.i)}; }
+
+template <int P, class T>
+__global__ void k_fused_last_reduce_ff(const C<T>* __restrict__ in, AxisDev A0, AxisDev A1, AxisDev AL, int dim,
                                        long long inner, int echunk, MediumFF M, int kmass, double* res) {
   __shared__ double sh[32];
   const int nL = AL.n, EL = AL.E, nq = AL.nq;
@@ -448,8 +476,7 @@ __global__ void k_fused_last_reduce_ff(const C<double>* __restrict__ in, AxisDev
 #pragma unroll
     for (int k = 0; k <= P; ++k) {
       const int j = e0 + k - 1;
-      const C<double> v = (j >= 0 && j < nL) ? in[(long long)j * inner + i] : czero<double>();
-      win[k] = cff{ff{(float)v.r, (float)(v.r - (double)(float)v.r)}, ff{(float)v.i, (float)(v.i - (double)(float)v.i)}};
+      win[k] = (j >= 0 && j < nL) ? to_cff(in[(long long)j * inner + i]) : cff{{0.f, 0.f}, {0.f, 0.f}};
     }
     for (int e = e0; e < e1; ++e) {
       for (int qq = 0; qq < nq; ++qq) {
@@ -480,8 +507,7 @@ __global__ void k_fused_last_reduce_ff(const C<double>* __restrict__ in, AxisDev
 #pragma unroll
       for (int k = 0; k < P; ++k) win[k] = win[k + 1];
       const int jn = e + P;
-      const C<double> v = (jn >= 0 && jn < nL && e + 1 < e1) ? in[(long long)jn * inner + i] : czero<double>();
-      win[P] = cff{ff{(float)v.r, (float)(v.r - (double)(float)v.r)}, ff{(float)v.i, (float)(v.i - (double)(float)v.i)}};
+      win[P] = (jn >= 0 && jn < nL && e + 1 < e1) ? to_cff(in[(long long)jn * inner + i]) : cff{{0.f, 0.f}, {0.f, 0.f}};
     }
   }
   for (int a = 0; a < 4; ++a) {
@@ -498,8 +524,8 @@ __global__ void k_hdot(const C<T>* __restrict__ a, const C<T>* __restrict__ b, l
   double re = 0.0, im = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const C<T> x = a[i], y = b[i];
-    re += (double)x.r * y.r + (double)x.i * y.i;
-    im += (double)x.r * y.i - (double)x.i * y.r;
+    re += (double)x.r * (double)y.r + (double)x.i * (double)y.i;
+    im += (double)x.r * (double)y.i - (double)x.i * (double)y.r;
   }
   re = block_sum(re, sh);
   im = block_sum(im, sh);
@@ -516,8 +542,8 @@ __global__ void k_bdot(const C<T>* __restrict__ a, const C<T>* __restrict__ b, l
   double re = 0.0, im = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const C<T> x = a[i], y = b[i];
-    re += (double)x.r * y.r - (double)x.i * y.i;
-    im += (double)x.r * y.i + (double)x.i * y.r;
+    re += (double)x.r * (double)y.r - (double)x.i * (double)y.i;
+    im += (double)x.r * (double)y.i + (double)x.i * (double)y.r;
   }
   re = block_sum(re, sh);
   im = block_sum(im, sh);
@@ -543,7 +569,7 @@ __global__ void k_cocg_update(C<T>* __restrict__ x, C<T>* __restrict__ r, const 
     rv.i -= a_r * qv.i + a_i * qv.r;
     x[i] = xv;
     r[i] = rv;
-    acc += (double)rv.r * rv.r + (double)rv.i * rv.i;
+    acc += (double)rv.r * (double)rv.r + (double)rv.i * (double)rv.i;
   }
   acc = block_sum(acc, sh);
   if (threadIdx.x == 0) atomicAdd(res, acc);
@@ -564,6 +590,10 @@ template <class Tx, class Ty>
 __global__ void k_axby(const C<Tx>* __restrict__ x, C<Ty>* __restrict__ y, long long n, double a, double b) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const C<Tx> xv = x[i];
+    if (b == 0.0) {  // y is output only
+      y[i] = C<Ty>{(Ty)(a * (double)xv.r), (Ty)(a * (double)xv.i)};
+      continue;
+    }
     const C<Ty> yv = y[i];
     y[i] = C<Ty>{(Ty)(a * (double)xv.r + b * (double)yv.r), (Ty)(a * (double)xv.i + b * (double)yv.i)};
   }
@@ -575,7 +605,7 @@ __global__ void k_nrm(const C<T>* __restrict__ a, long long n, double* res) {
   double acc = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const C<T> x = a[i];
-    acc += (double)x.r * x.r + (double)x.i * x.i;
+    acc += (double)x.r * (double)x.r + (double)x.i * (double)x.i;
   }
   acc = block_sum(acc, sh);
   if (threadIdx.x == 0) atomicAdd(res, acc);
@@ -630,7 +660,7 @@ __global__ void k_line_solve(C<T>* __restrict__ v, const C<T>* __restrict__ Lc, 
 //   stage 2: W[(dy, dx)][iy nx + ix] = sum_{qy} w_y (B_iy B_jy F1 + dB_iy dB_jy F2),
 // with jx = ix + dx, jy = iy + dy. Layout [offset][row] so that a warp reads one offset of 32
 // consecutive rows in one transaction.
-__global__ void k_w_ftab(AxisDev ax, AxisDev ay, MediumDev M, int varmass, double* __restrict__ fV,
+__global__ void k_w_ftab(AxisDev ax, AxisDev ay, MediumT<double> M, int varmass, double* __restrict__ fV,
                          double* __restrict__ fK) {
   const long long total = (long long)ax.Q * ay.Q;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
@@ -690,7 +720,8 @@ __global__ void k_w_stage1(AxisDev ax, AxisDev ay, int varmass, const double* __
 // one thread per (iy, dx, ix): the 2P+1 offsets dy
 template <int P>
 __global__ void k_w_stage2(AxisDev ax, AxisDev ay, int varmass, const double* __restrict__ F1,
-                           const double* __restrict__ F2, double* __restrict__ W64, float* __restrict__ W32) {
+                           const double* __restrict__ F2, double* __restrict__ W64, float* __restrict__ W32,
+                           fx* __restrict__ Wx) {
   constexpr int W = 2 * P + 1;
   const long long N = (long long)ax.n * ay.n;
   const long long total = N * W;
@@ -727,8 +758,10 @@ __global__ void k_w_stage2(AxisDev ax, AxisDev ay, int varmass, const double* __
       const int jy = iy + dyi - P;
       const bool in = jx >= 0 && jx < ax.n && jy >= 0 && jy < ay.n;
       const size_t o = (size_t)(dyi * W + dxi) * N + row;
-      W64[o] = in ? s[dyi] : 0.0;
-      W32[o] = in ? (float)s[dyi] : 0.0f;
+      const double v = in ? s[dyi] : 0.0;
+      if (W64) W64[o] = v;
+      if (W32) W32[o] = (float)v;
+      if (Wx) Wx[o] = fx(v);
     }
   }
 }
@@ -736,7 +769,7 @@ __global__ void k_w_stage2(AxisDev ax, AxisDev ay, int varmass, const double* __
 // y += i tau W x  (W real symmetric stencil, layout [(dy + P)(2P + 1) + dx + P][row])
 template <class T, int P>
 __global__ void k_wapply(const T* __restrict__ Wm, const C<T>* __restrict__ x, C<T>* __restrict__ y, int nx, int ny,
-                         double tau) {
+                         T tau) {
   constexpr int W = 2 * P + 1;
   const long long N = (long long)nx * ny;
   for (long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x; row < N;
@@ -758,9 +791,8 @@ __global__ void k_wapply(const T* __restrict__ Wm, const C<T>* __restrict__ x, C
         si += w * v.i;
       }
     }
-    const T t = (T)tau;
     const C<T> o = y[row];
-    y[row] = C<T>{o.r - t * si, o.i + t * sr};
+    y[row] = C<T>{o.r - tau * si, o.i + tau * sr};
   }
 }
 
@@ -813,6 +845,15 @@ int nd_cuda_fail(cudaError_t e, const char* what) {
 
 inline int grid_for(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + TPB - 1) / TPB, 148 * 16)); }
 
+// element chunks of the fused last-axis passes: enough threads (about 150k) over the pencils, each
+// chunk at least 2P+2 elements long
+inline long long fused_nchunks(int E, long long inner, int P, int* echunk) {
+  long long nch = std::max<long long>(1, std::min<long long>(E / (2 * P + 2), (150000 + inner - 1) / inner));
+  const int ec = (int)((E + nch - 1) / nch);
+  *echunk = ec;
+  return (E + ec - 1) / ec;
+}
+
 struct NdRun {
   int ops = 0;
   int dim = 0, P = 0;
@@ -843,8 +884,10 @@ struct NdGeo {
   double* V64[3] = {nullptr, nullptr, nullptr};
   float* V32[3] = {nullptr, nullptr, nullptr};
   double* lam[3] = {nullptr, nullptr, nullptr};
-  double* W64 = nullptr;
-  float* W32 = nullptr;
+  double* W64 = nullptr;  // binary64 batches
+  float* W32 = nullptr;   // mixed: inner FP32 solve
+  fx* Wx = nullptr;       // mixed: double-float residual
+  bool has_stencil() const { return W64 || W32; }
 };
 
 struct NdBatch {
@@ -870,6 +913,7 @@ struct NdBatch {
   void* pre_L[3] = {nullptr, nullptr, nullptr};  // per run would be needed for different sizes; refreshed per run
   void* pre_D[3] = {nullptr, nullptr, nullptr};
   double* d_red = nullptr;  // reduction scratch (16 doubles)
+  void* d_side = nullptr;   // chunk-boundary partial sums of the fused last-axis pass
   std::vector<double> obs;  // host copy [run][nsteps][2+3dim]
   long long last_nsteps = 0;
   double tol = 1e-12;
@@ -934,7 +978,7 @@ struct Apply {
       const bool last = ax == D - 1;
       C<T>* a_out = last ? nullptr : bufs[nb++ % 4];
       C<T>* b_out = last ? out : bufs[nb++ % 4];
-      BandTerms ta{}, tb{};
+      BandTerms<T> ta{}, tb{};
       if (mode == 0) {  // A_sep
         // a stream: S_ax a
         ta.nt = 1;
@@ -1037,12 +1081,14 @@ struct Apply {
     for (int a = 0; a < L; ++a) inner *= len[a];
     const AxisDev& AL = r->ax[L];
     cudaMemsetAsync(U, 0, sizeof(C<T>) * (size_t)AL.n * inner, b->st);
-    long long nch = std::max<long long>(1, std::min<long long>(AL.E / (2 * P + 2), (150000 + inner - 1) / inner));
-    const int echunk = (int)((AL.E + nch - 1) / nch);
-    nch = (AL.E + echunk - 1) / echunk;
-    k_fused_last<T, P><<<grid_for(inner * nch), TPB, 0, b->st>>>(in, U, tab<T>(AL, L == dax ? TDB : TB), AL.nq, AL.n,
-                                                                 AL.E, inner, echunk, grid(), r->med, kind, faxis, cr,
-                                                                 ci);
+    int echunk = 1;
+    const long long nch = fused_nchunks(AL.E, inner, P, &echunk);
+    C<T>* side = static_cast<C<T>*>(b->d_side);
+    k_fused_last<T, P><<<grid_for(inner * nch), TPB, 0, b->st>>>(in, U, side, tab<T>(AL, L == dax ? TDB : TB), AL.nq,
+                                                                 AL.n, AL.E, inner, echunk, grid(), medium_t<T>(r->med),
+                                                                 kind, faxis, cr, ci);
+    if (nch > 1)
+      k_fused_fixup<T, P><<<grid_for((nch - 1) * P * inner), TPB, 0, b->st>>>(U, side, AL.n, inner, echunk, (int)nch);
     len[L] = AL.n;
     C<T>* cur = U;
     for (int ax = L - 1; ax >= 0; --ax) {
@@ -1063,7 +1109,7 @@ struct Apply {
   void apply(const C<T>* x, C<T>* y, double tau, const double* ebar) {
     kron(x, y, 0, tau, ebar);
     if (Wm) {  // i tau (V + variable-mass kinetic) through the assembled stencil
-      k_wapply<T, P><<<grid_for(r->N), TPB, 0, b->st>>>(Wm, x, y, r->n[0], r->n[1], tau);
+      k_wapply<T, P><<<grid_for(r->N), TPB, 0, b->st>>>(Wm, x, y, r->n[0], r->n[1], (T)tau);
       return;
     }
     if (r->med.pot_kind != TDZ_POT_ZERO) quad(x, y, -1, 0, 0, 0.0, tau);  // i tau V
@@ -1244,38 +1290,36 @@ MediumFF medium_ff(const MediumDev& d) {
   return m;
 }
 
-// observables of the binary64 state: [d_a, a_a, norm]
-template <int P>
-void observe(NdBatch* b, NdRun* r, Apply<double, P>& op, const double* Et, double* out) {
+// observables of the state c (given in the operator's arithmetic T: binary64 or double-float):
+// [d_a, a_a, norm]; y is scratch of the state's size
+template <class T, int P>
+void observe(NdBatch* b, NdRun* r, Apply<T, P>& op, const C<T>* c, C<T>* y, const double* Et, double* out) {
   const long long N = r->N;
   double h[4];
-  const C<double>* c = reinterpret_cast<const C<double>*>(r->c);
-  C<double>* y = reinterpret_cast<C<double>*>(b->d_y);
   double zero3[3] = {0, 0, 0};
   op.kron(c, y, 1, 0.0, zero3);
   red_zero(b, 2);
-  k_hdot<double><<<grid_for(N), TPB, 0, b->st>>>(c, y, N, b->d_red);
+  k_hdot<T><<<grid_for(N), TPB, 0, b->st>>>(c, y, N, b->d_red);
   const double norm = red_get(b, 2, h)[0];
   double dvals[3], gvals[3];
   for (int a = 0; a < r->dim; ++a) {
     op.kron(c, y, 2, 0.0, zero3, a);
     red_zero(b, 2);
-    k_hdot<double><<<grid_for(N), TPB, 0, b->st>>>(c, y, N, b->d_red);
+    k_hdot<T><<<grid_for(N), TPB, 0, b->st>>>(c, y, N, b->d_red);
     dvals[a] = red_get(b, 2, h)[0];
   }
   // c^H G_a c and (variable mass) c^H K c at the Gauss points, fused along the last axis
-  const C<double>* X = op.to_pencils(c, -1);
+  const C<T>* X = op.to_pencils(c, -1);
   const int L = r->dim - 1;
   long long inner = 1;
   for (int a = 0; a < L; ++a) inner *= r->Q[a];
   const AxisDev& AL = r->ax[L];
-  long long nch = std::max<long long>(1, std::min<long long>(AL.E / (2 * P + 2), (150000 + inner - 1) / inner));
-  const int echunk = (int)((AL.E + nch - 1) / nch);
-  nch = (AL.E + echunk - 1) / echunk;
+  int echunk = 1;
+  const long long nch = fused_nchunks(AL.E, inner, P, &echunk);
   red_zero(b, 4);
-  k_fused_last_reduce_ff<P><<<grid_for(inner * nch), TPB, 0, b->st>>>(X, r->ax[0], r->ax[1], AL, r->dim, inner, echunk,
-                                                                      medium_ff(r->med), r->const_mass ? 0 : 1,
-                                                                      b->d_red);
+  k_fused_last_reduce_ff<P, T><<<grid_for(inner * nch), TPB, 0, b->st>>>(X, r->ax[0], r->ax[1], AL, r->dim, inner,
+                                                                         echunk, medium_ff(r->med),
+                                                                         r->const_mass ? 0 : 1, b->d_red);
   double q4[4];
   red_get(b, 4, q4);
   const double kq = r->const_mass ? r->cm * norm : q4[3];
@@ -1294,95 +1338,118 @@ int propagate_run(NdBatch* b, NdRun* r, const tdz::Ops& o, const double* field, 
   const long long N = r->N;
   const double tau = 0.5 * dt;
   const int D = r->dim;
-  // binary64 operator and buffers
-  Apply<double, P> op64{b, r, reinterpret_cast<C<double>*>(b->d_t1), reinterpret_cast<C<double>*>(b->d_t2),
-                        reinterpret_cast<C<double>*>(b->d_t3), reinterpret_cast<C<double>*>(b->d_t4),
-                        reinterpret_cast<C<double>*>(b->d_qa), reinterpret_cast<C<double>*>(b->d_qb)};
-  Apply<float, P> op32{b, r, static_cast<C<float>*>(b->w_t1), static_cast<C<float>*>(b->w_t2),
-                       static_cast<C<float>*>(b->w_t3), static_cast<C<float>*>(b->w_t4),
-                       static_cast<C<float>*>(b->w_qa), static_cast<C<float>*>(b->w_qb)};
   const bool mixed = b->prec == TDZ_MIXED;
   const NdGeo& G = b->geo[r->geo];
-  if (G.W64 && b->opt_operator != TDZ_OPERATOR_QUADRATURE) {
-    op64.Wm = G.W64;
-    op32.Wm = G.W32;
-  }
+  const bool stencil = G.has_stencil() && b->opt_operator != TDZ_OPERATOR_QUADRATURE;
   if (!use_fd(b, r)) {
     if (mixed) factor_precond<float>(b, r, o, tau);
     else factor_precond<double>(b, r, o, tau);
   }
   C<double>* c = reinterpret_cast<C<double>*>(r->c);
-  C<double>* r0 = reinterpret_cast<C<double>*>(b->d_r0);
-  C<double>* y = reinterpret_cast<C<double>*>(b->d_y);
   double h[4];
-  for (long long s = 0; s < nsteps && r->status == TDZ_OK; ++s) {
-    double ebar[3] = {0, 0, 0}, Et[3] = {0, 0, 0};
-    for (int a = 0; a < D; ++a) {
-      ebar[a] = 0.5 * (field[s * D + a] + field[(s + 1) * D + a]);
-      Et[a] = field[(s + 1) * D + a];
-    }
-    // r0 = 2 (S c - A c): y = A c, r0 = S c, r0 = 2 r0 - 2 y
-    op64.apply(c, y, tau, ebar);
-    double zero3[3] = {0, 0, 0};
-    op64.kron(c, r0, 1, 0.0, zero3);
-    red_zero(b, 1);
-    k_nrm<double><<<grid_for(N), TPB, 0, b->st>>>(r0, N, b->d_red);
-    const double bb = red_get(b, 1, h)[0];
-    k_axby<double, double><<<grid_for(N), TPB, 0, b->st>>>(y, r0, N, -2.0, 2.0);
-    const double tol2 = b->tol * b->tol * bb;
-    double rel = 0.0;
-    bool ok = false;
-    if (!mixed) {
-      C<double>* x = reinterpret_cast<C<double>*>(b->d_y);
+  if (!mixed) {
+    // binary64 throughout: r0 = 2 (S c - A c), COCG on A delta = r0 to the tolerance, c += delta
+    Apply<double, P> op{b, r, reinterpret_cast<C<double>*>(b->d_t1), reinterpret_cast<C<double>*>(b->d_t2),
+                        reinterpret_cast<C<double>*>(b->d_t3), reinterpret_cast<C<double>*>(b->d_t4),
+                        reinterpret_cast<C<double>*>(b->d_qa), reinterpret_cast<C<double>*>(b->d_qb)};
+    if (stencil) op.Wm = G.W64;
+    C<double>* r0 = reinterpret_cast<C<double>*>(b->d_r0);
+    C<double>* y = reinterpret_cast<C<double>*>(b->d_y);
+    for (long long s = 0; s < nsteps && r->status == TDZ_OK; ++s) {
+      double ebar[3] = {0, 0, 0}, Et[3] = {0, 0, 0};
+      for (int a = 0; a < D; ++a) {
+        ebar[a] = 0.5 * (field[s * D + a] + field[(s + 1) * D + a]);
+        Et[a] = field[(s + 1) * D + a];
+      }
+      double zero3[3] = {0, 0, 0};
+      op.apply(c, y, tau, ebar);
+      op.kron(c, r0, 1, 0.0, zero3);
+      red_zero(b, 1);
+      k_nrm<double><<<grid_for(N), TPB, 0, b->st>>>(r0, N, b->d_red);
+      const double bb = red_get(b, 1, h)[0];
+      k_axby<double, double><<<grid_for(N), TPB, 0, b->st>>>(y, r0, N, -2.0, 2.0);
       double rr = 0;
-      const int its = cocg<double, P>(b, r, op64, x, r0, reinterpret_cast<C<double>*>(b->d_z),
+      const int its = cocg<double, P>(b, r, op, y, r0, reinterpret_cast<C<double>*>(b->d_z),
                                       reinterpret_cast<C<double>*>(b->d_p), reinterpret_cast<C<double>*>(b->d_q), tau,
-                                      ebar, tol2, b->max_it, &rr);
-      (void)its;
+                                      ebar, b->tol * b->tol * bb, b->max_it, &rr);
       r->iters += its;
-      rel = std::sqrt(rr / std::max(bb, 1e-300));
-      ok = rel <= b->tol;
-      k_axby<double, double><<<grid_for(N), TPB, 0, b->st>>>(x, c, N, 1.0, 1.0);  // c += delta
       r->nsolve++;
-    } else {
-      // outer refinement: r = r0 - A delta (binary64), inner FP32 COCG
-      C<double>* delta = y;
-      cudaMemsetAsync(delta, 0, sizeof(C<double>) * N, b->st);
-      C<double>* rcur = reinterpret_cast<C<double>*>(b->d_rc);  // binary64 residual
-      cudaMemcpyAsync(rcur, r0, sizeof(C<double>) * N, cudaMemcpyDeviceToDevice, b->st);
+      const double rel = std::sqrt(rr / std::max(bb, 1e-300));
+      k_axby<double, double><<<grid_for(N), TPB, 0, b->st>>>(y, c, N, 1.0, 1.0);  // c += delta
+      r->max_rel = std::max(r->max_rel, rel);
+      if (!(rel <= b->tol) && r->status == TDZ_OK) r->status = TDZ_ENOCONV;
+      double* row = obs_out + s * (2 + 3 * D);
+      row[0] = (double)(step0 + s + 1) * dt;
+      for (int a = 0; a < D; ++a) row[1 + a] = Et[a];
+      observe<double, P>(b, r, op, c, y, Et, row + 1 + D);
+      if (!std::isfinite(row[1 + 3 * D]) || !std::isfinite(row[1 + D])) r->status = TDZ_ENONFINITE;
+    }
+  } else {
+    // mixed: the binary64-class residuals r0 = 2 (S c - A c) and r = r0 - A delta in double-float,
+    // inner solves by FP32 COCG, delta accumulated in double-float, c += delta in binary64
+    Apply<fx, P> opx{b, r, reinterpret_cast<C<fx>*>(b->d_t1), reinterpret_cast<C<fx>*>(b->d_t2),
+                     reinterpret_cast<C<fx>*>(b->d_t3), reinterpret_cast<C<fx>*>(b->d_t4),
+                     reinterpret_cast<C<fx>*>(b->d_qa), reinterpret_cast<C<fx>*>(b->d_qb)};
+    Apply<float, P> op32{b, r, static_cast<C<float>*>(b->w_t1), static_cast<C<float>*>(b->w_t2),
+                         static_cast<C<float>*>(b->w_t3), static_cast<C<float>*>(b->w_t4),
+                         static_cast<C<float>*>(b->w_qa), static_cast<C<float>*>(b->w_qb)};
+    if (stencil) {
+      opx.Wm = G.Wx;
+      op32.Wm = G.W32;
+    }
+    C<fx>* cx_ = reinterpret_cast<C<fx>*>(b->d_z);    // c in double-float
+    C<fx>* r0 = reinterpret_cast<C<fx>*>(b->d_r0);
+    C<fx>* y = reinterpret_cast<C<fx>*>(b->d_y);      // A c, then delta
+    C<fx>* rc = reinterpret_cast<C<fx>*>(b->d_rc);    // current residual
+    C<float>* rf = static_cast<C<float>*>(b->w_r);
+    C<float>* xf = static_cast<C<float>*>(b->w_x);
+    for (long long s = 0; s < nsteps && r->status == TDZ_OK; ++s) {
+      double ebar[3] = {0, 0, 0}, Et[3] = {0, 0, 0};
+      for (int a = 0; a < D; ++a) {
+        ebar[a] = 0.5 * (field[s * D + a] + field[(s + 1) * D + a]);
+        Et[a] = field[(s + 1) * D + a];
+      }
+      double zero3[3] = {0, 0, 0};
+      k_axby<double, fx><<<grid_for(N), TPB, 0, b->st>>>(c, cx_, N, 1.0, 0.0);
+      opx.apply(cx_, y, tau, ebar);
+      opx.kron(cx_, r0, 1, 0.0, zero3);
+      red_zero(b, 1);
+      k_nrm<fx><<<grid_for(N), TPB, 0, b->st>>>(r0, N, b->d_red);
+      const double bb = red_get(b, 1, h)[0];
+      const double tol2 = b->tol * b->tol * bb;
+      k_axby<fx, fx><<<grid_for(N), TPB, 0, b->st>>>(y, r0, N, -2.0, 2.0);
+      cudaMemsetAsync(y, 0, sizeof(C<fx>) * N, b->st);  // y is delta from here on
+      cudaMemcpyAsync(rc, r0, sizeof(C<fx>) * N, cudaMemcpyDeviceToDevice, b->st);
       double rr = bb * 1e300;
       red_zero(b, 1);
-      k_nrm<double><<<grid_for(N), TPB, 0, b->st>>>(rcur, N, b->d_red);
+      k_nrm<fx><<<grid_for(N), TPB, 0, b->st>>>(rc, N, b->d_red);
       rr = red_get(b, 1, h)[0];
       for (int outer = 0; outer < 8 && rr > tol2; ++outer) {
-        C<float>* rf = static_cast<C<float>*>(b->w_r);
-        C<float>* xf = static_cast<C<float>*>(b->w_x);
-        k_axby<double, float><<<grid_for(N), TPB, 0, b->st>>>(rcur, rf, N, 1.0, 0.0);
+        k_axby<fx, float><<<grid_for(N), TPB, 0, b->st>>>(rc, rf, N, 1.0, 0.0);
         double rri = 0;
         const int its = cocg<float, P>(b, r, op32, xf, rf, static_cast<C<float>*>(b->w_z),
                                        static_cast<C<float>*>(b->w_p), static_cast<C<float>*>(b->w_q), tau, ebar,
                                        rr * b->inner_tol * b->inner_tol, b->max_it, &rri);
         r->iters += its;
         r->nsolve++;
-        k_axby<float, double><<<grid_for(N), TPB, 0, b->st>>>(xf, delta, N, 1.0, 1.0);
-        // rcur = r0 - A delta
-        op64.apply(delta, rcur, tau, ebar);
-        k_axby<double, double><<<grid_for(N), TPB, 0, b->st>>>(r0, rcur, N, 1.0, -1.0);
+        k_axby<float, fx><<<grid_for(N), TPB, 0, b->st>>>(xf, y, N, 1.0, 1.0);
+        opx.apply(y, rc, tau, ebar);                                         // rc = A delta
+        k_axby<fx, fx><<<grid_for(N), TPB, 0, b->st>>>(r0, rc, N, 1.0, -1.0);  // rc = r0 - A delta
         red_zero(b, 1);
-        k_nrm<double><<<grid_for(N), TPB, 0, b->st>>>(rcur, N, b->d_red);
+        k_nrm<fx><<<grid_for(N), TPB, 0, b->st>>>(rc, N, b->d_red);
         rr = red_get(b, 1, h)[0];
       }
-      rel = std::sqrt(rr / std::max(bb, 1e-300));
-      ok = rel <= b->tol;
-      k_axby<double, double><<<grid_for(N), TPB, 0, b->st>>>(delta, c, N, 1.0, 1.0);
+      const double rel = std::sqrt(rr / std::max(bb, 1e-300));
+      k_axby<fx, double><<<grid_for(N), TPB, 0, b->st>>>(y, c, N, 1.0, 1.0);  // c += delta
+      r->max_rel = std::max(r->max_rel, rel);
+      if (!(rel <= b->tol) && r->status == TDZ_OK) r->status = TDZ_ENOCONV;
+      double* row = obs_out + s * (2 + 3 * D);
+      row[0] = (double)(step0 + s + 1) * dt;
+      for (int a = 0; a < D; ++a) row[1 + a] = Et[a];
+      k_axby<double, fx><<<grid_for(N), TPB, 0, b->st>>>(c, cx_, N, 1.0, 0.0);
+      observe<fx, P>(b, r, opx, cx_, y, Et, row + 1 + D);
+      if (!std::isfinite(row[1 + 3 * D]) || !std::isfinite(row[1 + D])) r->status = TDZ_ENONFINITE;
     }
-    r->max_rel = std::max(r->max_rel, rel);
-    if (!ok && r->status == TDZ_OK) r->status = TDZ_ENOCONV;
-    double* row = obs_out + s * (2 + 3 * D);
-    row[0] = (double)(step0 + s + 1) * dt;
-    for (int a = 0; a < D; ++a) row[1 + a] = Et[a];
-    observe<P>(b, r, op64, Et, row + 1 + D);
-    if (!std::isfinite(row[1 + 3 * D]) || !std::isfinite(row[1 + D])) r->status = TDZ_ENONFINITE;
   }
   cudaError_t e = cudaStreamSynchronize(b->st);
   if (e != cudaSuccess) return nd_cuda_fail(e, "tdz_propagate (2-D/3-D)");
@@ -1461,9 +1528,14 @@ int stencil_setup_p(NdBatch* b, NdGeo& G, const AxisDev& ax, const AxisDev& ay, 
   const long long N = (long long)ax.n * ay.n;
   const size_t nf = (size_t)ay.Q * ax.n * W;
   const size_t nt = (size_t)ax.Q * ay.Q;
-  G.W64 = static_cast<double*>(b->alloc(sizeof(double) * N * W * W));
-  G.W32 = static_cast<float*>(b->alloc(sizeof(float) * N * W * W));
-  if (!G.W64 || !G.W32) return TDZ_ENOMEM;
+  if (b->prec == TDZ_MIXED) {
+    G.W32 = static_cast<float*>(b->alloc(sizeof(float) * N * W * W));
+    G.Wx = static_cast<fx*>(b->alloc(sizeof(fx) * N * W * W));
+    if (!G.W32 || !G.Wx) return TDZ_ENOMEM;
+  } else {
+    G.W64 = static_cast<double*>(b->alloc(sizeof(double) * N * W * W));
+    if (!G.W64) return TDZ_ENOMEM;
+  }
   double *F1 = nullptr, *F2 = nullptr, *fV = nullptr, *fK = nullptr;
   if (cudaMalloc(&F1, sizeof(double) * nf) != cudaSuccess || cudaMalloc(&fV, sizeof(double) * nt) != cudaSuccess ||
       (varmass && (cudaMalloc(&F2, sizeof(double) * nf) != cudaSuccess ||
@@ -1476,9 +1548,9 @@ int stencil_setup_p(NdBatch* b, NdGeo& G, const AxisDev& ax, const AxisDev& ay, 
     return TDZ_ENOMEM;
   }
   const int vm = varmass ? 1 : 0;
-  k_w_ftab<<<grid_for((long long)nt), TPB, 0, b->st>>>(ax, ay, M, vm, fV, fK);
+  k_w_ftab<<<grid_for((long long)nt), TPB, 0, b->st>>>(ax, ay, medium_t<double>(M), vm, fV, fK);
   k_w_stage1<P><<<grid_for((long long)ay.Q * ax.n), TPB, 0, b->st>>>(ax, ay, vm, fV, fK, F1, F2);
-  k_w_stage2<P><<<grid_for(N * W), TPB, 0, b->st>>>(ax, ay, vm, F1, F2, G.W64, G.W32);
+  k_w_stage2<P><<<grid_for(N * W), TPB, 0, b->st>>>(ax, ay, vm, F1, F2, G.W64, G.W32, G.Wx);
   cudaError_t e = cudaStreamSynchronize(b->st);
   cudaFree(F1);
   cudaFree(F2);
@@ -1576,8 +1648,25 @@ int nd_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* o
       A.lB = upl(B.val);
       A.lx = upl(B.xq);
       A.lw = upl(B.wq);
+      auto upx = [&](const std::vector<double>& v) -> fx* {
+        std::vector<fx> h(v.size());
+        for (size_t k = 0; k < v.size(); ++k) h[k] = fx(v[k]);
+        void* p = b->alloc(sizeof(fx) * h.size());
+        if (!p) return nullptr;
+        cudaMemcpyAsync(p, h.data(), sizeof(fx) * h.size(), cudaMemcpyHostToDevice, b->st);
+        cudaStreamSynchronize(b->st);
+        return static_cast<fx*>(p);
+      };
+      A.xB = upx(B.val);
+      A.xdB = upx(B.der);
+      A.xx = upx(B.xq);
+      A.xw = upx(B.wq);
+      A.xS = upx(o.Sa[a].a);
+      A.xT1 = upx(o.T1a[a].a);
+      A.xD = upx(o.Da[a].a);
       if (!A.B || !A.dB || !A.x || !A.w || !A.S || !A.T1 || !A.D || !A.fB || !A.fdB || !A.fx || !A.fw || !A.fS ||
-          !A.fT1 || !A.fD || !A.lB || !A.lx || !A.lw) {
+          !A.fT1 || !A.fD || !A.lB || !A.lx || !A.lw || !A.xB || !A.xdB || !A.xx || !A.xw || !A.xS || !A.xT1 ||
+          !A.xD) {
         delete b;
         return TDZ_ENOMEM;
       }
@@ -1589,7 +1678,7 @@ int nd_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* o
     }
   }
   b->runs.resize(nruns);
-  size_t maxN = 0, maxQ = 0;
+  size_t maxN = 0, maxQ = 0, maxSide = 0;
   int maxn = 0;
   for (int r = 0; r < nruns; ++r) {
     const Ops& o = ops[ops_index[r]]->o;
@@ -1629,6 +1718,13 @@ int nd_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* o
       mq = std::max(mq, part);
     }
     maxQ = std::max(maxQ, mq);
+    {
+      long long inner = 1;
+      for (int a = 0; a + 1 < dim; ++a) inner *= R.Q[a];
+      int ec = 1;
+      const long long nch = fused_nchunks(R.E[dim - 1], inner, P, &ec);
+      maxSide = std::max(maxSide, (size_t)((nch - 1) * P * inner));
+    }
     (void)NQ;
   }
   b->maxN = maxN;
@@ -1643,6 +1739,7 @@ int nd_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* o
   b->d_qa = static_cast<double2*>(b->alloc(z64 * maxQ));
   b->d_qb = static_cast<double2*>(b->alloc(z64 * maxQ));
   b->d_red = static_cast<double*>(b->alloc(sizeof(double) * 16));
+  b->d_side = b->alloc(sizeof(double2) * std::max<size_t>(maxSide, 1));
   b->d_z = static_cast<double2*>(b->alloc(z64 * maxN));
   b->d_p = static_cast<double2*>(b->alloc(z64 * maxN));
   b->d_q = static_cast<double2*>(b->alloc(z64 * maxN));
@@ -1674,7 +1771,7 @@ int nd_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* o
       return TDZ_ENOMEM;
     }
   }
-  if (!b->d_qb || !b->d_red) {
+  if (!b->d_qb || !b->d_red || !b->d_side) {
     delete b;
     set_error("tdz_batch_create: device allocation for 2-D/3-D work buffers failed");
     return TDZ_ENOMEM;
@@ -1689,7 +1786,8 @@ int nd_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* o
   size_t stencil_bytes = 0;
   if (dim == 2)
     for (int g = 0; g < nops; ++g)
-      stencil_bytes += (size_t)geo[g].n[0] * geo[g].n[1] * (2 * P + 1) * (2 * P + 1) * (sizeof(double) + sizeof(float));
+      stencil_bytes += (size_t)geo[g].n[0] * geo[g].n[1] * (2 * P + 1) * (2 * P + 1) *
+                       (precision == TDZ_MIXED ? sizeof(fx) + sizeof(float) : sizeof(double));
   size_t free_b = 0, total_b = 0;
   cudaMemGetInfo(&free_b, &total_b);
   const bool want_stencil = dim == 2 && stencil_bytes < free_b / 2;
@@ -1809,7 +1907,7 @@ int nd_set_option(NdBatch* b, int option, int value) {
     if (value < TDZ_OPERATOR_AUTO || value > TDZ_OPERATOR_STENCIL) return TDZ_EINVAL;
     if (value == TDZ_OPERATOR_STENCIL)
       for (const auto& g : b->geo)
-        if (!g.W64) {
+        if (!g.has_stencil()) {
           set_error("tdz_batch_set_option: the stencil operator exists for 2-D batches with enough device memory");
           return TDZ_EUNSUPPORTED;
         }
