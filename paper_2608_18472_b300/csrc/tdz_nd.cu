@@ -272,7 +272,7 @@ struct QGrid {
 template <class T, int P>
 __global__ void k_fused_last(const C<T>* __restrict__ in, C<T>* __restrict__ out, C<T>* __restrict__ side,
                              const T* __restrict__ Bl, int nq, int nL, int EL, long long inner, int echunk, QGrid<T> g,
-                             MediumT<T> M, int kind, int axis, double cr, double ci) {
+                             MediumT<T> M, int kind, int axis, double cr, double ci, const T* __restrict__ ftab) {
   const int nchunks = (EL + echunk - 1) / echunk;
   const long long total = inner * nchunks;
   const int L = g.dim - 1;
@@ -310,8 +310,13 @@ __global__ void k_fused_last(const C<T>* __restrict__ in, C<T>* __restrict__ out
           pr += b[k] * win[k].r;
           pi += b[k] * win[k].i;
         }
-        r[L] = g.x[L][q];
-        const T f = wp * g.w[L][q] * medium_f<T>(M, kind, axis, r, g.dim);
+        T f;
+        if (ftab) {  // w(q) f(r_q) tabulated at the Gauss points, [q_L][pencil]
+          f = ftab[(long long)q * inner + i];
+        } else {
+          r[L] = g.x[L][q];
+          f = wp * g.w[L][q] * medium_f<T>(M, kind, axis, r, g.dim);
+        }
         const T fr = f * tcr, fi = f * tci;
         const T gr = fr * pr - fi * pi, gi = fr * pi + fi * pr;
 #pragma unroll
@@ -350,6 +355,23 @@ __global__ void k_fused_last(const C<T>* __restrict__ in, C<T>* __restrict__ out
         *o = C<T>{v.r + acc[k].r, v.i + acc[k].i};
       }
     }
+  }
+}
+
+// w(q) V(r_q) at every Gauss point of a 3-D grid, [q_z][q_y][q_x] (x fastest), evaluated in binary64 and
+// stored as FP32 and double-float: the per-point factor of the potential term of k_fused_last
+__global__ void k_vtab3(AxisDev A0, AxisDev A1, AxisDev A2, MediumT<double> M, float* __restrict__ t32,
+                        fx* __restrict__ tx) {
+  const long long total = (long long)A0.Q * A1.Q * A2.Q;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int q0 = (int)(idx % A0.Q);
+    const long long t = idx / A0.Q;
+    const int q1 = (int)(t % A1.Q), q2 = (int)(t / A1.Q);
+    double r[3] = {A0.x[q0], A1.x[q1], A2.x[q2]};
+    const double v = A0.w[q0] * A1.w[q1] * A2.w[q2] * medium_f<double>(M, 0, 0, r, 3);
+    t32[idx] = (float)v;
+    tx[idx] = fx(v);
   }
 }
 
@@ -888,6 +910,9 @@ struct NdGeo {
   float* W32 = nullptr;   // mixed: inner FP32 solve
   fx* Wx = nullptr;       // mixed: double-float residual
   bool has_stencil() const { return W64 || W32; }
+  // 3-D mixed: w V at the Gauss points ([q_z][q_y][q_x]) for the FP32 and double-float passes
+  float* Vq32 = nullptr;
+  fx* Vqx = nullptr;
 };
 
 struct NdBatch {
@@ -951,6 +976,7 @@ struct Apply {
   C<T>* qa;
   C<T>* qb;
   const T* Wm = nullptr;  // assembled 2-D stencil of the non-separable terms, or null (quadrature)
+  const T* Vtab = nullptr;  // w V at the Gauss points (3-D), or null (evaluated per point)
 
   // shape helpers: lengths of axes with the first `k` axes already in quadrature space
   void shape(int axis, const int* len, long long& outer, long long& inner) const {
@@ -1084,9 +1110,10 @@ struct Apply {
     int echunk = 1;
     const long long nch = fused_nchunks(AL.E, inner, P, &echunk);
     C<T>* side = static_cast<C<T>*>(b->d_side);
+    const T* ftab = (kind == 0 && dax < 0 && D == 3) ? Vtab : nullptr;
     k_fused_last<T, P><<<grid_for(inner * nch), TPB, 0, b->st>>>(in, U, side, tab<T>(AL, L == dax ? TDB : TB), AL.nq,
                                                                  AL.n, AL.E, inner, echunk, grid(), medium_t<T>(r->med),
-                                                                 kind, faxis, cr, ci);
+                                                                 kind, faxis, cr, ci, ftab);
     if (nch > 1)
       k_fused_fixup<T, P><<<grid_for((nch - 1) * P * inner), TPB, 0, b->st>>>(U, side, AL.n, inner, echunk, (int)nch);
     len[L] = AL.n;
@@ -1397,6 +1424,8 @@ int propagate_run(NdBatch* b, NdRun* r, const tdz::Ops& o, const double* field, 
       opx.Wm = G.Wx;
       op32.Wm = G.W32;
     }
+    opx.Vtab = G.Vqx;
+    op32.Vtab = G.Vq32;
     C<fx>* cx_ = reinterpret_cast<C<fx>*>(b->d_z);    // c in double-float
     C<fx>* r0 = reinterpret_cast<C<fx>*>(b->d_r0);
     C<fx>* y = reinterpret_cast<C<fx>*>(b->d_y);      // A c, then delta
@@ -1803,6 +1832,31 @@ int nd_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* o
       if (rs != TDZ_OK) {
         delete b;
         return rs;
+      }
+    }
+  }
+  // 3-D mixed batches: tabulate w V at the Gauss points when the device has room for it (12 bytes
+  // per point, at most half of the free memory); otherwise V is evaluated per point
+  if (dim == 3 && precision == TDZ_MIXED) {
+    size_t need = 0;
+    for (int g = 0; g < nops; ++g)
+      if (ops[g]->o.med.pot_kind != TDZ_POT_ZERO)
+        need += (size_t)geo[g].Q[0] * geo[g].Q[1] * geo[g].Q[2] * (sizeof(float) + sizeof(fx));
+    cudaMemGetInfo(&free_b, &total_b);
+    if (need > 0 && need < free_b / 2) {
+      for (int g = 0; g < nops; ++g) {
+        if (ops[g]->o.med.pot_kind == TDZ_POT_ZERO) continue;
+        const size_t nq3 = (size_t)geo[g].Q[0] * geo[g].Q[1] * geo[g].Q[2];
+        b->geo[g].Vq32 = static_cast<float*>(b->alloc(sizeof(float) * nq3));
+        b->geo[g].Vqx = static_cast<fx*>(b->alloc(sizeof(fx) * nq3));
+        if (!b->geo[g].Vq32 || !b->geo[g].Vqx) {
+          delete b;
+          set_error("tdz_batch_create: device allocation for the 3-D potential table failed");
+          return TDZ_ENOMEM;
+        }
+        k_vtab3<<<grid_for((long long)nq3), TPB, 0, b->st>>>(geo[g].ax[0], geo[g].ax[1], geo[g].ax[2],
+                                                             medium_t<double>(medium_dev(ops[g]->o.med)),
+                                                             b->geo[g].Vq32, b->geo[g].Vqx);
       }
     }
   }
