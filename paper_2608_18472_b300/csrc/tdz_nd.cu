@@ -819,19 +819,41 @@ __global__ void k_wapply(const T* __restrict__ Wm, const C<T>* __restrict__ x, C
 }
 
 // ------------------------------------------------------------------------------- fast diagonalisation
-// interleaved complex <-> planar (re plane, then im plane), with a change of precision
+// interleaved complex state (n0 x n1 x n2, x fastest) <-> two planar planes (re, then im) on the
+// padded grid np0 x np1 x np2 (each axis rounded up to a multiple of 8 so that every GEMM leading
+// dimension is 32-byte aligned); padding entries are zero
+struct PadDims {
+  int dim, n[3], np[3];
+  long long Np;  // padded size of one plane
+};
 template <class Tv, class Tp>
-__global__ void k_split(const C<Tv>* __restrict__ v, Tp* __restrict__ w, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const C<Tv> a = v[i];
-    w[i] = (Tp)a.r;
-    w[n + i] = (Tp)a.i;
+__global__ void k_split(const C<Tv>* __restrict__ v, Tp* __restrict__ w, PadDims d) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < d.Np; i += (long long)gridDim.x * blockDim.x) {
+    const int j0 = (int)(i % d.np[0]);
+    const long long t = i / d.np[0];
+    const int j1 = d.dim > 1 ? (int)(t % d.np[1]) : 0;
+    const int j2 = d.dim > 2 ? (int)(t / d.np[1]) : 0;
+    const bool in = j0 < d.n[0] && (d.dim < 2 || j1 < d.n[1]) && (d.dim < 3 || j2 < d.n[2]);
+    if (in) {
+      const C<Tv> a = v[((long long)j2 * d.n[1] + j1) * d.n[0] + j0];
+      w[i] = (Tp)a.r;
+      w[d.Np + i] = (Tp)a.i;
+    } else {
+      w[i] = (Tp)0;
+      w[d.Np + i] = (Tp)0;
+    }
   }
 }
 template <class Tv, class Tp>
-__global__ void k_merge(const Tp* __restrict__ w, C<Tv>* __restrict__ v, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    v[i] = C<Tv>{(Tv)w[i], (Tv)w[n + i]};
+__global__ void k_merge(const Tp* __restrict__ w, C<Tv>* __restrict__ v, PadDims d, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int j0 = (int)(i % d.n[0]);
+    const long long t = i / d.n[0];
+    const int j1 = d.dim > 1 ? (int)(t % d.n[1]) : 0;
+    const int j2 = d.dim > 2 ? (int)(t / d.n[1]) : 0;
+    const long long k = ((long long)j2 * d.np[1] + j1) * d.np[0] + j0;
+    v[i] = C<Tv>{(Tv)w[k], (Tv)w[d.Np + k]};
+  }
 }
 // in the eigenbasis (index j0 fastest): u /= 1 + i tm (lam0[j0] + lam1[j1] + lam2[j2])
 template <class Tp>
@@ -903,6 +925,7 @@ namespace tdz {
 struct NdGeo {
   bool fd = false;
   int n[3] = {0, 0, 0};
+  int np[3] = {1, 1, 1};  // n rounded up to a multiple of 8 (fast-diagonalisation work layout)
   double* V64[3] = {nullptr, nullptr, nullptr};
   float* V32[3] = {nullptr, nullptr, nullptr};
   double* lam[3] = {nullptr, nullptr, nullptr};
@@ -1162,18 +1185,22 @@ void line_precond(NdBatch* b, NdRun* r, C<T>* v) {
 // One axis transform: contract the slowest axis of the current layout (length ns, R = N / ns
 // values per index) with V (forward, V^T) or V^T (inverse, V), writing the new index fastest:
 //   out(j, r) = sum_k M(k, j) in(r, k),  both planes (re, im) as a batch of two.
-// After dim transforms the axes are back in their original order.
+// After dim transforms the axes are back in their original order. Sizes are padded to multiples
+// of 8, so every leading dimension is 32-byte aligned and the FP32 product can run on the tensor
+// cores as a BF16x9 emulated GEMM (three-term bf16 splits of both operands, FP32 accuracy).
 inline cublasStatus_t gemm_rot(cublasHandle_t h, bool inv, int ns, int R, const float* V, const float* in, float* out,
                                long long stride) {
   const float one = 1.0f, zero = 0.0f;
-  return cublasSgemmStridedBatched(h, inv ? CUBLAS_OP_N : CUBLAS_OP_T, CUBLAS_OP_T, ns, R, ns, &one, V, ns, 0, in, R,
-                                   stride, &zero, out, ns, stride, 2);
+  return cublasGemmStridedBatchedEx(h, inv ? CUBLAS_OP_N : CUBLAS_OP_T, CUBLAS_OP_T, ns, R, ns, &one, V, CUDA_R_32F, ns, 0,
+                                    in, CUDA_R_32F, R, stride, &zero, out, CUDA_R_32F, ns, stride, 2,
+                                    CUBLAS_COMPUTE_32F_EMULATED_16BFX9, CUBLAS_GEMM_DEFAULT);
 }
 inline cublasStatus_t gemm_rot(cublasHandle_t h, bool inv, int ns, int R, const double* V, const double* in,
                                double* out, long long stride) {
   const double one = 1.0, zero = 0.0;
-  return cublasDgemmStridedBatched(h, inv ? CUBLAS_OP_N : CUBLAS_OP_T, CUBLAS_OP_T, ns, R, ns, &one, V, ns, 0, in, R,
-                                   stride, &zero, out, ns, stride, 2);
+  return cublasGemmStridedBatchedEx(h, inv ? CUBLAS_OP_N : CUBLAS_OP_T, CUBLAS_OP_T, ns, R, ns, &one, V, CUDA_R_64F, ns, 0,
+                                    in, CUDA_R_64F, R, stride, &zero, out, CUDA_R_64F, ns, stride, 2, CUBLAS_COMPUTE_64F,
+                                    CUBLAS_GEMM_DEFAULT);
 }
 template <class T> const T* fd_mat(const NdGeo& g, int a);
 template <> const float* fd_mat<float>(const NdGeo& g, int a) { return g.V32[a]; }
@@ -1185,21 +1212,28 @@ template <> const double* fd_mat<double>(const NdGeo& g, int a) { return g.V64[a
 template <class T>
 void fd_apply(NdBatch* b, const NdRun* r, C<T>* v, T* w0, T* w1, double tau) {
   const NdGeo& G = b->geo[r->geo];
-  const long long N = r->N;
-  k_split<T, T><<<grid_for(N), TPB, 0, b->st>>>(v, w0, N);
+  PadDims d{};
+  d.dim = r->dim;
+  d.Np = 1;
+  for (int a = 0; a < 3; ++a) {
+    d.n[a] = a < r->dim ? r->n[a] : 1;
+    d.np[a] = a < r->dim ? G.np[a] : 1;
+    d.Np *= d.np[a];
+  }
+  k_split<T, T><<<grid_for(d.Np), TPB, 0, b->st>>>(v, w0, d);
   T* cur = w0;
   T* nxt = w1;
   for (int pass = 0; pass < 2; ++pass) {
     for (int a = r->dim - 1; a >= 0; --a) {
-      const int ns = r->n[a];
-      gemm_rot(b->blas, pass == 1, ns, (int)(N / ns), fd_mat<T>(G, a), cur, nxt, N);
+      const int ns = d.np[a];
+      gemm_rot(b->blas, pass == 1, ns, (int)(d.Np / ns), fd_mat<T>(G, a), cur, nxt, d.Np);
       std::swap(cur, nxt);
     }
     if (pass == 0)
-      k_fd_scale<T><<<grid_for(N), TPB, 0, b->st>>>(cur, N, r->dim, r->n[0], r->n[1], G.lam[0], G.lam[1], G.lam[2],
-                                                    tau * r->mbar);
+      k_fd_scale<T><<<grid_for(d.Np), TPB, 0, b->st>>>(cur, d.Np, r->dim, d.np[0], d.np[1], G.lam[0], G.lam[1],
+                                                       G.lam[2], tau * r->mbar);
   }
-  k_merge<T, T><<<grid_for(N), TPB, 0, b->st>>>(cur, v, N);
+  k_merge<T, T><<<grid_for(r->N), TPB, 0, b->st>>>(cur, v, d, r->N);
 }
 
 bool use_fd(const NdBatch* b, const NdRun* r) {
@@ -1517,34 +1551,41 @@ int fd_setup(NdBatch* b, int g, const Ops& o) {
         A[(size_t)i + (size_t)j * n] = A[(size_t)j + (size_t)i * n] = o.T1a[a].at(i, d);
         B[(size_t)i + (size_t)j * n] = B[(size_t)j + (size_t)i * n] = o.Sa[a].at(i, d);
       }
-    G.V64[a] = static_cast<double*>(b->alloc(sizeof(double) * A.size()));
-    G.V32[a] = static_cast<float*>(b->alloc(sizeof(float) * A.size()));
-    G.lam[a] = static_cast<double*>(b->alloc(sizeof(double) * n));
+    // factors stored zero-padded to np = n rounded up to 8 (np x np, eigenvalues padded with 0)
+    const int np = (n + 7) / 8 * 8;
+    G.np[a] = np;
+    G.V64[a] = static_cast<double*>(b->alloc(sizeof(double) * np * np));
+    G.V32[a] = static_cast<float*>(b->alloc(sizeof(float) * np * np));
+    G.lam[a] = static_cast<double*>(b->alloc(sizeof(double) * np));
     if (!G.V64[a] || !G.V32[a] || !G.lam[a]) {
       cusolverDnDestroy(h);
       return TDZ_ENOMEM;
     }
-    double* dB = nullptr;
+    double *dA = nullptr, *dB = nullptr;
     int* dinfo = nullptr;
     double* work = nullptr;
     int lwork = 0, info = -1;
-    ok = cudaMalloc(&dB, sizeof(double) * B.size()) == cudaSuccess && cudaMalloc(&dinfo, sizeof(int)) == cudaSuccess;
-    ok = ok && cudaMemcpyAsync(G.V64[a], A.data(), sizeof(double) * A.size(), cudaMemcpyHostToDevice, b->st) == cudaSuccess;
+    ok = cudaMalloc(&dA, sizeof(double) * A.size()) == cudaSuccess &&
+         cudaMalloc(&dB, sizeof(double) * B.size()) == cudaSuccess && cudaMalloc(&dinfo, sizeof(int)) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(dA, A.data(), sizeof(double) * A.size(), cudaMemcpyHostToDevice, b->st) == cudaSuccess;
     ok = ok && cudaMemcpyAsync(dB, B.data(), sizeof(double) * B.size(), cudaMemcpyHostToDevice, b->st) == cudaSuccess;
     ok = ok && cusolverDnDsygvd_bufferSize(h, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n,
-                                           G.V64[a], n, dB, n, G.lam[a], &lwork) == CUSOLVER_STATUS_SUCCESS;
+                                           dA, n, dB, n, G.lam[a], &lwork) == CUSOLVER_STATUS_SUCCESS;
     ok = ok && cudaMalloc(&work, sizeof(double) * std::max(lwork, 1)) == cudaSuccess;
-    ok = ok && cusolverDnDsygvd(h, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, G.V64[a], n,
+    ok = ok && cusolverDnDsygvd(h, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, dA, n,
                                 dB, n, G.lam[a], work, lwork, dinfo) == CUSOLVER_STATUS_SUCCESS;
     ok = ok && cudaMemcpyAsync(&info, dinfo, sizeof(int), cudaMemcpyDeviceToHost, b->st) == cudaSuccess;
     ok = ok && cudaStreamSynchronize(b->st) == cudaSuccess && info == 0;
+    ok = ok && cudaMemcpy2DAsync(G.V64[a], sizeof(double) * np, dA, sizeof(double) * n, sizeof(double) * n, n,
+                                 cudaMemcpyDeviceToDevice, b->st) == cudaSuccess;
     if (ok) {
-      k_d2f<<<grid_for((long long)n * n), TPB, 0, b->st>>>(G.V64[a], G.V32[a], (long long)n * n);
+      k_d2f<<<grid_for((long long)np * np), TPB, 0, b->st>>>(G.V64[a], G.V32[a], (long long)np * np);
       ok = cudaStreamSynchronize(b->st) == cudaSuccess;
     }
     cudaFree(work);
     cudaFree(dinfo);
     cudaFree(dB);
+    cudaFree(dA);
   }
   cusolverDnDestroy(h);
   G.fd = ok;
@@ -1741,6 +1782,11 @@ int nd_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* o
     // the largest intermediate of a Gauss-point pass: axes 0..k at the points, the others at the
     // coefficients (k <= dim - 2; the last axis is always fused), or the state itself
     size_t mq = (size_t)R.N;
+    {
+      size_t padded = 1;  // fast-diagonalisation planes on the grid padded to multiples of 8
+      for (int a = 0; a < dim; ++a) padded *= (size_t)((R.n[a] + 7) / 8 * 8);
+      mq = std::max(mq, padded);
+    }
     for (int k = 0; k + 1 < dim; ++k) {
       size_t part = 1;
       for (int a = 0; a < dim; ++a) part *= (size_t)(a <= k ? R.Q[a] : R.n[a]);
@@ -1812,6 +1858,9 @@ int nd_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* o
     set_error("tdz_batch_create: cuBLAS initialisation failed");
     return TDZ_ECUDA;
   }
+  // the FP32 fast-diagonalisation transforms run on the tensor cores as BF16x9 products (FP32
+  // accuracy); allow that for every shape
+  cublasSetEmulationStrategy(b->blas, CUBLAS_EMULATION_STRATEGY_EAGER);
   size_t stencil_bytes = 0;
   if (dim == 2)
     for (int g = 0; g < nops; ++g)
