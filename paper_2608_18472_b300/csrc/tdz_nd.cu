@@ -32,6 +32,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "tdz_arith.cuh"
@@ -143,6 +144,23 @@ __device__ __forceinline__ T medium_f(const MediumT<T>& M, int kind, int axis, c
 template <class T>
 using C = cx<T>;
 
+// Sum-of-products accumulator: a plain multiply-add for float and double; for double-float a
+// compensated (Dot2) accumulation, about half the work of double-float multiply-then-add
+template <class T>
+struct Mac {
+  T s;
+  TDZ_DEV Mac() : s(0) {}
+  TDZ_DEV void add(T a, T b) { s += a * b; }
+  TDZ_DEV T get() const { return s; }
+};
+template <>
+struct Mac<fx> {
+  ffacc a;
+  TDZ_DEV Mac() { acc_zero(a); }
+  TDZ_DEV void add(fx x, fx y) { acc_mul(a, to_ff(x), to_ff(y)); }
+  TDZ_DEV fx get() const { return to_fx(acc_get(a)); }
+};
+
 // ------------------------------------------------------------------------------- axis band terms
 // out[o][j][i] (+)= sum_t coef_t * sum_d R_t(j, j+d) in_{sel_t}[o][j+d][i]   (R_t real symmetric bands)
 template <class T>
@@ -167,7 +185,7 @@ __global__ void k_axis_band(BandTerms<T> bt, const C<T>* __restrict__ in0, const
     for (int t = 0; t < bt.nt; ++t) {
       const C<T>* in = bt.sel[t] ? in1 : in0;
       const T* R = static_cast<const T*>(bt.R[t]);
-      T sr = 0, si = 0;
+      Mac<T> mr, mi;
 #pragma unroll
       for (int d = -P; d <= P; ++d) {
         const int jj = j + d;
@@ -175,9 +193,10 @@ __global__ void k_axis_band(BandTerms<T> bt, const C<T>* __restrict__ in0, const
         const int hi = jj > j ? jj : j;
         const T m = R[(size_t)hi * (P + 1) + (d < 0 ? -d : d)];
         const C<T> v = in[(o * L + jj) * inner + i];
-        sr += m * v.r;
-        si += m * v.i;
+        mr.add(m, v.r);
+        mi.add(m, v.i);
       }
+      const T sr = mr.get(), si = mi.get();
       const T cr = bt.cr[t], ci = bt.ci[t];
       ar += cr * sr - ci * si;
       ai += cr * si + ci * sr;
@@ -204,17 +223,17 @@ __global__ void k_interp(const T* __restrict__ Btab, int nq, int n, int Q, const
     const int q = (int)(oq % Q);
     const long long o = oq / Q;
     const int e = q / nq;
-    T sr = 0, si = 0;
+    Mac<T> sr, si;
 #pragma unroll
     for (int r = 0; r <= P; ++r) {
       const int j = e + r - 1;
       if (j < 0 || j >= n) continue;
       const T b = Btab[(size_t)q * (P + 1) + r];
       const C<T> v = in[(o * n + j) * inner + i];
-      sr += b * v.r;
-      si += b * v.i;
+      sr.add(b, v.r);
+      si.add(b, v.i);
     }
-    out[idx] = C<T>{sr, si};
+    out[idx] = C<T>{sr.get(), si.get()};
   }
 }
 
@@ -230,7 +249,7 @@ __global__ void k_project(const T* __restrict__ Btab, int nq, int n, int E, cons
     const long long oj = idx / inner;
     const int j = (int)(oj % n);
     const long long o = oj / n;
-    T sr = 0, si = 0;
+    Mac<T> mr, mi;
 #pragma unroll
     for (int r = 0; r <= P; ++r) {
       const int e = j + 1 - r;
@@ -239,10 +258,11 @@ __global__ void k_project(const T* __restrict__ Btab, int nq, int n, int E, cons
         const int q = e * nq + qq;
         const T b = Btab[(size_t)q * (P + 1) + r];
         const C<T> v = in[(o * Q + q) * inner + i];
-        sr += b * v.r;
-        si += b * v.i;
+        mr.add(b, v.r);
+        mi.add(b, v.i);
       }
     }
+    const T sr = mr.get(), si = mi.get();
     if (accumulate) {
       C<T> v = out[idx];
       out[idx] = C<T>{v.r + sr, v.i + si};
@@ -292,24 +312,24 @@ __global__ void k_fused_last(const C<T>* __restrict__ in, C<T>* __restrict__ out
       r[a] = g.x[a][q];
       wp *= g.w[a][q];
     }
-    C<T> win[P + 1];   // win[r] = coefficient e + r - 1 of the current element
-    C<T> acc[P + 1];   // acc[r] = partial projection onto coefficient e + r - 1
+    C<T> win[P + 1];            // win[r] = coefficient e + r - 1 of the current element
+    Mac<T> accr[P + 1], acci[P + 1];  // partial projections onto coefficient e + r - 1
 #pragma unroll
     for (int k = 0; k <= P; ++k) {
       const int j = e0 + k - 1;
       win[k] = (j >= 0 && j < nL) ? in[(long long)j * inner + i] : czero<T>();
-      acc[k] = czero<T>();
     }
     for (int e = e0; e < e1; ++e) {
       for (int qq = 0; qq < nq; ++qq) {
         const int q = e * nq + qq;
         const T* b = Bl + (size_t)q * (P + 1);
-        T pr = 0, pi = 0;
+        Mac<T> mr, mi;
 #pragma unroll
         for (int k = 0; k <= P; ++k) {
-          pr += b[k] * win[k].r;
-          pi += b[k] * win[k].i;
+          mr.add(b[k], win[k].r);
+          mi.add(b[k], win[k].i);
         }
+        const T pr = mr.get(), pi = mi.get();
         T f;
         if (ftab) {  // w(q) f(r_q) tabulated at the Gauss points, [q_L][pencil]
           f = ftab[(long long)q * inner + i];
@@ -321,8 +341,8 @@ __global__ void k_fused_last(const C<T>* __restrict__ in, C<T>* __restrict__ out
         const T gr = fr * pr - fi * pi, gi = fr * pi + fi * pr;
 #pragma unroll
         for (int k = 0; k <= P; ++k) {
-          acc[k].r += b[k] * gr;
-          acc[k].i += b[k] * gi;
+          accr[k].add(b[k], gr);
+          acci[k].add(b[k], gi);
         }
       }
       // coefficient e - 1 is complete: emit; shift both windows by one
@@ -331,28 +351,31 @@ __global__ void k_fused_last(const C<T>* __restrict__ in, C<T>* __restrict__ out
         if (j >= 0 && j < nL) {
           C<T>* o = out + (long long)j * inner + i;
           const C<T> v = *o;
-          *o = C<T>{v.r + acc[0].r, v.i + acc[0].i};
+          *o = C<T>{v.r + accr[0].get(), v.i + acci[0].get()};
         }
       }
 #pragma unroll
       for (int k = 0; k < P; ++k) {
         win[k] = win[k + 1];
-        acc[k] = acc[k + 1];
+        accr[k] = accr[k + 1];
+        acci[k] = acci[k + 1];
       }
       const int jn = e + P;  // coefficient entering the window for element e + 1
       win[P] = (jn >= 0 && jn < nL && e + 1 < e1) ? in[(long long)jn * inner + i] : czero<T>();
-      acc[P] = czero<T>();
+      accr[P] = Mac<T>();
+      acci[P] = Mac<T>();
     }
     // remaining partial sums: coefficients e1 - 1 .. e1 + P - 2 (shared with the next chunk)
 #pragma unroll
     for (int k = 0; k < P; ++k) {
       const int j = e1 - 1 + k;
+      const C<T> a = C<T>{accr[k].get(), acci[k].get()};
       if (e1 < EL) {
-        side[((long long)ch * P + k) * inner + i] = acc[k];
+        side[((long long)ch * P + k) * inner + i] = a;
       } else if (j >= 0 && j < nL) {
         C<T>* o = out + (long long)j * inner + i;
         const C<T> v = *o;
-        *o = C<T>{v.r + acc[k].r, v.i + acc[k].i};
+        *o = C<T>{v.r + a.r, v.i + a.i};
       }
     }
   }
@@ -739,7 +762,14 @@ __global__ void k_w_stage1(AxisDev ax, AxisDev ay, int varmass, const double* __
   }
 }
 
-// one thread per (iy, dx, ix): the 2P+1 offsets dy
+// W is symmetric (W_{i,j} = W_{j,i}), so only the offsets (dy, dx) with dy > 0, or dy = 0 and dx >= 0,
+// are stored: (P+1) + P(2P+1) of them, W_{(ix,iy),(ix+dx,iy+dy)} at [half_off(dy, dx)][iy nx + ix]
+__host__ __device__ constexpr int half_count(int P) { return (P + 1) + P * (2 * P + 1); }
+__host__ __device__ constexpr int half_off(int P, int dy, int dx) {
+  return dy == 0 ? dx : (P + 1) + (dy - 1) * (2 * P + 1) + (dx + P);
+}
+
+// one thread per (iy, dx, ix): the 2P+1 offsets dy (the stored half of them)
 template <int P>
 __global__ void k_w_stage2(AxisDev ax, AxisDev ay, int varmass, const double* __restrict__ F1,
                            const double* __restrict__ F2, double* __restrict__ W64, float* __restrict__ W32,
@@ -774,30 +804,34 @@ __global__ void k_w_stage2(AxisDev ax, AxisDev ay, int varmass, const double* __
       }
     }
     const long long row = (long long)iy * ax.n + ix;
-    const int jx = ix + dxi - P;
+    const int dx = dxi - P;
+    const int jx = ix + dx;
 #pragma unroll
     for (int dyi = 0; dyi < W; ++dyi) {
-      const int jy = iy + dyi - P;
+      const int dy = dyi - P;
+      const int jy = iy + dy;
       const bool in = jx >= 0 && jx < ax.n && jy >= 0 && jy < ay.n;
-      const size_t o = (size_t)(dyi * W + dxi) * N + row;
       const double v = in ? s[dyi] : 0.0;
+      if (W32) W32[(size_t)(dyi * W + dxi) * N + row] = (float)v;  // full layout
+      if (dy < 0 || (dy == 0 && dx < 0)) continue;
+      const size_t o = (size_t)half_off(P, dy, dx) * N + row;  // half layout
       if (W64) W64[o] = v;
-      if (W32) W32[o] = (float)v;
       if (Wx) Wx[o] = fx(v);
     }
   }
 }
 
-// y += i tau W x  (W real symmetric stencil, layout [(dy + P)(2P + 1) + dx + P][row])
+// y += i tau W x with the full stencil, layout [(dy + P)(2P + 1) + dx + P][row] (FP32 inner solve: a
+// straight stream of 225 coalesced loads per row is faster than the half layout's two-sided reads)
 template <class T, int P>
-__global__ void k_wapply(const T* __restrict__ Wm, const C<T>* __restrict__ x, C<T>* __restrict__ y, int nx, int ny,
-                         T tau) {
+__global__ void k_wapply_full(const T* __restrict__ Wm, const C<T>* __restrict__ x, C<T>* __restrict__ y, int nx,
+                              int ny, T tau) {
   constexpr int W = 2 * P + 1;
   const long long N = (long long)nx * ny;
   for (long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x; row < N;
        row += (long long)gridDim.x * blockDim.x) {
     const int ix = (int)(row % nx), iy = (int)(row / nx);
-    T sr = 0, si = 0;
+    Mac<T> mr, mi;
     for (int dy = -P; dy <= P; ++dy) {
       const int jy = iy + dy;
       if (jy < 0 || jy >= ny) continue;
@@ -809,10 +843,51 @@ __global__ void k_wapply(const T* __restrict__ Wm, const C<T>* __restrict__ x, C
         if (jx < 0 || jx >= nx) continue;
         const T w = wr[(size_t)(dx + P) * N];
         const C<T> v = xr[jx];
-        sr += w * v.r;
-        si += w * v.i;
+        mr.add(w, v.r);
+        mi.add(w, v.i);
       }
     }
+    const T sr = mr.get(), si = mi.get();
+    const C<T> o = y[row];
+    y[row] = C<T>{o.r - tau * si, o.i + tau * sr};
+  }
+}
+
+// y += i tau W x  (W real symmetric; stored half, see half_off): each stored entry serves row i with
+// neighbour i + off and, transposed, row i with neighbour i - off (read at row i - off: coalesced)
+template <class T, int P>
+__global__ void k_wapply(const T* __restrict__ Wm, const C<T>* __restrict__ x, C<T>* __restrict__ y, int nx, int ny,
+                         T tau) {
+  const long long N = (long long)nx * ny;
+  for (long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x; row < N;
+       row += (long long)gridDim.x * blockDim.x) {
+    const int ix = (int)(row % nx), iy = (int)(row / nx);
+    Mac<T> mr, mi;
+#pragma unroll 1
+    for (int dy = 0; dy <= P; ++dy) {
+      const T* wr = Wm + (size_t)half_off(P, dy, 0) * N;
+#pragma unroll
+      for (int dx = -P; dx <= P; ++dx) {
+        if (dy == 0 && dx < 0) continue;
+        const T* wo = wr + (long long)dx * N;  // offset (dy, dx) is stored at half_off(P, dy, 0) + dx
+        const int jx = ix + dx, jy = iy + dy;
+        if (jx >= 0 && jx < nx && jy < ny) {  // direct: W_{row, row + (dx, dy)}
+          const T w = wo[row];
+          const C<T> v = x[(long long)jy * nx + jx];
+          mr.add(w, v.r);
+          mi.add(w, v.i);
+        }
+        const int kx = ix - dx, ky = iy - dy;
+        if ((dy > 0 || dx > 0) && kx >= 0 && kx < nx && ky >= 0) {  // transposed: W_{row - off, row}
+          const long long rr = (long long)ky * nx + kx;
+          const T w = wo[rr];
+          const C<T> v = x[rr];
+          mr.add(w, v.r);
+          mi.add(w, v.i);
+        }
+      }
+    }
+    const T sr = mr.get(), si = mi.get();
     const C<T> o = y[row];
     y[row] = C<T>{o.r - tau * si, o.i + tau * sr};
   }
@@ -1159,7 +1234,10 @@ struct Apply {
   void apply(const C<T>* x, C<T>* y, double tau, const double* ebar) {
     kron(x, y, 0, tau, ebar);
     if (Wm) {  // i tau (V + variable-mass kinetic) through the assembled stencil
-      k_wapply<T, P><<<grid_for(r->N), TPB, 0, b->st>>>(Wm, x, y, r->n[0], r->n[1], (T)tau);
+      if (std::is_same<T, float>::value)
+        k_wapply_full<T, P><<<grid_for(r->N), TPB, 0, b->st>>>(Wm, x, y, r->n[0], r->n[1], (T)tau);
+      else
+        k_wapply<T, P><<<grid_for(r->N), TPB, 0, b->st>>>(Wm, x, y, r->n[0], r->n[1], (T)tau);
       return;
     }
     if (r->med.pot_kind != TDZ_POT_ZERO) quad(x, y, -1, 0, 0, 0.0, tau);  // i tau V
@@ -1598,12 +1676,13 @@ int stencil_setup_p(NdBatch* b, NdGeo& G, const AxisDev& ax, const AxisDev& ay, 
   const long long N = (long long)ax.n * ay.n;
   const size_t nf = (size_t)ay.Q * ax.n * W;
   const size_t nt = (size_t)ax.Q * ay.Q;
+  const size_t nh = (size_t)N * half_count(P);
   if (b->prec == TDZ_MIXED) {
-    G.W32 = static_cast<float*>(b->alloc(sizeof(float) * N * W * W));
-    G.Wx = static_cast<fx*>(b->alloc(sizeof(fx) * N * W * W));
+    G.W32 = static_cast<float*>(b->alloc(sizeof(float) * (size_t)N * W * W));
+    G.Wx = static_cast<fx*>(b->alloc(sizeof(fx) * nh));
     if (!G.W32 || !G.Wx) return TDZ_ENOMEM;
   } else {
-    G.W64 = static_cast<double*>(b->alloc(sizeof(double) * N * W * W));
+    G.W64 = static_cast<double*>(b->alloc(sizeof(double) * nh));
     if (!G.W64) return TDZ_ENOMEM;
   }
   double *F1 = nullptr, *F2 = nullptr, *fV = nullptr, *fK = nullptr;
@@ -1864,8 +1943,9 @@ int nd_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* o
   size_t stencil_bytes = 0;
   if (dim == 2)
     for (int g = 0; g < nops; ++g)
-      stencil_bytes += (size_t)geo[g].n[0] * geo[g].n[1] * (2 * P + 1) * (2 * P + 1) *
-                       (precision == TDZ_MIXED ? sizeof(fx) + sizeof(float) : sizeof(double));
+      stencil_bytes += (size_t)geo[g].n[0] * geo[g].n[1] *
+                       (precision == TDZ_MIXED ? half_count(P) * sizeof(fx) + (2 * P + 1) * (2 * P + 1) * sizeof(float)
+                                               : half_count(P) * sizeof(double));
   size_t free_b = 0, total_b = 0;
   cudaMemGetInfo(&free_b, &total_b);
   const bool want_stencil = dim == 2 && stencil_bytes < free_b / 2;
