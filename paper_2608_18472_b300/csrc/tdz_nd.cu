@@ -34,6 +34,8 @@
 #include <string>
 #include <type_traits>
 #include <vector>
+#include <atomic>
+#include <thread>
 
 #include "tdz_arith.cuh"
 #include "tdz_internal.h"
@@ -1037,6 +1039,13 @@ struct NdBatch {
   void* pre_D[3] = {nullptr, nullptr, nullptr};
   double* d_red = nullptr;  // reduction scratch (16 doubles)
   void* d_side = nullptr;   // chunk-boundary partial sums of the fused last-axis pass
+  size_t maxSide = 0;
+  int maxn = 0;
+  size_t work_bytes = 0;  // device bytes of one worker's work buffers
+  // batches of several runs: extra workers (own stream, cuBLAS handle and work buffers; geometry
+  // tables and run states shared with this batch) that propagate runs concurrently
+  std::vector<NdBatch*> workers;
+  bool own_stream = false;
   std::vector<double> obs;  // host copy [run][nsteps][2+3dim]
   long long last_nsteps = 0;
   double tol = 1e-12;
@@ -1053,8 +1062,10 @@ struct NdBatch {
     return p;
   }
   ~NdBatch() {
+    for (NdBatch* w : workers) delete w;
     if (blas) cublasDestroy(blas);
     for (void* p : bufs) cudaFree(p);
+    if (own_stream && st) cudaStreamDestroy(st);
   }
 };
 
@@ -1597,6 +1608,87 @@ int propagate_run(NdBatch* b, NdRun* r, const tdz::Ops& o, const double* field, 
   return TDZ_OK;
 }
 
+// work buffers of one worker, sized for the largest run of the batch (maxN, maxQ, maxSide, maxn set)
+bool alloc_work(NdBatch* b) {
+  const size_t z64 = sizeof(double2), maxN = b->maxN, maxQ = b->maxQ;
+  b->d_r0 = static_cast<double2*>(b->alloc(z64 * maxN));
+  b->d_y = static_cast<double2*>(b->alloc(z64 * maxN));
+  b->d_t1 = static_cast<double2*>(b->alloc(z64 * maxN));
+  b->d_t2 = static_cast<double2*>(b->alloc(z64 * maxN));
+  b->d_t3 = static_cast<double2*>(b->alloc(z64 * maxN));
+  b->d_t4 = static_cast<double2*>(b->alloc(z64 * maxN));
+  b->d_qa = static_cast<double2*>(b->alloc(z64 * maxQ));
+  b->d_qb = static_cast<double2*>(b->alloc(z64 * maxQ));
+  b->d_red = static_cast<double*>(b->alloc(sizeof(double) * 16));
+  b->d_side = b->alloc(sizeof(double2) * std::max<size_t>(b->maxSide, 1));
+  b->d_z = static_cast<double2*>(b->alloc(z64 * maxN));
+  b->d_p = static_cast<double2*>(b->alloc(z64 * maxN));
+  b->d_q = static_cast<double2*>(b->alloc(z64 * maxN));
+  b->d_rc = static_cast<double2*>(b->alloc(z64 * maxN));
+  bool ok = b->d_r0 && b->d_y && b->d_t1 && b->d_t2 && b->d_t3 && b->d_t4 && b->d_qa && b->d_qb && b->d_red &&
+            b->d_side && b->d_z && b->d_p && b->d_q && b->d_rc;
+  const size_t zs = b->prec == TDZ_MIXED ? sizeof(float2) : sizeof(double2);
+  for (int a = 0; a < 3; ++a) {
+    b->pre_L[a] = b->alloc(zs * (size_t)std::max(b->maxn, 1) * b->P);
+    b->pre_D[a] = b->alloc(zs * (size_t)std::max(b->maxn, 1));
+    ok = ok && b->pre_L[a] && b->pre_D[a];
+  }
+  if (b->prec == TDZ_MIXED) {
+    const size_t f = sizeof(float2);
+    void** w[] = {&b->w_x, &b->w_r, &b->w_z, &b->w_p, &b->w_q, &b->w_t1, &b->w_t2, &b->w_t3, &b->w_t4};
+    for (void** pp : w) {
+      *pp = b->alloc(f * maxN);
+      ok = ok && *pp;
+    }
+    b->w_qa = b->alloc(f * maxQ);
+    b->w_qb = b->alloc(f * maxQ);
+    ok = ok && b->w_qa && b->w_qb;
+  }
+  return ok;
+}
+
+// Extra workers for a batch of several runs (up to 8, within a quarter of the free device memory)
+int make_workers(NdBatch* b) {
+  const int want = std::min(b->nruns, 8) - 1;
+  if (want <= 0) return TDZ_OK;
+  size_t free_b = 0, total_b = 0;
+  cudaMemGetInfo(&free_b, &total_b);
+  const size_t per = b->work_bytes;
+  for (int k = 0; k < want && (size_t)(k + 1) * per < free_b / 4; ++k) {
+    NdBatch* w = new (std::nothrow) NdBatch;
+    if (!w) return TDZ_ENOMEM;
+    w->prec = b->prec;
+    w->dim = b->dim;
+    w->P = b->P;
+    w->nruns = 0;
+    w->geo = b->geo;
+    w->maxN = b->maxN;
+    w->maxQ = b->maxQ;
+    w->maxSide = b->maxSide;
+    w->maxn = b->maxn;
+    if (cudaStreamCreateWithFlags(&w->st, cudaStreamNonBlocking) != cudaSuccess) {
+      delete w;
+      return TDZ_ECUDA;
+    }
+    w->own_stream = true;
+    if (cublasCreate(&w->blas) != CUBLAS_STATUS_SUCCESS || cublasSetStream(w->blas, w->st) != CUBLAS_STATUS_SUCCESS) {
+      delete w;
+      return TDZ_ECUDA;
+    }
+    cublasSetEmulationStrategy(w->blas, CUBLAS_EMULATION_STRATEGY_EAGER);
+    if (!alloc_work(w)) {
+      delete w;
+      return TDZ_ENOMEM;
+    }
+    if (cudaStreamSynchronize(w->st) != cudaSuccess) {
+      delete w;
+      return TDZ_ECUDA;
+    }
+    b->workers.push_back(w);
+  }
+  return TDZ_OK;
+}
+
 MediumDev medium_dev(const Medium& m) {
   MediumDev d{};
   d.mass_kind = m.mass_kind;
@@ -1883,49 +1975,12 @@ int nd_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* o
   }
   b->maxN = maxN;
   b->maxQ = maxQ;
-  const size_t z64 = sizeof(double2);
-  b->d_r0 = static_cast<double2*>(b->alloc(z64 * maxN));
-  b->d_y = static_cast<double2*>(b->alloc(z64 * maxN));
-  b->d_t1 = static_cast<double2*>(b->alloc(z64 * maxN));
-  b->d_t2 = static_cast<double2*>(b->alloc(z64 * maxN));
-  b->d_t3 = static_cast<double2*>(b->alloc(z64 * maxN));
-  b->d_t4 = static_cast<double2*>(b->alloc(z64 * maxN));
-  b->d_qa = static_cast<double2*>(b->alloc(z64 * maxQ));
-  b->d_qb = static_cast<double2*>(b->alloc(z64 * maxQ));
-  b->d_red = static_cast<double*>(b->alloc(sizeof(double) * 16));
-  b->d_side = b->alloc(sizeof(double2) * std::max<size_t>(maxSide, 1));
-  b->d_z = static_cast<double2*>(b->alloc(z64 * maxN));
-  b->d_p = static_cast<double2*>(b->alloc(z64 * maxN));
-  b->d_q = static_cast<double2*>(b->alloc(z64 * maxN));
-  b->d_rc = static_cast<double2*>(b->alloc(z64 * maxN));
-  if (!b->d_z || !b->d_p || !b->d_q || !b->d_rc) {
-    delete b;
-    return TDZ_ENOMEM;
-  }
-  const size_t zs = precision == TDZ_MIXED ? sizeof(float2) : sizeof(double2);
-  for (int a = 0; a < 3; ++a) {
-    b->pre_L[a] = b->alloc(zs * (size_t)std::max(maxn, 1) * P);
-    b->pre_D[a] = b->alloc(zs * (size_t)std::max(maxn, 1));
-  }
-  if (precision == TDZ_MIXED) {
-    const size_t f = sizeof(float2);
-    b->w_x = b->alloc(f * maxN);
-    b->w_r = b->alloc(f * maxN);
-    b->w_z = b->alloc(f * maxN);
-    b->w_p = b->alloc(f * maxN);
-    b->w_q = b->alloc(f * maxN);
-    b->w_t1 = b->alloc(f * maxN);
-    b->w_t2 = b->alloc(f * maxN);
-    b->w_t3 = b->alloc(f * maxN);
-    b->w_t4 = b->alloc(f * maxN);
-    b->w_qa = b->alloc(f * maxQ);
-    b->w_qb = b->alloc(f * maxQ);
-    if (!b->w_qb) {
-      delete b;
-      return TDZ_ENOMEM;
-    }
-  }
-  if (!b->d_qb || !b->d_red || !b->d_side) {
+  b->maxSide = maxSide;
+  b->maxn = maxn;
+  const size_t before_work = b->dev_bytes;
+  const bool work_ok = alloc_work(b);
+  b->work_bytes = b->dev_bytes - before_work;
+  if (!work_ok) {
     delete b;
     set_error("tdz_batch_create: device allocation for 2-D/3-D work buffers failed");
     return TDZ_ENOMEM;
@@ -1994,6 +2049,12 @@ int nd_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* o
     delete b;
     return nd_cuda_fail(e, "tdz_batch_create (2-D/3-D)");
   }
+  const int rw = make_workers(b);
+  if (rw != TDZ_OK) {
+    delete b;
+    set_error("tdz_batch_create: creating the 2-D/3-D workers failed");
+    return rw;
+  }
   *out = b;
   return TDZ_OK;
 }
@@ -2025,26 +2086,74 @@ int nd_get_state(const NdBatch* b, int run, double* c, bool device) {
   return TDZ_OK;
 }
 
+static int propagate_one(NdBatch* w, NdBatch* b, int r, const double* field_host, double dt, long long step0,
+                         long long nsteps) {
+  const int D = b->dim, cols = 2 + 3 * D;
+  NdRun& R = b->runs[r];
+  const double* f = field_host + (size_t)r * (nsteps + 1) * D;
+  double* o = &b->obs[(size_t)r * nsteps * cols];
+  const Ops& ops = b->ops[R.ops];
+  switch (b->P) {
+    case 1: return propagate_run<1>(w, &R, ops, f, dt, step0, nsteps, o);
+    case 2: return propagate_run<2>(w, &R, ops, f, dt, step0, nsteps, o);
+    case 3: return propagate_run<3>(w, &R, ops, f, dt, step0, nsteps, o);
+    case 4: return propagate_run<4>(w, &R, ops, f, dt, step0, nsteps, o);
+    case 5: return propagate_run<5>(w, &R, ops, f, dt, step0, nsteps, o);
+    case 6: return propagate_run<6>(w, &R, ops, f, dt, step0, nsteps, o);
+    case 7: return propagate_run<7>(w, &R, ops, f, dt, step0, nsteps, o);
+    default: return propagate_run<8>(w, &R, ops, f, dt, step0, nsteps, o);
+  }
+}
+
+// Runs are independent: with workers, host threads take runs longest first from a shared counter,
+// each on its own worker (stream, handle, buffers); the call returns when all runs are done.
 int nd_propagate(NdBatch* b, const double* field_host, double dt, long long step0, long long nsteps) {
   const int D = b->dim;
   const int cols = 2 + 3 * D;
   b->obs.assign((size_t)b->nruns * nsteps * cols, 0.0);
-  for (int r = 0; r < b->nruns; ++r) {
-    NdRun& R = b->runs[r];
-    const double* f = field_host + (size_t)r * (nsteps + 1) * D;
-    int rc = TDZ_OK;
-    switch (b->P) {
-      case 1: rc = propagate_run<1>(b, &R, b->ops[R.ops], f, dt, step0, nsteps, &b->obs[(size_t)r * nsteps * cols]); break;
-      case 2: rc = propagate_run<2>(b, &R, b->ops[R.ops], f, dt, step0, nsteps, &b->obs[(size_t)r * nsteps * cols]); break;
-      case 3: rc = propagate_run<3>(b, &R, b->ops[R.ops], f, dt, step0, nsteps, &b->obs[(size_t)r * nsteps * cols]); break;
-      case 4: rc = propagate_run<4>(b, &R, b->ops[R.ops], f, dt, step0, nsteps, &b->obs[(size_t)r * nsteps * cols]); break;
-      case 5: rc = propagate_run<5>(b, &R, b->ops[R.ops], f, dt, step0, nsteps, &b->obs[(size_t)r * nsteps * cols]); break;
-      case 6: rc = propagate_run<6>(b, &R, b->ops[R.ops], f, dt, step0, nsteps, &b->obs[(size_t)r * nsteps * cols]); break;
-      case 7: rc = propagate_run<7>(b, &R, b->ops[R.ops], f, dt, step0, nsteps, &b->obs[(size_t)r * nsteps * cols]); break;
-      default: rc = propagate_run<8>(b, &R, b->ops[R.ops], f, dt, step0, nsteps, &b->obs[(size_t)r * nsteps * cols]); break;
+  const int nw = (int)std::min<size_t>(b->workers.size() + 1, (size_t)b->nruns);
+  if (nw <= 1) {
+    for (int r = 0; r < b->nruns; ++r) {
+      const int rc = propagate_one(b, b, r, field_host, dt, step0, nsteps);
+      if (rc != TDZ_OK) return rc;
     }
-    if (rc != TDZ_OK) return rc;
+    b->last_nsteps = nsteps;
+    return TDZ_OK;
   }
+  cudaError_t e = cudaStreamSynchronize(b->st);
+  if (e != cudaSuccess) return nd_cuda_fail(e, "tdz_propagate (2-D/3-D)");
+  for (NdBatch* w : b->workers) {  // solver settings may have changed since creation
+    w->tol = b->tol;
+    w->max_it = b->max_it;
+    w->inner_tol = b->inner_tol;
+    w->opt_precond = b->opt_precond;
+    w->opt_operator = b->opt_operator;
+  }
+  std::vector<int> order(b->nruns);
+  for (int r = 0; r < b->nruns; ++r) order[r] = r;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return b->runs[x].N > b->runs[y].N; });
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::atomic<int> next(0);
+  std::vector<int> rcs(nw, TDZ_OK);
+  std::vector<std::thread> th;
+  for (int t = 0; t < nw; ++t) {
+    th.emplace_back([&, t]() {
+      cudaSetDevice(dev);
+      NdBatch* w = t == 0 ? b : b->workers[t - 1];
+      for (int k = next++; k < b->nruns; k = next++) {
+        const int rc = propagate_one(w, b, order[k], field_host, dt, step0, nsteps);
+        if (rc != TDZ_OK) {
+          rcs[t] = rc;
+          break;
+        }
+      }
+      if (cudaStreamSynchronize(w->st) != cudaSuccess && rcs[t] == TDZ_OK) rcs[t] = TDZ_ECUDA;
+    });
+  }
+  for (auto& x : th) x.join();
+  for (int rc : rcs)
+    if (rc != TDZ_OK) return rc;
   b->last_nsteps = nsteps;
   return TDZ_OK;
 }
@@ -2109,5 +2218,9 @@ void nd_set_refinement(NdBatch* b, double tol, int max_it) {
 
 namespace tdz {
 int nd_dim(const NdBatch* b) { return b->dim; }
-size_t nd_device_bytes(const NdBatch* b) { return b->dev_bytes; }
+size_t nd_device_bytes(const NdBatch* b) {
+  size_t t = b->dev_bytes;
+  for (const NdBatch* w : b->workers) t += w->dev_bytes;
+  return t;
+}
 }  // namespace tdz
