@@ -224,7 +224,7 @@ def _gauss_state(knots, p, dim):
     return (c / np.linalg.norm(c)).astype(complex)
 
 
-def nd_legs(tdz, nsteps, which):
+def nd_legs(tdz, nsteps, which, n2d=1024, n3d=256):
     """2-D/3-D workloads beside the 1-D batch:
     softcore_atom_2d: V = -1/sqrt(r^2+0.5) on [-150,150]^2, 1024 order-7 splines per axis (1.04 M
       coefficients), 800 nm 1e14 W/cm^2 sin^2 pulse, dt = 0.05;
@@ -233,7 +233,7 @@ def nd_legs(tdz, nsteps, which):
       (0.3) 800 nm pulse, dt = 0.05."""
     out = {}
     if "2d" in which:
-        p, t = 7, wl.knots_for_nsplines(-150.0, 150.0, 1024, 7)
+        p, t = 7, wl.knots_for_nsplines(-150.0, 150.0, n2d, 7)
         ops = tdz.Ops([tdz.Basis(t, p, p + 1) for _ in range(2)], wl.softcore_medium(0.5))
         dt = 0.05
         f = wl.sin2_pulse(wl.time_grid(dt, nsteps + 1), wl.e0_from_intensity(1e14), wl.omega_from_nm(800.0), 4.0,
@@ -250,7 +250,7 @@ def nd_legs(tdz, nsteps, which):
                                          {"operator": "assembled stencil (variable mass + step potential)",
                                           "preconditioner": "fast diagonalisation, mean 1/m"})
     if "3d" in which:
-        p, t = 6, wl.knots_for_nsplines(-100.0, 100.0, 256, 6)
+        p, t = 6, wl.knots_for_nsplines(-100.0, 100.0, n3d, 6)
         ops = tdz.Ops([tdz.Basis(t, p, p + 1) for _ in range(3)], wl.softcore_medium(0.5))
         dt = 0.05
         f = wl.sin2_pulse(wl.time_grid(dt, nsteps + 1), 0.05, wl.omega_from_nm(800.0), 4.0, ellipticity=0.3, dim=3)
@@ -273,6 +273,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--nd-steps", type=int, default=2)
     ap.add_argument("--nd-legs", default="2d,dots,3d", help="comma list of 2d, dots, 3d (empty: none)")
+    ap.add_argument("--nd-2d-splines", type=int, default=1024, help="splines per axis of the 2-D atom")
+    ap.add_argument("--nd-3d-splines", type=int, default=256, help="splines per axis of the 3-D atom")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -407,7 +409,7 @@ def main():
     # ---------------- 2-D leg: the soft-core atom of the 2-D configuration (1024 x 1024 order-7 splines),
     # a few steps in both precisions (Kronecker + Gauss-point operator, preconditioned COCG)
     if rank == 0 and args.nd_steps > 0 and args.nd_legs:
-        line.update(nd_legs(tdz, args.nd_steps, args.nd_legs.split(",")))
+        line.update(nd_legs(tdz, args.nd_steps, args.nd_legs.split(","), args.nd_2d_splines, args.nd_3d_splines))
     if rank == 0 and not args.no_cpu:
         # bounded oracle sample sized to ~cpu_seconds; GPU mixed path compared on the same sample
         ns_probe = 20
