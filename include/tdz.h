@@ -96,8 +96,11 @@ typedef struct tdz_medium {
  *   V = <B|V|B>, D_a = <B|x_a|B> (potential/dipole element formulas),
  *   G_a = <B| m^-1 dV/dx_a |B>, K = <B| m^-1 |B>  (acceleration, Eq. pdm_acceleration),
  * with the Dirichlet end functions removed. 1-D results are symmetric band
- * matrices, half bandwidth = degree. dim = 1 only in this build (2-D/3-D
- * return TDZ_EUNSUPPORTED).
+ * matrices, half bandwidth = degree. For dim = 2, 3 the operators keep the
+ * per-axis 1-D factors S_a, T1_a = 1/2 <dB|dB>, D_a (Eq. tensor3d) and the
+ * quadrature tables; the non-separable terms are applied by the batch from the
+ * medium (one element per knot span and equal degrees are required, else
+ * TDZ_EUNSUPPORTED; layered and Quesne media are 1-D only).
  */
 typedef struct tdz_ops tdz_ops;
 #define TDZ_MAT_S  0
@@ -121,9 +124,11 @@ void tdz_ops_destroy(tdz_ops* ops);
 int  tdz_ground_state(const tdz_ops* ops, double* energy, double* c);
 
 /* ------------------------------------------------------------------ batch
- * A batch is a set of independent runs propagated together on one GPU (one
- * persistent launch per tdz_propagate call). Run r uses ops[ops_index[r]];
- * runs may have different sizes. precision is TDZ_FP64 or TDZ_MIXED.
+ * A batch is a set of independent runs propagated together on one GPU (1-D:
+ * one persistent launch per tdz_propagate call; 2-D/3-D: preconditioned COCG per
+ * step, runs of a batch on concurrent workers). Run r uses ops[ops_index[r]];
+ * runs may have different sizes; all operators of a batch have the same
+ * dimension and degree. precision is TDZ_FP64 or TDZ_MIXED.
  * cuda_stream: a cudaStream_t (NULL = the legacy default stream); every GPU
  * operation of the batch is enqueued on it. The batch owns its device memory
  * (allocated here with cudaMalloc, freed by tdz_batch_destroy).
@@ -138,6 +143,13 @@ int  tdz_batch_info(const tdz_batch* b, int* nruns, int64_t* total_dof, size_t* 
 int  tdz_set_state(tdz_batch* b, int run, const double* c);
 /* Copy the state of one run to c[2n], host or device. */
 int  tdz_get_state(const tdz_batch* b, int run, double* c);
+/* Set the states of all runs at once: c holds every run's coefficients (re, im interleaved) in
+ * run order, c[2 (off_r + i) + {0,1}] with off_r = n_0 + ... + n_{r-1}; host or device. One upload
+ * for the whole batch (a host array is staged in a device buffer allocated on first use, 16 bytes
+ * per coefficient, held until tdz_batch_destroy). Resets every run's history and status like
+ * tdz_set_state. Errors: TDZ_EINVAL, TDZ_ENONFINITE (a non-finite coefficient; the states are then
+ * undefined), TDZ_ECUDA. Synchronises the batch stream. */
+int  tdz_set_state_all(tdz_batch* b, const double* c);
 
 /* Mixed-precision refinement control: after each FP32 solve the step is accepted when
  * ||B_n c^n - A_n c^{n+1}|| <= tol ||S c^n||; at most max_solves FP32 solves per step
@@ -193,6 +205,10 @@ int  tdz_propagate(tdz_batch* b, const double* field, double dt, int64_t step0, 
  * run's status: TDZ_OK, TDZ_ENONFINITE or TDZ_ENOCONV (first failure wins).
  * Synchronises the batch stream. */
 int  tdz_observe(const tdz_batch* b, int run, double* out, int* status);
+/* Observables of all runs at once: out[nruns][nsteps][2+3*dim] (host or device, may be NULL) in the
+ * layout of tdz_observe for each run, status[nruns] (host, may be NULL). Synchronises the batch
+ * stream. */
+int  tdz_observe_all(const tdz_batch* b, double* out, int* status);
 /* Largest relative residual ||b - A c||/||b|| seen by the refinement of any run
  * (mixed precision; 0 for a 1-D TDZ_FP64 batch) and the total number of solves of
  * all runs, both since the batch was created. Synchronises the batch stream. */

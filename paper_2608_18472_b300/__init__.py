@@ -68,6 +68,8 @@ _sig = {
     "tdz_observe": (C.c_int, [_vp, C.c_int, _vp, C.POINTER(C.c_int)]),
     "tdz_refine_stats": (C.c_int, [_vp, _dp, _dp]),
     "tdz_batch_set_option": (C.c_int, [_vp, C.c_int, C.c_int]),
+    "tdz_set_state_all": (C.c_int, [_vp, _vp]),
+    "tdz_observe_all": (C.c_int, [_vp, _vp, C.POINTER(C.c_int)]),
     "tdz_krylov_stats": (C.c_int, [_vp, _dp]),
     "tdz_batch_destroy": (None, [_vp]),
 }
@@ -242,6 +244,23 @@ class Batch:
             _check(_lib.tdz_set_state(self._h, run, _vp(_ptr(buf))), "tdz_set_state")
         else:
             _check(_lib.tdz_set_state(self._h, run, _vp(_ptr(c))), "tdz_set_state")
+
+    def set_states(self, c):
+        """All runs at once: c = every run's coefficients concatenated in run order, as a complex numpy
+        array or an interleaved float64 array/tensor (host or device)."""
+        if isinstance(c, np.ndarray) and np.iscomplexobj(c):
+            buf = np.ascontiguousarray(np.stack([c.real, c.imag], axis=1).reshape(-1), dtype=np.float64)
+            _check(_lib.tdz_set_state_all(self._h, _vp(_ptr(buf))), "tdz_set_state_all")
+        else:
+            _check(_lib.tdz_set_state_all(self._h, _vp(_ptr(c))), "tdz_set_state_all")
+
+    def observe_all(self, out=None):
+        """Observables of all runs [nruns, nsteps, 2+3dim] and their statuses. Returns (array, statuses)."""
+        st = (C.c_int * self.nruns)()
+        if out is None:
+            out = np.zeros((self.nruns, self._last_nsteps, 2 + 3 * self.dim))
+        _check(_lib.tdz_observe_all(self._h, _vp(_ptr(out)), st), "tdz_observe_all")
+        return out, np.array(list(st))
 
     def get_state(self, run: int, out=None):
         if out is None:

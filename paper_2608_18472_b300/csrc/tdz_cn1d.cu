@@ -1081,6 +1081,44 @@ __global__ void __launch_bounds__(256) cn1d_kernel(StepArgs A) {
 
 }  // namespace tdz
 
+// ============================================================================ batched state upload
+// All runs' coefficients, natural order, concatenated in run order (re, im interleaved) -> each run's
+// chunk-interleaved state; padding rows zero; the mixed path's correction and difference history
+// are reset (like a per-run set_state). One block per run. *bad is set on a non-finite coefficient.
+template <bool MIXED>
+__global__ void k_set_states(const double* __restrict__ src, const long long* __restrict__ off, tdz::RunDev* runs,
+                             const tdz::GeomDev* __restrict__ geoms, int nruns, int* bad) {
+  for (int r = blockIdx.x; r < nruns; r += gridDim.x) {
+    const tdz::RunDev R = runs[r];
+    const tdz::GeomDev g = geoms[R.geom];
+    const long long base = off[r];
+    const long long rows = (long long)g.m * g.ks;
+    for (long long e = threadIdx.x; e < rows; e += blockDim.x) {
+      const int i = (int)(e / g.ks), k = (int)(e % g.ks);
+      const long long gi = (long long)k * g.m + i;
+      double re = 0.0, im = 0.0;
+      if (k < g.K && gi < g.n) {
+        re = src[2 * (base + gi)];
+        im = src[2 * (base + gi) + 1];
+        if (!isfinite(re) || !isfinite(im)) *bad = 1;
+      }
+      if constexpr (MIXED) {
+        const float rh = (float)re, ih = (float)im;
+        static_cast<float4*>(R.state)[e] = make_float4(rh, ih, (float)(re - (double)rh), (float)(im - (double)ih));
+        R.W[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+        R.d1[e] = make_float2(0.f, 0.f);
+        R.d2[e] = make_float2(0.f, 0.f);
+      } else {
+        static_cast<double2*>(R.state)[e] = make_double2(re, im);
+      }
+    }
+    if (threadIdx.x == 0) {
+      runs[r].status = TDZ_OK;
+      runs[r].hist = 0;
+    }
+  }
+}
+
 // ============================================================================ host side
 using namespace tdz;
 
@@ -1238,6 +1276,10 @@ struct tdz_batch {
   RunDev* d_runs = nullptr;
   std::vector<RunDev> h_runs;
   int* d_order = nullptr;  // schedule slots: run * 2 + sub, or -1
+  long long* d_off = nullptr;  // first coefficient of every run in a concatenated state vector
+  std::vector<long long> h_off;
+  double* d_stage = nullptr;   // staging for a host-side concatenated state (allocated on first use)
+  int* d_bad = nullptr;
   int nslots = 0;
   int* d_counter = nullptr;
   double* d_obs = nullptr;
@@ -1265,6 +1307,7 @@ struct tdz_batch {
     for (auto& b : bufs) cudaFree(b.p);
     if (d_obs) cudaFree(d_obs);
     if (d_field) cudaFree(d_field);
+    if (d_stage) cudaFree(d_stage);
   }
 };
 
@@ -1465,13 +1508,18 @@ int tdz_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* 
   b->nslots = (int)slots.size();
   b->d_order = static_cast<int*>(b->alloc(sizeof(int) * slots.size()));
   b->d_counter = static_cast<int*>(b->alloc(sizeof(int)));
-  if (!b->d_geoms || !b->d_runs || !b->d_order || !b->d_counter) {
+  b->d_off = static_cast<long long*>(b->alloc(sizeof(long long) * (nruns + 1)));
+  b->d_bad = static_cast<int*>(b->alloc(sizeof(int)));
+  b->h_off.assign(nruns + 1, 0);
+  for (int r = 0; r < nruns; ++r) b->h_off[r + 1] = b->h_off[r] + b->geo[ops_index[r]].n;
+  if (!b->d_geoms || !b->d_runs || !b->d_order || !b->d_counter || !b->d_off || !b->d_bad) {
     delete b;
     return TDZ_ENOMEM;
   }
   cudaMemcpyAsync(b->d_geoms, hg.data(), sizeof(GeomDev) * nops, cudaMemcpyHostToDevice, b->stream);
   cudaMemcpyAsync(b->d_runs, b->h_runs.data(), sizeof(RunDev) * nruns, cudaMemcpyHostToDevice, b->stream);
   cudaMemcpyAsync(b->d_order, slots.data(), sizeof(int) * slots.size(), cudaMemcpyHostToDevice, b->stream);
+  cudaMemcpyAsync(b->d_off, b->h_off.data(), sizeof(long long) * (nruns + 1), cudaMemcpyHostToDevice, b->stream);
   cudaError_t e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) {
     delete b;
@@ -1682,6 +1730,74 @@ int tdz_observe(const tdz_batch* b, int run, double* out, int* status) {
     e = cudaMemcpy(&st, &b->d_runs[run].status, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "tdz_observe");
     *status = st;
+  }
+  return TDZ_OK;
+}
+
+int tdz_set_state_all(tdz_batch* b, const double* c) {
+  if (!b || !c) return TDZ_EINVAL;
+  const bool dev = is_device_ptr(c);
+  if (b->nd) {
+    long long o = 0;
+    for (int r = 0; r < b->nruns; ++r) {
+      const int rc = tdz::nd_set_state(b->nd, r, c + 2 * o, dev);
+      if (rc != TDZ_OK) return rc;
+      o += tdz::nd_run_size(b->nd, r);
+    }
+    return TDZ_OK;
+  }
+  const size_t cnt = (size_t)2 * b->total_dof;
+  const double* src = c;
+  cudaError_t e = cudaSuccess;
+  if (!dev) {
+    if (!b->d_stage) {
+      e = cudaMalloc(&b->d_stage, sizeof(double) * cnt);
+      if (e != cudaSuccess) return cuda_fail(e, "tdz_set_state_all: staging buffer");
+    }
+    e = cudaMemcpyAsync(b->d_stage, c, sizeof(double) * cnt, cudaMemcpyHostToDevice, b->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "tdz_set_state_all: upload");
+    src = b->d_stage;
+  }
+  cudaMemsetAsync(b->d_bad, 0, sizeof(int), b->stream);
+  const int grid = std::min(b->nruns, 148 * 8);
+  if (b->prec == TDZ_MIXED)
+    k_set_states<true><<<grid, 256, 0, b->stream>>>(src, b->d_off, b->d_runs, b->d_geoms, b->nruns, b->d_bad);
+  else
+    k_set_states<false><<<grid, 256, 0, b->stream>>>(src, b->d_off, b->d_runs, b->d_geoms, b->nruns, b->d_bad);
+  int bad = 0;
+  e = cudaMemcpyAsync(&bad, b->d_bad, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "tdz_set_state_all");
+  if (bad) {
+    set_error("tdz_set_state_all: non-finite coefficient");
+    return TDZ_ENONFINITE;
+  }
+  return TDZ_OK;
+}
+
+int tdz_observe_all(const tdz_batch* b, double* out, int* status) {
+  if (!b) return TDZ_EINVAL;
+  if (b->nd) {
+    const int cols = 2 + 3 * tdz::nd_dim(b->nd);
+    const bool dev = out ? is_device_ptr(out) : false;
+    for (int r = 0; r < b->nruns; ++r) {
+      const int rc = tdz::nd_observe(b->nd, r, out ? out + (size_t)r * b->last_nsteps * cols : nullptr,
+                                     status ? status + r : nullptr, dev);
+      if (rc != TDZ_OK) return rc;
+    }
+    return TDZ_OK;
+  }
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "tdz_observe_all");
+  if (out && b->last_nsteps > 0) {
+    e = cudaMemcpy(out, b->d_obs, sizeof(double) * (size_t)b->nruns * b->last_nsteps * 5, cudaMemcpyDefault);
+    if (e != cudaSuccess) return cuda_fail(e, "tdz_observe_all");
+  }
+  if (status) {
+    std::vector<RunDev> r(b->nruns);
+    e = cudaMemcpy(r.data(), b->d_runs, sizeof(RunDev) * b->nruns, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "tdz_observe_all");
+    for (int k = 0; k < b->nruns; ++k) status[k] = r[k].status;
   }
   return TDZ_OK;
 }

@@ -209,3 +209,35 @@ def test_invalid_arguments_are_rejected(tdz):
     assert ei.value.code == tdz.TDZ_EINVAL
     with pytest.raises(tdz.TDZError):
         tdz.Batch([ops], [0], 7)
+
+
+def test_batched_state_upload_and_observables_match_per_run_calls(tdz):
+    """tdz_set_state_all / tdz_observe_all against tdz_set_state / tdz_observe on an uneven batch:
+    identical states (the device split of a coefficient into hi + lo rounds exactly as the host one)
+    and identical observables after propagation, in both precisions."""
+    wk = wl.dqw_batch(n_geometries=3, fields_per_geometry=2, nsplines_range=(500, 900), nsteps=20, seed=5)
+    ops = [tdz.assemble_1d(wk.runs[2 * g].knots, 6, wk.runs[2 * g].medium, 7) for g in range(3)]
+    run_ops = [r.geometry for r in wk.runs]
+    rng = np.random.default_rng(3)
+    c0 = [rng.standard_normal(ops[g].n) + 1j * rng.standard_normal(ops[g].n) for g in run_ops]
+    field = np.stack([r.field for r in wk.runs])
+    for prec in (tdz.FP64, tdz.MIXED):
+        a, b = tdz.Batch(ops, run_ops, prec), tdz.Batch(ops, run_ops, prec)
+        for i, c in enumerate(c0):
+            a.set_state(i, c)
+        b.set_states(np.concatenate(c0))
+        for i in range(len(c0)):
+            assert np.array_equal(a.get_state(i), b.get_state(i)), (prec, i)
+        a.propagate(field, wk.dt, 0, wk.nsteps)
+        b.propagate(field, wk.dt, 0, wk.nsteps)
+        obs_all, st_all = b.observe_all()
+        for i in range(len(c0)):
+            o, st = a.observe(i)
+            assert st == st_all[i] == tdz.TDZ_OK
+            assert np.array_equal(o, obs_all[i]), (prec, i)
+            assert np.array_equal(a.get_state(i), b.get_state(i)), (prec, i)
+    bad = np.concatenate(c0)
+    bad[7] = np.nan
+    with pytest.raises(tdz.TDZError) as ei:
+        b.set_states(bad)
+    assert ei.value.code == tdz.TDZ_ENONFINITE

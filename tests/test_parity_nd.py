@@ -166,3 +166,25 @@ def test_options_are_validated(tdz):
     with pytest.raises(tdz.TDZError) as ei:
         b.set_option(tdz.OPT_PRECOND, 7)
     assert ei.value.code == tdz.TDZ_EINVAL
+
+
+def test_batched_state_upload_and_observables_nd(tdz):
+    """The batched calls on a 2-D batch of two geometries equal the per-run calls."""
+    p, dt, nsteps = 3, 0.1, 3
+    ops = [tdz.Ops([tdz.Basis(wl.knots_for_nsplines(-6.0, 6.0, n, p), p, p + 1)] * 2, wl.softcore_medium(0.5))
+           for n in (16, 20)]
+    rng = np.random.default_rng(4)
+    c0 = [rng.standard_normal(o.n) + 1j * rng.standard_normal(o.n) for o in ops]
+    field = np.stack([wl.sin2_pulse(wl.time_grid(dt, nsteps), 0.1, 0.5, 1.0, dim=2)] * 2)
+    a, b = tdz.Batch(ops, [0, 1], tdz.FP64), tdz.Batch(ops, [0, 1], tdz.FP64)
+    for i, c in enumerate(c0):
+        a.set_state(i, c)
+    b.set_states(np.concatenate(c0))
+    a.propagate(field, dt, 0, nsteps)
+    b.propagate(field, dt, 0, nsteps)
+    obs_all, st_all = b.observe_all()
+    for i in range(2):
+        o, st = a.observe(i)
+        assert st == st_all[i] == tdz.TDZ_OK
+        assert np.allclose(o, obs_all[i], rtol=1e-12, atol=1e-14)
+        assert np.allclose(a.get_state(i), b.get_state(i), rtol=1e-12, atol=1e-14)
