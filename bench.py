@@ -207,12 +207,43 @@ def _nd_time(tdz, name, ops, run_ops, c0s, fields, dt, nsteps, extra):
                       "solves_per_run_step": (solves - solves0) / nsteps_runs, "device_gb": b.device_bytes / 1e9,
                       "create_s": t_create}
         states[label] = [b.get_state(i) for i in range(len(run_ops))]
+        if label == "mixed" and dim == 2:
+            res["fused_apply"] = _apply_roofline(tdz, b, ops, run_ops)
         del b
     num = sum(np.linalg.norm(x - y) ** 2 for x, y in zip(states["mixed"], states["fp64"]))
     den = sum(np.linalg.norm(y) ** 2 for y in states["fp64"])
     res["mixed_vs_fp64_rel_l2"] = float(np.sqrt(num / den))
     res["speedup_mixed"] = res["fp64"]["ms_per_step"] / res["mixed"]["ms_per_step"]
     return res
+
+
+def _apply_roofline(tdz, b, ops, run_ops):
+    """HBM roofline of the fused FP32 2-D apply for the largest geometry of the batch, from the
+    autotuner's CUDA-event timing (best of three, batch creation). Algorithmic bytes per apply: the
+    (2p+1)^2-point FP32 stencil (4 B per entry) plus x read and y written (8 B each per coefficient)."""
+    peaks = _measured_peaks()
+    g = max(set(run_ops), key=lambda k: ops[k].n)
+    groups, ms = b.tuning(g)
+    if not groups:
+        return None
+    p = ops[g].degree[0]
+    n = ops[g].n
+    nbytes = n * ((2 * p + 1) ** 2 * 4 + 16)
+    t = ms[groups] * 1e-3
+    ach = nbytes / t / 1e9
+    return {"kernel": f"k_apply2d_tma<{p},{groups}>", "coefficients": n, "bound": "hbm",
+            "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
+            "peak_source": peaks["source"], "algorithmic_bytes": nbytes, "ms_per_apply": ms[groups],
+            "variants_ms": {str(k): v for k, v in ms.items()}}
+
+
+def _measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6400.0, "source": "fallback"}
 
 
 def _gauss_state(knots, p, dim):

@@ -170,10 +170,15 @@ int  tdz_batch_set_refinement(tdz_batch* b, double tol, int max_solves);
  *   TDZ_OPERATOR_QUADRATURE  sum factorisation at the Gauss points, f(r) evaluated on the fly;
  *   TDZ_OPERATOR_STENCIL     2-D only: the same quadrature assembled once into a (2p+1)^2-point
  *                            stencil per DoF.
+ * TDZ_OPT_APPLY_GROUPS selects the variant of the fused FP32 2-D operator apply of mixed batches
+ * with a stencil (how many warps split the 2p+1 offsets dy of a row tile): 0 (default) = the
+ * variant the autotuner chose at tdz_batch_create, or 8 or 16 to force one. Results do not depend
+ * on it beyond FP32 rounding.
  * Both choices give the same A_n up to rounding. Errors: TDZ_EINVAL (unknown option or value),
  * TDZ_EUNSUPPORTED (the choice was not set up for this batch). */
 #define TDZ_OPT_PRECOND          1
 #define TDZ_OPT_OPERATOR         2
+#define TDZ_OPT_APPLY_GROUPS     3
 #define TDZ_PRECOND_AUTO         0
 #define TDZ_PRECOND_LINES        1
 #define TDZ_PRECOND_FD           2
@@ -181,6 +186,13 @@ int  tdz_batch_set_refinement(tdz_batch* b, double tol, int max_solves);
 #define TDZ_OPERATOR_QUADRATURE  1
 #define TDZ_OPERATOR_STENCIL     2
 int  tdz_batch_set_option(tdz_batch* b, int option, int value);
+/* Autotuner result for geometry `geometry` (index into the ops array of tdz_batch_create) of a
+ * 2-D mixed batch: at creation every variant of the fused FP32 operator apply is timed on the
+ * batch's own buffers (CUDA events, best of three) and the fastest is kept. groups (host, optional):
+ * the chosen variant (8 or 16; 0 when the geometry has no FP32 stencil or the batch is not 2-D
+ * mixed); ms (host, optional, 2 doubles): the measured ms per apply of the variants 8 and 16.
+ * Errors: TDZ_EINVAL (bad handle or geometry index). */
+int  tdz_batch_tuning(const tdz_batch* b, int geometry, int* groups, double* ms);
 /* Total Krylov iterations of all runs since the batch was created (2-D/3-D; 0 in 1-D, whose
  * solve is direct). Synchronises the batch stream. */
 int  tdz_krylov_stats(const tdz_batch* b, double* iterations);

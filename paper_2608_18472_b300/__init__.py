@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libtdz.so")
 
 TDZ_OK, TDZ_EINVAL, TDZ_ENOMEM, TDZ_ECUDA, TDZ_ENOCONV, TDZ_ENONFINITE, TDZ_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 FP64, MIXED = 0, 1
-OPT_PRECOND, OPT_OPERATOR = 1, 2
+OPT_PRECOND, OPT_OPERATOR, OPT_APPLY_GROUPS = 1, 2, 3
 PRECOND_AUTO, PRECOND_LINES, PRECOND_FD = 0, 1, 2
 OPERATOR_AUTO, OPERATOR_QUADRATURE, OPERATOR_STENCIL = 0, 1, 2
 MAT = {"S": 0, "T": 1, "V": 2, "H0": 3, "D": 4, "G": 5, "K": 6}
@@ -71,6 +71,7 @@ _sig = {
     "tdz_set_state_all": (C.c_int, [_vp, _vp]),
     "tdz_observe_all": (C.c_int, [_vp, _vp, C.POINTER(C.c_int)]),
     "tdz_krylov_stats": (C.c_int, [_vp, _dp]),
+    "tdz_batch_tuning": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int), _dp]),
     "tdz_batch_destroy": (None, [_vp]),
 }
 for _name, (_res, _args) in _sig.items():
@@ -292,8 +293,18 @@ class Batch:
         return mx.value, ns.value
 
     def set_option(self, option: int, value: int):
-        """2-D/3-D solver options: OPT_PRECOND (PRECOND_*) or OPT_OPERATOR (OPERATOR_*)."""
+        """2-D/3-D solver options: OPT_PRECOND (PRECOND_*), OPT_OPERATOR (OPERATOR_*) or
+        OPT_APPLY_GROUPS (0 = autotuned, 8 or 16: variant of the fused FP32 2-D apply)."""
         _check(_lib.tdz_batch_set_option(self._h, int(option), int(value)), "tdz_batch_set_option")
+
+    def tuning(self, geometry: int = 0):
+        """Autotuner result of a 2-D mixed batch for one geometry: (chosen variant of the fused FP32
+        apply, {variant: measured ms per apply}); (0, {}) where no FP32 stencil exists."""
+        g = C.c_int()
+        ms = np.zeros(2)
+        _check(_lib.tdz_batch_tuning(self._h, int(geometry), C.byref(g), ms.ctypes.data_as(_dp)),
+               "tdz_batch_tuning")
+        return g.value, ({8: float(ms[0]), 16: float(ms[1])} if g.value else {})
 
     def krylov_stats(self) -> float:
         """Total Krylov iterations of all runs since creation (0 for 1-D batches)."""

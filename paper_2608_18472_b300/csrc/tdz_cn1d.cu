@@ -1825,7 +1825,16 @@ int tdz_batch_set_option(tdz_batch* b, int option, int value) {
   if (b->nd) return tdz::nd_set_option(b->nd, option, value);
   if (option == TDZ_OPT_PRECOND && value >= TDZ_PRECOND_AUTO && value <= TDZ_PRECOND_FD) return TDZ_OK;
   if (option == TDZ_OPT_OPERATOR && value >= TDZ_OPERATOR_AUTO && value <= TDZ_OPERATOR_STENCIL) return TDZ_OK;
+  if (option == TDZ_OPT_APPLY_GROUPS && (value == 0 || value == 8 || value == 16)) return TDZ_OK;
   return TDZ_EINVAL;
+}
+
+int tdz_batch_tuning(const tdz_batch* b, int geometry, int* groups, double* ms) {
+  if (!b || geometry < 0) return TDZ_EINVAL;
+  if (b->nd) return tdz::nd_tuning(b->nd, geometry, groups, ms);
+  if (groups) *groups = 0;
+  if (ms) ms[0] = ms[1] = 0.0;
+  return TDZ_OK;
 }
 
 int tdz_krylov_stats(const tdz_batch* b, double* iterations) {

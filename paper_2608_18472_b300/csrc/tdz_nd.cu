@@ -26,6 +26,8 @@
 #include <cuda_runtime.h>
 #include <cusolverDn.h>
 
+#include <cstdint>
+
 #include <algorithm>
 #include <cmath>
 #include <complex>
@@ -697,6 +699,17 @@ __global__ void k_line_solve(C<T>* __restrict__ v, const C<T>* __restrict__ Lc, 
 }
 
 // ------------------------------------------------------------------------------- 2-D stencil operator
+// FP32 stencil tiles: kWtRows consecutive x-indices of one grid row iy (a tile never crosses a grid
+// row; the last tile of a row is zero padded), layout [tile][offset][row in tile] with tile index
+// iy * ceil(nx / kWtRows) + ix / kWtRows
+constexpr int kWtRows = 64;  // rows per stencil tile
+
+__host__ __device__ inline int wt_tiles_per_row(int nx) { return (nx + kWtRows - 1) / kWtRows; }
+__host__ __device__ inline size_t wt_index(int noff, int off, int ix, int iy, int nx) {
+  const size_t tile = (size_t)iy * wt_tiles_per_row(nx) + ix / kWtRows;
+  return (tile * noff + off) * kWtRows + (size_t)(ix % kWtRows);
+}
+
 // In 2-D the non-separable part of H (the potential and, for a position-dependent mass, the kinetic
 // term 1/2 <d_a B| m^-1 |d_a B>, Sec. "Parallel assembly") couples DoF (ix, iy) only with
 // (ix + dx, iy + dy), |dx|, |dy| <= P. It is assembled once, exactly as the Gauss-point quadrature
@@ -705,8 +718,9 @@ __global__ void k_line_solve(C<T>* __restrict__ v, const C<T>* __restrict__ Lc, 
 //   stage 1: F1[qy][dx][ix] = sum_{qx} w_x (fV B_ix B_jx + fK dB_ix dB_jx),
 //            F2[qy][dx][ix] = sum_{qx} w_x  fK B_ix B_jx                   (variable mass only)
 //   stage 2: W[(dy, dx)][iy nx + ix] = sum_{qy} w_y (B_iy B_jy F1 + dB_iy dB_jy F2),
-// with jx = ix + dx, jy = iy + dy. Layout [offset][row] so that a warp reads one offset of 32
-// consecutive rows in one transaction.
+// with jx = ix + dx, jy = iy + dy. Binary64 and double-float copies: symmetric half, layout
+// [offset][row], so that a warp reads one offset of 32 consecutive rows in one transaction. FP32
+// copy: the full stencil, tile-major (see the fused 2-D apply).
 __global__ void k_w_ftab(AxisDev ax, AxisDev ay, MediumT<double> M, int varmass, double* __restrict__ fV,
                          double* __restrict__ fK) {
   const long long total = (long long)ax.Q * ay.Q;
@@ -814,44 +828,12 @@ __global__ void k_w_stage2(AxisDev ax, AxisDev ay, int varmass, const double* __
       const int jy = iy + dy;
       const bool in = jx >= 0 && jx < ax.n && jy >= 0 && jy < ay.n;
       const double v = in ? s[dyi] : 0.0;
-      if (W32) W32[(size_t)(dyi * W + dxi) * N + row] = (float)v;  // full layout
+      if (W32) W32[wt_index(W * W, dyi * W + dxi, ix, iy, ax.n)] = (float)v;  // full stencil, tile-major
       if (dy < 0 || (dy == 0 && dx < 0)) continue;
       const size_t o = (size_t)half_off(P, dy, dx) * N + row;  // half layout
       if (W64) W64[o] = v;
       if (Wx) Wx[o] = fx(v);
     }
-  }
-}
-
-// y += i tau W x with the full stencil, layout [(dy + P)(2P + 1) + dx + P][row] (FP32 inner solve: a
-// straight stream of 225 coalesced loads per row is faster than the half layout's two-sided reads)
-template <class T, int P>
-__global__ void k_wapply_full(const T* __restrict__ Wm, const C<T>* __restrict__ x, C<T>* __restrict__ y, int nx,
-                              int ny, T tau) {
-  constexpr int W = 2 * P + 1;
-  const long long N = (long long)nx * ny;
-  for (long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x; row < N;
-       row += (long long)gridDim.x * blockDim.x) {
-    const int ix = (int)(row % nx), iy = (int)(row / nx);
-    Mac<T> mr, mi;
-    for (int dy = -P; dy <= P; ++dy) {
-      const int jy = iy + dy;
-      if (jy < 0 || jy >= ny) continue;
-      const T* wr = Wm + (size_t)(dy + P) * W * N + row;
-      const C<T>* xr = x + (long long)jy * nx;
-#pragma unroll
-      for (int dx = -P; dx <= P; ++dx) {
-        const int jx = ix + dx;
-        if (jx < 0 || jx >= nx) continue;
-        const T w = wr[(size_t)(dx + P) * N];
-        const C<T> v = xr[jx];
-        mr.add(w, v.r);
-        mi.add(w, v.i);
-      }
-    }
-    const T sr = mr.get(), si = mi.get();
-    const C<T> o = y[row];
-    y[row] = C<T>{o.r - tau * si, o.i + tau * sr};
   }
 }
 
@@ -892,6 +874,291 @@ __global__ void k_wapply(const T* __restrict__ Wm, const C<T>* __restrict__ x, C
     const T sr = mr.get(), si = mi.get();
     const C<T> o = y[row];
     y[row] = C<T>{o.r - tau * si, o.i + tau * sr};
+  }
+}
+
+// ------------------------------------------------------------------ fused 2-D apply (FP32 inner solve)
+// y = A_n x for a 2-D tensor basis in one pass over memory:
+//   A_n = S_y(x)(S_x + i tau K_x) + i tau K_y(x)S_x + i tau W,   K_a = cm T1_a + Ebar_a D_a,
+// i.e. the Kronecker terms of the separable operator (evaluated on the fly from per-axis coefficient
+// rows) plus the assembled non-separable stencil W. W is the only large operand (4 (2P+1)^2 bytes per
+// DoF); it is stored tile-major (tiles of kWtRows x-indices of one grid row), so that a tile is one
+// contiguous block that a single bulk TMA copy moves into shared memory. A persistent CTA streams
+// its tiles through a ring of stages (mbarrier completion, every wait bounded) with the copies of the
+// next tiles in flight, and stages the (2P+1) x (kWtRows + 2P) neighbourhood of x one tile ahead.
+
+// per-axis coefficient rows of the separable part: out[i][k] = {S(i, j), cm T1(i, j) + e D(i, j)},
+// j = i + k - P, k = 0..2P; zero where j is outside [0, n) and in the pad entry k = 2P + 1
+template <int P>
+__global__ void k_rowband(const float* __restrict__ S, const float* __restrict__ T1, const float* __restrict__ D,
+                          int n, float cm, float e, float2* __restrict__ out) {
+  constexpr int PW = 2 * P + 2;
+  const long long total = (long long)n * PW;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / PW), k = (int)(idx % PW);
+    const int d = k - P, j = i + d;
+    float2 v = make_float2(0.f, 0.f);
+    if (k <= 2 * P && j >= 0 && j < n) {
+      const size_t o = (size_t)(j > i ? j : i) * (P + 1) + (d < 0 ? -d : d);
+      v = make_float2(S[o], cm * T1[o] + e * D[o]);
+    }
+    out[idx] = v;
+  }
+}
+
+// ---- bulk-copy / mbarrier primitives (inline PTX, sm_90+ forms available on sm_103a)
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// contiguous global -> shared copy by the TMA unit; completion is signalled on the mbarrier
+// (addresses 16-byte aligned, size a multiple of 16)
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// wait for the phase with the given parity to complete; gives up after `limit` SM cycles
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, long long limit) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > limit) return false;
+  return true;
+}
+constexpr long long kWaitLimit = 4000000000LL;  // about 2 s at the maximum SM clock
+
+template <int P, int G>
+struct Apply2dCfg {
+  static constexpr int W = 2 * P + 1;
+  static constexpr int NOFF = W * W;
+  static constexpr int R = kWtRows;
+  static constexpr int HW = R + 2 * P;                 // halo width (x-indices) of a tile
+  static constexpr int PW = 2 * P + 2;                 // coefficient row length (float2)
+  static constexpr int XH = W * HW;                    // float2: (2P+1) rows of x around the tile
+  static constexpr int CB = R * PW;                    // float2: coefficient rows of the tile's x-indices
+  // per tile, one buffer: x halo, then the x-axis coefficient rows as [j][row parity][row / 2] float4
+  // (conflict-free when lane l reads rows 2l and 2l + 1), then the y-axis coefficient row of iy
+  static constexpr int HALO_BYTES = (XH + CB + PW) * 8;
+  static constexpr int STAGE_BYTES = NOFF * R * 4;
+  static constexpr int RED_BYTES = 2 * (G - 1) * R * 8;
+  static constexpr int FIXED = RED_BYTES + 2 * HALO_BYTES + 64;
+  static constexpr int NST = (3 * STAGE_BYTES + FIXED <= 227 * 1024) ? 3 : 2;
+  static constexpr int THREADS = 32 * G;               // one warp per group; a lane owns two rows
+  static constexpr size_t SMEM = (size_t)NST * STAGE_BYTES + RED_BYTES + 2 * HALO_BYTES + 8 * NST;
+};
+
+// cp.async of one float2 into shared memory, zero-filled when `in` is false (nothing is read then)
+__device__ __forceinline__ void cp_async8(uint32_t dst, const float2* src, bool in) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(in ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool in) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(in ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// packed FP32 pair: d = a * b + c on both lanes (one f32x2 instruction)
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+      "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+__device__ __forceinline__ float2 splat(float a) { return make_float2(a, a); }
+
+// Everything a tile (iy, bx) reads besides its stencil block, into one shared buffer h:
+//   h[(dy + P) * HW + c] = x(iy + dy, bx * R - P + c)   (zero outside the grid),
+//   x-axis coefficient rows of ix = bx * R + row (zero beyond nx) at XH as float4 [j][row & 1][row / 2],
+//   the y-axis coefficient row of iy at XH + CB.
+template <int P, int G>
+__device__ __forceinline__ void load_halo(float2* h, const float2* __restrict__ x, const float2* __restrict__ xb,
+                                          const float2* __restrict__ yb, int iy, int bx, int nx, int ny) {
+  using Cfg = Apply2dCfg<P, G>;
+  constexpr int HW = Cfg::HW, HE = Cfg::XH, R = Cfg::R, PW = Cfg::PW, NJ = PW / 2;
+  const int jx0 = bx * R - P;
+  for (int e = threadIdx.x; e < HE; e += Cfg::THREADS) {
+    const int jy = iy + e / HW - P, jx = jx0 + e % HW;
+    const bool in = jy >= 0 && jy < ny && jx >= 0 && jx < nx;
+    cp_async8(smem_addr(h + e), in ? x + (long long)jy * nx + jx : x, in);
+  }
+  float4* cb = reinterpret_cast<float4*>(h + HE);
+  for (int e = threadIdx.x; e < R * NJ; e += Cfg::THREADS) {
+    const int row = e / NJ, j = e % NJ, ix = bx * R + row;
+    const bool in = ix < nx;
+    cp_async16(smem_addr(cb + (j * 2 + (row & 1)) * (R / 2) + row / 2), in ? xb + (size_t)ix * PW + 2 * j : xb, in);
+  }
+  for (int e = threadIdx.x; e < NJ; e += Cfg::THREADS)
+    cp_async16(smem_addr(reinterpret_cast<float4*>(h + HE + Cfg::CB) + e), yb + (size_t)iy * PW + 2 * e, true);
+  cp_async_commit();
+}
+
+// Offsets dy0 .. dy0 + PER - 1 of the two rows rl, rl + 1 of a lane (h: halo at column rl, w: stage
+// at row rl). Per row and dy: a_S += S_y u_S and a_T += S_y u_K + K_y u_S + u_W, with u_S, u_K, u_W
+// the sums over dx of S_x x, K_x x and W x along grid row jy = iy + dy of x (zero outside the grid,
+// so no bounds checks). The 2P+2 halo values of both rows come as float4 loads, W of both rows as
+// one float2 per offset; complex-times-real products are packed f32x2 FMAs.
+template <int P, int G, int PER>
+__device__ __forceinline__ void stencil_pair(const float2* h, const float* w, const float2* cyv,
+                                             const float2 (&b0)[2 * P + 2], const float2 (&b1)[2 * P + 2], int dy0,
+                                             float2 (&aS)[2], float2 (&aT)[2]) {
+  using Cfg = Apply2dCfg<P, G>;
+  constexpr int W = 2 * P + 1, R = kWtRows, HW = Cfg::HW, PW = 2 * P + 2;
+#pragma unroll
+  for (int t = 0; t < PER; ++t) {
+    const int dy = dy0 + t;
+    if (dy > P) break;
+    const float2 cy = cyv[t];
+    const float4* xr4 = reinterpret_cast<const float4*>(h + (dy + P) * HW);
+    float2 xv[PW];
+#pragma unroll
+    for (int j = 0; j < PW / 2; ++j) {
+      const float4 v = xr4[j];
+      xv[2 * j] = make_float2(v.x, v.y);
+      xv[2 * j + 1] = make_float2(v.z, v.w);
+    }
+    const float2* wr = reinterpret_cast<const float2*>(w + (dy + P) * W * R);
+    float2 uS0 = splat(0.f), uK0 = splat(0.f), uW0 = splat(0.f), uS1 = splat(0.f), uK1 = splat(0.f),
+           uW1 = splat(0.f);
+#pragma unroll
+    for (int d = 0; d < W; ++d) {
+      const float2 wd = wr[d * (R / 2)];  // {W(row rl), W(row rl + 1)} at offset d
+      uS0 = ffma2(splat(b0[d].x), xv[d], uS0);
+      uK0 = ffma2(splat(b0[d].y), xv[d], uK0);
+      uW0 = ffma2(splat(wd.x), xv[d], uW0);
+      uS1 = ffma2(splat(b1[d].x), xv[d + 1], uS1);
+      uK1 = ffma2(splat(b1[d].y), xv[d + 1], uK1);
+      uW1 = ffma2(splat(wd.y), xv[d + 1], uW1);
+    }
+    aS[0] = ffma2(splat(cy.x), uS0, aS[0]);
+    aS[1] = ffma2(splat(cy.x), uS1, aS[1]);
+    aT[0] = ffma2(splat(cy.x), uK0, ffma2(splat(cy.y), uS0, make_float2(aT[0].x + uW0.x, aT[0].y + uW0.y)));
+    aT[1] = ffma2(splat(cy.x), uK1, ffma2(splat(cy.y), uS1, make_float2(aT[1].x + uW1.x, aT[1].y + uW1.y)));
+  }
+}
+
+// One warp per group g of offsets dy; lane l owns rows rl = 2l, 2l + 1 of the tile. Group 0 adds
+// up the G partial sums (double-buffered in shared memory by tile parity, so one barrier per tile
+// suffices). Per tile: the stencil block arrives by bulk copy (ring of NST stages, issued NST tiles
+// ahead), the x halo by zero-filling cp.async (one tile ahead). err: set to 1 if a stencil copy did
+// not complete in time.
+template <int P, int G>
+__global__ void __launch_bounds__(32 * G, 1)
+    k_apply2d_tma(const float* __restrict__ Wt, long long ntiles, const float2* __restrict__ x, float2* __restrict__ y,
+                  const float2* __restrict__ xb, const float2* __restrict__ yb, int nx, int ny, float tau,
+                  int* __restrict__ err) {
+  using Cfg = Apply2dCfg<P, G>;
+  constexpr int R = Cfg::R, NST = Cfg::NST, PW = 2 * P + 2;
+  constexpr int PER = (2 * P + 1 + G - 1) / G;  // offsets dy per group
+  extern __shared__ __align__(128) unsigned char smem[];
+  float* stages = reinterpret_cast<float*>(smem);
+  float2* red = reinterpret_cast<float2*>(smem + (size_t)NST * Cfg::STAGE_BYTES);
+  float2* halo = reinterpret_cast<float2*>(smem + (size_t)NST * Cfg::STAGE_BYTES + Cfg::RED_BYTES);
+  uint64_t* bars =
+      reinterpret_cast<uint64_t*>(smem + (size_t)NST * Cfg::STAGE_BYTES + Cfg::RED_BYTES + 2 * Cfg::HALO_BYTES);
+  const int tid = threadIdx.x;
+  const int rl = 2 * (tid & 31);
+  const int g = tid >> 5;
+  const int dy0 = g * PER - P;
+  const int tpr = wt_tiles_per_row(nx);
+  const long long mine = (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x;  // tiles of this CTA
+  if (tid == 0) {
+    for (int s = 0; s < NST; ++s) mbar_init(smem_addr(&bars[s]), 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  if (tid == 0)
+    for (int s = 0; s < NST && s < mine; ++s) {
+      const long long t = blockIdx.x + (long long)s * gridDim.x;
+      mbar_expect_tx(smem_addr(&bars[s]), Cfg::STAGE_BYTES);
+      bulk_load(smem_addr(stages + (size_t)s * (Cfg::STAGE_BYTES / 4)), Wt + (size_t)t * (Cfg::STAGE_BYTES / 4),
+                Cfg::STAGE_BYTES, smem_addr(&bars[s]));
+    }
+  if (mine > 0) load_halo<P, G>(halo, x, xb, yb, (int)(blockIdx.x / tpr), (int)(blockIdx.x % tpr), nx, ny);
+  for (long long k = 0; k < mine; ++k) {
+    const int s = (int)(k % NST);
+    const bool ok = mbar_wait_bounded(smem_addr(&bars[s]), (uint32_t)((k / NST) & 1), kWaitLimit);
+    cp_async_wait_all();  // this thread's halo copies of tile k
+    if (__syncthreads_or(!ok)) {
+      // give up: report, then let the copies still in flight land (bounded) before leaving
+      if (tid == 0) {
+        atomicExch(err, 1);
+        for (long long j = k; j < mine && j < k + NST; ++j)
+          mbar_wait_bounded(smem_addr(&bars[j % NST]), (uint32_t)((j / NST) & 1), kWaitLimit);
+      }
+      __syncthreads();
+      return;
+    }
+    const long long tile = blockIdx.x + k * gridDim.x;
+    const int iy = (int)(tile / tpr), bxi = (int)(tile % tpr);
+    if (k + 1 < mine) {  // halo of the next tile into the other buffer (last read two tiles ago)
+      const long long tn = tile + gridDim.x;
+      load_halo<P, G>(halo + (size_t)((k + 1) & 1) * (Cfg::HALO_BYTES / 8), x, xb, yb, (int)(tn / tpr),
+                      (int)(tn % tpr), nx, ny);
+    }
+    const int ix = bxi * R + rl;  // rows ix, ix + 1
+    float2 aS[2] = {splat(0.f), splat(0.f)}, aT[2] = {splat(0.f), splat(0.f)};
+    if (ix < nx) {
+      const float2* hb = halo + (size_t)(k & 1) * (Cfg::HALO_BYTES / 8);
+      const float4* cb = reinterpret_cast<const float4*>(hb + Cfg::XH);  // rows ix, ix + 1 (zero beyond nx)
+      float2 b0[PW], b1[PW];
+#pragma unroll
+      for (int j = 0; j < PW / 2; ++j) {
+        const float4 v0 = cb[(2 * j) * (R / 2) + (tid & 31)], v1 = cb[(2 * j + 1) * (R / 2) + (tid & 31)];
+        b0[2 * j] = make_float2(v0.x, v0.y);
+        b0[2 * j + 1] = make_float2(v0.z, v0.w);
+        b1[2 * j] = make_float2(v1.x, v1.y);
+        b1[2 * j + 1] = make_float2(v1.z, v1.w);
+      }
+      const float2* by = hb + Cfg::XH + Cfg::CB;
+      float2 cyv[PER];
+#pragma unroll
+      for (int t = 0; t < PER; ++t) {  // {S_y, K_y}(iy, iy + dy): zero where iy + dy is outside the grid
+        const int dy = dy0 + t;
+        cyv[t] = dy <= P ? by[dy + P] : splat(0.f);
+      }
+      const float* w = stages + (size_t)s * (Cfg::STAGE_BYTES / 4) + rl;
+      stencil_pair<P, G, PER>(hb + rl, w, cyv, b0, b1, dy0, aS, aT);
+    }
+    float4 part = make_float4(aS[0].x - tau * aT[0].y, aS[0].y + tau * aT[0].x, aS[1].x - tau * aT[1].y,
+                              aS[1].y + tau * aT[1].x);
+    float4* rb = reinterpret_cast<float4*>(red + (size_t)(k & 1) * (G - 1) * R);
+    if (g > 0) rb[(g - 1) * (R / 2) + (tid & 31)] = part;
+    __syncthreads();  // stage s and halo k consumed, partial sums visible
+    if (tid == 0 && k + NST < mine) {
+      const long long t = tile + (long long)NST * gridDim.x;
+      mbar_expect_tx(smem_addr(&bars[s]), Cfg::STAGE_BYTES);
+      bulk_load(smem_addr(stages + (size_t)s * (Cfg::STAGE_BYTES / 4)), Wt + (size_t)t * (Cfg::STAGE_BYTES / 4),
+                Cfg::STAGE_BYTES, smem_addr(&bars[s]));
+    }
+    if (g == 0 && ix < nx) {
+#pragma unroll
+      for (int hh = 0; hh < G - 1; ++hh) {
+        const float4 o = rb[hh * (R / 2) + (tid & 31)];
+        part.x += o.x;
+        part.y += o.y;
+        part.z += o.z;
+        part.w += o.w;
+      }
+      float2* yr = y + (long long)iy * nx + ix;
+      yr[0] = make_float2(part.x, part.y);
+      if (ix + 1 < nx) yr[1] = make_float2(part.z, part.w);
+    }
   }
 }
 
@@ -1010,6 +1277,8 @@ struct NdGeo {
   float* W32 = nullptr;   // mixed: inner FP32 solve
   fx* Wx = nullptr;       // mixed: double-float residual
   bool has_stencil() const { return W64 || W32; }
+  int apply_groups = 8;  // variant of the fused FP32 2-D apply (groups of offsets dy per row)
+  float tune_ms[2] = {0.f, 0.f};  // autotuner timings of the variants G = 8, 16 (ms per apply)
   // 3-D mixed: w V at the Gauss points ([q_z][q_y][q_x]) for the FP32 and double-float passes
   float* Vq32 = nullptr;
   fx* Vqx = nullptr;
@@ -1027,6 +1296,7 @@ struct NdBatch {
   cublasHandle_t blas = nullptr;
   int opt_precond = TDZ_PRECOND_AUTO;
   int opt_operator = TDZ_OPERATOR_AUTO;
+  int opt_groups = 0;  // fused 2-D apply variant: 0 = the autotuned one, else 8 or 16 groups
   std::vector<void*> bufs;
   // work vectors sized for the largest run: binary64 and solve precision
   size_t maxN = 0, maxQ = 0;
@@ -1038,6 +1308,13 @@ struct NdBatch {
   void* pre_L[3] = {nullptr, nullptr, nullptr};  // per run would be needed for different sizes; refreshed per run
   void* pre_D[3] = {nullptr, nullptr, nullptr};
   double* d_red = nullptr;  // reduction scratch (16 doubles)
+  int* d_err = nullptr;     // set to nonzero by a kernel whose bounded wait ran out
+  // coefficient rows {S, K} of the separable part for the fused FP32 2-D apply (x and y axes), and
+  // what they were computed for: geometry, Ebar_x, Ebar_y, constant-mass m^-1
+  float2* rb32[2] = {nullptr, nullptr};
+  int rb_geo = -1;
+  double rb_key[3] = {0, 0, 0};
+  int nsm = 148;  // SM count of the device (persistent grids)
   void* d_side = nullptr;   // chunk-boundary partial sums of the fused last-axis pass
   size_t maxSide = 0;
   int maxn = 0;
@@ -1074,6 +1351,107 @@ struct NdBatch {
 namespace {
 
 // ---------------------------------------------------------------- operator application (templated)
+// y = A_n x through the fused TMA-fed 2-D kernel (FP32) with G groups of offsets dy per row
+template <int P, int G>
+void launch_apply2d(NdBatch* b, const NdRun* r, const float* Wt, const float2* x, float2* y, double tau) {
+  using Cfg = Apply2dCfg<P, G>;
+  cudaFuncSetAttribute(k_apply2d_tma<P, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
+  const long long ntiles = (long long)r->n[1] * wt_tiles_per_row(r->n[0]);
+  const int grid = (int)std::min<long long>(ntiles, b->nsm);
+  k_apply2d_tma<P, G><<<grid, Cfg::THREADS, Cfg::SMEM, b->st>>>(Wt, ntiles, x, y, b->rb32[0], b->rb32[1], r->n[0],
+                                                                r->n[1], (float)tau, b->d_err);
+}
+
+// refresh the per-axis coefficient rows when the geometry or the field changed, then one
+// persistent launch over the stencil tiles in the variant chosen for this geometry
+template <int P>
+void apply2d_fused(NdBatch* b, NdRun* r, const float* Wt, const C<float>* x, C<float>* y, double tau,
+                   const double* ebar) {
+  constexpr int PW = 2 * P + 2;
+  const double cm = r->const_mass ? r->cm : 0.0;
+  if (b->rb_geo != r->geo || b->rb_key[0] != ebar[0] || b->rb_key[1] != ebar[1] || b->rb_key[2] != cm) {
+    for (int a = 0; a < 2; ++a) {
+      const AxisDev& A = r->ax[a];
+      k_rowband<P><<<grid_for((long long)A.n * PW), TPB, 0, b->st>>>(A.fS, A.fT1, A.fD, A.n, (float)cm,
+                                                                    (float)ebar[a], b->rb32[a]);
+    }
+    b->rb_geo = r->geo;
+    b->rb_key[0] = ebar[0];
+    b->rb_key[1] = ebar[1];
+    b->rb_key[2] = cm;
+  }
+  const float2* xv = reinterpret_cast<const float2*>(x);
+  float2* yv = reinterpret_cast<float2*>(y);
+  const int groups = b->opt_groups ? b->opt_groups : b->geo[r->geo].apply_groups;
+  if (groups == 16) launch_apply2d<P, 16>(b, r, Wt, xv, yv, tau);
+  else launch_apply2d<P, 8>(b, r, Wt, xv, yv, tau);
+}
+
+// Autotuner of the fused FP32 2-D apply: every variant is timed on this batch's own work buffers
+// (CUDA events on the batch stream, one warm-up launch, then the best of three) for the first run
+// of each geometry with a stencil, and the fastest is kept for that geometry.
+template <int P>
+int autotune_apply2d(NdBatch* b) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return TDZ_ECUDA;
+  }
+  const int cand[2] = {8, 16};
+  const double zero[3] = {0.0, 0.0, 0.0};
+  const double tau = 0.025;
+  int rc = TDZ_OK;
+  for (size_t g = 0; g < b->geo.size() && rc == TDZ_OK; ++g) {
+    NdGeo& G = b->geo[g];
+    NdRun* r = nullptr;
+    for (auto& run : b->runs)
+      if (run.geo == (int)g) {
+        r = &run;
+        break;
+      }
+    if (!G.W32 || !r) continue;
+    const C<float>* x = static_cast<const C<float>*>(b->w_p);
+    C<float>* y = static_cast<C<float>*>(b->w_q);
+    float best = 0.f;
+    for (int c = 0; c < 2; ++c) {
+      G.apply_groups = cand[c];
+      apply2d_fused<P>(b, r, G.W32, x, y, tau, zero);
+      float tmin = 0.f;
+      for (int k = 0; k < 3; ++k) {
+        cudaEventRecord(e0, b->st);
+        apply2d_fused<P>(b, r, G.W32, x, y, tau, zero);
+        cudaEventRecord(e1, b->st);
+        float ms = 0.f;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+          rc = TDZ_ECUDA;
+          break;
+        }
+        tmin = k == 0 ? ms : std::min(tmin, ms);
+      }
+      G.tune_ms[c] = tmin;
+      if (c == 0 || tmin < best) best = tmin;
+    }
+    G.apply_groups = G.tune_ms[1] < G.tune_ms[0] ? 16 : 8;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->rb_geo = -1;
+  return rc;
+}
+
+int autotune(NdBatch* b) {
+  switch (b->P) {
+    case 1: return autotune_apply2d<1>(b);
+    case 2: return autotune_apply2d<2>(b);
+    case 3: return autotune_apply2d<3>(b);
+    case 4: return autotune_apply2d<4>(b);
+    case 5: return autotune_apply2d<5>(b);
+    case 6: return autotune_apply2d<6>(b);
+    case 7: return autotune_apply2d<7>(b);
+    default: return autotune_apply2d<8>(b);
+  }
+}
+
 template <class T, int P>
 struct Apply {
   NdBatch* b;
@@ -1243,12 +1621,15 @@ struct Apply {
 
   // y = A_n x
   void apply(const C<T>* x, C<T>* y, double tau, const double* ebar) {
+    if constexpr (std::is_same<T, float>::value) {
+      if (Wm && r->dim == 2) {  // FP32 2-D with the stencil: one fused pass (Kronecker terms + W)
+        apply2d_fused<P>(b, r, Wm, x, y, tau, ebar);
+        return;
+      }
+    }
     kron(x, y, 0, tau, ebar);
-    if (Wm) {  // i tau (V + variable-mass kinetic) through the assembled stencil
-      if (std::is_same<T, float>::value)
-        k_wapply_full<T, P><<<grid_for(r->N), TPB, 0, b->st>>>(Wm, x, y, r->n[0], r->n[1], (T)tau);
-      else
-        k_wapply<T, P><<<grid_for(r->N), TPB, 0, b->st>>>(Wm, x, y, r->n[0], r->n[1], (T)tau);
+    if (Wm) {  // i tau (V + variable-mass kinetic) through the assembled stencil (half storage)
+      k_wapply<T, P><<<grid_for(r->N), TPB, 0, b->st>>>(Wm, x, y, r->n[0], r->n[1], (T)tau);
       return;
     }
     if (r->med.pot_kind != TDZ_POT_ZERO) quad(x, y, -1, 0, 0, 0.0, tau);  // i tau V
@@ -1605,12 +1986,23 @@ int propagate_run(NdBatch* b, NdRun* r, const tdz::Ops& o, const double* field, 
   }
   cudaError_t e = cudaStreamSynchronize(b->st);
   if (e != cudaSuccess) return nd_cuda_fail(e, "tdz_propagate (2-D/3-D)");
+  int werr = 0;
+  e = cudaMemcpy(&werr, b->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return nd_cuda_fail(e, "tdz_propagate (2-D/3-D)");
+  if (werr != 0) {
+    cudaMemsetAsync(b->d_err, 0, sizeof(int), b->st);
+    cudaStreamSynchronize(b->st);
+    r->status = TDZ_ECUDA;
+    set_error("tdz_propagate (2-D): a stencil tile copy did not complete within the wait limit");
+    return TDZ_ECUDA;
+  }
   return TDZ_OK;
 }
 
 // work buffers of one worker, sized for the largest run of the batch (maxN, maxQ, maxSide, maxn set)
 bool alloc_work(NdBatch* b) {
   const size_t z64 = sizeof(double2), maxN = b->maxN, maxQ = b->maxQ;
+  bool ok = true;
   b->d_r0 = static_cast<double2*>(b->alloc(z64 * maxN));
   b->d_y = static_cast<double2*>(b->alloc(z64 * maxN));
   b->d_t1 = static_cast<double2*>(b->alloc(z64 * maxN));
@@ -1620,12 +2012,19 @@ bool alloc_work(NdBatch* b) {
   b->d_qa = static_cast<double2*>(b->alloc(z64 * maxQ));
   b->d_qb = static_cast<double2*>(b->alloc(z64 * maxQ));
   b->d_red = static_cast<double*>(b->alloc(sizeof(double) * 16));
+  b->d_err = static_cast<int*>(b->alloc(sizeof(int) * 4));
+  ok = ok && b->d_err;
+  if (b->prec == TDZ_MIXED && b->dim == 2)
+    for (int a = 0; a < 2; ++a) {
+      b->rb32[a] = static_cast<float2*>(b->alloc(sizeof(float2) * (size_t)std::max(b->maxn, 1) * (2 * b->P + 2)));
+      ok = ok && b->rb32[a];
+    }
   b->d_side = b->alloc(sizeof(double2) * std::max<size_t>(b->maxSide, 1));
   b->d_z = static_cast<double2*>(b->alloc(z64 * maxN));
   b->d_p = static_cast<double2*>(b->alloc(z64 * maxN));
   b->d_q = static_cast<double2*>(b->alloc(z64 * maxN));
   b->d_rc = static_cast<double2*>(b->alloc(z64 * maxN));
-  bool ok = b->d_r0 && b->d_y && b->d_t1 && b->d_t2 && b->d_t3 && b->d_t4 && b->d_qa && b->d_qb && b->d_red &&
+  ok = ok && b->d_r0 && b->d_y && b->d_t1 && b->d_t2 && b->d_t3 && b->d_t4 && b->d_qa && b->d_qb && b->d_red &&
             b->d_side && b->d_z && b->d_p && b->d_q && b->d_rc;
   const size_t zs = b->prec == TDZ_MIXED ? sizeof(float2) : sizeof(double2);
   for (int a = 0; a < 3; ++a) {
@@ -1666,6 +2065,7 @@ int make_workers(NdBatch* b) {
     w->maxQ = b->maxQ;
     w->maxSide = b->maxSide;
     w->maxn = b->maxn;
+    w->nsm = b->nsm;
     if (cudaStreamCreateWithFlags(&w->st, cudaStreamNonBlocking) != cudaSuccess) {
       delete w;
       return TDZ_ECUDA;
@@ -1770,7 +2170,8 @@ int stencil_setup_p(NdBatch* b, NdGeo& G, const AxisDev& ax, const AxisDev& ay, 
   const size_t nt = (size_t)ax.Q * ay.Q;
   const size_t nh = (size_t)N * half_count(P);
   if (b->prec == TDZ_MIXED) {
-    G.W32 = static_cast<float*>(b->alloc(sizeof(float) * (size_t)N * W * W));
+    const size_t ntiles = (size_t)ay.n * wt_tiles_per_row(ax.n);
+    G.W32 = static_cast<float*>(b->alloc(sizeof(float) * ntiles * kWtRows * W * W));  // zero padded rows
     G.Wx = static_cast<fx*>(b->alloc(sizeof(fx) * nh));
     if (!G.W32 || !G.Wx) return TDZ_ENOMEM;
   } else {
@@ -1977,6 +2378,12 @@ int nd_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* o
   b->maxQ = maxQ;
   b->maxSide = maxSide;
   b->maxn = maxn;
+  {
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && nsm > 0)
+      b->nsm = nsm;
+  }
   const size_t before_work = b->dev_bytes;
   const bool work_ok = alloc_work(b);
   b->work_bytes = b->dev_bytes - before_work;
@@ -2048,6 +2455,11 @@ int nd_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* o
   if (e != cudaSuccess) {
     delete b;
     return nd_cuda_fail(e, "tdz_batch_create (2-D/3-D)");
+  }
+  if (dim == 2 && precision == TDZ_MIXED && want_stencil && autotune(b) != TDZ_OK) {
+    delete b;
+    set_error("tdz_batch_create: timing the 2-D apply variants failed");
+    return TDZ_ECUDA;
   }
   const int rw = make_workers(b);
   if (rw != TDZ_OK) {
@@ -2128,6 +2540,7 @@ int nd_propagate(NdBatch* b, const double* field_host, double dt, long long step
     w->inner_tol = b->inner_tol;
     w->opt_precond = b->opt_precond;
     w->opt_operator = b->opt_operator;
+    w->opt_groups = b->opt_groups;
   }
   std::vector<int> order(b->nruns);
   for (int r = 0; r < b->nruns; ++r) order[r] = r;
@@ -2206,7 +2619,28 @@ int nd_set_option(NdBatch* b, int option, int value) {
     b->opt_operator = value;
     return TDZ_OK;
   }
+  if (option == TDZ_OPT_APPLY_GROUPS) {
+    if (value != 0 && value != 8 && value != 16) return TDZ_EINVAL;
+    b->opt_groups = value;
+    return TDZ_OK;
+  }
   return TDZ_EINVAL;
+}
+
+int nd_tuning(const NdBatch* b, int geometry, int* groups, double* ms) {
+  if (geometry < 0 || geometry >= (int)b->geo.size()) return TDZ_EINVAL;
+  const NdGeo& G = b->geo[geometry];
+  if (!G.W32) {
+    if (groups) *groups = 0;
+    if (ms) ms[0] = ms[1] = 0.0;
+    return TDZ_OK;
+  }
+  if (groups) *groups = G.apply_groups;
+  if (ms) {
+    ms[0] = G.tune_ms[0];
+    ms[1] = G.tune_ms[1];
+  }
+  return TDZ_OK;
 }
 
 void nd_set_refinement(NdBatch* b, double tol, int max_it) {

@@ -99,6 +99,32 @@ def test_nd_matches_oracle(tdz, name, op, pc):
             assert np.max(np.abs(og[:, col] - obs[:, col])) < 10 * tol * scale, (prec, col)
 
 
+@pytest.mark.parametrize("name", ["ho2d", "softcore2d", "dot2d"])
+def test_fused_apply_variants_and_autotuner(tdz, name):
+    """The fused FP32 2-D apply (Kronecker terms + stencil tiles streamed by bulk copies) in every
+    variant: the autotuner picks one of the timed variants at batch creation, and each forced
+    variant propagates to the oracle's trajectory (the grids here are 7-9 stencil tiles of 64 rows,
+    two of them with a ragged last tile). A binary64 batch has no FP32 stencil and reports no tuning."""
+    knots, p, med, dt, nsteps, e0 = _case(name)
+    m, c0, field, c, obs = _reference(name)
+    ops = tdz.Ops([tdz.Basis(k, p, p + 1) for k in knots], med)
+    states = {}
+    for groups in (0, 8, 16):
+        b = tdz.Batch([ops], [0], tdz.MIXED)
+        chosen, ms = b.tuning(0)
+        assert chosen in (8, 16) and set(ms) == {8, 16} and all(v > 0 for v in ms.values()), (chosen, ms)
+        b.set_option(tdz.OPT_APPLY_GROUPS, groups)
+        b.set_state(0, c0)
+        b.propagate(field.reshape(1, nsteps + 1, 2), dt, 0, nsteps)
+        assert b.observe(0)[1] == tdz.TDZ_OK
+        states[groups] = b.get_state(0)
+        assert np.linalg.norm(states[groups] - c) < 1e-8 * np.linalg.norm(c), groups
+    assert np.linalg.norm(states[8] - states[16]) < 1e-9 * np.linalg.norm(states[16])
+    with pytest.raises(tdz.TDZError):
+        b.set_option(tdz.OPT_APPLY_GROUPS, 5)
+    assert tdz.Batch([ops], [0], tdz.FP64).tuning(0) == (0, {})
+
+
 def test_fast_diagonalisation_needs_fewer_iterations(tdz):
     """With tau * lam_max(T1) >> 1 (fine grid, long step) the per-axis product preconditioner carries the
     cross term (i tau)^2 T1(x)T1; the exact inverse of the field-free separable part does not, and needs
