@@ -153,8 +153,11 @@ int  tdz_set_state_all(tdz_batch* b, const double* c);
 
 /* Mixed-precision refinement control: after each FP32 solve the step is accepted when
  * ||B_n c^n - A_n c^{n+1}|| <= tol ||S c^n||; at most max_solves FP32 solves per step
- * (then the run's status becomes TDZ_ENOCONV and propagation continues). Defaults:
- * tol = 1e-11, max_solves = 6. Ignored by TDZ_FP64 batches (one exact solve per step). */
+ * (then the run's status becomes TDZ_ENOCONV and propagation continues). A solve after the
+ * first is accepted without forming its residual when the contraction measured on the first
+ * solve (below 1e-2) predicts a residual at most tol/10; the predicted value then enters
+ * tdz_refine_stats. Defaults: tol = 1e-11, max_solves = 6. Ignored by TDZ_FP64 batches (one
+ * exact solve per step). */
 int  tdz_batch_set_refinement(tdz_batch* b, double tol, int max_solves);
 
 /* Solver options of 2-D/3-D batches (1-D batches accept and ignore them).
