@@ -7,7 +7,12 @@ intensities (lambda = 10 um, Keldysh gamma 2.3/1.5/1.0/0.5) = 1024 uneven runs i
 persistent launch, dt = 0.5 a.u., mixed precision (FP32 factors + double-float
 refinement). A step = one CN step of every run incl. the per-step observables.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Beside the headline line: the paper's 1-D H2+ run (30 007 order-7 splines, hydrogenic knots;
+config_h2p_1d) and the 2-D/3-D workloads (config_2d, config_dots_2d, config_3d), each in both
+precisions.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--h2p-steps S]
+                  [--nd-legs 2d,dots,3d] [--nd-steps S]
 
 Prints one JSON line. With torchrun (N > 1) each rank propagates its own full batch (weak
 scaling, no data-path collective); rank 0 prints the line with the max time over ranks.
@@ -291,6 +296,42 @@ def nd_legs(tdz, nsteps, which, n2d=1024, n3d=256):
     return out
 
 
+def h2p_leg(tdz, nsteps):
+    """The paper's 1-D H2+ run (Sec. Molecular HHG): one run of 30 007 order-7 splines on [-4000, 4000]
+    with hydrogenic knots, 6-cycle trapezoidal pulse (w0 = 0.057, 1e14 W/cm^2), dt = 0.05, from the
+    library's own ground state; `nsteps` timed steps of the ramp in each precision (CUDA events)."""
+    import torch
+    wk = wl.h2p_1d(nsteps=nsteps + 2)
+    r = wk.runs[0]
+    ops = tdz.assemble_1d(r.knots, r.degree, r.medium, r.nquad)
+    e_ground, c0 = ops.ground_state()
+    field = np.ascontiguousarray(r.field.reshape(1, -1, 1))
+    res = {"workload": "h2p_1d", "runs": 1, "coefficients": ops.n, "degree": r.degree, "dt": wk.dt, "steps": nsteps,
+           "ground_energy": e_ground, "grid": {k: wk.notes[k] for k in ("l_max", "r1", "n_lin", "n_exp")}}
+    states = {}
+    for label, prec in (("mixed", tdz.MIXED), ("fp64", tdz.FP64)):
+        b = tdz.Batch([ops], [0], prec)
+        b.set_state(0, c0)
+        b.propagate(np.ascontiguousarray(field[:, :3]), wk.dt, 0, 2)  # warm-up
+        b.set_state(0, c0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.propagate(np.ascontiguousarray(field[:, :nsteps + 1]), wk.dt, 0, nsteps)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / nsteps
+        o, st = b.observe(0)
+        res[label] = {"value": ops.n / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "status": st,
+                      "norm_drift": float(np.max(np.abs(o[:, 4] - 1.0)))}
+        states[label] = b.get_state(0)
+        del b
+    res["mixed_vs_fp64_rel_l2"] = float(np.linalg.norm(states["mixed"] - states["fp64"]) /
+                                        np.linalg.norm(states["fp64"]))
+    res["speedup_mixed"] = res["fp64"]["ms_per_step"] / res["mixed"]["ms_per_step"]
+    return res
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -306,6 +347,7 @@ def main():
     ap.add_argument("--nd-legs", default="2d,dots,3d", help="comma list of 2d, dots, 3d (empty: none)")
     ap.add_argument("--nd-2d-splines", type=int, default=1024, help="splines per axis of the 2-D atom")
     ap.add_argument("--nd-3d-splines", type=int, default=256, help="splines per axis of the 3-D atom")
+    ap.add_argument("--h2p-steps", type=int, default=200, help="timed steps of the 1-D H2+ run (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -440,6 +482,8 @@ def main():
             "clocks": clk.summary()}
     # ---------------- 2-D leg: the soft-core atom of the 2-D configuration (1024 x 1024 order-7 splines),
     # a few steps in both precisions (Kronecker + Gauss-point operator, preconditioned COCG)
+    if rank == 0 and args.h2p_steps > 0:
+        line["config_h2p_1d"] = h2p_leg(tdz, args.h2p_steps)
     if rank == 0 and args.nd_steps > 0 and args.nd_legs:
         line.update(nd_legs(tdz, args.nd_steps, args.nd_legs.split(","), args.nd_2d_splines, args.nd_3d_splines))
     if rank == 0 and not args.no_cpu:

@@ -2,6 +2,8 @@
 
 * 1-D DQW batch (1024 runs, 1.87 M coefficients): sampled runs against the oracle, element by
   element; norm conservation and status of every run.
+* 1-D H2+ (30 007 order-7 splines on [-4000, 4000], hydrogenic knots): 100 steps of the
+  trapezoidal pulse in both precisions against the oracle.
 * 2-D soft-core atom (1022^2, agreement 1e-9) and 64 elliptical dots (16 M coefficients, 1e-8: the
   mid-IR step makes A_n ill-conditioned): too large for the oracle's
   sparse direct solve, so two independent GPU solvers are compared: the mixed path (assembled
@@ -93,6 +95,28 @@ def _two_solvers(tdz, ops_list, run_ops, c0s, fields, dt, nsteps, tol):
         assert _rel(out["mixed"][0][i], out["fp64"][0][i]) < tol, i
         om, of = out["mixed"][1][i], out["fp64"][1][i]
         assert np.max(np.abs(om - of)) < tol * max(1.0, np.max(np.abs(of))), i
+
+
+def test_h2p_full_size_against_oracle(tdz):
+    """The paper's 1-D H2+ grid at full size (one run of 30 005 coefficients, the longest chain of
+    the 1-D solver: two warps of 469-row chunks), 100 steps of the trapezoidal pulse from the ground
+    state, both precisions against the oracle's banded LU."""
+    from oracle import eigen
+    wk = wl.h2p_1d(nsteps=100)
+    r = wk.runs[0]
+    m = assemble.assemble_1d(r.knots, r.degree, r.nquad, r.medium)
+    _, c0 = eigen.ground_state(m, sigma=-1.2, dense_max=0)
+    c, obs = propagate.cn_propagate(m, c0, r.field, wk.dt, wk.nsteps)
+    ops = tdz.assemble_1d(r.knots, r.degree, r.medium, r.nquad)
+    for prec, tol in ((tdz.FP64, 1e-9), (tdz.MIXED, 1e-8)):
+        b = tdz.Batch([ops], [0], prec)
+        b.set_state(0, c0)
+        b.propagate(r.field.reshape(1, wk.nsteps + 1, 1), wk.dt, 0, wk.nsteps)
+        og, st = b.observe(0)
+        assert st == tdz.TDZ_OK, prec
+        assert _rel(b.get_state(0), c) < tol, prec
+        assert np.max(np.abs(og[:, 4] - obs[:, 4])) < tol, prec
+        assert np.max(np.abs(og[:, 2] - obs[:, 2])) < 10 * tol * np.max(np.abs(obs[:, 2])), prec
 
 
 def test_softcore_atom_2d_full_size_two_solvers(tdz):

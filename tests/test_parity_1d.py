@@ -139,6 +139,25 @@ def test_config1_full_fp64_and_mixed(tdz):
     assert np.max(np.abs(Ym / Yo - 1)) < 1e-3
 
 
+def test_h2p_hydrogenic_grid_both_precisions(tdz):
+    """The 1-D H2+ workload (Sec. Molecular HHG) on a reduced hydrogenic grid: 3007 order-7 splines on
+    [-400, 400] (spacing 0.2 a.u. inside |x| < 153, growing to 0.52), trapezoidal pulse, 600 steps
+    from the ground state: binary64 rel-L2 <= 1e-9 and norm drift <= 1e-10, mixed <= 1e-8 and
+    <= 1e-8, dipoles against the oracle's."""
+    wk = wl.h2p_1d(nsplines=3007, l_max=400.0, nsteps=600)
+    r = wk.runs[0]
+    m = assemble.assemble_1d(r.knots, r.degree, r.nquad, r.medium)
+    e0, c0 = eigen.ground_state(m, sigma=-1.2, dense_max=0)
+    assert abs(e0 + 1.1026) < 5e-5
+    c, obs = propagate.cn_propagate(m, c0, r.field, wk.dt, wk.nsteps)
+    for prec, tol, drift in ((tdz.FP64, 1e-9, 1e-10), (tdz.MIXED, 1e-8, 1e-8)):
+        cg, og, st, _ = _gpu_run(tdz, r.knots, r.degree, r.nquad, r.medium, r.field, wk.dt, wk.nsteps, c0, prec)
+        assert st == tdz.TDZ_OK, prec
+        assert _rel(cg, c) < tol, (prec, _rel(cg, c))
+        assert np.max(np.abs(og[:, 4] - 1.0)) < drift, prec
+        assert np.max(np.abs(og[:, 2] - obs[:, 2])) < 10 * tol * np.max(np.abs(obs[:, 2])), prec
+
+
 def test_restart_and_state_roundtrip(tdz):
     dt, nsteps = 0.05, 80
     knots, med, field = _case(300, 6, L=40.0, dt=dt, nsteps=nsteps)

@@ -67,6 +67,20 @@ def knots_for_nsplines(a: float, b: float, nsplines: int, p: int) -> np.ndarray:
     return open_uniform_knots(a, b, nsplines - p, p)
 
 
+
+def hydrogenic_knots(l_max: float, r1: float, n_lin: int, n_exp: int, p: int) -> np.ndarray:
+    """Symmetric open knots on [-l_max, l_max] from the hydrogenic grading (Tab. gradings):
+    r_i = i r1 for i <= n_lin, then r_i = r_cross exp((i - n_lin) ln(l_max / r_cross) / n_exp),
+    r_cross = n_lin r1, up to i = n_lin + n_exp; mirrored to x < 0 (2 (n_lin + n_exp) elements)."""
+    r_cross = n_lin * r1
+    lin = r1 * np.arange(1, n_lin + 1, dtype=np.float64)
+    i = np.arange(1, n_exp + 1, dtype=np.float64)
+    ex = r_cross * np.exp(i * math.log(l_max / r_cross) / n_exp)
+    ex[-1] = l_max
+    pos = np.concatenate([lin, ex])
+    inner = np.concatenate([-pos[::-1], [0.0], pos])
+    return np.concatenate([np.full(p, -l_max), inner, np.full(p, l_max)])
+
 # ---------------------------------------------------------------- media
 def medium(mass: Dict, potential: Dict) -> Dict:
     return {"mass": dict(mass), "potential": dict(potential)}
@@ -188,6 +202,52 @@ def softcore_atom_1d(nsplines: int = 1000, p: int = 7, L: float = 200.0, eps: fl
                     {"nsplines": nsplines, "p": p, "L": L, "eps": eps, "E0": e0, "omega": omega,
                      "ncycles": ncycles, "T": T})
 
+
+
+def h2p_medium(R: float = 2.0, eps: float = 1.472) -> Dict:
+    """1-D H2+ model: two soft-core centres at +-R/2 (Sec. Molecular HHG)."""
+    return medium({"kind": "const", "m": 1.0}, {"kind": "h2p_softcore", "R": R, "eps": eps})
+
+
+def hydrogenic_split(l_max: float, r1: float, n_side: int) -> int:
+    """Number of linear intervals n_lin (of n_side on one side) for which the hydrogenic grading has
+    no jump in spacing: the first exponential interval r_cross (exp(ln(l_max/r_cross)/n_exp) - 1)
+    equals r1 (bisection; that interval grows with n_lin)."""
+    def first_exp_step(n_lin):
+        rc = n_lin * r1
+        return rc * math.expm1(math.log(l_max / rc) / (n_side - n_lin))
+    lo, hi = 1, n_side - 1
+    while hi - lo > 1:
+        mid = (lo + hi) // 2
+        if mid * r1 < l_max and first_exp_step(mid) < r1:
+            lo = mid
+        else:
+            hi = mid
+    return lo
+
+
+def h2p_1d(nsplines: int = 30007, p: int = 7, l_max: float = 4000.0, r1: float = 0.2,
+           e0: Optional[float] = None, omega: float = 0.057, ramp_cycles: float = 1.0, flat_cycles: float = 4.0,
+           dt: float = 0.05, nsteps: Optional[int] = None) -> Workload:
+    """1-D H2+ (R = 2, eps = 1.472) on [-l_max, l_max] with hydrogenic knots, 6-cycle trapezoidal
+    pulse at w0 = 0.057 and 1e14 W/cm^2 (Sec. Molecular HHG). nsplines - p elements, split evenly
+    between the two sides; on each side the linear part (step r1) is as long as keeps the spacing
+    continuous into the exponential part (hydrogenic_split)."""
+    n_side = (nsplines - p) // 2
+    if 2 * n_side != nsplines - p:
+        raise ValueError("nsplines - p must be even (symmetric grid)")
+    n_lin = hydrogenic_split(l_max, r1, n_side)
+    knots = hydrogenic_knots(l_max, r1, n_lin, n_side - n_lin, p)
+    if e0 is None:
+        e0 = e0_from_intensity(1e14)
+    T = (2 * ramp_cycles + flat_cycles) * 2 * math.pi / omega
+    if nsteps is None:
+        nsteps = int(math.ceil(T / dt - 1e-9))
+    t = time_grid(dt, nsteps)
+    run = Run1D(knots, p, p + 1, h2p_medium(), trapezoid_pulse(t, e0, omega, ramp_cycles, flat_cycles), dt)
+    return Workload("h2p_1d", [run], nsteps, dt,
+                    {"nsplines": nsplines, "p": p, "l_max": l_max, "r1": r1, "n_lin": n_lin,
+                     "n_exp": n_side - n_lin, "E0": e0, "omega": omega, "T": T})
 
 def dqw_knots(med: Dict, nsplines: int, p: int, well_weight: float = 2.0) -> np.ndarray:
     """Piecewise-uniform knots with all interfaces as knots; wells and the central barrier are
