@@ -329,6 +329,40 @@ def h2p_leg(tdz, nsteps):
     res["mixed_vs_fp64_rel_l2"] = float(np.linalg.norm(states["mixed"] - states["fp64"]) /
                                         np.linalg.norm(states["fp64"]))
     res["speedup_mixed"] = res["fp64"]["ms_per_step"] / res["mixed"]["ms_per_step"]
+    # the same grid as a scan: 148 independent runs (one per SM) of 37 intensities (0.5-2.0e14 W/cm^2,
+    # log-spaced) x 4 carrier-envelope phases, sharing one geometry, in one persistent launch
+    nscan, nsteps_scan = 148, max(10, nsteps // 4)
+    t = wl.time_grid(wk.dt, nsteps_scan + 2)
+    fields = []
+    for k in range(nscan):
+        e0 = wl.e0_from_intensity(1e14 * 10 ** (math.log10(0.5) + (math.log10(2.0) - math.log10(0.5)) * (k // 4) / 36))
+        cep = 0.5 * math.pi * (k % 4)
+        Tc = 2 * math.pi / 0.057
+        env = np.clip(np.minimum(t / Tc, (6 * Tc - t) / Tc), 0.0, 1.0)
+        fields.append(e0 * env * np.sin(0.057 * t + cep))
+    fields = np.ascontiguousarray(np.stack(fields)[:, :, None])
+    scan = {"runs": nscan, "coefficients": nscan * ops.n, "steps": nsteps_scan,
+            "scan": "37 intensities 0.5-2e14 W/cm^2 (log) x 4 CEPs, trapezoidal 1+4+1 cycles"}
+    for label, prec in (("mixed", tdz.MIXED), ("fp64", tdz.FP64)):
+        b = tdz.Batch([ops], [0] * nscan, prec)
+        c_all = np.concatenate([c0] * nscan)
+        b.set_states(c_all)
+        b.propagate(np.ascontiguousarray(fields[:, :3]), wk.dt, 0, 2)  # warm-up
+        b.set_states(c_all)
+        torch.cuda.synchronize()
+        e0_, e1_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0_.record()
+        b.propagate(np.ascontiguousarray(fields[:, :nsteps_scan + 1]), wk.dt, 0, nsteps_scan)
+        e1_.record()
+        torch.cuda.synchronize()
+        ms = e0_.elapsed_time(e1_) / nsteps_scan
+        obs, sts = b.observe_all()
+        scan[label] = {"value": nscan * ops.n / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                       "runs_not_ok": int(sum(int(x) != 0 for x in sts)),
+                       "norm_drift": float(np.max(np.abs(obs[:, :, 4] - 1.0)))}
+        del b
+    scan["speedup_mixed"] = scan["fp64"]["ms_per_step"] / scan["mixed"]["ms_per_step"]
+    res["scan"] = scan
     return res
 
 
