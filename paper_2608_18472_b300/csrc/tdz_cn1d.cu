@@ -9,8 +9,8 @@
 // extrapolation from the last two steps (mixed path). Observables of Sec. "Dipoles" are
 // reduced after every step.
 //
-// GPU organisation (one warp per run, the whole time loop inside one persistent launch):
-//   * the n rows of a run are split into K <= 32 chunks of m rows, one per lane; the last
+// GPU organisation (1, 2, 4 or 8 warps per run, the whole time loop inside one persistent launch):
+//   * the n rows of a run are split into K <= 32 x warps chunks of m rows, one per lane; the last
 //     P rows of every chunk but the last are a separator ("Sep_k"), the rest its interior;
 //   * sweep 1 (top-down): each lane eliminates its interior with a register-window band
 //     LDL^T, carrying the coupling to the separator above (the "spike") and the right-hand
@@ -18,10 +18,10 @@
 //   * sweep 2 (bottom-up): each lane eliminates its interior from the bottom to obtain the
 //     Schur complement of the separator above it (no storage);
 //   * the separators form a block-tridiagonal system (K-1 blocks of P x P), factored and
-//     solved by the whole warp in shared memory (block LDL^T with explicit pivot inverses);
+//     solved by the run's first warp in shared memory (block LDL^T with explicit pivot inverses);
 //   * forward/back substitution of every interior with the separator values;
 //   * state update and observables.
-// All arrays of a run are interleaved [row][lane] so that every warp access is coalesced.
+// All arrays of a run are interleaved [row][lane of the run] so that every warp access is coalesced.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -39,6 +39,7 @@
 namespace tdz {
 
 constexpr int LANES = 32;
+constexpr int kSlotW = 8;  // schedule slots encode run * kSlotW + warp of the run (at most 8 warps per run)
 constexpr int MAXP = 8;
 
 struct GeomDev {
@@ -118,8 +119,9 @@ struct Lane {
 };
 
 // Shared-memory elements per warp slot for the reduced system. A run of w warps has up to 32w - 1
-// separators and uses the areas of its w slots: Dg and E (cap P x P blocks each), rb (cap x P) and
-// one P x P scratch tile, cap = 32w - 1; 2 * 32 P^2 + 32 P + P^2 per slot covers w = 1 and w = 2.
+// separators and uses the areas of its w adjacent slots: Dg and E (cap P x P blocks each), rb
+// (cap x P) and one P x P scratch tile, cap = 32w - 1; 2 * 32 P^2 + 32 P + P^2 per slot covers
+// every w, since w of them hold 2 (32w - 1) P^2 + (32w - 1) P + P^2.
 __host__ __device__ constexpr int red_elems(int P) { return 2 * 32 * P * P + 32 * P + P * P; }
 
 template <class T>
@@ -885,7 +887,7 @@ TDZ_DEV double warp_sum(double v) {
   return v;
 }
 
-// Sums over all lanes of a run (one or two warps), identical in every lane of the run. Called by
+// Sums over all lanes of a run (nw adjacent warps), identical in every lane of the run. Called by
 // every thread of the block (it contains block barriers); idle warps pass zeros.
 template <int NV>
 TDZ_DEV void run_sum(double (&v)[NV], double (*sh)[4], int wib, int sub, int nw) {
@@ -897,16 +899,20 @@ TDZ_DEV void run_sum(double (&v)[NV], double (*sh)[4], int wib, int sub, int nw)
   __syncthreads();
   const int first = wib - sub;
 #pragma unroll
-  for (int q = 0; q < NV; ++q) v[q] = sh[first][q] + (nw == 2 ? sh[first + 1][q] : 0.0);
+  for (int q = 0; q < NV; ++q) {
+    double t = 0.0;
+    for (int s = 0; s < nw; ++s) t += sh[first + s][q];
+    v[q] = t;
+  }
   __syncthreads();
 }
 
 // ============================================================================ the kernel
-// The block's warps are slots of a schedule built on the host: a slot holds one run (run * 2 + 0)
-// or one half of a two-warp run (run * 2 + sub), or nothing (-1); the two warps of a run are
-// adjacent in one block. The block advances its runs in lock step: it crosses each phase of a step
-// together (block barriers), so all warps of an SM execute the same code region at a time and the
-// two warps of a run see each other's chunk boundaries and shared reduced system. The adaptive
+// The block's warps are slots of a schedule built on the host: a slot holds warp `sub` of run `run`
+// (encoded run * kSlotW + sub; a run has 1, 2, 4 or 8 warps), or nothing (-1); the warps of a run
+// are adjacent in one block. The block advances its runs in lock step: it crosses each phase of a
+// step together (block barriers), so all warps of an SM execute the same code region at a time and
+// the warps of a run see each other's chunk boundaries and shared reduced system. The adaptive
 // refinement decides collectively how many extra solves the block makes; warps whose run is
 // already converged skip the work of those rounds.
 template <int P, bool MIXED>
@@ -929,8 +935,8 @@ __global__ void __launch_bounds__(256) cn1d_kernel(StepArgs A) {
     if (done) break;
     const int slot = item < A.nruns ? A.order[item] : -1;
     const bool has = slot >= 0;
-    const int rid = has ? slot >> 1 : 0;
-    const int sub = has ? slot & 1 : 0;
+    const int rid = has ? slot / kSlotW : 0;
+    const int sub = has ? slot % kSlotW : 0;
     RunDev run = A.runs[rid];
     const GeomDev g = A.geoms[run.geom];
     const int nw = has ? g.ks / LANES : 1;  // warps of this run
@@ -1152,8 +1158,8 @@ size_t smem_per_warp(int P, bool mixed) {
 
 namespace {
 
-// Chunking of a run of n rows over the lanes of `warps` warps: K <= 32 warps chunks of m rows, each
-// interior at least P + 1 rows long (the separator of a chunk is its last P rows).
+// Chunking of a run of n rows over the lanes of `warps` warps (1..8): K <= 32 warps chunks of m rows,
+// each interior at least P + 1 rows long (the separator of a chunk is its last P rows).
 struct Chunking {
   int K, m, ks;
 };
@@ -1169,38 +1175,47 @@ Chunking chunking(int n, int P, int warps) {
 
 // Schedule of the persistent launch. A block holds `wpb` warp slots and keeps them until all their
 // runs are done, so its duration is that of its longest run; `resident` blocks run at a time and
-// the next group of slots goes to the first block that finishes. With allow_pairs, runs longer than
-// a threshold get two warps (64 chunks, half the rows per lane); the threshold is chosen by
-// simulating this list schedule (cost of a run per step ~ rows per lane + a small term per
-// separator) and keeping the shortest makespan. (The binary64 kernel is bound by the FP64 pipe, so
-// the extra separator work of a second warp does not pay there; it keeps one warp per run.) Slots are run * 2 + sub (sub = warp of a two-warp run), -1 when empty; the two
-// warps of a run are adjacent in one block. Returns the slots (a multiple of wpb) and, per
-// geometry, the warps per run.
+// the next group of slots goes to the first block that finishes. Candidate warp assignments are
+// compared by simulating this list schedule (cost of a run per step ~ rows per lane + a small term
+// per separator) and the shortest makespan is kept:
+//   * with allow_pairs, runs of geometries above a threshold get two warps (64 chunks, half the rows
+//     per lane), for every threshold among the geometry sizes (the binary64 kernel is bound by the
+//     FP64 pipe when the batch fills the GPU, so it does not try these);
+//   * every run gets W = 2, 4 or 8 warps (W <= wpb): a batch of few long chains, down to a single
+//     run, then spreads over up to 256 chunks instead of idling the rest of the GPU.
+// Slots are run * kSlotW + sub (sub = warp of the run), -1 when empty; the warps of a run are
+// adjacent in one block. Returns the slots (a multiple of wpb) and, per geometry, the warps per run.
 std::vector<int> schedule_runs(const std::vector<int>& gsize, const int* ops_index, int nruns, int P, int wpb,
                                int resident, bool allow_pairs, std::vector<int>& gwarps) {
   const int nops = (int)gsize.size();
-  std::vector<int> cand = {INT32_MAX};
+  std::vector<int> thr_list = {INT32_MAX};
   if (wpb >= 2 && allow_pairs)
-    for (int gi = 0; gi < nops; ++gi) cand.push_back(gsize[gi]);
-  std::sort(cand.begin(), cand.end());
-  cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+    for (int gi = 0; gi < nops; ++gi) thr_list.push_back(gsize[gi]);
+  std::sort(thr_list.begin(), thr_list.end());
+  thr_list.erase(std::unique(thr_list.begin(), thr_list.end()), thr_list.end());
+  // candidates: (threshold, 0) = two warps for geometries above the threshold; (0, W) = W warps for
+  // every run (W = 2, 4, 8 up to the block's slots), which is what a few long chains need
+  std::vector<std::pair<int, int>> cand;
+  for (int t : thr_list) cand.push_back({t, 0});
+  for (int W = 2; W <= std::min(kSlotW, wpb); W *= 2) cand.push_back({0, W});
   double best = 1e300;
   std::vector<int> best_slots;
   std::vector<int> best_w(nops, 1);
   std::vector<int> w(nops);
   std::vector<double> cost(nops);
   std::vector<int> order(nruns);
-  for (int thr : cand) {
+  for (const auto& cw : cand) {
+    const int thr = cw.first, uniform = cw.second;
     for (int gi = 0; gi < nops; ++gi) {
-      w[gi] = (gsize[gi] > thr && wpb >= 2) ? 2 : 1;
+      w[gi] = uniform ? uniform : ((gsize[gi] > thr && wpb >= 2) ? 2 : 1);
       const Chunking c = chunking(gsize[gi], P, w[gi]);
       cost[gi] = c.m + 0.05 * c.K;
     }
     for (int r = 0; r < nruns; ++r) order[r] = r;
     std::stable_sort(order.begin(), order.end(),
                      [&](int x, int y) { return cost[ops_index[x]] > cost[ops_index[y]]; });
-    // pack into blocks in that order; a two-warp run that does not fit in the current block's
-    // remaining slot is preceded by the next one-warp run (or an empty slot)
+    // pack into blocks in that order; a multi-warp run that does not fit in the current block's
+    // remaining slots is preceded by the next one-warp run (or empty slots)
     std::vector<int> slots;
     std::vector<double> btime;
     std::vector<char> used(nruns, 0);
@@ -1227,7 +1242,7 @@ std::vector<int> schedule_runs(const std::vector<int>& gsize, const int* ops_ind
         if (j < order.size()) {
           const int r1 = order[j];
           used[r1] = 1;
-          slots.push_back(2 * r1);
+          slots.push_back(kSlotW * r1);
           bt = std::max(bt, cost[ops_index[r1]]);
           ++fill;
         }
@@ -1235,7 +1250,7 @@ std::vector<int> schedule_runs(const std::vector<int>& gsize, const int* ops_ind
         continue;
       }
       used[r] = 1;
-      for (int q = 0; q < rw; ++q) slots.push_back(2 * r + q);
+      for (int q = 0; q < rw; ++q) slots.push_back(kSlotW * r + q);
       bt = std::max(bt, cost[ops_index[r]]);
       fill += rw;
       if (fill == wpb) close_block();
