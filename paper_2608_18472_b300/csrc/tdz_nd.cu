@@ -2109,6 +2109,7 @@ int make_workers(NdBatch* b) {
       return TDZ_ECUDA;
     }
     cublasSetEmulationStrategy(w->blas, CUBLAS_EMULATION_STRATEGY_EAGER);
+    cublasSetEmulationSpecialValuesSupport(w->blas, CUDA_EMULATION_SPECIAL_VALUES_SUPPORT_NONE);
     if (!alloc_work(w)) {
       delete w;
       return TDZ_ENOMEM;
@@ -2433,8 +2434,11 @@ int nd_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* o
     return TDZ_ECUDA;
   }
   // the FP32 fast-diagonalisation transforms run on the tensor cores as BF16x9 products (FP32
-  // accuracy); allow that for every shape
+  // accuracy); allow that for every shape. Their operands (states, eigenvectors) are finite, so the
+  // emulation's scan for infinities and NaNs is switched off (a non-finite state is still caught by
+  // the norm of the observables and by the refinement residual, neither of which goes through it)
   cublasSetEmulationStrategy(b->blas, CUBLAS_EMULATION_STRATEGY_EAGER);
+  cublasSetEmulationSpecialValuesSupport(b->blas, CUDA_EMULATION_SPECIAL_VALUES_SUPPORT_NONE);
   size_t stencil_bytes = 0;
   if (dim == 2)
     for (int g = 0; g < nops; ++g)
