@@ -177,11 +177,15 @@ int  tdz_batch_set_refinement(tdz_batch* b, double tol, int max_solves);
  * with a stencil (how many warps split the 2p+1 offsets dy of a row tile): 0 (default) = the
  * variant the autotuner chose at tdz_batch_create, or 8 or 16 to force one. Results do not depend
  * on it beyond FP32 rounding.
+ * TDZ_OPT_WAIT_TEST (test aid for the bounded waits; 0 = off, the default): with 1 the fused FP32
+ * 2-D apply issues no stencil copies and waits at most about 10 ms for them, so its wait runs out
+ * and tdz_propagate returns TDZ_ECUDA with the run's status set; the device stays usable.
  * Both choices give the same A_n up to rounding. Errors: TDZ_EINVAL (unknown option or value),
  * TDZ_EUNSUPPORTED (the choice was not set up for this batch). */
 #define TDZ_OPT_PRECOND          1
 #define TDZ_OPT_OPERATOR         2
 #define TDZ_OPT_APPLY_GROUPS     3
+#define TDZ_OPT_WAIT_TEST        4
 #define TDZ_PRECOND_AUTO         0
 #define TDZ_PRECOND_LINES        1
 #define TDZ_PRECOND_FD           2

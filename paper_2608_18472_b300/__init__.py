@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libtdz.so")
 
 TDZ_OK, TDZ_EINVAL, TDZ_ENOMEM, TDZ_ECUDA, TDZ_ENOCONV, TDZ_ENONFINITE, TDZ_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 FP64, MIXED = 0, 1
-OPT_PRECOND, OPT_OPERATOR, OPT_APPLY_GROUPS = 1, 2, 3
+OPT_PRECOND, OPT_OPERATOR, OPT_APPLY_GROUPS, OPT_WAIT_TEST = 1, 2, 3, 4
 PRECOND_AUTO, PRECOND_LINES, PRECOND_FD = 0, 1, 2
 OPERATOR_AUTO, OPERATOR_QUADRATURE, OPERATOR_STENCIL = 0, 1, 2
 MAT = {"S": 0, "T": 1, "V": 2, "H0": 3, "D": 4, "G": 5, "K": 6}

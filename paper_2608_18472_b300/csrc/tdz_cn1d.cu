@@ -1841,6 +1841,7 @@ int tdz_batch_set_option(tdz_batch* b, int option, int value) {
   if (option == TDZ_OPT_PRECOND && value >= TDZ_PRECOND_AUTO && value <= TDZ_PRECOND_FD) return TDZ_OK;
   if (option == TDZ_OPT_OPERATOR && value >= TDZ_OPERATOR_AUTO && value <= TDZ_OPERATOR_STENCIL) return TDZ_OK;
   if (option == TDZ_OPT_APPLY_GROUPS && (value == 0 || value == 8 || value == 16)) return TDZ_OK;
+  if (option == TDZ_OPT_WAIT_TEST && (value == 0 || value == 1)) return TDZ_OK;
   return TDZ_EINVAL;
 }
 

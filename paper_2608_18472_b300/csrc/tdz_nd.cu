@@ -961,7 +961,8 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
     if (clock64() - t0 > limit) return false;
   return true;
 }
-constexpr long long kWaitLimit = 4000000000LL;  // about 2 s at the maximum SM clock
+constexpr long long kWaitLimit = 4000000000LL;    // about 2 s at the maximum SM clock
+constexpr long long kWaitLimitTest = 20000000LL;  // about 10 ms (TDZ_OPT_WAIT_TEST)
 
 template <int P, int G>
 struct Apply2dCfg {
@@ -1078,12 +1079,13 @@ __device__ __forceinline__ void stencil_pair(const float2* h, const float* w, co
 // up the G partial sums (double-buffered in shared memory by tile parity, so one barrier per tile
 // suffices). Per tile: the stencil block arrives by bulk copy (ring of NST stages, issued NST tiles
 // ahead), the x halo by zero-filling cp.async (one tile ahead). err: set to 1 if a stencil copy did
-// not complete in time.
+// not complete in time. wait_limit: SM cycles a wait may take; issue = 0 (test aid) issues no
+// stencil copies, so that the first wait runs out and the error path is taken.
 template <int P, int G>
 __global__ void __launch_bounds__(32 * G, 1)
     k_apply2d_tma(const float* __restrict__ Wt, long long ntiles, const float2* __restrict__ x, float2* __restrict__ y,
                   const float2* __restrict__ xb, const float2* __restrict__ yb, int nx, int ny, float tau,
-                  int* __restrict__ err) {
+                  int* __restrict__ err, long long wait_limit, int issue) {
   using Cfg = Apply2dCfg<P, G>;
   constexpr int R = Cfg::R, NST = Cfg::NST, PW = 2 * P + 2;
   constexpr int PER = (2 * P + 1 + G - 1) / G;  // offsets dy per group
@@ -1104,7 +1106,7 @@ __global__ void __launch_bounds__(32 * G, 1)
     mbar_init_fence();
   }
   __syncthreads();
-  if (tid == 0)
+  if (tid == 0 && issue)
     for (int s = 0; s < NST && s < mine; ++s) {
       const long long t = blockIdx.x + (long long)s * gridDim.x;
       mbar_expect_tx(smem_addr(&bars[s]), Cfg::STAGE_BYTES);
@@ -1114,14 +1116,14 @@ __global__ void __launch_bounds__(32 * G, 1)
   if (mine > 0) load_halo<P, G>(halo, x, xb, yb, (int)(blockIdx.x / tpr), (int)(blockIdx.x % tpr), nx, ny);
   for (long long k = 0; k < mine; ++k) {
     const int s = (int)(k % NST);
-    const bool ok = mbar_wait_bounded(smem_addr(&bars[s]), (uint32_t)((k / NST) & 1), kWaitLimit);
+    const bool ok = mbar_wait_bounded(smem_addr(&bars[s]), (uint32_t)((k / NST) & 1), wait_limit);
     cp_async_wait_all();  // this thread's halo copies of tile k
     if (__syncthreads_or(!ok)) {
       // give up: report, then let the copies still in flight land (bounded) before leaving
       if (tid == 0) {
         atomicExch(err, 1);
         for (long long j = k; j < mine && j < k + NST; ++j)
-          mbar_wait_bounded(smem_addr(&bars[j % NST]), (uint32_t)((j / NST) & 1), kWaitLimit);
+          mbar_wait_bounded(smem_addr(&bars[j % NST]), (uint32_t)((j / NST) & 1), wait_limit);
       }
       __syncthreads();
       return;
@@ -1319,6 +1321,7 @@ struct NdBatch {
   int opt_precond = TDZ_PRECOND_AUTO;
   int opt_operator = TDZ_OPERATOR_AUTO;
   int opt_groups = 0;  // fused 2-D apply variant: 0 = the autotuned one, else 8 or 16 groups
+  int opt_wait_test = 0;  // test aid: the fused 2-D apply issues no copies and its waits run out
   std::vector<void*> bufs;
   // work vectors sized for the largest run: binary64 and solve precision
   size_t maxN = 0, maxQ = 0;
@@ -1330,7 +1333,8 @@ struct NdBatch {
   void* pre_L[3] = {nullptr, nullptr, nullptr};  // per run would be needed for different sizes; refreshed per run
   void* pre_D[3] = {nullptr, nullptr, nullptr};
   double* d_red = nullptr;  // reduction scratch (16 doubles)
-  int* d_err = nullptr;     // set to nonzero by a kernel whose bounded wait ran out
+  int* d_err = nullptr;     // set to nonzero by a kernel whose bounded wait ran out (in d_red's last slot)
+  bool wait_failed = false;  // host copy of *d_err as of the last reduction read
   // coefficient rows {S, K} of the separable part for the fused FP32 2-D apply (x and y axes), and
   // what they were computed for: geometry, Ebar_x, Ebar_y, constant-mass m^-1
   float2* rb32[2] = {nullptr, nullptr};
@@ -1380,8 +1384,10 @@ void launch_apply2d(NdBatch* b, const NdRun* r, const float* Wt, const float2* x
   cudaFuncSetAttribute(k_apply2d_tma<P, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
   const long long ntiles = (long long)r->n[1] * wt_tiles_per_row(r->n[0]);
   const int grid = (int)std::min<long long>(ntiles, b->nsm);
+  const long long limit = b->opt_wait_test ? kWaitLimitTest : kWaitLimit;
   k_apply2d_tma<P, G><<<grid, Cfg::THREADS, Cfg::SMEM, b->st>>>(Wt, ntiles, x, y, b->rb32[0], b->rb32[1], r->n[0],
-                                                                r->n[1], (float)tau, b->d_err);
+                                                                r->n[1], (float)tau, b->d_err, limit,
+                                                                b->opt_wait_test ? 0 : 1);
 }
 
 // refresh the per-axis coefficient rows when the geometry or the field changed, then one
@@ -1738,9 +1744,15 @@ void precond(NdBatch* b, NdRun* r, Apply<T, P>& op, C<T>* v, double tau) {
   else line_precond<T, P>(b, r, v);
 }
 
+// reads the reduction slots (and, in the same copy, the error word in the last slot)
 double* red_get(NdBatch* b, int k, double* host) {
-  cudaMemcpyAsync(host, b->d_red, sizeof(double) * k, cudaMemcpyDeviceToHost, b->st);
+  double all[16];
+  cudaMemcpyAsync(all, b->d_red, sizeof(all), cudaMemcpyDeviceToHost, b->st);
   cudaStreamSynchronize(b->st);
+  for (int q = 0; q < k; ++q) host[q] = all[q];
+  int werr = 0;
+  std::memcpy(&werr, &all[15], sizeof(int));
+  b->wait_failed = werr != 0;
   return host;
 }
 
@@ -1770,7 +1782,7 @@ int cocg(NdBatch* b, NdRun* r, Apply<T, P>& op, C<T>* x, C<T>* res, C<T>* z, C<T
     k_bdot<T><<<grid_for(N), TPB, 0, b->st>>>(p, q, N, b->d_red);
     red_get(b, 2, h);
     const std::complex<double> pq(h[0], h[1]);
-    if (std::abs(pq) == 0.0) break;
+    if (b->wait_failed || std::abs(pq) == 0.0) break;
     const std::complex<double> alpha = rho / pq;
     red_zero(b, 1);
     k_cocg_update<T><<<grid_for(N), TPB, 0, b->st>>>(x, res, p, q, N, alpha.real(), alpha.imag(), b->d_red);
@@ -1958,7 +1970,7 @@ int propagate_run(NdBatch* b, NdRun* r, const tdz::Ops& o, const double* field, 
     C<fx>* rc = reinterpret_cast<C<fx>*>(b->d_rc);    // current residual
     C<float>* rf = static_cast<C<float>*>(b->w_r);
     C<float>* xf = static_cast<C<float>*>(b->w_x);
-    for (long long s = 0; s < nsteps && r->status == TDZ_OK; ++s) {
+    for (long long s = 0; s < nsteps && r->status == TDZ_OK && !b->wait_failed; ++s) {
       double ebar[3] = {0, 0, 0}, Et[3] = {0, 0, 0};
       for (int a = 0; a < D; ++a) {
         ebar[a] = 0.5 * (field[s * D + a] + field[(s + 1) * D + a]);
@@ -1983,7 +1995,7 @@ int propagate_run(NdBatch* b, NdRun* r, const tdz::Ops& o, const double* field, 
       // next solve is predicted to end at or below a tenth of the tolerance (and rho < 1e-2), its
       // residual is not formed (one double-float apply saved), the same rule as the 1-D path.
       double rho = 1.0;
-      for (int outer = 0; outer < 8 && rr > tol2; ++outer) {
+      for (int outer = 0; outer < 8 && rr > tol2 && !b->wait_failed; ++outer) {
         k_axby<fx, float><<<grid_for(N), TPB, 0, b->st>>>(rc, rf, N, 1.0, 0.0);
         double rri = 0;
         const int its = cocg<float, P>(b, r, op32, xf, rf, static_cast<C<float>*>(b->w_z),
@@ -2025,6 +2037,7 @@ int propagate_run(NdBatch* b, NdRun* r, const tdz::Ops& o, const double* field, 
   if (werr != 0) {
     cudaMemsetAsync(b->d_err, 0, sizeof(int), b->st);
     cudaStreamSynchronize(b->st);
+    b->wait_failed = false;
     r->status = TDZ_ECUDA;
     set_error("tdz_propagate (2-D): a stencil tile copy did not complete within the wait limit");
     return TDZ_ECUDA;
@@ -2045,8 +2058,7 @@ bool alloc_work(NdBatch* b) {
   b->d_qa = static_cast<double2*>(b->alloc(z64 * maxQ));
   b->d_qb = static_cast<double2*>(b->alloc(z64 * maxQ));
   b->d_red = static_cast<double*>(b->alloc(sizeof(double) * 16));
-  b->d_err = static_cast<int*>(b->alloc(sizeof(int) * 4));
-  ok = ok && b->d_err;
+  b->d_err = b->d_red ? reinterpret_cast<int*>(b->d_red + 15) : nullptr;  // red_zero never clears it
   if (b->prec == TDZ_MIXED && b->dim == 2)
     for (int a = 0; a < 2; ++a) {
       b->rb32[a] = static_cast<float2*>(b->alloc(sizeof(float2) * (size_t)std::max(b->maxn, 1) * (2 * b->P + 2)));
@@ -2560,6 +2572,7 @@ int nd_propagate(NdBatch* b, const double* field_host, double dt, long long step
   const int D = b->dim;
   const int cols = 2 + 3 * D;
   b->obs.assign((size_t)b->nruns * nsteps * cols, 0.0);
+  b->last_nsteps = 0;  // set again when the call succeeds (tdz_observe then reads the new buffer)
   const int nw = (int)std::min<size_t>(b->workers.size() + 1, (size_t)b->nruns);
   if (nw <= 1) {
     for (int r = 0; r < b->nruns; ++r) {
@@ -2578,6 +2591,7 @@ int nd_propagate(NdBatch* b, const double* field_host, double dt, long long step
     w->opt_precond = b->opt_precond;
     w->opt_operator = b->opt_operator;
     w->opt_groups = b->opt_groups;
+    w->opt_wait_test = b->opt_wait_test;
   }
   std::vector<int> order(b->nruns);
   for (int r = 0; r < b->nruns; ++r) order[r] = r;
@@ -2659,6 +2673,11 @@ int nd_set_option(NdBatch* b, int option, int value) {
   if (option == TDZ_OPT_APPLY_GROUPS) {
     if (value != 0 && value != 8 && value != 16) return TDZ_EINVAL;
     b->opt_groups = value;
+    return TDZ_OK;
+  }
+  if (option == TDZ_OPT_WAIT_TEST) {
+    if (value != 0 && value != 1) return TDZ_EINVAL;
+    b->opt_wait_test = value;
     return TDZ_OK;
   }
   return TDZ_EINVAL;

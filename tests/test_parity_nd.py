@@ -125,6 +125,30 @@ def test_fused_apply_variants_and_autotuner(tdz, name):
     assert tdz.Batch([ops], [0], tdz.FP64).tuning(0) == (0, {})
 
 
+def test_fused_apply_wait_limit_reports_error(tdz):
+    """Failure detection of the fused 2-D apply's bounded waits: with the test aid TDZ_OPT_WAIT_TEST
+    no stencil copy is issued, every CTA's mbarrier wait runs out after about 10 ms, the kernel sets
+    the error word and returns, and tdz_propagate reports TDZ_ECUDA with the run's status. The
+    device stays usable: a new batch on the same context then propagates to the oracle's result."""
+    knots, p, med, dt, nsteps, e0 = _case("softcore2d")
+    m, c0, field, c, obs = _reference("softcore2d")
+    ops = tdz.Ops([tdz.Basis(k, p, p + 1) for k in knots], med)
+    b = tdz.Batch([ops], [0], tdz.MIXED)
+    b.set_option(tdz.OPT_WAIT_TEST, 1)
+    b.set_state(0, c0)
+    with pytest.raises(tdz.TDZError) as ei:
+        b.propagate(np.ascontiguousarray(field[:3]).reshape(1, 3, 2), dt, 0, 2)
+    assert ei.value.code == tdz.TDZ_ECUDA
+    assert "wait limit" in str(ei.value)
+    assert b.observe(0)[1] == tdz.TDZ_ECUDA
+    del b
+    b2 = tdz.Batch([ops], [0], tdz.MIXED)
+    b2.set_state(0, c0)
+    b2.propagate(field.reshape(1, nsteps + 1, 2), dt, 0, nsteps)
+    assert b2.observe(0)[1] == tdz.TDZ_OK
+    assert np.linalg.norm(b2.get_state(0) - c) < 1e-8 * np.linalg.norm(c)
+
+
 def test_fast_diagonalisation_needs_fewer_iterations(tdz):
     """With tau * lam_max(T1) >> 1 (fine grid, long step) the per-axis product preconditioner carries the
     cross term (i tau)^2 T1(x)T1; the exact inverse of the field-free separable part does not, and needs
