@@ -345,6 +345,17 @@ __global__ void k_fused_last(const C<T>* __restrict__ in, C<T>* __restrict__ out
       const int j = e0 + k - 1;
       win[k] = (j >= 0 && j < nL) ? in[(long long)j * inner + i] : czero<T>();
     }
+    // tabulated w(q) f(r_q) of the next kFPre points of the pencil, loaded ahead of use (HBM latency)
+    constexpr int kFPre = 4;
+    const int qend = e1 * nq;
+    T fpre[kFPre];
+    if (ftab) {
+#pragma unroll
+      for (int u = 0; u < kFPre; ++u) {
+        const int qp = e0 * nq + u;
+        fpre[u] = qp < qend ? ftab[(long long)qp * inner + i] : T(0);
+      }
+    }
     for (int e = e0; e < e1; ++e) {
       for (int qq = 0; qq < nq; ++qq) {
         const int q = e * nq + qq;
@@ -358,7 +369,11 @@ __global__ void k_fused_last(const C<T>* __restrict__ in, C<T>* __restrict__ out
         const T pr = mr.get(), pi = mi.get();
         T f;
         if (ftab) {  // w(q) f(r_q) tabulated at the Gauss points, [q_L][pencil]
-          f = ftab[(long long)q * inner + i];
+          f = fpre[0];
+#pragma unroll
+          for (int u = 0; u + 1 < kFPre; ++u) fpre[u] = fpre[u + 1];
+          const int qn = q + kFPre;
+          fpre[kFPre - 1] = qn < qend ? ftab[(long long)qn * inner + i] : T(0);
         } else {
           r[L] = g.x[L][q];
           f = wp * g.w[L][q] * medium_f<T>(M, kind, axis, r, g.dim);
