@@ -42,10 +42,11 @@ sys.path.insert(0, ROOT)
 import workloads as wl  # noqa: E402
 
 CPU_MAX_STEPS = 2000
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per coefficient-step of the mixed 1-D
-# kernel, from one ncu capture of this kernel version on the DQW batch (2.880 GB over 3 steps of
-# 1.873 M coefficients); the traffic of a timed launch is this times its coefficient-steps.
-NCU_DRAM_BYTES_PER_COEFF_STEP = 513.0
+# DRAM bytes (read + write) per coefficient-step of the mixed 1-D kernel, from one ncu capture of
+# this kernel version on the DQW batch (dram__bytes 826.27 GB/s over the 3.469 ms warm-up launch:
+# 2.867 GB for 3 steps of 1 873 260 coefficients); the traffic of a timed launch is this times its
+# coefficient-steps.
+NCU_DRAM_BYTES_PER_COEFF_STEP = 510.1
 METRIC = "TDSE coefficient-updates/s: batched mixed vs plain FP64 at stated HHG/norm error"
 UNIT = "coefficient-updates/s"
 
