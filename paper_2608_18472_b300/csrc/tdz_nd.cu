@@ -1455,7 +1455,6 @@ int autotune_apply2d(NdBatch* b) {
     if (!G.W32 || !r) continue;
     const C<float>* x = static_cast<const C<float>*>(b->w_p);
     C<float>* y = static_cast<C<float>*>(b->w_q);
-    float best = 0.f;
     for (int c = 0; c < 2; ++c) {
       G.apply_groups = cand[c];
       apply2d_fused<P>(b, r, G.W32, x, y, tau, zero);
@@ -1472,13 +1471,15 @@ int autotune_apply2d(NdBatch* b) {
         tmin = k == 0 ? ms : std::min(tmin, ms);
       }
       G.tune_ms[c] = tmin;
-      if (c == 0 || tmin < best) best = tmin;
     }
     G.apply_groups = G.tune_ms[1] < G.tune_ms[0] ? 16 : 8;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   b->rb_geo = -1;
+  int werr = 0;  // a wait that ran out while timing
+  if (rc == TDZ_OK && (cudaMemcpy(&werr, b->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess || werr != 0))
+    rc = TDZ_ECUDA;
   return rc;
 }
 
