@@ -1238,6 +1238,33 @@ __global__ void k_merge(const Tp* __restrict__ w, C<Tv>* __restrict__ v, PadDims
     v[i] = C<Tv>{(Tv)w[k], (Tv)w[d.Np + k]};
   }
 }
+// k_merge that also accumulates the bilinear product res[0..1] += sum a_i v_i (binary64) of the merged
+// vector with `a` (the preconditioned residual's rho = r^T z of COCG, without another pass)
+template <class Tv, class Tp>
+__global__ void k_merge_dot(const Tp* __restrict__ w, C<Tv>* __restrict__ v, PadDims d, long long n,
+                            const C<Tv>* __restrict__ a, double* res) {
+  __shared__ double sh[32];
+  double re = 0.0, im = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int j0 = (int)(i % d.n[0]);
+    const long long t = i / d.n[0];
+    const int j1 = d.dim > 1 ? (int)(t % d.n[1]) : 0;
+    const int j2 = d.dim > 2 ? (int)(t / d.n[1]) : 0;
+    const long long k = ((long long)j2 * d.np[1] + j1) * d.np[0] + j0;
+    const C<Tv> z = C<Tv>{(Tv)w[k], (Tv)w[d.Np + k]};
+    v[i] = z;
+    const C<Tv> x = a[i];
+    re += (double)x.r * (double)z.r - (double)x.i * (double)z.i;
+    im += (double)x.r * (double)z.i + (double)x.i * (double)z.r;
+  }
+  re = block_sum(re, sh);
+  im = block_sum(im, sh);
+  if (threadIdx.x == 0) {
+    atomicAdd(res, re);
+    atomicAdd(res + 1, im);
+  }
+}
+
 // in the eigenbasis (index j0 fastest): u /= 1 + i tm (lam0[j0] + lam1[j1] + lam2[j2])
 template <class Tp>
 __global__ void k_fd_scale(Tp* __restrict__ w, long long n, int dim, int n0, int n1, const double* __restrict__ l0,
@@ -1723,8 +1750,10 @@ template <> const double* fd_mat<double>(const NdGeo& g, int a) { return g.V64[a
 // v <- M^-1 v, M = S(x)S + i tau mbar sum_a (T1_a on axis a, S elsewhere):
 //   M^-1 = ((x)V_a) diag(1 / (1 + i tau mbar sum_a lam_a)) ((x)V_a)^T   since V_a^T S_a V_a = I,
 //   V_a^T T1_a V_a = diag(lam_a). w0, w1: planar scratch of 2N values each.
+//   dst = M^-1 src (src == dst allowed); with dot, also dot[0..1] += src^T dst (src != dst).
 template <class T>
-void fd_apply(NdBatch* b, const NdRun* r, C<T>* v, T* w0, T* w1, double tau) {
+void fd_apply(NdBatch* b, const NdRun* r, const C<T>* src, C<T>* dst, T* w0, T* w1, double tau,
+              double* dot = nullptr) {
   const NdGeo& G = b->geo[r->geo];
   PadDims d{};
   d.dim = r->dim;
@@ -1734,7 +1763,7 @@ void fd_apply(NdBatch* b, const NdRun* r, C<T>* v, T* w0, T* w1, double tau) {
     d.np[a] = a < r->dim ? G.np[a] : 1;
     d.Np *= d.np[a];
   }
-  k_split<T, T><<<grid_for(d.Np), TPB, 0, b->st>>>(v, w0, d);
+  k_split<T, T><<<grid_for(d.Np), TPB, 0, b->st>>>(src, w0, d);
   T* cur = w0;
   T* nxt = w1;
   for (int pass = 0; pass < 2; ++pass) {
@@ -1747,17 +1776,27 @@ void fd_apply(NdBatch* b, const NdRun* r, C<T>* v, T* w0, T* w1, double tau) {
       k_fd_scale<T><<<grid_for(d.Np), TPB, 0, b->st>>>(cur, d.Np, r->dim, d.np[0], d.np[1], G.lam[0], G.lam[1],
                                                        G.lam[2], tau * r->mbar);
   }
-  k_merge<T, T><<<grid_for(r->N), TPB, 0, b->st>>>(cur, v, d, r->N);
+  if (dot)
+    k_merge_dot<T, T><<<grid_for(r->N), TPB, 0, b->st>>>(cur, dst, d, r->N, src, dot);
+  else
+    k_merge<T, T><<<grid_for(r->N), TPB, 0, b->st>>>(cur, dst, d, r->N);
 }
 
 bool use_fd(const NdBatch* b, const NdRun* r) {
   return b->opt_precond != TDZ_PRECOND_LINES && b->geo[r->geo].fd;
 }
 
+// z = M^-1 res and d_red[0..1] += res^T z (the rho of COCG; d_red zeroed by the caller): on the fast
+// diagonalisation path the product is accumulated while the result is written
 template <class T, int P>
-void precond(NdBatch* b, NdRun* r, Apply<T, P>& op, C<T>* v, double tau) {
-  if (use_fd(b, r)) fd_apply<T>(b, r, v, reinterpret_cast<T*>(op.qa), reinterpret_cast<T*>(op.qb), tau);
-  else line_precond<T, P>(b, r, v);
+void precond_dot(NdBatch* b, NdRun* r, Apply<T, P>& op, const C<T>* res, C<T>* z, double tau) {
+  if (use_fd(b, r)) {
+    fd_apply<T>(b, r, res, z, reinterpret_cast<T*>(op.qa), reinterpret_cast<T*>(op.qb), tau, b->d_red);
+    return;
+  }
+  cudaMemcpyAsync(z, res, sizeof(C<T>) * r->N, cudaMemcpyDeviceToDevice, b->st);
+  line_precond<T, P>(b, r, z);
+  k_bdot<T><<<grid_for(r->N), TPB, 0, b->st>>>(res, z, r->N, b->d_red);
 }
 
 // reads the reduction slots (and, in the same copy, the error word in the last slot)
@@ -1781,11 +1820,9 @@ int cocg(NdBatch* b, NdRun* r, Apply<T, P>& op, C<T>* x, C<T>* res, C<T>* z, C<T
   const long long N = r->N;
   double h[4];
   cudaMemsetAsync(x, 0, sizeof(C<T>) * N, b->st);
-  cudaMemcpyAsync(z, res, sizeof(C<T>) * N, cudaMemcpyDeviceToDevice, b->st);
-  precond<T, P>(b, r, op, z, tau);
-  cudaMemcpyAsync(p, z, sizeof(C<T>) * N, cudaMemcpyDeviceToDevice, b->st);
   red_zero(b, 2);
-  k_bdot<T><<<grid_for(N), TPB, 0, b->st>>>(res, z, N, b->d_red);
+  precond_dot<T, P>(b, r, op, res, z, tau);
+  cudaMemcpyAsync(p, z, sizeof(C<T>) * N, cudaMemcpyDeviceToDevice, b->st);
   red_get(b, 2, h);
   std::complex<double> rho(h[0], h[1]);
   red_zero(b, 1);
@@ -1805,10 +1842,8 @@ int cocg(NdBatch* b, NdRun* r, Apply<T, P>& op, C<T>* x, C<T>* res, C<T>* z, C<T
     rr = red_get(b, 1, h)[0];
     ++it;
     if (!(rr > tol_abs2)) break;
-    cudaMemcpyAsync(z, res, sizeof(C<T>) * N, cudaMemcpyDeviceToDevice, b->st);
-    precond<T, P>(b, r, op, z, tau);
     red_zero(b, 2);
-    k_bdot<T><<<grid_for(N), TPB, 0, b->st>>>(res, z, N, b->d_red);
+    precond_dot<T, P>(b, r, op, res, z, tau);
     red_get(b, 2, h);
     const std::complex<double> rho_new(h[0], h[1]);
     if (std::abs(rho) == 0.0) break;
