@@ -639,6 +639,50 @@ __global__ void k_bdot(const C<T>* __restrict__ a, const C<T>* __restrict__ b, l
   }
 }
 
+// The Kronecker quadratic forms of the 2-D observables in one pass along y, given t = S_x c and
+// u = D_x c (x-passes): res[0] += c^H (S_y(x)S_x) c (norm), res[1] += c^H (S_y(x)D_x) c (d_x),
+// res[2] += c^H (D_y(x)S_x) c (d_y); the y-sums in the arithmetic T, the products with conj(c) and the
+// accumulation in binary64 (real parts: the forms are Hermitian)
+template <class T, int P>
+__global__ void k_qform2_y(const C<T>* __restrict__ c, const C<T>* __restrict__ t, const C<T>* __restrict__ u,
+                           const T* __restrict__ Sy, const T* __restrict__ Dy, int nx, int ny, double* res) {
+  __shared__ double sh[32];
+  double q0 = 0.0, q1 = 0.0, q2 = 0.0;
+  const long long N = (long long)nx * ny;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < N;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int ix = (int)(idx % nx), iy = (int)(idx / nx);
+    Mac<T> sr, si, dr, di, ur, ui;
+#pragma unroll
+    for (int d = -P; d <= P; ++d) {
+      const int jy = iy + d;
+      if (jy < 0 || jy >= ny) continue;
+      const size_t bi = (size_t)(jy > iy ? jy : iy) * (P + 1) + (d < 0 ? -d : d);
+      const T sv = Sy[bi], dv = Dy[bi];
+      const C<T> tv = t[(long long)jy * nx + ix], uv = u[(long long)jy * nx + ix];
+      sr.add(sv, tv.r);
+      si.add(sv, tv.i);
+      dr.add(dv, tv.r);
+      di.add(dv, tv.i);
+      ur.add(sv, uv.r);
+      ui.add(sv, uv.i);
+    }
+    const C<T> cv = c[idx];
+    const double cr = (double)cv.r, ci = (double)cv.i;
+    q0 += cr * (double)sr.get() + ci * (double)si.get();
+    q1 += cr * (double)ur.get() + ci * (double)ui.get();
+    q2 += cr * (double)dr.get() + ci * (double)di.get();
+  }
+  q0 = block_sum(q0, sh);
+  q1 = block_sum(q1, sh);
+  q2 = block_sum(q2, sh);
+  if (threadIdx.x == 0) {
+    atomicAdd(res, q0);
+    atomicAdd(res + 1, q1);
+    atomicAdd(res + 2, q2);
+  }
+}
+
 // COCG update: x += alpha p; r -= alpha q; res[0] += ||r||^2
 template <class T>
 __global__ void k_cocg_update(C<T>* __restrict__ x, C<T>* __restrict__ r, const C<T>* __restrict__ p,
@@ -1913,16 +1957,37 @@ void observe(NdBatch* b, NdRun* r, Apply<T, P>& op, const C<T>* c, C<T>* y, cons
   const long long N = r->N;
   double h[4];
   double zero3[3] = {0, 0, 0};
-  op.kron(c, y, 1, 0.0, zero3);
-  red_zero(b, 2);
-  k_hdot<T><<<grid_for(N), TPB, 0, b->st>>>(c, y, N, b->d_red);
-  const double norm = red_get(b, 2, h)[0];
-  double dvals[3], gvals[3];
-  for (int a = 0; a < r->dim; ++a) {
-    op.kron(c, y, 2, 0.0, zero3, a);
+  double norm = 0.0, dvals[3] = {0, 0, 0}, gvals[3];
+  if (r->dim == 2) {
+    // x-passes t = S_x c, u = D_x c, then the three forms in one y-pass
+    const AxisDev& A0 = r->ax[0];
+    BandTerms<T> bs{}, bd{};
+    bs.nt = bd.nt = 1;
+    bs.R[0] = tab<T>(A0, TS);
+    bd.R[0] = tab<T>(A0, TD);
+    bs.cr[0] = bd.cr[0] = 1;
+    const long long tot = N;
+    launch_axis_band<T, P>(b->st, grid_for(tot), bs, c, c, op.t1, r->n[1], r->n[0], 1);
+    launch_axis_band<T, P>(b->st, grid_for(tot), bd, c, c, op.t2, r->n[1], r->n[0], 1);
+    red_zero(b, 3);
+    k_qform2_y<T, P><<<grid_for(N), TPB, 0, b->st>>>(c, op.t1, op.t2, tab<T>(r->ax[1], TS), tab<T>(r->ax[1], TD),
+                                                     r->n[0], r->n[1], b->d_red);
+    double q3[3];
+    red_get(b, 3, q3);
+    norm = q3[0];
+    dvals[0] = q3[1];
+    dvals[1] = q3[2];
+  } else {
+    op.kron(c, y, 1, 0.0, zero3);
     red_zero(b, 2);
     k_hdot<T><<<grid_for(N), TPB, 0, b->st>>>(c, y, N, b->d_red);
-    dvals[a] = red_get(b, 2, h)[0];
+    norm = red_get(b, 2, h)[0];
+    for (int a = 0; a < r->dim; ++a) {
+      op.kron(c, y, 2, 0.0, zero3, a);
+      red_zero(b, 2);
+      k_hdot<T><<<grid_for(N), TPB, 0, b->st>>>(c, y, N, b->d_red);
+      dvals[a] = red_get(b, 2, h)[0];
+    }
   }
   // c^H G_a c and (variable mass) c^H K c at the Gauss points, fused along the last axis
   const C<T>* X = op.to_pencils(c, -1);
