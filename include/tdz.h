@@ -173,6 +173,7 @@ int  tdz_batch_set_refinement(tdz_batch* b, double tol, int max_solves);
  *   TDZ_OPERATOR_QUADRATURE  sum factorisation at the Gauss points, f(r) evaluated on the fly;
  *   TDZ_OPERATOR_STENCIL     2-D only: the same quadrature assembled once into a (2p+1)^2-point
  *                            stencil per DoF.
+ * Both operator choices give the same A_n up to rounding.
  * TDZ_OPT_APPLY_GROUPS selects the variant of the fused FP32 2-D operator apply of mixed batches
  * with a stencil (how many warps split the 2p+1 offsets dy of a row tile): 0 (default) = the
  * variant the autotuner chose at tdz_batch_create, or 8 or 16 to force one. Results do not depend
@@ -180,8 +181,8 @@ int  tdz_batch_set_refinement(tdz_batch* b, double tol, int max_solves);
  * TDZ_OPT_WAIT_TEST (test aid for the bounded waits; 0 = off, the default): with 1 the fused FP32
  * 2-D apply issues no stencil copies and waits at most about 10 ms for them, so its wait runs out
  * and tdz_propagate returns TDZ_ECUDA with the run's status set; the device stays usable.
- * Both choices give the same A_n up to rounding. Errors: TDZ_EINVAL (unknown option or value),
- * TDZ_EUNSUPPORTED (the choice was not set up for this batch). */
+ * Errors: TDZ_EINVAL (unknown option or value), TDZ_EUNSUPPORTED (the choice was not set up for
+ * this batch). */
 #define TDZ_OPT_PRECOND          1
 #define TDZ_OPT_OPERATOR         2
 #define TDZ_OPT_APPLY_GROUPS     3
