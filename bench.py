@@ -14,8 +14,13 @@ precisions.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--h2p-steps S]
                   [--nd-legs 2d,dots,3d] [--nd-steps S]
 
-Prints one JSON line. With torchrun (N > 1) each rank propagates its own full batch (weak
-scaling, no data-path collective); rank 0 prints the line with the max time over ranks.
+Prints one JSON line. With torchrun (N > 1) the batch grows to N x 256 geometries and is split over
+the ranks by the longest-processing-time rule on coefficients x steps (weak scaling: each rank holds
+about the one-GPU batch; no collective inside the time loop); rank 0 prints the line with the max time
+over ranks and gathers every run's status on the host.
+
+The CPU baseline is the oracle on the host cores (one run per spawned process); the same runs, whole
+pulse, also check the mixed path's harmonic yields against the oracle's.
 """
 from __future__ import annotations
 
@@ -41,7 +46,6 @@ sys.path.insert(0, ROOT)
 
 import workloads as wl  # noqa: E402
 
-CPU_MAX_STEPS = 2000
 # DRAM bytes (read + write) per coefficient-step of the mixed 1-D kernel, from one ncu capture of
 # this kernel version on the DQW batch (dram__bytes 826.27 GB/s over the 3.469 ms warm-up launch:
 # 2.867 GB for 3 steps of 1 873 260 coefficients); the traffic of a timed launch is this times its
@@ -126,52 +130,119 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- CPU baseline (oracle)
-def cpu_oracle_leg(wk, c0s, nruns_sample, nsteps_sample, ops_mats=None):
-    """Time the CPU oracle (as it stands) on a bounded sample: the first `nruns_sample` runs for
-    `nsteps_sample` steps. Returns (value, details, final states, observables)."""
+def _oracle_worker(job):
+    """One run through the CPU oracle, as it stands, in a spawned worker process (one BLAS thread):
+    assembly, `warm` untimed and then `steps` timed Crank-Nicolson steps. Returns (job index, final
+    state, observables of the timed steps, timed seconds, coefficients)."""
+    idx, run, c0, dt, warm, steps = job
     from oracle import assemble, propagate
-    mats = {}
-    finals, obs = [], []
-    t_asm = 0.0
-    if nsteps_sample + 1 > len(wk.runs[0].field):
-        raise ValueError("field shorter than the requested oracle sample")
-    for i in range(nruns_sample):
-        r = wk.runs[i]
-        if r.geometry not in mats:
-            t0 = time.perf_counter()
-            mats[r.geometry] = assemble.assemble_1d(r.knots, r.degree, r.nquad, r.medium)
-            t_asm += time.perf_counter() - t0
+    m = assemble.assemble_1d(run.knots, run.degree, run.nquad, run.medium)
+    c = np.asarray(c0, dtype=np.complex128)
+    if warm:
+        c, _ = propagate.cn_propagate(m, c, run.field, dt, warm)
     t0 = time.perf_counter()
-    dof = 0
-    for i in range(nruns_sample):
-        r = wk.runs[i]
-        c, o = propagate.cn_propagate(mats[r.geometry], c0s[i], r.field, wk.dt, nsteps_sample)
-        finals.append(c)
-        obs.append(o)
-        dof += len(c)
-    t = time.perf_counter() - t0
-    return dof * nsteps_sample / t, {"seconds": t, "dof": dof, "assembly_s": t_asm}, finals, obs
+    c, obs = propagate.cn_propagate(m, c, run.field, dt, steps, step0=warm)
+    return idx, c, obs, time.perf_counter() - t0, len(c)
+
+
+def oracle_pool_leg(runs, c0s, dt, warm, steps):
+    """The CPU oracle on the host cores: one independent run per spawned process, all concurrently.
+    Throughput = coefficient-steps of all runs / the longest run's timed seconds. Returns (value,
+    details, per-run results in input order)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    jobs = [(i, runs[i], c0s[i], dt, warm, steps) for i in range(len(runs))]
+    t0 = time.perf_counter()
+    with ctx.Pool(len(jobs)) as pool:
+        out = sorted(pool.map(_oracle_worker, jobs, chunksize=1), key=lambda x: x[0])
+    wall = time.perf_counter() - t0
+    secs = [o[3] for o in out]
+    dof = [o[4] for o in out]
+    longest = max(secs)
+    single = sum(d * steps / t for d, t in zip(dof, secs)) / len(out)
+    return sum(dof) * steps / longest, {"seconds": longest, "wall_s": wall, "dof": sum(dof), "single_core": single}, out
+
+
+def cpu_workers(args) -> int:
+    return max(1, min(os.cpu_count() or 1, args.cpu_workers))
 
 
 def reference_arm(args):
-    """--impl reference: the CPU oracle (the stated reference for this build) on host cores."""
+    """--impl reference: the CPU oracle (the stated reference for this build) on the host cores, one
+    run of the batch per process, W warm-up and K timed steps each."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    nsample = 8
+    nw = cpu_workers(args)
     wk = build_batch_inputs(args.n_geom, 4, args.warmup + args.steps + 1)
-    c0s = [initial_state(wk.runs[i], wk.runs[i].medium) for i in range(nsample)]
-    # warm-up: W steps on one run (imports, caches)
-    cpu_oracle_leg(wk, c0s, 1, max(1, args.warmup))
-    value, det, _, _ = cpu_oracle_leg(wk, c0s, nsample, args.steps)
-    sample = f"first {nsample} runs of the batch for {args.steps} steps ({det['dof']} coefficients/step)"
+    runs = wk.runs[:nw]
+    c0s = [initial_state(r, r.medium) for r in runs]
+    value, det, _ = oracle_pool_leg(runs, c0s, wk.dt, args.warmup, args.steps)
+    sample = (f"first {nw} runs of the batch ({det['dof']} coefficients), one per process, concurrently; "
+              f"{args.warmup} warm-up + {args.steps} timed steps each")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * det["seconds"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": "dqw_batch_1d", "runs": len(wk.runs), "sample_runs": nsample, "degree": 6},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "config": {"workload": "dqw_batch_1d", "runs": len(wk.runs), "sample_runs": nw, "degree": 6},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": nw, "nproc": os.cpu_count(), "kind": "oracle",
+                             "sample": sample, "single_core": {"value": det["single_core"], "unit": UNIT}},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def cpu_leg(tdz, args):
+    """CPU baseline and the accuracy of the mixed path on whole pulses. The first `cpu_workers` runs of
+    the batch (their whole 4-cycle pulse) go through the oracle, one run per host core, and through the
+    GPU mixed path; compared are the final states (rel-L2), the dipoles, the norm drift and every
+    odd-harmonic yield up to the run's cutoff I_p + 3.17 U_p (length form w^4 |d~|^2, Sec. "Dipoles";
+    I_p = barrier top minus the ground level, U_p with the well mass)."""
+    from oracle import assemble, eigen, hhg
+    nw = cpu_workers(args)
+    wk = build_batch_inputs(args.n_geom, 4, None)
+    runs = wk.runs[:nw]
+    c0s = [initial_state(r, r.medium) for r in runs]
+    value, det, out = oracle_pool_leg(runs, c0s, wk.dt, 0, wk.nsteps)
+    geoms = sorted({r.geometry for r in runs})
+    ops, ip = [], {}
+    for g in geoms:
+        r = next(x for x in runs if x.geometry == g)
+        ops.append(tdz.assemble_1d(r.knots, r.degree, r.medium, r.nquad))
+        m = assemble.assemble_1d(r.knots, r.degree, r.nquad, r.medium)
+        ip[g] = max(r.medium["potential"]["V"]) - eigen.ground_state(m, sigma=-1e-3, dense_max=0)[0]
+    b = tdz.Batch(ops, [geoms.index(r.geometry) for r in runs], tdz.MIXED)
+    for i, c in enumerate(c0s):
+        b.set_state(i, c)
+    b.propagate(np.ascontiguousarray(np.stack([r.field for r in runs])), wk.dt, 0, wk.nsteps)
+    w0 = wk.notes["omega"]
+    rel = dmax = herr = drift = 0.0
+    nharm = 0
+    for i, r in enumerate(runs):
+        _, c_o, obs_o, _, _ = out[i]
+        og, st = b.observe(i)
+        if st != 0:
+            raise RuntimeError(f"GPU run {i} status {st}")
+        rel = max(rel, float(np.linalg.norm(b.get_state(i) - c_o) / np.linalg.norm(c_o)))
+        dmax = max(dmax, float(np.max(np.abs(og[:, 2] - obs_o[:, 2])) / max(1e-30, np.max(np.abs(obs_o[:, 2])))))
+        drift = max(drift, float(np.max(np.abs(og[:, 4] - og[0, 4]))))
+        qcut = max(3, int(math.floor(hhg.cutoff_harmonic(ip[r.geometry], float(np.max(np.abs(r.field))), w0,
+                                                          m_eff=0.067))))
+        om, So = hhg.spectrum(obs_o[:, 2], wk.dt, length_form=True)
+        _, Sg = hhg.spectrum(og[:, 2], wk.dt, length_form=True)
+        _, Yo = hhg.harmonic_yields(om, So, w0, qcut)
+        _, Yg = hhg.harmonic_yields(om, Sg, w0, qcut)
+        herr = max(herr, float(np.max(np.abs(Yg / Yo - 1))))
+        nharm += len(Yo)
+    del b
+    cpu = {"value": value, "unit": UNIT, "cores": nw, "nproc": os.cpu_count(), "kind": "oracle",
+           "sample": (f"first {nw} runs of the batch, whole 4-cycle pulse ({wk.nsteps} steps, {det['dof']} "
+                      f"coefficients), one run per process, concurrently; value = coefficient-steps / the "
+                      f"longest run's {det['seconds']:.1f} s"),
+           "single_core": {"value": det["single_core"], "unit": UNIT, "cores": 1,
+                           "sample": "mean over the same runs of each run's own throughput"}}
+    acc = {"runs": nw, "steps": wk.nsteps, "max_rel_l2": rel, "max_dipole_rel_err": dmax, "max_norm_drift": drift,
+           "max_hhg_yield_rel_err": herr, "harmonics_compared": nharm,
+           "hhg": "odd q up to I_p + 3.17 U_p per run, w^4 |d~|^2 with a Kaiser (beta 8) window"}
+    return cpu, acc
 
 
 def _nd_time(tdz, name, ops, run_ops, c0s, fields, dt, nsteps, extra):
@@ -376,7 +447,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n-geom", type=int, default=256)
     ap.add_argument("--fp64-steps", type=int, default=10)
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-workers", type=int, default=16, help="oracle processes (one run each), <= nproc")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--nd-steps", type=int, default=2)
     ap.add_argument("--nd-legs", default="2d,dots,3d", help="comma list of 2d, dots, 3d (empty: none)")
@@ -401,21 +472,28 @@ def main():
     import paper_2608_18472_b300 as tdz
 
     nsteps_total = args.warmup + args.steps
-    # every rank builds its own shard: the full scan with a rank-dependent seed (weak scaling)
-    # field samples long enough for the timed window, the FP64 leg and the oracle sample (<= 2000 steps)
-    wk = build_batch_inputs(args.n_geom, 4, max(nsteps_total, args.fp64_steps, CPU_MAX_STEPS) + 1, seed=wl.SEED + rank)
-    runs = wk.runs
+    # one global batch of world x n_geom geometries x 4 intensities (seeded), split over the ranks by the
+    # longest-processing-time rule on coefficients x steps: every rank propagates only its own runs, about
+    # the work of the one-GPU batch (weak scaling), with no collective inside the time loop
+    from paper_2608_18472_b300 import shard
+    wk = build_batch_inputs(args.n_geom * world, 4, max(nsteps_total, args.fp64_steps) + 1)
+    run_dof = [len(r.knots) - r.degree - 3 for r in wk.runs]
+    dof_all = sum(run_dof)
+    mine = shard.lpt_partition([d * nsteps_total for d in run_dof], world)[rank]
+    runs = [wk.runs[i] for i in mine]
     geoms = {}
     for r in runs:
         if r.geometry not in geoms:
             geoms[r.geometry] = tdz.assemble_1d(r.knots, r.degree, r.medium, r.nquad)
-    ops = [geoms[g] for g in sorted(geoms)]
-    run_ops = [r.geometry for r in runs]
+    gids = sorted(geoms)
+    ops = [geoms[g] for g in gids]
+    run_ops = [gids.index(r.geometry) for r in runs]
     c0 = [initial_state(r, r.medium) for r in runs]
     p = runs[0].degree
     field_all = np.ascontiguousarray(np.stack([r.field for r in runs]))  # [runs, steps+1, 1]
     nruns = len(runs)
     dof = sum(ops[g].n for g in run_ops)
+    assert dof == sum(run_dof[i] for i in mine)
     stream = torch.cuda.current_stream()
 
     def make_batch(prec):
@@ -448,14 +526,19 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
         dist.barrier()
-    drift = 0.0
-    statuses = []
+    local = {}
     for i in range(nruns):
         o, st = bm.observe(i)
-        statuses.append(st)
-        drift = max(drift, float(np.max(np.abs(o[:, 4] - norm0[i]) / norm0[i])))
+        local[mine[i]] = (int(st), float(np.max(np.abs(o[:, 4] - norm0[i]) / norm0[i])))
     max_rel, nsolve = bm.refine_stats()
     solves_per_step = nsolve / (nruns * (args.warmup + args.steps))
+    summary = shard.gather_runs(local, len(wk.runs))       # host-side gather of every run's status and drift
+    if dist:
+        t = torch.tensor([max_rel, solves_per_step], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        max_rel, solves_per_step = float(t[0]), float(t[1])
+    statuses = [x[0] for x in summary] if summary else []
+    drift = max(x[1] for x in summary) if summary else 0.0
 
     # ---------------- plain FP64 on the same batch (comparison leg)
     bf = make_batch(tdz.FP64)
@@ -485,10 +568,14 @@ def main():
     bm.observe_all(out=obs_host)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
     h2d = (pinned_field.numel() * 8 + pinned_state.numel() * 8) / args.steps
     d2h = obs_host.numel() * 8 / args.steps
 
-    value = world * dof * args.steps / (ms * 1e-3)
+    value = dof_all * args.steps / (ms * 1e-3)
     value64 = dof * args.fp64_steps / (ms64 * 1e-3)
     flops = flops_per_dof_step(p) * dof * args.steps
     peak_fp32 = 148 * 128 * 2 * 2.032e9 / 1e12  # TFLOP/s, unit counts x max clock
@@ -497,9 +584,10 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+ff", "data": "synthetic",
-            "config": {"workload": "dqw_batch_1d", "runs": nruns, "geometries": len(ops), "coefficients": dof,
+            "config": {"workload": "dqw_batch_1d", "runs": len(wk.runs), "geometries": args.n_geom * world,
+                       "coefficients": dof_all, "runs_per_gpu": nruns, "coefficients_per_gpu": dof,
                        "degree": p, "dt": wk.dt, "precision": "mixed", "l2": "working set > L2 (126 MB): no flush",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"dp{world}: LPT shards of one batch" if world > 1 else "dp1"},
             "gpu_launches": 1,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
                          "frac": achieved / peak_fp32,
@@ -509,10 +597,10 @@ def main():
                                   "counts and max clock); traffic: DRAM bytes of the timed launch (ncu bytes per "
                                   "coefficient-step x coefficient-steps)")},
             "plain_fp64": {"value": value64, "unit": UNIT, "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps,
-                           "speedup_mixed": value / world / value64},
+                           "speedup_mixed": dof * args.steps / (ms * 1e-3) / value64},
             "accuracy": {"norm_drift_max": drift, "refine_max_rel_residual": max_rel,
                          "solves_per_step": solves_per_step, "runs_not_ok": int(sum(s != 0 for s in statuses))},
-            "e2e": {"value": world * dof * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "e2e": {"value": dof_all * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "clocks": clk.summary()}
     # ---------------- 2-D leg: the soft-core atom of the 2-D configuration (1024 x 1024 order-7 splines),
@@ -522,25 +610,7 @@ def main():
     if rank == 0 and args.nd_steps > 0 and args.nd_legs:
         line.update(nd_legs(tdz, args.nd_steps, args.nd_legs.split(","), args.nd_2d_splines, args.nd_3d_splines))
     if rank == 0 and not args.no_cpu:
-        # bounded oracle sample sized to ~cpu_seconds; GPU mixed path compared on the same sample
-        ns_probe = 20
-        v_probe, det, _, _ = cpu_oracle_leg(wk, c0, 1, ns_probe)
-        per_run_step = det["seconds"] / ns_probe
-        nsample = 8
-        nsteps_s = max(20, min(CPU_MAX_STEPS, int(args.cpu_seconds / (per_run_step * nsample))))
-        v, det, finals, oobs = cpu_oracle_leg(wk, c0, nsample, nsteps_s)
-        bs = tdz.Batch(ops, run_ops[:nsample], tdz.MIXED)
-        for i in range(nsample):
-            bs.set_state(i, c0[i])
-        bs.propagate(np.ascontiguousarray(field_all[:nsample, :nsteps_s + 1]), wk.dt, 0, nsteps_s)
-        rel = max(np.linalg.norm(bs.get_state(i) - finals[i]) / np.linalg.norm(finals[i]) for i in range(nsample))
-        dmax = max(np.max(np.abs(bs.observe(i)[0][:, 2] - oobs[i][:, 2])) / max(1e-30, np.max(np.abs(oobs[i][:, 2])))
-                   for i in range(nsample))
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"first {nsample} runs x {nsteps_s} steps ({det['dof']} coefficients), "
-                                          f"{det['seconds']:.1f} s single-threaded"}
-        line["accuracy"]["sample_vs_oracle"] = {"runs": nsample, "steps": nsteps_s, "max_rel_l2": rel,
-                                                "max_dipole_rel_err": dmax}
+        line["cpu_baseline"], line["accuracy"]["sample_vs_oracle"] = cpu_leg(tdz, args)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

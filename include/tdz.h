@@ -249,7 +249,10 @@ void tdz_batch_destroy(tdz_batch* b);
  *   field : device, E(t_{step0+k}) for k = 0..nsteps.   state: device, [2n] complex in/out.
  *   obs   : device, [nsteps][5] = t, E, d, a, norm (as tdz_observe).
  *   status: host, optional; if given the call synchronises the stream and stores the run status.
- * Limits: n <= TDZ_NOALLOC_MAX_N, degree <= 8; larger sizes return TDZ_EINVAL with a message.
+ *           Pass NULL when the call is recorded into a stream capture (a synchronisation is not
+ *           allowed there); read the status later from obs instead (non-finite norms).
+ * Limits: n <= TDZ_NOALLOC_MAX_N, degree <= 8; larger sizes return TDZ_EINVAL with a message, and
+ * so does a current device index of 64 or more.
  * The first call on a device resolves the array's device address with cudaGetSymbolAddress
  * (that device current); make that first call before any stream capture. Every call shares the
  * one array and overwrites it (the call initialises all of it that it reads), so calls that

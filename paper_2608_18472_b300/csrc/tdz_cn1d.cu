@@ -1154,6 +1154,31 @@ size_t smem_per_warp(int P, bool mixed) {
   return (size_t)red_elems(P) * cxsz;
 }
 
+// The dynamic shared-memory limit of a kernel is one attribute of the function, shared by every host
+// thread that launches it. It is only ever raised, straight to the largest size any launch of this
+// instantiation can use on the device (the most warp slots a block gets, times the per-warp reduced
+// system), so a launch made on one thread never finds the limit lowered by a call on another.
+template <int P, bool M>
+cudaError_t ensure_smem(size_t need) {
+  static std::mutex mu;
+  static size_t set_to[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(mu);
+  if (set_to[dev] >= need) return cudaSuccess;
+  int maxsm = 0;
+  e = cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  const size_t spw = smem_per_warp(P, M);
+  const size_t cap = std::min<size_t>(8, std::max<size_t>(1, (size_t)maxsm / spw)) * spw;
+  const size_t v = std::max(need, cap);
+  e = cudaFuncSetAttribute(cn1d_kernel<P, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v);
+  if (e == cudaSuccess) set_to[dev] = v;
+  return e;
+}
+
 }  // namespace
 
 namespace {
@@ -1331,7 +1356,7 @@ namespace {
 template <int P, bool M>
 cudaError_t launch_p(tdz_batch* b, const StepArgs& a) {
   const size_t sm = smem_per_warp(P, M) * b->warps_per_block;
-  cudaError_t e = cudaFuncSetAttribute(cn1d_kernel<P, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = ensure_smem<P, M>(sm);
   if (e != cudaSuccess) return e;
   cn1d_kernel<P, M><<<b->blocks, 32 * b->warps_per_block, sm, b->stream>>>(a);
   return cudaGetLastError();
@@ -1949,7 +1974,7 @@ static std::mutex g_noalloc_mu;
 template <int P>
 cudaError_t noalloc_launch(cudaStream_t st, const StepArgs& a) {
   const size_t sm = smem_per_warp(P, false);
-  cudaError_t e = cudaFuncSetAttribute(cn1d_kernel<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = ensure_smem<P, false>(sm);
   if (e != cudaSuccess) return e;
   cn1d_kernel<P, false><<<1, 32, sm, st>>>(a);
   return cudaGetLastError();
@@ -2000,7 +2025,11 @@ extern "C" int tdz_cn1d_propagate_noalloc(const double* bands, int64_t n, int de
   }
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= 64) return cuda_fail(e, "tdz_cn1d_propagate_noalloc: device");
+  if (e != cudaSuccess) return cuda_fail(e, "tdz_cn1d_propagate_noalloc: device");
+  if (dev < 0 || dev >= 64) {
+    set_error("tdz_cn1d_propagate_noalloc: device index " + std::to_string(dev) + " beyond the 64 devices supported");
+    return TDZ_EINVAL;
+  }
   double* scr = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_noalloc_mu);

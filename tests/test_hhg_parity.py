@@ -1,0 +1,103 @@
+"""The HHG bar of the mixed-precision path on whole pulses, against the CPU oracle.
+
+Sec. "Dipoles": S(w) = |int a W e^{iwt}|^2 ~ w^4 |int d W e^{iwt}|^2 with a Kaiser window W. The mixed
+path (FP32 factors and solves, double-float residuals) must give every odd-harmonic yield up to the
+cutoff I_p + 3.17 U_p within 1e-3 of the oracle's, with norm drift <= 1e-8; the binary64 path must
+match the oracle's final state to 1e-9 (rel-L2).
+
+* the headline workload's shape: one double-quantum-well geometry of the 1-D batch (800-900 order-6
+  splines, knots on every interface) under the batch's four mid-IR intensities (10 um, 4-cycle sin^2,
+  dt = 0.5: 11 032 steps), started from the batch's left-well wavepacket; the position-dependent-mass
+  runs use the length form w^4 |d~|^2 (the a_Q term of Eq. pdm_acceleration is not evaluated);
+* a small 2-D soft-core atom (22 x 22 order-4 splines) through a 3-cycle pulse (2 513 steps), both
+  length and acceleration forms.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import bench
+import workloads as wl
+from oracle import assemble, eigen, hhg, propagate
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tdz():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_2608_18472_b300 as m
+    return m
+
+
+def _yields(sig, dt, w0, qcut, length_form):
+    om, S = hhg.spectrum(sig, dt, length_form=length_form)
+    return hhg.harmonic_yields(om, S, w0, qcut)
+
+
+def test_dqw_runs_full_pulse_hhg_yields(tdz):
+    wk = wl.dqw_batch(n_geometries=1, fields_per_geometry=4, nsplines_range=(800, 900), seed=wl.SEED)
+    runs = wk.runs
+    r0 = runs[0]
+    m = assemble.assemble_1d(r0.knots, r0.degree, r0.nquad, r0.medium)
+    ops = tdz.assemble_1d(r0.knots, r0.degree, r0.medium, r0.nquad)
+    c0 = bench.initial_state(r0, r0.medium)
+    w0 = wk.notes["omega"]
+    e_ground = eigen.ground_state(m, sigma=-1e-3, dense_max=0)[0]
+    v0 = max(r0.medium["potential"]["V"])
+    field = np.stack([r.field for r in runs])
+    res = {}
+    for prec in (tdz.MIXED, tdz.FP64):
+        b = tdz.Batch([ops], [0] * len(runs), prec)
+        for i in range(len(runs)):
+            b.set_state(i, c0)
+        b.propagate(field, wk.dt, 0, wk.nsteps)
+        res[prec] = [(b.get_state(i), *b.observe(i)) for i in range(len(runs))]
+        del b
+    for i, r in enumerate(runs):
+        c, obs = propagate.cn_propagate(m, c0, r.field, wk.dt, wk.nsteps)
+        e0 = float(np.max(np.abs(r.field)))
+        qcut = max(3, int(math.floor(hhg.cutoff_harmonic(v0 - e_ground, e0, w0, m_eff=0.067))))
+        qs, Yo = _yields(obs[:, 2], wk.dt, w0, qcut, True)
+        cg, og, st = res[tdz.FP64][i]
+        assert st == tdz.TDZ_OK
+        assert np.linalg.norm(cg - c) / np.linalg.norm(c) < 1e-9, i
+        assert np.max(np.abs(og[:, 4] - og[0, 4])) < 1e-10, i
+        cm, om, stm = res[tdz.MIXED][i]
+        assert stm == tdz.TDZ_OK
+        assert np.max(np.abs(om[:, 4] - om[0, 4])) < 1e-8, i
+        _, Ym = _yields(om[:, 2], wk.dt, w0, qcut, True)
+        assert np.all(Yo > 0)
+        assert np.max(np.abs(Ym / Yo - 1)) < 1e-3, (i, qs, Ym / Yo - 1)
+
+
+def test_softcore_2d_full_pulse_hhg_yields(tdz):
+    p, dt = 4, 0.05
+    t = wl.knots_for_nsplines(-12.0, 12.0, 22, p)
+    med = wl.softcore_medium(0.5)
+    w0, e0, ncyc = 0.15, 0.12, 3.0
+    nsteps = int(math.ceil(ncyc * 2 * math.pi / w0 / dt))
+    field = wl.sin2_pulse(wl.time_grid(dt, nsteps), e0, w0, ncyc, dim=2)
+    m = assemble.assemble_nd([t, t], [p, p], [p + 1, p + 1], med)
+    e_ground, c0 = eigen.ground_state(m)
+    c, obs = propagate.cn_propagate(m, c0, field, dt, nsteps)
+    qcut = int(math.floor(hhg.cutoff_harmonic(-e_ground, e0, w0)))
+    assert qcut >= 5
+    ops = tdz.Ops([tdz.Basis(t, p, p + 1)] * 2, med)
+    for prec in (tdz.MIXED, tdz.FP64):
+        b = tdz.Batch([ops], [0], prec)
+        b.set_state(0, c0)
+        b.propagate(field.reshape(1, nsteps + 1, 2), dt, 0, nsteps)
+        og, st = b.observe(0)
+        assert st == tdz.TDZ_OK
+        assert np.max(np.abs(og[:, -1] - og[0, -1])) < (1e-8 if prec == tdz.MIXED else 1e-10)
+        if prec == tdz.FP64:
+            cg = b.get_state(0)
+            assert np.linalg.norm(cg - c) / np.linalg.norm(c) < 1e-9
+        for col, length in ((3, True), (5, False)):     # d_x (length form) and a_x (acceleration form)
+            qs, Yo = _yields(obs[:, col], dt, w0, qcut, length)
+            _, Yg = _yields(og[:, col], dt, w0, qcut, length)
+            assert np.max(np.abs(Yg / Yo - 1)) < 1e-3, (prec, col, qs, Yg / Yo - 1)
+        del b

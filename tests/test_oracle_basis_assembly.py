@@ -266,3 +266,184 @@ def test_hydrogenic_knots_follow_the_grading():
     nl = wl.hydrogenic_split(400.0, 0.2, n_side)
     rc = nl * 0.2
     assert abs(rc * np.expm1(np.log(400.0 / rc) / (n_side - nl)) - 0.2) < 2e-3
+
+
+# ------------------------------------------------------------------ 2-D / 3-D non-separable media
+# The elliptical dot (Sec. "Parallel assembly": m^-1 and V sampled pointwise at the Gauss points) and the
+# 2-D/3-D soft core have no closed-form matrices; these tests pin them to the separable 1-D assembly
+# (itself pinned above by the square-well and DQW tests) where the medium reduces to a product, and to
+# the symmetries the definitions fix.
+def _kr(a, b):
+    return sp.kron(a, b).tocsr()
+
+
+def _maxdiff(A, B):
+    return abs(A - B).max()
+
+
+def _layers_1d(bounds, m_vals, v_vals):
+    return wl.medium({"kind": "layers", "bounds": bounds, "m": m_vals}, {"kind": "layers", "bounds": bounds, "V": v_vals})
+
+
+def _ellipse(a, b, m_in, m_out, v_in, v_out):
+    return wl.medium({"kind": "ellipse", "a": a, "b": b, "m_in": m_in, "m_out": m_out},
+                     {"kind": "ellipse", "a": a, "b": b, "v_in": v_in, "v_out": v_out})
+
+
+def test_ellipse_covering_or_missing_the_domain_is_the_constant_medium():
+    """A dot that holds every Gauss point is the constant medium (m_in, v_in); one that holds none is
+    (m_out, v_out): T = m^-1 (S (x) T1 + T1 (x) S), V = v S (x) S, K = m^-1 S (x) S, G = 0."""
+    p, L = 3, 5.0
+    t = wl.knots_for_nsplines(-L, L, 13, p)
+    one = assemble.assemble_1d(t, p, p + 1, wl.medium({"kind": "const", "m": 1.0}, {"kind": "zero"}))
+    S1, T1 = one["S"], one["T"]
+    m_in, m_out, v_in, v_out = 0.4, 1.3, -0.7, 0.25
+    for a, m, v in ((40 * L, m_in, v_in), (1e-3, m_out, v_out)):
+        m2 = assemble.assemble_nd([t, t], [p, p], [p + 1, p + 1], _ellipse(a, a, m_in, m_out, v_in, v_out))
+        scale = abs(m2["T"]).max()
+        assert _maxdiff(m2["T"], (_kr(S1, T1) + _kr(T1, S1)) / m) < 1e-13 * scale
+        assert _maxdiff(m2["V"], v * _kr(S1, S1)) < 1e-14
+        assert _maxdiff(m2["K"], _kr(S1, S1) / m) < 1e-14
+        assert abs(m2["G"][0]).max() == 0.0 and abs(m2["G"][1]).max() == 0.0
+
+
+def test_ellipse_with_equal_inside_and_outside_is_separable():
+    """m_in = m_out and v_in = v_out: the dot's boundary must leave no trace."""
+    p = 3
+    t = wl.knots_for_nsplines(-6.0, 6.0, 14, p)
+    one = assemble.assemble_1d(t, p, p + 1, wl.medium({"kind": "const", "m": 1.0}, {"kind": "zero"}))
+    m2 = assemble.assemble_nd([t, t], [p, p], [p + 1, p + 1], _ellipse(3.0, 2.0, 0.6, 0.6, -0.3, -0.3))
+    S1, T1 = one["S"], one["T"]
+    assert _maxdiff(m2["T"], (_kr(S1, T1) + _kr(T1, S1)) / 0.6) < 1e-13 * abs(m2["T"]).max()
+    assert _maxdiff(m2["V"], -0.3 * _kr(S1, S1)) < 1e-14
+
+
+def test_ellipse_stripe_equals_layered_1d_assembly():
+    """A dot stretched along x far beyond the domain (a = 1e8) is a stripe |y| < b: with knots on y = +-b,
+    m^-1 and V depend on y alone and the 2-D matrices are Kronecker products of the 1-D layered assembly
+    along y (x fastest): T = K_y (x) T1_x + T_y (x) S_x, V = V_y (x) S_x, K = K_y (x) S_x, D_x = S_y (x) D_x,
+    D_y = D_y (x) S_x. Swapped semi-axes, a mass that misses the kinetic term or an inside/outside mix-up
+    all break it."""
+    p, L, b = 3, 6.0, 2.0
+    tx = wl.knots_for_nsplines(-L, L, 12, p)
+    ty = wl.open_piecewise_knots([-L, -b, b, L], [4, 5, 4], p)
+    m_in, m_out, v_in, v_out = 0.5, 1.25, -0.8, 0.3
+    m2 = assemble.assemble_nd([tx, ty], [p, p], [p + 1, p + 1], _ellipse(1e8, b, m_in, m_out, v_in, v_out))
+    mx = assemble.assemble_1d(tx, p, p + 1, wl.medium({"kind": "const", "m": 1.0}, {"kind": "zero"}))
+    my = assemble.assemble_1d(ty, p, p + 1, _layers_1d([-L, -b, b, L], [m_out, m_in, m_out], [v_out, v_in, v_out]))
+    tol = 1e-13 * abs(m2["T"]).max()
+    assert _maxdiff(m2["T"], _kr(my["K"], mx["T"]) + _kr(my["T"], mx["S"])) < tol
+    assert _maxdiff(m2["V"], _kr(my["V"], mx["S"])) < 1e-14
+    assert _maxdiff(m2["K"], _kr(my["K"], mx["S"])) < 1e-14
+    assert _maxdiff(m2["D"][0], _kr(my["S"], mx["D"][0])) < 1e-13
+    assert _maxdiff(m2["D"][1], _kr(my["D"][0], mx["S"])) < 1e-13
+    # the transposed stripe (long axis along y) is the same problem with x and y exchanged
+    m2t = assemble.assemble_nd([ty, tx], [p, p], [p + 1, p + 1], _ellipse(b, 1e8, m_in, m_out, v_in, v_out))
+    assert _maxdiff(m2t["T"], _kr(mx["T"], my["K"]) + _kr(mx["S"], my["T"])) < tol
+    assert _maxdiff(m2t["V"], _kr(mx["S"], my["V"])) < 1e-14
+
+
+def test_ellipse_point_classification():
+    """The dot's definition at chosen points: inside iff x^2/a^2 + y^2/b^2 < 1, the boundary outside
+    (the reading of the dot geometry); semi-axis a along x, b along y."""
+    med = _ellipse(4.0, 1.0, 0.5, 2.0, -1.0, 3.0)
+    X = (np.array([0.0, 3.9, 0.0, 0.0, 4.0, 0.0, 2.0]), np.array([0.0, 0.0, 0.9, 3.9, 0.0, 1.0, 0.8]))
+    inside = np.array([True, True, True, False, False, False, True])
+    assert np.array_equal(assemble.inv_mass(med, X), np.where(inside, 2.0, 0.5))
+    assert np.array_equal(assemble.potential(med, X), np.where(inside, -1.0, 3.0))
+    assert not np.any(assemble.grad_potential(med, X, 0)) and not np.any(assemble.grad_potential(med, X, 1))
+
+
+def _swap_xy(n):
+    """Permutation matrix of i_x + n i_y -> i_y + n i_x on an n x n grid."""
+    idx = np.arange(n * n)
+    ix, iy = idx % n, idx // n
+    return sp.csr_matrix((np.ones(n * n), (iy + n * ix, idx)), shape=(n * n, n * n))
+
+
+@pytest.mark.parametrize("kind", ["circle", "softcore"])
+def test_xy_exchange_symmetry_2d(kind):
+    """On equal x and y grids a circular dot and the 2-D soft core are invariant under x <-> y: S, T, V,
+    K keep their form, D_x and G_x turn into D_y and G_y; an ellipse turns into the one with exchanged
+    semi-axes. The first excited pair (p_x, p_y) of the symmetric problems is degenerate."""
+    p = 3
+    t = wl.knots_for_nsplines(-6.0, 6.0, 14, p)
+    med = _ellipse(3.0, 3.0, 0.5, 1.0, -1.0, 0.0) if kind == "circle" else wl.softcore_medium(0.5)
+    m = assemble.assemble_nd([t, t], [p, p], [p + 1, p + 1], med)
+    P = _swap_xy(m["shape"][0])
+    sw = lambda A: (P @ A @ P.T).tocsr()
+    for key in ("S", "T", "V", "K"):
+        assert _maxdiff(sw(m[key]), m[key]) < 1e-14 * max(1.0, abs(m[key]).max()), key
+    for a in (0, 1):
+        assert _maxdiff(sw(m["D"][a]), m["D"][1 - a]) < 1e-14
+        assert _maxdiff(sw(m["G"][a]), m["G"][1 - a]) < 1e-14
+    w, _ = eigen.lowest_states(m, 3)
+    assert abs(w[1] - w[2]) < 1e-10 * abs(w[1]) and w[1] - w[0] > 1e-3
+    if kind == "circle":
+        ma = assemble.assemble_nd([t, t], [p, p], [p + 1, p + 1], _ellipse(3.5, 2.0, 0.5, 1.0, -1.0, 0.0))
+        mb = assemble.assemble_nd([t, t], [p, p], [p + 1, p + 1], _ellipse(2.0, 3.5, 0.5, 1.0, -1.0, 0.0))
+        for key in ("T", "V", "K"):
+            assert _maxdiff(sw(ma[key]), mb[key]) < 1e-14 * max(1.0, abs(ma[key]).max()), key
+        assert _maxdiff(ma["T"], mb["T"]) > 1e-3         # the two orientations do differ
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_softcore_gradient_matches_finite_difference(dim):
+    """dV/dx_a of the soft core -z/sqrt(|r|^2 + eps) in 2-D and 3-D against a central difference of V at
+    random points and at the Gauss points of a grid (a wrong sign, power or axis fails it)."""
+    rng = np.random.default_rng(9)
+    med = wl.softcore_medium(0.5, z=1.3)
+    X = tuple(rng.uniform(-4, 4, 300) for _ in range(dim))
+    q = bspline.quadrature_1d(wl.knots_for_nsplines(-3.0, 3.0, 9, 3), 3, 4)["x"].ravel()
+    G = np.meshgrid(*([q] * dim), indexing="ij")
+    h = 1e-5
+    for pts in (X, tuple(g.ravel() for g in G)):
+        for a in range(dim):
+            up = tuple(x + (h if b == a else 0.0) for b, x in enumerate(pts))
+            dn = tuple(x - (h if b == a else 0.0) for b, x in enumerate(pts))
+            fd = (assemble.potential(med, up) - assemble.potential(med, dn)) / (2 * h)
+            assert np.allclose(assemble.grad_potential(med, pts, a), fd, atol=2e-9, rtol=1e-7), a
+
+
+def test_softcore_3d_exchange_symmetry_and_acceleration_matrices():
+    """3-D soft core on equal grids: S, T, V, K invariant under the axis exchanges x<->y and y<->z, D_a and
+    G_a permuted with the axes; K = S for unit mass. G_a must also equal the matrix of the finite
+    difference of V: assembling V of the medium shifted by +-h along axis a gives G_a = (V(-h) - V(+h))/2h
+    up to O(h^2), since V(r - h e_a) - V(r + h e_a) = -2h dV/dx_a."""
+    p = 2
+    t = wl.knots_for_nsplines(-4.0, 4.0, 7, p)
+    med = wl.softcore_medium(0.5)
+    m = assemble.assemble_nd([t] * 3, [p] * 3, [p + 1] * 3, med)
+    n = m["shape"][0]
+    idx = np.arange(n ** 3)
+    i = [idx % n, (idx // n) % n, idx // (n * n)]
+
+    def perm(a, b):
+        j = list(i)
+        j[a], j[b] = i[b], i[a]
+        tgt = j[0] + n * j[1] + n * n * j[2]
+        return sp.csr_matrix((np.ones(n ** 3), (tgt, idx)), shape=(n ** 3, n ** 3))
+    for a, b in ((0, 1), (1, 2)):
+        P = perm(a, b)
+        sw = lambda A: (P @ A @ P.T).tocsr()
+        for key in ("S", "T", "V", "K"):
+            assert _maxdiff(sw(m[key]), m[key]) < 1e-14 * max(1.0, abs(m[key]).max()), key
+        for c in range(3):
+            c2 = b if c == a else (a if c == b else c)
+            assert _maxdiff(sw(m["D"][c]), m["D"][c2]) < 1e-14
+            assert _maxdiff(sw(m["G"][c]), m["G"][c2]) < 1e-14
+    assert _maxdiff(m["K"], m["S"]) < 1e-15
+    h = 1e-4
+    orig = assemble.potential
+    for a in range(3):
+        vs = []
+        for sgn in (+1, -1):
+            def shifted(md, X, _s=sgn, _a=a):
+                return orig(md, tuple(x + (_s * h if b == _a else 0.0) for b, x in enumerate(X)))
+            assemble.potential = shifted
+            try:
+                vs.append(assemble.assemble_nd([t] * 3, [p] * 3, [p + 1] * 3, med)["V"])
+            finally:
+                assemble.potential = orig
+        fd = (vs[0] - vs[1]) / (2 * h)
+        assert _maxdiff(fd, m["G"][a]) < 1e-7 * abs(m["G"][a]).max(), a

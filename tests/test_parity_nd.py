@@ -238,3 +238,100 @@ def test_batched_state_upload_and_observables_nd(tdz):
         assert st == st_all[i] == tdz.TDZ_OK
         assert np.allclose(o, obs_all[i], rtol=1e-12, atol=1e-14)
         assert np.allclose(a.get_state(i), b.get_state(i), rtol=1e-12, atol=1e-14)
+
+
+# ------------------------------------------------------------------ the degrees of the 2-D/3-D workloads
+# The benchmarked instantiations differ from the p = 3/4 cases above in their inner loops: at p = 7 the
+# fused FP32 2-D apply with 8 warp groups gives each warp two dy offsets, and p = 6 drives the 3-D
+# last-axis passes and the double-float observables of the 3-D workload. These cases run those
+# instantiations against the oracle element by element.
+def _bench_case(name):
+    if name == "softcore2d_p7":
+        # x: 138 coefficients = two full 64-row stencil tiles and a ragged one of 10; y: 22
+        kn = [wl.knots_for_nsplines(-40.0, 40.0, 140, 7), wl.knots_for_nsplines(-8.0, 8.0, 24, 7)]
+        return kn, 7, wl.softcore_medium(0.5), 0.05, 20, 0.1
+    if name == "dot2d_p6":
+        t = wl.knots_for_nsplines(-6.0, 6.0, 32, 6)
+        med = wl.medium({"kind": "ellipse", "a": 3.0, "b": 2.0, "m_in": 0.5, "m_out": 1.0},
+                        {"kind": "ellipse", "a": 3.0, "b": 2.0, "v_in": -1.0, "v_out": 0.0})
+        return [t, t], 6, med, 0.05, 20, 0.1
+    raise KeyError(name)
+
+
+def _bench_reference(name):
+    key = ("bench", name)
+    if key not in _REF:
+        knots, p, med, dt, nsteps, e0 = _bench_case(name)
+        m = assemble.assemble_nd(knots, [p] * 2, [p + 1] * 2, med)
+        _, c0 = eigen.ground_state(m, sigma=-3.0, dense_max=0)
+        field = wl.sin2_pulse(wl.time_grid(dt, nsteps), e0, 0.5, 1.0, ellipticity=0.3, dim=2)
+        c, obs = propagate.cn_propagate(m, c0, field, dt, nsteps)
+        _REF[key] = (m, c0, field, c, obs)
+    return _REF[key]
+
+
+def _check_against(og, cg, c, obs, dim, tol, what):
+    rel = np.linalg.norm(cg - c) / np.linalg.norm(c)
+    assert rel < tol, (what, rel)
+    assert np.max(np.abs(og[:, 0] - obs[:, 0])) < 1e-12
+    for col in range(1 + dim, 2 + 3 * dim):
+        scale = max(1e-3, np.max(np.abs(obs[:, col])))
+        assert np.max(np.abs(og[:, col] - obs[:, col])) < 10 * tol * scale, (what, col)
+
+
+@pytest.mark.parametrize("name", ["softcore2d_p7", "dot2d_p6"])
+def test_workload_degrees_2d_against_oracle(tdz, name):
+    """2-D at p = 7 (soft core, 138 x 22 coefficients) and p = 6 (elliptical dot, 30 x 30): binary64 with
+    each operator form and preconditioner, mixed precision with the fused FP32 apply forced to 8 and to 16
+    warp groups, all element by element against the oracle (1e-9 binary64, 1e-8 mixed)."""
+    knots, p, med, dt, nsteps, e0 = _bench_case(name)
+    m, c0, field, c, obs = _bench_reference(name)
+    ops = tdz.Ops([tdz.Basis(k, p, p + 1) for k in knots], med)
+    assert ops.n == m["S"].shape[0]
+    f = field.reshape(1, nsteps + 1, 2)
+    runs = [(tdz.FP64, op, pc, 0, 1e-9) for op, pc in _combos(2)]
+    runs += [(tdz.MIXED, "auto", "auto", g, 1e-8) for g in (8, 16)]
+    runs += [(tdz.MIXED, "quadrature", "lines", 0, 1e-8)]
+    for prec, op, pc, groups, tol in runs:
+        b = tdz.Batch([ops], [0], prec)
+        _configure(tdz, b, op, pc)
+        if groups:
+            b.set_option(tdz.OPT_APPLY_GROUPS, groups)
+        b.set_state(0, c0)
+        b.propagate(f, dt, 0, nsteps)
+        og, st = b.observe(0)
+        assert st == tdz.TDZ_OK, (prec, op, pc, groups, st)
+        _check_against(og, b.get_state(0), c, obs, 2, tol, (prec, op, pc, groups))
+        del b
+
+
+def test_workload_degree_3d_against_oracle(tdz):
+    """3-D soft core at p = 6, 10 coefficients per axis (the degree of the 3-D workload): the oracle
+    trajectory is stored by tests/golden/make_softcore3d_p6.py (the oracle's full tensor quadrature takes
+    minutes at this degree); binary64 and mixed, every operator and preconditioner choice."""
+    import os
+    import sys
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    sys.path.insert(0, here)
+    try:
+        import make_softcore3d_p6 as gold
+    finally:
+        sys.path.remove(here)
+    ref = np.load(os.path.join(here, "softcore3d_p6.npz"))
+    assert [str(x) for x in ref["param_names"]] == sorted(gold.PARAMS)
+    assert np.array_equal(ref["params"], np.array([gold.PARAMS[k] for k in sorted(gold.PARAMS)]))
+    knots, med, field = gold.inputs()
+    P = gold.PARAMS
+    p, dt, nsteps = P["p"], P["dt"], P["nsteps"]
+    ops = tdz.Ops([tdz.Basis(k, p, p + 1) for k in knots], med)
+    assert ops.n == len(ref["c0"])
+    for prec, tol in ((tdz.FP64, 1e-9), (tdz.MIXED, 1e-8)):
+        for op, pc in _combos(3) + [("quadrature", "fd")]:
+            b = tdz.Batch([ops], [0], prec)
+            _configure(tdz, b, op, pc)
+            b.set_state(0, ref["c0"])
+            b.propagate(field.reshape(1, nsteps + 1, 3), dt, 0, nsteps)
+            og, st = b.observe(0)
+            assert st == tdz.TDZ_OK, (prec, op, pc, st)
+            _check_against(og, b.get_state(0), ref["c"], ref["obs"], 3, tol, (prec, op, pc))
+            del b

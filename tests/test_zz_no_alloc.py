@@ -25,7 +25,10 @@ def _entry(tdz):
     return f
 
 
-@pytest.mark.parametrize("nspl,p", [(600, 6), (1000, 7), (30, 3)])
+# (4098, 8): n = 4096 = TDZ_NOALLOC_MAX_N at the largest degree, the full static scratch;
+# (771, 8): n = 3 P 32 + 1, one row past the size where the 32 chunks of the single warp are
+# exactly 3P rows long, so the last chunk is ragged
+@pytest.mark.parametrize("nspl,p", [(600, 6), (1000, 7), (30, 3), (4098, 8), (771, 8)])
 def test_noalloc_matches_batch_entry_two_calls(nspl, p):
     import torch
 
