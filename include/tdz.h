@@ -78,6 +78,22 @@ void tdz_basis_destroy(tdz_basis* b);
 #define TDZ_POT_ELLIPSE   5  /* 2-D dot, pot_par = {a, b, v_in, v_out}                            */
 #define TDZ_POT_H2P       6  /* 1-D two-centre soft core, pot_par = {R, eps} (Sec. Molecular HHG) */
 
+/* Absorbing boundary layer: the complex absorbing potential -i eta(r) of Sec. "Parallel assembly" (CAP
+ * matrix W = <B|eta|B>), eta = sum over the axes a of a 1-D mask of |x_a| that starts at |x_a| = r0 and
+ * ends at |x_a| = R, s = (|x_a| - r0)/(R - r0) in (0, 1]. The paper names a Manolopoulos-type mask and
+ * prints no formula; these are the two readings this library implements:
+ *   TDZ_CAP_POLY          eta = eta0 s^k,                         cap_par = {r0, R, eta0, k}
+ *   TDZ_CAP_MANOLOPOULOS  eta = (1/(2m)) (2 pi/(R - r0))^2 f(c s), cap_par = {r0, R, m, 0},
+ *        f(y) = a y - b y^3 + 4/(c - y)^2 - 4/(c + y)^2, a = 1 - 16/c^3, b = (1 - 17/c^3)/c^2,
+ *        c = 2.62206 (D. E. Manolopoulos, J. Chem. Phys. 117, 9552 (2002): a transmission-free layer that
+ *        absorbs with little reflection above E_min = (c/(2 (R - r0)))^2/(2m); it diverges at |x_a| = R,
+ *        which must therefore be the edge of the domain).
+ * With a layer, Eq. cn_system becomes (S + tau W + i tau H) c^{n+1} = (S - tau W - i tau H) c^n: still
+ * complex symmetric, and the norm c^H S c decreases by the flux the layer absorbs. */
+#define TDZ_CAP_NONE          0
+#define TDZ_CAP_POLY          1
+#define TDZ_CAP_MANOLOPOULOS  2
+
 typedef struct tdz_medium {
   int mass_kind;
   int pot_kind;
@@ -87,6 +103,8 @@ typedef struct tdz_medium {
   const double* layer_bounds;  /* host, nlayers+1 increasing points      */
   const double* layer_mass;    /* host, nlayers                          */
   const double* layer_pot;     /* host, nlayers                          */
+  int cap_kind;                /* TDZ_CAP_*; TDZ_CAP_NONE: no absorbing layer */
+  double cap_par[4];
 } tdz_medium;
 
 /* ------------------------------------------------------------------ assembly
@@ -95,9 +113,10 @@ typedef struct tdz_medium {
  *   S = <B|B> (Eq. mass_elem), T = 1/2 <dB| m^-1 |dB> (Eq. bdd_elem),
  *   V = <B|V|B>, D_a = <B|x_a|B> (potential/dipole element formulas),
  *   G_a = <B| m^-1 dV/dx_a |B>, K = <B| m^-1 |B>  (acceleration, Eq. pdm_acceleration),
+ *   W = <B|eta|B> (the absorbing layer's mask, CAP matrix; zero without a layer),
  * with the Dirichlet end functions removed. 1-D results are symmetric band
  * matrices, half bandwidth = degree. For dim = 2, 3 the operators keep the
- * per-axis 1-D factors S_a, T1_a = 1/2 <dB|dB>, D_a (Eq. tensor3d) and the
+ * per-axis 1-D factors S_a, T1_a = 1/2 <dB|dB>, D_a, W_a (Eq. tensor3d) and the
  * quadrature tables; the non-separable terms are applied by the batch from the
  * medium (one element per knot span and equal degrees are required, else
  * TDZ_EUNSUPPORTED; layered and Quesne media are 1-D only).
@@ -110,12 +129,24 @@ typedef struct tdz_ops tdz_ops;
 #define TDZ_MAT_D  4
 #define TDZ_MAT_G  5
 #define TDZ_MAT_K  6
+#define TDZ_MAT_W  7   /* absorbing-layer mask <B|eta|B> (1-D), or the axis factor <B|eta_a|B> (2-D/3-D) */
+#define TDZ_MAT_VEL 8  /* 1-D velocity matrix of Eq. vel_elem as Vel = -(i/2) M: returns the real antisymmetric
+                          M, M_ab = sum_q w_q J_q m^-1 (N_a N_b' - N_a' N_b), lower band M(i, i-d)       */
 int  tdz_assemble(const tdz_basis* const* axes, int dim, const tdz_medium* medium, tdz_ops** out);
 /* n = DoF per axis (shape[0..dim-1]); degree per axis. */
 int  tdz_ops_info(const tdz_ops* ops, int* dim, int64_t* shape, int* degree);
 /* Copy a 1-D band matrix to host out[n*(degree+1)]: out[i*(degree+1)+d] = M(i, i-d). */
 int  tdz_ops_band(const tdz_ops* ops, int which, int axis, double* out);
 void tdz_ops_destroy(tdz_ops* ops);
+
+/* tdz_pdm_acceleration: the position-dependent-mass term a_Q of the dipole acceleration (Eq.
+ * aQ_definition; Eq. pdm_acceleration adds it to the Ehrenfest term that tdz_observe records) for nstates
+ * 1-D states c[nstates][2n] (host, interleaved complex), written to aq[nstates] (host). In 1-D a_Q =
+ * i <[T, v]> with T = 1/2 p m^-1 p and v the velocity operator (Eq. velocity_op); in the Galerkin basis an
+ * operator product A B is A S^-1 B, so a_Q = -2 Im[(T c)^H S^-1 (Vel c)]. It vanishes with the mass
+ * gradient. Host arithmetic in binary64 (one banded factorisation of S per call).
+ * Errors: TDZ_EINVAL (null pointers, nstates < 1, a 2-D/3-D operator), TDZ_ENOCONV. */
+int  tdz_pdm_acceleration(const tdz_ops* ops, const double* c, int64_t nstates, double* aq);
 
 /* Ground state of H0 c = eps S c (Eq. gen_ev) by shifted inverse iteration on
  * the host (1-D). Output: *energy and c[2n] (interleaved complex, real-valued,
@@ -187,6 +218,7 @@ int  tdz_batch_set_refinement(tdz_batch* b, double tol, int max_solves);
 #define TDZ_OPT_OPERATOR         2
 #define TDZ_OPT_APPLY_GROUPS     3
 #define TDZ_OPT_WAIT_TEST        4
+#define TDZ_OPT_CURRENT          5   /* 1-D: 1 = record J = c^H Vel c after every step (tdz_observe_current) */
 #define TDZ_PRECOND_AUTO         0
 #define TDZ_PRECOND_LINES        1
 #define TDZ_PRECOND_FD           2
@@ -229,12 +261,37 @@ int  tdz_observe(const tdz_batch* b, int run, double* out, int* status);
  * layout of tdz_observe for each run, status[nruns] (host, may be NULL). Synchronises the batch
  * stream. */
 int  tdz_observe_all(const tdz_batch* b, double* out, int* status);
+/* tdz_observe_current: the total dipole velocity J(t_{n+1}) = c^H Vel c (Sec. "Currents and coherence
+ * dynamics": the expectation of the velocity operator of Eq. velocity_op, equal to d<x>/dt) of run `run`
+ * for every step of the last tdz_propagate call, out[nsteps] (host or device). Recorded by 1-D batches
+ * after tdz_batch_set_option(b, TDZ_OPT_CURRENT, 1) (binary64 sums, or double-float in mixed precision).
+ * Errors: TDZ_EINVAL (no current recorded), TDZ_ECUDA. Synchronises the batch stream. */
+int  tdz_observe_current(const tdz_batch* b, int run, double* out);
 /* Largest relative residual ||b - A c||/||b|| seen by the refinement of any run
  * (mixed precision; 0 for a 1-D TDZ_FP64 batch) and the total number of solves of
  * all runs, both since the batch was created. Synchronises the batch stream. */
 int  tdz_refine_stats(const tdz_batch* b, double* max_rel_residual, double* mean_solves);
 void tdz_batch_destroy(tdz_batch* b);
 
+
+/* ------------------------------------------------------------------ harmonic spectrum
+ * tdz_spectrum: the windowed spectrum of Sec. "Dipoles", S(w) = |dt sum_k s(t_k) W_k e^{i w t_k}|^2 with
+ * t_k = k dt and the Kaiser window W_k = I0(beta sqrt(1 - (2k/(nt-1) - 1)^2)) / I0(beta), for nsig records
+ * at once, at the nw frequencies w_j = w_lo + j dw; length_form = 1 multiplies by w^4 (the acceleration
+ * spectrum from a dipole record), 0 leaves it (an acceleration record). Direct sums in binary64 on the GPU.
+ *   signal: host or device, record s sample k at signal[s * sig_stride + k * t_stride] (e.g. the d or a
+ *           column of tdz_observe_all's output: t_stride = 2 + 3 dim, sig_stride = nsteps t_stride).
+ *   S     : host or device, [nsig][nw] output.
+ *   cuda_stream: stream of the work (NULL: legacy default stream); the call synchronises it.
+ * Errors: TDZ_EINVAL (sizes, strides, dt <= 0, beta < 0, nsig > 65535), TDZ_ECUDA.
+ * tdz_harmonic_yields: per record, the yield of every odd harmonic q = 1, 3, ..., <= qmax of the
+ * fundamental omega0: the trapezoid integral of S over the grid points in [(q - 1/2) omega0,
+ * (q + 1/2) omega0]. S: host [nsig][nw] on the grid w_lo + j dw; Y: host [nsig][(qmax + 1)/2].
+ * Errors: TDZ_EINVAL. */
+int  tdz_spectrum(const double* signal, int64_t nsig, int64_t nt, int64_t sig_stride, int64_t t_stride, double dt,
+                  double beta, int length_form, double w_lo, double dw, int64_t nw, double* S, void* cuda_stream);
+int  tdz_harmonic_yields(const double* S, int64_t nsig, double w_lo, double dw, int64_t nw, double omega0, int qmax,
+                         double* Y);
 
 /* ------------------------------------------------------------------ allocation-free entry point
  * tdz_cn1d_propagate_noalloc: the binary64 1-D propagation of tdz_propagate for ONE run, for

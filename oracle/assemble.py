@@ -8,6 +8,10 @@ TEST INFRASTRUCTURE (oracle). Paper Sec. "Parallel assembly":
 and, for the Ehrenfest acceleration of Eq. pdm_acceleration (without a_Q):
     G_ab  = sum_q w_q J_q m^-1(r_q) d_alpha V(r_q) N_a N_b
     K_ab  = sum_q w_q J_q m^-1(r_q) N_a N_b
+and the real mask matrix of the complex absorbing potential (CAP matrix, -i W):
+    W_ab  = sum_q w_q J_q eta(r_q) N_a N_b
+and the BenDaniel-Duke velocity matrix of Eq. vel_elem, kept as its real antisymmetric part M_alpha:
+    Vel_alpha = -(i/2) M_alpha,   (M_alpha)_ab = sum_q w_q J_q m^-1(r_q) (N_a d_alpha N_b - d_alpha N_a N_b)
 Global matrices are sums of the element matrices; Dirichlet conditions drop the
 first and last B-spline along every axis (Sec. "Weak form").
 
@@ -101,6 +105,47 @@ def grad_potential(med, X, axis):
     raise ValueError(f"unknown potential kind {k}")
 
 
+# ------------------------------------------------------------------ absorbing layer (CAP)
+# Sec. "Parallel assembly", CAP matrix: W_ab = -i sum_q w_q J_q eta(r_q) N_a N_b with a smooth mask eta >= 0
+# that is non-zero only in a boundary layer; the paper implements a Manolopoulos-type mask and prints no
+# formula. Readings (medium key "cap"): eta is the sum over the axes of a 1-D mask of |x_a| that starts
+# at |x_a| = r0 and ends at |x_a| = R, with s = (|x_a| - r0)/(R - r0) in (0, 1]:
+#   "poly":          eta = eta0 s^k                        (closed-form integrals, the pinned case)
+#   "manolopoulos":  eta = (1/(2m)) (2 pi/(R - r0))^2 f(c s),  f(y) = a y - b y^3 + 4/(c - y)^2 - 4/(c + y)^2,
+#                    a = 1 - 16/c^3,  b = (1 - 17/c^3)/c^2,  c = sqrt(2) K(1/sqrt 2) = 2.62206
+# (Manolopoulos' transmission-free absorbing potential, J. Chem. Phys. 117, 9552 (2002): a layer of width
+# R - r0 = c/(2 k_min) absorbs with little reflection every wave of energy above E_min = k_min^2/(2m); the
+# mask diverges at |x_a| = R, which must be the domain's edge).
+MANOLOPOULOS_C = 2.62206
+
+
+def cap_mask(med, X):
+    """eta(r) at points (zero without a "cap" entry in the medium)."""
+    cap = med.get("cap")
+    out = np.zeros(X[0].shape)
+    if not cap:
+        return out
+    r0, R = float(cap["r0"]), float(cap["R"])
+    for x in X:
+        s = (np.abs(x) - r0) / (R - r0)
+        on = s > 0.0
+        sv = np.where(on, s, 0.0)
+        if cap["kind"] == "poly":
+            f = cap["eta0"] * sv ** cap["k"]
+        elif cap["kind"] == "manolopoulos":
+            if np.any(sv >= 1.0):
+                raise ValueError("Manolopoulos mask evaluated at or beyond its end R")
+            c = MANOLOPOULOS_C
+            a, b = 1.0 - 16.0 / c ** 3, (1.0 - 17.0 / c ** 3) / c ** 2
+            y = c * sv
+            scale = (2.0 * np.pi / (R - r0)) ** 2 / (2.0 * cap.get("m", 1.0))
+            f = scale * (a * y - b * y ** 3 + 4.0 / (c - y) ** 2 - 4.0 / (c + y) ** 2)
+        else:
+            raise ValueError(f"unknown CAP kind {cap['kind']}")
+        out = out + np.where(on, f, 0.0)
+    return out
+
+
 # ------------------------------------------------------------------ 1-D
 def _assemble_pairs(first, Ba, Bb, f, w, n):
     """sum over elements of local matrices loc[e,a,b] = sum_q w f Ba Bb, into an n x n CSR."""
@@ -134,6 +179,8 @@ def assemble_1d(knots, p, nq, med, trim=True):
         "D": [_assemble_pairs(first, B, B, q["x"], w, n)],
         "G": [_assemble_pairs(first, B, B, minv * grad_potential(med, X, 0), w, n)],
         "K": _assemble_pairs(first, B, B, minv, w, n),
+        "W": _assemble_pairs(first, B, B, cap_mask(med, X), w, n),
+        "M": [(_assemble_pairs(first, B, dB, minv, w, n) - _assemble_pairs(first, dB, B, minv, w, n)).tocsr()],
     }
     if trim:
         out = {k: ([_trim(m) for m in v] if isinstance(v, list) else _trim(v)) for k, v in out.items()}
@@ -152,10 +199,11 @@ def assemble_nd(knots_list, p_list, nq_list, med, trim=True):
     qs = [quadrature_1d(np.asarray(k, dtype=np.float64), p, nq) for k, p, nq in zip(knots_list, p_list, nq_list)]
     nfun = [len(k) - p - 1 for k, p in zip(knots_list, p_list)]
     N = int(np.prod(nfun))
-    acc = {"S": [], "T": [], "V": [], "K": []}
+    acc = {"S": [], "T": [], "V": [], "K": [], "W": []}
     for a in range(dim):
         acc[f"D{a}"] = []
         acc[f"G{a}"] = []
+        acc[f"M{a}"] = []
     rows_all, cols_all = [], []
     # loop over tensor elements (one numpy block per element row along the slowest axis)
     E = [len(q["span"]) for q in qs]
@@ -197,7 +245,9 @@ def assemble_nd(knots_list, p_list, nq_list, med, trim=True):
         acc["T"].append(tl)
         acc["V"].append(loc(Vq, Bf, Bf))
         acc["K"].append(loc(minv, Bf, Bf))
+        acc["W"].append(loc(cap_mask(med, X), Bf, Bf))
         for a in range(dim):
+            acc[f"M{a}"].append(loc(minv, Bf, dBf[a]) - loc(minv, dBf[a], Bf))
             acc[f"D{a}"].append(loc(X[a], Bf, Bf))
             acc[f"G{a}"].append(loc(minv * grad_potential(med, X, a), Bf, Bf))
         # global indices of local functions (x fastest)
@@ -219,8 +269,9 @@ def assemble_nd(knots_list, p_list, nq_list, med, trim=True):
         data = np.concatenate([m.reshape(-1) for m in acc[key]])
         return sp.coo_matrix((data, (rows, cols)), shape=(N, N)).tocsr()
 
-    out = {"S": build("S"), "T": build("T"), "V": build("V"), "K": build("K"),
-           "D": [build(f"D{a}") for a in range(dim)], "G": [build(f"G{a}") for a in range(dim)]}
+    out = {"S": build("S"), "T": build("T"), "V": build("V"), "K": build("K"), "W": build("W"),
+           "D": [build(f"D{a}") for a in range(dim)], "G": [build(f"G{a}") for a in range(dim)],
+           "M": [build(f"M{a}") for a in range(dim)]}
     shape = list(nfun)
     if trim:
         keep = np.ones(N, dtype=bool)

@@ -21,10 +21,11 @@ LIB_PATH = os.path.join(_HERE, "libtdz.so")
 
 TDZ_OK, TDZ_EINVAL, TDZ_ENOMEM, TDZ_ECUDA, TDZ_ENOCONV, TDZ_ENONFINITE, TDZ_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 FP64, MIXED = 0, 1
-OPT_PRECOND, OPT_OPERATOR, OPT_APPLY_GROUPS, OPT_WAIT_TEST = 1, 2, 3, 4
+OPT_PRECOND, OPT_OPERATOR, OPT_APPLY_GROUPS, OPT_WAIT_TEST, OPT_CURRENT = 1, 2, 3, 4, 5
 PRECOND_AUTO, PRECOND_LINES, PRECOND_FD = 0, 1, 2
 OPERATOR_AUTO, OPERATOR_QUADRATURE, OPERATOR_STENCIL = 0, 1, 2
-MAT = {"S": 0, "T": 1, "V": 2, "H0": 3, "D": 4, "G": 5, "K": 6}
+MAT = {"S": 0, "T": 1, "V": 2, "H0": 3, "D": 4, "G": 5, "K": 6, "W": 7, "VEL": 8}
+_CAP = {"poly": 1, "manolopoulos": 2}
 _MASS = {"const": 0, "quesne": 1, "layers": 2, "ellipse": 3}
 _POT = {"zero": 0, "softcore": 1, "ho": 2, "quesne": 3, "layers": 4, "ellipse": 5, "h2p_softcore": 6}
 
@@ -43,7 +44,8 @@ _lib = C.CDLL(LIB_PATH)
 class _Medium(C.Structure):
     _fields_ = [("mass_kind", C.c_int), ("pot_kind", C.c_int), ("mass_par", C.c_double * 4),
                 ("pot_par", C.c_double * 4), ("nlayers", C.c_int), ("layer_bounds", C.POINTER(C.c_double)),
-                ("layer_mass", C.POINTER(C.c_double)), ("layer_pot", C.POINTER(C.c_double))]
+                ("layer_mass", C.POINTER(C.c_double)), ("layer_pot", C.POINTER(C.c_double)),
+                ("cap_kind", C.c_int), ("cap_par", C.c_double * 4)]
 
 
 _dp = C.POINTER(C.c_double)
@@ -73,6 +75,11 @@ _sig = {
     "tdz_krylov_stats": (C.c_int, [_vp, _dp]),
     "tdz_batch_tuning": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int), _dp]),
     "tdz_batch_destroy": (None, [_vp]),
+    "tdz_observe_current": (C.c_int, [_vp, C.c_int, _vp]),
+    "tdz_pdm_acceleration": (C.c_int, [_vp, _dp, C.c_int64, _dp]),
+    "tdz_spectrum": (C.c_int, [_vp, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_double, C.c_double, C.c_int,
+                               C.c_double, C.c_double, C.c_int64, _vp, _vp]),
+    "tdz_harmonic_yields": (C.c_int, [_dp, C.c_int64, C.c_double, C.c_double, C.c_int64, C.c_double, C.c_int, _dp]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(_lib, _name)
@@ -153,6 +160,14 @@ def _medium_struct(med: Dict):
             s.pot_par[i] = v[key]
     elif vk == "h2p_softcore":
         s.pot_par[0], s.pot_par[1] = v["R"], v["eps"]
+    cap = med.get("cap")
+    if cap:
+        s.cap_kind = _CAP[cap["kind"]]
+        s.cap_par[0], s.cap_par[1] = cap["r0"], cap["R"]
+        if cap["kind"] == "poly":
+            s.cap_par[2], s.cap_par[3] = cap["eta0"], cap["k"]
+        else:
+            s.cap_par[2] = cap.get("m", 1.0)
     if mk == "layers" or vk == "layers":
         b = np.ascontiguousarray(m.get("bounds", v.get("bounds")), dtype=np.float64)
         s.nlayers = len(b) - 1
@@ -195,6 +210,14 @@ class Ops:
         _check(_lib.tdz_ops_band(self._h, MAT[which], axis, _dptr(out)), "tdz_ops_band")
         return out
 
+    def pdm_acceleration(self, states) -> np.ndarray:
+        """a_Q of Eq. aQ_definition for 1-D states (complex array [n] or [nstates, n]) (tdz_pdm_acceleration)."""
+        c = np.atleast_2d(np.asarray(states, dtype=np.complex128))
+        buf = np.ascontiguousarray(np.stack([c.real, c.imag], axis=2).reshape(-1))
+        out = np.zeros(c.shape[0])
+        _check(_lib.tdz_pdm_acceleration(self._h, _dptr(buf), c.shape[0], _dptr(out)), "tdz_pdm_acceleration")
+        return out
+
     def ground_state(self):
         e = C.c_double()
         c = np.zeros(2 * self.n)
@@ -209,6 +232,29 @@ class Ops:
 
 def assemble_1d(knots, degree: int, medium: Dict, nquad: Optional[int] = None) -> Ops:
     return Ops([Basis(knots, degree, nquad)], medium)
+
+
+def spectrum(signals, dt: float, w_lo: float, dw: float, nw: int, beta: float = 8.0, length_form: bool = False,
+             stream: Optional[int] = None) -> np.ndarray:
+    """Kaiser-windowed spectra S(w_j), w_j = w_lo + j dw, of the records in `signals` ([nsig, nt] or [nt],
+    float64 numpy array, host) on the GPU (tdz_spectrum). length_form multiplies by w^4."""
+    x = np.ascontiguousarray(np.atleast_2d(signals), dtype=np.float64)
+    nsig, nt = x.shape
+    S = np.zeros((nsig, int(nw)))
+    _check(_lib.tdz_spectrum(_vp(_ptr(x)), nsig, nt, nt, 1, float(dt), float(beta), int(bool(length_form)),
+                             float(w_lo), float(dw), int(nw), _vp(_ptr(S)), _vp(stream or 0)), "tdz_spectrum")
+    return S
+
+
+def harmonic_yields(S, w_lo: float, dw: float, omega0: float, qmax: int):
+    """Yields of the odd harmonics q = 1, 3, ... <= qmax (tdz_harmonic_yields). Returns (q, Y[nsig, nq])."""
+    S = np.ascontiguousarray(np.atleast_2d(S), dtype=np.float64)
+    nsig, nw = S.shape
+    nq = (int(qmax) + 1) // 2
+    Y = np.zeros((nsig, nq))
+    _check(_lib.tdz_harmonic_yields(_dptr(S), nsig, float(w_lo), float(dw), nw, float(omega0), int(qmax), _dptr(Y)),
+           "tdz_harmonic_yields")
+    return np.arange(1, 2 * nq, 2), Y
 
 
 class Batch:
@@ -286,6 +332,14 @@ class Batch:
             out = np.zeros((self._last_nsteps, 2 + 3 * self.dim))
         _check(_lib.tdz_observe(self._h, run, _vp(_ptr(out)), C.byref(st)), "tdz_observe")
         return out, st.value
+
+    def observe_current(self, run: int, out=None):
+        """Total dipole velocity J = c^H Vel c after every step of the last propagate() (1-D, after
+        set_option(OPT_CURRENT, 1))."""
+        if out is None:
+            out = np.zeros(self._last_nsteps)
+        _check(_lib.tdz_observe_current(self._h, run, _vp(_ptr(out))), "tdz_observe_current")
+        return out
 
     def refine_stats(self):
         mx, ns = C.c_double(), C.c_double()

@@ -55,6 +55,12 @@ struct GeomDev {
   const void* D;
   const void* G;
   const void* Km;
+  // absorbing-layer mask W (the real band of the CAP matrix), [m][P+1][32] like the others; null without a
+  // layer. binary64 path: double; mixed path: float2 {W.hi, W.lo}.
+  const void* Wc;
+  // lower band of the velocity matrix's antisymmetric part M (Vel = -(i/2) M), same layout and types as Wc;
+  // null unless the batch records the current
+  const void* Mv;
 };
 
 struct RunDev {
@@ -83,6 +89,7 @@ struct StepArgs {
   int* counter;
   const double* field;  // [run][nsteps+1]
   double* obs;          // [run][nsteps][5]
+  double* cur;          // [run][nsteps] total dipole velocity J = c^H Vel c, or null
   long long nsteps;
   long long step0;
   double dt;
@@ -98,16 +105,20 @@ TDZ_DEV int ridx(int i, int k, int ks) { return i * ks + k; }
 // early, so the loop does not pay a full memory round trip per row (no registers needed).
 TDZ_DEV void pf(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
 
-// A(i, i-d) entry for the factorisation, in the solve precision T.
-template <int P, class T, bool MIXED>
+// A(i, i-d) entry for the factorisation, in the solve precision T: S + tau W + i tau (H0 + Ebar D), the
+// absorbing layer's tau W only when CAP.
+template <int P, class T, bool MIXED, bool CAP>
 TDZ_DEV cx<T> a_entry(const GeomDev& g, int idx, T tau, T ebar) {
   if constexpr (MIXED) {
     const float4 v = __ldg(static_cast<const float4*>(g.S) + idx);
-    return cx<T>{v.x, tau * fmaf(ebar, v.z, v.y)};
+    float re = v.x;
+    if constexpr (CAP) re = fmaf(tau, __ldg(static_cast<const float2*>(g.Wc) + idx).x, re);
+    return cx<T>{re, tau * fmaf(ebar, v.z, v.y)};
   } else {
-    const double s = __ldg(static_cast<const double*>(g.S) + idx);
+    double s = __ldg(static_cast<const double*>(g.S) + idx);
     const double h = __ldg(static_cast<const double*>(g.H) + idx);
     const double d = __ldg(static_cast<const double*>(g.D) + idx);
+    if constexpr (CAP) s = fma(tau, __ldg(static_cast<const double*>(g.Wc) + idx), s);
     return cx<T>{s, tau * fma(ebar, d, h)};
   }
 }
@@ -136,7 +147,7 @@ struct Red {  // reduced system of one run in shared memory
 // Eliminates the interior rows 0..mI-1 of the lane's chunk. Stores L (column-wise: Lc[i][d-1]
 // = L(i+d, i)) and D^-1, and returns in registers the Schur complement of the rows mI..mI+P-1
 // (the lane's separator), their coupling to the separator above and their reduced rhs.
-template <int P, class T, bool MIXED>
+template <int P, class T, bool MIXED, bool CAP>
 TDZ_DEV void sweep1(const GeomDev& g, const RunDev& run, const Lane& L, T tau, T ebar, Red<T>& red) {
   const int ks = L.ks;
   cx<T> w[P + 1][P + 1];
@@ -149,10 +160,10 @@ TDZ_DEV void sweep1(const GeomDev& g, const RunDev& run, const Lane& L, T tau, T
 #pragma unroll
   for (int a = 0; a < P; ++a) {
 #pragma unroll
-    for (int b = 0; b <= a; ++b) w[a][b] = a_entry<P, T, MIXED>(g, bidx<P>(a, a - b, k, ks), tau, ebar);
+    for (int b = 0; b <= a; ++b) w[a][b] = a_entry<P, T, MIXED, CAP>(g, bidx<P>(a, a - b, k, ks), tau, ebar);
 #pragma unroll
     for (int j = 0; j < P; ++j)
-      cw[a][j] = (L.up && a <= j) ? a_entry<P, T, MIXED>(g, bidx<P>(a, a + P - j, k, ks), tau, ebar) : czero<T>();
+      cw[a][j] = (L.up && a <= j) ? a_entry<P, T, MIXED, CAP>(g, bidx<P>(a, a + P - j, k, ks), tau, ebar) : czero<T>();
     rw[a] = rhs[ridx(a, k, ks)];
   }
   for (int i = 0; i < L.mI; ++i) {
@@ -164,7 +175,7 @@ TDZ_DEV void sweep1(const GeomDev& g, const RunDev& run, const Lane& L, T tau, T
     }
     if (r < L.m) {
 #pragma unroll
-      for (int b = 0; b <= P; ++b) w[P][b] = a_entry<P, T, MIXED>(g, bidx<P>(r, P - b, k, ks), tau, ebar);
+      for (int b = 0; b <= P; ++b) w[P][b] = a_entry<P, T, MIXED, CAP>(g, bidx<P>(r, P - b, k, ks), tau, ebar);
       rw[P] = rhs[ridx(r, k, ks)];
     } else {
 #pragma unroll
@@ -219,7 +230,7 @@ TDZ_DEV void sweep1(const GeomDev& g, const RunDev& run, const Lane& L, T tau, T
 // Eliminates the interior from its last row upwards with the separator above (rows -P..-1)
 // entering with zero self block and zero rhs: what remains is -C^T A_II^-1 C and -C^T A_II^-1 b
 // for that separator; added into the shared reduced system.
-template <int P, class T, bool MIXED>
+template <int P, class T, bool MIXED, bool CAP>
 TDZ_DEV void sweep2(const GeomDev& g, const RunDev& run, const Lane& L, T tau, T ebar, Red<T>& red) {
   const int ks = L.ks;
   cx<T> w[P + 1][P + 1];  // w[a][b] = A(r-a, r-b), b <= a, r = current pivot row
@@ -230,7 +241,7 @@ TDZ_DEV void sweep2(const GeomDev& g, const RunDev& run, const Lane& L, T tau, T
 #pragma unroll
   for (int a = 0; a < P; ++a) {
 #pragma unroll
-    for (int b = 0; b <= a; ++b) w[a][b] = a_entry<P, T, MIXED>(g, bidx<P>(r0 - b, a - b, k, ks), tau, ebar);
+    for (int b = 0; b <= a; ++b) w[a][b] = a_entry<P, T, MIXED, CAP>(g, bidx<P>(r0 - b, a - b, k, ks), tau, ebar);
     rw[a] = rhs[ridx(r0 - a, k, ks)];
   }
   for (int t = 0; t < L.mI; ++t) {
@@ -244,7 +255,7 @@ TDZ_DEV void sweep2(const GeomDev& g, const RunDev& run, const Lane& L, T tau, T
 #pragma unroll
     for (int b = 0; b <= P; ++b) {
       const int rb = r - b;  // A(q, rb) stored at row rb (rb >= q), diagonal P - b
-      w[P][b] = (rb >= 0) ? a_entry<P, T, MIXED>(g, bidx<P>(rb, P - b, k, ks), tau, ebar) : czero<T>();
+      w[P][b] = (rb >= 0) ? a_entry<P, T, MIXED, CAP>(g, bidx<P>(rb, P - b, k, ks), tau, ebar) : czero<T>();
     }
     rw[P] = (q >= 0) ? rhs[ridx(q, k, ks)] : czero<T>();
     const cx<T> dinv = crecip(w[0][0]);
@@ -394,7 +405,7 @@ TDZ_DEV void accumulate(const RunDev& run, int idx, cx<T> x) {
   }
 }
 
-template <int P, class T, bool MIXED>
+template <int P, class T, bool MIXED, bool CAP>
 TDZ_DEV void substitute(const GeomDev& g, const RunDev& run, const Lane& L, T tau, T ebar, const Red<T>& red) {
   const int ks = L.ks;
   const int k = L.k;
@@ -422,7 +433,7 @@ TDZ_DEV void substitute(const GeomDev& g, const RunDev& run, const Lane& L, T ta
     if (L.up && i < P) {
 #pragma unroll
       for (int j = 0; j < P; ++j)
-        if (j >= i) b = cmsub(b, a_entry<P, T, MIXED>(g, bidx<P>(i, i + P - j, k, ks), tau, ebar), xup[j]);
+        if (j >= i) b = cmsub(b, a_entry<P, T, MIXED, CAP>(g, bidx<P>(i, i + P - j, k, ks), tau, ebar), xup[j]);
     }
 #pragma unroll
     for (int d = 1; d <= P; ++d)
@@ -507,7 +518,7 @@ TDZ_DEV void resolve_fwd(const GeomDev& g, const RunDev& run, const Lane& L, Red
   }
 }
 
-template <int P, class T, bool MIXED>
+template <int P, class T, bool MIXED, bool CAP>
 TDZ_DEV void resolve_bwd(const GeomDev& g, const RunDev& run, const Lane& L, T tau, T ebar, Red<T>& red) {
   const int ks = L.ks;
   const int k = L.k;
@@ -535,7 +546,7 @@ TDZ_DEV void resolve_bwd(const GeomDev& g, const RunDev& run, const Lane& L, T t
     cx<T> acc = czero<T>();
 #pragma unroll
     for (int i = 0; i <= j; ++i)
-      if (i < L.mI) acc = cmadd(acc, a_entry<P, T, MIXED>(g, bidx<P>(i, i + P - j, k, ks), tau, ebar), zw[1 + i]);
+      if (i < L.mI) acc = cmadd(acc, a_entry<P, T, MIXED, CAP>(g, bidx<P>(i, i + P - j, k, ks), tau, ebar), zw[1 + i]);
     red.rb[(k - 1) * P + j] = red.rb[(k - 1) * P + j] - acc;
   }
 }
@@ -556,26 +567,29 @@ TDZ_DEV bool locate(const Lane& L, int j, int& row, int& chunk) {
 }
 
 // ============================================================================ binary64 rhs
-// r = -i tau H_n (2 c), scatter form over rows -P..m+P-1 with pending sums for P+1 rows.
-template <int P>
+// r = -(tau W + i tau H_n) (2 c), scatter form over rows -P..m+P-1 with pending sums for P+1 rows (the
+// absorbing layer's tau W only when CAP).
+template <int P, bool CAP>
 TDZ_DEV void rhs_fp64(const GeomDev& g, const RunDev& run, const Lane& L, double tau, double ebar) {
   const int ks = L.ks;
   const double2* c = static_cast<const double2*>(run.state);
   cx<double>* rhs = static_cast<cx<double>*>(run.rhs);
   cx<double> uw[P + 1];   // uw[d] = u_{j-d}
   cx<double> acc[P + 1];  // acc[d] = pending H u for row j-d
+  cx<double> acw[P + 1];  // acw[d] = pending W u for row j-d (CAP)
 #pragma unroll
   for (int d = 0; d <= P; ++d) {
     uw[d] = czero<double>();
     acc[d] = czero<double>();
+    acw[d] = czero<double>();
   }
   for (int j = -P; j < L.m + P; ++j) {
     int row, chunk;
     const bool ok = locate(L, j, row, chunk);
     cx<double> u = czero<double>();
-    double h[P + 1];
+    double h[P + 1], wv[P + 1];
 #pragma unroll
-    for (int d = 0; d <= P; ++d) h[d] = 0.0;
+    for (int d = 0; d <= P; ++d) h[d] = wv[d] = 0.0;
     if (ok) {
       double2 cc = c[ridx(row, chunk, ks)];
       u = cx<double>{2.0 * cc.x, 2.0 * cc.y};
@@ -584,6 +598,7 @@ TDZ_DEV void rhs_fp64(const GeomDev& g, const RunDev& run, const Lane& L, double
         for (int d = 0; d <= P; ++d) {
           const int idx = bidx<P>(row, d, chunk, ks);
           h[d] = tau * fma(ebar, static_cast<const double*>(g.D)[idx], static_cast<const double*>(g.H)[idx]);
+          if constexpr (CAP) wv[d] = tau * static_cast<const double*>(g.Wc)[idx];
         }
       }
     }
@@ -591,15 +606,21 @@ TDZ_DEV void rhs_fp64(const GeomDev& g, const RunDev& run, const Lane& L, double
 #pragma unroll
     for (int d = P; d >= 1; --d) {
       acc[d] = acc[d - 1];
+      if constexpr (CAP) acw[d] = acw[d - 1];
       uw[d] = uw[d - 1];
     }
     uw[0] = u;
     acc[0] = czero<double>();
+    acw[0] = czero<double>();
     if (j >= 0 && j < L.m) {  // row j's own sum: lower part
 #pragma unroll
       for (int d = 0; d <= P; ++d) {
         acc[0].r += h[d] * uw[d].r;
         acc[0].i += h[d] * uw[d].i;
+        if constexpr (CAP) {
+          acw[0].r += wv[d] * uw[d].r;
+          acw[0].i += wv[d] * uw[d].i;
+        }
       }
     }
     // upper contributions of row j to rows j-d
@@ -608,27 +629,33 @@ TDZ_DEV void rhs_fp64(const GeomDev& g, const RunDev& run, const Lane& L, double
       if (j - d >= 0 && j - d < L.m) {
         acc[d].r += h[d] * u.r;
         acc[d].i += h[d] * u.i;
+        if constexpr (CAP) {
+          acw[d].r += wv[d] * u.r;
+          acw[d].i += wv[d] * u.i;
+        }
       }
     }
     const int jf = j - P;  // row complete
     if (jf >= 0 && jf < L.m) {
-      // r = -i * acc  ->  (acc.i, -acc.r)
-      rhs[ridx(jf, L.k, ks)] = cx<double>{acc[P].i, -acc[P].r};
+      // r = -i acc - acw  ->  (acc.i - acw.r, -acc.r - acw.i)
+      rhs[ridx(jf, L.k, ks)] = cx<double>{acc[P].i - acw[P].r, -acc[P].r - acw[P].i};
     }
   }
 }
 
 // ============================================================================ double-float rhs
-// r = -S w - i (tau H_n) u,  u = 2c + w, all products in double-float (Dot2 accumulation), scatter
+// r = -S w - (tau W + i tau H_n) u,  u = 2c + w (the absorbing layer's tau W only when CAP), all products
+// in double-float (Dot2 accumulation), scatter
 // form with pending sums for P+1 rows. Accumulates ||r||^2 and, when SCALE, ||S c||^2 (FP32) as the
 // reference for the relative residual.
-template <int P, bool SCALE>
+template <int P, bool SCALE, bool CAP>
 TDZ_DEV void rhs_mixed(const GeomDev& g, const RunDev& run, const Lane& L, ff tau, ff ebar, float& rr, float& bb) {
   const int ks = L.ks;
   const float4* __restrict__ c = static_cast<const float4*>(run.state);
   const float4* __restrict__ W = run.W;
   const float4* __restrict__ A4 = static_cast<const float4*>(g.S);
   const float2* __restrict__ HD = static_cast<const float2*>(g.H);
+  const float2* __restrict__ WC = static_cast<const float2*>(g.Wc);
   cx<float>* __restrict__ rhs = static_cast<cx<float>*>(run.rhs);
   cff uw[P + 1], ww[P + 1];
   float2 cw[P + 1];
@@ -664,9 +691,9 @@ TDZ_DEV void rhs_mixed(const GeomDev& g, const RunDev& run, const Lane& L, ff ta
     }
     cff u = cff{{0.f, 0.f}, {0.f, 0.f}}, w = u;
     float2 chi = make_float2(0.f, 0.f);
-    ff s[P + 1], h[P + 1];
+    ff s[P + 1], h[P + 1], wv[P + 1];
 #pragma unroll
-    for (int d = 0; d <= P; ++d) s[d] = h[d] = ff{0.f, 0.f};
+    for (int d = 0; d <= P; ++d) s[d] = h[d] = wv[d] = ff{0.f, 0.f};
     if (ok) {
       const float4 cc = c[ridx(row, chunk, ks)];
       const float4 wq = W[ridx(row, chunk, ks)];
@@ -681,6 +708,10 @@ TDZ_DEV void rhs_mixed(const GeomDev& g, const RunDev& run, const Lane& L, ff ta
           const float2 lo = __ldg(HD + idx);
           s[d] = ff{v.x, v.w};
           h[d] = ff_mul(tau, ff_add(ff{v.y, lo.x}, ff_mul(ebar, ff{v.z, lo.y})));  // tau (H0 + Ebar D)
+          if constexpr (CAP) {
+            const float2 wq2 = __ldg(WC + idx);
+            wv[d] = ff_mul(tau, ff{wq2.x, wq2.y});  // tau W
+          }
         }
       }
     }
@@ -716,6 +747,10 @@ TDZ_DEV void rhs_mixed(const GeomDev& g, const RunDev& run, const Lane& L, ff ta
         acc_mul(pr[2 + (d & 1)], h[d], uw[d].i);
         acc_mul(pi[(d & 1)], ff_neg(s[d]), ww[d].i);
         acc_mul(pi[2 + (d & 1)], ff_neg(h[d]), uw[d].r);
+        if constexpr (CAP) {
+          acc_mul(pr[(d & 1)], ff_neg(wv[d]), uw[d].r);
+          acc_mul(pi[(d & 1)], ff_neg(wv[d]), uw[d].i);
+        }
         if (SCALE) {
           sc[0].r = fmaf(s[d].h, cw[d].x, sc[0].r);
           sc[0].i = fmaf(s[d].h, cw[d].y, sc[0].i);
@@ -735,6 +770,10 @@ TDZ_DEV void rhs_mixed(const GeomDev& g, const RunDev& run, const Lane& L, ff ta
         acc_mul(ar[d], h[d], u.i);
         acc_mul(ai[d], ff_neg(s[d]), w.i);
         acc_mul(ai[d], ff_neg(h[d]), u.r);
+        if constexpr (CAP) {
+          acc_mul(ar[d], ff_neg(wv[d]), u.r);
+          acc_mul(ai[d], ff_neg(wv[d]), u.i);
+        }
         if (SCALE) {
           sc[d].r = fmaf(s[d].h, chi.x, sc[d].r);
           sc[d].i = fmaf(s[d].h, chi.y, sc[d].i);
@@ -754,13 +793,13 @@ TDZ_DEV void rhs_mixed(const GeomDev& g, const RunDev& run, const Lane& L, ff ta
 // ============================================================================ observables
 // c^H M c = sum_j M_jj |c_j|^2 + 2 sum_{d>=1} M(j, j-d) Re(conj(c_j) c_{j-d}) for M = S, D, G, K.
 template <int P>
-TDZ_DEV void observe_fp64(const GeomDev& g, const RunDev& run, const Lane& L, double out[4]) {
+TDZ_DEV void observe_fp64(const GeomDev& g, const RunDev& run, const Lane& L, bool cur, double out[5]) {
   const int ks = L.ks;
   const double2* c = static_cast<const double2*>(run.state);
   double2 cwin[P + 1];
 #pragma unroll
   for (int d = 0; d <= P; ++d) cwin[d] = make_double2(0.0, 0.0);
-  double s = 0, dd = 0, gg = 0, kk = 0;
+  double s = 0, dd = 0, gg = 0, kk = 0, jv = 0;
   for (int j = -P; j < L.m; ++j) {
     int row, chunk;
     const bool ok = locate(L, j, row, chunk);
@@ -778,12 +817,18 @@ TDZ_DEV void observe_fp64(const GeomDev& g, const RunDev& run, const Lane& L, do
         gg = fma(static_cast<const double*>(g.G)[idx], u, gg);
         kk = fma(static_cast<const double*>(g.Km)[idx], u, kk);
       }
+      if (cur) {  // J = sum_{d >= 1} M(j, j-d) Im(conj(c_j) c_{j-d})
+#pragma unroll
+        for (int d = 1; d <= P; ++d)
+          jv = fma(static_cast<const double*>(g.Mv)[bidx<P>(row, d, chunk, ks)], cj.x * cwin[d].y - cj.y * cwin[d].x, jv);
+      }
     }
   }
   out[0] = s;
   out[1] = dd;
   out[2] = gg;
   out[3] = kk;
+  out[4] = jv;
 }
 
 // Mixed path: c <- c + w (double-float), difference history d2 <- d1, d1 <- w, next predictor
@@ -791,7 +836,8 @@ TDZ_DEV void observe_fp64(const GeomDev& g, const RunDev& run, const Lane& L, do
 // the new state, in one pass. The new values of the P rows above the chunk (the previous lane's
 // separator) are formed from that lane's c and w before anyone overwrites them.
 template <int P>
-TDZ_DEV void update_observe_mixed(const GeomDev& g, const RunDev& run, const Lane& L, int hist_new, double out[4]) {
+TDZ_DEV void update_observe_mixed(const GeomDev& g, const RunDev& run, const Lane& L, int hist_new, bool cur,
+                                  double out[5]) {
   const int ks = L.ks;
   float4* __restrict__ c = static_cast<float4*>(run.state);
   float4* __restrict__ W = run.W;
@@ -810,11 +856,12 @@ TDZ_DEV void update_observe_mixed(const GeomDev& g, const RunDev& run, const Lan
     }
   }
   __syncthreads();  // the previous chunk may belong to the other warp of this run: every thread calls this
-  ffacc s, dd, gg, kk;
+  ffacc s, dd, gg, kk, jv;
   acc_zero(s);
   acc_zero(dd);
   acc_zero(gg);
   acc_zero(kk);
+  acc_zero(jv);
   if (L.active) {
     for (int j = 0; j < L.m; ++j) {
       const int idx = ridx(j, L.k, ks);
@@ -872,13 +919,26 @@ TDZ_DEV void update_observe_mixed(const GeomDev& g, const RunDev& run, const Lan
       acc_add(dd, ff_add(acc_get(pd[0]), acc_get(pd[1])));
       acc_add(gg, ff_add(acc_get(pg[0]), acc_get(pg[1])));
       acc_add(kk, ff_add(acc_get(pk[0]), acc_get(pk[1])));
+      if (cur) {  // J = sum_{d >= 1} M(j, j-d) Im(conj(c_j) c_{j-d}), in double-float
+        const float2* __restrict__ MV = static_cast<const float2*>(g.Mv);
+#pragma unroll
+        for (int d = 1; d <= P; ++d) {
+          ffacc ui;
+          acc_zero(ui);
+          acc_mul(ui, cj.r, cwin[d].i);
+          acc_mul(ui, ff_neg(cj.i), cwin[d].r);
+          const float2 mq = __ldg(MV + bidx<P>(j, d, L.k, ks));
+          acc_mul(jv, ff{mq.x, mq.y}, acc_get(ui));
+        }
+      }
     }
   }
-  const ff fs = acc_get(s), fd = acc_get(dd), fg = acc_get(gg), fk = acc_get(kk);
+  const ff fs = acc_get(s), fd = acc_get(dd), fg = acc_get(gg), fk = acc_get(kk), fj = acc_get(jv);
   out[0] = (double)fs.h + (double)fs.l;
   out[1] = (double)fd.h + (double)fd.l;
   out[2] = (double)fg.h + (double)fg.l;
   out[3] = (double)fk.h + (double)fk.l;
+  out[4] = (double)fj.h + (double)fj.l;
 }
 
 TDZ_DEV double warp_sum(double v) {
@@ -890,7 +950,7 @@ TDZ_DEV double warp_sum(double v) {
 // Sums over all lanes of a run (nw adjacent warps), identical in every lane of the run. Called by
 // every thread of the block (it contains block barriers); idle warps pass zeros.
 template <int NV>
-TDZ_DEV void run_sum(double (&v)[NV], double (*sh)[4], int wib, int sub, int nw) {
+TDZ_DEV void run_sum(double (&v)[NV], double (*sh)[5], int wib, int sub, int nw) {
 #pragma unroll
   for (int q = 0; q < NV; ++q) v[q] = warp_sum(v[q]);
   if ((threadIdx.x & 31) == 0)
@@ -915,12 +975,12 @@ TDZ_DEV void run_sum(double (&v)[NV], double (*sh)[4], int wib, int sub, int nw)
 // the warps of a run see each other's chunk boundaries and shared reduced system. The adaptive
 // refinement decides collectively how many extra solves the block makes; warps whose run is
 // already converged skip the work of those rounds.
-template <int P, bool MIXED>
+template <int P, bool MIXED, bool CAP>
 __global__ void __launch_bounds__(256) cn1d_kernel(StepArgs A) {
   using T = typename std::conditional<MIXED, float, double>::type;
   extern __shared__ unsigned char smem_raw[];
   __shared__ int s_base;
-  __shared__ double s_sum[8][4];
+  __shared__ double s_sum[8][5];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int wpb = blockDim.x >> 5;
@@ -975,48 +1035,49 @@ __global__ void __launch_bounds__(256) cn1d_kernel(StepArgs A) {
       const int nsep = work ? L.K - 1 : 0;
       const double ebar_d = 0.5 * (E[s] + E[s + 1]);
       const double tau_d = 0.5 * A.dt;
-      double o[4] = {0, 0, 0, 0};
+      double o[5] = {0, 0, 0, 0, 0};
+      const bool cur = A.cur != nullptr;
       if constexpr (!MIXED) {
-        if (W.active) rhs_fp64<P>(g, run, W, tau_d, ebar_d);
+        if (W.active) rhs_fp64<P, CAP>(g, run, W, tau_d, ebar_d);
         __syncthreads();
-        if (W.active) sweep1<P, double, false>(g, run, W, tau_d, ebar_d, red);
+        if (W.active) sweep1<P, double, false, CAP>(g, run, W, tau_d, ebar_d, red);
         __syncthreads();
-        if (W.up) sweep2<P, double, false>(g, run, W, tau_d, ebar_d, red);
+        if (W.up) sweep2<P, double, false, CAP>(g, run, W, tau_d, ebar_d, red);
         __syncthreads();
         if (lead && nsep > 0) {
           red_factor<P, double>(red, nsep, lane);
           red_solve<P, double>(red, nsep, lane);
         }
         __syncthreads();
-        if (W.active) substitute<P, double, false>(g, run, W, tau_d, ebar_d, red);  // c += delta
+        if (W.active) substitute<P, double, false, CAP>(g, run, W, tau_d, ebar_d, red);  // c += delta
         __syncthreads();
         nsolve += work;
-        if (W.active) observe_fp64<P>(g, run, W, o);
+        if (W.active) observe_fp64<P>(g, run, W, cur, o);
       } else {
         const float tau_f = (float)tau_d, ebar_f = (float)ebar_d;
         const ff tau_ff = ff{tau_f, (float)(tau_d - (double)tau_f)};
         const ff ebar_ff = ff{ebar_f, (float)(ebar_d - (double)ebar_f)};
         // residual of the predictor y0 = c + w, then one factorising FP32 solve
         float rr = 0.f, bb = 0.f;
-        if (W.active) rhs_mixed<P, true>(g, run, W, tau_ff, ebar_ff, rr, bb);
+        if (W.active) rhs_mixed<P, true, CAP>(g, run, W, tau_ff, ebar_ff, rr, bb);
         double sums[2] = {(double)rr, (double)bb};
         run_sum(sums, s_sum, wib, sub, nw);
         const double bbs = fmax(sums[1], 1e-300);
         const double rel0 = sqrt(sums[0] / bbs);
-        if (W.active) sweep1<P, float, true>(g, run, W, tau_f, ebar_f, red);
+        if (W.active) sweep1<P, float, true, CAP>(g, run, W, tau_f, ebar_f, red);
         __syncthreads();
-        if (W.up) sweep2<P, float, true>(g, run, W, tau_f, ebar_f, red);
+        if (W.up) sweep2<P, float, true, CAP>(g, run, W, tau_f, ebar_f, red);
         __syncthreads();
         if (lead && nsep > 0) {
           red_factor<P, float>(red, nsep, lane);
           red_solve<P, float>(red, nsep, lane);
         }
         __syncthreads();
-        if (W.active) substitute<P, float, true>(g, run, W, tau_f, ebar_f, red);  // w += delta
+        if (W.active) substitute<P, float, true, CAP>(g, run, W, tau_f, ebar_f, red);  // w += delta
         __syncthreads();
         nsolve += work;
         // residual after the solve; refine with the stored factors while above tolerance
-        if (W.active) rhs_mixed<P, false>(g, run, W, tau_ff, ebar_ff, rr, bb);
+        if (W.active) rhs_mixed<P, false, CAP>(g, run, W, tau_ff, ebar_ff, rr, bb);
         double r1[1] = {W.active ? (double)rr : 0.0};
         run_sum(r1, s_sum, wib, sub, nw);
         double rel = sqrt(r1[0] / bbs);
@@ -1027,11 +1088,11 @@ __global__ void __launch_bounds__(256) cn1d_kernel(StepArgs A) {
         while (__syncthreads_or(need)) {
           if (need && W.active) resolve_fwd<P, float, true>(g, run, W, red);
           __syncthreads();
-          if (need && W.up) resolve_bwd<P, float, true>(g, run, W, tau_f, ebar_f, red);
+          if (need && W.up) resolve_bwd<P, float, true, CAP>(g, run, W, tau_f, ebar_f, red);
           __syncthreads();
           if (need && lead && nsep > 0) red_solve<P, float>(red, nsep, lane);
           __syncthreads();
-          if (need && W.active) substitute<P, float, true>(g, run, W, tau_f, ebar_f, red);
+          if (need && W.active) substitute<P, float, true, CAP>(g, run, W, tau_f, ebar_f, red);
           __syncthreads();
           if (need) {
             nsolve++;
@@ -1043,7 +1104,7 @@ __global__ void __launch_bounds__(256) cn1d_kernel(StepArgs A) {
             }
           }
           const bool check = need && !ok;
-          if (check && W.active) rhs_mixed<P, false>(g, run, W, tau_ff, ebar_ff, rr, bb);
+          if (check && W.active) rhs_mixed<P, false, CAP>(g, run, W, tau_ff, ebar_ff, rr, bb);
           double rc[1] = {(check && W.active) ? (double)rr : 0.0};
           run_sum(rc, s_sum, wib, sub, nw);
           if (check) {
@@ -1058,7 +1119,7 @@ __global__ void __launch_bounds__(256) cn1d_kernel(StepArgs A) {
           hist = hist + 1;
         }
         __syncthreads();
-        update_observe_mixed<P>(g, run, W, hist, o);
+        update_observe_mixed<P>(g, run, W, hist, cur, o);
       }
       run_sum(o, s_sum, wib, sub, nw);
       if (work) {
@@ -1070,6 +1131,7 @@ __global__ void __launch_bounds__(256) cn1d_kernel(StepArgs A) {
           row[2] = o[1];
           row[3] = -o[2] - Et * o[3];
           row[4] = o[0];
+          if (cur) A.cur[(size_t)rid * A.nsteps + s] = o[4];
         }
         if (!isfinite(o[0]) || !isfinite(o[1])) status = TDZ_ENONFINITE;
       }
@@ -1158,7 +1220,7 @@ size_t smem_per_warp(int P, bool mixed) {
 // thread that launches it. It is only ever raised, straight to the largest size any launch of this
 // instantiation can use on the device (the most warp slots a block gets, times the per-warp reduced
 // system), so a launch made on one thread never finds the limit lowered by a call on another.
-template <int P, bool M>
+template <int P, bool M, bool CAP>
 cudaError_t ensure_smem(size_t need) {
   static std::mutex mu;
   static size_t set_to[64] = {};
@@ -1174,7 +1236,7 @@ cudaError_t ensure_smem(size_t need) {
   const size_t spw = smem_per_warp(P, M);
   const size_t cap = std::min<size_t>(8, std::max<size_t>(1, (size_t)maxsm / spw)) * spw;
   const size_t v = std::max(need, cap);
-  e = cudaFuncSetAttribute(cn1d_kernel<P, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v);
+  e = cudaFuncSetAttribute(cn1d_kernel<P, M, CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v);
   if (e == cudaSuccess) set_to[dev] = v;
   return e;
 }
@@ -1331,6 +1393,13 @@ struct tdz_batch {
   size_t dev_bytes = 0;
   int warps_per_block = 4;
   int blocks = 0;
+  bool cap = false;  // some geometry has an absorbing layer: every run takes the kernel with the W band
+  // total dipole velocity per step (TDZ_OPT_CURRENT): velocity bands uploaded on first use, per-step buffer
+  bool current = false;
+  std::vector<GeomDev> h_geoms;
+  std::vector<const Ops*> ops_of;
+  double* d_cur = nullptr;
+  size_t cur_len = 0;
   double tol = 1e-11;
   int max_it = 6;
 
@@ -1348,33 +1417,39 @@ struct tdz_batch {
     if (d_obs) cudaFree(d_obs);
     if (d_field) cudaFree(d_field);
     if (d_stage) cudaFree(d_stage);
+    if (d_cur) cudaFree(d_cur);
   }
 };
 
 namespace {
 
-template <int P, bool M>
+template <int P, bool M, bool CAP>
 cudaError_t launch_p(tdz_batch* b, const StepArgs& a) {
   const size_t sm = smem_per_warp(P, M) * b->warps_per_block;
-  cudaError_t e = ensure_smem<P, M>(sm);
+  cudaError_t e = ensure_smem<P, M, CAP>(sm);
   if (e != cudaSuccess) return e;
-  cn1d_kernel<P, M><<<b->blocks, 32 * b->warps_per_block, sm, b->stream>>>(a);
+  cn1d_kernel<P, M, CAP><<<b->blocks, 32 * b->warps_per_block, sm, b->stream>>>(a);
   return cudaGetLastError();
+}
+
+template <bool M, bool CAP>
+cudaError_t launch_c(tdz_batch* b, const StepArgs& a) {
+  switch (b->P) {
+    case 1: return launch_p<1, M, CAP>(b, a);
+    case 2: return launch_p<2, M, CAP>(b, a);
+    case 3: return launch_p<3, M, CAP>(b, a);
+    case 4: return launch_p<4, M, CAP>(b, a);
+    case 5: return launch_p<5, M, CAP>(b, a);
+    case 6: return launch_p<6, M, CAP>(b, a);
+    case 7: return launch_p<7, M, CAP>(b, a);
+    case 8: return launch_p<8, M, CAP>(b, a);
+  }
+  return cudaErrorInvalidValue;
 }
 
 template <bool M>
 cudaError_t launch(tdz_batch* b, const StepArgs& a) {
-  switch (b->P) {
-    case 1: return launch_p<1, M>(b, a);
-    case 2: return launch_p<2, M>(b, a);
-    case 3: return launch_p<3, M>(b, a);
-    case 4: return launch_p<4, M>(b, a);
-    case 5: return launch_p<5, M>(b, a);
-    case 6: return launch_p<6, M>(b, a);
-    case 7: return launch_p<7, M>(b, a);
-    case 8: return launch_p<8, M>(b, a);
-  }
-  return cudaErrorInvalidValue;
+  return b->cap ? launch_c<M, true>(b, a) : launch_c<M, false>(b, a);
 }
 
 }  // namespace
@@ -1427,6 +1502,7 @@ int tdz_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* 
   if (!b) return TDZ_ENOMEM;
   b->prec = precision;
   b->P = P;
+  for (int g = 0; g < nops; ++g) b->cap = b->cap || ops[g]->o.has_cap();
   b->nruns = nruns;
   b->stream = static_cast<cudaStream_t>(cuda_stream);
   const bool mixed = precision == TDZ_MIXED;
@@ -1454,7 +1530,7 @@ int tdz_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* 
     const int K = ch.K, m = ch.m, LS = ch.ks;
     b->geo[gi] = {n, m, K, LS};
     const size_t nb = (size_t)m * P1 * LS;
-    const Band* src[5] = {&o.S, &o.H0, &o.D, &o.G, &o.K};
+    const Band* src[6] = {&o.S, &o.H0, &o.D, &o.G, &o.K, &o.W};
     // value of matrix q at interleaved position (i, d, k); padding rows are identity in S
     auto val = [&](int q, int i, int d, int k) -> double {
       const int64_t gr = (int64_t)k * m + i;
@@ -1464,7 +1540,8 @@ int tdz_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* 
     };
     auto hi = [](double v) { return (float)v; };
     auto lo = [](double v) { return (float)(v - (double)(float)v); };
-    void* dst[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    void* dst[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    auto val_w = [&](int i, int d, int k) -> double { return o.has_cap() ? val(5, i, d, k) : 0.0; };
     auto upload = [&](const void* h, size_t bytes) -> void* {
       void* p = b->alloc(bytes);
       if (!p) return nullptr;
@@ -1494,6 +1571,18 @@ int tdz_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* 
       dst[0] = upload(a4.data(), nb * 16);
       dst[1] = upload(hd.data(), nb * 8);
       dst[3] = upload(gk.data(), nb * 16);
+      if (b->cap) {
+        std::vector<float> wc(nb * 2);
+        for (int k = 0; k < LS; ++k)
+          for (int i = 0; i < m; ++i)
+            for (int d = 0; d <= P; ++d) {
+              const size_t idx = ((size_t)i * P1 + d) * LS + k;
+              wc[2 * idx + 0] = hi(val_w(i, d, k));
+              wc[2 * idx + 1] = lo(val_w(i, d, k));
+            }
+        dst[5] = upload(wc.data(), nb * 8);
+        if (!dst[5]) dst[0] = nullptr;
+      }
       if (!dst[0] || !dst[1] || !dst[3]) {
         delete b;
         set_error("tdz_batch_create: band upload failed");
@@ -1501,10 +1590,11 @@ int tdz_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* 
       }
     } else {
       std::vector<double> hd(nb);
-      for (int q = 0; q < 5; ++q) {
+      for (int q = 0; q < (b->cap ? 6 : 5); ++q) {
         for (int k = 0; k < LS; ++k)
           for (int i = 0; i < m; ++i)
-            for (int d = 0; d <= P; ++d) hd[((size_t)i * P1 + d) * LS + k] = val(q, i, d, k);
+            for (int d = 0; d <= P; ++d)
+              hd[((size_t)i * P1 + d) * LS + k] = q == 5 ? val_w(i, d, k) : val(q, i, d, k);
         dst[q] = upload(hd.data(), nb * 8);
         if (!dst[q]) {
           delete b;
@@ -1513,7 +1603,7 @@ int tdz_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* 
         }
       }
     }
-    hg[gi] = GeomDev{n, m, K, LS, dst[0], dst[1], dst[2], dst[3], dst[4]};
+    hg[gi] = GeomDev{n, m, K, LS, dst[0], dst[1], dst[2], dst[3], dst[4], b->cap ? dst[5] : nullptr, nullptr};
   }
   // ---------------------------------------------------------------- runs
   b->h_runs.resize(nruns);
@@ -1557,6 +1647,8 @@ int tdz_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* 
     return TDZ_ENOMEM;
   }
   cudaMemcpyAsync(b->d_geoms, hg.data(), sizeof(GeomDev) * nops, cudaMemcpyHostToDevice, b->stream);
+  b->h_geoms = hg;
+  for (int g = 0; g < nops; ++g) b->ops_of.push_back(&ops[g]->o);
   cudaMemcpyAsync(b->d_runs, b->h_runs.data(), sizeof(RunDev) * nruns, cudaMemcpyHostToDevice, b->stream);
   cudaMemcpyAsync(b->d_order, slots.data(), sizeof(int) * slots.size(), cudaMemcpyHostToDevice, b->stream);
   cudaMemcpyAsync(b->d_off, b->h_off.data(), sizeof(long long) * (nruns + 1), cudaMemcpyHostToDevice, b->stream);
@@ -1730,6 +1822,13 @@ int tdz_propagate(tdz_batch* b, const double* field, double dt, int64_t step0, i
     if (e != cudaSuccess) return cuda_fail(e, "tdz_propagate: observable buffer");
     b->obs_steps = obs_need;
   }
+  if (b->current && b->cur_len < (size_t)b->nruns * nsteps) {
+    if (b->d_cur) cudaFreeAsync(b->d_cur, b->stream);
+    b->d_cur = nullptr;
+    e = cudaMallocAsync(reinterpret_cast<void**>(&b->d_cur), sizeof(double) * b->nruns * nsteps, b->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "tdz_propagate: current buffer");
+    b->cur_len = (size_t)b->nruns * nsteps;
+  }
   e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->stream);
   if (e != cudaSuccess) return cuda_fail(e, "tdz_propagate");
   StepArgs a;
@@ -1740,6 +1839,7 @@ int tdz_propagate(tdz_batch* b, const double* field, double dt, int64_t step0, i
   a.counter = b->d_counter;
   a.field = dfield;
   a.obs = b->d_obs;
+  a.cur = b->current ? b->d_cur : nullptr;
   a.nsteps = nsteps;
   a.step0 = step0;
   a.dt = dt;
@@ -1862,12 +1962,74 @@ int tdz_refine_stats(const tdz_batch* b, double* max_rel_residual, double* mean_
 
 int tdz_batch_set_option(tdz_batch* b, int option, int value) {
   if (!b) return TDZ_EINVAL;
+  if (option == TDZ_OPT_CURRENT) {
+    if (value != 0 && value != 1) return TDZ_EINVAL;
+    if (b->nd) {
+      set_error("tdz_batch_set_option: the per-step current is recorded by 1-D batches only");
+      return TDZ_EUNSUPPORTED;
+    }
+    if (value == 1 && !b->h_geoms.empty() && !b->h_geoms[0].Mv) {
+      // upload the velocity bands in the batch's interleaved layout (binary64, or float2 {hi, lo})
+      for (size_t gi = 0; gi < b->h_geoms.size(); ++gi) {
+        const auto& G = b->geo[gi];
+        const Band& M = b->ops_of[gi]->M;
+        const int P1 = b->P + 1;
+        const size_t nb = (size_t)G.m * P1 * G.ks;
+        std::vector<double> hv(nb, 0.0);
+        for (int k = 0; k < G.K; ++k)
+          for (int i = 0; i < G.m; ++i) {
+            const int64_t gr = (int64_t)k * G.m + i;
+            if (gr >= G.n) continue;
+            for (int d = 1; d <= b->P && gr - d >= 0; ++d) hv[((size_t)i * P1 + d) * G.ks + k] = M.at(gr, d);
+          }
+        void* dst = nullptr;
+        if (b->prec == TDZ_MIXED) {
+          std::vector<float> hf(2 * nb);
+          for (size_t q = 0; q < nb; ++q) {
+            hf[2 * q] = (float)hv[q];
+            hf[2 * q + 1] = (float)(hv[q] - (double)(float)hv[q]);
+          }
+          dst = b->alloc(nb * 8);
+          if (dst && cudaMemcpyAsync(dst, hf.data(), nb * 8, cudaMemcpyHostToDevice, b->stream) != cudaSuccess) dst = nullptr;
+          if (dst && cudaStreamSynchronize(b->stream) != cudaSuccess) dst = nullptr;
+        } else {
+          dst = b->alloc(nb * 8);
+          if (dst && cudaMemcpyAsync(dst, hv.data(), nb * 8, cudaMemcpyHostToDevice, b->stream) != cudaSuccess) dst = nullptr;
+          if (dst && cudaStreamSynchronize(b->stream) != cudaSuccess) dst = nullptr;
+        }
+        if (!dst) {
+          set_error("tdz_batch_set_option: velocity band upload failed");
+          return TDZ_ENOMEM;
+        }
+        b->h_geoms[gi].Mv = dst;
+      }
+      cudaError_t e = cudaMemcpyAsync(b->d_geoms, b->h_geoms.data(), sizeof(GeomDev) * b->h_geoms.size(),
+                                      cudaMemcpyHostToDevice, b->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "tdz_batch_set_option");
+    }
+    b->current = value == 1;
+    return TDZ_OK;
+  }
   if (b->nd) return tdz::nd_set_option(b->nd, option, value);
   if (option == TDZ_OPT_PRECOND && value >= TDZ_PRECOND_AUTO && value <= TDZ_PRECOND_FD) return TDZ_OK;
   if (option == TDZ_OPT_OPERATOR && value >= TDZ_OPERATOR_AUTO && value <= TDZ_OPERATOR_STENCIL) return TDZ_OK;
   if (option == TDZ_OPT_APPLY_GROUPS && (value == 0 || value == 8 || value == 16)) return TDZ_OK;
   if (option == TDZ_OPT_WAIT_TEST && (value == 0 || value == 1)) return TDZ_OK;
   return TDZ_EINVAL;
+}
+
+int tdz_observe_current(const tdz_batch* b, int run, double* out) {
+  if (!b || !out || run < 0 || run >= b->nruns) return TDZ_EINVAL;
+  if (b->nd || !b->current || !b->d_cur || b->last_nsteps < 1) {
+    set_error("tdz_observe_current: no current recorded (1-D batch with TDZ_OPT_CURRENT set before tdz_propagate)");
+    return TDZ_EINVAL;
+  }
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(out, b->d_cur + (size_t)run * b->last_nsteps, sizeof(double) * b->last_nsteps, cudaMemcpyDefault);
+  if (e != cudaSuccess) return cuda_fail(e, "tdz_observe_current");
+  return TDZ_OK;
 }
 
 int tdz_batch_tuning(const tdz_batch* b, int geometry, int* groups, double* ms) {
@@ -1943,7 +2105,7 @@ __global__ void noalloc_pack(double* scr, NoAllocLayout L, const double* bands, 
     int* order = reinterpret_cast<int*>(R + 1);
     const size_t nb = rows * P1;
     *G = GeomDev{L.n, L.m, L.K, LANES, scr + L.band, scr + L.band + nb, scr + L.band + 2 * nb, scr + L.band + 3 * nb,
-                 scr + L.band + 4 * nb};
+                 scr + L.band + 4 * nb, nullptr, nullptr};
     RunDev r{};
     r.geom = 0;
     r.status = TDZ_OK;
@@ -1974,9 +2136,9 @@ static std::mutex g_noalloc_mu;
 template <int P>
 cudaError_t noalloc_launch(cudaStream_t st, const StepArgs& a) {
   const size_t sm = smem_per_warp(P, false);
-  cudaError_t e = ensure_smem<P, false>(sm);
+  cudaError_t e = ensure_smem<P, false, false>(sm);
   if (e != cudaSuccess) return e;
-  cn1d_kernel<P, false><<<1, 32, sm, st>>>(a);
+  cn1d_kernel<P, false, false><<<1, 32, sm, st>>>(a);
   return cudaGetLastError();
 }
 }  // namespace tdz
@@ -2057,6 +2219,7 @@ extern "C" int tdz_cn1d_propagate_noalloc(const double* bands, int64_t n, int de
   a.counter = order + 1;
   a.field = field;
   a.obs = obs;
+  a.cur = nullptr;
   a.nsteps = nsteps;
   a.step0 = step0;
   a.dt = dt;

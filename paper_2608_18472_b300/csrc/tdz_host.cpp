@@ -165,24 +165,40 @@ double Medium::dpotential(const double* r, int dim, int axis) const {
   }
 }
 
+// 1-D absorbing mask of one coordinate (the layer's definition is in tdz.h, TDZ_CAP_*).
+double Medium::cap_axis(double x) const {
+  if (cap_kind == TDZ_CAP_NONE) return 0.0;
+  const double r0 = cap_par[0], R = cap_par[1];
+  const double s = (std::fabs(x) - r0) / (R - r0);
+  if (!(s > 0.0)) return 0.0;
+  if (cap_kind == TDZ_CAP_POLY) return cap_par[2] * std::pow(s, cap_par[3]);
+  // Manolopoulos: (1/(2m)) (2 pi / width)^2 f(c s)
+  const double c = 2.62206, c3 = c * c * c;
+  const double ca = 1.0 - 16.0 / c3, cb = (1.0 - 17.0 / c3) / (c * c);
+  const double y = c * s;
+  const double k = 2.0 * M_PI / (R - r0);
+  return 0.5 / cap_par[2] * k * k * (ca * y - cb * y * y * y + 4.0 / ((c - y) * (c - y)) - 4.0 / ((c + y) * (c + y)));
+}
+
 // ----------------------------------------------------------------------------- 1-D assembly
 // One pass over the elements fills all seven band matrices (the fused multi-matrix pass of
 // Sec. "Parallel assembly"); Dirichlet end functions are skipped when scattering.
 static void assemble_1d(const Basis& B, const Medium& med, Ops& o) {
   const int p = B.p, nq = B.nq, P1 = p + 1;
   const int64_t n = B.nfun - 2;
-  Band* mats[] = {&o.S, &o.T, &o.V, &o.H0, &o.D, &o.G, &o.K};
+  Band* mats[] = {&o.S, &o.T, &o.V, &o.H0, &o.D, &o.G, &o.K, &o.W, &o.M};
   for (Band* m : mats) {
     m->n = n;
     m->p = p;
     m->a.assign((size_t)n * P1, 0.0);
   }
-  std::vector<double> loc(7 * P1 * P1);
+  std::vector<double> loc(9 * P1 * P1);
   for (int64_t e = 0; e < B.nelem(); ++e) {
     std::fill(loc.begin(), loc.end(), 0.0);
     for (int q = 0; q < nq; ++q) {
       double x = B.xq[e * nq + q], w = B.wq[e * nq + q];
       double mi = med.inv_mass(&x, 1), v = med.potential(&x, 1), dv = med.dpotential(&x, 1, 0);
+      const double eta = med.cap_axis(x);
       const double* N = &B.val[(e * nq + q) * P1];
       const double* dN = &B.der[(e * nq + q) * P1];
       for (int a = 0; a < P1; ++a) {
@@ -195,6 +211,8 @@ static void assemble_1d(const Basis& B, const Medium& med, Ops& o) {
           L[4 * P1 * P1] += nn * x;                       // D
           L[5 * P1 * P1] += nn * mi * dv;                 // G
           L[6 * P1 * P1] += nn * mi;                      // K
+          L[7 * P1 * P1] += nn * eta;                     // W (absorbing mask)
+          L[8 * P1 * P1] += w * mi * (N[a] * dN[c] - dN[a] * N[c]);  // M (velocity, Eq. vel_elem)
         }
       }
     }
@@ -205,7 +223,10 @@ static void assemble_1d(const Basis& B, const Medium& med, Ops& o) {
         if (fj < 1 || fi > B.nfun - 2) continue;
         int64_t i = fi - 1;
         int d = (int)(fi - fj);
-        for (int k : {0, 1, 2, 4, 5, 6}) mats[k]->a[(size_t)i * P1 + d] += loc[k * P1 * P1 + a * P1 + c];
+        for (int k : {0, 1, 2, 4, 5, 6, 7}) mats[k]->a[(size_t)i * P1 + d] += loc[k * P1 * P1 + a * P1 + c];
+        // M is antisymmetric: the local (a, c) entry is M(fi, fj) only when the two local functions map in
+        // that order (fi >= fj holds since a >= c and first is common)
+        mats[8]->a[(size_t)i * P1 + d] += loc[8 * P1 * P1 + a * P1 + c];
       }
     }
   }
@@ -216,10 +237,10 @@ static void assemble_1d(const Basis& B, const Medium& med, Ops& o) {
 // Per-axis 1-D bands of the tensor-product basis (Eq. tensor3d): S_a, the unit-mass kinetic factor
 // T1_a = 1/2 <N'|N'> and the dipole factor D_a, by the same element quadrature as in 1-D. The
 // non-separable potential and mass are applied on the GPU at the Gauss points of the same tables.
-static void assemble_axis(const Basis& B, Band& S, Band& T1, Band& D) {
+static void assemble_axis(const Basis& B, const Medium& med, Band& S, Band& T1, Band& D, Band& Wm) {
   const int p = B.p, nq = B.nq, P1 = p + 1;
   const int64_t n = B.nfun - 2;
-  for (Band* m : {&S, &T1, &D}) {
+  for (Band* m : {&S, &T1, &D, &Wm}) {
     m->n = n;
     m->p = p;
     m->a.assign((size_t)n * P1, 0.0);
@@ -230,7 +251,7 @@ static void assemble_axis(const Basis& B, Band& S, Band& T1, Band& D) {
       for (int c = 0; c <= a; ++c) {
         const int64_t fi = first + a, fj = first + c;
         if (fj < 1 || fi > B.nfun - 2) continue;
-        double s = 0, t = 0, d = 0;
+        double s = 0, t = 0, d = 0, wm = 0;
         for (int q = 0; q < nq; ++q) {
           const double w = B.wq[e * nq + q], x = B.xq[e * nq + q];
           const double* N = &B.val[(e * nq + q) * P1];
@@ -238,11 +259,13 @@ static void assemble_axis(const Basis& B, Band& S, Band& T1, Band& D) {
           s += w * N[a] * N[c];
           t += 0.5 * w * dN[a] * dN[c];
           d += w * x * N[a] * N[c];
+          wm += w * med.cap_axis(x) * N[a] * N[c];
         }
         const size_t k = (size_t)(fi - 1) * P1 + (fi - fj);
         S.a[k] += s;
         T1.a[k] += t;
         D.a[k] += d;
+        Wm.a[k] += wm;
       }
   }
 }
@@ -432,6 +455,28 @@ int tdz_assemble(const tdz_basis* const* axes, int dim, const tdz_medium* medium
     }
   }
   if (med.mass_kind == TDZ_MASS_CONST && !(med.mass_par[0] > 0)) return TDZ_EINVAL;
+  med.cap_kind = medium->cap_kind;
+  std::memcpy(med.cap_par, medium->cap_par, sizeof(med.cap_par));
+  if (med.cap_kind < TDZ_CAP_NONE || med.cap_kind > TDZ_CAP_MANOLOPOULOS) {
+    set_error("tdz_assemble: unknown absorbing-layer kind");
+    return TDZ_EINVAL;
+  }
+  if (med.cap_kind != TDZ_CAP_NONE) {
+    const double r0 = med.cap_par[0], R = med.cap_par[1];
+    bool ok = r0 >= 0.0 && R > r0 && std::isfinite(R);
+    if (med.cap_kind == TDZ_CAP_POLY) ok = ok && med.cap_par[2] >= 0.0 && med.cap_par[3] >= 0.0;
+    if (med.cap_kind == TDZ_CAP_MANOLOPOULOS) {
+      ok = ok && med.cap_par[2] > 0.0;
+      // the mask diverges at |x_a| = R: no quadrature point may reach it (R at or beyond the domain's edge)
+      for (int a = 0; a < dim && ok; ++a)
+        for (double x : axes[a]->b.xq) ok = ok && std::fabs(x) < R;
+    }
+    if (!ok) {
+      set_error("tdz_assemble: invalid absorbing-layer parameters (0 <= r0 < R; eta0, k >= 0; m > 0; the "
+                "Manolopoulos layer must end at or beyond the domain's edge)");
+      return TDZ_EINVAL;
+    }
+  }
   if (dim > 1 && (med.mass_kind == TDZ_MASS_LAYERS || med.mass_kind == TDZ_MASS_QUESNE ||
                   med.pot_kind == TDZ_POT_LAYERS || med.pot_kind == TDZ_POT_QUESNE || med.pot_kind == TDZ_POT_H2P)) {
     set_error("tdz_assemble: 1-D-only medium kind in a 2-D/3-D assembly");
@@ -452,7 +497,7 @@ int tdz_assemble(const tdz_basis* const* axes, int dim, const tdz_medium* medium
     } else {
       for (int a = 0; a < dim; ++a) {
         o.axis[a] = axes[a]->b;
-        assemble_axis(o.axis[a], o.Sa[a], o.T1a[a], o.Da[a]);
+        assemble_axis(o.axis[a], med, o.Sa[a], o.T1a[a], o.Da[a], o.Wa[a]);
       }
     }
   } catch (const std::bad_alloc&) {
@@ -481,8 +526,9 @@ int tdz_ops_band(const tdz_ops* ops, int which, int axis, double* out) {
       case TDZ_MAT_S: m = &ops->o.Sa[axis]; break;
       case TDZ_MAT_T: m = &ops->o.T1a[axis]; break;
       case TDZ_MAT_D: m = &ops->o.Da[axis]; break;
+      case TDZ_MAT_W: m = &ops->o.Wa[axis]; break;
       default:
-        set_error("tdz_ops_band: 2-D/3-D operators expose the per-axis S, T (unit mass) and D factors");
+        set_error("tdz_ops_band: 2-D/3-D operators expose the per-axis S, T (unit mass), D and W factors");
         return TDZ_EINVAL;
     }
     std::memcpy(out, m->a.data(), sizeof(double) * m->a.size());
@@ -496,6 +542,8 @@ int tdz_ops_band(const tdz_ops* ops, int which, int axis, double* out) {
     case TDZ_MAT_D: m = &ops->o.D; break;
     case TDZ_MAT_G: m = &ops->o.G; break;
     case TDZ_MAT_K: m = &ops->o.K; break;
+    case TDZ_MAT_W: m = &ops->o.W; break;
+    case TDZ_MAT_VEL: m = &ops->o.M; break;
     default: return TDZ_EINVAL;
   }
   std::memcpy(out, m->a.data(), sizeof(double) * m->a.size());
@@ -569,3 +617,54 @@ int tdz_ground_state(const tdz_ops* ops, double* energy, double* c) {
 }
 
 }  // extern "C"
+
+// ----------------------------------------------------------------------------- a_Q
+// The position-dependent-mass term of the dipole acceleration (Eq. aQ_definition) in 1-D: (i/4) <[p m^-1 p,
+// p m^-1 + m^-1 p]> = i <[T, v]>; in the Galerkin basis an operator product A B is A S^-1 B, so
+// a_Q = i c^H (T S^-1 Vel - Vel S^-1 T) c = -2 Im[(T c)^H S^-1 (Vel c)], with Vel = -(i/2) M.
+// S is factored once (real symmetric positive definite band, LDL^T) and reused for every state.
+extern "C" int tdz_pdm_acceleration(const tdz_ops* ops, const double* c, int64_t nstates, double* aq) {
+  if (!ops || !c || !aq || nstates < 1 || ops->o.dim != 1) return TDZ_EINVAL;
+  const Ops& o = ops->o;
+  const int64_t n = o.S.n;
+  const int p = o.S.p, P1 = p + 1;
+  std::vector<double> f(o.S.a);
+  if (!band_ldlt(f, n, p)) {
+    set_error("tdz_pdm_acceleration: overlap factorisation failed");
+    return TDZ_ENOCONV;
+  }
+  std::vector<double> cr(n), ci(n), tr(n), ti(n), vr(n), vi(n);
+  for (int64_t s = 0; s < nstates; ++s) {
+    const double* x = c + 2 * n * s;
+    for (int64_t i = 0; i < n; ++i) {
+      cr[i] = x[2 * i];
+      ci[i] = x[2 * i + 1];
+    }
+    band_matvec(o.T, cr, tr);
+    band_matvec(o.T, ci, ti);
+    // M c with M antisymmetric: row i sums M(i, i-d) c_{i-d} - M(i+d, i) c_{i+d}
+    for (int64_t i = 0; i < n; ++i) {
+      double ar = 0.0, ai = 0.0;
+      for (int d = 1; d <= p; ++d) {
+        if (i - d >= 0) {
+          ar += o.M.a[(size_t)i * P1 + d] * cr[i - d];
+          ai += o.M.a[(size_t)i * P1 + d] * ci[i - d];
+        }
+        if (i + d < n) {
+          ar -= o.M.a[(size_t)(i + d) * P1 + d] * cr[i + d];
+          ai -= o.M.a[(size_t)(i + d) * P1 + d] * ci[i + d];
+        }
+      }
+      // Vel c = -(i/2) M c
+      vr[i] = 0.5 * ai;
+      vi[i] = -0.5 * ar;
+    }
+    band_ldlt_solve(f, n, p, vr);
+    band_ldlt_solve(f, n, p, vi);
+    // z = (T c)^H x = sum conj(t_i) x_i; a_Q = -2 Im z
+    double zi = 0.0;
+    for (int64_t i = 0; i < n; ++i) zi += tr[i] * vi[i] - ti[i] * vr[i];
+    aq[s] = -2.0 * zi;
+  }
+  return TDZ_OK;
+}

@@ -27,9 +27,12 @@ struct Medium {
   double mass_par[4] = {1, 0, 0, 0};
   double pot_par[4] = {0, 0, 0, 0};
   std::vector<double> bounds, lmass, lpot;
+  int cap_kind = TDZ_CAP_NONE;
+  double cap_par[4] = {0, 0, 0, 0};
   double inv_mass(const double* r, int dim) const;
   double potential(const double* r, int dim) const;
   double dpotential(const double* r, int dim, int axis) const;
+  double cap_axis(double x) const;  // 1-D absorbing mask of one coordinate (eta = sum over the axes)
 };
 
 // symmetric lower band: band[i*(p+1)+d] = M(i, i-d)
@@ -45,10 +48,13 @@ struct Ops {
   int64_t n[3] = {0, 0, 0};
   int p[3] = {0, 0, 0};
   Medium med;
-  // 1-D matrices
-  Band S, T, V, H0, D, G, K;
-  // 2-D / 3-D: per-axis 1-D factors (unit-mass kinetic T1 = 1/2 <N'|N'>) and quadrature tables
-  Band Sa[3], T1a[3], Da[3];
+  // 1-D matrices (W: absorbing-layer mask, all zero without one; M: the real antisymmetric part of the
+  // velocity matrix, Vel = -(i/2) M, stored as its lower band M(i, i-d), d >= 1)
+  Band S, T, V, H0, D, G, K, W, M;
+  // 2-D / 3-D: per-axis 1-D factors (unit-mass kinetic T1 = 1/2 <N'|N'>, the axis' absorbing mask W_a)
+  // and quadrature tables
+  Band Sa[3], T1a[3], Da[3], Wa[3];
+  bool has_cap() const { return med.cap_kind != TDZ_CAP_NONE; }
   Basis axis[3];
 };
 

@@ -60,6 +60,10 @@ MEDIA = [
     ("ho", lambda: (wl.knots_for_nsplines(-10, 10, 60, 4), 4, 5, wl.ho_medium([1.0]))),
     ("h2p", lambda: (wl.knots_for_nsplines(-60, 60, 150, 7), 7, 8,
                      wl.medium({"kind": "const", "m": 1.0}, {"kind": "h2p_softcore", "R": 2.0, "eps": 1.472}))),
+    ("cap_manolopoulos", lambda: (wl.knots_for_nsplines(-40, 40, 120, 6), 6, 7,
+                                  wl.with_cap(wl.softcore_medium(2.0), "manolopoulos", 22.0, 40.0, m=1.0))),
+    ("cap_poly", lambda: (wl.dqw_knots(wl.dqw_medium(10.0, 3.0, 0.24), 400, 6), 6, 7,
+                          wl.with_cap(wl.dqw_medium(10.0, 3.0, 0.24), "poly", 300.0, 1000.0, eta0=0.01, k=2.0))),
 ]
 
 
@@ -68,9 +72,10 @@ def test_band_assembly_matches_oracle(tdz, name, make):
     knots, p, nq, med = make()
     ops = tdz.assemble_1d(knots, p, med, nq)
     ref = assemble.assemble_1d(knots, p, nq, med)
-    for key in ("S", "T", "V", "H0", "K"):
+    for key in ("S", "T", "V", "H0", "K", "W"):
         a, b = ops.band(key), _lower_band(ref[key], p)
         assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(b)) + 1e-300, key
+    assert (np.max(np.abs(ops.band("W"))) > 0) == ("cap" in med)
     for key in ("D", "G"):
         a, b = ops.band(key), _lower_band(ref[key][0], p)
         assert np.max(np.abs(a - b)) <= 1e-12 * max(np.max(np.abs(b)), 1e-300) + 1e-300, key
@@ -114,3 +119,38 @@ def test_axis_factors_for_tensor_bases_match_oracle(tdz):
         assert np.max(np.abs(ops.band("S", a) - _lower_band(ref["S"], 4))) < 1e-13
         assert np.max(np.abs(ops.band("T", a) - _lower_band(ref["T"], 4))) < 1e-12
         assert np.max(np.abs(ops.band("D", a) - _lower_band(ref["D"][0], 4))) < 1e-13
+
+
+def test_harmonic_yields_match_oracle(tdz):
+    """tdz_harmonic_yields (host) against the oracle's trapezoid yields on the oracle's own FFT grid, for a
+    record with odd harmonics spanning ten decades (Sec. "Dipoles")."""
+    from oracle import hhg
+    dt, w0 = 0.05, 0.057
+    t = np.arange(9000) * dt
+    sig = sum(10.0 ** (-(q - 1) / 2) * np.sin(q * w0 * t + 0.3 * q) for q in range(1, 22, 2))
+    om, S = hhg.spectrum(sig, dt, length_form=True)
+    qs, Yo = hhg.harmonic_yields(om, S, w0, 21)
+    q2, Y = tdz.harmonic_yields(S, 0.0, om[1] - om[0], w0, 21)
+    assert np.array_equal(qs, q2)
+    assert np.max(np.abs(Y[0] / Yo - 1)) < 1e-12
+
+
+def test_velocity_band_and_pdm_acceleration_match_oracle(tdz):
+    """The velocity matrix's antisymmetric part M (Eq. vel_elem, Vel = -(i/2) M) of a smooth and of a
+    stepped position-dependent mass, and a_Q (Eq. aQ_definition) of a few states, against the oracle."""
+    from oracle import propagate
+    cases = [(wl.open_uniform_knots(-2.0, 30.0, 200, 7), 7, 8, wl.quesne_medium()),
+             (wl.dqw_knots(wl.dqw_medium(10.0, 3.0, 0.24), 500, 6), 6, 7, wl.dqw_medium(10.0, 3.0, 0.24))]
+    rng = np.random.default_rng(11)
+    for knots, p, nq, med in cases:
+        ops = tdz.assemble_1d(knots, p, med, nq)
+        ref = assemble.assemble_1d(knots, p, nq, med)
+        M = ref["M"][0]
+        a, b = ops.band("VEL"), _lower_band(M, p)
+        assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(b))
+        assert np.all(a[:, 0] == 0.0)
+        states = [rng.standard_normal(ops.n) + 1j * rng.standard_normal(ops.n) for _ in range(3)]
+        aq = ops.pdm_acceleration(np.stack(states))
+        for x, v in zip(states, aq):
+            r = propagate.a_quantum(ref, x)
+            assert abs(v - r) <= 1e-10 * max(1.0, abs(r)), (v, r)

@@ -158,3 +158,100 @@ def test_hhg_cutoff_and_spectrum():
 def _golden(name):
     import os
     return os.path.join(os.path.dirname(__file__), "golden", name)
+
+
+# ------------------------------------------------------------------ absorbing layer (CAP matrix)
+def test_cap_polynomial_mask_closed_forms():
+    """Sec. "Parallel assembly", CAP matrix W = <B|eta|B>: for eta = eta0 s^k, s = (|x| - r0)/(R - r0), on a
+    grid with knots at 0 and +-r0 (eta is a polynomial on every element) and enough Gauss points, the
+    untrimmed W gives exactly 1^T W 1 = int eta dx and g^T W g = int eta x^2 dx (g: Greville abscissae,
+    sum_a g_a N_a(x) = x), W is positive semidefinite and vanishes on functions inside |x| < r0."""
+    p, k, eta0, r0, R = 3, 3, 0.7, 4.0, 10.0
+    t = wl.open_piecewise_knots([-R, -r0, 0.0, r0, R], [6, 5, 5, 6], p)
+    med = wl.with_cap(wl.softcore_medium(2.0), "poly", r0, R, eta0=eta0, k=k)
+    m = assemble.assemble_1d(t, p, p + 4, med, trim=False)
+    W = m["W"]
+    n = W.shape[0]
+    g = np.array([t[i + 1:i + p + 1].mean() for i in range(n)])
+    D = R - r0
+    assert abs(np.ones(n) @ W @ np.ones(n) - 2 * eta0 * D / (k + 1)) < 1e-13
+    mom2 = 2 * eta0 * D * (r0 ** 2 / (k + 1) + 2 * r0 * D / (k + 2) + D ** 2 / (k + 3))
+    assert abs(g @ W @ g - mom2) < 1e-12 * mom2
+    assert np.linalg.eigvalsh(W.toarray()).min() > -1e-14
+    inner = [i for i in range(n) if -r0 <= t[i] and t[i + p + 1] <= r0]
+    assert len(inner) > 3 and abs(W[inner, :]).max() == 0.0
+
+
+def test_cap_norm_loss_identity_and_absorption():
+    """Crank-Nicolson with the absorbing layer, A = S + tau W + i tau H: the S-norm drops each step by
+    exactly 4 tau c_bar^H W c_bar (c_bar = (c^{n+1} + c^n)/2), from the scheme's own algebra; and a
+    wavepacket sent into a Manolopoulos layer with energy well above its E_min leaves almost nothing
+    behind (transmission-free absorption), while the same packet without the layer keeps its norm."""
+    p, L, r0 = 5, 60.0, 30.0
+    t = wl.knots_for_nsplines(-L, L, 400, p)
+    base = wl.medium({"kind": "const", "m": 1.0}, {"kind": "zero"})
+    med = wl.with_cap(base, "manolopoulos", r0, L, m=1.0)
+    m = assemble.assemble_1d(t, p, p + 1, med)
+    g = wl.greville(t, p)
+    k0 = 1.5                                  # E = 1.125 >> E_min = (c/(2 (L - r0)))^2 / 2 ~ 9.5e-4
+    c0 = np.exp(-0.5 * ((g - 5.0) / 3.0) ** 2 + 1j * k0 * g)
+    c0 = c0 / np.sqrt(np.real(np.conj(c0) @ (m["S"] @ c0)))
+    dt, nsteps = 0.05, 2400                   # the packet travels ~180 bohr: absorbed, or reflected back
+    field = np.zeros((nsteps + 1, 1))
+    tau = dt / 2
+    c1, _ = propagate.cn_propagate(m, c0, field, dt, 1)
+    cb = 0.5 * (c1 + c0)
+    n0 = np.real(np.conj(c0) @ (m["S"] @ c0))
+    n1 = np.real(np.conj(c1) @ (m["S"] @ c1))
+    loss = 4 * tau * np.real(np.conj(cb) @ (m["W"] @ cb))
+    assert loss > 0 and abs((n0 - n1) - loss) < 1e-14
+    c, obs = propagate.cn_propagate(m, c0, field, dt, nsteps)
+    assert np.all(np.diff(obs[:, -1]) <= 1e-15)
+    assert obs[-1, -1] < 1e-5
+    _, obs_free = propagate.cn_propagate(assemble.assemble_1d(t, p, p + 1, base), c0, field, dt, nsteps)
+    assert abs(obs_free[-1, -1] - 1.0) < 1e-12
+
+
+# ------------------------------------------------------------------ velocity form and the PDM term a_Q
+def test_velocity_matrix_and_driven_ho_current():
+    """Eq. vel_elem: Vel = -(i/2) M with M real antisymmetric (Vel Hermitian); for the Appendix A oscillator
+    (m = 1) the current J = c^H Vel c = d<x>/dt follows the closed form -(E0/2) t sin t, at second order in dt."""
+    e0 = 0.2
+    errs = []
+    for dt in (0.02, 0.01):
+        wk = wl.driven_ho_1d(e0=e0, dt=dt, t_end=10.0, L=20.0, nsplines=200, p=5)
+        r = wk.runs[0]
+        m = assemble.assemble_1d(r.knots, r.degree, r.nquad, r.medium)
+        M = m["M"][0]
+        assert abs(M + M.T).max() < 1e-15 and abs(M).max() > 0.1
+        _, v = eigen.lowest_states(m, 1)
+        c, obs, J = propagate.cn_propagate(m, v[:, 0], r.field, dt, wk.nsteps, currents=True)
+        errs.append(np.max(np.abs(J[:, 0] + 0.5 * e0 * obs[:, 0] * np.sin(obs[:, 0]))))
+    assert errs[1] < 4e-4
+    assert 3.5 < errs[0] / errs[1] < 4.5
+
+
+def test_pdm_current_and_acceleration_against_time_derivatives():
+    """Quesne medium (smooth position-dependent mass), a superposition of the two lowest levels: the
+    current J (Sec. "Currents and coherence dynamics") is the time derivative of the dipole, and the full
+    Ehrenfest acceleration a + a_Q (Eq. pdm_acceleration with Eq. aQ_definition) is the time derivative
+    of J; without a_Q the acceleration misses by half its scale."""
+    m = assemble.assemble_1d(wl.open_uniform_knots(-2.0, 30.0, 300, 7), 7, 8, wl.quesne_medium())
+    _, v = eigen.lowest_states(m, 2, dense_max=10 ** 9)
+    c0 = (v[:, 0] + v[:, 1]) / math.sqrt(2)
+    dt, n = 0.002, 200
+    c, obs, J = propagate.cn_propagate(m, c0, np.zeros((n + 1, 1)), dt, n, currents=True)
+    d = obs[:, 2]
+    assert np.max(np.abs(J[1:-1, 0] - (d[2:] - d[:-2]) / (2 * dt))) < 1e-6 * np.max(np.abs(J))
+    cs = [c0]
+    for k in range(n):
+        cs.append(propagate.cn_propagate(m, cs[-1], np.zeros((2, 1)), dt, 1, record=False)[0])
+    aq = np.array([propagate.a_quantum(m, x) for x in cs[1:]])
+    dJ = (J[2:, 0] - J[:-2, 0]) / (2 * dt)
+    a = obs[1:-1, 3]
+    assert np.max(np.abs(a + aq[1:-1] - dJ)) < 1e-5 * np.max(np.abs(dJ))
+    assert np.max(np.abs(a - dJ)) > 0.3 * np.max(np.abs(dJ))
+    # constant mass: the commutator [T, v] of the continuum vanishes; the Galerkin a_Q is small
+    ms = assemble.assemble_1d(wl.knots_for_nsplines(-20, 20, 200, 6), 6, 7, wl.softcore_medium(2.0))
+    _, g = eigen.lowest_states(ms, 2)
+    assert abs(propagate.a_quantum(ms, (g[:, 0] + g[:, 1]) / math.sqrt(2))) < 1e-6

@@ -91,6 +91,16 @@ def softcore_medium(eps: float, z: float = 1.0) -> Dict:
     return medium({"kind": "const", "m": 1.0}, {"kind": "softcore", "z": z, "eps": eps})
 
 
+def with_cap(med: Dict, kind: str, r0: float, R: float, **par) -> Dict:
+    """A copy of `med` with an absorbing layer (complex absorbing potential -i eta) in r0 < |x_a| < R on
+    every axis: kind "poly" (eta0, k) or "manolopoulos" (m, the mass in the layer; R must be the edge)."""
+    out = {"mass": dict(med["mass"]), "potential": dict(med["potential"])}
+    cap = {"kind": kind, "r0": float(r0), "R": float(R)}
+    cap.update({k: float(v) for k, v in par.items()})
+    out["cap"] = cap
+    return out
+
+
 def ho_medium(omega: Sequence[float]) -> Dict:
     """Constant unit mass, V = 1/2 sum_a omega_a^2 x_a^2."""
     return medium({"kind": "const", "m": 1.0}, {"kind": "ho", "omega": list(map(float, omega))})
