@@ -9,16 +9,19 @@
 // extrapolation from the last two steps (mixed path). Observables of Sec. "Dipoles" are
 // reduced after every step.
 //
-// GPU organisation (1, 2, 4 or 8 warps per run, the whole time loop inside one persistent launch):
-//   * the n rows of a run are split into K <= 32 x warps chunks of m rows, one per lane; the last
-//     P rows of every chunk but the last are a separator ("Sep_k"), the rest its interior;
+// GPU organisation (the whole time loop inside one persistent launch):
+//   * the n rows of a run are split into K chunks of m rows, one per lane, K chosen on the host so that
+//     every run of the batch has about the same m; the runs are packed lane by lane into blocks (a run's
+//     K lanes are consecutive threads of one block, and may span warps); the last P rows of every chunk
+//     but the last are a separator ("Sep_k"), the rest its interior;
 //   * sweep 1 (top-down): each lane eliminates its interior with a register-window band
 //     LDL^T, carrying the coupling to the separator above (the "spike") and the right-hand
 //     side; it stores L and D^-1 and leaves the Schur complement of its lower separator;
 //   * sweep 2 (bottom-up): each lane eliminates its interior from the bottom to obtain the
 //     Schur complement of the separator above it (no storage);
-//   * the separators form a block-tridiagonal system (K-1 blocks of P x P), factored and
-//     solved by the run's first warp in shared memory (block LDL^T with explicit pivot inverses);
+//   * the separators form a block-tridiagonal system (K-1 blocks of P x P), kept in the shared memory of
+//     the run's own lanes and factored and solved by the warp that holds the run's first lane (block
+//     LDL^T with explicit pivot inverses);
 //   * forward/back substitution of every interior with the separator values;
 //   * state update and observables.
 // All arrays of a run are interleaved [row][lane of the run] so that every warp access is coalesced.
@@ -39,12 +42,11 @@
 namespace tdz {
 
 constexpr int LANES = 32;
-constexpr int kSlotW = 8;  // schedule slots encode run * kSlotW + warp of the run (at most 8 warps per run)
 constexpr int MAXP = 8;
 
 struct GeomDev {
   int n, m, K;
-  int ks;  // interleave stride of the per-row arrays: 32 x (warps per run)
+  int ks;  // interleave stride of the per-row arrays: the run's lanes (K)
   // Band arrays, [m][P+1][32] each.
   //   binary64 path: S, H (= H0 = T + V), D, G, Km (<m^-1>) as double.
   //   mixed path:    S  = float4 {S.hi, H0.hi, D.hi, S.lo}   (one 16-byte load per entry in the sweeps)
@@ -84,8 +86,8 @@ struct RunDev {
 struct StepArgs {
   const GeomDev* geoms;
   RunDev* runs;
-  const int* order;
-  int nruns;
+  const int* lanes;  // [ngroups][threads per block]: run << 8 | lane of the run, or -1 (no run)
+  int ngroups;
   int* counter;
   const double* field;  // [run][nsteps+1]
   double* obs;          // [run][nsteps][5]
@@ -129,11 +131,12 @@ struct Lane {
   bool active, up, dn;
 };
 
-// Shared-memory elements per warp slot for the reduced system. A run of w warps has up to 32w - 1
-// separators and uses the areas of its w adjacent slots: Dg and E (cap P x P blocks each), rb
-// (cap x P) and one P x P scratch tile, cap = 32w - 1; 2 * 32 P^2 + 32 P + P^2 per slot covers
-// every w, since w of them hold 2 (32w - 1) P^2 + (32w - 1) P + P^2.
-__host__ __device__ constexpr int red_elems(int P) { return 2 * 32 * P * P + 32 * P + P * P; }
+// Shared memory of a block (elements of the solve precision's complex type, then doubles):
+//   * per lane 2 P^2 + P: a run of K lanes keeps its K - 1 separators' Dg and E blocks and rb vectors in
+//     the area of its own lanes;
+//   * per warp one P x P scratch tile for the reduced factorisation the warp runs;
+//   * per lane 2 x 5 doubles for the run sums.
+__host__ __device__ constexpr int red_lane_elems(int P) { return 2 * P * P + P; }
 
 template <class T>
 struct Red {  // reduced system of one run in shared memory
@@ -291,31 +294,68 @@ TDZ_DEV void sweep2(const GeomDev& g, const RunDev& run, const Lane& L, T tau, T
 }
 
 // ============================================================================ reduced system
+// Lower-triangle pair number t (row-wise, 0 <= t < P(P+1)/2) -> (i, j), i >= j.
+TDZ_DEV void tri_pair(int t, int& i, int& j) {
+  i = 0;
+  while (t > i) {
+    t -= i + 1;
+    ++i;
+  }
+  j = t;
+}
+
+// In-place inverse of a complex symmetric P x P block (no pivoting) by the symmetric sweep operator: sweeping
+// pivot k replaces a_kk by -1/a_kk, a_ik and a_ki by a_ik / a_kk and every other a_ij by a_ij - a_ik a_kj /
+// a_kk; the matrix stays symmetric throughout and all P sweeps leave -A^-1. Only the P(P+1)/2 entries of
+// the lower triangle are computed (one per lane) and written to both halves.
 template <int P, class T>
 TDZ_DEV void red_invert(cx<T>* M, int lane) {
-  // in-place Gauss-Jordan inversion (no pivoting) of a P x P complex symmetric block
-  for (int q = 0; q < P; ++q) {
-    cx<T> piv = crecip(M[q * P + q]);
-    cx<T> nv[2];
-    int cnt = 0;
-    for (int t = lane; t < P * P; t += LANES, ++cnt) {
-      int r = t / P, c = t % P;
-      cx<T> v;
-      if (r == q && c == q) v = piv;
-      else if (r == q) v = cmul(M[q * P + c], piv);
-      else if (c == q) v = czero<T>() - cmul(M[r * P + q], piv);
-      else v = cmsub(M[r * P + c], cmul(M[r * P + q], piv), M[q * P + c]);
-      nv[cnt] = v;
+  constexpr int NT = P * (P + 1) / 2;
+  constexpr int R = (NT + LANES - 1) / LANES;
+  int ti[R], tj[R];
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    ti[u] = tj[u] = 0;
+    if (lane + u * LANES < NT) tri_pair(lane + u * LANES, ti[u], tj[u]);
+  }
+  for (int k = 0; k < P; ++k) {
+    cx<T> nv[R];
+    const cx<T> piv = crecip(M[k * P + k]);
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+      if (lane + u * LANES < NT) {
+        const int i = ti[u], j = tj[u];
+        if (i == k && j == k) nv[u] = czero<T>() - piv;
+        else if (i == k) nv[u] = cmul(M[j * P + k], piv);
+        else if (j == k) nv[u] = cmul(M[i * P + k], piv);
+        else nv[u] = cmsub(M[i * P + j], cmul(M[i * P + k], piv), M[j * P + k]);
+      }
     }
     __syncwarp();
-    cnt = 0;
-    for (int t = lane; t < P * P; t += LANES, ++cnt) M[t] = nv[cnt];
+#pragma unroll
+    for (int u = 0; u < R; ++u)
+      if (lane + u * LANES < NT) M[ti[u] * P + tj[u]] = M[tj[u] * P + ti[u]] = nv[u];
     __syncwarp();
   }
+#pragma unroll
+  for (int u = 0; u < R; ++u)
+    if (lane + u * LANES < NT) {
+      const cx<T> v = czero<T>() - M[ti[u] * P + tj[u]];
+      M[ti[u] * P + tj[u]] = M[tj[u] * P + ti[u]] = v;
+    }
+  __syncwarp();
 }
 
 template <int P, class T>
 TDZ_DEV void red_factor(Red<T>& red, int nsep, int lane) {
+  constexpr int NT = P * (P + 1) / 2;
+  constexpr int R = (NT + LANES - 1) / LANES;
+  int ti[R], tj[R];
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    ti[u] = tj[u] = 0;
+    if (lane + u * LANES < NT) tri_pair(lane + u * LANES, ti[u], tj[u]);
+  }
   for (int s = 0; s < nsep; ++s) {
     cx<T>* D = red.Dg + s * P * P;
     if (s > 0) {
@@ -330,22 +370,23 @@ TDZ_DEV void red_factor(Red<T>& red, int nsep, int lane) {
         red.Wt[t] = acc;
       }
       __syncwarp();
-      // D -= F * E^T ; E <- F
-      cx<T> nv[2];
-      int cnt = 0;
-      for (int t = lane; t < P * P; t += LANES, ++cnt) {
-        int r = t / P, c = t % P;
-        cx<T> acc = D[t];
+      // D -= F * E^T (symmetric: the lower triangle, mirrored); E <- F
+      cx<T> nv[R];
 #pragma unroll
-        for (int q = 0; q < P; ++q) acc = cmsub(acc, red.Wt[r * P + q], E[c * P + q]);
-        nv[cnt] = acc;
+      for (int u = 0; u < R; ++u) {
+        if (lane + u * LANES < NT) {
+          const int r = ti[u], c = tj[u];
+          cx<T> acc = D[r * P + c];
+#pragma unroll
+          for (int q = 0; q < P; ++q) acc = cmsub(acc, red.Wt[r * P + q], E[c * P + q]);
+          nv[u] = acc;
+        }
       }
       __syncwarp();
-      cnt = 0;
-      for (int t = lane; t < P * P; t += LANES, ++cnt) {
-        D[t] = nv[cnt];
-        E[t] = red.Wt[t];
-      }
+#pragma unroll
+      for (int u = 0; u < R; ++u)
+        if (lane + u * LANES < NT) D[ti[u] * P + tj[u]] = D[tj[u] * P + ti[u]] = nv[u];
+      for (int t = lane; t < P * P; t += LANES) E[t] = red.Wt[t];
       __syncwarp();
     }
     red_invert<P, T>(D, lane);
@@ -941,77 +982,86 @@ TDZ_DEV void update_observe_mixed(const GeomDev& g, const RunDev& run, const Lan
   out[4] = (double)fj.h + (double)fj.l;
 }
 
-TDZ_DEV double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Sums over all lanes of a run (nw adjacent warps), identical in every lane of the run. Called by
-// every thread of the block (it contains block barriers); idle warps pass zeros.
+// Sums over the K lanes of a run (consecutive threads of the block, possibly in several warps), the same
+// value in every lane of the run, in a fixed order (lane 0 of the run adds its lanes' values in lane
+// order). sh and tot are this block's per-lane scratch. Called by every thread of the block (it contains
+// block barriers); threads without a run pass has = false.
 template <int NV>
-TDZ_DEV void run_sum(double (&v)[NV], double (*sh)[5], int wib, int sub, int nw) {
+TDZ_DEV void run_sum(double (&v)[NV], double (*sh)[5], double (*tot)[5], int k, int K, bool has) {
+  const int j = threadIdx.x;
 #pragma unroll
-  for (int q = 0; q < NV; ++q) v[q] = warp_sum(v[q]);
-  if ((threadIdx.x & 31) == 0)
-#pragma unroll
-    for (int q = 0; q < NV; ++q) sh[wib][q] = v[q];
+  for (int q = 0; q < NV; ++q) sh[j][q] = v[q];
   __syncthreads();
-  const int first = wib - sub;
+  if (has && k == 0) {
 #pragma unroll
-  for (int q = 0; q < NV; ++q) {
-    double t = 0.0;
-    for (int s = 0; s < nw; ++s) t += sh[first + s][q];
-    v[q] = t;
+    for (int q = 0; q < NV; ++q) {
+      double t = 0.0;
+      for (int l = 0; l < K; ++l) t += sh[j + l][q];
+      tot[j][q] = t;
+    }
   }
   __syncthreads();
+  if (has)
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] = tot[j - k][q];
+}
+
+// The reduced systems of the runs whose first lane sits in the calling warp, one after the other, by the
+// whole warp (each run's separator blocks are in its own lanes' shared memory). `mine` describes the
+// calling lane's run, `go` whether that run takes part; a run is processed when its first lane says so.
+template <int P, class T>
+TDZ_DEV void warp_chains(unsigned starts, const Red<T>& mine, int nsep, bool go, cx<T>* wt, int lane, bool factor,
+                         bool solve) {
+  unsigned rest = starts;
+  while (rest) {
+    const int b = __ffs(rest) - 1;
+    rest &= rest - 1;
+    const int ns = __shfl_sync(0xffffffffu, nsep, b);
+    const bool gob = __shfl_sync(0xffffffffu, (int)go, b) != 0;
+    if (!gob || ns <= 0) continue;
+    Red<T> r;
+    r.Dg = reinterpret_cast<cx<T>*>(__shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(mine.Dg), b));
+    r.E = reinterpret_cast<cx<T>*>(__shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(mine.E), b));
+    r.rb = reinterpret_cast<cx<T>*>(__shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(mine.rb), b));
+    r.Wt = wt;
+    if (factor) red_factor<P, T>(r, ns, lane);
+    if (solve) red_solve<P, T>(r, ns, lane);
+  }
 }
 
 // ============================================================================ the kernel
-// The block's warps are slots of a schedule built on the host: a slot holds warp `sub` of run `run`
-// (encoded run * kSlotW + sub; a run has 1, 2, 4 or 8 warps), or nothing (-1); the warps of a run
-// are adjacent in one block. The block advances its runs in lock step: it crosses each phase of a
-// step together (block barriers), so all warps of an SM execute the same code region at a time and
-// the warps of a run see each other's chunk boundaries and shared reduced system. The adaptive
-// refinement decides collectively how many extra solves the block makes; warps whose run is
-// already converged skip the work of those rounds.
+// A block takes a group of runs from a schedule built on the host: the group's lane map gives every thread
+// its run and its lane (chunk) in that run, or no run. The block advances its runs in lock step: it
+// crosses each phase of a step together (block barriers), so all warps of an SM execute the same code
+// region at a time and the lanes of a run see each other's chunk boundaries and the run's shared reduced
+// system. The adaptive refinement decides collectively how many extra solves the block makes; lanes whose
+// run is already converged skip the work of those rounds.
 template <int P, bool MIXED, bool CAP>
 __global__ void __launch_bounds__(256) cn1d_kernel(StepArgs A) {
   using T = typename std::conditional<MIXED, float, double>::type;
-  extern __shared__ unsigned char smem_raw[];
-  __shared__ int s_base;
-  __shared__ double s_sum[8][5];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_group;
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  const int wpb = blockDim.x >> 5;
-  const size_t per_warp = (size_t)red_elems(P) * sizeof(cx<T>);
+  const int lpb = blockDim.x;
+  cx<T>* lane_area = reinterpret_cast<cx<T>*>(smem_raw);
+  cx<T>* wt_area = lane_area + (size_t)lpb * red_lane_elems(P);
+  double (*s_sum)[5] = reinterpret_cast<double (*)[5]>(wt_area + (size_t)(lpb / 32) * P * P);
+  double (*s_tot)[5] = s_sum + lpb;
 
   while (true) {
-    if (threadIdx.x == 0) s_base = atomicAdd(A.counter, wpb);
+    if (threadIdx.x == 0) s_group = atomicAdd(A.counter, 1);
     __syncthreads();
-    const int item = s_base + wib;
-    const bool done = s_base >= A.nruns;
+    const int grp = s_group;
     __syncthreads();
-    if (done) break;
-    const int slot = item < A.nruns ? A.order[item] : -1;
-    const bool has = slot >= 0;
-    const int rid = has ? slot / kSlotW : 0;
-    const int sub = has ? slot % kSlotW : 0;
+    if (grp >= A.ngroups) break;
+    const int ent = A.lanes[(size_t)grp * lpb + threadIdx.x];
+    const bool has = ent >= 0;
+    const int rid = has ? (ent >> 8) : 0;
     RunDev run = A.runs[rid];
     const GeomDev g = A.geoms[run.geom];
-    const int nw = has ? g.ks / LANES : 1;  // warps of this run
-    // reduced system of the run, in the shared memory of its first warp (and the second's)
-    Red<T> red;
-    {
-      const int cap = 32 * nw - 1;
-      cx<T>* base = reinterpret_cast<cx<T>*>(smem_raw + (wib - sub) * per_warp);
-      red.Dg = base;
-      red.E = base + cap * P * P;
-      red.rb = base + 2 * cap * P * P;
-      red.Wt = base + 2 * cap * P * P + cap * P;
-    }
     Lane L;
-    L.k = sub * LANES + lane;
+    L.k = has ? (ent & 255) : 0;
     L.K = has ? g.K : 1;
     L.m = g.m;
     L.ks = g.ks;
@@ -1019,7 +1069,18 @@ __global__ void __launch_bounds__(256) cn1d_kernel(StepArgs A) {
     L.up = L.active && L.k >= 1;
     L.dn = L.active && L.k < g.K - 1;
     L.mI = L.dn ? g.m - P : g.m;
-    const bool lead = has && sub == 0;  // solves the reduced system and writes the run's results
+    // the run's reduced system, in the shared memory of its own lanes (first lane at threadIdx.x - k)
+    Red<T> red;
+    {
+      const int cap = L.K - 1;
+      cx<T>* base = lane_area + (size_t)(threadIdx.x - L.k) * red_lane_elems(P);
+      red.Dg = base;
+      red.E = base + cap * P * P;
+      red.rb = base + 2 * cap * P * P;
+      red.Wt = wt_area + wib * P * P;
+    }
+    const bool lead = has && L.k == 0;  // writes the run's results; its warp runs the reduced system
+    const unsigned starts = __ballot_sync(0xffffffffu, lead);
     const double* E = A.field + (size_t)rid * (A.nsteps + 1);
     double* obs = A.obs + (size_t)rid * A.nsteps * 5;
     int status = has ? run.status : TDZ_OK;
@@ -1044,10 +1105,7 @@ __global__ void __launch_bounds__(256) cn1d_kernel(StepArgs A) {
         __syncthreads();
         if (W.up) sweep2<P, double, false, CAP>(g, run, W, tau_d, ebar_d, red);
         __syncthreads();
-        if (lead && nsep > 0) {
-          red_factor<P, double>(red, nsep, lane);
-          red_solve<P, double>(red, nsep, lane);
-        }
+        warp_chains<P, double>(starts, red, nsep, work, red.Wt, lane, true, true);
         __syncthreads();
         if (W.active) substitute<P, double, false, CAP>(g, run, W, tau_d, ebar_d, red);  // c += delta
         __syncthreads();
@@ -1061,17 +1119,14 @@ __global__ void __launch_bounds__(256) cn1d_kernel(StepArgs A) {
         float rr = 0.f, bb = 0.f;
         if (W.active) rhs_mixed<P, true, CAP>(g, run, W, tau_ff, ebar_ff, rr, bb);
         double sums[2] = {(double)rr, (double)bb};
-        run_sum(sums, s_sum, wib, sub, nw);
+        run_sum(sums, s_sum, s_tot, L.k, L.K, has);
         const double bbs = fmax(sums[1], 1e-300);
         const double rel0 = sqrt(sums[0] / bbs);
         if (W.active) sweep1<P, float, true, CAP>(g, run, W, tau_f, ebar_f, red);
         __syncthreads();
         if (W.up) sweep2<P, float, true, CAP>(g, run, W, tau_f, ebar_f, red);
         __syncthreads();
-        if (lead && nsep > 0) {
-          red_factor<P, float>(red, nsep, lane);
-          red_solve<P, float>(red, nsep, lane);
-        }
+        warp_chains<P, float>(starts, red, nsep, work, red.Wt, lane, true, true);
         __syncthreads();
         if (W.active) substitute<P, float, true, CAP>(g, run, W, tau_f, ebar_f, red);  // w += delta
         __syncthreads();
@@ -1079,7 +1134,7 @@ __global__ void __launch_bounds__(256) cn1d_kernel(StepArgs A) {
         // residual after the solve; refine with the stored factors while above tolerance
         if (W.active) rhs_mixed<P, false, CAP>(g, run, W, tau_ff, ebar_ff, rr, bb);
         double r1[1] = {W.active ? (double)rr : 0.0};
-        run_sum(r1, s_sum, wib, sub, nw);
+        run_sum(r1, s_sum, s_tot, L.k, L.K, has);
         double rel = sqrt(r1[0] / bbs);
         const double rho = fmin(rel / fmax(rel0, 1e-300), 1.0);  // contraction of one FP32 solve
         int it = 1;
@@ -1090,7 +1145,7 @@ __global__ void __launch_bounds__(256) cn1d_kernel(StepArgs A) {
           __syncthreads();
           if (need && W.up) resolve_bwd<P, float, true, CAP>(g, run, W, tau_f, ebar_f, red);
           __syncthreads();
-          if (need && lead && nsep > 0) red_solve<P, float>(red, nsep, lane);
+          warp_chains<P, float>(starts, red, nsep, need, red.Wt, lane, false, true);
           __syncthreads();
           if (need && W.active) substitute<P, float, true, CAP>(g, run, W, tau_f, ebar_f, red);
           __syncthreads();
@@ -1106,7 +1161,7 @@ __global__ void __launch_bounds__(256) cn1d_kernel(StepArgs A) {
           const bool check = need && !ok;
           if (check && W.active) rhs_mixed<P, false, CAP>(g, run, W, tau_ff, ebar_ff, rr, bb);
           double rc[1] = {(check && W.active) ? (double)rr : 0.0};
-          run_sum(rc, s_sum, wib, sub, nw);
+          run_sum(rc, s_sum, s_tot, L.k, L.K, has);
           if (check) {
             rel = sqrt(rc[0] / bbs);
             ok = rel <= A.tol;
@@ -1121,10 +1176,10 @@ __global__ void __launch_bounds__(256) cn1d_kernel(StepArgs A) {
         __syncthreads();
         update_observe_mixed<P>(g, run, W, hist, cur, o);
       }
-      run_sum(o, s_sum, wib, sub, nw);
+      run_sum(o, s_sum, s_tot, L.k, L.K, has);
       if (work) {
         const double Et = E[s + 1];
-        if (lead && lane == 0) {
+        if (lead) {
           double* row = obs + s * 5;
           row[0] = (double)(A.step0 + s + 1) * A.dt;
           row[1] = Et;
@@ -1137,7 +1192,7 @@ __global__ void __launch_bounds__(256) cn1d_kernel(StepArgs A) {
       }
       __syncthreads();
     }
-    if (lead && lane == 0) {
+    if (lead) {
       A.runs[rid].status = status;
       A.runs[rid].hist = hist;
       A.runs[rid].max_rel = fmax(run.max_rel, max_rel);
@@ -1211,15 +1266,24 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-size_t smem_per_warp(int P, bool mixed) {
+// Dynamic shared memory of a block of `lanes` threads (the layout is described at red_lane_elems).
+size_t block_smem(int P, bool mixed, int lanes) {
   const size_t cxsz = mixed ? 8 : 16;
-  return (size_t)red_elems(P) * cxsz;
+  return (size_t)lanes * red_lane_elems(P) * cxsz + (size_t)(lanes / 32) * P * P * cxsz +
+         (size_t)lanes * 10 * sizeof(double);
+}
+
+// Most warps (<= 8) a block can have within `maxsm` bytes of shared memory.
+int max_warps(int P, bool mixed, int maxsm) {
+  int w = 8;
+  while (w > 1 && block_smem(P, mixed, 32 * w) > (size_t)maxsm) --w;
+  return w;
 }
 
 // The dynamic shared-memory limit of a kernel is one attribute of the function, shared by every host
 // thread that launches it. It is only ever raised, straight to the largest size any launch of this
-// instantiation can use on the device (the most warp slots a block gets, times the per-warp reduced
-// system), so a launch made on one thread never finds the limit lowered by a call on another.
+// instantiation can use on the device (a block of the most warps its shared memory allows), so a launch
+// made on one thread never finds the limit lowered by a call on another.
 template <int P, bool M, bool CAP>
 cudaError_t ensure_smem(size_t need) {
   static std::mutex mu;
@@ -1233,8 +1297,7 @@ cudaError_t ensure_smem(size_t need) {
   int maxsm = 0;
   e = cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
-  const size_t spw = smem_per_warp(P, M);
-  const size_t cap = std::min<size_t>(8, std::max<size_t>(1, (size_t)maxsm / spw)) * spw;
+  const size_t cap = block_smem(P, M, 32 * max_warps(P, M, maxsm));
   const size_t v = std::max(need, cap);
   e = cudaFuncSetAttribute(cn1d_kernel<P, M, CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v);
   if (e == cudaSuccess) set_to[dev] = v;
@@ -1245,119 +1308,75 @@ cudaError_t ensure_smem(size_t need) {
 
 namespace {
 
-// Chunking of a run of n rows over the lanes of `warps` warps (1..8): K <= 32 warps chunks of m rows,
-// each interior at least P + 1 rows long (the separator of a chunk is its last P rows).
-struct Chunking {
-  int K, m, ks;
-};
-Chunking chunking(int n, int P, int warps) {
-  int K = std::max(1, std::min(LANES * warps, n / (3 * P)));
+// Chunks (lanes) of a run of n rows for a target of mt rows per lane: K = ceil(n / mt), at most `lanes`,
+// reduced until every interior is at least P + 1 rows long (the separator of a chunk is its last P rows).
+int chunks_for(int n, int P, int mt, int lanes) {
+  int K = std::max(1, std::min(lanes, (n + mt - 1) / mt));
   int m = (n + K - 1) / K;
   while (K > 1 && m - P < P + 1) {
     --K;
     m = (n + K - 1) / K;
   }
-  return {K, m, LANES * warps};
+  return K;
 }
 
-// Schedule of the persistent launch. A block holds `wpb` warp slots and keeps them until all their
-// runs are done, so its duration is that of its longest run; `resident` blocks run at a time and
-// the next group of slots goes to the first block that finishes. Candidate warp assignments are
-// compared by simulating this list schedule (cost of a run per step ~ rows per lane + a small term
-// per separator) and the shortest makespan is kept:
-//   * with allow_pairs, runs of geometries above a threshold get two warps (64 chunks, half the rows
-//     per lane), for every threshold among the geometry sizes (the binary64 kernel is bound by the
-//     FP64 pipe when the batch fills the GPU, so it does not try these);
-//   * every run gets W = 2, 4 or 8 warps (W <= wpb): a batch of few long chains, down to a single
-//     run, then spreads over up to 256 chunks instead of idling the rest of the GPU.
-// Slots are run * kSlotW + sub (sub = warp of the run), -1 when empty; the warps of a run are
-// adjacent in one block. Returns the slots (a multiple of wpb) and, per geometry, the warps per run.
-std::vector<int> schedule_runs(const std::vector<int>& gsize, const int* ops_index, int nruns, int P, int wpb,
-                               int resident, bool allow_pairs, std::vector<int>& gwarps) {
+// Schedule of the persistent launch: the runs are packed lane by lane into groups of `lpb` lanes (one block
+// each). Every geometry gets the K chunks that give its runs about the same rows per lane, mt, so that all
+// lanes of the launch take about the same time per step; the runs then go, largest K first and the runs of
+// one geometry together (they share their band arrays), into the first group with room (first-fit
+// decreasing). mt starts at the batch's rows over all resident lanes and grows until the groups fit the
+// resident blocks (one round); a batch with more runs than resident lanes runs its groups in several
+// rounds. Returns the lane map (groups x lpb; run << 8 | lane of the run, or -1) and each geometry's K.
+struct Packing {
+  std::vector<int> lanes;
+  int ngroups = 0;
+  std::vector<int> gK;
+};
+
+Packing pack_runs(const std::vector<int>& gsize, const int* ops_index, int nruns, int P, int lpb, int resident) {
   const int nops = (int)gsize.size();
-  std::vector<int> thr_list = {INT32_MAX};
-  if (wpb >= 2 && allow_pairs)
-    for (int gi = 0; gi < nops; ++gi) thr_list.push_back(gsize[gi]);
-  std::sort(thr_list.begin(), thr_list.end());
-  thr_list.erase(std::unique(thr_list.begin(), thr_list.end()), thr_list.end());
-  // candidates: (threshold, 0) = two warps for geometries above the threshold; (0, W) = W warps for
-  // every run (W = 2, 4, 8 up to the block's slots), which is what a few long chains need
-  std::vector<std::pair<int, int>> cand;
-  for (int t : thr_list) cand.push_back({t, 0});
-  for (int W = 2; W <= std::min(kSlotW, wpb); W *= 2) cand.push_back({0, W});
-  double best = 1e300;
-  std::vector<int> best_slots;
-  std::vector<int> best_w(nops, 1);
-  std::vector<int> w(nops);
-  std::vector<double> cost(nops);
+  long long total = 0;
+  int nmax = 1;
+  for (int r = 0; r < nruns; ++r) total += gsize[ops_index[r]];
+  for (int g = 0; g < nops; ++g) nmax = std::max(nmax, gsize[g]);
+  const long long slots = (long long)std::max(1, resident) * lpb;
+  int mt = std::max(2 * P + 1, (int)((total + slots - 1) / slots));
+  Packing pk;
   std::vector<int> order(nruns);
-  for (const auto& cw : cand) {
-    const int thr = cw.first, uniform = cw.second;
-    for (int gi = 0; gi < nops; ++gi) {
-      w[gi] = uniform ? uniform : ((gsize[gi] > thr && wpb >= 2) ? 2 : 1);
-      const Chunking c = chunking(gsize[gi], P, w[gi]);
-      cost[gi] = c.m + 0.05 * c.K;
-    }
+  for (;;) {
+    std::vector<int> gK(nops);
+    for (int g = 0; g < nops; ++g) gK[g] = chunks_for(gsize[g], P, mt, lpb);
     for (int r = 0; r < nruns; ++r) order[r] = r;
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int x, int y) { return cost[ops_index[x]] > cost[ops_index[y]]; });
-    // pack into blocks in that order; a multi-warp run that does not fit in the current block's
-    // remaining slots is preceded by the next one-warp run (or empty slots)
-    std::vector<int> slots;
-    std::vector<double> btime;
-    std::vector<char> used(nruns, 0);
-    size_t next = 0;
-    int fill = 0;
-    double bt = 0.0;
-    auto close_block = [&]() {
-      while (fill < wpb) {
-        slots.push_back(-1);
-        ++fill;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+      const int kx = gK[ops_index[x]], ky = gK[ops_index[y]];
+      return kx != ky ? kx > ky : ops_index[x] < ops_index[y];
+    });
+    std::vector<int> fill;
+    std::vector<std::vector<int>> members;
+    for (int r : order) {
+      const int K = gK[ops_index[r]];
+      size_t b = 0;
+      while (b < fill.size() && fill[b] + K > lpb) ++b;
+      if (b == fill.size()) {
+        fill.push_back(0);
+        members.emplace_back();
       }
-      btime.push_back(bt);
-      fill = 0;
-      bt = 0.0;
-    };
-    for (;;) {
-      while (next < order.size() && used[order[next]]) ++next;
-      if (next >= order.size()) break;
-      const int r = order[next];
-      const int rw = w[ops_index[r]];
-      if (rw > wpb - fill) {  // fill the last slot with a one-warp run if one is left
-        size_t j = next + 1;
-        while (j < order.size() && (used[order[j]] || w[ops_index[order[j]]] != 1)) ++j;
-        if (j < order.size()) {
-          const int r1 = order[j];
-          used[r1] = 1;
-          slots.push_back(kSlotW * r1);
-          bt = std::max(bt, cost[ops_index[r1]]);
-          ++fill;
-        }
-        close_block();
-        continue;
+      fill[b] += K;
+      members[b].push_back(r);
+    }
+    if ((int)fill.size() <= resident || mt >= nmax) {
+      pk.gK = gK;
+      pk.ngroups = (int)fill.size();
+      pk.lanes.assign((size_t)pk.ngroups * lpb, -1);
+      for (int b = 0; b < pk.ngroups; ++b) {
+        int j = 0;
+        for (int r : members[b])
+          for (int k = 0; k < gK[ops_index[r]]; ++k) pk.lanes[(size_t)b * lpb + j++] = (r << 8) | k;
       }
-      used[r] = 1;
-      for (int q = 0; q < rw; ++q) slots.push_back(kSlotW * r + q);
-      bt = std::max(bt, cost[ops_index[r]]);
-      fill += rw;
-      if (fill == wpb) close_block();
+      return pk;
     }
-    if (fill > 0) close_block();
-    // list schedule of the blocks over the resident block slots
-    std::vector<double> fin(std::min<size_t>(std::max(1, resident), btime.size()), 0.0);
-    for (size_t q = 0; q < btime.size(); ++q) {
-      auto it = std::min_element(fin.begin(), fin.end());
-      *it += btime[q];
-    }
-    const double mk = fin.empty() ? 0.0 : *std::max_element(fin.begin(), fin.end());
-    if (mk < best * (1.0 - 1e-9)) {
-      best = mk;
-      best_slots = slots;
-      best_w = w;
-    }
+    mt += std::max(1, mt / 32);
   }
-  gwarps = best_w;
-  return best_slots;
 }
 
 }  // namespace
@@ -1377,12 +1396,12 @@ struct tdz_batch {
   GeomDev* d_geoms = nullptr;
   RunDev* d_runs = nullptr;
   std::vector<RunDev> h_runs;
-  int* d_order = nullptr;  // schedule slots: run * 2 + sub, or -1
+  int* d_lanes = nullptr;  // lane map of the launch's groups (pack_runs)
   long long* d_off = nullptr;  // first coefficient of every run in a concatenated state vector
   std::vector<long long> h_off;
   double* d_stage = nullptr;   // staging for a host-side concatenated state (allocated on first use)
   int* d_bad = nullptr;
-  int nslots = 0;
+  int ngroups = 0;
   int* d_counter = nullptr;
   double* d_obs = nullptr;
   size_t obs_steps = 0;
@@ -1391,7 +1410,7 @@ struct tdz_batch {
   long long last_nsteps = 0;
   int64_t total_dof = 0;
   size_t dev_bytes = 0;
-  int warps_per_block = 4;
+  int lanes_per_block = 256;
   int blocks = 0;
   bool cap = false;  // some geometry has an absorbing layer: every run takes the kernel with the W band
   // total dipole velocity per step (TDZ_OPT_CURRENT): velocity bands uploaded on first use, per-step buffer
@@ -1425,10 +1444,10 @@ namespace {
 
 template <int P, bool M, bool CAP>
 cudaError_t launch_p(tdz_batch* b, const StepArgs& a) {
-  const size_t sm = smem_per_warp(P, M) * b->warps_per_block;
+  const size_t sm = block_smem(P, M, b->lanes_per_block);
   cudaError_t e = ensure_smem<P, M, CAP>(sm);
   if (e != cudaSuccess) return e;
-  cn1d_kernel<P, M, CAP><<<b->blocks, 32 * b->warps_per_block, sm, b->stream>>>(a);
+  cn1d_kernel<P, M, CAP><<<b->blocks, b->lanes_per_block, sm, b->stream>>>(a);
   return cudaGetLastError();
 }
 
@@ -1513,21 +1532,22 @@ int tdz_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* 
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  const size_t spw = smem_per_warp(P, mixed);
-  const int wpb = (int)std::min<size_t>(8, std::max<size_t>(1, (size_t)maxsm / spw));
-  const int per_sm = std::max(1, (int)((size_t)228 * 1024 / (spw * wpb + 1024)));
+  const int wpb = max_warps(P, mixed, maxsm);
+  const int lpb = 32 * wpb;
+  // blocks resident per SM: shared memory (228 KB per SM, 1 KB reserved per block) and registers (the
+  // kernels are built for at most 255 per thread)
+  const int per_sm = std::max(1, std::min((int)((size_t)228 * 1024 / (block_smem(P, mixed, lpb) + 1024)),
+                                          65536 / (256 * lpb)));
   std::vector<int> gsize(nops);
   for (int gi = 0; gi < nops; ++gi) gsize[gi] = (int)ops[gi]->o.n[0];
-  std::vector<int> gwarps;
-  std::vector<int> slots = schedule_runs(gsize, ops_index, nruns, P, wpb, sms * per_sm, mixed, gwarps);
+  const Packing pk = pack_runs(gsize, ops_index, nruns, P, lpb, sms * per_sm);
   // ---------------------------------------------------------------- geometries
   std::vector<GeomDev> hg(nops);
   b->geo.resize(nops);
   for (int gi = 0; gi < nops; ++gi) {
     const Ops& o = ops[gi]->o;
     const int n = (int)o.n[0];
-    const Chunking ch = chunking(n, P, gwarps[gi]);
-    const int K = ch.K, m = ch.m, LS = ch.ks;
+    const int K = pk.gK[gi], m = (n + K - 1) / K, LS = K;
     b->geo[gi] = {n, m, K, LS};
     const size_t nb = (size_t)m * P1 * LS;
     const Band* src[6] = {&o.S, &o.H0, &o.D, &o.G, &o.K, &o.W};
@@ -1635,14 +1655,14 @@ int tdz_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* 
   }
   b->d_geoms = static_cast<GeomDev*>(b->alloc(sizeof(GeomDev) * nops));
   b->d_runs = static_cast<RunDev*>(b->alloc(sizeof(RunDev) * nruns));
-  b->nslots = (int)slots.size();
-  b->d_order = static_cast<int*>(b->alloc(sizeof(int) * slots.size()));
+  b->ngroups = pk.ngroups;
+  b->d_lanes = static_cast<int*>(b->alloc(sizeof(int) * pk.lanes.size()));
   b->d_counter = static_cast<int*>(b->alloc(sizeof(int)));
   b->d_off = static_cast<long long*>(b->alloc(sizeof(long long) * (nruns + 1)));
   b->d_bad = static_cast<int*>(b->alloc(sizeof(int)));
   b->h_off.assign(nruns + 1, 0);
   for (int r = 0; r < nruns; ++r) b->h_off[r + 1] = b->h_off[r] + b->geo[ops_index[r]].n;
-  if (!b->d_geoms || !b->d_runs || !b->d_order || !b->d_counter || !b->d_off || !b->d_bad) {
+  if (!b->d_geoms || !b->d_runs || !b->d_lanes || !b->d_counter || !b->d_off || !b->d_bad) {
     delete b;
     return TDZ_ENOMEM;
   }
@@ -1650,15 +1670,15 @@ int tdz_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* 
   b->h_geoms = hg;
   for (int g = 0; g < nops; ++g) b->ops_of.push_back(&ops[g]->o);
   cudaMemcpyAsync(b->d_runs, b->h_runs.data(), sizeof(RunDev) * nruns, cudaMemcpyHostToDevice, b->stream);
-  cudaMemcpyAsync(b->d_order, slots.data(), sizeof(int) * slots.size(), cudaMemcpyHostToDevice, b->stream);
+  cudaMemcpyAsync(b->d_lanes, pk.lanes.data(), sizeof(int) * pk.lanes.size(), cudaMemcpyHostToDevice, b->stream);
   cudaMemcpyAsync(b->d_off, b->h_off.data(), sizeof(long long) * (nruns + 1), cudaMemcpyHostToDevice, b->stream);
   cudaError_t e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) {
     delete b;
     return cuda_fail(e, "tdz_batch_create");
   }
-  b->warps_per_block = wpb;
-  b->blocks = std::max(1, std::min(b->nslots / wpb, sms * per_sm));
+  b->lanes_per_block = lpb;
+  b->blocks = std::max(1, std::min(b->ngroups, sms * per_sm));
   *out = b;
   return TDZ_OK;
 }
@@ -1834,8 +1854,8 @@ int tdz_propagate(tdz_batch* b, const double* field, double dt, int64_t step0, i
   StepArgs a;
   a.geoms = b->d_geoms;
   a.runs = b->d_runs;
-  a.order = b->d_order;
-  a.nruns = b->nslots;
+  a.lanes = b->d_lanes;
+  a.ngroups = b->ngroups;
   a.counter = b->d_counter;
   a.field = dfield;
   a.obs = b->d_obs;
@@ -2102,7 +2122,7 @@ __global__ void noalloc_pack(double* scr, NoAllocLayout L, const double* bands, 
   if (tid == 0) {
     GeomDev* G = reinterpret_cast<GeomDev*>(scr + L.desc);
     RunDev* R = reinterpret_cast<RunDev*>(G + 1);
-    int* order = reinterpret_cast<int*>(R + 1);
+    int* lanes = reinterpret_cast<int*>(R + 1);
     const size_t nb = rows * P1;
     *G = GeomDev{L.n, L.m, L.K, LANES, scr + L.band, scr + L.band + nb, scr + L.band + 2 * nb, scr + L.band + 3 * nb,
                  scr + L.band + 4 * nb, nullptr, nullptr};
@@ -2116,8 +2136,8 @@ __global__ void noalloc_pack(double* scr, NoAllocLayout L, const double* bands, 
     r.gd = scr + L.gd;
     r.dl = scr + L.dl;
     *R = r;
-    order[0] = 0;
-    order[1] = 0;  // work counter
+    for (int k = 0; k < LANES; ++k) lanes[k] = k < L.K ? k : -1;  // run 0, lane k (one warp)
+    lanes[LANES] = 0;                                             // work counter
   }
 }
 
@@ -2135,10 +2155,10 @@ static std::mutex g_noalloc_mu;
 
 template <int P>
 cudaError_t noalloc_launch(cudaStream_t st, const StepArgs& a) {
-  const size_t sm = smem_per_warp(P, false);
+  const size_t sm = block_smem(P, false, LANES);
   cudaError_t e = ensure_smem<P, false, false>(sm);
   if (e != cudaSuccess) return e;
-  cn1d_kernel<P, false, false><<<1, 32, sm, st>>>(a);
+  cn1d_kernel<P, false, false><<<1, LANES, sm, st>>>(a);
   return cudaGetLastError();
 }
 }  // namespace tdz
@@ -2210,13 +2230,13 @@ extern "C" int tdz_cn1d_propagate_noalloc(const double* bands, int64_t n, int de
   if (e != cudaSuccess) return cuda_fail(e, "tdz_cn1d_propagate_noalloc: pack");
   GeomDev* G = reinterpret_cast<GeomDev*>(scr + L.desc);
   RunDev* R = reinterpret_cast<RunDev*>(G + 1);
-  int* order = reinterpret_cast<int*>(R + 1);
+  int* lanes = reinterpret_cast<int*>(R + 1);
   StepArgs a;
   a.geoms = G;
   a.runs = R;
-  a.order = order;
-  a.nruns = 1;
-  a.counter = order + 1;
+  a.lanes = lanes;
+  a.ngroups = 1;
+  a.counter = lanes + LANES;
   a.field = field;
   a.obs = obs;
   a.cur = nullptr;
