@@ -46,11 +46,10 @@ sys.path.insert(0, ROOT)
 
 import workloads as wl  # noqa: E402
 
-# DRAM bytes (read + write) per coefficient-step of the mixed 1-D kernel, from one ncu capture of
-# this kernel version on the DQW batch (dram__bytes 826.27 GB/s over the 3.469 ms warm-up launch:
-# 2.867 GB for 3 steps of 1 873 260 coefficients); the traffic of a timed launch is this times its
-# coefficient-steps.
-NCU_DRAM_BYTES_PER_COEFF_STEP = 510.1
+# DRAM bytes (read + write) per coefficient-step of the mixed 1-D kernel, from one ncu capture of the
+# current kernel version on the DQW batch (None until captured for this version); the traffic of a timed
+# launch is this times its coefficient-steps.
+NCU_DRAM_BYTES_PER_COEFF_STEP = None
 METRIC = "TDSE coefficient-updates/s: batched mixed vs plain FP64 at stated HHG/norm error"
 UNIT = "coefficient-updates/s"
 
@@ -591,7 +590,8 @@ def main():
             "gpu_launches": 1,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
                          "frac": achieved / peak_fp32,
-                         "traffic": NCU_DRAM_BYTES_PER_COEFF_STEP * dof * args.steps,
+                         "traffic": (NCU_DRAM_BYTES_PER_COEFF_STEP * dof * args.steps
+                                     if NCU_DRAM_BYTES_PER_COEFF_STEP else None),
                          "note": ("achieved: algorithmic flops per coefficient-step x coefficient-steps of the timed "
                                   "launch / its event time; peak: 148 SM x 128 FP32 lanes x 2 flop x 2.032 GHz (unit "
                                   "counts and max clock); traffic: DRAM bytes of the timed launch (ncu bytes per "
@@ -603,6 +603,9 @@ def main():
             "e2e": {"value": dof_all * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "clocks": clk.summary()}
+    r32, r64 = tdz.device_rates()
+    line["device_rates"] = {"fp32_fma_tflops": r32 / 1e12, "fp64_fma_tflops": r64 / 1e12, "ratio": r32 / r64,
+                            "how": "tdz_device_rates: 8 independent FMA chains per thread, 8 x 256 threads per SM"}
     # ---------------- 2-D leg: the soft-core atom of the 2-D configuration (1024 x 1024 order-7 splines),
     # a few steps in both precisions (Kronecker + Gauss-point operator, preconditioned COCG)
     if rank == 0 and args.h2p_steps > 0:

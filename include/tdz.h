@@ -148,6 +148,31 @@ void tdz_ops_destroy(tdz_ops* ops);
  * Errors: TDZ_EINVAL (null pointers, nstates < 1, a 2-D/3-D operator), TDZ_ENOCONV. */
 int  tdz_pdm_acceleration(const tdz_ops* ops, const double* c, int64_t nstates, double* aq);
 
+/* tdz_lowest_states: the nstates lowest eigenpairs of H0 c = eps S c (Eq. gen_ev) of nops 1-D geometries
+ * (one degree) at once on the GPU: subspace inverse iteration with nstates + 2 vectors, a shift below the
+ * spectrum (H0 - sigma S positive definite, factored once per geometry) and Rayleigh-Ritz in binary64, one
+ * warp per geometry; stops when every wanted pair has ||H0 c - eps S c|| <= 1e-11 ||eps S c||.
+ *   energies : host [nops][nstates], ascending per geometry.
+ *   states   : host, geometry after geometry, [nstates][2 n_g] interleaved complex (real-valued,
+ *              S-normalised, largest component positive: Sec. "Wavefunction realignment").
+ *   residuals: host [nops][nstates] relative residuals (may be NULL); iterations: host [nops] (may be NULL).
+ *   cuda_stream: the stream of the work (NULL: legacy default); the call synchronises it.
+ * Errors: TDZ_EINVAL (nstates outside 1..6, a 2-D/3-D operator, mixed degrees, fewer than nstates + 2
+ * coefficients), TDZ_EUNSUPPORTED (degree > 8), TDZ_ENOCONV (some geometry did not converge within 2000
+ * iterations; its best pairs are still returned), TDZ_ECUDA. */
+int  tdz_lowest_states(const tdz_ops* const* ops, int nops, int nstates, double* energies, double* states,
+                       double* residuals, int* iterations, void* cuda_stream);
+
+/* tdz_populations: projections of nstates 1-D states c[nstates][2n] on nev field-free eigenstates
+ * phi[nev][2n] (S-orthonormal, e.g. from tdz_lowest_states), Sec. "Currents and coherence dynamics":
+ *   pop [nstates][nev] (may be NULL): |c_n|^2 with c_n = phi_n^H S c;
+ *   jdec[nstates][4]   (may be NULL): J_tot = c^H Vel c, J_intra = sum_n |c_n|^2 v_nn, J_inter =
+ *        sum_{m != n} conj(c_m) c_n v_mn (v_mn = phi_m^H Vel phi_n) and J_bc = J_tot - J_intra - J_inter
+ *        (Eqs. Jdecomp-Jbc); for real eigenstates v_nn = 0, so J_intra = 0.
+ * Host arrays, binary64 host arithmetic. Errors: TDZ_EINVAL. */
+int  tdz_populations(const tdz_ops* ops, const double* phi, int nev, const double* c, int64_t nstates, double* pop,
+                     double* jdec);
+
 /* Ground state of H0 c = eps S c (Eq. gen_ev) by shifted inverse iteration on
  * the host (1-D). Output: *energy and c[2n] (interleaved complex, real-valued,
  * S-normalised, largest component positive: Sec. "Wavefunction realignment").
@@ -292,6 +317,13 @@ int  tdz_spectrum(const double* signal, int64_t nsig, int64_t nt, int64_t sig_st
                   double beta, int length_form, double w_lo, double dw, int64_t nw, double* S, void* cuda_stream);
 int  tdz_harmonic_yields(const double* S, int64_t nsig, double w_lo, double dw, int64_t nw, double omega0, int qmax,
                          double* Y);
+
+/* ------------------------------------------------------------------ device rates
+ * tdz_device_rates: the FP32 and binary64 fused multiply-add throughput of the current device in flop/s
+ * (eight independent FMA chains per thread, 8 blocks of 256 threads per SM, CUDA events, best of three
+ * timed launches). The ratio is what makes the mixed path form its binary64-class residuals in
+ * double-float on B300. No counterpart in the paper. Errors: TDZ_EINVAL, TDZ_ECUDA. */
+int  tdz_device_rates(double* fp32_flops, double* fp64_flops);
 
 /* ------------------------------------------------------------------ allocation-free entry point
  * tdz_cn1d_propagate_noalloc: the binary64 1-D propagation of tdz_propagate for ONE run, for

@@ -76,6 +76,9 @@ _sig = {
     "tdz_batch_tuning": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int), _dp]),
     "tdz_batch_destroy": (None, [_vp]),
     "tdz_observe_current": (C.c_int, [_vp, C.c_int, _vp]),
+    "tdz_lowest_states": (C.c_int, [C.POINTER(_vp), C.c_int, C.c_int, _dp, _dp, _dp, C.POINTER(C.c_int), _vp]),
+    "tdz_populations": (C.c_int, [_vp, _dp, C.c_int, _dp, C.c_int64, _dp, _dp]),
+    "tdz_device_rates": (C.c_int, [_dp, _dp]),
     "tdz_pdm_acceleration": (C.c_int, [_vp, _dp, C.c_int64, _dp]),
     "tdz_spectrum": (C.c_int, [_vp, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_double, C.c_double, C.c_int,
                                C.c_double, C.c_double, C.c_int64, _vp, _vp]),
@@ -218,6 +221,19 @@ class Ops:
         _check(_lib.tdz_pdm_acceleration(self._h, _dptr(buf), c.shape[0], _dptr(out)), "tdz_pdm_acceleration")
         return out
 
+    def populations(self, phi, states):
+        """Projections on field-free eigenstates phi [nev, n] of states [nstates, n] (tdz_populations):
+        returns (populations [nstates, nev], currents [nstates, 4] = J_tot, J_intra, J_inter, J_bc)."""
+        def pack(z):
+            z = np.atleast_2d(np.asarray(z, dtype=np.complex128))
+            return np.ascontiguousarray(np.stack([z.real, z.imag], axis=2).reshape(-1)), z.shape[0]
+        pb, nev = pack(phi)
+        cb, ns = pack(states)
+        pop = np.zeros((ns, nev))
+        jd = np.zeros((ns, 4))
+        _check(_lib.tdz_populations(self._h, _dptr(pb), nev, _dptr(cb), ns, _dptr(pop), _dptr(jd)), "tdz_populations")
+        return pop, jd
+
     def ground_state(self):
         e = C.c_double()
         c = np.zeros(2 * self.n)
@@ -228,6 +244,33 @@ class Ops:
         if getattr(self, "_h", None):
             _lib.tdz_ops_destroy(self._h)
             self._h = None
+
+
+def device_rates():
+    """FP32 and binary64 FMA throughput of the current device in flop/s (tdz_device_rates)."""
+    a, b = C.c_double(), C.c_double()
+    _check(_lib.tdz_device_rates(C.byref(a), C.byref(b)), "tdz_device_rates")
+    return a.value, b.value
+
+
+def lowest_states(ops: Sequence["Ops"], nstates: int = 1, stream: Optional[int] = None):
+    """The nstates lowest eigenpairs of H0 c = eps S c of several 1-D geometries at once on the GPU
+    (tdz_lowest_states). Returns (energies [nops, nstates], list of state arrays [nstates, n_g] complex,
+    residuals [nops, nstates], iterations [nops])."""
+    arr = (_vp * len(ops))(*[o._h for o in ops])
+    sizes = [o.n for o in ops]
+    en = np.zeros((len(ops), nstates))
+    res = np.zeros((len(ops), nstates))
+    st = np.zeros(2 * nstates * sum(sizes))
+    its = (C.c_int * len(ops))()
+    _check(_lib.tdz_lowest_states(arr, len(ops), int(nstates), _dptr(en), _dptr(st), _dptr(res), its, _vp(stream or 0)),
+           "tdz_lowest_states")
+    out, o = [], 0
+    for n in sizes:
+        blk = st[o:o + 2 * n * nstates].reshape(nstates, n, 2)
+        out.append(blk[:, :, 0] + 1j * blk[:, :, 1])
+        o += 2 * n * nstates
+    return en, out, res, np.array(list(its))
 
 
 def assemble_1d(knots, degree: int, medium: Dict, nquad: Optional[int] = None) -> Ops:

@@ -1532,15 +1532,18 @@ int tdz_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* 
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  const int wpb = max_warps(P, mixed, maxsm);
-  const int lpb = 32 * wpb;
   // blocks resident per SM: shared memory (228 KB per SM, 1 KB reserved per block) and registers (the
   // kernels are built for at most 255 per thread)
-  const int per_sm = std::max(1, std::min((int)((size_t)228 * 1024 / (block_smem(P, mixed, lpb) + 1024)),
-                                          65536 / (256 * lpb)));
+  auto resident_per_sm = [&](int lanes) {
+    return std::max(1, std::min((int)((size_t)228 * 1024 / (block_smem(P, mixed, lanes) + 1024)),
+                                65536 / (256 * lanes)));
+  };
+  const int lpb = 32 * max_warps(P, mixed, maxsm);
+  const int per_sm = resident_per_sm(lpb);
   std::vector<int> gsize(nops);
   for (int gi = 0; gi < nops; ++gi) gsize[gi] = (int)ops[gi]->o.n[0];
   const Packing pk = pack_runs(gsize, ops_index, nruns, P, lpb, sms * per_sm);
+
   // ---------------------------------------------------------------- geometries
   std::vector<GeomDev> hg(nops);
   b->geo.resize(nops);

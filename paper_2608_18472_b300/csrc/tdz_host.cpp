@@ -9,6 +9,7 @@
 //   Eq. gen_ev                ground state for the initial condition
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -665,6 +666,86 @@ extern "C" int tdz_pdm_acceleration(const tdz_ops* ops, const double* c, int64_t
     double zi = 0.0;
     for (int64_t i = 0; i < n; ++i) zi += tr[i] * vi[i] - ti[i] * vr[i];
     aq[s] = -2.0 * zi;
+  }
+  return TDZ_OK;
+}
+
+// ----------------------------------------------------------------------------- populations and currents
+// Projections of 1-D states on nev field-free eigenstates phi_n (Sec. "Currents and coherence dynamics"):
+// c_n = phi_n^H S c, the populations |c_n|^2, and the decomposition of the total dipole velocity
+// J_tot = c^H Vel c into J_intra = sum_n |c_n|^2 v_nn, J_inter = sum_{m != n} conj(c_m) c_n v_mn (v_mn =
+// phi_m^H Vel phi_n, Vel = -(i/2) M) and the remainder J_bc = J_tot - J_intra - J_inter (Eqs.
+// Jdecomp-Jbc).
+extern "C" int tdz_populations(const tdz_ops* ops, const double* phi, int nev, const double* c, int64_t nstates,
+                               double* pop, double* jdec) {
+  if (!ops || !phi || !c || nev < 1 || nstates < 1 || ops->o.dim != 1 || (!pop && !jdec)) return TDZ_EINVAL;
+  const Ops& o = ops->o;
+  const int64_t n = o.S.n;
+  const int p = o.S.p, P1 = p + 1;
+  using cd = std::complex<double>;
+  auto load = [&](const double* x, std::vector<cd>& v) {
+    v.resize(n);
+    for (int64_t i = 0; i < n; ++i) v[i] = cd(x[2 * i], x[2 * i + 1]);
+  };
+  auto band = [&](const Band& B, const std::vector<cd>& x, std::vector<cd>& y) {  // symmetric band
+    y.assign(n, cd(0.0, 0.0));
+    for (int64_t i = 0; i < n; ++i) {
+      cd s = B.at(i, 0) * x[i];
+      for (int d = 1; d <= p; ++d) {
+        if (i - d >= 0) s += B.at(i, d) * x[i - d];
+        if (i + d < n) s += B.at(i + d, d) * x[i + d];
+      }
+      y[i] = s;
+    }
+  };
+  auto vel = [&](const std::vector<cd>& x, std::vector<cd>& y) {  // Vel x = -(i/2) M x, M antisymmetric
+    y.assign(n, cd(0.0, 0.0));
+    for (int64_t i = 0; i < n; ++i) {
+      cd s(0.0, 0.0);
+      for (int d = 1; d <= p; ++d) {
+        if (i - d >= 0) s += o.M.a[(size_t)i * P1 + d] * x[i - d];
+        if (i + d < n) s -= o.M.a[(size_t)(i + d) * P1 + d] * x[i + d];
+      }
+      y[i] = cd(0.0, -0.5) * s;
+    }
+  };
+  auto dotc = [&](const std::vector<cd>& a, const std::vector<cd>& b) {
+    cd s(0.0, 0.0);
+    for (int64_t i = 0; i < n; ++i) s += std::conj(a[i]) * b[i];
+    return s;
+  };
+  std::vector<std::vector<cd>> ph(nev), vph(nev);
+  for (int k = 0; k < nev; ++k) {
+    load(phi + 2 * n * k, ph[k]);
+    vel(ph[k], vph[k]);
+  }
+  std::vector<cd> vmn((size_t)nev * nev);
+  for (int m = 0; m < nev; ++m)
+    for (int k = 0; k < nev; ++k) vmn[(size_t)m * nev + k] = dotc(ph[m], vph[k]);
+  std::vector<cd> x, sx, vx;
+  std::vector<cd> cn(nev);
+  for (int64_t s = 0; s < nstates; ++s) {
+    load(c + 2 * n * s, x);
+    band(o.S, x, sx);
+    for (int k = 0; k < nev; ++k) {
+      cn[k] = dotc(ph[k], sx);
+      if (pop) pop[s * nev + k] = std::norm(cn[k]);
+    }
+    if (jdec) {
+      vel(x, vx);
+      const double jt = std::real(dotc(x, vx));
+      double ji = 0.0, je = 0.0;
+      for (int m = 0; m < nev; ++m)
+        for (int k = 0; k < nev; ++k) {
+          const double t = std::real(std::conj(cn[m]) * cn[k] * vmn[(size_t)m * nev + k]);
+          if (m == k) ji += t;
+          else je += t;
+        }
+      jdec[4 * s + 0] = jt;
+      jdec[4 * s + 1] = ji;
+      jdec[4 * s + 2] = je;
+      jdec[4 * s + 3] = jt - ji - je;
+    }
   }
   return TDZ_OK;
 }

@@ -62,18 +62,22 @@ struct AxisDev {
   const float *lB, *lx, *lw;
   // double-float copies of every table (the binary64-class residual of the mixed path)
   const tdz::fx *xB, *xdB, *xx, *xw, *xS, *xT1, *xD;
+  // the absorbing layer's axis factor W_a = <B|eta_a|B> (lower band, as S) in the three precisions, or null
+  const double* Wc;
+  const float* fWc;
+  const tdz::fx* xWc;
 };
 template <class T> __host__ __device__ inline const T* tab(const AxisDev& A, int which);
 template <> __host__ __device__ inline const double* tab<double>(const AxisDev& A, int which) {
-  switch (which) { case 0: return A.B; case 1: return A.dB; case 2: return A.x; case 3: return A.w; case 4: return A.S; case 5: return A.T1; default: return A.D; }
+  switch (which) { case 0: return A.B; case 1: return A.dB; case 2: return A.x; case 3: return A.w; case 4: return A.S; case 5: return A.T1; case 7: return A.Wc; default: return A.D; }
 }
 template <> __host__ __device__ inline const tdz::fx* tab<tdz::fx>(const AxisDev& A, int which) {
-  switch (which) { case 0: return A.xB; case 1: return A.xdB; case 2: return A.xx; case 3: return A.xw; case 4: return A.xS; case 5: return A.xT1; default: return A.xD; }
+  switch (which) { case 0: return A.xB; case 1: return A.xdB; case 2: return A.xx; case 3: return A.xw; case 4: return A.xS; case 5: return A.xT1; case 7: return A.xWc; default: return A.xD; }
 }
 template <> __host__ __device__ inline const float* tab<float>(const AxisDev& A, int which) {
-  switch (which) { case 0: return A.fB; case 1: return A.fdB; case 2: return A.fx; case 3: return A.fw; case 4: return A.fS; case 5: return A.fT1; default: return A.fD; }
+  switch (which) { case 0: return A.fB; case 1: return A.fdB; case 2: return A.fx; case 3: return A.fw; case 4: return A.fS; case 5: return A.fT1; case 7: return A.fWc; default: return A.fD; }
 }
-enum { TB = 0, TDB = 1, TX = 2, TW = 3, TS = 4, TT1 = 5, TD = 6 };
+enum { TB = 0, TDB = 1, TX = 2, TW = 3, TS = 4, TT1 = 5, TD = 6, TCAP = 7 };
 
 struct MediumDev {
   int mass_kind, pot_kind;
@@ -226,11 +230,13 @@ __global__ void k_axis_band(BandTerms<T> bt, const C<T>* __restrict__ in0, const
   }
 }
 
-// one axis pass with bt.nt (1 or 3) terms
+// one axis pass with bt.nt (1, 3 or 4) terms
 template <class T, int P>
 void launch_axis_band(cudaStream_t st, int blocks, const BandTerms<T>& bt, const C<T>* in0, const C<T>* in1,
                       C<T>* out, long long outer, int L, long long inner) {
-  if (bt.nt == 3)
+  if (bt.nt == 4)
+    k_axis_band<T, P, 4><<<blocks, 256, 0, st>>>(bt, in0, in1, out, outer, L, inner, 0);
+  else if (bt.nt == 3)
     k_axis_band<T, P, 3><<<blocks, 256, 0, st>>>(bt, in0, in1, out, outer, L, inner, 0);
   else
     k_axis_band<T, P, 1><<<blocks, 256, 0, st>>>(bt, in0, in1, out, outer, L, inner, 0);
@@ -1361,6 +1367,7 @@ struct NdRun {
   MediumDev med;
   int geo = 0;          // index of the geometry tables (fast diagonalisation, stencil)
   bool const_mass = true;
+  bool cap = false;     // the geometry has an absorbing layer (tau W_a terms in the Kronecker pass)
   double cm = 1.0;      // m^-1 for constant mass
   double mbar = 1.0;    // mean m^-1 for the preconditioner
   double2* c = nullptr;  // state, binary64
@@ -1523,7 +1530,7 @@ int autotune_apply2d(NdBatch* b) {
         r = &run;
         break;
       }
-    if (!G.W32 || !r) continue;
+    if (!G.W32 || !r || r->cap) continue;  // an absorbing layer takes the unfused apply
     const C<float>* x = static_cast<const C<float>*>(b->w_p);
     C<float>* y = static_cast<C<float>*>(b->w_q);
     for (int c = 0; c < 2; ++c) {
@@ -1590,7 +1597,8 @@ struct Apply {
 
   // out = sum over Kronecker terms: factors per axis f[a] applied to input; generic two-stream scheme
   // out = [S_z] [S_y] (S_x + i tau K_x) x + i tau [S_z] K_y S_x x + i tau K_z S_y S_x x   (3-D)
-  // with K_a = cm T1_a + Ebar_a D_a. Mode "S only": out = (x)S x. Mode "D_a": D_a on axis a, S elsewhere.
+  // with K_a = cm T1_a + Ebar_a D_a - i W_a (the absorbing layer's axis factor W_a, when present, enters
+  // as the real term tau W_a). Mode "S only": out = (x)S x. Mode "D_a": D_a on axis a, S elsewhere.
   void kron(const C<T>* x, C<T>* out, int mode, double tau, const double* ebar, int daxis = 0) {
     const int D = r->dim;
     int len[3] = {r->n[0], r->n[1], r->n[2]};
@@ -1628,6 +1636,13 @@ struct Apply {
         tb.cr[2] = 0;
         tb.ci[2] = tau * ebar[ax];
         tb.sel[2] = 0;
+        if (r->cap) {
+          tb.nt = 4;
+          tb.R[3] = tab<T>(A, TCAP);
+          tb.cr[3] = tau;
+          tb.ci[3] = 0;
+          tb.sel[3] = 0;
+        }
       } else if (mode == 1) {  // S only
         ta.nt = 1;
         ta.R[0] = tab<T>(A, TS);
@@ -1737,7 +1752,7 @@ struct Apply {
   // y = A_n x
   void apply(const C<T>* x, C<T>* y, double tau, const double* ebar) {
     if constexpr (std::is_same<T, float>::value) {
-      if (Wm && r->dim == 2) {  // FP32 2-D with the stencil: one fused pass (Kronecker terms + W)
+      if (Wm && r->dim == 2 && !r->cap) {  // FP32 2-D with the stencil: one fused pass (Kronecker terms + W)
         apply2d_fused<P>(b, r, Wm, x, y, tau, ebar);
         return;
       }
@@ -2076,7 +2091,9 @@ int propagate_run(NdBatch* b, NdRun* r, const tdz::Ops& o, const double* field, 
                          static_cast<C<float>*>(b->w_qa), static_cast<C<float>*>(b->w_qb)};
     if (stencil) {
       opx.Wm = G.Wx;
-      op32.Wm = G.W32;
+      // the FP32 stencil is stored tile-major for the fused apply, which has no absorbing-layer term; with
+      // a layer the FP32 inner solve applies V and the mass term by quadrature instead (the same operator)
+      op32.Wm = r->cap ? nullptr : G.W32;
     }
     opx.Vtab = G.Vqx;
     op32.Vtab = G.Vq32;
@@ -2468,6 +2485,18 @@ int nd_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* o
       A.xS = upx(o.Sa[a].a);
       A.xT1 = upx(o.T1a[a].a);
       A.xD = upx(o.Da[a].a);
+      A.Wc = nullptr;
+      A.fWc = nullptr;
+      A.xWc = nullptr;
+      if (o.has_cap()) {
+        A.Wc = up(o.Wa[a].a);
+        A.fWc = upf(o.Wa[a].a);
+        A.xWc = upx(o.Wa[a].a);
+        if (!A.Wc || !A.fWc || !A.xWc) {
+          delete b;
+          return TDZ_ENOMEM;
+        }
+      }
       if (!A.B || !A.dB || !A.x || !A.w || !A.S || !A.T1 || !A.D || !A.fB || !A.fdB || !A.fx || !A.fw || !A.fS ||
           !A.fT1 || !A.fD || !A.lB || !A.lx || !A.lw || !A.xB || !A.xdB || !A.xx || !A.xw || !A.xS || !A.xT1 ||
           !A.xD) {
@@ -2505,6 +2534,7 @@ int nd_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* o
     }
     R.med = medium_dev(o.med);
     R.const_mass = o.med.mass_kind == TDZ_MASS_CONST;
+    R.cap = o.has_cap();
     R.cm = R.const_mass ? 1.0 / o.med.mass_par[0] : 0.0;
     R.mbar = R.const_mass ? R.cm : 0.5 * (1.0 / o.med.mass_par[2] + 1.0 / o.med.mass_par[3]);
     R.c = static_cast<double2*>(b->alloc(sizeof(double2) * R.N));

@@ -154,3 +154,30 @@ def test_velocity_band_and_pdm_acceleration_match_oracle(tdz):
         for x, v in zip(states, aq):
             r = propagate.a_quantum(ref, x)
             assert abs(v - r) <= 1e-10 * max(1.0, abs(r)), (v, r)
+
+
+def test_populations_and_current_decomposition(tdz):
+    """tdz_populations against the oracle: the driven oscillator of Appendix A populates its levels as a
+    coherent state (P_n = e^{-|a|^2} |a|^{2n} / n!), and J_tot = J_intra + J_inter + J_bc with J_intra = 0
+    for real eigenstates (Sec. "Currents and coherence dynamics")."""
+    import math
+    from oracle import propagate
+    e0 = 0.1
+    wk = wl.driven_ho_1d(e0=e0, dt=0.01, t_end=6.0, L=20.0, nsplines=200, p=5)
+    r = wk.runs[0]
+    m = assemble.assemble_1d(r.knots, r.degree, r.nquad, r.medium)
+    w, v = eigen.lowest_states(m, 6)
+    c, obs, J = propagate.cn_propagate(m, v[:, 0], r.field, wk.dt, wk.nsteps, currents=True)
+    ops = tdz.assemble_1d(r.knots, r.degree, r.medium, r.nquad)
+    pop, jd = ops.populations(v.T, c)
+    T = obs[-1, 0]
+    a2 = e0 ** 2 / 8 * (T * T + math.sin(T) ** 2 - T * math.sin(2 * T))
+    for k in range(4):
+        assert abs(pop[0, k] - math.exp(-a2) * a2 ** k / math.factorial(k)) < 2e-4
+    ref = np.abs(v.conj().T @ (m["S"] @ c)) ** 2
+    assert np.allclose(pop[0], ref, rtol=0, atol=1e-13)
+    assert abs(jd[0, 0] - J[-1, 0]) < 1e-12
+    assert abs(jd[0, 1]) < 1e-14
+    assert abs(jd[0, 0] - jd[0, 1] - jd[0, 2] - jd[0, 3]) < 1e-14
+    # almost all of the coherent state lives in the six lowest levels: the remainder current is small
+    assert abs(jd[0, 3]) < 1e-3 * abs(jd[0, 0])

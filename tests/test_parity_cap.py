@@ -98,3 +98,52 @@ def test_cap_parameters_are_validated(tdz):
         with pytest.raises(tdz.TDZError) as ei:
             tdz.assemble_1d(t, 4, med, 5)
         assert ei.value.code == tdz.TDZ_EINVAL
+
+
+def _nd_case(dim, kind):
+    if dim == 2:
+        p, L, nspl = 4, 12.0, 28
+    else:
+        p, L, nspl = 3, 9.0, 13
+    t = wl.knots_for_nsplines(-L, L, nspl, p)
+    base = wl.softcore_medium(0.5)
+    if kind == "manolopoulos":
+        med = wl.with_cap(base, "manolopoulos", 0.55 * L, L, m=1.0)
+    else:
+        med = wl.with_cap(base, "poly", 0.55 * L, L, eta0=0.3, k=2.0)
+    return [t] * dim, p, base, med
+
+
+@pytest.mark.parametrize("dim,kind", [(2, "manolopoulos"), (2, "poly"), (3, "manolopoulos")])
+def test_cap_nd_matches_oracle(tdz, dim, kind):
+    """2-D/3-D soft core with an absorbing layer on every axis (eta = sum of the axes' masks, so W = sum_a
+    W_a (x) S (x) S, the separable term tau W_a beside i tau K_a in the Kronecker pass): a strong pulse
+    drives part of the ground state into the layer; final state, norm and dipoles against the oracle for
+    every operator form and preconditioner, both precisions."""
+    knots, p, base, med = _nd_case(dim, kind)
+    dt, nsteps = 0.05, 60 if dim == 2 else 30
+    m = assemble.assemble_nd(knots, [p] * dim, [p + 1] * dim, med)
+    assert abs(m["W"]).max() > 0
+    _, c0 = eigen.ground_state(assemble.assemble_nd(knots, [p] * dim, [p + 1] * dim, base))
+    field = wl.sin2_pulse(wl.time_grid(dt, nsteps), 0.3, 0.6, 1.0, ellipticity=0.3, dim=dim)
+    c, obs = propagate.cn_propagate(m, c0, field, dt, nsteps)
+    assert obs[-1, -1] < obs[0, -1] - 1e-6                      # absorption is visible
+    ops = tdz.Ops([tdz.Basis(k, p, p + 1) for k in knots], med)
+    assert np.max(np.abs(ops.band("W", 0))) > 0
+    combos = [("auto", "auto"), ("quadrature", "lines")] + ([("stencil", "fd")] if dim == 2 else [])
+    for prec, tol in ((tdz.FP64, 1e-9), (tdz.MIXED, 1e-8)):
+        for op, pc in combos:
+            b = tdz.Batch([ops], [0], prec)
+            b.set_option(tdz.OPT_OPERATOR, {"auto": tdz.OPERATOR_AUTO, "quadrature": tdz.OPERATOR_QUADRATURE,
+                                            "stencil": tdz.OPERATOR_STENCIL}[op])
+            b.set_option(tdz.OPT_PRECOND, {"auto": tdz.PRECOND_AUTO, "lines": tdz.PRECOND_LINES, "fd": tdz.PRECOND_FD}[pc])
+            b.set_state(0, c0)
+            b.propagate(field.reshape(1, nsteps + 1, dim), dt, 0, nsteps)
+            og, st = b.observe(0)
+            assert st == tdz.TDZ_OK, (prec, op, pc, st)
+            cg = b.get_state(0)
+            assert np.linalg.norm(cg - c) / np.linalg.norm(c) < tol, (prec, op, pc)
+            assert np.max(np.abs(og[:, -1] - obs[:, -1])) < tol, (prec, op, pc)
+            for col in range(1 + dim, 1 + 2 * dim):
+                assert np.max(np.abs(og[:, col] - obs[:, col])) < 10 * tol * max(1.0, np.max(np.abs(obs[:, col])))
+            del b
