@@ -47,9 +47,10 @@ sys.path.insert(0, ROOT)
 import workloads as wl  # noqa: E402
 
 # DRAM bytes (read + write) per coefficient-step of the mixed 1-D kernel, from one ncu capture of the
-# current kernel version on the DQW batch (None until captured for this version); the traffic of a timed
-# launch is this times its coefficient-steps.
-NCU_DRAM_BYTES_PER_COEFF_STEP = None
+# current (lane-packed) kernel on the DQW batch: 3.3137 GB read + 0.9207 GB written in the 3-step
+# warm-up launch of 1 873 260 coefficients; the traffic of a timed launch is this times its
+# coefficient-steps.
+NCU_DRAM_BYTES_PER_COEFF_STEP = 753.5
 METRIC = "TDSE coefficient-updates/s: batched mixed vs plain FP64 at stated HHG/norm error"
 UNIT = "coefficient-updates/s"
 

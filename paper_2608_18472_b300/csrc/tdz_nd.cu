@@ -481,6 +481,36 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return v;
 }
 
+// Fixed-order grid reduction, so that repeated runs give bitwise equal sums: every block stores its block
+// sums in its own slot of `part`; the last block to arrive (ticket counter) adds the slots in block order -
+// the same order whichever block finishes last - and adds the totals to res[0..NV). Called by every thread
+// of the block, with v holding the block's sums in thread 0.
+struct GridRed {
+  double* part;      // [blocks][4]
+  unsigned* ticket;  // zero between launches (the last block resets it)
+};
+template <int NV>
+__device__ __forceinline__ void grid_reduce(const double (&v)[NV], double* res, GridRed gr, double* sh) {
+  __shared__ int s_last;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) gr.part[(size_t)blockIdx.x * 4 + k] = v[k];
+    __threadfence();
+    s_last = atomicAdd(gr.ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double t = 0.0;
+    for (unsigned q = threadIdx.x; q < gridDim.x; q += blockDim.x) t += __ldcg(gr.part + (size_t)q * 4 + k);
+    t = block_sum(t, sh);
+    if (threadIdx.x == 0) res[k] += t;
+  }
+  if (threadIdx.x == 0) *gr.ticket = 0;
+}
+
 // Medium constants as double-float numbers (prepared on the host once per launch).
 struct MediumFF {
   int mass_kind, pot_kind;
@@ -537,7 +567,7 @@ TDZ_DEV cff to_cff(const C<fx>& v) { return cff{to_ff(v.r), to_ff(v.i)}; }
 
 template <int P, class T>
 __global__ void k_fused_last_reduce_ff(const C<T>* __restrict__ in, AxisDev A0, AxisDev A1, AxisDev AL, int dim,
-                                       long long inner, int echunk, MediumFF M, int kmass, double* res) {
+                                       long long inner, int echunk, MediumFF M, int kmass, double* res, GridRed gr) {
   __shared__ double sh[32];
   const int nL = AL.n, EL = AL.E, nq = AL.nq;
   const int nchunks = (EL + echunk - 1) / echunk;
@@ -602,16 +632,18 @@ __global__ void k_fused_last_reduce_ff(const C<T>* __restrict__ in, AxisDev A0, 
       win[P] = (jn >= 0 && jn < nL && e + 1 < e1) ? to_cff(in[(long long)jn * inner + i]) : cff{{0.f, 0.f}, {0.f, 0.f}};
     }
   }
+  double v[4];
   for (int a = 0; a < 4; ++a) {
     const ff t = acc_get(acc[a]);
-    const double v = block_sum((double)t.h + (double)t.l, sh);
-    if (threadIdx.x == 0) atomicAdd(res + a, v);
+    v[a] = block_sum((double)t.h + (double)t.l, sh);
   }
+  grid_reduce<4>(v, res, gr, sh);
 }
 
 // res[0] += Re sum conj(a) b ; res[1] += Im   (Hermitian product, for observables)
 template <class T>
-__global__ void k_hdot(const C<T>* __restrict__ a, const C<T>* __restrict__ b, long long n, double* res) {
+__global__ void k_hdot(const C<T>* __restrict__ a, const C<T>* __restrict__ b, long long n, double* res,
+                       GridRed gr) {
   __shared__ double sh[32];
   double re = 0.0, im = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -621,15 +653,14 @@ __global__ void k_hdot(const C<T>* __restrict__ a, const C<T>* __restrict__ b, l
   }
   re = block_sum(re, sh);
   im = block_sum(im, sh);
-  if (threadIdx.x == 0) {
-    atomicAdd(res, re);
-    atomicAdd(res + 1, im);
-  }
+  const double sums[2] = {re, im};
+  grid_reduce<2>(sums, res, gr, sh);
 }
 
 // res[0..1] += sum a b (bilinear, no conjugation: COCG); res[2] += ||b||^2 if nrm
 template <class T>
-__global__ void k_bdot(const C<T>* __restrict__ a, const C<T>* __restrict__ b, long long n, double* res) {
+__global__ void k_bdot(const C<T>* __restrict__ a, const C<T>* __restrict__ b, long long n, double* res,
+                       GridRed gr) {
   __shared__ double sh[32];
   double re = 0.0, im = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -639,10 +670,8 @@ __global__ void k_bdot(const C<T>* __restrict__ a, const C<T>* __restrict__ b, l
   }
   re = block_sum(re, sh);
   im = block_sum(im, sh);
-  if (threadIdx.x == 0) {
-    atomicAdd(res, re);
-    atomicAdd(res + 1, im);
-  }
+  const double sums[2] = {re, im};
+  grid_reduce<2>(sums, res, gr, sh);
 }
 
 // The Kronecker quadratic forms of the 2-D observables in one pass along y, given t = S_x c and
@@ -651,7 +680,8 @@ __global__ void k_bdot(const C<T>* __restrict__ a, const C<T>* __restrict__ b, l
 // accumulation in binary64 (real parts: the forms are Hermitian)
 template <class T, int P>
 __global__ void k_qform2_y(const C<T>* __restrict__ c, const C<T>* __restrict__ t, const C<T>* __restrict__ u,
-                           const T* __restrict__ Sy, const T* __restrict__ Dy, int nx, int ny, double* res) {
+                           const T* __restrict__ Sy, const T* __restrict__ Dy, int nx, int ny, double* res,
+                           GridRed gr) {
   __shared__ double sh[32];
   double q0 = 0.0, q1 = 0.0, q2 = 0.0;
   const long long N = (long long)nx * ny;
@@ -682,17 +712,15 @@ __global__ void k_qform2_y(const C<T>* __restrict__ c, const C<T>* __restrict__ 
   q0 = block_sum(q0, sh);
   q1 = block_sum(q1, sh);
   q2 = block_sum(q2, sh);
-  if (threadIdx.x == 0) {
-    atomicAdd(res, q0);
-    atomicAdd(res + 1, q1);
-    atomicAdd(res + 2, q2);
-  }
+  const double v[3] = {q0, q1, q2};
+  grid_reduce<3>(v, res, gr, sh);
 }
 
 // COCG update: x += alpha p; r -= alpha q; res[0] += ||r||^2
 template <class T>
 __global__ void k_cocg_update(C<T>* __restrict__ x, C<T>* __restrict__ r, const C<T>* __restrict__ p,
-                              const C<T>* __restrict__ q, long long n, double ar, double ai, double* res) {
+                              const C<T>* __restrict__ q, long long n, double ar, double ai, double* res,
+                              GridRed gr) {
   __shared__ double sh[32];
   double acc = 0.0;
   const T a_r = (T)ar, a_i = (T)ai;
@@ -708,7 +736,8 @@ __global__ void k_cocg_update(C<T>* __restrict__ x, C<T>* __restrict__ r, const 
     acc += (double)rv.r * (double)rv.r + (double)rv.i * (double)rv.i;
   }
   acc = block_sum(acc, sh);
-  if (threadIdx.x == 0) atomicAdd(res, acc);
+  const double v[1] = {acc};
+  grid_reduce<1>(v, res, gr, sh);
 }
 
 // p = z + beta p
@@ -736,7 +765,7 @@ __global__ void k_axby(const C<Tx>* __restrict__ x, C<Ty>* __restrict__ y, long 
 }
 
 template <class T>
-__global__ void k_nrm(const C<T>* __restrict__ a, long long n, double* res) {
+__global__ void k_nrm(const C<T>* __restrict__ a, long long n, double* res, GridRed gr) {
   __shared__ double sh[32];
   double acc = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -744,7 +773,8 @@ __global__ void k_nrm(const C<T>* __restrict__ a, long long n, double* res) {
     acc += (double)x.r * (double)x.r + (double)x.i * (double)x.i;
   }
   acc = block_sum(acc, sh);
-  if (threadIdx.x == 0) atomicAdd(res, acc);
+  const double v[1] = {acc};
+  grid_reduce<1>(v, res, gr, sh);
 }
 
 // ------------------------------------------------------------------------------- preconditioner
@@ -1292,7 +1322,7 @@ __global__ void k_merge(const Tp* __restrict__ w, C<Tv>* __restrict__ v, PadDims
 // vector with `a` (the preconditioned residual's rho = r^T z of COCG, without another pass)
 template <class Tv, class Tp>
 __global__ void k_merge_dot(const Tp* __restrict__ w, C<Tv>* __restrict__ v, PadDims d, long long n,
-                            const C<Tv>* __restrict__ a, double* res) {
+                            const C<Tv>* __restrict__ a, double* res, GridRed gr) {
   __shared__ double sh[32];
   double re = 0.0, im = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -1309,10 +1339,8 @@ __global__ void k_merge_dot(const Tp* __restrict__ w, C<Tv>* __restrict__ v, Pad
   }
   re = block_sum(re, sh);
   im = block_sum(im, sh);
-  if (threadIdx.x == 0) {
-    atomicAdd(res, re);
-    atomicAdd(res + 1, im);
-  }
+  const double sums[2] = {re, im};
+  grid_reduce<2>(sums, res, gr, sh);
 }
 
 // in the eigenbasis (index j0 fastest): u /= 1 + i tm (lam0[j0] + lam1[j1] + lam2[j2])
@@ -1426,6 +1454,7 @@ struct NdBatch {
   void* pre_L[3] = {nullptr, nullptr, nullptr};  // per run would be needed for different sizes; refreshed per run
   void* pre_D[3] = {nullptr, nullptr, nullptr};
   double* d_red = nullptr;  // reduction scratch (16 doubles)
+  GridRed gr{};             // per-block partial sums of the fixed-order reductions
   int* d_err = nullptr;     // set to nonzero by a kernel whose bounded wait ran out (in d_red's last slot)
   bool wait_failed = false;  // host copy of *d_err as of the last reduction read
   // coefficient rows {S, K} of the separable part for the fused FP32 2-D apply (x and y axes), and
@@ -1836,7 +1865,7 @@ void fd_apply(NdBatch* b, const NdRun* r, const C<T>* src, C<T>* dst, T* w0, T* 
                                                        G.lam[2], tau * r->mbar);
   }
   if (dot)
-    k_merge_dot<T, T><<<grid_for(r->N), TPB, 0, b->st>>>(cur, dst, d, r->N, src, dot);
+    k_merge_dot<T, T><<<grid_for(r->N), TPB, 0, b->st>>>(cur, dst, d, r->N, src, dot, b->gr);
   else
     k_merge<T, T><<<grid_for(r->N), TPB, 0, b->st>>>(cur, dst, d, r->N);
 }
@@ -1855,7 +1884,7 @@ void precond_dot(NdBatch* b, NdRun* r, Apply<T, P>& op, const C<T>* res, C<T>* z
   }
   cudaMemcpyAsync(z, res, sizeof(C<T>) * r->N, cudaMemcpyDeviceToDevice, b->st);
   line_precond<T, P>(b, r, z);
-  k_bdot<T><<<grid_for(r->N), TPB, 0, b->st>>>(res, z, r->N, b->d_red);
+  k_bdot<T><<<grid_for(r->N), TPB, 0, b->st>>>(res, z, r->N, b->d_red, b->gr);
 }
 
 // reads the reduction slots (and, in the same copy, the error word in the last slot)
@@ -1885,19 +1914,19 @@ int cocg(NdBatch* b, NdRun* r, Apply<T, P>& op, C<T>* x, C<T>* res, C<T>* z, C<T
   red_get(b, 2, h);
   std::complex<double> rho(h[0], h[1]);
   red_zero(b, 1);
-  k_nrm<T><<<grid_for(N), TPB, 0, b->st>>>(res, N, b->d_red);
+  k_nrm<T><<<grid_for(N), TPB, 0, b->st>>>(res, N, b->d_red, b->gr);
   double rr = red_get(b, 1, h)[0];
   int it = 0;
   while (rr > tol_abs2 && it < maxit) {
     op.apply(p, q, tau, ebar);
     red_zero(b, 2);
-    k_bdot<T><<<grid_for(N), TPB, 0, b->st>>>(p, q, N, b->d_red);
+    k_bdot<T><<<grid_for(N), TPB, 0, b->st>>>(p, q, N, b->d_red, b->gr);
     red_get(b, 2, h);
     const std::complex<double> pq(h[0], h[1]);
     if (b->wait_failed || std::abs(pq) == 0.0) break;
     const std::complex<double> alpha = rho / pq;
     red_zero(b, 1);
-    k_cocg_update<T><<<grid_for(N), TPB, 0, b->st>>>(x, res, p, q, N, alpha.real(), alpha.imag(), b->d_red);
+    k_cocg_update<T><<<grid_for(N), TPB, 0, b->st>>>(x, res, p, q, N, alpha.real(), alpha.imag(), b->d_red, b->gr);
     rr = red_get(b, 1, h)[0];
     ++it;
     if (!(rr > tol_abs2)) break;
@@ -1986,7 +2015,7 @@ void observe(NdBatch* b, NdRun* r, Apply<T, P>& op, const C<T>* c, C<T>* y, cons
     launch_axis_band<T, P>(b->st, grid_for(tot), bd, c, c, op.t2, r->n[1], r->n[0], 1);
     red_zero(b, 3);
     k_qform2_y<T, P><<<grid_for(N), TPB, 0, b->st>>>(c, op.t1, op.t2, tab<T>(r->ax[1], TS), tab<T>(r->ax[1], TD),
-                                                     r->n[0], r->n[1], b->d_red);
+                                                     r->n[0], r->n[1], b->d_red, b->gr);
     double q3[3];
     red_get(b, 3, q3);
     norm = q3[0];
@@ -1995,12 +2024,12 @@ void observe(NdBatch* b, NdRun* r, Apply<T, P>& op, const C<T>* c, C<T>* y, cons
   } else {
     op.kron(c, y, 1, 0.0, zero3);
     red_zero(b, 2);
-    k_hdot<T><<<grid_for(N), TPB, 0, b->st>>>(c, y, N, b->d_red);
+    k_hdot<T><<<grid_for(N), TPB, 0, b->st>>>(c, y, N, b->d_red, b->gr);
     norm = red_get(b, 2, h)[0];
     for (int a = 0; a < r->dim; ++a) {
       op.kron(c, y, 2, 0.0, zero3, a);
       red_zero(b, 2);
-      k_hdot<T><<<grid_for(N), TPB, 0, b->st>>>(c, y, N, b->d_red);
+      k_hdot<T><<<grid_for(N), TPB, 0, b->st>>>(c, y, N, b->d_red, b->gr);
       dvals[a] = red_get(b, 2, h)[0];
     }
   }
@@ -2015,7 +2044,7 @@ void observe(NdBatch* b, NdRun* r, Apply<T, P>& op, const C<T>* c, C<T>* y, cons
   red_zero(b, 4);
   k_fused_last_reduce_ff<P, T><<<grid_for(inner * nch), TPB, 0, b->st>>>(X, r->ax[0], r->ax[1], AL, r->dim, inner,
                                                                          echunk, medium_ff(r->med),
-                                                                         r->const_mass ? 0 : 1, b->d_red);
+                                                                         r->const_mass ? 0 : 1, b->d_red, b->gr);
   double q4[4];
   red_get(b, 4, q4);
   const double kq = r->const_mass ? r->cm * norm : q4[3];
@@ -2061,7 +2090,7 @@ int propagate_run(NdBatch* b, NdRun* r, const tdz::Ops& o, const double* field, 
       op.apply(c, y, tau, ebar);
       op.kron(c, r0, 1, 0.0, zero3);
       red_zero(b, 1);
-      k_nrm<double><<<grid_for(N), TPB, 0, b->st>>>(r0, N, b->d_red);
+      k_nrm<double><<<grid_for(N), TPB, 0, b->st>>>(r0, N, b->d_red, b->gr);
       const double bb = red_get(b, 1, h)[0];
       k_axby<double, double><<<grid_for(N), TPB, 0, b->st>>>(y, r0, N, -2.0, 2.0);
       double rr = 0;
@@ -2114,7 +2143,7 @@ int propagate_run(NdBatch* b, NdRun* r, const tdz::Ops& o, const double* field, 
       opx.apply(cx_, y, tau, ebar);
       opx.kron(cx_, r0, 1, 0.0, zero3);
       red_zero(b, 1);
-      k_nrm<fx><<<grid_for(N), TPB, 0, b->st>>>(r0, N, b->d_red);
+      k_nrm<fx><<<grid_for(N), TPB, 0, b->st>>>(r0, N, b->d_red, b->gr);
       const double bb = red_get(b, 1, h)[0];
       const double tol2 = b->tol * b->tol * bb;
       k_axby<fx, fx><<<grid_for(N), TPB, 0, b->st>>>(y, r0, N, -2.0, 2.0);
@@ -2122,7 +2151,7 @@ int propagate_run(NdBatch* b, NdRun* r, const tdz::Ops& o, const double* field, 
       cudaMemcpyAsync(rc, r0, sizeof(C<fx>) * N, cudaMemcpyDeviceToDevice, b->st);
       double rr = bb * 1e300;
       red_zero(b, 1);
-      k_nrm<fx><<<grid_for(N), TPB, 0, b->st>>>(rc, N, b->d_red);
+      k_nrm<fx><<<grid_for(N), TPB, 0, b->st>>>(rc, N, b->d_red, b->gr);
       rr = red_get(b, 1, h)[0];
       // Each FP32 solve contracts the residual by a factor rho, measured on the first one; when the
       // next solve is predicted to end at or below a tenth of the tolerance (and rho < 1e-2), its
@@ -2145,7 +2174,7 @@ int propagate_run(NdBatch* b, NdRun* r, const tdz::Ops& o, const double* field, 
         opx.apply(y, rc, tau, ebar);                                         // rc = A delta
         k_axby<fx, fx><<<grid_for(N), TPB, 0, b->st>>>(r0, rc, N, 1.0, -1.0);  // rc = r0 - A delta
         red_zero(b, 1);
-        k_nrm<fx><<<grid_for(N), TPB, 0, b->st>>>(rc, N, b->d_red);
+        k_nrm<fx><<<grid_for(N), TPB, 0, b->st>>>(rc, N, b->d_red, b->gr);
         const double rr_new = red_get(b, 1, h)[0];
         if (outer == 0) rho = std::min(1.0, std::sqrt(rr_new / std::max(rr, 1e-300)));
         rr = rr_new;
@@ -2191,6 +2220,9 @@ bool alloc_work(NdBatch* b) {
   b->d_qa = static_cast<double2*>(b->alloc(z64 * maxQ));
   b->d_qb = static_cast<double2*>(b->alloc(z64 * maxQ));
   b->d_red = static_cast<double*>(b->alloc(sizeof(double) * 16));
+  b->gr.part = static_cast<double*>(b->alloc(sizeof(double) * 4 * 148 * 16));  // grid_for's block cap
+  b->gr.ticket = static_cast<unsigned*>(b->alloc(sizeof(unsigned) * 4));
+  ok = ok && b->gr.part && b->gr.ticket;
   b->d_err = b->d_red ? reinterpret_cast<int*>(b->d_red + 15) : nullptr;  // red_zero never clears it
   if (b->prec == TDZ_MIXED && b->dim == 2)
     for (int a = 0; a < 2; ++a) {

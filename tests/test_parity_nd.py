@@ -363,3 +363,31 @@ def test_workload_degree_3d_against_oracle(tdz):
                 scale = max(1e-3, np.max(np.abs(ref["obs"][:, col])))
                 assert np.max(np.abs(og[:, col] - ref["obs"][:, col])) < 10 * tol * scale, (prec, op, pc, col)
             del b
+
+
+@pytest.mark.parametrize("name", ["softcore2d", "softcore3d"])
+def test_repeat_runs_are_bitwise_equal(tdz, name):
+    """The Krylov dots, norms and observable sums are fixed-order grid reductions (per-block partials
+    added in block order by the last block), so two runs of the same batch give bitwise equal states and
+    observables, in both precisions. The autotuner may pick another variant of the fused FP32 2-D apply
+    at each batch creation (the variants differ in FP32 rounding), so the second run is pinned to the
+    first run's variant."""
+    knots, p, med, dt, nsteps, e0 = _case(name)
+    m, c0, field, c, obs = _reference(name)
+    dim = len(knots)
+    ops = tdz.Ops([tdz.Basis(k, p, p + 1) for k in knots], med)
+    for prec in (tdz.FP64, tdz.MIXED):
+        out = []
+        for rep in range(2):
+            b = tdz.Batch([ops], [0], prec)
+            if rep == 0:
+                groups = b.tuning(0)[0] if dim == 2 else 0
+            elif groups:
+                b.set_option(tdz.OPT_APPLY_GROUPS, groups)
+            b.set_state(0, c0)
+            b.propagate(field.reshape(1, nsteps + 1, dim), dt, 0, nsteps)
+            out.append((b.get_state(0), b.observe(0)[0], b.krylov_stats()))
+            del b
+        assert np.array_equal(out[0][0], out[1][0]), prec
+        assert np.array_equal(out[0][1], out[1][1]), prec
+        assert out[0][2] == out[1][2]
