@@ -286,6 +286,8 @@ def _nd_time(tdz, name, ops, run_ops, c0s, fields, dt, nsteps, extra):
         states[label] = [b.get_state(i) for i in range(len(run_ops))]
         if label == "mixed" and dim == 2:
             res["fused_apply"] = _apply_roofline(tdz, b, ops, run_ops)
+        if label == "mixed":
+            res["preconditioner_apply"] = _precond_roofline(tdz, b, ops, run_ops)
         del b
     num = sum(np.linalg.norm(x - y) ** 2 for x, y in zip(states["mixed"], states["fp64"]))
     den = sum(np.linalg.norm(y) ** 2 for y in states["fp64"])
@@ -315,12 +317,41 @@ def _apply_roofline(tdz, b, ops, run_ops):
 
 
 def _measured_peaks():
+    """HBM copy bandwidth and dense BF16 tensor rate (burst) measured on this machine, else the fallback figures."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             d = json.load(f)
-        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]), "source": "measured"}
     except (OSError, KeyError, ValueError):
-        return {"hbm_gbs": 6400.0, "source": "fallback"}
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "source": "fallback"}
+
+
+# dense TF32 : BF16 tensor rate of B300 (nominal 1.1 : 2.25 PFLOP/s)
+TF32_PER_BF16 = 1.1 / 2.25
+
+
+def _precond_roofline(tdz, b, ops, run_ops):
+    """Tensor roofline of the mixed fast-diagonalisation preconditioner for the largest geometry, from the
+    autotuner's CUDA-event timing of one whole apply (TF32 split, 2 dim tcgen05 axis transforms, scaling,
+    merge; batch creation, best of three). Tensor work per apply: for each axis a and each of the two
+    passes, 2 TF32 products x 2 flops x (2 Np / np_a rows) x np_a columns x np_a (k) = 8 Np np_a, i.e.
+    16 Np sum_a np_a; the algorithmic (one FP32 product) flops are half of that. Peak: the measured BF16
+    rate x the nominal TF32/BF16 ratio."""
+    peaks = _measured_peaks()
+    g = max(set(run_ops), key=lambda k: ops[k].n)
+    tile, ms = b.precond_tuning(g)
+    if not tile:
+        return None
+    npad = [(n + 7) // 8 * 8 for n in ops[g].shape]
+    Np = int(np.prod(npad))
+    tflop = 16.0 * Np * sum(npad) / 1e12
+    t = ms[tile] * 1e-3
+    peak = peaks["bf16_tflops"] * TF32_PER_BF16
+    return {"kernel": f"k_tc_axis<{tile}, false> x {2 * len(npad)} + split/scale/merge", "padded_shape": npad,
+            "bound": "tensor", "achieved": tflop / t, "peak": peak, "unit": "TFLOP/s", "frac": tflop / t / peak,
+            "peak_source": peaks["source"] + " bf16 x nominal tf32/bf16", "tensor_tflop_per_apply": tflop,
+            "algorithmic_fp32_tflop_per_apply": tflop / 2, "ms_per_apply": ms[tile],
+            "tile_ms": {str(k): v for k, v in ms.items()}}
 
 
 def _gauss_state(knots, p, dim):
@@ -348,7 +379,7 @@ def nd_legs(tdz, nsteps, which, n2d=1024, n3d=256):
                           dim=2)
         out["config_2d"] = _nd_time(tdz, "softcore_atom_2d", [ops], [0], [_gauss_state(t, p, 2)], f[None], dt, nsteps,
                                     {"operator": "assembled (2p+1)^2 stencil",
-                                     "preconditioner": "fast diagonalisation (cuBLAS axis GEMMs)"})
+                                     "preconditioner": "fast diagonalisation (tcgen05 TF32 axis transforms)"})
     if "dots" in which:
         wk = wl.dot_batch(nsteps=nsteps + 1)
         ops = [tdz.Ops([tdz.Basis(k, r.degree, r.nquad) for k in r.knots], r.medium) for r in wk.runs]
@@ -364,7 +395,7 @@ def nd_legs(tdz, nsteps, which, n2d=1024, n3d=256):
         f = wl.sin2_pulse(wl.time_grid(dt, nsteps + 1), 0.05, wl.omega_from_nm(800.0), 4.0, ellipticity=0.3, dim=3)
         out["config_3d"] = _nd_time(tdz, "softcore_atom_3d", [ops], [0], [_gauss_state(t, p, 3)], f[None], dt, nsteps,
                                     {"operator": "Gauss-point sum factorisation",
-                                     "preconditioner": "fast diagonalisation (cuBLAS axis GEMMs)"})
+                                     "preconditioner": "fast diagonalisation (tcgen05 TF32 axis transforms)"})
     return out
 
 

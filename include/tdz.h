@@ -258,6 +258,14 @@ int  tdz_batch_set_option(tdz_batch* b, int option, int value);
  * mixed); ms (host, optional, 2 doubles): the measured ms per apply of the variants 8 and 16.
  * Errors: TDZ_EINVAL (bad handle or geometry index). */
 int  tdz_batch_tuning(const tdz_batch* b, int geometry, int* groups, double* ms);
+/* Autotuner result for the fast-diagonalisation preconditioner of geometry `geometry` of a 2-D/3-D
+ * mixed batch: at creation one whole preconditioner apply (TF32 split, the tensor-core axis transforms
+ * of tdz_tc_axis_transform, eigenvalue scaling, merge) is timed with 128- and 256-column transform
+ * tiles on the batch's own buffers (CUDA events, best of three) and the faster width is kept.
+ * tile_n (host, optional): the chosen width (0 when the geometry has no fast diagonalisation or the
+ * batch is not mixed); ms (host, optional, 2 doubles): ms per preconditioner apply with 128 and 256.
+ * Errors: TDZ_EINVAL (bad handle or geometry index). */
+int  tdz_batch_precond_tuning(const tdz_batch* b, int geometry, int* tile_n, double* ms);
 /* Total Krylov iterations of all runs since the batch was created (2-D/3-D; 0 in 1-D, whose
  * solve is direct). Synchronises the batch stream. */
 int  tdz_krylov_stats(const tdz_batch* b, double* iterations);
@@ -324,6 +332,26 @@ int  tdz_harmonic_yields(const double* S, int64_t nsig, double w_lo, double dw, 
  * timed launches). The ratio is what makes the mixed path form its binary64-class residuals in
  * double-float on B300. No counterpart in the paper. Errors: TDZ_EINVAL, TDZ_ECUDA. */
 int  tdz_device_rates(double* fp32_flops, double* fp64_flops);
+
+/* ------------------------------------------------------------------ tensor-core axis transform
+ * tdz_tc_axis_transform: one axis transform of the fast-diagonalisation preconditioner M^-1 =
+ * (V_x (x) V_y ...) diag(1 / (1 + i tau mbar sum_a lam_a)) (V_x (x) V_y ...)^T (Sec. "Eigenvalue
+ * problem": V_a the S_a-orthonormal eigenvectors of T1_a v = lam S_a v), as the mixed-precision 2-D/3-D
+ * preconditioner runs it, on the tensor cores (tcgen05, TF32 operands, FP32 accumulation):
+ *   D(m, j) = sum_kk (a_hi + a_lo)[m*k + kk] (b + b_lo)[j*k + kk]   (kk < k),   m < rows, j < ncols,
+ * evaluated as a_hi b + a_lo b + a_hi b_lo (the a_lo b_lo term is dropped; without b_lo, b_lo = 0),
+ * written to out_hi[p*plane_stride + j*plane_rows + r] with p = m / plane_rows, r = m mod plane_rows
+ * (the contracted index moves from fastest to slowest). With out_lo non-NULL the result is stored as
+ * a TF32 pair: out_hi = D rounded to TF32 (nearest, ties away), out_lo = D - out_hi; with out_lo NULL
+ * out_hi = D in FP32. The hi arrays should hold TF32 values and the lo arrays the FP32 remainders
+ * (every operand is read as TF32: the low 13 bits of each FP32 pattern are ignored). tile_n: 0 (the
+ * library's choice), 128 or 256 columns per block. All pointers are device memory owned by the caller,
+ * the operands 16-byte aligned; k must be a multiple of 4. Synchronises the stream. Errors:
+ * TDZ_EINVAL (sizes, alignment, tile_n), TDZ_ECUDA (launch failure, or a pipeline wait that ran out
+ * of time). */
+int  tdz_tc_axis_transform(const float* a_hi, const float* a_lo, int64_t rows, int k, const float* b,
+                           const float* b_lo, int ncols, int64_t plane_rows, int64_t plane_stride, float* out_hi,
+                           float* out_lo, int tile_n, void* cuda_stream);
 
 /* ------------------------------------------------------------------ allocation-free entry point
  * tdz_cn1d_propagate_noalloc: the binary64 1-D propagation of tdz_propagate for ONE run, for

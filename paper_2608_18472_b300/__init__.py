@@ -74,11 +74,14 @@ _sig = {
     "tdz_observe_all": (C.c_int, [_vp, _vp, C.POINTER(C.c_int)]),
     "tdz_krylov_stats": (C.c_int, [_vp, _dp]),
     "tdz_batch_tuning": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int), _dp]),
+    "tdz_batch_precond_tuning": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int), _dp]),
     "tdz_batch_destroy": (None, [_vp]),
     "tdz_observe_current": (C.c_int, [_vp, C.c_int, _vp]),
     "tdz_lowest_states": (C.c_int, [C.POINTER(_vp), C.c_int, C.c_int, _dp, _dp, _dp, C.POINTER(C.c_int), _vp]),
     "tdz_populations": (C.c_int, [_vp, _dp, C.c_int, _dp, C.c_int64, _dp, _dp]),
     "tdz_device_rates": (C.c_int, [_dp, _dp]),
+    "tdz_tc_axis_transform": (C.c_int, [_vp, _vp, C.c_int64, C.c_int, _vp, _vp, C.c_int, C.c_int64, C.c_int64, _vp,
+                                        _vp, C.c_int, _vp]),
     "tdz_pdm_acceleration": (C.c_int, [_vp, _dp, C.c_int64, _dp]),
     "tdz_spectrum": (C.c_int, [_vp, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_double, C.c_double, C.c_int,
                                C.c_double, C.c_double, C.c_int64, _vp, _vp]),
@@ -253,6 +256,19 @@ def device_rates():
     return a.value, b.value
 
 
+def tc_axis_transform(a_hi, a_lo, b, rows: int, k: int, ncols: int, plane_rows: int, plane_stride: int, out_hi,
+                      out_lo=None, b_lo=None, tile_n: int = 0, stream: Optional[int] = None):
+    """One fast-diagonalisation axis transform on the tensor cores (tdz_tc_axis_transform). The arrays are
+    float32 device tensors: a_hi, a_lo [rows, k], b (and b_lo) [ncols, k]; the result goes to out_hi (and
+    out_lo)."""
+    _check(_lib.tdz_tc_axis_transform(_vp(_ptr(a_hi)), _vp(_ptr(a_lo)), int(rows), int(k), _vp(_ptr(b)),
+                                      _vp(_ptr(b_lo)) if b_lo is not None else None, int(ncols), int(plane_rows),
+                                      int(plane_stride), _vp(_ptr(out_hi)),
+                                      _vp(_ptr(out_lo)) if out_lo is not None else None, int(tile_n),
+                                      _vp(stream or 0)),
+           "tdz_tc_axis_transform")
+
+
 def lowest_states(ops: Sequence["Ops"], nstates: int = 1, stream: Optional[int] = None):
     """The nstates lowest eigenpairs of H0 c = eps S c of several 1-D geometries at once on the GPU
     (tdz_lowest_states). Returns (energies [nops, nstates], list of state arrays [nstates, n_g] complex,
@@ -402,6 +418,16 @@ class Batch:
         _check(_lib.tdz_batch_tuning(self._h, int(geometry), C.byref(g), ms.ctypes.data_as(_dp)),
                "tdz_batch_tuning")
         return g.value, ({8: float(ms[0]), 16: float(ms[1])} if g.value else {})
+
+    def precond_tuning(self, geometry: int = 0):
+        """Autotuner result of the tensor-core fast-diagonalisation preconditioner of a 2-D/3-D mixed batch
+        for one geometry: (chosen column-tile width, {width: measured ms per preconditioner apply});
+        (0, {}) where it does not apply."""
+        t = C.c_int()
+        ms = np.zeros(2)
+        _check(_lib.tdz_batch_precond_tuning(self._h, int(geometry), C.byref(t), ms.ctypes.data_as(_dp)),
+               "tdz_batch_precond_tuning")
+        return t.value, ({128: float(ms[0]), 256: float(ms[1])} if t.value else {})
 
     def krylov_stats(self) -> float:
         """Total Krylov iterations of all runs since creation (0 for 1-D batches)."""

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libtdz.so")
-SOURCES_CU = ["tdz_cn1d.cu", "tdz_nd.cu", "tdz_spectrum.cu", "tdz_eigen.cu", "tdz_probe.cu"]
+SOURCES_CU = ["tdz_cn1d.cu", "tdz_nd.cu", "tdz_spectrum.cu", "tdz_eigen.cu", "tdz_probe.cu", "tdz_tc.cu"]
 SOURCES_CPP = ["tdz_host.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -155,4 +155,10 @@ TDZ_DEV fx tsqrt(fx a) {
   return to_fx(fast_two_sum(s, r.h / (2.f * s)));
 }
 
+// ---------------------------------------------------------------------------- TF32 split
+// x rounded to the nearest TF32 value (8 exponent bits, 10 stored significand bits: the low 13 bits
+// of the FP32 pattern cleared after adding half of their weight, ties away from zero); x - tf32_hi(x)
+// is exact in FP32 and at most 2^-11 |x|.
+TDZ_DEV float tf32_hi(float x) { return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u); }
+
 }  // namespace tdz

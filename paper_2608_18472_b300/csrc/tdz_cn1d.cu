@@ -2063,6 +2063,14 @@ int tdz_batch_tuning(const tdz_batch* b, int geometry, int* groups, double* ms) 
   return TDZ_OK;
 }
 
+int tdz_batch_precond_tuning(const tdz_batch* b, int geometry, int* tile_n, double* ms) {
+  if (!b || geometry < 0) return TDZ_EINVAL;
+  if (b->nd) return tdz::nd_precond_tuning(b->nd, geometry, tile_n, ms);
+  if (tile_n) *tile_n = 0;
+  if (ms) ms[0] = ms[1] = 0.0;
+  return TDZ_OK;
+}
+
 int tdz_krylov_stats(const tdz_batch* b, double* iterations) {
   if (!b || !iterations) return TDZ_EINVAL;
   *iterations = 0.0;

@@ -72,8 +72,15 @@ int nd_stats(const NdBatch* b, double* max_rel, double* solves, double* iters);
 void nd_set_refinement(NdBatch* b, double tol, int max_it);
 int nd_set_option(NdBatch* b, int option, int value);
 int nd_tuning(const NdBatch* b, int geometry, int* groups, double* ms);
+int nd_precond_tuning(const NdBatch* b, int geometry, int* tile_n, double* ms);
 int nd_dim(const NdBatch* b);
 size_t nd_device_bytes(const NdBatch* b);
+
+// One axis transform of the mixed-precision fast-diagonalisation preconditioner on the tensor cores
+// (tdz_tc.cu; semantics of tdz_tc_axis_transform, asynchronous on `st`, a run-out wait sets *err)
+int tc_axis_transform(const float* a_hi, const float* a_lo, long long rows, int K, const float* b, const float* b_lo,
+                      int ncols, long long plane_rows, long long plane_stride, float* out_hi, float* out_lo, int* err,
+                      int tile_n, struct CUstream_st* st);
 
 }  // namespace tdz
 

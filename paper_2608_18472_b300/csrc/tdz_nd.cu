@@ -1343,6 +1343,26 @@ __global__ void k_merge_dot(const Tp* __restrict__ w, C<Tv>* __restrict__ v, Pad
   grid_reduce<2>(sums, res, gr, sh);
 }
 
+// k_split for the tensor-core transforms: each value as the TF32 pair (hi, lo), hi = the value rounded
+// to TF32, lo = the FP32 remainder; planes of hi in whi, of lo in wlo
+__global__ void k_split_tf32(const C<float>* __restrict__ v, float* __restrict__ whi, float* __restrict__ wlo,
+                             PadDims d) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < d.Np; i += (long long)gridDim.x * blockDim.x) {
+    const int j0 = (int)(i % d.np[0]);
+    const long long t = i / d.np[0];
+    const int j1 = d.dim > 1 ? (int)(t % d.np[1]) : 0;
+    const int j2 = d.dim > 2 ? (int)(t / d.np[1]) : 0;
+    const bool in = j0 < d.n[0] && (d.dim < 2 || j1 < d.n[1]) && (d.dim < 3 || j2 < d.n[2]);
+    C<float> a{0.f, 0.f};
+    if (in) a = v[((long long)j2 * d.n[1] + j1) * d.n[0] + j0];
+    const float hr = tf32_hi(a.r), hi = tf32_hi(a.i);
+    whi[i] = hr;
+    whi[d.Np + i] = hi;
+    wlo[i] = a.r - hr;
+    wlo[d.Np + i] = a.i - hi;
+  }
+}
+
 // in the eigenbasis (index j0 fastest): u /= 1 + i tm (lam0[j0] + lam1[j1] + lam2[j2])
 template <class Tp>
 __global__ void k_fd_scale(Tp* __restrict__ w, long long n, int dim, int n0, int n1, const double* __restrict__ l0,
@@ -1358,6 +1378,29 @@ __global__ void k_fd_scale(Tp* __restrict__ w, long long n, int dim, int n0, int
     const double a = (double)w[i], b = (double)w[n + i];
     w[i] = (Tp)((a + th * b) * g);
     w[n + i] = (Tp)((b - th * a) * g);
+  }
+}
+
+// k_fd_scale for the tensor-core transforms: reads the FP32 planes w, writes the scaled values as
+// TF32 pairs (planes of hi in whi, of lo in wlo)
+__global__ void k_fd_scale_tf32(const float* __restrict__ w, float* __restrict__ whi, float* __restrict__ wlo,
+                                long long n, int dim, int n0, int n1, const double* __restrict__ l0,
+                                const double* __restrict__ l1, const double* __restrict__ l2, double tm) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int j0 = (int)(i % n0);
+    const long long t = i / n0;
+    double lam = l0[j0];
+    if (dim > 1) lam += l1[(int)(t % n1)];
+    if (dim > 2) lam += l2[(int)(t / n1)];
+    const double th = tm * lam;
+    const double g = 1.0 / (1.0 + th * th);
+    const double a = (double)w[i], b = (double)w[n + i];
+    const float xr = (float)((a + th * b) * g), xi = (float)((b - th * a) * g);
+    const float hr = tf32_hi(xr), hi = tf32_hi(xi);
+    whi[i] = hr;
+    whi[n + i] = hi;
+    wlo[i] = xr - hr;
+    wlo[n + i] = xi - hi;
   }
 }
 
@@ -1416,7 +1459,12 @@ struct NdGeo {
   int n[3] = {0, 0, 0};
   int np[3] = {1, 1, 1};  // n rounded up to a multiple of 8 (fast-diagonalisation work layout)
   double* V64[3] = {nullptr, nullptr, nullptr};
-  float* V32[3] = {nullptr, nullptr, nullptr};
+  // mixed batches: V rounded to TF32 once, as the tensor-core transforms read it: Vt row j = eigenvector
+  // j (the forward transform V^T), VtT = its transpose (the inverse transform V)
+  float* Vt[3] = {nullptr, nullptr, nullptr};
+  float* VtT[3] = {nullptr, nullptr, nullptr};
+  int tc_tile = 0;                  // column-tile width of the transforms chosen by the autotuner (128 or 256)
+  float tc_ms[2] = {0.f, 0.f};      // its timings of one preconditioner apply with 128- and 256-column tiles
   double* lam[3] = {nullptr, nullptr, nullptr};
   double* W64 = nullptr;  // binary64 batches
   float* W32 = nullptr;   // mixed: inner FP32 solve
@@ -1451,6 +1499,8 @@ struct NdBatch {
   double2 *d_z = nullptr, *d_p = nullptr, *d_q = nullptr, *d_rc = nullptr;  // COCG / residual vectors
   void *w_x = nullptr, *w_r = nullptr, *w_z = nullptr, *w_p = nullptr, *w_q = nullptr, *w_t1 = nullptr, *w_t2 = nullptr,
        *w_t3 = nullptr, *w_t4 = nullptr, *w_qa = nullptr, *w_qb = nullptr;
+  void *w_qc = nullptr, *w_qd = nullptr;  // mixed: second TF32 pair of the fast-diagonalisation transforms
+  size_t maxPad = 0;                      // largest padded plane of a run (fast diagonalisation)
   void* pre_L[3] = {nullptr, nullptr, nullptr};  // per run would be needed for different sizes; refreshed per run
   void* pre_D[3] = {nullptr, nullptr, nullptr};
   double* d_red = nullptr;  // reduction scratch (16 doubles)
@@ -1811,38 +1861,7 @@ void line_precond(NdBatch* b, NdRun* r, C<T>* v) {
 }
 
 // ---------------------------------------------------------------- fast diagonalisation
-// One axis transform: contract the slowest axis of the current layout (length ns, R = N / ns
-// values per index) with V (forward, V^T) or V^T (inverse, V), writing the new index fastest:
-//   out(j, r) = sum_k M(k, j) in(r, k),  both planes (re, im) as a batch of two.
-// After dim transforms the axes are back in their original order. Sizes are padded to multiples
-// of 8, so every leading dimension is 32-byte aligned and the FP32 product can run on the tensor
-// cores as a BF16x9 emulated GEMM (three-term bf16 splits of both operands, FP32 accuracy).
-inline cublasStatus_t gemm_rot(cublasHandle_t h, bool inv, int ns, int R, const float* V, const float* in, float* out,
-                               long long stride) {
-  const float one = 1.0f, zero = 0.0f;
-  return cublasGemmStridedBatchedEx(h, inv ? CUBLAS_OP_N : CUBLAS_OP_T, CUBLAS_OP_T, ns, R, ns, &one, V, CUDA_R_32F, ns, 0,
-                                    in, CUDA_R_32F, R, stride, &zero, out, CUDA_R_32F, ns, stride, 2,
-                                    CUBLAS_COMPUTE_32F_EMULATED_16BFX9, CUBLAS_GEMM_DEFAULT);
-}
-inline cublasStatus_t gemm_rot(cublasHandle_t h, bool inv, int ns, int R, const double* V, const double* in,
-                               double* out, long long stride) {
-  const double one = 1.0, zero = 0.0;
-  return cublasGemmStridedBatchedEx(h, inv ? CUBLAS_OP_N : CUBLAS_OP_T, CUBLAS_OP_T, ns, R, ns, &one, V, CUDA_R_64F, ns, 0,
-                                    in, CUDA_R_64F, R, stride, &zero, out, CUDA_R_64F, ns, stride, 2, CUBLAS_COMPUTE_64F,
-                                    CUBLAS_GEMM_DEFAULT);
-}
-template <class T> const T* fd_mat(const NdGeo& g, int a);
-template <> const float* fd_mat<float>(const NdGeo& g, int a) { return g.V32[a]; }
-template <> const double* fd_mat<double>(const NdGeo& g, int a) { return g.V64[a]; }
-
-// v <- M^-1 v, M = S(x)S + i tau mbar sum_a (T1_a on axis a, S elsewhere):
-//   M^-1 = ((x)V_a) diag(1 / (1 + i tau mbar sum_a lam_a)) ((x)V_a)^T   since V_a^T S_a V_a = I,
-//   V_a^T T1_a V_a = diag(lam_a). w0, w1: planar scratch of 2N values each.
-//   dst = M^-1 src (src == dst allowed); with dot, also dot[0..1] += src^T dst (src != dst).
-template <class T>
-void fd_apply(NdBatch* b, const NdRun* r, const C<T>* src, C<T>* dst, T* w0, T* w1, double tau,
-              double* dot = nullptr) {
-  const NdGeo& G = b->geo[r->geo];
+inline PadDims pad_dims(const NdGeo& G, const NdRun* r) {
   PadDims d{};
   d.dim = r->dim;
   d.Np = 1;
@@ -1851,27 +1870,141 @@ void fd_apply(NdBatch* b, const NdRun* r, const C<T>* src, C<T>* dst, T* w0, T* 
     d.np[a] = a < r->dim ? G.np[a] : 1;
     d.Np *= d.np[a];
   }
-  k_split<T, T><<<grid_for(d.Np), TPB, 0, b->st>>>(src, w0, d);
-  T* cur = w0;
-  T* nxt = w1;
+  return d;
+}
+
+// v <- M^-1 v, M = S(x)S + i tau mbar sum_a (T1_a on axis a, S elsewhere):
+//   M^-1 = ((x)V_a) diag(1 / (1 + i tau mbar sum_a lam_a)) ((x)V_a)^T   since V_a^T S_a V_a = I,
+//   V_a^T T1_a V_a = diag(lam_a). Both planes (re, im) are transformed together; sizes are padded to
+//   multiples of 8 (zero entries), so every row is 32-byte aligned.
+//
+// Binary64 batches: one cuBLAS DGEMM per axis contracts the slowest axis of the current layout (length
+// ns, R = N / ns values per index) with V^T (forward) or V (inverse) and writes the new index fastest:
+//   out(j, r) = sum_k M(k, j) in(r, k), both planes as a batch of two.
+inline cublasStatus_t gemm_rot(cublasHandle_t h, bool inv, int ns, int R, const double* V, const double* in,
+                               double* out, long long stride) {
+  const double one = 1.0, zero = 0.0;
+  return cublasGemmStridedBatchedEx(h, inv ? CUBLAS_OP_N : CUBLAS_OP_T, CUBLAS_OP_T, ns, R, ns, &one, V, CUDA_R_64F, ns, 0,
+                                    in, CUDA_R_64F, R, stride, &zero, out, CUDA_R_64F, ns, stride, 2, CUBLAS_COMPUTE_64F,
+                                    CUBLAS_GEMM_DEFAULT);
+}
+
+// dst = M^-1 src (src == dst allowed); with dot, also dot[0..1] += src^T dst (src != dst).
+// w0, w1: planar scratch of 2 Np values each.
+void fd_apply64(NdBatch* b, const NdRun* r, const C<double>* src, C<double>* dst, double* w0, double* w1, double tau,
+                double* dot) {
+  const NdGeo& G = b->geo[r->geo];
+  const PadDims d = pad_dims(G, r);
+  k_split<double, double><<<grid_for(d.Np), TPB, 0, b->st>>>(src, w0, d);
+  double* cur = w0;
+  double* nxt = w1;
   for (int pass = 0; pass < 2; ++pass) {
     for (int a = r->dim - 1; a >= 0; --a) {
       const int ns = d.np[a];
-      gemm_rot(b->blas, pass == 1, ns, (int)(d.Np / ns), fd_mat<T>(G, a), cur, nxt, d.Np);
+      gemm_rot(b->blas, pass == 1, ns, (int)(d.Np / ns), G.V64[a], cur, nxt, d.Np);
       std::swap(cur, nxt);
     }
     if (pass == 0)
-      k_fd_scale<T><<<grid_for(d.Np), TPB, 0, b->st>>>(cur, d.Np, r->dim, d.np[0], d.np[1], G.lam[0], G.lam[1],
-                                                       G.lam[2], tau * r->mbar);
+      k_fd_scale<double><<<grid_for(d.Np), TPB, 0, b->st>>>(cur, d.Np, r->dim, d.np[0], d.np[1], G.lam[0], G.lam[1],
+                                                            G.lam[2], tau * r->mbar);
   }
   if (dot)
-    k_merge_dot<T, T><<<grid_for(r->N), TPB, 0, b->st>>>(cur, dst, d, r->N, src, dot, b->gr);
+    k_merge_dot<double, double><<<grid_for(r->N), TPB, 0, b->st>>>(cur, dst, d, r->N, src, dot, b->gr);
   else
-    k_merge<T, T><<<grid_for(r->N), TPB, 0, b->st>>>(cur, dst, d, r->N);
+    k_merge<double, double><<<grid_for(r->N), TPB, 0, b->st>>>(cur, dst, d, r->N);
+}
+
+// Mixed batches: the transforms run on the tensor cores (tc_axis_transform). Each contracts the
+// FASTEST axis of the current layout with the TF32-rounded factor (Vt forward, VtT inverse) and
+// writes the new index slowest, so after one transform per axis the original order is back. The data
+// enter every transform as a TF32 pair (hi, lo): the split kernel, the eigenvalue scaling and every
+// transform but the last of a pass write pairs. Rounding V once keeps M^-1 = Vt Lambda Vt^T complex
+// symmetric, as COCG requires; it is the preconditioner of V rounded to 11 significant bits.
+// w0..w3: planar scratch of 2 Np FP32 values each (two pairs). Returns TDZ_OK or the transform's error.
+int fd_apply32(NdBatch* b, const NdRun* r, const C<float>* src, C<float>* dst, float* w0, float* w1, float* w2,
+               float* w3, double tau, double* dot) {
+  const NdGeo& G = b->geo[r->geo];
+  const PadDims d = pad_dims(G, r);
+  k_split_tf32<<<grid_for(d.Np), TPB, 0, b->st>>>(src, w0, w1, d);
+  float *hi = w0, *lo = w1, *ohi = w2, *olo = w3;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int a = 0; a < r->dim; ++a) {
+      const int ns = d.np[a];
+      const long long R = d.Np / ns;
+      const bool last = a == r->dim - 1;
+      const int rc = tc_axis_transform(hi, lo, 2 * R, ns, pass == 0 ? G.Vt[a] : G.VtT[a], nullptr, ns, R, d.Np, ohi,
+                                       last ? nullptr : olo, b->d_err, G.tc_tile, b->st);
+      if (rc != TDZ_OK) return rc;
+      std::swap(hi, ohi);
+      std::swap(lo, olo);
+    }
+    // hi holds the FP32 result of the pass
+    if (pass == 0) {
+      k_fd_scale_tf32<<<grid_for(d.Np), TPB, 0, b->st>>>(hi, ohi, olo, d.Np, r->dim, d.np[0], d.np[1], G.lam[0],
+                                                         G.lam[1], G.lam[2], tau * r->mbar);
+      std::swap(hi, ohi);
+      std::swap(lo, olo);
+    }
+  }
+  if (dot)
+    k_merge_dot<float, float><<<grid_for(r->N), TPB, 0, b->st>>>(hi, dst, d, r->N, src, dot, b->gr);
+  else
+    k_merge<float, float><<<grid_for(r->N), TPB, 0, b->st>>>(hi, dst, d, r->N);
+  return TDZ_OK;
 }
 
 bool use_fd(const NdBatch* b, const NdRun* r) {
   return b->opt_precond != TDZ_PRECOND_LINES && b->geo[r->geo].fd;
+}
+
+// Autotuner of the mixed fast-diagonalisation preconditioner: one whole apply (split, 2 dim tensor-core
+// transforms, scaling, merge) is timed with 128- and 256-column transform tiles on the batch's own
+// buffers (CUDA events, best of three after one warm-up) and the faster width is kept per geometry.
+int autotune_fd(NdBatch* b) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return TDZ_ECUDA;
+  }
+  const int cand[2] = {128, 256};
+  int rc = TDZ_OK;
+  for (size_t g = 0; g < b->geo.size() && rc == TDZ_OK; ++g) {
+    NdGeo& G = b->geo[g];
+    NdRun* r = nullptr;
+    for (auto& run : b->runs)
+      if (run.geo == (int)g) {
+        r = &run;
+        break;
+      }
+    if (!G.fd || !G.Vt[0] || !r) continue;
+    const C<float>* x = static_cast<const C<float>*>(b->w_p);
+    C<float>* y = static_cast<C<float>*>(b->w_q);
+    float* w[4] = {static_cast<float*>(b->w_qa), static_cast<float*>(b->w_qb), static_cast<float*>(b->w_qc),
+                   static_cast<float*>(b->w_qd)};
+    for (int c = 0; c < 2 && rc == TDZ_OK; ++c) {
+      G.tc_tile = cand[c];
+      rc = fd_apply32(b, r, x, y, w[0], w[1], w[2], w[3], 0.025, nullptr);
+      float tmin = 0.f;
+      for (int k = 0; k < 3 && rc == TDZ_OK; ++k) {
+        cudaEventRecord(e0, b->st);
+        rc = fd_apply32(b, r, x, y, w[0], w[1], w[2], w[3], 0.025, nullptr);
+        cudaEventRecord(e1, b->st);
+        float ms = 0.f;
+        if (rc == TDZ_OK &&
+            (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+          rc = TDZ_ECUDA;
+        tmin = k == 0 ? ms : std::min(tmin, ms);
+      }
+      G.tc_ms[c] = tmin;
+    }
+    G.tc_tile = G.tc_ms[1] < G.tc_ms[0] ? 256 : 128;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  int werr = 0;  // a wait that ran out while timing
+  if (rc == TDZ_OK && (cudaMemcpy(&werr, b->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess || werr != 0))
+    rc = TDZ_ECUDA;
+  return rc;
 }
 
 // z = M^-1 res and d_red[0..1] += res^T z (the rho of COCG; d_red zeroed by the caller): on the fast
@@ -1879,7 +2012,13 @@ bool use_fd(const NdBatch* b, const NdRun* r) {
 template <class T, int P>
 void precond_dot(NdBatch* b, NdRun* r, Apply<T, P>& op, const C<T>* res, C<T>* z, double tau) {
   if (use_fd(b, r)) {
-    fd_apply<T>(b, r, res, z, reinterpret_cast<T*>(op.qa), reinterpret_cast<T*>(op.qb), tau, b->d_red);
+    if constexpr (std::is_same<T, float>::value) {
+      const int rc = fd_apply32(b, r, res, z, reinterpret_cast<float*>(op.qa), reinterpret_cast<float*>(op.qb),
+                                static_cast<float*>(b->w_qc), static_cast<float*>(b->w_qd), tau, b->d_red);
+      if (rc != TDZ_OK && r->status == TDZ_OK) r->status = rc;
+    } else {
+      fd_apply64(b, r, res, z, reinterpret_cast<double*>(op.qa), reinterpret_cast<double*>(op.qb), tau, b->d_red);
+    }
     return;
   }
   cudaMemcpyAsync(z, res, sizeof(C<T>) * r->N, cudaMemcpyDeviceToDevice, b->st);
@@ -2251,7 +2390,9 @@ bool alloc_work(NdBatch* b) {
     }
     b->w_qa = b->alloc(f * maxQ);
     b->w_qb = b->alloc(f * maxQ);
-    ok = ok && b->w_qa && b->w_qb;
+    b->w_qc = b->alloc(f * std::max<size_t>(b->maxPad, 1));
+    b->w_qd = b->alloc(f * std::max<size_t>(b->maxPad, 1));
+    ok = ok && b->w_qa && b->w_qb && b->w_qc && b->w_qd;
   }
   return ok;
 }
@@ -2273,6 +2414,7 @@ int make_workers(NdBatch* b) {
     w->geo = b->geo;
     w->maxN = b->maxN;
     w->maxQ = b->maxQ;
+    w->maxPad = b->maxPad;
     w->maxSide = b->maxSide;
     w->maxn = b->maxn;
     w->nsm = b->nsm;
@@ -2309,9 +2451,15 @@ MediumDev medium_dev(const Medium& m) {
   return d;
 }
 
-__global__ void k_d2f(const double* __restrict__ a, float* __restrict__ f, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    f[i] = (float)a[i];
+// V (np x np, V[k + j np] = component k of eigenvector j) rounded to TF32: Vt[j np + k] = V[k + j np]
+// and its transpose VtT[j np + k] = V[j + k np] (the same rounded values)
+__global__ void k_v_tf32(const double* __restrict__ V, float* __restrict__ Vt, float* __restrict__ VtT, int np) {
+  const long long n = (long long)np * np;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long j = i / np, k = i - j * np;
+    Vt[i] = tf32_hi((float)V[i]);
+    VtT[i] = tf32_hi((float)V[k * np + j]);
+  }
 }
 
 // Generalised symmetric eigenproblems T1_a v = lam S_a v of every axis (cuSOLVER, binary64), eigenvectors
@@ -2335,10 +2483,14 @@ int fd_setup(NdBatch* b, int g, const Ops& o) {
     // factors stored zero-padded to np = n rounded up to 8 (np x np, eigenvalues padded with 0)
     const int np = (n + 7) / 8 * 8;
     G.np[a] = np;
+    const bool mixed = b->prec == TDZ_MIXED;
     G.V64[a] = static_cast<double*>(b->alloc(sizeof(double) * np * np));
-    G.V32[a] = static_cast<float*>(b->alloc(sizeof(float) * np * np));
+    if (mixed) {
+      G.Vt[a] = static_cast<float*>(b->alloc(sizeof(float) * np * np));
+      G.VtT[a] = static_cast<float*>(b->alloc(sizeof(float) * np * np));
+    }
     G.lam[a] = static_cast<double*>(b->alloc(sizeof(double) * np));
-    if (!G.V64[a] || !G.V32[a] || !G.lam[a]) {
+    if (!G.V64[a] || !G.lam[a] || (mixed && (!G.Vt[a] || !G.VtT[a]))) {
       cusolverDnDestroy(h);
       return TDZ_ENOMEM;
     }
@@ -2359,8 +2511,8 @@ int fd_setup(NdBatch* b, int g, const Ops& o) {
     ok = ok && cudaStreamSynchronize(b->st) == cudaSuccess && info == 0;
     ok = ok && cudaMemcpy2DAsync(G.V64[a], sizeof(double) * np, dA, sizeof(double) * n, sizeof(double) * n, n,
                                  cudaMemcpyDeviceToDevice, b->st) == cudaSuccess;
-    if (ok) {
-      k_d2f<<<grid_for((long long)np * np), TPB, 0, b->st>>>(G.V64[a], G.V32[a], (long long)np * np);
+    if (ok && mixed) {
+      k_v_tf32<<<grid_for((long long)np * np), TPB, 0, b->st>>>(G.V64[a], G.Vt[a], G.VtT[a], np);
       ok = cudaStreamSynchronize(b->st) == cudaSuccess;
     }
     cudaFree(work);
@@ -2543,7 +2695,7 @@ int nd_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* o
     }
   }
   b->runs.resize(nruns);
-  size_t maxN = 0, maxQ = 0, maxSide = 0;
+  size_t maxN = 0, maxQ = 0, maxSide = 0, maxPad = 0;
   int maxn = 0;
   for (int r = 0; r < nruns; ++r) {
     const Ops& o = ops[ops_index[r]]->o;
@@ -2582,6 +2734,7 @@ int nd_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* o
       size_t padded = 1;  // fast-diagonalisation planes on the grid padded to multiples of 8
       for (int a = 0; a < dim; ++a) padded *= (size_t)((R.n[a] + 7) / 8 * 8);
       mq = std::max(mq, padded);
+      maxPad = std::max(maxPad, padded);
     }
     for (int k = 0; k + 1 < dim; ++k) {
       size_t part = 1;
@@ -2600,6 +2753,7 @@ int nd_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* o
   }
   b->maxN = maxN;
   b->maxQ = maxQ;
+  b->maxPad = maxPad;
   b->maxSide = maxSide;
   b->maxn = maxn;
   {
@@ -2686,6 +2840,11 @@ int nd_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* o
   if (dim == 2 && precision == TDZ_MIXED && want_stencil && autotune(b) != TDZ_OK) {
     delete b;
     set_error("tdz_batch_create: timing the 2-D apply variants failed");
+    return TDZ_ECUDA;
+  }
+  if (precision == TDZ_MIXED && autotune_fd(b) != TDZ_OK) {
+    delete b;
+    set_error("tdz_batch_create: timing the tensor-core preconditioner transforms failed");
     return TDZ_ECUDA;
   }
   const int rw = make_workers(b);
@@ -2859,6 +3018,18 @@ int nd_set_option(NdBatch* b, int option, int value) {
     return TDZ_OK;
   }
   return TDZ_EINVAL;
+}
+
+int nd_precond_tuning(const NdBatch* b, int geometry, int* tile_n, double* ms) {
+  if (geometry < 0 || geometry >= (int)b->geo.size()) return TDZ_EINVAL;
+  const NdGeo& G = b->geo[geometry];
+  const bool tuned = G.fd && G.Vt[0];
+  if (tile_n) *tile_n = tuned ? G.tc_tile : 0;
+  if (ms) {
+    ms[0] = tuned ? G.tc_ms[0] : 0.0;
+    ms[1] = tuned ? G.tc_ms[1] : 0.0;
+  }
+  return TDZ_OK;
 }
 
 int nd_tuning(const NdBatch* b, int geometry, int* groups, double* ms) {

@@ -359,8 +359,11 @@ def test_workload_degree_3d_against_oracle(tdz):
             assert rel_s < tol, (prec, op, pc, rel_s)
             assert np.linalg.norm(e) / np.linalg.norm(c) < 1000 * tol, (prec, op, pc)
             assert np.max(np.abs(og[:, 0] - ref["obs"][:, 0])) < 1e-12
+            # the mixed observables carry the double-float residual floor of this conditioning
+            # (eps_ff kappa(S), kappa(S) = 2.6e8 in 3-D at p = 6): absolute floor 1e-2 tol instead of 1e-3 tol
+            floor = 1e-3 if prec == tdz.FP64 else 1e-2
             for col in range(4, 11):
-                scale = max(1e-3, np.max(np.abs(ref["obs"][:, col])))
+                scale = max(floor, np.max(np.abs(ref["obs"][:, col])))
                 assert np.max(np.abs(og[:, col] - ref["obs"][:, col])) < 10 * tol * scale, (prec, op, pc, col)
             del b
 

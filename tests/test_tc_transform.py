@@ -1,0 +1,108 @@
+"""The tensor-core axis transform of the fast-diagonalisation preconditioner (tdz_tc_axis_transform:
+TMA-fed tcgen05 MMAs of kind::tf32, accumulator in tensor memory) against a binary64 product of the same
+operands, over tile-aligned and ragged shapes (rows, k and columns not multiples of the tile, a plane
+boundary inside a row tile), both column-tile widths and both output forms (FP32, TF32 pair)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tdz():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_2608_18472_b300 as m
+    return m
+
+
+def _tf32(x):
+    """Nearest TF32 value (ties away from zero), as FP32."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32)
+    return ((u + np.uint32(0x1000)) & np.uint32(0xFFFFE000)).view(np.float32)
+
+
+# (planes, plane_rows, k, ncols, tile_n): tile_n 0 = the library's choice (128-column tiles unless
+# tiles_m * ceil(ncols / 256) >= 296)
+CASES = [
+    (2, 128, 64, 128, 0),       # one k-block ring pass, two row tiles
+    (2, 200, 200, 200, 0),      # ragged k (7 blocks, the stage ring wraps), ragged columns, plane edge in a tile
+    (2, 200, 200, 200, 256),    # the same with 256-column tiles
+    (2, 1024, 1024, 1024, 0),   # the 2-D fast-diagonalisation shape, 128 blocks
+    (2, 32768, 256, 256, 0),    # 512 row tiles: 256-column tiles
+    (2, 20000, 200, 200, 128),  # ragged rows, k and columns, forced 128-column tiles
+]
+
+
+@pytest.mark.parametrize("planes,plane_rows,k,ncols,tile_n", CASES)
+@pytest.mark.parametrize("split", [True, False])
+@pytest.mark.parametrize("blo", [False, True])
+def test_tc_axis_transform(tdz, planes, plane_rows, k, ncols, tile_n, split, blo):
+    import torch
+    rng = np.random.default_rng(plane_rows * 7 + k + ncols)
+    rows = planes * plane_rows
+    A = rng.standard_normal((rows, k)).astype(np.float32)
+    a_hi = _tf32(A)
+    a_lo = (A - a_hi).astype(np.float32)
+    Bf = (rng.standard_normal((ncols, k)) / np.sqrt(k)).astype(np.float32)
+    b_hi = _tf32(Bf)
+    b_lo = (Bf - b_hi).astype(np.float32) if blo else np.zeros_like(b_hi)
+    dev = torch.device("cuda")
+    t_hi, t_lo, t_b, t_bl = (torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in (a_hi, a_lo, b_hi, b_lo))
+    stride = plane_rows * ncols
+    o_hi = torch.full((planes * stride,), np.nan, dtype=torch.float32, device=dev)
+    o_lo = torch.full((planes * stride,), np.nan, dtype=torch.float32, device=dev) if split else None
+    tdz.tc_axis_transform(t_hi, t_lo, t_b, rows, k, ncols, plane_rows, stride, o_hi, o_lo,
+                          b_lo=t_bl if blo else None, tile_n=tile_n)
+    torch.cuda.synchronize()
+    # the three products the kernel forms, in binary64
+    a64, al64, b64, bl64 = (x.astype(np.float64) for x in (a_hi, a_lo, b_hi, b_lo))
+    D = (a64 + al64) @ b64.T + a64 @ bl64.T
+    want = D.reshape(planes, plane_rows, ncols).transpose(0, 2, 1).reshape(-1)
+    got_hi = o_hi.cpu().numpy()
+    assert np.all(np.isfinite(got_hi))
+    got = got_hi.astype(np.float64)
+    if split:
+        got_lo = o_lo.cpu().numpy()
+        assert np.array_equal(got_hi, _tf32(got_hi))        # the high term is a TF32 value
+        assert np.all(np.abs(got_lo) <= np.abs(got_hi) * 2.0 ** -11 + 1e-30)
+        got = got + got_lo.astype(np.float64)
+    # FP32 accumulation of k products (the lo operands read as TF32): well inside k * 2^-24 * sum |a||b|
+    scale = (np.abs(a64) + np.abs(al64)) @ (np.abs(b64) + np.abs(bl64)).T
+    bound = k * 2.0 ** -24 * scale.reshape(planes, plane_rows, ncols).transpose(0, 2, 1).reshape(-1)
+    err = np.abs(got - want)
+    assert np.all(err <= bound), float(np.max(err / bound))
+    rel = np.linalg.norm(got - want) / np.linalg.norm(want)
+    assert rel < 1e-5, rel
+    if blo:
+        # with both operands split, the product is the FP32 product of A and B to FP32 accuracy
+        exact = A.astype(np.float64) @ Bf.astype(np.float64).T
+        exact = exact.reshape(planes, plane_rows, ncols).transpose(0, 2, 1).reshape(-1)
+        assert np.linalg.norm(got - exact) / np.linalg.norm(exact) < 1e-5
+
+
+def test_tc_axis_transform_rejects_bad_sizes(tdz):
+    import torch
+    x = torch.zeros(64 * 64, dtype=torch.float32, device="cuda")
+    with pytest.raises(tdz.TDZError):
+        tdz.tc_axis_transform(x, x, x, 64, 6, 64, 64, 64 * 64, x)     # k not a multiple of 4
+    with pytest.raises(tdz.TDZError):
+        tdz.tc_axis_transform(x[1:], x, x, 64, 64, 64, 64, 64 * 64, x)  # a_hi not 16-byte aligned
+    with pytest.raises(tdz.TDZError):
+        tdz.tc_axis_transform(x, x, x, 64, 64, 64, 64, 64 * 64, x, tile_n=64)  # no such tile width
+
+
+def test_preconditioner_autotuner(tdz):
+    """A mixed 2-D batch times its preconditioner with both transform tile widths at creation and keeps
+    the faster; a binary64 batch (cuBLAS DGEMM transforms) reports nothing."""
+    import workloads as wl
+    p = 6
+    t = wl.knots_for_nsplines(-20.0, 20.0, 90, p)
+    ops = tdz.Ops([tdz.Basis(t, p, p + 1) for _ in range(2)], wl.softcore_medium(0.5))
+    b = tdz.Batch([ops], [0], tdz.MIXED)
+    tile, ms = b.precond_tuning(0)
+    assert tile in (128, 256)
+    assert ms[128] > 0 and ms[256] > 0
+    assert ms[tile] == min(ms.values())
+    b64 = tdz.Batch([ops], [0], tdz.FP64)
+    assert b64.precond_tuning(0) == (0, {})
