@@ -245,15 +245,19 @@ def cpu_leg(tdz, args):
     return cpu, acc
 
 
-def _nd_time(tdz, name, ops, run_ops, c0s, fields, dt, nsteps, extra):
-    """Time `nsteps` steps of a 2-D/3-D batch in both precisions after one warm-up step."""
+def _nd_time(tdz, name, ops, run_ops, c0s, fields, dt, nsteps, extra, fp64_steps=None):
+    """Time `nsteps` steps of a 2-D/3-D batch in mixed precision and `fp64_steps` (default: the same) in
+    binary64, each after one warm-up step; the rel-L2 comparison of the two is taken after the binary64
+    window (the mixed run is repeated to that length first when the windows differ)."""
     import torch
+    fp64_steps = nsteps if fp64_steps is None else fp64_steps
     res = {"workload": name, "runs": len(run_ops), "coefficients": int(sum(ops[g].n for g in run_ops)),
-           "steps": nsteps}
+           "steps": {"mixed": nsteps, "fp64": fp64_steps}}
     res.update(extra)
     dim = fields.shape[2]
     states = {}
     for label, prec in (("mixed", tdz.MIXED), ("fp64", tdz.FP64)):
+        k = nsteps if label == "mixed" else fp64_steps
         t0 = time.perf_counter()
         b = tdz.Batch(ops, run_ops, prec)
         t_create = time.perf_counter() - t0
@@ -267,22 +271,26 @@ def _nd_time(tdz, name, ops, run_ops, c0s, fields, dt, nsteps, extra):
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        b.propagate(np.ascontiguousarray(fields[:, :nsteps + 1]), dt, 0, nsteps)
+        b.propagate(np.ascontiguousarray(fields[:, :k + 1]), dt, 0, k)
         e1.record()
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / nsteps
+        ms = e0.elapsed_time(e1) / k
         drift, st_bad = 0.0, 0
         for i in range(len(run_ops)):
             o, st = b.observe(i)
             drift = max(drift, float(np.max(np.abs(o[:, -1] - o[0, -1]))))
             st_bad += int(st != 0)
         _, solves = b.refine_stats()
-        nsteps_runs = nsteps * len(run_ops)
+        nsteps_runs = k * len(run_ops)
         res[label] = {"value": res["coefficients"] / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
                       "runs_not_ok": st_bad, "norm_drift": drift,
                       "krylov_iterations_per_run_step": (b.krylov_stats() - it0) / nsteps_runs,
                       "solves_per_run_step": (solves - solves0) / nsteps_runs, "device_gb": b.device_bytes / 1e9,
                       "create_s": t_create}
+        if label == "mixed" and k != fp64_steps:  # the state after the binary64 window, for the comparison
+            for i, c in enumerate(c0s):
+                b.set_state(i, c)
+            b.propagate(np.ascontiguousarray(fields[:, :fp64_steps + 1]), dt, 0, fp64_steps)
         states[label] = [b.get_state(i) for i in range(len(run_ops))]
         if label == "mixed" and dim == 2:
             res["fused_apply"] = _apply_roofline(tdz, b, ops, run_ops)
@@ -332,26 +340,29 @@ TF32_PER_BF16 = 1.1 / 2.25
 
 def _precond_roofline(tdz, b, ops, run_ops):
     """Tensor roofline of the mixed fast-diagonalisation preconditioner for the largest geometry, from the
-    autotuner's CUDA-event timing of one whole apply (TF32 split, 2 dim tcgen05 axis transforms, scaling,
-    merge; batch creation, best of three). Tensor work per apply: for each axis a and each of the two
-    passes, 2 TF32 products x 2 flops x (2 Np / np_a rows) x np_a columns x np_a (k) = 8 Np np_a, i.e.
+    autotuner's CUDA-event timing of one whole apply (split, 2 dim tcgen05 axis transforms, scaling, merge;
+    batch creation, best of three, four variants). Tensor work per apply: for each axis a and each of the
+    two passes, 2 TF32 products x 2 flops x (2 Np / np_a rows) x np_a columns x np_a (k) = 8 Np np_a, i.e.
     16 Np sum_a np_a; the algorithmic (one FP32 product) flops are half of that. Peak: the measured BF16
     rate x the nominal TF32/BF16 ratio."""
     peaks = _measured_peaks()
     g = max(set(run_ops), key=lambda k: ops[k].n)
-    tile, ms = b.precond_tuning(g)
-    if not tile:
+    v, ms = b.precond_tuning(g)
+    if v < 0:
         return None
     npad = [(n + 7) // 8 * 8 for n in ops[g].shape]
     Np = int(np.prod(npad))
     tflop = 16.0 * Np * sum(npad) / 1e12
-    t = ms[tile] * 1e-3
+    t = ms[v] * 1e-3
     peak = peaks["bf16_tflops"] * TF32_PER_BF16
-    return {"kernel": f"k_tc_axis<{tile}, false> x {2 * len(npad)} + split/scale/merge", "padded_shape": npad,
+    names = [f"{128 << (c & 1)}-column tiles, " + ("split in shared memory" if c & 2 else "TF32 pairs in memory")
+             for c in range(4)]
+    return {"kernel": f"k_tc_axis<{128 << (v & 1)}, false, {'true' if v & 2 else 'false'}> x {2 * len(npad)}"
+                      " + split/scale/merge", "padded_shape": npad, "variant": names[v],
             "bound": "tensor", "achieved": tflop / t, "peak": peak, "unit": "TFLOP/s", "frac": tflop / t / peak,
             "peak_source": peaks["source"] + " bf16 x nominal tf32/bf16", "tensor_tflop_per_apply": tflop,
-            "algorithmic_fp32_tflop_per_apply": tflop / 2, "ms_per_apply": ms[tile],
-            "tile_ms": {str(k): v for k, v in ms.items()}}
+            "algorithmic_fp32_tflop_per_apply": tflop / 2, "ms_per_apply": ms[v],
+            "variants_ms": {names[c]: ms[c] for c in range(4)}}
 
 
 def _gauss_state(knots, p, dim):
@@ -363,39 +374,51 @@ def _gauss_state(knots, p, dim):
     return (c / np.linalg.norm(c)).astype(complex)
 
 
+# timed steps (mixed, binary64) of the 2-D/3-D legs by default
+ND_WINDOWS = {"2d": (200, 20), "dots": (20, 4), "3d": (20, 3)}
+
+
 def nd_legs(tdz, nsteps, which, n2d=1024, n3d=256):
-    """2-D/3-D workloads beside the 1-D batch:
+    """2-D/3-D workloads beside the 1-D batch, timed over ND_WINDOWS (mixed, binary64) steps unless
+    `nsteps` (> 0) sets both windows:
     softcore_atom_2d: V = -1/sqrt(r^2+0.5) on [-150,150]^2, 1024 order-7 splines per axis (1.04 M
       coefficients), 800 nm 1e14 W/cm^2 sin^2 pulse, dt = 0.05;
     dot_batch_2d: 64 elliptical GaAs dots (16 M coefficients), 10 um, 8 intensities x 8 CEPs, dt = 0.5;
     softcore_atom_3d: [-100,100]^3, 256 order-6 splines per axis (16.4 M coefficients), elliptical
       (0.3) 800 nm pulse, dt = 0.05."""
+    def win(leg):
+        return (nsteps, nsteps) if nsteps else ND_WINDOWS[leg]
+
     out = {}
     if "2d" in which:
+        km, kd = win("2d")
         p, t = 7, wl.knots_for_nsplines(-150.0, 150.0, n2d, 7)
         ops = tdz.Ops([tdz.Basis(t, p, p + 1) for _ in range(2)], wl.softcore_medium(0.5))
         dt = 0.05
-        f = wl.sin2_pulse(wl.time_grid(dt, nsteps + 1), wl.e0_from_intensity(1e14), wl.omega_from_nm(800.0), 4.0,
+        f = wl.sin2_pulse(wl.time_grid(dt, max(km, kd) + 1), wl.e0_from_intensity(1e14), wl.omega_from_nm(800.0), 4.0,
                           dim=2)
-        out["config_2d"] = _nd_time(tdz, "softcore_atom_2d", [ops], [0], [_gauss_state(t, p, 2)], f[None], dt, nsteps,
+        out["config_2d"] = _nd_time(tdz, "softcore_atom_2d", [ops], [0], [_gauss_state(t, p, 2)], f[None], dt, km,
                                     {"operator": "assembled (2p+1)^2 stencil",
-                                     "preconditioner": "fast diagonalisation (tcgen05 TF32 axis transforms)"})
+                                     "preconditioner": "fast diagonalisation (tcgen05 TF32 axis transforms)"}, kd)
     if "dots" in which:
-        wk = wl.dot_batch(nsteps=nsteps + 1)
+        km, kd = win("dots")
+        wk = wl.dot_batch(nsteps=max(km, kd) + 1)
         ops = [tdz.Ops([tdz.Basis(k, r.degree, r.nquad) for k in r.knots], r.medium) for r in wk.runs]
         c0s = [_gauss_state(r.knots[0], r.degree, 2) for r in wk.runs]
         fields = np.stack([r.field for r in wk.runs])
-        out["config_dots_2d"] = _nd_time(tdz, "dot_batch_2d", ops, list(range(len(ops))), c0s, fields, wk.dt, nsteps,
+        out["config_dots_2d"] = _nd_time(tdz, "dot_batch_2d", ops, list(range(len(ops))), c0s, fields, wk.dt, km,
                                          {"operator": "assembled stencil (variable mass + step potential)",
-                                          "preconditioner": "fast diagonalisation, mean 1/m"})
+                                          "preconditioner": "fast diagonalisation, mean 1/m"}, kd)
     if "3d" in which:
+        km, kd = win("3d")
         p, t = 6, wl.knots_for_nsplines(-100.0, 100.0, n3d, 6)
         ops = tdz.Ops([tdz.Basis(t, p, p + 1) for _ in range(3)], wl.softcore_medium(0.5))
         dt = 0.05
-        f = wl.sin2_pulse(wl.time_grid(dt, nsteps + 1), 0.05, wl.omega_from_nm(800.0), 4.0, ellipticity=0.3, dim=3)
-        out["config_3d"] = _nd_time(tdz, "softcore_atom_3d", [ops], [0], [_gauss_state(t, p, 3)], f[None], dt, nsteps,
+        f = wl.sin2_pulse(wl.time_grid(dt, max(km, kd) + 1), 0.05, wl.omega_from_nm(800.0), 4.0, ellipticity=0.3,
+                          dim=3)
+        out["config_3d"] = _nd_time(tdz, "softcore_atom_3d", [ops], [0], [_gauss_state(t, p, 3)], f[None], dt, km,
                                     {"operator": "Gauss-point sum factorisation",
-                                     "preconditioner": "fast diagonalisation (tcgen05 TF32 axis transforms)"})
+                                     "preconditioner": "fast diagonalisation (tcgen05 TF32 axis transforms)"}, kd)
     return out
 
 
@@ -480,7 +503,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--cpu-workers", type=int, default=16, help="oracle processes (one run each), <= nproc")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--nd-steps", type=int, default=2)
+    ap.add_argument("--nd-steps", type=int, default=0,
+                    help="timed steps of each 2-D/3-D leg in both precisions (0: the per-leg windows ND_WINDOWS)")
     ap.add_argument("--nd-legs", default="2d,dots,3d", help="comma list of 2d, dots, 3d (empty: none)")
     ap.add_argument("--nd-2d-splines", type=int, default=1024, help="splines per axis of the 2-D atom")
     ap.add_argument("--nd-3d-splines", type=int, default=256, help="splines per axis of the 3-D atom")
@@ -642,7 +666,7 @@ def main():
     # a few steps in both precisions (Kronecker + Gauss-point operator, preconditioned COCG)
     if rank == 0 and args.h2p_steps > 0:
         line["config_h2p_1d"] = h2p_leg(tdz, args.h2p_steps)
-    if rank == 0 and args.nd_steps > 0 and args.nd_legs:
+    if rank == 0 and args.nd_steps >= 0 and args.nd_legs:
         line.update(nd_legs(tdz, args.nd_steps, args.nd_legs.split(","), args.nd_2d_splines, args.nd_3d_splines))
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"], line["accuracy"]["sample_vs_oracle"] = cpu_leg(tdz, args)

@@ -259,13 +259,15 @@ int  tdz_batch_set_option(tdz_batch* b, int option, int value);
  * Errors: TDZ_EINVAL (bad handle or geometry index). */
 int  tdz_batch_tuning(const tdz_batch* b, int geometry, int* groups, double* ms);
 /* Autotuner result for the fast-diagonalisation preconditioner of geometry `geometry` of a 2-D/3-D
- * mixed batch: at creation one whole preconditioner apply (TF32 split, the tensor-core axis transforms
- * of tdz_tc_axis_transform, eigenvalue scaling, merge) is timed with 128- and 256-column transform
- * tiles on the batch's own buffers (CUDA events, best of three) and the faster width is kept.
- * tile_n (host, optional): the chosen width (0 when the geometry has no fast diagonalisation or the
- * batch is not mixed); ms (host, optional, 2 doubles): ms per preconditioner apply with 128 and 256.
- * Errors: TDZ_EINVAL (bad handle or geometry index). */
-int  tdz_batch_precond_tuning(const tdz_batch* b, int geometry, int* tile_n, double* ms);
+ * mixed batch: at creation one whole preconditioner apply (the tensor-core axis transforms of
+ * tdz_tc_axis_transform with the split, eigenvalue scaling and merge around them) is timed on the
+ * batch's own buffers (CUDA events, best of three) in four variants and the fastest is kept:
+ * variant v uses 256-column transform tiles if bit 0 is set (else 128) and splits the data into TF32
+ * pairs inside the transform, in shared memory, if bit 1 is set (else the kernels around the
+ * transforms write the pairs to memory). variant (host, optional): the chosen v (-1 when the geometry
+ * has no fast diagonalisation or the batch is not mixed); ms (host, optional, 4 doubles): ms per
+ * preconditioner apply of variants 0..3. Errors: TDZ_EINVAL (bad handle or geometry index). */
+int  tdz_batch_precond_tuning(const tdz_batch* b, int geometry, int* variant, double* ms);
 /* Total Krylov iterations of all runs since the batch was created (2-D/3-D; 0 in 1-D, whose
  * solve is direct). Synchronises the batch stream. */
 int  tdz_krylov_stats(const tdz_batch* b, double* iterations);
@@ -344,7 +346,8 @@ int  tdz_device_rates(double* fp32_flops, double* fp64_flops);
  * (the contracted index moves from fastest to slowest). With out_lo non-NULL the result is stored as
  * a TF32 pair: out_hi = D rounded to TF32 (nearest, ties away), out_lo = D - out_hi; with out_lo NULL
  * out_hi = D in FP32. The hi arrays should hold TF32 values and the lo arrays the FP32 remainders
- * (every operand is read as TF32: the low 13 bits of each FP32 pattern are ignored). tile_n: 0 (the
+ * (every operand is read as TF32: the low 13 bits of each FP32 pattern are ignored). With a_lo NULL,
+ * a_hi holds the data in FP32 and each block splits its tiles into the pair in shared memory. tile_n: 0 (the
  * library's choice), 128 or 256 columns per block. All pointers are device memory owned by the caller,
  * the operands 16-byte aligned; k must be a multiple of 4. Synchronises the stream. Errors:
  * TDZ_EINVAL (sizes, alignment, tile_n), TDZ_ECUDA (launch failure, or a pipeline wait that ran out

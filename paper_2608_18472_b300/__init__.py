@@ -260,8 +260,8 @@ def tc_axis_transform(a_hi, a_lo, b, rows: int, k: int, ncols: int, plane_rows: 
                       out_lo=None, b_lo=None, tile_n: int = 0, stream: Optional[int] = None):
     """One fast-diagonalisation axis transform on the tensor cores (tdz_tc_axis_transform). The arrays are
     float32 device tensors: a_hi, a_lo [rows, k], b (and b_lo) [ncols, k]; the result goes to out_hi (and
-    out_lo)."""
-    _check(_lib.tdz_tc_axis_transform(_vp(_ptr(a_hi)), _vp(_ptr(a_lo)), int(rows), int(k), _vp(_ptr(b)),
+    out_lo). With a_lo None, a_hi is the FP32 data and the kernel splits it in shared memory."""
+    _check(_lib.tdz_tc_axis_transform(_vp(_ptr(a_hi)), _vp(_ptr(a_lo)) if a_lo is not None else None, int(rows), int(k), _vp(_ptr(b)),
                                       _vp(_ptr(b_lo)) if b_lo is not None else None, int(ncols), int(plane_rows),
                                       int(plane_stride), _vp(_ptr(out_hi)),
                                       _vp(_ptr(out_lo)) if out_lo is not None else None, int(tile_n),
@@ -421,13 +421,13 @@ class Batch:
 
     def precond_tuning(self, geometry: int = 0):
         """Autotuner result of the tensor-core fast-diagonalisation preconditioner of a 2-D/3-D mixed batch
-        for one geometry: (chosen column-tile width, {width: measured ms per preconditioner apply});
-        (0, {}) where it does not apply."""
-        t = C.c_int()
-        ms = np.zeros(2)
-        _check(_lib.tdz_batch_precond_tuning(self._h, int(geometry), C.byref(t), ms.ctypes.data_as(_dp)),
+        for one geometry: (chosen variant, [ms per preconditioner apply of variants 0..3]); variant bit 0 =
+        256-column tiles, bit 1 = TF32 split in shared memory. (-1, []) where it does not apply."""
+        v = C.c_int()
+        ms = np.zeros(4)
+        _check(_lib.tdz_batch_precond_tuning(self._h, int(geometry), C.byref(v), ms.ctypes.data_as(_dp)),
                "tdz_batch_precond_tuning")
-        return t.value, ({128: float(ms[0]), 256: float(ms[1])} if t.value else {})
+        return v.value, ([float(x) for x in ms] if v.value >= 0 else [])
 
     def krylov_stats(self) -> float:
         """Total Krylov iterations of all runs since creation (0 for 1-D batches)."""

@@ -2063,11 +2063,12 @@ int tdz_batch_tuning(const tdz_batch* b, int geometry, int* groups, double* ms) 
   return TDZ_OK;
 }
 
-int tdz_batch_precond_tuning(const tdz_batch* b, int geometry, int* tile_n, double* ms) {
+int tdz_batch_precond_tuning(const tdz_batch* b, int geometry, int* variant, double* ms) {
   if (!b || geometry < 0) return TDZ_EINVAL;
-  if (b->nd) return tdz::nd_precond_tuning(b->nd, geometry, tile_n, ms);
-  if (tile_n) *tile_n = 0;
-  if (ms) ms[0] = ms[1] = 0.0;
+  if (b->nd) return tdz::nd_precond_tuning(b->nd, geometry, variant, ms);
+  if (variant) *variant = -1;
+  if (ms)
+    for (int c = 0; c < 4; ++c) ms[c] = 0.0;
   return TDZ_OK;
 }
 

@@ -72,7 +72,7 @@ int nd_stats(const NdBatch* b, double* max_rel, double* solves, double* iters);
 void nd_set_refinement(NdBatch* b, double tol, int max_it);
 int nd_set_option(NdBatch* b, int option, int value);
 int nd_tuning(const NdBatch* b, int geometry, int* groups, double* ms);
-int nd_precond_tuning(const NdBatch* b, int geometry, int* tile_n, double* ms);
+int nd_precond_tuning(const NdBatch* b, int geometry, int* variant, double* ms);
 int nd_dim(const NdBatch* b);
 size_t nd_device_bytes(const NdBatch* b);
 

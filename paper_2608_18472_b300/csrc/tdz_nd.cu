@@ -1287,15 +1287,41 @@ __global__ void __launch_bounds__(32 * G, 1)
 // dimension is 32-byte aligned); padding entries are zero
 struct PadDims {
   int dim, n[3], np[3];
-  long long Np;  // padded size of one plane
+  long long Np;  // padded size of one plane (below 2^31: the index arithmetic below is 32-bit)
 };
+// padded plane index -> axis indices (j0 fastest)
+__device__ __forceinline__ void pad_index(const PadDims& d, unsigned i, int& j0, int& j1, int& j2) {
+  const unsigned n0 = (unsigned)d.np[0];
+  const unsigned t = i / n0;
+  j0 = (int)(i - t * n0);
+  if (d.dim > 1) {
+    const unsigned n1 = (unsigned)d.np[1];
+    const unsigned u = t / n1;
+    j1 = (int)(t - u * n1);
+    j2 = (int)u;
+  } else {
+    j1 = 0;
+    j2 = 0;
+  }
+}
+// state index -> padded plane index
+__device__ __forceinline__ unsigned pad_of_state(const PadDims& d, unsigned i) {
+  const unsigned n0 = (unsigned)d.n[0];
+  const unsigned t = i / n0;
+  const unsigned j0 = i - t * n0;
+  unsigned j1 = 0, j2 = 0;
+  if (d.dim > 1) {
+    const unsigned n1 = (unsigned)d.n[1];
+    j2 = t / n1;
+    j1 = t - j2 * n1;
+  }
+  return (j2 * (unsigned)d.np[1] + j1) * (unsigned)d.np[0] + j0;
+}
 template <class Tv, class Tp>
 __global__ void k_split(const C<Tv>* __restrict__ v, Tp* __restrict__ w, PadDims d) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < d.Np; i += (long long)gridDim.x * blockDim.x) {
-    const int j0 = (int)(i % d.np[0]);
-    const long long t = i / d.np[0];
-    const int j1 = d.dim > 1 ? (int)(t % d.np[1]) : 0;
-    const int j2 = d.dim > 2 ? (int)(t / d.np[1]) : 0;
+    int j0, j1, j2;
+    pad_index(d, (unsigned)i, j0, j1, j2);
     const bool in = j0 < d.n[0] && (d.dim < 2 || j1 < d.n[1]) && (d.dim < 3 || j2 < d.n[2]);
     if (in) {
       const C<Tv> a = v[((long long)j2 * d.n[1] + j1) * d.n[0] + j0];
@@ -1310,11 +1336,7 @@ __global__ void k_split(const C<Tv>* __restrict__ v, Tp* __restrict__ w, PadDims
 template <class Tv, class Tp>
 __global__ void k_merge(const Tp* __restrict__ w, C<Tv>* __restrict__ v, PadDims d, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const int j0 = (int)(i % d.n[0]);
-    const long long t = i / d.n[0];
-    const int j1 = d.dim > 1 ? (int)(t % d.n[1]) : 0;
-    const int j2 = d.dim > 2 ? (int)(t / d.n[1]) : 0;
-    const long long k = ((long long)j2 * d.np[1] + j1) * d.np[0] + j0;
+    const long long k = pad_of_state(d, (unsigned)i);
     v[i] = C<Tv>{(Tv)w[k], (Tv)w[d.Np + k]};
   }
 }
@@ -1326,11 +1348,7 @@ __global__ void k_merge_dot(const Tp* __restrict__ w, C<Tv>* __restrict__ v, Pad
   __shared__ double sh[32];
   double re = 0.0, im = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const int j0 = (int)(i % d.n[0]);
-    const long long t = i / d.n[0];
-    const int j1 = d.dim > 1 ? (int)(t % d.n[1]) : 0;
-    const int j2 = d.dim > 2 ? (int)(t / d.n[1]) : 0;
-    const long long k = ((long long)j2 * d.np[1] + j1) * d.np[0] + j0;
+    const long long k = pad_of_state(d, (unsigned)i);
     const C<Tv> z = C<Tv>{(Tv)w[k], (Tv)w[d.Np + k]};
     v[i] = z;
     const C<Tv> x = a[i];
@@ -1348,10 +1366,8 @@ __global__ void k_merge_dot(const Tp* __restrict__ w, C<Tv>* __restrict__ v, Pad
 __global__ void k_split_tf32(const C<float>* __restrict__ v, float* __restrict__ whi, float* __restrict__ wlo,
                              PadDims d) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < d.Np; i += (long long)gridDim.x * blockDim.x) {
-    const int j0 = (int)(i % d.np[0]);
-    const long long t = i / d.np[0];
-    const int j1 = d.dim > 1 ? (int)(t % d.np[1]) : 0;
-    const int j2 = d.dim > 2 ? (int)(t / d.np[1]) : 0;
+    int j0, j1, j2;
+    pad_index(d, (unsigned)i, j0, j1, j2);
     const bool in = j0 < d.n[0] && (d.dim < 2 || j1 < d.n[1]) && (d.dim < 3 || j2 < d.n[2]);
     C<float> a{0.f, 0.f};
     if (in) a = v[((long long)j2 * d.n[1] + j1) * d.n[0] + j0];
@@ -1363,7 +1379,7 @@ __global__ void k_split_tf32(const C<float>* __restrict__ v, float* __restrict__
   }
 }
 
-// in the eigenbasis (index j0 fastest): u /= 1 + i tm (lam0[j0] + lam1[j1] + lam2[j2])
+// in the eigenbasis (index j0 fastest): u /= 1 + i tm (lam0[j0] + lam1[j1] + lam2[j2]); binary64
 template <class Tp>
 __global__ void k_fd_scale(Tp* __restrict__ w, long long n, int dim, int n0, int n1, const double* __restrict__ l0,
                            const double* __restrict__ l1, const double* __restrict__ l2, double tm) {
@@ -1381,21 +1397,39 @@ __global__ void k_fd_scale(Tp* __restrict__ w, long long n, int dim, int n0, int
   }
 }
 
-// k_fd_scale for the tensor-core transforms: reads the FP32 planes w, writes the scaled values as
+// the same scaling in FP32 (eigenvalues in FP32), in place; the mixed preconditioner runs in FP32
+__global__ void k_fd_scale32(float* __restrict__ w, PadDims d, const float* __restrict__ l0,
+                             const float* __restrict__ l1, const float* __restrict__ l2, float tm) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < d.Np; i += (long long)gridDim.x * blockDim.x) {
+    int j0, j1, j2;
+    pad_index(d, (unsigned)i, j0, j1, j2);
+    float lam = l0[j0];
+    if (d.dim > 1) lam += l1[j1];
+    if (d.dim > 2) lam += l2[j2];
+    const float th = tm * lam;
+    const float g = 1.0f / fmaf(th, th, 1.0f);
+    const float a = w[i], b = w[d.Np + i];
+    w[i] = fmaf(th, b, a) * g;
+    w[d.Np + i] = fmaf(-th, a, b) * g;
+  }
+}
+
+// k_fd_scale32 for the tensor-core transforms: reads the FP32 planes w, writes the scaled values as
 // TF32 pairs (planes of hi in whi, of lo in wlo)
 __global__ void k_fd_scale_tf32(const float* __restrict__ w, float* __restrict__ whi, float* __restrict__ wlo,
-                                long long n, int dim, int n0, int n1, const double* __restrict__ l0,
-                                const double* __restrict__ l1, const double* __restrict__ l2, double tm) {
+                                PadDims d, const float* __restrict__ l0, const float* __restrict__ l1,
+                                const float* __restrict__ l2, float tm) {
+  const long long n = d.Np;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const int j0 = (int)(i % n0);
-    const long long t = i / n0;
-    double lam = l0[j0];
-    if (dim > 1) lam += l1[(int)(t % n1)];
-    if (dim > 2) lam += l2[(int)(t / n1)];
-    const double th = tm * lam;
-    const double g = 1.0 / (1.0 + th * th);
-    const double a = (double)w[i], b = (double)w[n + i];
-    const float xr = (float)((a + th * b) * g), xi = (float)((b - th * a) * g);
+    int j0, j1, j2;
+    pad_index(d, (unsigned)i, j0, j1, j2);
+    float lam = l0[j0];
+    if (d.dim > 1) lam += l1[j1];
+    if (d.dim > 2) lam += l2[j2];
+    const float th = tm * lam;
+    const float g = 1.0f / fmaf(th, th, 1.0f);
+    const float a = w[i], b = w[n + i];
+    const float xr = fmaf(th, b, a) * g, xi = fmaf(-th, a, b) * g;
     const float hr = tf32_hi(xr), hi = tf32_hi(xi);
     whi[i] = hr;
     whi[n + i] = hi;
@@ -1463,8 +1497,12 @@ struct NdGeo {
   // j (the forward transform V^T), VtT = its transpose (the inverse transform V)
   float* Vt[3] = {nullptr, nullptr, nullptr};
   float* VtT[3] = {nullptr, nullptr, nullptr};
-  int tc_tile = 0;                  // column-tile width of the transforms chosen by the autotuner (128 or 256)
-  float tc_ms[2] = {0.f, 0.f};      // its timings of one preconditioner apply with 128- and 256-column tiles
+  float* lam32[3] = {nullptr, nullptr, nullptr};  // the eigenvalues in FP32 (mixed batches)
+  // transform variant chosen by the autotuner: bit 0 = 256-column tiles (else 128), bit 1 = the data
+  // split into TF32 pairs in shared memory by the transform (else by the producing kernels, as pairs
+  // in memory); -1 = not tuned
+  int tc_variant = -1;
+  float tc_ms[4] = {0.f, 0.f, 0.f, 0.f};  // the autotuner's ms per preconditioner apply of variants 0..3
   double* lam[3] = {nullptr, nullptr, nullptr};
   double* W64 = nullptr;  // binary64 batches
   float* W32 = nullptr;   // mixed: inner FP32 solve
@@ -1917,39 +1955,65 @@ void fd_apply64(NdBatch* b, const NdRun* r, const C<double>* src, C<double>* dst
 // Mixed batches: the transforms run on the tensor cores (tc_axis_transform). Each contracts the
 // FASTEST axis of the current layout with the TF32-rounded factor (Vt forward, VtT inverse) and
 // writes the new index slowest, so after one transform per axis the original order is back. The data
-// enter every transform as a TF32 pair (hi, lo): the split kernel, the eigenvalue scaling and every
-// transform but the last of a pass write pairs. Rounding V once keeps M^-1 = Vt Lambda Vt^T complex
-// symmetric, as COCG requires; it is the preconditioner of V rounded to 11 significant bits.
-// w0..w3: planar scratch of 2 Np FP32 values each (two pairs). Returns TDZ_OK or the transform's error.
+// enter every transform as a TF32 pair (hi, lo), either split by the transform itself in shared
+// memory (FP32 planes in memory) or written as pairs by the split kernel, the eigenvalue scaling and
+// every transform but the last of a pass (variant bit 1 clear). Rounding V once keeps
+// M^-1 = Vt Lambda Vt^T complex symmetric, as COCG requires; it is the preconditioner of V rounded to
+// 11 significant bits. w0..w3: planar scratch of 2 Np FP32 values each (w2, w3 only for pairs in
+// memory). Returns TDZ_OK or the transform's error.
 int fd_apply32(NdBatch* b, const NdRun* r, const C<float>* src, C<float>* dst, float* w0, float* w1, float* w2,
                float* w3, double tau, double* dot) {
   const NdGeo& G = b->geo[r->geo];
   const PadDims d = pad_dims(G, r);
-  k_split_tf32<<<grid_for(d.Np), TPB, 0, b->st>>>(src, w0, w1, d);
-  float *hi = w0, *lo = w1, *ohi = w2, *olo = w3;
-  for (int pass = 0; pass < 2; ++pass) {
-    for (int a = 0; a < r->dim; ++a) {
-      const int ns = d.np[a];
-      const long long R = d.Np / ns;
-      const bool last = a == r->dim - 1;
-      const int rc = tc_axis_transform(hi, lo, 2 * R, ns, pass == 0 ? G.Vt[a] : G.VtT[a], nullptr, ns, R, d.Np, ohi,
-                                       last ? nullptr : olo, b->d_err, G.tc_tile, b->st);
-      if (rc != TDZ_OK) return rc;
-      std::swap(hi, ohi);
-      std::swap(lo, olo);
+  const int v = G.tc_variant < 0 ? 0 : G.tc_variant;
+  const int tile = (v & 1) ? 256 : 128;
+  const bool smem_split = (v & 2) != 0;
+  float* out = nullptr;  // the FP32 result of the last transform
+  if (smem_split) {
+    k_split<float, float><<<grid_for(d.Np), TPB, 0, b->st>>>(src, w0, d);
+    float *cur = w0, *nxt = w1;
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int a = 0; a < r->dim; ++a) {
+        const int ns = d.np[a];
+        const long long R = d.Np / ns;
+        const int rc = tc_axis_transform(cur, nullptr, 2 * R, ns, pass == 0 ? G.Vt[a] : G.VtT[a], nullptr, ns, R, d.Np,
+                                         nxt, nullptr, b->d_err, tile, b->st);
+        if (rc != TDZ_OK) return rc;
+        std::swap(cur, nxt);
+      }
+      if (pass == 0)
+        k_fd_scale32<<<grid_for(d.Np), TPB, 0, b->st>>>(cur, d, G.lam32[0], G.lam32[1], G.lam32[2],
+                                                        (float)(tau * r->mbar));
     }
-    // hi holds the FP32 result of the pass
-    if (pass == 0) {
-      k_fd_scale_tf32<<<grid_for(d.Np), TPB, 0, b->st>>>(hi, ohi, olo, d.Np, r->dim, d.np[0], d.np[1], G.lam[0],
-                                                         G.lam[1], G.lam[2], tau * r->mbar);
-      std::swap(hi, ohi);
-      std::swap(lo, olo);
+    out = cur;
+  } else {
+    k_split_tf32<<<grid_for(d.Np), TPB, 0, b->st>>>(src, w0, w1, d);
+    float *hi = w0, *lo = w1, *ohi = w2, *olo = w3;
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int a = 0; a < r->dim; ++a) {
+        const int ns = d.np[a];
+        const long long R = d.Np / ns;
+        const bool last = a == r->dim - 1;
+        const int rc = tc_axis_transform(hi, lo, 2 * R, ns, pass == 0 ? G.Vt[a] : G.VtT[a], nullptr, ns, R, d.Np, ohi,
+                                         last ? nullptr : olo, b->d_err, tile, b->st);
+        if (rc != TDZ_OK) return rc;
+        std::swap(hi, ohi);
+        std::swap(lo, olo);
+      }
+      // hi holds the FP32 result of the pass
+      if (pass == 0) {
+        k_fd_scale_tf32<<<grid_for(d.Np), TPB, 0, b->st>>>(hi, ohi, olo, d, G.lam32[0], G.lam32[1], G.lam32[2],
+                                                           (float)(tau * r->mbar));
+        std::swap(hi, ohi);
+        std::swap(lo, olo);
+      }
     }
+    out = hi;
   }
   if (dot)
-    k_merge_dot<float, float><<<grid_for(r->N), TPB, 0, b->st>>>(hi, dst, d, r->N, src, dot, b->gr);
+    k_merge_dot<float, float><<<grid_for(r->N), TPB, 0, b->st>>>(out, dst, d, r->N, src, dot, b->gr);
   else
-    k_merge<float, float><<<grid_for(r->N), TPB, 0, b->st>>>(hi, dst, d, r->N);
+    k_merge<float, float><<<grid_for(r->N), TPB, 0, b->st>>>(out, dst, d, r->N);
   return TDZ_OK;
 }
 
@@ -1958,15 +2022,15 @@ bool use_fd(const NdBatch* b, const NdRun* r) {
 }
 
 // Autotuner of the mixed fast-diagonalisation preconditioner: one whole apply (split, 2 dim tensor-core
-// transforms, scaling, merge) is timed with 128- and 256-column transform tiles on the batch's own
-// buffers (CUDA events, best of three after one warm-up) and the faster width is kept per geometry.
+// transforms, scaling, merge) is timed in each of the four transform variants (128- or 256-column
+// tiles; data split into TF32 pairs in shared memory or by the producing kernels) on the batch's own
+// buffers (CUDA events, best of three after one warm-up) and the fastest is kept per geometry.
 int autotune_fd(NdBatch* b) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
     if (e0) cudaEventDestroy(e0);
     return TDZ_ECUDA;
   }
-  const int cand[2] = {128, 256};
   int rc = TDZ_OK;
   for (size_t g = 0; g < b->geo.size() && rc == TDZ_OK; ++g) {
     NdGeo& G = b->geo[g];
@@ -1981,8 +2045,8 @@ int autotune_fd(NdBatch* b) {
     C<float>* y = static_cast<C<float>*>(b->w_q);
     float* w[4] = {static_cast<float*>(b->w_qa), static_cast<float*>(b->w_qb), static_cast<float*>(b->w_qc),
                    static_cast<float*>(b->w_qd)};
-    for (int c = 0; c < 2 && rc == TDZ_OK; ++c) {
-      G.tc_tile = cand[c];
+    for (int c = 0; c < 4 && rc == TDZ_OK; ++c) {
+      G.tc_variant = c;
       rc = fd_apply32(b, r, x, y, w[0], w[1], w[2], w[3], 0.025, nullptr);
       float tmin = 0.f;
       for (int k = 0; k < 3 && rc == TDZ_OK; ++k) {
@@ -1997,7 +2061,10 @@ int autotune_fd(NdBatch* b) {
       }
       G.tc_ms[c] = tmin;
     }
-    G.tc_tile = G.tc_ms[1] < G.tc_ms[0] ? 256 : 128;
+    int best = 0;
+    for (int c = 1; c < 4; ++c)
+      if (G.tc_ms[c] < G.tc_ms[best]) best = c;
+    G.tc_variant = best;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -2451,6 +2518,11 @@ MediumDev medium_dev(const Medium& m) {
   return d;
 }
 
+__global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ f, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    f[i] = (float)a[i];
+}
+
 // V (np x np, V[k + j np] = component k of eigenvector j) rounded to TF32: Vt[j np + k] = V[k + j np]
 // and its transpose VtT[j np + k] = V[j + k np] (the same rounded values)
 __global__ void k_v_tf32(const double* __restrict__ V, float* __restrict__ Vt, float* __restrict__ VtT, int np) {
@@ -2466,6 +2538,12 @@ __global__ void k_v_tf32(const double* __restrict__ V, float* __restrict__ Vt, f
 // S_a-orthonormal. On a solver failure the geometry keeps the line preconditioner (fd = false).
 int fd_setup(NdBatch* b, int g, const Ops& o) {
   NdGeo& G = b->geo[g];
+  {
+    // the split, scaling and merge kernels index a padded plane in 32 bits
+    long long planes = 1;
+    for (int a = 0; a < o.dim; ++a) planes *= (o.n[a] + 7) / 8 * 8;
+    if (planes >= (1LL << 31)) return TDZ_OK;  // fd stays false: the line preconditioner is used
+  }
   cusolverDnHandle_t h = nullptr;
   if (cusolverDnCreate(&h) != CUSOLVER_STATUS_SUCCESS) return TDZ_OK;
   cusolverDnSetStream(h, b->st);
@@ -2488,9 +2566,10 @@ int fd_setup(NdBatch* b, int g, const Ops& o) {
     if (mixed) {
       G.Vt[a] = static_cast<float*>(b->alloc(sizeof(float) * np * np));
       G.VtT[a] = static_cast<float*>(b->alloc(sizeof(float) * np * np));
+      G.lam32[a] = static_cast<float*>(b->alloc(sizeof(float) * np));
     }
     G.lam[a] = static_cast<double*>(b->alloc(sizeof(double) * np));
-    if (!G.V64[a] || !G.lam[a] || (mixed && (!G.Vt[a] || !G.VtT[a]))) {
+    if (!G.V64[a] || !G.lam[a] || (mixed && (!G.Vt[a] || !G.VtT[a] || !G.lam32[a]))) {
       cusolverDnDestroy(h);
       return TDZ_ENOMEM;
     }
@@ -2513,6 +2592,7 @@ int fd_setup(NdBatch* b, int g, const Ops& o) {
                                  cudaMemcpyDeviceToDevice, b->st) == cudaSuccess;
     if (ok && mixed) {
       k_v_tf32<<<grid_for((long long)np * np), TPB, 0, b->st>>>(G.V64[a], G.Vt[a], G.VtT[a], np);
+      k_to_f32<<<grid_for(np), TPB, 0, b->st>>>(G.lam[a], G.lam32[a], np);
       ok = cudaStreamSynchronize(b->st) == cudaSuccess;
     }
     cudaFree(work);
@@ -3020,15 +3100,13 @@ int nd_set_option(NdBatch* b, int option, int value) {
   return TDZ_EINVAL;
 }
 
-int nd_precond_tuning(const NdBatch* b, int geometry, int* tile_n, double* ms) {
+int nd_precond_tuning(const NdBatch* b, int geometry, int* variant, double* ms) {
   if (geometry < 0 || geometry >= (int)b->geo.size()) return TDZ_EINVAL;
   const NdGeo& G = b->geo[geometry];
-  const bool tuned = G.fd && G.Vt[0];
-  if (tile_n) *tile_n = tuned ? G.tc_tile : 0;
-  if (ms) {
-    ms[0] = tuned ? G.tc_ms[0] : 0.0;
-    ms[1] = tuned ? G.tc_ms[1] : 0.0;
-  }
+  const bool tuned = G.fd && G.Vt[0] && G.tc_variant >= 0;
+  if (variant) *variant = tuned ? G.tc_variant : -1;
+  if (ms)
+    for (int c = 0; c < 4; ++c) ms[c] = tuned ? G.tc_ms[c] : 0.0;
   return TDZ_OK;
 }
 

@@ -7,7 +7,8 @@
 //   D(m, j) = sum_k (A_hi(m, k) + A_lo(m, k)) (B(j, k) + B_lo(j, k)),   m < rows, j < ncols, k < K,
 //
 // with A (rows x K) and B (ncols x K) row-major, k fastest: both operands are K-major. Each operand is
-// a TF32 pair (hi = the value rounded to TF32, lo = the FP32 remainder), and the product keeps the
+// a TF32 pair (hi = the value rounded to TF32, lo = the FP32 remainder; A is either given as a pair
+// or given in FP32 and split in shared memory by the block), and the product keeps the
 // three terms A_hi B_hi + A_lo B_hi + A_hi B_lo (the published "3xTF32" scheme, Ootomo and Yokota,
 // 2022), so both operands enter with about 22 significant bits and the accumulation is FP32. Without
 // B_lo (B exact in TF32) the third product is skipped.
@@ -158,7 +159,9 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-template <int BN, bool BLO>
+// ASPLIT: A arrives as FP32 (one copy per stage, into the A_hi slot) and warps 2-5 split it in shared
+// memory (hi in place, lo into the A_lo slot) before the MMAs read it; otherwise A arrives as a pair.
+template <int BN, bool BLO, bool ASPLIT>
 __global__ void __launch_bounds__(THREADS, 1)
     k_tc_axis(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant__ CUtensorMap map_alo,
               const __grid_constant__ CUtensorMap map_b, const __grid_constant__ CUtensorMap map_blo, long long rows,
@@ -166,8 +169,9 @@ __global__ void __launch_bounds__(THREADS, 1)
               float* __restrict__ out_lo, int* __restrict__ err) {
   using G = Cfg<BN, BLO>;
   constexpr int S = G::STAGES;
+  constexpr uint32_t TX = G::STAGE_BYTES - (ASPLIT ? G::A_BYTES : 0u);  // bytes the copies of one stage bring
   extern __shared__ unsigned char dyn[];
-  __shared__ __align__(8) uint64_t bars[2 * S + 1];  // full[S], empty[S], accumulator ready
+  __shared__ __align__(8) uint64_t bars[3 * S + 1];  // full[S], empty[S], accumulator ready, split[S]
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   const uint32_t ring = (smem_u32(dyn) + 1023u) & ~1023u;
@@ -177,12 +181,14 @@ __global__ void __launch_bounds__(THREADS, 1)
   const long long m0 = (long long)(blockIdx.x / ntn) * BM;
   const int nk = (K + BK - 1) / BK;
   const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[S]), accum = smem_u32(&bars[2 * S]);
+  const uint32_t split0 = smem_u32(&bars[2 * S + 1]);
   volatile int* ab = &abort_flag;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
+      mbar_init(split0 + 8 * s, 4 * 32);  // every thread of warps 2-5
     }
     mbar_init(accum, 1);
     abort_flag = 0;
@@ -201,9 +207,9 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int s = kb % S;
         if (kb >= S && !wait_phase(empty0 + 8 * s, ((kb / S) - 1) & 1, ab)) break;
         const uint32_t st = ring + s * G::STAGE_BYTES;
-        mbar_expect_tx(full0 + 8 * s, G::STAGE_BYTES);
+        mbar_expect_tx(full0 + 8 * s, TX);
         tma_load_2d(st, &map_ahi, full0 + 8 * s, kb * BK, (int)m0);
-        tma_load_2d(st + G::A_BYTES, &map_alo, full0 + 8 * s, kb * BK, (int)m0);
+        if (!ASPLIT) tma_load_2d(st + G::A_BYTES, &map_alo, full0 + 8 * s, kb * BK, (int)m0);
         tma_load_2d(st + 2 * G::A_BYTES, &map_b, full0 + 8 * s, kb * BK, n0);
         if (BLO) tma_load_2d(st + 2 * G::A_BYTES + G::B_BYTES, &map_blo, full0 + 8 * s, kb * BK, n0);
         issued = kb + 1;
@@ -216,7 +222,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       constexpr uint32_t idesc = idesc_tf32(BM, BN);
       for (int kb = 0; kb < nk; ++kb) {
         const int s = kb % S;
-        if (!wait_phase(full0 + 8 * s, (kb / S) & 1, ab)) break;
+        if (!wait_phase((ASPLIT ? split0 : full0) + 8 * s, (kb / S) & 1, ab)) break;
         tc_fence_after();
         const uint32_t st = ring + s * G::STAGE_BYTES;
         const uint64_t dah = desc_sw128(st), dal = desc_sw128(st + G::A_BYTES), db = desc_sw128(st + 2 * G::A_BYTES);
@@ -233,6 +239,30 @@ __global__ void __launch_bounds__(THREADS, 1)
       mma_commit(accum);  // always: the read-back and the release wait on it
     }
   } else {
+    if (ASPLIT) {
+      // split every stage's A tile: thread t owns row t (128 bytes: eight 16-byte chunks, wherever the
+      // swizzle put them, so the layout is kept); hi in place, lo into the A_lo slot
+      const int t = threadIdx.x - 64;
+      unsigned char* gring = dyn + (ring - smem_u32(dyn));
+      for (int kb = 0; kb < nk; ++kb) {
+        const int s = kb % S;
+        bool ok = false;
+        if (lane == 0) ok = wait_phase(full0 + 8 * s, (kb / S) & 1, ab);
+        if (__shfl_sync(0xffffffffu, ok ? 1 : 0, 0) == 0) break;
+        float4* hi = reinterpret_cast<float4*>(gring + (size_t)s * G::STAGE_BYTES + (size_t)t * 128);
+        float4* lo = reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(hi) + G::A_BYTES);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const float4 v = hi[c];
+          const float4 h = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
+          hi[c] = h;
+          lo[c] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+        }
+        // the tensor cores (async proxy) read what these generic stores wrote
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(split0 + 8 * s) : "memory");
+      }
+    }
     const int q = warp & 3;  // the tensor-memory lane quadrant this warp may read
     bool go = false;
     if (lane == 0) go = wait_phase(accum, 0, ab) && !*ab;
@@ -338,7 +368,7 @@ bool make_map(CUtensorMap* m, const float* p, long long nrows, int K, int box_ro
   return true;
 }
 
-template <int BN, bool BLO>
+template <int BN, bool BLO, bool ASPLIT>
 cudaError_t launch(const CUtensorMap& ah, const CUtensorMap& al, const CUtensorMap& mb, const CUtensorMap& mbl,
                    long long rows, int K, int ncols, long long plane_rows, long long plane_stride, float* out_hi,
                    float* out_lo, int* err, long long blocks, cudaStream_t st) {
@@ -346,12 +376,29 @@ cudaError_t launch(const CUtensorMap& ah, const CUtensorMap& al, const CUtensorM
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
   std::call_once(once, [] {
-    attr = cudaFuncSetAttribute(k_tc_axis<BN, BLO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
+    attr = cudaFuncSetAttribute(k_tc_axis<BN, BLO, ASPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)G::SMEM);
   });
   if (attr != cudaSuccess) return attr;
-  k_tc_axis<BN, BLO><<<(unsigned)blocks, THREADS, G::SMEM, st>>>(ah, al, mb, mbl, rows, K, ncols, plane_rows,
-                                                                 plane_stride, out_hi, out_lo, err);
+  k_tc_axis<BN, BLO, ASPLIT><<<(unsigned)blocks, THREADS, G::SMEM, st>>>(ah, al, mb, mbl, rows, K, ncols, plane_rows,
+                                                                         plane_stride, out_hi, out_lo, err);
   return cudaGetLastError();
+}
+
+template <int BN>
+cudaError_t launch_any(bool blo, bool asplit, const CUtensorMap& ah, const CUtensorMap& al, const CUtensorMap& mb,
+                       const CUtensorMap& mbl, long long rows, int K, int ncols, long long plane_rows,
+                       long long plane_stride, float* out_hi, float* out_lo, int* err, long long blocks,
+                       cudaStream_t st) {
+  if (blo)
+    return asplit ? launch<BN, true, true>(ah, al, mb, mbl, rows, K, ncols, plane_rows, plane_stride, out_hi, out_lo,
+                                           err, blocks, st)
+                  : launch<BN, true, false>(ah, al, mb, mbl, rows, K, ncols, plane_rows, plane_stride, out_hi, out_lo,
+                                            err, blocks, st);
+  return asplit ? launch<BN, false, true>(ah, al, mb, mbl, rows, K, ncols, plane_rows, plane_stride, out_hi, out_lo,
+                                          err, blocks, st)
+                : launch<BN, false, false>(ah, al, mb, mbl, rows, K, ncols, plane_rows, plane_stride, out_hi, out_lo,
+                                           err, blocks, st);
 }
 
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
@@ -362,10 +409,11 @@ int tc_axis_transform(const float* a_hi, const float* a_lo, long long rows, int 
                       int ncols, long long plane_rows, long long plane_stride, float* out_hi, float* out_lo, int* err,
                       int tile_n, cudaStream_t st) {
   using namespace tc;
-  if (!a_hi || !a_lo || !b || !out_hi || !err || rows < 1 || K < 4 || K % 4 != 0 || ncols < 1 || plane_rows < 1 ||
+  if (!a_hi || !b || !out_hi || !err || rows < 1 || K < 4 || K % 4 != 0 || ncols < 1 || plane_rows < 1 ||
       plane_stride < 0 || rows > INT_MAX - BM || ncols > INT_MAX - 256 || (tile_n != 0 && tile_n != 128 && tile_n != 256))
     return TDZ_EINVAL;
-  if (!aligned16(a_hi) || !aligned16(a_lo) || !aligned16(b) || (b_lo && !aligned16(b_lo))) return TDZ_EINVAL;
+  if (!aligned16(a_hi) || (a_lo && !aligned16(a_lo)) || !aligned16(b) || (b_lo && !aligned16(b_lo)))
+    return TDZ_EINVAL;
   const long long tiles_m = (rows + BM - 1) / BM;
   // default: 256-column tiles where there are enough of them to fill the device twice, else 128
   const bool wide = tile_n ? tile_n == 256 : tiles_m * ((ncols + 255) / 256) >= 2 * 148;
@@ -373,20 +421,15 @@ int tc_axis_transform(const float* a_hi, const float* a_lo, long long rows, int 
   const long long blocks = tiles_m * ((ncols + bn - 1) / bn);
   if (blocks > INT_MAX) return TDZ_EINVAL;
   CUtensorMap mah, mal, mb, mbl;
-  if (!make_map(&mah, a_hi, rows, K, BM) || !make_map(&mal, a_lo, rows, K, BM) || !make_map(&mb, b, ncols, K, bn) ||
+  if (!make_map(&mah, a_hi, rows, K, BM) || !make_map(&mal, a_lo ? a_lo : a_hi, rows, K, BM) ||
+      !make_map(&mb, b, ncols, K, bn) ||
       !make_map(&mbl, b_lo ? b_lo : b, ncols, K, bn))
     return TDZ_ECUDA;
-  cudaError_t e;
-  if (wide)
-    e = b_lo ? launch<256, true>(mah, mal, mb, mbl, rows, K, ncols, plane_rows, plane_stride, out_hi, out_lo, err,
-                                 blocks, st)
-             : launch<256, false>(mah, mal, mb, mbl, rows, K, ncols, plane_rows, plane_stride, out_hi, out_lo, err,
-                                  blocks, st);
-  else
-    e = b_lo ? launch<128, true>(mah, mal, mb, mbl, rows, K, ncols, plane_rows, plane_stride, out_hi, out_lo, err,
-                                 blocks, st)
-             : launch<128, false>(mah, mal, mb, mbl, rows, K, ncols, plane_rows, plane_stride, out_hi, out_lo, err,
-                                  blocks, st);
+  const bool asplit = a_lo == nullptr;
+  const cudaError_t e = wide ? launch_any<256>(b_lo != nullptr, asplit, mah, mal, mb, mbl, rows, K, ncols, plane_rows,
+                                               plane_stride, out_hi, out_lo, err, blocks, st)
+                             : launch_any<128>(b_lo != nullptr, asplit, mah, mal, mb, mbl, rows, K, ncols, plane_rows,
+                                               plane_stride, out_hi, out_lo, err, blocks, st);
   if (e != cudaSuccess) {
     set_error(std::string("tensor-core axis transform: ") + cudaGetErrorString(e));
     return TDZ_ECUDA;

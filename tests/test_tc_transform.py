@@ -37,7 +37,9 @@ CASES = [
 @pytest.mark.parametrize("planes,plane_rows,k,ncols,tile_n", CASES)
 @pytest.mark.parametrize("split", [True, False])
 @pytest.mark.parametrize("blo", [False, True])
-def test_tc_axis_transform(tdz, planes, plane_rows, k, ncols, tile_n, split, blo):
+@pytest.mark.parametrize("asplit", [False, True])
+def test_tc_axis_transform(tdz, planes, plane_rows, k, ncols, tile_n, split, blo, asplit):
+    """asplit: A given in FP32 and split into the TF32 pair by the kernel, in shared memory."""
     import torch
     rng = np.random.default_rng(plane_rows * 7 + k + ncols)
     rows = planes * plane_rows
@@ -49,6 +51,8 @@ def test_tc_axis_transform(tdz, planes, plane_rows, k, ncols, tile_n, split, blo
     b_lo = (Bf - b_hi).astype(np.float32) if blo else np.zeros_like(b_hi)
     dev = torch.device("cuda")
     t_hi, t_lo, t_b, t_bl = (torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in (a_hi, a_lo, b_hi, b_lo))
+    if asplit:
+        t_hi, t_lo = torch.from_numpy(np.ascontiguousarray(A)).to(dev), None
     stride = plane_rows * ncols
     o_hi = torch.full((planes * stride,), np.nan, dtype=torch.float32, device=dev)
     o_lo = torch.full((planes * stride,), np.nan, dtype=torch.float32, device=dev) if split else None
@@ -93,16 +97,16 @@ def test_tc_axis_transform_rejects_bad_sizes(tdz):
 
 
 def test_preconditioner_autotuner(tdz):
-    """A mixed 2-D batch times its preconditioner with both transform tile widths at creation and keeps
-    the faster; a binary64 batch (cuBLAS DGEMM transforms) reports nothing."""
+    """A mixed 2-D batch times its preconditioner in the four transform variants at creation and keeps
+    the fastest; a binary64 batch (cuBLAS DGEMM transforms) reports nothing."""
     import workloads as wl
     p = 6
     t = wl.knots_for_nsplines(-20.0, 20.0, 90, p)
     ops = tdz.Ops([tdz.Basis(t, p, p + 1) for _ in range(2)], wl.softcore_medium(0.5))
     b = tdz.Batch([ops], [0], tdz.MIXED)
-    tile, ms = b.precond_tuning(0)
-    assert tile in (128, 256)
-    assert ms[128] > 0 and ms[256] > 0
-    assert ms[tile] == min(ms.values())
+    v, ms = b.precond_tuning(0)
+    assert v in (0, 1, 2, 3)
+    assert len(ms) == 4 and min(ms) > 0
+    assert ms[v] == min(ms)
     b64 = tdz.Batch([ops], [0], tdz.FP64)
-    assert b64.precond_tuning(0) == (0, {})
+    assert b64.precond_tuning(0) == (-1, [])
