@@ -294,8 +294,11 @@ def _nd_time(tdz, name, ops, run_ops, c0s, fields, dt, nsteps, extra, fp64_steps
         states[label] = [b.get_state(i) for i in range(len(run_ops))]
         if label == "mixed" and dim == 2:
             res["fused_apply"] = _apply_roofline(tdz, b, ops, run_ops)
+            res["operator_choice"] = _operator_choice(tdz, b, ops, run_ops)
         if label == "mixed":
             res["preconditioner_apply"] = _precond_roofline(tdz, b, ops, run_ops)
+            if dim == 3:
+                res["operator_apply"] = _quad_roofline(tdz, b, ops, run_ops)
         del b
     num = sum(np.linalg.norm(x - y) ** 2 for x, y in zip(states["mixed"], states["fp64"]))
     den = sum(np.linalg.norm(y) ** 2 for y in states["fp64"])
@@ -318,10 +321,67 @@ def _apply_roofline(tdz, b, ops, run_ops):
     nbytes = n * ((2 * p + 1) ** 2 * 4 + 16)
     t = ms[groups] * 1e-3
     ach = nbytes / t / 1e9
+    fpd = quad_flops_per_dof(ops[g].shape, p, p + 1)
+    alu = fpd * n / t / 1e12
     return {"kernel": f"k_apply2d_tma<{p},{groups}>", "coefficients": n, "bound": "hbm",
             "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
             "peak_source": peaks["source"], "algorithmic_bytes": nbytes, "ms_per_apply": ms[groups],
-            "variants_ms": {str(k): v for k, v in ms.items()}}
+            "variants_ms": {str(k): v for k, v in ms.items()},
+            "state_only_bytes": n * 16, "state_only_frac": n * 16 / t / 1e9 / peaks["hbm_gbs"],
+            "quadrature_view": {"flops_per_coefficient": fpd, "achieved_tflops": alu, "peak_tflops": PEAK_FP32_TFLOPS,
+                                "frac": alu / PEAK_FP32_TFLOPS,
+                                "note": "the same operator's on-the-fly Gauss-point flops over this kernel's time"}}
+
+
+def quad_flops_per_dof(shape, p, nq):
+    """Algorithmic FP32 flops of one Gauss-point sum-factorised apply of the non-separable term, per
+    coefficient: interpolation passes over the first dim-1 axes (4(p+1) flops per output: a real basis
+    value times a complex coefficient, fused multiply-add on both parts), the fused last-axis pass
+    (interpolate, scale by the complex point factor, project back: 8(p+1) + 6 per Gauss point) and the
+    projection passes (the same count as the interpolations)."""
+    E = [n - p for n in shape]
+    Q = [nq * e for e in E]
+    total = 0.0
+    for a in range(len(shape) - 1):
+        pts = float(np.prod(Q[:a + 1])) * float(np.prod(shape[a + 1:]))
+        total += 2 * 4 * (p + 1) * pts
+    total += float(np.prod(Q)) * (8 * (p + 1) + 6)
+    return total / float(np.prod(shape))
+
+
+def _quad_roofline(tdz, b, ops, run_ops):
+    """FP32-ALU roofline of the 3-D inner-solve operator apply (Kronecker passes plus the Gauss-point sum
+    factorisation of the soft-core V) for the largest geometry: one apply timed by the library with CUDA
+    events (tdz_batch_time_operator, best of 3); algorithmic flops: quad_flops_per_dof (the Kronecker
+    passes, about 60 flops per coefficient each, are left out)."""
+    g = max(set(run_ops), key=lambda k: ops[k].n)
+    ms = b.time_operator(g, 3)
+    p = ops[g].degree[0]
+    fpd = quad_flops_per_dof(ops[g].shape, p, p + 1)
+    ach = fpd * ops[g].n / (ms * 1e-3) / 1e12
+    return {"kernels": "k_interp, k_fused_last, k_project (FP32) + Kronecker axis passes", "coefficients": ops[g].n,
+            "bound": "alu", "flops_per_coefficient": fpd, "ms_per_apply": ms, "achieved": ach, "peak": PEAK_FP32_TFLOPS,
+            "unit": "TFLOP/s", "frac": ach / PEAK_FP32_TFLOPS,
+            "peak_source": "148 SM x 128 FP32 lanes x 2 flop x 2.032 GHz (unit counts and max clock)"}
+
+
+def _operator_choice(tdz, b, ops, run_ops):
+    """The two ways the library applies the 2-D operator in the FP32 inner solve, timed on the same
+    batch (tdz_batch_time_operator, best of 3): the fused kernel over the assembled (2p+1)^2 stencil
+    (HBM-bound), and the Gauss-point sum factorisation with V evaluated at the points (FP32-ALU-bound).
+    The library's default is the stencil where it is assembled."""
+    g = max(set(run_ops), key=lambda k: ops[k].n)
+    p = ops[g].degree[0]
+    n = ops[g].n
+    ms_stencil = b.time_operator(g, 3)
+    b.set_option(tdz.OPT_OPERATOR, tdz.OPERATOR_QUADRATURE)
+    ms_quad = b.time_operator(g, 3)
+    b.set_option(tdz.OPT_OPERATOR, tdz.OPERATOR_AUTO)
+    fpd = quad_flops_per_dof(ops[g].shape, p, p + 1)
+    return {"stencil_ms": ms_stencil, "quadrature_ms": ms_quad,
+            "quadrature_tflops": fpd * n / (ms_quad * 1e-3) / 1e12,
+            "quadrature_frac_fp32_peak": fpd * n / (ms_quad * 1e-3) / 1e12 / PEAK_FP32_TFLOPS,
+            "faster": "stencil" if ms_stencil <= ms_quad else "quadrature"}
 
 
 def _measured_peaks():
@@ -333,6 +393,9 @@ def _measured_peaks():
     except (OSError, KeyError, ValueError):
         return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "source": "fallback"}
 
+
+# FP32 ALU peak: 148 SM x 128 FP32 lanes x 2 flop x 2.032 GHz (unit counts and max clock), TFLOP/s
+PEAK_FP32_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 
 # dense TF32 : BF16 tensor rate of B300 (nominal 1.1 : 2.25 PFLOP/s)
 TF32_PER_BF16 = 1.1 / 2.25
@@ -633,7 +696,7 @@ def main():
     value = dof_all * args.steps / (ms * 1e-3)
     value64 = dof * args.fp64_steps / (ms64 * 1e-3)
     flops = flops_per_dof_step(p) * dof * args.steps
-    peak_fp32 = 148 * 128 * 2 * 2.032e9 / 1e12  # TFLOP/s, unit counts x max clock
+    peak_fp32 = PEAK_FP32_TFLOPS
     achieved = flops / (ms * 1e-3) / 1e12
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -268,6 +268,12 @@ int  tdz_batch_tuning(const tdz_batch* b, int geometry, int* groups, double* ms)
  * has no fast diagonalisation or the batch is not mixed); ms (host, optional, 4 doubles): ms per
  * preconditioner apply of variants 0..3. Errors: TDZ_EINVAL (bad handle or geometry index). */
 int  tdz_batch_precond_tuning(const tdz_batch* b, int geometry, int* variant, double* ms);
+/* tdz_batch_time_operator (2-D/3-D): time one apply of the inner-solve operator y = A_n x of Eq. cn_system
+ * (FP32 in a mixed batch, binary64 otherwise; the batch's operator and absorbing-layer choices) for a run
+ * of geometry `geometry`, on the batch's own work buffers, with CUDA events on the batch stream: *ms = the
+ * best of `reps` applies after one warm-up. Run states are not touched. Synchronises the stream.
+ * Errors: TDZ_EINVAL (bad handle, geometry or reps), TDZ_EUNSUPPORTED (1-D batch), TDZ_ECUDA. */
+int  tdz_batch_time_operator(tdz_batch* b, int geometry, int reps, double* ms);
 /* Total Krylov iterations of all runs since the batch was created (2-D/3-D; 0 in 1-D, whose
  * solve is direct). Synchronises the batch stream. */
 int  tdz_krylov_stats(const tdz_batch* b, double* iterations);

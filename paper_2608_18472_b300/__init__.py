@@ -75,6 +75,7 @@ _sig = {
     "tdz_krylov_stats": (C.c_int, [_vp, _dp]),
     "tdz_batch_tuning": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int), _dp]),
     "tdz_batch_precond_tuning": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int), _dp]),
+    "tdz_batch_time_operator": (C.c_int, [_vp, C.c_int, C.c_int, _dp]),
     "tdz_batch_destroy": (None, [_vp]),
     "tdz_observe_current": (C.c_int, [_vp, C.c_int, _vp]),
     "tdz_lowest_states": (C.c_int, [C.POINTER(_vp), C.c_int, C.c_int, _dp, _dp, _dp, C.POINTER(C.c_int), _vp]),
@@ -428,6 +429,13 @@ class Batch:
         _check(_lib.tdz_batch_precond_tuning(self._h, int(geometry), C.byref(v), ms.ctypes.data_as(_dp)),
                "tdz_batch_precond_tuning")
         return v.value, ([float(x) for x in ms] if v.value >= 0 else [])
+
+    def time_operator(self, geometry: int = 0, reps: int = 3) -> float:
+        """ms of one inner-solve operator apply y = A_n x (FP32 in mixed batches) for a run of the geometry,
+        best of `reps` (tdz_batch_time_operator)."""
+        ms = C.c_double()
+        _check(_lib.tdz_batch_time_operator(self._h, int(geometry), int(reps), C.byref(ms)), "tdz_batch_time_operator")
+        return ms.value
 
     def krylov_stats(self) -> float:
         """Total Krylov iterations of all runs since creation (0 for 1-D batches)."""

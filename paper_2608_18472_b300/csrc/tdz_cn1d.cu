@@ -2072,6 +2072,12 @@ int tdz_batch_precond_tuning(const tdz_batch* b, int geometry, int* variant, dou
   return TDZ_OK;
 }
 
+int tdz_batch_time_operator(tdz_batch* b, int geometry, int reps, double* ms) {
+  if (!b || !ms || geometry < 0 || reps < 1) return TDZ_EINVAL;
+  if (!b->nd) return TDZ_EUNSUPPORTED;
+  return tdz::nd_time_operator(b->nd, geometry, reps, ms);
+}
+
 int tdz_krylov_stats(const tdz_batch* b, double* iterations) {
   if (!b || !iterations) return TDZ_EINVAL;
   *iterations = 0.0;

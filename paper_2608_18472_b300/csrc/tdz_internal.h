@@ -73,6 +73,7 @@ void nd_set_refinement(NdBatch* b, double tol, int max_it);
 int nd_set_option(NdBatch* b, int option, int value);
 int nd_tuning(const NdBatch* b, int geometry, int* groups, double* ms);
 int nd_precond_tuning(const NdBatch* b, int geometry, int* variant, double* ms);
+int nd_time_operator(NdBatch* b, int geometry, int reps, double* ms);
 int nd_dim(const NdBatch* b);
 size_t nd_device_bytes(const NdBatch* b);
 

@@ -304,6 +304,110 @@ __global__ void k_project(const T* __restrict__ Btab, int nq, int n, int E, cons
   }
 }
 
+// The same two passes along an axis whose points have a contiguous inner extent (inner >= 32): one
+// thread per (outer, inner) pencil walks the elements with a sliding window of P+1 coefficients, so
+// each coefficient (interpolation) or Gauss-point value (projection) is read once and the index
+// arithmetic is done once per pencil. The sums are those of k_interp / k_project, the interpolation
+// split into even and odd terms.
+template <class T, int P>
+__global__ void k_interp_win(const T* __restrict__ Btab, int nq, int n, int E, const C<T>* __restrict__ in,
+                             C<T>* __restrict__ out, long long outer, long long inner) {
+  const long long total = outer * inner;
+  const long long Q = (long long)E * nq;
+  for (long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x; tid < total;
+       tid += (long long)gridDim.x * blockDim.x) {
+    const long long i = tid % inner, o = tid / inner;
+    const C<T>* src = in + o * n * inner + i;
+    C<T>* dst = out + o * Q * inner + i;
+    C<T> win[P + 1];  // win[r] = coefficient e + r - 1 of the current element
+#pragma unroll
+    for (int k = 0; k <= P; ++k) {
+      const int j = k - 1;
+      win[k] = (j >= 0 && j < n) ? src[(long long)j * inner] : czero<T>();
+    }
+    for (int e = 0; e < E; ++e) {
+      const int jn = e + P;  // enters the window for element e + 1; loaded a whole element ahead
+      const C<T> next = (jn < n && e + 1 < E) ? src[(long long)jn * inner] : czero<T>();
+      for (int qq = 0; qq < nq; ++qq) {
+        const int q = e * nq + qq;
+        const T* b = Btab + (size_t)q * (P + 1);
+        Mac<T> r0, i0, r1, i1;
+#pragma unroll
+        for (int k = 0; k <= P; ++k) {
+          if (k & 1) {
+            r1.add(b[k], win[k].r);
+            i1.add(b[k], win[k].i);
+          } else {
+            r0.add(b[k], win[k].r);
+            i0.add(b[k], win[k].i);
+          }
+        }
+        dst[(long long)q * inner] = C<T>{r0.get() + r1.get(), i0.get() + i1.get()};
+      }
+#pragma unroll
+      for (int k = 0; k < P; ++k) win[k] = win[k + 1];
+      win[P] = next;
+    }
+  }
+}
+
+template <class T, int P>
+__global__ void k_project_win(const T* __restrict__ Btab, int nq, int n, int E, const C<T>* __restrict__ in,
+                              C<T>* __restrict__ out, long long outer, long long inner, int accumulate) {
+  const long long total = outer * inner;
+  const long long Q = (long long)E * nq;
+  for (long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x; tid < total;
+       tid += (long long)gridDim.x * blockDim.x) {
+    const long long i = tid % inner, o = tid / inner;
+    const C<T>* src = in + o * Q * inner + i;
+    C<T>* dst = out + o * n * inner + i;
+    Mac<T> ar[P + 1], ai[P + 1];  // partial projections onto coefficient e + r - 1
+    for (int e = 0; e < E; ++e) {
+      for (int qq = 0; qq < nq; ++qq) {
+        const int q = e * nq + qq;
+        const T* b = Btab + (size_t)q * (P + 1);
+        const C<T> v = src[(long long)q * inner];
+#pragma unroll
+        for (int k = 0; k <= P; ++k) {
+          ar[k].add(b[k], v.r);
+          ai[k].add(b[k], v.i);
+        }
+      }
+      const int j = e - 1;  // coefficient e - 1 is complete
+      if (j >= 0 && j < n) {
+        C<T>* d = dst + (long long)j * inner;
+        const C<T> v = C<T>{ar[0].get(), ai[0].get()};
+        if (accumulate) {
+          const C<T> u = *d;
+          *d = C<T>{u.r + v.r, u.i + v.i};
+        } else {
+          *d = v;
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < P; ++k) {
+        ar[k] = ar[k + 1];
+        ai[k] = ai[k + 1];
+      }
+      ar[P] = Mac<T>();
+      ai[P] = Mac<T>();
+    }
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+      const int j = E - 1 + k;
+      if (j < 0 || j >= n) continue;
+      C<T>* d = dst + (long long)j * inner;
+      const C<T> v = C<T>{ar[k].get(), ai[k].get()};
+      if (accumulate) {
+        const C<T> u = *d;
+        *d = C<T>{u.r + v.r, u.i + v.i};
+      } else {
+        *d = v;
+      }
+    }
+  }
+}
+
 template <class T>
 struct QGrid {
   int dim;
@@ -316,7 +420,7 @@ struct QGrid {
 // Along the last (slowest) axis L: for every pencil (one point of the faster axes, already
 // interpolated) and chunk of elements, walk the elements with a sliding window of P+1
 // coefficients: interpolate to the nq points (table Bl), multiply by coef * w(q) * f(r_q), and
-// project back with the same table, accumulating into out (shape [n_L][inner], zero on entry).
+// project back with the same table into out (shape [n_L][inner]; every coefficient is stored once).
 // A coefficient completed inside a chunk's element loop is written by that chunk alone; the last
 // P partial sums of every chunk but the last (shared with the next chunk) go to `side`
 // ([chunk][P][inner]) and k_fused_fixup adds them, so no atomics are needed and the sum order is
@@ -363,16 +467,24 @@ __global__ void k_fused_last(const C<T>* __restrict__ in, C<T>* __restrict__ out
       }
     }
     for (int e = e0; e < e1; ++e) {
+      const int jn = e + P;  // coefficient entering the window for element e + 1, loaded a whole element ahead
+      const C<T> next = (jn >= 0 && jn < nL && e + 1 < e1) ? in[(long long)jn * inner + i] : czero<T>();
       for (int qq = 0; qq < nq; ++qq) {
         const int q = e * nq + qq;
         const T* b = Bl + (size_t)q * (P + 1);
-        Mac<T> mr, mi;
+        // even and odd terms in separate chains (half the dependent latency per point)
+        Mac<T> mr0, mi0, mr1, mi1;
 #pragma unroll
         for (int k = 0; k <= P; ++k) {
-          mr.add(b[k], win[k].r);
-          mi.add(b[k], win[k].i);
+          if (k & 1) {
+            mr1.add(b[k], win[k].r);
+            mi1.add(b[k], win[k].i);
+          } else {
+            mr0.add(b[k], win[k].r);
+            mi0.add(b[k], win[k].i);
+          }
         }
-        const T pr = mr.get(), pi = mi.get();
+        const T pr = mr0.get() + mr1.get(), pi = mi0.get() + mi1.get();
         T f;
         if (ftab) {  // w(q) f(r_q) tabulated at the Gauss points, [q_L][pencil]
           f = fpre[0];
@@ -392,14 +504,10 @@ __global__ void k_fused_last(const C<T>* __restrict__ in, C<T>* __restrict__ out
           acci[k].add(b[k], gi);
         }
       }
-      // coefficient e - 1 is complete: emit; shift both windows by one
+      // coefficient e - 1 is complete: emit (its only writer; out needs no clearing); shift both windows
       {
         const int j = e - 1;
-        if (j >= 0 && j < nL) {
-          C<T>* o = out + (long long)j * inner + i;
-          const C<T> v = *o;
-          *o = C<T>{v.r + accr[0].get(), v.i + acci[0].get()};
-        }
+        if (j >= 0 && j < nL) out[(long long)j * inner + i] = C<T>{accr[0].get(), acci[0].get()};
       }
 #pragma unroll
       for (int k = 0; k < P; ++k) {
@@ -407,8 +515,7 @@ __global__ void k_fused_last(const C<T>* __restrict__ in, C<T>* __restrict__ out
         accr[k] = accr[k + 1];
         acci[k] = acci[k + 1];
       }
-      const int jn = e + P;  // coefficient entering the window for element e + 1
-      win[P] = (jn >= 0 && jn < nL && e + 1 < e1) ? in[(long long)jn * inner + i] : czero<T>();
+      win[P] = next;
       accr[P] = Mac<T>();
       acci[P] = Mac<T>();
     }
@@ -420,9 +527,7 @@ __global__ void k_fused_last(const C<T>* __restrict__ in, C<T>* __restrict__ out
       if (e1 < EL) {
         side[((long long)ch * P + k) * inner + i] = a;
       } else if (j >= 0 && j < nL) {
-        C<T>* o = out + (long long)j * inner + i;
-        const C<T> v = *o;
-        *o = C<T>{v.r + a.r, v.i + a.i};
+        out[(long long)j * inner + i] = a;
       }
     }
   }
@@ -1799,6 +1904,21 @@ struct Apply {
 
   // interpolate x along the faster axes 0..dim-2 (derivative on axis dax if dax < dim - 1); returns the
   // result (shape [n_last][Q_0..Q_{dim-2}]) in qa or qb
+  // one interpolation / projection pass along an axis: the sliding-window kernels where the inner
+  // extent is contiguous enough to coalesce, else one thread per output
+  void interp(const T* B, const AxisDev& A, const C<T>* in, C<T>* out, long long outer, long long inner) {
+    if (inner >= 32)
+      k_interp_win<T, P><<<grid_for(outer * inner), TPB, 0, b->st>>>(B, A.nq, A.n, A.E, in, out, outer, inner);
+    else
+      k_interp<T, P><<<grid_for(outer * A.Q * inner), TPB, 0, b->st>>>(B, A.nq, A.n, A.Q, in, out, outer, inner);
+  }
+  void project(const T* B, const AxisDev& A, const C<T>* in, C<T>* out, long long outer, long long inner, int acc) {
+    if (inner >= 32)
+      k_project_win<T, P><<<grid_for(outer * inner), TPB, 0, b->st>>>(B, A.nq, A.n, A.E, in, out, outer, inner, acc);
+    else
+      k_project<T, P><<<grid_for(outer * A.n * inner), TPB, 0, b->st>>>(B, A.nq, A.n, A.E, in, out, outer, inner, acc);
+  }
+
   const C<T>* to_pencils(const C<T>* x, int dax) {
     const int D = r->dim, L = D - 1;
     int len[3] = {r->n[0], r->n[1], r->n[2]};
@@ -1808,9 +1928,7 @@ struct Apply {
       shape(ax, len, outer, inner);
       const AxisDev& A = r->ax[ax];
       C<T>* X = (ax % 2 == 0) ? qa : qb;
-      const long long tot = outer * A.Q * inner;
-      k_interp<T, P><<<grid_for(tot), TPB, 0, b->st>>>(tab<T>(A, ax == dax ? TDB : TB), A.nq, A.n, A.Q, in, X, outer,
-                                                        inner);
+      interp(tab<T>(A, ax == dax ? TDB : TB), A, in, X, outer, inner);
       len[ax] = A.Q;
       in = X;
     }
@@ -1830,9 +1948,7 @@ struct Apply {
       shape(ax, len, outer, inner);
       const AxisDev& A = r->ax[ax];
       X = (ax % 2 == 0) ? qa : qb;
-      const long long tot = outer * A.Q * inner;
-      k_interp<T, P><<<grid_for(tot), TPB, 0, b->st>>>(tab<T>(A, ax == dax ? TDB : TB), A.nq, A.n, A.Q, in, X, outer,
-                                                        inner);
+      interp(tab<T>(A, ax == dax ? TDB : TB), A, in, X, outer, inner);
       len[ax] = A.Q;
       in = X;
     }
@@ -1840,7 +1956,6 @@ struct Apply {
     long long inner = 1;
     for (int a = 0; a < L; ++a) inner *= len[a];
     const AxisDev& AL = r->ax[L];
-    cudaMemsetAsync(U, 0, sizeof(C<T>) * (size_t)AL.n * inner, b->st);
     int echunk = 1;
     const long long nch = fused_nchunks(AL.E, inner, P, &echunk);
     C<T>* side = static_cast<C<T>*>(b->d_side);
@@ -1858,9 +1973,7 @@ struct Apply {
       const AxisDev& A = r->ax[ax];
       const bool last = ax == 0;
       C<T>* out = last ? y : ((cur == qa) ? qb : qa);
-      const long long tot = outer2 * A.n * inner2;
-      k_project<T, P><<<grid_for(tot), TPB, 0, b->st>>>(tab<T>(A, ax == dax ? TDB : TB), A.nq, A.n, A.E, cur, out,
-                                                         outer2, inner2, last ? 1 : 0);
+      project(tab<T>(A, ax == dax ? TDB : TB), A, cur, out, outer2, inner2, last ? 1 : 0);
       len[ax] = A.n;
       cur = out;
     }
@@ -2962,6 +3075,81 @@ int nd_get_state(const NdBatch* b, int run, double* c, bool device) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
   if (e != cudaSuccess) return nd_cuda_fail(e, "tdz_get_state");
   return TDZ_OK;
+}
+
+// One apply of the inner-solve operator y = A_n x (FP32 in mixed batches, binary64 otherwise) for run r,
+// on the batch's work buffers, timed with CUDA events: best of `reps` after one warm-up apply.
+template <int P>
+int time_operator_p(NdBatch* b, NdRun* r, int reps, double* ms_out) {
+  const NdGeo& G = b->geo[r->geo];
+  const bool stencil = G.has_stencil() && b->opt_operator != TDZ_OPERATOR_QUADRATURE;
+  const double tau = 0.025, ebar[3] = {0.01, 0.01, 0.01};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return TDZ_ECUDA;
+  }
+  float best = 0.f;
+  cudaError_t e = cudaSuccess;
+  auto timed = [&](auto&& apply_once) {
+    apply_once();
+    for (int k = 0; k < reps && e == cudaSuccess; ++k) {
+      cudaEventRecord(e0, b->st);
+      apply_once();
+      cudaEventRecord(e1, b->st);
+      float ms = 0.f;
+      e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      best = k == 0 ? ms : std::min(best, ms);
+    }
+  };
+  if (b->prec == TDZ_MIXED) {
+    Apply<float, P> op{b, r, static_cast<C<float>*>(b->w_t1), static_cast<C<float>*>(b->w_t2),
+                       static_cast<C<float>*>(b->w_t3), static_cast<C<float>*>(b->w_t4),
+                       static_cast<C<float>*>(b->w_qa), static_cast<C<float>*>(b->w_qb)};
+    if (stencil) op.Wm = r->cap ? nullptr : G.W32;
+    op.Vtab = G.Vq32;
+    const C<float>* x = static_cast<const C<float>*>(b->w_p);
+    C<float>* y = static_cast<C<float>*>(b->w_q);
+    timed([&]() { op.apply(x, y, tau, ebar); });
+  } else {
+    Apply<double, P> op{b, r, reinterpret_cast<C<double>*>(b->d_t1), reinterpret_cast<C<double>*>(b->d_t2),
+                        reinterpret_cast<C<double>*>(b->d_t3), reinterpret_cast<C<double>*>(b->d_t4),
+                        reinterpret_cast<C<double>*>(b->d_qa), reinterpret_cast<C<double>*>(b->d_qb)};
+    if (stencil) op.Wm = G.W64;
+    const C<double>* x = reinterpret_cast<const C<double>*>(b->d_p);
+    C<double>* y = reinterpret_cast<C<double>*>(b->d_q);
+    timed([&]() { op.apply(x, y, tau, ebar); });
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->rb_geo = -1;
+  if (e != cudaSuccess) return nd_cuda_fail(e, "tdz_batch_time_operator");
+  int werr = 0;
+  if (cudaMemcpy(&werr, b->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess || werr != 0) return TDZ_ECUDA;
+  *ms_out = best;
+  return TDZ_OK;
+}
+
+int nd_time_operator(NdBatch* b, int geometry, int reps, double* ms) {
+  if (geometry < 0 || geometry >= (int)b->geo.size() || reps < 1 || !ms) return TDZ_EINVAL;
+  NdRun* r = nullptr;
+  for (auto& run : b->runs)
+    if (run.geo == geometry) {
+      r = &run;
+      break;
+    }
+  if (!r) return TDZ_EINVAL;
+  switch (b->P) {
+    case 1: return time_operator_p<1>(b, r, reps, ms);
+    case 2: return time_operator_p<2>(b, r, reps, ms);
+    case 3: return time_operator_p<3>(b, r, reps, ms);
+    case 4: return time_operator_p<4>(b, r, reps, ms);
+    case 5: return time_operator_p<5>(b, r, reps, ms);
+    case 6: return time_operator_p<6>(b, r, reps, ms);
+    case 7: return time_operator_p<7>(b, r, reps, ms);
+    default: return time_operator_p<8>(b, r, reps, ms);
+  }
 }
 
 static int propagate_one(NdBatch* w, NdBatch* b, int r, const double* field_host, double dt, long long step0,

@@ -110,3 +110,20 @@ def test_preconditioner_autotuner(tdz):
     assert ms[v] == min(ms)
     b64 = tdz.Batch([ops], [0], tdz.FP64)
     assert b64.precond_tuning(0) == (-1, [])
+
+
+def test_operator_timing(tdz):
+    """tdz_batch_time_operator times one inner-solve operator apply of a 2-D/3-D batch; 1-D batches have
+    no such operator."""
+    import workloads as wl
+    p = 6
+    t = wl.knots_for_nsplines(-20.0, 20.0, 40, p)
+    for dim in (2, 3):
+        ops = tdz.Ops([tdz.Basis(t, p, p + 1) for _ in range(dim)], wl.softcore_medium(0.5))
+        for prec in (tdz.MIXED, tdz.FP64):
+            b = tdz.Batch([ops], [0], prec)
+            assert b.time_operator(0, 2) > 0
+    ops1 = tdz.assemble_1d(t, p, wl.softcore_medium(0.5))
+    b1 = tdz.Batch([ops1], [0], tdz.MIXED)
+    with pytest.raises(tdz.TDZError):
+        b1.time_operator(0, 2)
