@@ -155,6 +155,106 @@ TDZ_DEV fx tsqrt(fx a) {
   return to_fx(fast_two_sum(s, r.h / (2.f * s)));
 }
 
+// ---------------------------------------------------------------------------- packed FP32 pairs
+// Two FP32 values in one 64-bit register, operated on by the f32x2 instructions of sm_100 and later
+// (one instruction, two IEEE round-to-nearest results). A complex double-float number keeps its real
+// and imaginary parts in the two lanes, so each step of a double-float operation on a complex number
+// is one instruction instead of two; the results are bitwise those of the scalar operations above.
+struct f2 {
+  unsigned long long v;
+};
+TDZ_DEV f2 f2_pack(float a, float b) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
+  return r;
+}
+TDZ_DEV float2 f2_unpack(f2 a) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(a.v));
+  return r;
+}
+TDZ_DEV f2 f2_add(f2 a, f2 b) {
+  f2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+TDZ_DEV f2 f2_sub(f2 a, f2 b) {
+  f2 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+TDZ_DEV f2 f2_mul(f2 a, f2 b) {
+  f2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+TDZ_DEV f2 f2_fma(f2 a, f2 b, f2 c) {
+  f2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+  return r;
+}
+
+// complex double-float, packed: h = (re.h, im.h), l = (re.l, im.l)
+struct pcff {
+  f2 h, l;
+};
+// a real double-float factor as the packed broadcasts the products below take: x.h, -x.h, -x.l
+struct pfac {
+  f2 h, nh, nl;
+};
+TDZ_DEV pfac pfac_of(float h, float l) { return pfac{f2_pack(h, h), f2_pack(-h, -h), f2_pack(-l, -l)}; }
+// a different real factor per lane: (h0 + l0) on lane 0, (h1 + l1) on lane 1
+TDZ_DEV pfac pfac2_of(float h0, float l0, float h1, float l1) {
+  return pfac{f2_pack(h0, h1), f2_pack(-h0, -h1), f2_pack(-l0, -l1)};
+}
+// the lanes exchanged: (im, re)
+TDZ_DEV pcff pcff_swap(pcff a) {
+  const float2 h = f2_unpack(a.h), l = f2_unpack(a.l);
+  return pcff{f2_pack(h.y, h.x), f2_pack(l.y, l.x)};
+}
+// fast_two_sum on both lanes
+TDZ_DEV pcff p_fast_two_sum(f2 a, f2 b) {
+  const f2 s = f2_add(a, b);
+  return pcff{s, f2_sub(b, f2_sub(s, a))};
+}
+// a + b (ff_add on both lanes)
+TDZ_DEV pcff pcff_add(pcff a, pcff b) {
+  const f2 s = f2_add(a.h, b.h);
+  const f2 bb = f2_sub(s, a.h);
+  const f2 e = f2_add(f2_sub(a.h, f2_sub(s, bb)), f2_sub(b.h, bb));
+  return p_fast_two_sum(s, f2_add(e, f2_add(a.l, b.l)));
+}
+// x * y for a real factor x (ff_mul on both lanes; the error term is carried negated)
+TDZ_DEV pcff pcff_scale(const pfac& x, pcff y) {
+  const f2 p = f2_mul(x.h, y.h);
+  f2 ne = f2_fma(x.nh, y.h, p);
+  ne = f2_fma(x.nh, y.l, ne);
+  ne = f2_fma(x.nl, y.h, ne);
+  const f2 s = f2_sub(p, ne);  // fast_two_sum(p, e) with e = -ne
+  return pcff{s, f2_sub(f2_sub(p, s), ne)};
+}
+// Dot2 accumulator of a complex sum, packed (acc_mul / acc_get on both lanes)
+struct pacc {
+  f2 s, c;
+};
+TDZ_DEV void pacc_zero(pacc& a) {
+  a.s = f2_pack(0.f, 0.f);
+  a.c = a.s;
+}
+// a += x * y (x real double-float, y complex double-float)
+TDZ_DEV void pacc_mul(pacc& a, const pfac& x, pcff y) {
+  const f2 p = f2_mul(x.h, y.h);
+  f2 ne = f2_fma(x.nh, y.h, p);  // -(x.h y.h - p), exact
+  ne = f2_fma(x.nh, y.l, ne);
+  ne = f2_fma(x.nl, y.h, ne);
+  const f2 s = f2_add(a.s, p);
+  const f2 bb = f2_sub(s, a.s);
+  const f2 t = f2_add(f2_sub(a.s, f2_sub(s, bb)), f2_sub(p, bb));
+  a.s = s;
+  a.c = f2_add(a.c, f2_sub(t, ne));
+}
+TDZ_DEV pcff pacc_get(const pacc& a) { return p_fast_two_sum(a.s, a.c); }
+
 // ---------------------------------------------------------------------------- TF32 split
 // x rounded to the nearest TF32 value (8 exponent bits, 10 stored significand bits: the low 13 bits
 // of the FP32 pattern cleared after adding half of their weight, ties away from zero); x - tf32_hi(x)

@@ -149,6 +149,12 @@ __device__ __forceinline__ T medium_f(const MediumT<T>& M, int kind, int axis, c
   }
 }
 
+// reciprocal square root for the FP32 soft-core factor (hardware approximation); the other types never
+// take that path
+__device__ __forceinline__ float frsqrt(float v) { return rsqrtf(v); }
+template <class T>
+__device__ __forceinline__ T frsqrt(T v) { return T(1) / tsqrt(v); }
+
 template <class T>
 using C = cx<T>;
 
@@ -408,6 +414,76 @@ __global__ void k_project_win(const T* __restrict__ Btab, int nq, int n, int E, 
   }
 }
 
+// The same two passes along the fastest axis (inner = 1): one thread per Gauss point (interpolation) or
+// coefficient (projection) of a row, the rows spread over the grid's y dimension, so no index is
+// divided per output; the basis values of an interpolation point stay in registers across rows.
+template <class T, int P>
+__global__ void k_interp_row(const T* __restrict__ Btab, int nq, int n, int Q, const C<T>* __restrict__ in,
+                             C<T>* __restrict__ out, long long outer) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= Q) return;
+  const int e = q / nq;
+  T bq[P + 1];
+#pragma unroll
+  for (int r = 0; r <= P; ++r) bq[r] = Btab[(size_t)q * (P + 1) + r];
+  for (long long o = blockIdx.y; o < outer; o += gridDim.y) {
+    const C<T>* src = in + o * n;
+    Mac<T> r0, i0, r1, i1;
+#pragma unroll
+    for (int r = 0; r <= P; ++r) {
+      const int j = e + r - 1;
+      if (j < 0 || j >= n) continue;
+      const C<T> v = src[j];
+      if (r & 1) {
+        r1.add(bq[r], v.r);
+        i1.add(bq[r], v.i);
+      } else {
+        r0.add(bq[r], v.r);
+        i0.add(bq[r], v.i);
+      }
+    }
+    out[o * Q + q] = C<T>{r0.get() + r1.get(), i0.get() + i1.get()};
+  }
+}
+
+template <class T, int P>
+__global__ void k_project_row(const T* __restrict__ Btab, int nq, int n, int E, const C<T>* __restrict__ in,
+                              C<T>* __restrict__ out, long long outer, int accumulate) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const long long Q = (long long)E * nq;
+  for (long long o = blockIdx.y; o < outer; o += gridDim.y) {
+    const C<T>* src = in + o * Q;
+    Mac<T> r0, i0, r1, i1;
+#pragma unroll
+    for (int r = 0; r <= P; ++r) {
+      const int e = j + 1 - r;
+      if (e < 0 || e >= E) continue;
+      const T* bq = Btab + (size_t)e * nq * (P + 1) + r;
+      const C<T>* s = src + (long long)e * nq;
+      for (int qq = 0; qq < nq; ++qq) {
+        const T bv = bq[(size_t)qq * (P + 1)];
+        const C<T> v = s[qq];
+        if (qq & 1) {
+          r1.add(bv, v.r);
+          i1.add(bv, v.i);
+        } else {
+          r0.add(bv, v.r);
+          i0.add(bv, v.i);
+        }
+      }
+    }
+    const C<T> v = C<T>{r0.get() + r1.get(), i0.get() + i1.get()};
+    C<T>* d = out + o * n + j;
+    if (accumulate) {
+      const C<T> u = *d;
+      *d = C<T>{u.r + v.r, u.i + v.i};
+    } else {
+      *d = v;
+    }
+  }
+}
+
 template <class T>
 struct QGrid {
   int dim;
@@ -428,11 +504,38 @@ struct QGrid {
 template <class T, int P>
 __global__ void k_fused_last(const C<T>* __restrict__ in, C<T>* __restrict__ out, C<T>* __restrict__ side,
                              const T* __restrict__ Bl, int nq, int nL, int EL, long long inner, int echunk, QGrid<T> g,
-                             MediumT<T> M, int kind, int axis, double cr, double ci, const T* __restrict__ ftab) {
+                             MediumT<T> M, int kind, int axis, double cr, double ci, const T* __restrict__ ftab,
+                             int stage) {
   const int nchunks = (EL + echunk - 1) / echunk;
   const long long total = inner * nchunks;
   const int L = g.dim - 1;
   const T tcr = (T)cr, tci = (T)ci;
+  // with `stage`, the block copies the last axis' basis table (and, without ftab, its point coordinates
+  // and weights) to shared memory once: every thread reads the same entries in the same order
+  extern __shared__ __align__(16) unsigned char fl_smem[];
+  const int QL = EL * nq;
+  const T* Bt = Bl;
+  const T* xt = g.x[L];
+  const T* wt = g.w[L];
+  if (stage) {
+    T* sB = reinterpret_cast<T*>(fl_smem);
+    for (int k = threadIdx.x; k < QL * (P + 1); k += blockDim.x) sB[k] = Bl[k];
+    Bt = sB;
+    if (!ftab) {
+      T* sx = sB + (size_t)QL * (P + 1);
+      T* sw = sx + QL;
+      for (int k = threadIdx.x; k < QL; k += blockDim.x) {
+        sx[k] = g.x[L][k];
+        sw[k] = g.w[L][k];
+      }
+      xt = sx;
+      wt = sw;
+    }
+    __syncthreads();
+  }
+  // FP32 soft-core potential: f = w (-Z) / sqrt(r^2 + eps) with the pencil's part of r^2 hoisted and a
+  // hardware reciprocal square root (the inner solve's precision)
+  const bool soft = std::is_same<T, float>::value && kind == 0 && M.pot_kind == TDZ_POT_SOFTCORE;
   for (long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x; tid < total;
        tid += (long long)gridDim.x * blockDim.x) {
     const long long i = tid % inner;
@@ -448,6 +551,10 @@ __global__ void k_fused_last(const C<T>* __restrict__ in, C<T>* __restrict__ out
       r[a] = g.x[a][q];
       wp *= g.w[a][q];
     }
+    T r2p = soft ? M.vp[1] : T(0);  // eps + the faster axes' r^2
+    if (soft)
+      for (int a = 0; a < L; ++a) r2p += r[a] * r[a];
+    const T mz = -M.vp[0] * wp;
     C<T> win[P + 1];            // win[r] = coefficient e + r - 1 of the current element
     Mac<T> accr[P + 1], acci[P + 1];  // partial projections onto coefficient e + r - 1
 #pragma unroll
@@ -471,7 +578,7 @@ __global__ void k_fused_last(const C<T>* __restrict__ in, C<T>* __restrict__ out
       const C<T> next = (jn >= 0 && jn < nL && e + 1 < e1) ? in[(long long)jn * inner + i] : czero<T>();
       for (int qq = 0; qq < nq; ++qq) {
         const int q = e * nq + qq;
-        const T* b = Bl + (size_t)q * (P + 1);
+        const T* b = Bt + (size_t)q * (P + 1);
         // even and odd terms in separate chains (half the dependent latency per point)
         Mac<T> mr0, mi0, mr1, mi1;
 #pragma unroll
@@ -492,9 +599,12 @@ __global__ void k_fused_last(const C<T>* __restrict__ in, C<T>* __restrict__ out
           for (int u = 0; u + 1 < kFPre; ++u) fpre[u] = fpre[u + 1];
           const int qn = q + kFPre;
           fpre[kFPre - 1] = qn < qend ? ftab[(long long)qn * inner + i] : T(0);
+        } else if (soft) {
+          const T xq = xt[q];
+          f = mz * wt[q] * frsqrt(r2p + xq * xq);
         } else {
-          r[L] = g.x[L][q];
-          f = wp * g.w[L][q] * medium_f<T>(M, kind, axis, r, g.dim);
+          r[L] = xt[q];
+          f = wp * wt[q] * medium_f<T>(M, kind, axis, r, g.dim);
         }
         const T fr = f * tcr, fi = f * tci;
         const T gr = fr * pr - fi * pi, gi = fr * pi + fi * pr;
@@ -533,10 +643,123 @@ __global__ void k_fused_last(const C<T>* __restrict__ in, C<T>* __restrict__ out
   }
 }
 
+// k_fused_last for double-float (the mixed path's residual applies): the same pass and the same
+// arithmetic, bitwise, with the real and imaginary parts of each complex double-float value carried in
+// the two lanes of packed f32x2 registers, so every double-float step serves both parts at once.
+__device__ __forceinline__ pcff pcff_load(const C<fx>* p) {
+  const float4 v = *reinterpret_cast<const float4*>(p);  // r.h, r.l, i.h, i.l
+  return pcff{f2_pack(v.x, v.z), f2_pack(v.y, v.w)};
+}
+__device__ __forceinline__ void pcff_store(C<fx>* p, pcff a) {
+  const float2 h = f2_unpack(a.h), l = f2_unpack(a.l);
+  *reinterpret_cast<float4*>(p) = make_float4(h.x, l.x, h.y, l.y);
+}
+__device__ __forceinline__ pcff pcff_zero() { return pcff{f2_pack(0.f, 0.f), f2_pack(0.f, 0.f)}; }
+// (-im, re): multiplication by i
+__device__ __forceinline__ pcff pcff_times_i(pcff a) {
+  const float2 h = f2_unpack(a.h), l = f2_unpack(a.l);
+  return pcff{f2_pack(-h.y, h.x), f2_pack(-l.y, l.x)};
+}
+
+template <int P>
+__global__ void k_fused_last_fx(const C<fx>* __restrict__ in, C<fx>* __restrict__ out, C<fx>* __restrict__ side,
+                                const fx* __restrict__ Bl, int nq, int nL, int EL, long long inner, int echunk,
+                                QGrid<fx> g, MediumT<fx> M, int kind, int axis, double cr, double ci,
+                                const fx* __restrict__ ftab) {
+  const int nchunks = (EL + echunk - 1) / echunk;
+  const long long total = inner * nchunks;
+  const int L = g.dim - 1;
+  const fx tcr = fx(cr), tci = fx(ci);
+  for (long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x; tid < total;
+       tid += (long long)gridDim.x * blockDim.x) {
+    const long long i = tid % inner;
+    const int ch = (int)(tid / inner);
+    const int e0 = ch * echunk, e1 = min(EL, e0 + echunk);
+    fx r[3];
+    fx wp = 1;
+    long long t = i;
+    for (int a = 0; a < L; ++a) {
+      const int q = (int)(t % g.Q[a]);
+      t /= g.Q[a];
+      r[a] = g.x[a][q];
+      wp *= g.w[a][q];
+    }
+    pcff win[P + 1];  // coefficient e + k - 1 of the current element
+    pacc acc[P + 1];  // partial projections onto coefficient e + k - 1
+#pragma unroll
+    for (int k = 0; k <= P; ++k) {
+      const int j = e0 + k - 1;
+      win[k] = (j >= 0 && j < nL) ? pcff_load(in + (long long)j * inner + i) : pcff_zero();
+      pacc_zero(acc[k]);
+    }
+    constexpr int kFPre = 4;
+    const int qend = e1 * nq;
+    fx fpre[kFPre];
+    if (ftab) {
+#pragma unroll
+      for (int u = 0; u < kFPre; ++u) {
+        const int qp = e0 * nq + u;
+        fpre[u] = qp < qend ? ftab[(long long)qp * inner + i] : fx(0);
+      }
+    }
+    for (int e = e0; e < e1; ++e) {
+      const int jn = e + P;
+      const pcff next = (jn >= 0 && jn < nL && e + 1 < e1) ? pcff_load(in + (long long)jn * inner + i) : pcff_zero();
+      for (int qq = 0; qq < nq; ++qq) {
+        const int q = e * nq + qq;
+        const fx* b = Bl + (size_t)q * (P + 1);
+        pacc m0, m1;
+        pacc_zero(m0);
+        pacc_zero(m1);
+#pragma unroll
+        for (int k = 0; k <= P; ++k) pacc_mul((k & 1) ? m1 : m0, pfac_of(b[k].h, b[k].l), win[k]);
+        const pcff pv = pcff_add(pacc_get(m0), pacc_get(m1));
+        fx f;
+        if (ftab) {
+          f = fpre[0];
+#pragma unroll
+          for (int u = 0; u + 1 < kFPre; ++u) fpre[u] = fpre[u + 1];
+          const int qn = q + kFPre;
+          fpre[kFPre - 1] = qn < qend ? ftab[(long long)qn * inner + i] : fx(0);
+        } else {
+          r[L] = g.x[L][q];
+          f = wp * g.w[L][q] * medium_f<fx>(M, kind, axis, r, g.dim);
+        }
+        const fx fr = f * tcr, fi = f * tci;
+        // g = (fr + i fi) p: fr p + fi (i p), lane by lane the scalar fr pr - fi pi, fr pi + fi pr
+        const pcff gv = pcff_add(pcff_scale(pfac_of(fr.h, fr.l), pv), pcff_scale(pfac_of(fi.h, fi.l), pcff_times_i(pv)));
+#pragma unroll
+        for (int k = 0; k <= P; ++k) pacc_mul(acc[k], pfac_of(b[k].h, b[k].l), gv);
+      }
+      {
+        const int j = e - 1;
+        if (j >= 0 && j < nL) pcff_store(out + (long long)j * inner + i, pacc_get(acc[0]));
+      }
+#pragma unroll
+      for (int k = 0; k < P; ++k) {
+        win[k] = win[k + 1];
+        acc[k] = acc[k + 1];
+      }
+      win[P] = next;
+      pacc_zero(acc[P]);
+    }
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+      const int j = e1 - 1 + k;
+      const pcff a = pacc_get(acc[k]);
+      if (e1 < EL) {
+        pcff_store(side + ((long long)ch * P + k) * inner + i, a);
+      } else if (j >= 0 && j < nL) {
+        pcff_store(out + (long long)j * inner + i, a);
+      }
+    }
+  }
+}
+
 // w(q) V(r_q) at every Gauss point of a 3-D grid, [q_z][q_y][q_x] (x fastest), evaluated in binary64 and
-// stored as FP32 and double-float: the per-point factor of the potential term of k_fused_last
-__global__ void k_vtab3(AxisDev A0, AxisDev A1, AxisDev A2, MediumT<double> M, float* __restrict__ t32,
-                        fx* __restrict__ tx) {
+// stored as double-float: the per-point factor of the potential term of the double-float k_fused_last
+// (the FP32 pass evaluates the potential at the points)
+__global__ void k_vtab3(AxisDev A0, AxisDev A1, AxisDev A2, MediumT<double> M, fx* __restrict__ tx) {
   const long long total = (long long)A0.Q * A1.Q * A2.Q;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
@@ -545,7 +768,6 @@ __global__ void k_vtab3(AxisDev A0, AxisDev A1, AxisDev A2, MediumT<double> M, f
     const int q1 = (int)(t % A1.Q), q2 = (int)(t / A1.Q);
     double r[3] = {A0.x[q0], A1.x[q1], A2.x[q2]};
     const double v = A0.w[q0] * A1.w[q1] * A2.w[q2] * medium_f<double>(M, 0, 0, r, 3);
-    t32[idx] = (float)v;
     tx[idx] = fx(v);
   }
 }
@@ -699,27 +921,26 @@ __global__ void k_fused_last_reduce_ff(const C<T>* __restrict__ in, AxisDev A0, 
         wp = ff_mul(wp, ff{A.fw[q], A.lw[q]});
       }
     }
-    cff win[P + 1];  // coefficient e + k - 1 of the current element
+    // coefficient e + k - 1 of the current element, real and imaginary parts in the lanes of packed pairs
+    auto packed = [](const cff& c) { return pcff{f2_pack(c.r.h, c.i.h), f2_pack(c.r.l, c.i.l)}; };
+    pcff win[P + 1];
 #pragma unroll
     for (int k = 0; k <= P; ++k) {
       const int j = e0 + k - 1;
-      win[k] = (j >= 0 && j < nL) ? to_cff(in[(long long)j * inner + i]) : cff{{0.f, 0.f}, {0.f, 0.f}};
+      win[k] = packed((j >= 0 && j < nL) ? to_cff(in[(long long)j * inner + i]) : cff{{0.f, 0.f}, {0.f, 0.f}});
     }
     for (int e = e0; e < e1; ++e) {
       for (int qq = 0; qq < nq; ++qq) {
         const int q = e * nq + qq;
         const float* bh = AL.fB + (size_t)q * (P + 1);
         const float* bl = AL.lB + (size_t)q * (P + 1);
-        ffacc pr, pi;
-        acc_zero(pr);
-        acc_zero(pi);
+        pacc pm;  // the state at the point (both parts in one Dot2 chain of packed pairs)
+        pacc_zero(pm);
 #pragma unroll
-        for (int k = 0; k <= P; ++k) {
-          const ff bk = ff{bh[k], bl[k]};
-          acc_mul(pr, bk, win[k].r);
-          acc_mul(pi, bk, win[k].i);
-        }
-        const ff psr = acc_get(pr), psi = acc_get(pi);
+        for (int k = 0; k <= P; ++k) pacc_mul(pm, pfac_of(bh[k], bl[k]), win[k]);
+        const pcff pv = pacc_get(pm);
+        const float2 vh = f2_unpack(pv.h), vl = f2_unpack(pv.l);
+        const ff psr = ff{vh.x, vl.x}, psi = ff{vh.y, vl.y};
         ffacc m2;
         acc_zero(m2);
         acc_mul(m2, psr, psr);
@@ -734,7 +955,8 @@ __global__ void k_fused_last_reduce_ff(const C<T>* __restrict__ in, AxisDev A0, 
 #pragma unroll
       for (int k = 0; k < P; ++k) win[k] = win[k + 1];
       const int jn = e + P;
-      win[P] = (jn >= 0 && jn < nL && e + 1 < e1) ? to_cff(in[(long long)jn * inner + i]) : cff{{0.f, 0.f}, {0.f, 0.f}};
+      win[P] = packed((jn >= 0 && jn < nL && e + 1 < e1) ? to_cff(in[(long long)jn * inner + i])
+                                                         : cff{{0.f, 0.f}, {0.f, 0.f}});
     }
   }
   double v[4];
@@ -1557,6 +1779,15 @@ int nd_cuda_fail(cudaError_t e, const char* what) {
   return TDZ_ECUDA;
 }
 
+// grid of the row kernels: x over a row's `width` outputs, y over rows (grid-stride), about 16 blocks per SM
+inline dim3 row_grid(int width, long long rows) {
+  const int gx = (width + TPB - 1) / TPB;
+  const long long gy = std::max<long long>(1, std::min<long long>({rows, 65535LL, (148LL * 16 + gx - 1) / gx}));
+  return dim3((unsigned)gx, (unsigned)gy);
+}
+
+constexpr size_t kFusedStageMax = 72 * 1024;  // shared-memory tables of k_fused_last: three blocks per SM
+
 inline int grid_for(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + TPB - 1) / TPB, 148 * 16)); }
 
 // element chunks of the fused last-axis passes: enough threads (about 150k) over the pencils, each
@@ -1616,7 +1847,6 @@ struct NdGeo {
   int apply_groups = 8;  // variant of the fused FP32 2-D apply (groups of offsets dy per row)
   float tune_ms[2] = {0.f, 0.f};  // autotuner timings of the variants G = 8, 16 (ms per apply)
   // 3-D mixed: w V at the Gauss points ([q_z][q_y][q_x]) for the FP32 and double-float passes
-  float* Vq32 = nullptr;
   fx* Vqx = nullptr;
 };
 
@@ -1909,12 +2139,16 @@ struct Apply {
   void interp(const T* B, const AxisDev& A, const C<T>* in, C<T>* out, long long outer, long long inner) {
     if (inner >= 32)
       k_interp_win<T, P><<<grid_for(outer * inner), TPB, 0, b->st>>>(B, A.nq, A.n, A.E, in, out, outer, inner);
+    else if (inner == 1)
+      k_interp_row<T, P><<<row_grid(A.Q, outer), TPB, 0, b->st>>>(B, A.nq, A.n, A.Q, in, out, outer);
     else
       k_interp<T, P><<<grid_for(outer * A.Q * inner), TPB, 0, b->st>>>(B, A.nq, A.n, A.Q, in, out, outer, inner);
   }
   void project(const T* B, const AxisDev& A, const C<T>* in, C<T>* out, long long outer, long long inner, int acc) {
     if (inner >= 32)
       k_project_win<T, P><<<grid_for(outer * inner), TPB, 0, b->st>>>(B, A.nq, A.n, A.E, in, out, outer, inner, acc);
+    else if (inner == 1)
+      k_project_row<T, P><<<row_grid(A.n, outer), TPB, 0, b->st>>>(B, A.nq, A.n, A.E, in, out, outer, acc);
     else
       k_project<T, P><<<grid_for(outer * A.n * inner), TPB, 0, b->st>>>(B, A.nq, A.n, A.E, in, out, outer, inner, acc);
   }
@@ -1960,9 +2194,23 @@ struct Apply {
     const long long nch = fused_nchunks(AL.E, inner, P, &echunk);
     C<T>* side = static_cast<C<T>*>(b->d_side);
     const T* ftab = (kind == 0 && dax < 0 && D == 3) ? Vtab : nullptr;
-    k_fused_last<T, P><<<grid_for(inner * nch), TPB, 0, b->st>>>(in, U, side, tab<T>(AL, L == dax ? TDB : TB), AL.nq,
-                                                                 AL.n, AL.E, inner, echunk, grid(), medium_t<T>(r->med),
-                                                                 kind, faxis, cr, ci, ftab);
+    // stage the last axis' tables in shared memory when they fit three blocks per SM
+    const size_t QL = (size_t)AL.E * AL.nq;
+    const size_t tab_bytes = sizeof(T) * QL * (P + 1 + (ftab ? 0 : 2));
+    const bool stage = tab_bytes <= kFusedStageMax;
+    static bool attr_set = false;
+    if (stage && !attr_set) {
+      cudaFuncSetAttribute(k_fused_last<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedStageMax);
+      attr_set = true;
+    }
+    if constexpr (std::is_same<T, fx>::value)
+      k_fused_last_fx<P><<<grid_for(inner * nch), TPB, 0, b->st>>>(in, U, side, tab<T>(AL, L == dax ? TDB : TB), AL.nq,
+                                                                   AL.n, AL.E, inner, echunk, grid(),
+                                                                   medium_t<T>(r->med), kind, faxis, cr, ci, ftab);
+    else
+      k_fused_last<T, P><<<grid_for(inner * nch), TPB, stage ? tab_bytes : 0, b->st>>>(
+          in, U, side, tab<T>(AL, L == dax ? TDB : TB), AL.nq, AL.n, AL.E, inner, echunk, grid(),
+          medium_t<T>(r->med), kind, faxis, cr, ci, ftab, stage ? 1 : 0);
     if (nch > 1)
       k_fused_fixup<T, P><<<grid_for((nch - 1) * P * inner), TPB, 0, b->st>>>(U, side, AL.n, inner, echunk, (int)nch);
     len[L] = AL.n;
@@ -2443,8 +2691,7 @@ int propagate_run(NdBatch* b, NdRun* r, const tdz::Ops& o, const double* field, 
       // a layer the FP32 inner solve applies V and the mass term by quadrature instead (the same operator)
       op32.Wm = r->cap ? nullptr : G.W32;
     }
-    opx.Vtab = G.Vqx;
-    op32.Vtab = G.Vq32;
+    opx.Vtab = G.Vqx;  // the FP32 inner solve evaluates the potential at the points instead
     C<fx>* cx_ = reinterpret_cast<C<fx>*>(b->d_z);    // c in double-float
     C<fx>* r0 = reinterpret_cast<C<fx>*>(b->d_r0);
     C<fx>* y = reinterpret_cast<C<fx>*>(b->d_y);      // A c, then delta
@@ -2970,12 +3217,8 @@ int nd_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* o
     set_error("tdz_batch_create: cuBLAS initialisation failed");
     return TDZ_ECUDA;
   }
-  // the FP32 fast-diagonalisation transforms run on the tensor cores as BF16x9 products (FP32
-  // accuracy); allow that for every shape. Their operands (states, eigenvectors) are finite, so the
-  // emulation's scan for infinities and NaNs is switched off (a non-finite state is still caught by
-  // the norm of the observables and by the refinement residual, neither of which goes through it)
-  cublasSetEmulationStrategy(b->blas, CUBLAS_EMULATION_STRATEGY_EAGER);
-  cublasSetEmulationSpecialValuesSupport(b->blas, CUDA_EMULATION_SPECIAL_VALUES_SUPPORT_NONE);
+  // cuBLAS serves only the binary64 path's fast-diagonalisation DGEMMs; the mixed path's transforms are
+  // the library's own tensor-core kernel (tdz_tc.cu)
   size_t stencil_bytes = 0;
   if (dim == 2)
     for (int g = 0; g < nops; ++g)
@@ -3012,16 +3255,15 @@ int nd_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* o
       for (int g = 0; g < nops; ++g) {
         if (ops[g]->o.med.pot_kind == TDZ_POT_ZERO) continue;
         const size_t nq3 = (size_t)geo[g].Q[0] * geo[g].Q[1] * geo[g].Q[2];
-        b->geo[g].Vq32 = static_cast<float*>(b->alloc(sizeof(float) * nq3));
         b->geo[g].Vqx = static_cast<fx*>(b->alloc(sizeof(fx) * nq3));
-        if (!b->geo[g].Vq32 || !b->geo[g].Vqx) {
+        if (!b->geo[g].Vqx) {
           delete b;
           set_error("tdz_batch_create: device allocation for the 3-D potential table failed");
           return TDZ_ENOMEM;
         }
         k_vtab3<<<grid_for((long long)nq3), TPB, 0, b->st>>>(geo[g].ax[0], geo[g].ax[1], geo[g].ax[2],
                                                              medium_t<double>(medium_dev(ops[g]->o.med)),
-                                                             b->geo[g].Vq32, b->geo[g].Vqx);
+                                                             b->geo[g].Vqx);
       }
     }
   }
@@ -3108,7 +3350,7 @@ int time_operator_p(NdBatch* b, NdRun* r, int reps, double* ms_out) {
                        static_cast<C<float>*>(b->w_t3), static_cast<C<float>*>(b->w_t4),
                        static_cast<C<float>*>(b->w_qa), static_cast<C<float>*>(b->w_qb)};
     if (stencil) op.Wm = r->cap ? nullptr : G.W32;
-    op.Vtab = G.Vq32;
+    op.Vtab = nullptr;  // the FP32 apply evaluates the potential at the points
     const C<float>* x = static_cast<const C<float>*>(b->w_p);
     C<float>* y = static_cast<C<float>*>(b->w_q);
     timed([&]() { op.apply(x, y, tau, ebar); });
