@@ -691,6 +691,9 @@ TDZ_DEV void rhs_fp64(const GeomDev& g, const RunDev& run, const Lane& L, double
 // reference for the relative residual.
 template <int P, bool SCALE, bool CAP>
 TDZ_DEV void rhs_mixed(const GeomDev& g, const RunDev& run, const Lane& L, ff tau, ff ebar, float& rr, float& bb) {
+  // complex double-float values are carried as packed pairs (real part in lane 0, imaginary in lane 1),
+  // so each Dot2 step of the two components is one f32x2 instruction; the sums and their order are
+  // those of the scalar form, component by component
   const int ks = L.ks;
   const float4* __restrict__ c = static_cast<const float4*>(run.state);
   const float4* __restrict__ W = run.W;
@@ -698,17 +701,17 @@ TDZ_DEV void rhs_mixed(const GeomDev& g, const RunDev& run, const Lane& L, ff ta
   const float2* __restrict__ HD = static_cast<const float2*>(g.H);
   const float2* __restrict__ WC = static_cast<const float2*>(g.Wc);
   cx<float>* __restrict__ rhs = static_cast<cx<float>*>(run.rhs);
-  cff uw[P + 1], ww[P + 1];
+  const pcff zero = pcff{f2_pack(0.f, 0.f), f2_pack(0.f, 0.f)};
+  pcff uw[P + 1], ww[P + 1];
   float2 cw[P + 1];
-  ffacc ar[P + 1], ai[P + 1];
+  pacc ac[P + 1];  // pending sums of rows j - d: (re, im)
   cx<float> sc[P + 1];
 #pragma unroll
   for (int d = 0; d <= P; ++d) {
-    uw[d] = cff{{0.f, 0.f}, {0.f, 0.f}};
-    ww[d] = uw[d];
+    uw[d] = zero;
+    ww[d] = zero;
     cw[d] = make_float2(0.f, 0.f);
-    acc_zero(ar[d]);
-    acc_zero(ai[d]);
+    pacc_zero(ac[d]);
     sc[d] = czero<float>();
   }
   rr = 0.f;
@@ -730,16 +733,16 @@ TDZ_DEV void rhs_mixed(const GeomDev& g, const RunDev& run, const Lane& L, ff ta
         }
       }
     }
-    cff u = cff{{0.f, 0.f}, {0.f, 0.f}}, w = u;
+    pcff u = zero, w = zero;
     float2 chi = make_float2(0.f, 0.f);
     ff s[P + 1], h[P + 1], wv[P + 1];
 #pragma unroll
     for (int d = 0; d <= P; ++d) s[d] = h[d] = wv[d] = ff{0.f, 0.f};
     if (ok) {
-      const float4 cc = c[ridx(row, chunk, ks)];
+      const float4 cc = c[ridx(row, chunk, ks)];  // (re.h, im.h, re.l, im.l)
       const float4 wq = W[ridx(row, chunk, ks)];
-      w = cff{{wq.x, wq.z}, {wq.y, wq.w}};
-      u = cff_add(cff{{2.f * cc.x, 2.f * cc.z}, {2.f * cc.y, 2.f * cc.w}}, w);
+      w = pcff{f2_pack(wq.x, wq.y), f2_pack(wq.z, wq.w)};
+      u = pcff_add(pcff{f2_pack(2.f * cc.x, 2.f * cc.y), f2_pack(2.f * cc.z, 2.f * cc.w)}, w);
       chi = make_float2(cc.x, cc.y);
       if (j >= 0) {
 #pragma unroll
@@ -758,8 +761,7 @@ TDZ_DEV void rhs_mixed(const GeomDev& g, const RunDev& run, const Lane& L, ff ta
     }
 #pragma unroll
     for (int d = P; d >= 1; --d) {
-      ar[d] = ar[d - 1];
-      ai[d] = ai[d - 1];
+      ac[d] = ac[d - 1];
       uw[d] = uw[d - 1];
       ww[d] = ww[d - 1];
       if (SCALE) {
@@ -770,51 +772,35 @@ TDZ_DEV void rhs_mixed(const GeomDev& g, const RunDev& run, const Lane& L, ff ta
     uw[0] = u;
     ww[0] = w;
     cw[0] = chi;
-    acc_zero(ar[0]);
-    acc_zero(ai[0]);
+    pacc_zero(ac[0]);
     sc[0] = czero<float>();
-    // r.re = -S w.re + (tau H) u.im ;  r.im = -S w.im - (tau H) u.re
-    // own row: four independent compensated partial sums per component (short dependency chains)
+    // r.re = -S w.re + (tau H) u.im - (tau W) u.re ;  r.im = -S w.im - (tau H) u.re - (tau W) u.im
+    // own row: four independent compensated partial sums (short dependency chains)
     if (j >= 0 && j < L.m) {
-      ffacc pr[4], pi[4];
+      pacc pa[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        acc_zero(pr[q]);
-        acc_zero(pi[q]);
-      }
+      for (int q = 0; q < 4; ++q) pacc_zero(pa[q]);
 #pragma unroll
       for (int d = 0; d <= P; ++d) {
-        acc_mul(pr[(d & 1)], ff_neg(s[d]), ww[d].r);
-        acc_mul(pr[2 + (d & 1)], h[d], uw[d].i);
-        acc_mul(pi[(d & 1)], ff_neg(s[d]), ww[d].i);
-        acc_mul(pi[2 + (d & 1)], ff_neg(h[d]), uw[d].r);
-        if constexpr (CAP) {
-          acc_mul(pr[(d & 1)], ff_neg(wv[d]), uw[d].r);
-          acc_mul(pi[(d & 1)], ff_neg(wv[d]), uw[d].i);
-        }
+        const pfac ns = pfac_of(-s[d].h, -s[d].l);
+        pacc_mul(pa[(d & 1)], ns, ww[d]);
+        pacc_mul(pa[2 + (d & 1)], pfac2_of(h[d].h, h[d].l, -h[d].h, -h[d].l), pcff_swap(uw[d]));
+        if constexpr (CAP) pacc_mul(pa[(d & 1)], pfac_of(-wv[d].h, -wv[d].l), uw[d]);
         if (SCALE) {
           sc[0].r = fmaf(s[d].h, cw[d].x, sc[0].r);
           sc[0].i = fmaf(s[d].h, cw[d].y, sc[0].i);
         }
       }
-      ff tr = ff_add(ff_add(acc_get(pr[0]), acc_get(pr[1])), ff_add(acc_get(pr[2]), acc_get(pr[3])));
-      ff ti = ff_add(ff_add(acc_get(pi[0]), acc_get(pi[1])), ff_add(acc_get(pi[2]), acc_get(pi[3])));
-      ar[0].s = tr.h;
-      ar[0].c = tr.l;
-      ai[0].s = ti.h;
-      ai[0].c = ti.l;
+      const pcff t = pcff_add(pcff_add(pacc_get(pa[0]), pacc_get(pa[1])), pcff_add(pacc_get(pa[2]), pacc_get(pa[3])));
+      ac[0].s = t.h;
+      ac[0].c = t.l;
     }
 #pragma unroll
     for (int d = 1; d <= P; ++d) {
       if (j - d >= 0 && j - d < L.m) {
-        acc_mul(ar[d], ff_neg(s[d]), w.r);
-        acc_mul(ar[d], h[d], u.i);
-        acc_mul(ai[d], ff_neg(s[d]), w.i);
-        acc_mul(ai[d], ff_neg(h[d]), u.r);
-        if constexpr (CAP) {
-          acc_mul(ar[d], ff_neg(wv[d]), u.r);
-          acc_mul(ai[d], ff_neg(wv[d]), u.i);
-        }
+        pacc_mul(ac[d], pfac_of(-s[d].h, -s[d].l), w);
+        pacc_mul(ac[d], pfac2_of(h[d].h, h[d].l, -h[d].h, -h[d].l), pcff_swap(u));
+        if constexpr (CAP) pacc_mul(ac[d], pfac_of(-wv[d].h, -wv[d].l), u);
         if (SCALE) {
           sc[d].r = fmaf(s[d].h, chi.x, sc[d].r);
           sc[d].i = fmaf(s[d].h, chi.y, sc[d].i);
@@ -823,7 +809,9 @@ TDZ_DEV void rhs_mixed(const GeomDev& g, const RunDev& run, const Lane& L, ff ta
     }
     const int jf = j - P;
     if (jf >= 0 && jf < L.m) {
-      const cx<float> r = cx<float>{ff_f(acc_get(ar[P])), ff_f(acc_get(ai[P]))};
+      const pcff a = pacc_get(ac[P]);
+      const float2 f = f2_unpack(f2_add(a.h, a.l));  // ff_f on both lanes
+      const cx<float> r = cx<float>{f.x, f.y};
       rhs[ridx(jf, L.k, ks)] = r;
       rr = fmaf(r.r, r.r, fmaf(r.i, r.i, rr));
       if (SCALE) bb = fmaf(sc[P].r, sc[P].r, fmaf(sc[P].i, sc[P].i, bb));
