@@ -266,7 +266,11 @@ int  tdz_batch_tuning(const tdz_batch* b, int geometry, int* groups, double* ms)
  * pairs inside the transform, in shared memory, if bit 1 is set (else the kernels around the
  * transforms write the pairs to memory). variant (host, optional): the chosen v (-1 when the geometry
  * has no fast diagonalisation or the batch is not mixed); ms (host, optional, 4 doubles): ms per
- * preconditioner apply of variants 0..3. Errors: TDZ_EINVAL (bad handle or geometry index). */
+ * preconditioner apply of variants 0..3. Errors: TDZ_EINVAL (bad handle or geometry index).
+ * Autotuner cache (both autotuners): with the environment variable TDZ_TUNE_CACHE naming a file, each
+ * result is appended to it as one JSON object per line, {"key": ..., "values": [...]}, keyed by what
+ * was tuned, the sizes, the precision and the device name; a later batch creation with the same key
+ * takes the stored result instead of timing (the ms reported are then the stored timings). */
 int  tdz_batch_precond_tuning(const tdz_batch* b, int geometry, int* variant, double* ms);
 /* tdz_batch_time_operator (2-D/3-D): time one apply of the inner-solve operator y = A_n x of Eq. cn_system
  * (FP32 in a mixed batch, binary64 otherwise; the batch's operator and absorbing-layer choices) for a run

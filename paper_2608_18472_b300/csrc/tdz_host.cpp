@@ -10,7 +10,10 @@
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#include <cstdlib>
 #include <cstring>
+#include <fstream>
+#include <map>
 #include <mutex>
 #include <new>
 #include <string>
@@ -22,6 +25,73 @@ namespace tdz {
 
 static thread_local std::string g_err;
 void set_error(const std::string& msg) { g_err = msg; }
+
+// ----------------------------------------------------------------------------- autotuner cache
+// One JSON object per line, {"key": "...", "values": [v0, v1, ...]}, in the file named by the
+// environment variable TDZ_TUNE_CACHE; without it nothing is read or written. Keys name what was
+// tuned, the sizes, the precision and the GPU; a later line for the same key replaces an earlier one.
+namespace {
+std::mutex g_tune_mu;
+std::string g_tune_path;
+std::map<std::string, std::vector<double>> g_tune;
+
+void tune_load(const std::string& path) {
+  g_tune.clear();
+  g_tune_path = path;
+  std::ifstream f(path);
+  std::string line;
+  while (std::getline(f, line)) {
+    const std::string kk = "\"key\": \"", vk = "\"values\": [";
+    const size_t a = line.find(kk);
+    if (a == std::string::npos) continue;
+    const size_t b = line.find('"', a + kk.size());
+    const size_t c = line.find(vk, b == std::string::npos ? 0 : b);
+    if (b == std::string::npos || c == std::string::npos) continue;
+    const size_t d = line.find(']', c);
+    if (d == std::string::npos) continue;
+    std::vector<double> vals;
+    const std::string body = line.substr(c + vk.size(), d - c - vk.size());
+    size_t pos = 0;
+    bool ok = true;
+    while (pos < body.size() && ok) {
+      size_t e = body.find(',', pos);
+      if (e == std::string::npos) e = body.size();
+      const std::string tok = body.substr(pos, e - pos);
+      char* end = nullptr;
+      const double v = std::strtod(tok.c_str(), &end);
+      ok = end != tok.c_str();
+      if (ok) vals.push_back(v);
+      pos = e + 1;
+    }
+    if (ok) g_tune[line.substr(a + kk.size(), b - a - kk.size())] = vals;
+  }
+}
+}  // namespace
+
+bool tune_cache_get(const std::string& key, std::vector<double>& values) {
+  const char* path = std::getenv("TDZ_TUNE_CACHE");
+  if (!path || !*path) return false;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  if (g_tune_path != path) tune_load(path);
+  const auto it = g_tune.find(key);
+  if (it == g_tune.end()) return false;
+  values = it->second;
+  return true;
+}
+
+void tune_cache_put(const std::string& key, const std::vector<double>& values) {
+  const char* path = std::getenv("TDZ_TUNE_CACHE");
+  if (!path || !*path || key.find('"') != std::string::npos) return;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  if (g_tune_path != path) tune_load(path);
+  g_tune[key] = values;
+  std::ofstream f(path, std::ios::app);
+  if (!f) return;
+  f.precision(17);
+  f << "{\"key\": \"" << key << "\", \"values\": [";
+  for (size_t i = 0; i < values.size(); ++i) f << (i ? ", " : "") << values[i];
+  f << "]}\n";
+}
 
 // ----------------------------------------------------------------------------- Gauss-Legendre
 // Nodes are the roots of P_n, found by Newton's method on the three-term recurrence

@@ -9,6 +9,9 @@
 namespace tdz {
 
 void set_error(const std::string& msg);
+// autotuner cache in the file named by TDZ_TUNE_CACHE (absent: no cache)
+bool tune_cache_get(const std::string& key, std::vector<double>& values);
+void tune_cache_put(const std::string& key, const std::vector<double>& values);
 
 struct Basis {
   std::vector<double> knots;

@@ -1886,6 +1886,7 @@ struct NdBatch {
   int rb_geo = -1;
   double rb_key[3] = {0, 0, 0};
   int nsm = 148;  // SM count of the device (persistent grids)
+  std::string dev_name;  // the device's name (autotuner cache keys)
   void* d_side = nullptr;   // chunk-boundary partial sums of the fused last-axis pass
   size_t maxSide = 0;
   int maxn = 0;
@@ -1983,6 +1984,15 @@ int autotune_apply2d(NdBatch* b) {
         break;
       }
     if (!G.W32 || !r || r->cap) continue;  // an absorbing layer takes the unfused apply
+    const std::string key = "apply2d p=" + std::to_string(P) + " n=" + std::to_string(r->n[0]) + "," +
+                            std::to_string(r->n[1]) + " mixed dev=" + b->dev_name;
+    std::vector<double> hit;
+    if (tune_cache_get(key, hit) && hit.size() == 3 && (hit[0] == 8 || hit[0] == 16)) {
+      G.apply_groups = (int)hit[0];
+      G.tune_ms[0] = (float)hit[1];
+      G.tune_ms[1] = (float)hit[2];
+      continue;
+    }
     const C<float>* x = static_cast<const C<float>*>(b->w_p);
     C<float>* y = static_cast<C<float>*>(b->w_q);
     for (int c = 0; c < 2; ++c) {
@@ -2003,6 +2013,7 @@ int autotune_apply2d(NdBatch* b) {
       G.tune_ms[c] = tmin;
     }
     G.apply_groups = G.tune_ms[1] < G.tune_ms[0] ? 16 : 8;
+    if (rc == TDZ_OK) tune_cache_put(key, {(double)G.apply_groups, (double)G.tune_ms[0], (double)G.tune_ms[1]});
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -2402,6 +2413,15 @@ int autotune_fd(NdBatch* b) {
         break;
       }
     if (!G.fd || !G.Vt[0] || !r) continue;
+    std::string key = "fdtc dim=" + std::to_string(r->dim) + " np=";
+    for (int a = 0; a < r->dim; ++a) key += (a ? "," : "") + std::to_string(G.np[a]);
+    key += " mixed dev=" + b->dev_name;
+    std::vector<double> hit;
+    if (tune_cache_get(key, hit) && hit.size() == 5 && hit[0] >= 0 && hit[0] <= 3) {
+      G.tc_variant = (int)hit[0];
+      for (int c = 0; c < 4; ++c) G.tc_ms[c] = (float)hit[1 + c];
+      continue;
+    }
     const C<float>* x = static_cast<const C<float>*>(b->w_p);
     C<float>* y = static_cast<C<float>*>(b->w_q);
     float* w[4] = {static_cast<float*>(b->w_qa), static_cast<float*>(b->w_qb), static_cast<float*>(b->w_qc),
@@ -2426,6 +2446,8 @@ int autotune_fd(NdBatch* b) {
     for (int c = 1; c < 4; ++c)
       if (G.tc_ms[c] < G.tc_ms[best]) best = c;
     G.tc_variant = best;
+    if (rc == TDZ_OK)
+      tune_cache_put(key, {(double)best, (double)G.tc_ms[0], (double)G.tc_ms[1], (double)G.tc_ms[2], (double)G.tc_ms[3]});
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -3201,6 +3223,8 @@ int nd_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* o
     if (cudaGetDevice(&dev) == cudaSuccess &&
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && nsm > 0)
       b->nsm = nsm;
+    cudaDeviceProp prop{};
+    if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) b->dev_name = prop.name;
   }
   const size_t before_work = b->dev_bytes;
   const bool work_ok = alloc_work(b);

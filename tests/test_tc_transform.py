@@ -127,3 +127,24 @@ def test_operator_timing(tdz):
     b1 = tdz.Batch([ops1], [0], tdz.MIXED)
     with pytest.raises(tdz.TDZError):
         b1.time_operator(0, 2)
+
+
+def test_autotuner_cache(tdz, tmp_path, monkeypatch):
+    """With TDZ_TUNE_CACHE set, the autotuners write their results (one JSON object per line, keyed by
+    what was tuned, the sizes and the GPU) and a later batch of the same shapes reads them instead of
+    timing again."""
+    import json
+    import workloads as wl
+    path = tmp_path / "tune.jsonl"
+    monkeypatch.setenv("TDZ_TUNE_CACHE", str(path))
+    p = 7
+    t = wl.knots_for_nsplines(-20.0, 20.0, 70, p)
+    ops = tdz.Ops([tdz.Basis(t, p, p + 1) for _ in range(2)], wl.softcore_medium(0.5))
+    b1 = tdz.Batch([ops], [0], tdz.MIXED)
+    first = (b1.tuning(0), b1.precond_tuning(0))
+    lines = [json.loads(x) for x in path.read_text().splitlines()]
+    keys = [x["key"] for x in lines]
+    assert any(k.startswith("apply2d p=7 n=") for k in keys) and any(k.startswith("fdtc dim=2 np=") for k in keys)
+    b2 = tdz.Batch([ops], [0], tdz.MIXED)
+    assert (b2.tuning(0), b2.precond_tuning(0)) == first      # the cached values, not a new timing
+    assert len(path.read_text().splitlines()) == len(lines)   # nothing new written
