@@ -772,6 +772,24 @@ __global__ void k_vtab3(AxisDev A0, AxisDev A1, AxisDev A2, MediumT<double> M, f
   }
 }
 
+// w(q) m^-1 Z (r_q^2 + eps)^(-3/2) at every Gauss point of a 2-D/3-D grid (x fastest), in binary64,
+// stored as double-float: the point factor of the soft-core observables c^H G_a c (times x_a)
+__global__ void k_gtab(AxisDev A0, AxisDev A1, AxisDev A2, int dim, double zm, double eps, fx* __restrict__ tx) {
+  const long long total = (long long)A0.Q * A1.Q * (dim > 2 ? A2.Q : 1);
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int q0 = (int)(idx % A0.Q);
+    const long long t = idx / A0.Q;
+    const int q1 = (int)(t % A1.Q), q2 = dim > 2 ? (int)(t / A1.Q) : 0;
+    double w = A0.w[q0] * A1.w[q1], r2 = A0.x[q0] * A0.x[q0] + A1.x[q1] * A1.x[q1] + eps;
+    if (dim > 2) {
+      w *= A2.w[q2];
+      r2 += A2.x[q2] * A2.x[q2];
+    }
+    tx[idx] = fx(w * zm / (r2 * sqrt(r2)));
+  }
+}
+
 // out[e1(c) - 1 + k] += side[c][k] for every chunk c but the last (after k_fused_last)
 template <class T, int P>
 __global__ void k_fused_fixup(C<T>* __restrict__ out, const C<T>* __restrict__ side, int nL, long long inner,
@@ -894,7 +912,8 @@ TDZ_DEV cff to_cff(const C<fx>& v) { return cff{to_ff(v.r), to_ff(v.i)}; }
 
 template <int P, class T>
 __global__ void k_fused_last_reduce_ff(const C<T>* __restrict__ in, AxisDev A0, AxisDev A1, AxisDev AL, int dim,
-                                       long long inner, int echunk, MediumFF M, int kmass, double* res, GridRed gr) {
+                                       long long inner, int echunk, MediumFF M, int kmass,
+                                       const fx* __restrict__ gtab, double* res, GridRed gr) {
   __shared__ double sh[32];
   const int nL = AL.n, EL = AL.E, nq = AL.nq;
   const int nchunks = (EL + echunk - 1) / echunk;
@@ -946,11 +965,16 @@ __global__ void k_fused_last_reduce_ff(const C<T>* __restrict__ in, AxisDev A0, 
         acc_mul(m2, psr, psr);
         acc_mul(m2, psi, psi);
         r[L] = ff{AL.fx[q], AL.lx[q]};
-        const ff wq = ff_mul(ff_mul(wp, ff{AL.fw[q], AL.lw[q]}), acc_get(m2));
-        ff g[3], minv;
-        medium_grad_ff(M, r, dim, g, minv);
-        for (int a = 0; a < dim; ++a) acc_mul(acc[a], wq, g[a]);
-        if (kmass) acc_mul(acc[3], wq, minv);
+        if (gtab) {  // w m^-1 Z (r^2 + eps)^(-3/2) tabulated: the soft-core gradient is that times r_a
+          const ff wq = ff_mul(acc_get(m2), to_ff(gtab[(long long)q * inner + i]));
+          for (int a = 0; a < dim; ++a) acc_mul(acc[a], wq, r[a]);
+        } else {
+          const ff wq = ff_mul(ff_mul(wp, ff{AL.fw[q], AL.lw[q]}), acc_get(m2));
+          ff g[3], minv;
+          medium_grad_ff(M, r, dim, g, minv);
+          for (int a = 0; a < dim; ++a) acc_mul(acc[a], wq, g[a]);
+          if (kmass) acc_mul(acc[3], wq, minv);
+        }
       }
 #pragma unroll
       for (int k = 0; k < P; ++k) win[k] = win[k + 1];
@@ -1848,6 +1872,7 @@ struct NdGeo {
   float tune_ms[2] = {0.f, 0.f};  // autotuner timings of the variants G = 8, 16 (ms per apply)
   // 3-D mixed: w V at the Gauss points ([q_z][q_y][q_x]) for the FP32 and double-float passes
   fx* Vqx = nullptr;
+  fx* Gq = nullptr;  // soft-core observables' point factor (double-float), or null (evaluated per point)
 };
 
 struct NdBatch {
@@ -2633,7 +2658,8 @@ void observe(NdBatch* b, NdRun* r, Apply<T, P>& op, const C<T>* c, C<T>* y, cons
   red_zero(b, 4);
   k_fused_last_reduce_ff<P, T><<<grid_for(inner * nch), TPB, 0, b->st>>>(X, r->ax[0], r->ax[1], AL, r->dim, inner,
                                                                          echunk, medium_ff(r->med),
-                                                                         r->const_mass ? 0 : 1, b->d_red, b->gr);
+                                                                         r->const_mass ? 0 : 1, b->geo[r->geo].Gq,
+                                                                         b->d_red, b->gr);
   double q4[4];
   red_get(b, 4, q4);
   const double kq = r->const_mass ? r->cm * norm : q4[3];
@@ -3267,13 +3293,13 @@ int nd_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* o
       }
     }
   }
-  // 3-D mixed batches: tabulate w V at the Gauss points when the device has room for it (12 bytes
-  // per point, at most half of the free memory); otherwise V is evaluated per point
+  // 3-D mixed batches: tabulate w V at the Gauss points for the double-float passes when the device has
+  // room for it (8 bytes per point, at most half of the free memory); otherwise V is evaluated per point
   if (dim == 3 && precision == TDZ_MIXED) {
     size_t need = 0;
     for (int g = 0; g < nops; ++g)
       if (ops[g]->o.med.pot_kind != TDZ_POT_ZERO)
-        need += (size_t)geo[g].Q[0] * geo[g].Q[1] * geo[g].Q[2] * (sizeof(float) + sizeof(fx));
+        need += (size_t)geo[g].Q[0] * geo[g].Q[1] * geo[g].Q[2] * sizeof(fx);
     cudaMemGetInfo(&free_b, &total_b);
     if (need > 0 && need < free_b / 2) {
       for (int g = 0; g < nops; ++g) {
@@ -3290,6 +3316,20 @@ int nd_batch_create(const tdz_ops* const* ops, int nops, int nruns, const int* o
                                                              b->geo[g].Vqx);
       }
     }
+  }
+  // soft-core geometries of constant mass (both precisions): tabulate the observables' point factor
+  // w m^-1 Z (r^2 + eps)^(-3/2) when the device has room (8 bytes per point, at most half of the free
+  // memory); otherwise the gradient is evaluated per point in double-float
+  for (int g = 0; g < nops; ++g) {
+    const Medium& md = ops[g]->o.med;
+    if (md.pot_kind != TDZ_POT_SOFTCORE || md.mass_kind != TDZ_MASS_CONST) continue;
+    const size_t npts = (size_t)geo[g].Q[0] * geo[g].Q[1] * (dim > 2 ? geo[g].Q[2] : 1);
+    cudaMemGetInfo(&free_b, &total_b);
+    if (npts * sizeof(fx) >= free_b / 2) continue;
+    b->geo[g].Gq = static_cast<fx*>(b->alloc(sizeof(fx) * npts));
+    if (!b->geo[g].Gq) continue;
+    k_gtab<<<grid_for((long long)npts), TPB, 0, b->st>>>(geo[g].ax[0], geo[g].ax[1], geo[g].ax[dim > 2 ? 2 : 1], dim,
+                                                         md.pot_par[0] / md.mass_par[0], md.pot_par[1], b->geo[g].Gq);
   }
   cudaError_t e = cudaStreamSynchronize(b->st);
   if (e != cudaSuccess) {
