@@ -182,7 +182,9 @@ int  tdz_ground_state(const tdz_ops* ops, double* energy, double* c);
 /* ------------------------------------------------------------------ batch
  * A batch is a set of independent runs propagated together on one GPU (1-D:
  * one persistent launch per tdz_propagate call; 2-D/3-D: preconditioned COCG per
- * step, runs of a batch on concurrent workers). Run r uses ops[ops_index[r]];
+ * step, runs of a batch on concurrent workers: host threads with their own streams and work
+ * buffers, 8 by default or the environment variable TDZ_ND_WORKERS (1..64) at creation, bounded by
+ * a quarter of the free device memory). Run r uses ops[ops_index[r]];
  * runs may have different sizes; all operators of a batch have the same
  * dimension and degree. precision is TDZ_FP64 or TDZ_MIXED.
  * cuda_stream: a cudaStream_t (NULL = the legacy default stream); every GPU

@@ -1068,14 +1068,29 @@ __global__ void k_qform2_y(const C<T>* __restrict__ c, const C<T>* __restrict__ 
   grid_reduce<3>(v, res, gr, sh);
 }
 
-// COCG update: x += alpha p; r -= alpha q; res[0] += ||r||^2
+
+
+// a / b for complex binary64 scalars, 0 when b = 0
+__device__ __forceinline__ double2 cdiv_or_zero(const double* a, const double* b) {
+  const double br = b[0], bi = b[1];
+  const double d = br * br + bi * bi;
+  if (d == 0.0) return make_double2(0.0, 0.0);
+  return make_double2((a[0] * br + a[1] * bi) / d, (a[1] * br - a[0] * bi) / d);
+}
+
+// COCG update: x += alpha p; r -= alpha q; res[0] += ||r||^2, with alpha = rho / (p^T q) read from the
+// reduction slots (0 when p^T q = 0)
 template <class T>
-__global__ void k_cocg_update(C<T>* __restrict__ x, C<T>* __restrict__ r, const C<T>* __restrict__ p,
-                              const C<T>* __restrict__ q, long long n, double ar, double ai, double* res,
-                              GridRed gr) {
+__global__ void k_cocg_update_dev(C<T>* __restrict__ x, C<T>* __restrict__ r, const C<T>* __restrict__ p,
+                                  const C<T>* __restrict__ q, long long n, const double* rho, const double* pq,
+                                  double* res, GridRed gr) {
   __shared__ double sh[32];
+  __shared__ double2 s_al;  // one complex division per block, not per thread (the FP64 rate is low)
+  if (threadIdx.x == 0) s_al = cdiv_or_zero(rho, pq);
+  __syncthreads();
+  const double2 al = s_al;
   double acc = 0.0;
-  const T a_r = (T)ar, a_i = (T)ai;
+  const T a_r = (T)al.x, a_i = (T)al.y;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const C<T> pv = p[i], qv = q[i];
     C<T> xv = x[i], rv = r[i];
@@ -1092,10 +1107,15 @@ __global__ void k_cocg_update(C<T>* __restrict__ x, C<T>* __restrict__ r, const 
   grid_reduce<1>(v, res, gr, sh);
 }
 
-// p = z + beta p
+// p = z + beta p with beta = rho_new / rho read from the reduction slots (0 when rho = 0)
 template <class T>
-__global__ void k_xpby(C<T>* __restrict__ p, const C<T>* __restrict__ z, long long n, double br, double bi) {
-  const T b_r = (T)br, b_i = (T)bi;
+__global__ void k_xpby_dev(C<T>* __restrict__ p, const C<T>* __restrict__ z, long long n, const double* rho_new,
+                           const double* rho) {
+  __shared__ double2 s_be;  // one complex division per block
+  if (threadIdx.x == 0) s_be = cdiv_or_zero(rho_new, rho);
+  __syncthreads();
+  const double2 be = s_be;
+  const T b_r = (T)be.x, b_i = (T)be.y;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const C<T> pv = p[i], zv = z[i];
     p[i] = C<T>{zv.r + b_r * pv.r - b_i * pv.i, zv.i + b_r * pv.i + b_i * pv.r};
@@ -2486,20 +2506,20 @@ int autotune_fd(NdBatch* b) {
 // z = M^-1 res and d_red[0..1] += res^T z (the rho of COCG; d_red zeroed by the caller): on the fast
 // diagonalisation path the product is accumulated while the result is written
 template <class T, int P>
-void precond_dot(NdBatch* b, NdRun* r, Apply<T, P>& op, const C<T>* res, C<T>* z, double tau) {
+void precond_dot(NdBatch* b, NdRun* r, Apply<T, P>& op, const C<T>* res, C<T>* z, double tau, double* dot) {
   if (use_fd(b, r)) {
     if constexpr (std::is_same<T, float>::value) {
       const int rc = fd_apply32(b, r, res, z, reinterpret_cast<float*>(op.qa), reinterpret_cast<float*>(op.qb),
-                                static_cast<float*>(b->w_qc), static_cast<float*>(b->w_qd), tau, b->d_red);
+                                static_cast<float*>(b->w_qc), static_cast<float*>(b->w_qd), tau, dot);
       if (rc != TDZ_OK && r->status == TDZ_OK) r->status = rc;
     } else {
-      fd_apply64(b, r, res, z, reinterpret_cast<double*>(op.qa), reinterpret_cast<double*>(op.qb), tau, b->d_red);
+      fd_apply64(b, r, res, z, reinterpret_cast<double*>(op.qa), reinterpret_cast<double*>(op.qb), tau, dot);
     }
     return;
   }
   cudaMemcpyAsync(z, res, sizeof(C<T>) * r->N, cudaMemcpyDeviceToDevice, b->st);
   line_precond<T, P>(b, r, z);
-  k_bdot<T><<<grid_for(r->N), TPB, 0, b->st>>>(res, z, r->N, b->d_red, b->gr);
+  k_bdot<T><<<grid_for(r->N), TPB, 0, b->st>>>(res, z, r->N, dot, b->gr);
 }
 
 // reads the reduction slots (and, in the same copy, the error word in the last slot)
@@ -2517,42 +2537,45 @@ double* red_get(NdBatch* b, int k, double* host) {
 void red_zero(NdBatch* b, int k) { cudaMemsetAsync(b->d_red, 0, sizeof(double) * k, b->st); }
 
 // Preconditioned COCG on A x = r (x starts at 0). Returns iterations; final ||r||^2 in *rr.
+// The step lengths alpha = rho / (p^T q) and beta = rho_new / rho are formed on the device from the
+// reduction slots (rho alternates between two slots, so no kernel reads a slot it overwrites), and
+// the host reads the slots once per iteration, after the update, for the convergence test.
+// Slots of d_red: [0..1] p^T q, [2] ||r||^2, [4..5] and [6..7] rho.
 template <class T, int P>
 int cocg(NdBatch* b, NdRun* r, Apply<T, P>& op, C<T>* x, C<T>* res, C<T>* z, C<T>* p, C<T>* q, double tau,
          const double* ebar, double tol_abs2, int maxit, double* rr_out) {
   const long long N = r->N;
-  double h[4];
+  double h[8];
+  double* const pq = b->d_red;
+  double* const rrs = b->d_red + 2;
+  double* rho_slot[2] = {b->d_red + 4, b->d_red + 6};
+  int cur = 0;
   cudaMemsetAsync(x, 0, sizeof(C<T>) * N, b->st);
-  red_zero(b, 2);
-  precond_dot<T, P>(b, r, op, res, z, tau);
+  red_zero(b, 8);
+  precond_dot<T, P>(b, r, op, res, z, tau, rho_slot[cur]);
   cudaMemcpyAsync(p, z, sizeof(C<T>) * N, cudaMemcpyDeviceToDevice, b->st);
-  red_get(b, 2, h);
-  std::complex<double> rho(h[0], h[1]);
-  red_zero(b, 1);
-  k_nrm<T><<<grid_for(N), TPB, 0, b->st>>>(res, N, b->d_red, b->gr);
-  double rr = red_get(b, 1, h)[0];
+  k_nrm<T><<<grid_for(N), TPB, 0, b->st>>>(res, N, rrs, b->gr);
+  double rr = red_get(b, 8, h)[2];
   int it = 0;
+  if (b->wait_failed || (h[4] == 0.0 && h[5] == 0.0)) {
+    *rr_out = rr;
+    return 0;
+  }
   while (rr > tol_abs2 && it < maxit) {
     op.apply(p, q, tau, ebar);
-    red_zero(b, 2);
-    k_bdot<T><<<grid_for(N), TPB, 0, b->st>>>(p, q, N, b->d_red, b->gr);
-    red_get(b, 2, h);
-    const std::complex<double> pq(h[0], h[1]);
-    if (b->wait_failed || std::abs(pq) == 0.0) break;
-    const std::complex<double> alpha = rho / pq;
-    red_zero(b, 1);
-    k_cocg_update<T><<<grid_for(N), TPB, 0, b->st>>>(x, res, p, q, N, alpha.real(), alpha.imag(), b->d_red, b->gr);
-    rr = red_get(b, 1, h)[0];
+    cudaMemsetAsync(pq, 0, sizeof(double) * 3, b->st);
+    k_bdot<T><<<grid_for(N), TPB, 0, b->st>>>(p, q, N, pq, b->gr);
+    k_cocg_update_dev<T><<<grid_for(N), TPB, 0, b->st>>>(x, res, p, q, N, rho_slot[cur], pq, rrs, b->gr);
+    red_get(b, 8, h);
+    if (b->wait_failed || (h[0] == 0.0 && h[1] == 0.0)) break;  // p^T q = 0: the update was skipped
+    rr = h[2];
     ++it;
     if (!(rr > tol_abs2)) break;
-    red_zero(b, 2);
-    precond_dot<T, P>(b, r, op, res, z, tau);
-    red_get(b, 2, h);
-    const std::complex<double> rho_new(h[0], h[1]);
-    if (std::abs(rho) == 0.0) break;
-    const std::complex<double> beta = rho_new / rho;
-    rho = rho_new;
-    k_xpby<T><<<grid_for(N), TPB, 0, b->st>>>(p, z, N, beta.real(), beta.imag());
+    const int nxt = 1 - cur;
+    cudaMemsetAsync(rho_slot[nxt], 0, sizeof(double) * 2, b->st);
+    precond_dot<T, P>(b, r, op, res, z, tau, rho_slot[nxt]);
+    k_xpby_dev<T><<<grid_for(N), TPB, 0, b->st>>>(p, z, N, rho_slot[nxt], rho_slot[cur]);
+    cur = nxt;
   }
   *rr_out = rr;
   return it;
@@ -2875,7 +2898,13 @@ bool alloc_work(NdBatch* b) {
 
 // Extra workers for a batch of several runs (up to 8, within a quarter of the free device memory)
 int make_workers(NdBatch* b) {
-  const int want = std::min(b->nruns, 8) - 1;
+  // host threads (one stream each) that propagate runs concurrently: TDZ_ND_WORKERS (1..64), default 8
+  int nmax = 8;
+  if (const char* env = std::getenv("TDZ_ND_WORKERS")) {
+    const int v = std::atoi(env);
+    if (v >= 1 && v <= 64) nmax = v;
+  }
+  const int want = std::min(b->nruns, nmax) - 1;
   if (want <= 0) return TDZ_OK;
   size_t free_b = 0, total_b = 0;
   cudaMemGetInfo(&free_b, &total_b);
@@ -2903,8 +2932,6 @@ int make_workers(NdBatch* b) {
       delete w;
       return TDZ_ECUDA;
     }
-    cublasSetEmulationStrategy(w->blas, CUBLAS_EMULATION_STRATEGY_EAGER);
-    cublasSetEmulationSpecialValuesSupport(w->blas, CUDA_EMULATION_SPECIAL_VALUES_SUPPORT_NONE);
     if (!alloc_work(w)) {
       delete w;
       return TDZ_ENOMEM;
