@@ -994,23 +994,23 @@ TDZ_DEV void run_sum(double (&v)[NV], double (*sh)[5], double (*tot)[5], int k, 
     for (int q = 0; q < NV; ++q) v[q] = tot[j - k][q];
 }
 
-// The reduced systems of the runs whose first lane sits in the calling warp, one after the other, by the
-// whole warp (each run's separator blocks are in its own lanes' shared memory). `mine` describes the
-// calling lane's run, `go` whether that run takes part; a run is processed when its first lane says so.
+
+// The separator chains of a block's runs spread over its warps: chain j (the j-th run start in lane
+// order) goes to warp j mod (warps per block), so two runs that start in one warp are not solved one
+// after the other. Every thread of the block calls this (it holds a block barrier).
 template <int P, class T>
-TDZ_DEV void warp_chains(unsigned starts, const Red<T>& mine, int nsep, bool go, cx<T>* wt, int lane, bool factor,
-                         bool solve) {
-  unsigned rest = starts;
-  while (rest) {
-    const int b = __ffs(rest) - 1;
-    rest &= rest - 1;
-    const int ns = __shfl_sync(0xffffffffu, nsep, b);
-    const bool gob = __shfl_sync(0xffffffffu, (int)go, b) != 0;
-    if (!gob || ns <= 0) continue;
+TDZ_DEV void block_chains(const short* s_lead, int nlead, int* s_ns, int my_lead, bool lead, int nsep, bool go,
+                          cx<T>* lane_area, cx<T>* wt, int wib, int nwarps, int lane, bool factor, bool solve) {
+  if (lead) s_ns[my_lead] = go ? nsep : 0;
+  __syncthreads();
+  for (int j = wib; j < nlead; j += nwarps) {
+    const int ns = s_ns[j];
+    if (ns <= 0) continue;
+    cx<T>* base = lane_area + (size_t)s_lead[j] * red_lane_elems(P);
     Red<T> r;
-    r.Dg = reinterpret_cast<cx<T>*>(__shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(mine.Dg), b));
-    r.E = reinterpret_cast<cx<T>*>(__shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(mine.E), b));
-    r.rb = reinterpret_cast<cx<T>*>(__shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(mine.rb), b));
+    r.Dg = base;
+    r.E = base + ns * P * P;
+    r.rb = base + 2 * ns * P * P;
     r.Wt = wt;
     if (factor) red_factor<P, T>(r, ns, lane);
     if (solve) red_solve<P, T>(r, ns, lane);
@@ -1029,6 +1029,10 @@ __global__ void __launch_bounds__(256) cn1d_kernel(StepArgs A) {
   using T = typename std::conditional<MIXED, float, double>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_group;
+  __shared__ short s_lead[256];  // lanes that start a run, in lane order
+  __shared__ int s_ns[256];      // their chain lengths for the current chain call
+  __shared__ int s_wcnt[8];
+  __shared__ int s_nlead;
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int lpb = blockDim.x;
@@ -1069,6 +1073,24 @@ __global__ void __launch_bounds__(256) cn1d_kernel(StepArgs A) {
     }
     const bool lead = has && L.k == 0;  // writes the run's results; its warp runs the reduced system
     const unsigned starts = __ballot_sync(0xffffffffu, lead);
+    int my_lead = -1;
+    {
+      if (lane == 0) s_wcnt[wib] = __popc(starts);
+      __syncthreads();
+      if (lead) {
+        int off = __popc(starts & ((1u << lane) - 1u));
+        for (int w = 0; w < wib; ++w) off += s_wcnt[w];
+        my_lead = off;
+        s_lead[off] = (short)threadIdx.x;
+      }
+      if (threadIdx.x == 0) {
+        int n = 0;
+        for (int w = 0; w < (lpb >> 5); ++w) n += s_wcnt[w];
+        s_nlead = n;
+      }
+      __syncthreads();
+    }
+    const int nlead = s_nlead;
     const double* E = A.field + (size_t)rid * (A.nsteps + 1);
     double* obs = A.obs + (size_t)rid * A.nsteps * 5;
     int status = has ? run.status : TDZ_OK;
@@ -1093,7 +1115,8 @@ __global__ void __launch_bounds__(256) cn1d_kernel(StepArgs A) {
         __syncthreads();
         if (W.up) sweep2<P, double, false, CAP>(g, run, W, tau_d, ebar_d, red);
         __syncthreads();
-        warp_chains<P, double>(starts, red, nsep, work, red.Wt, lane, true, true);
+        block_chains<P, double>(s_lead, nlead, s_ns, my_lead, lead, nsep, work, lane_area, red.Wt, wib, lpb >> 5, lane,
+                                true, true);
         __syncthreads();
         if (W.active) substitute<P, double, false, CAP>(g, run, W, tau_d, ebar_d, red);  // c += delta
         __syncthreads();
@@ -1114,7 +1137,8 @@ __global__ void __launch_bounds__(256) cn1d_kernel(StepArgs A) {
         __syncthreads();
         if (W.up) sweep2<P, float, true, CAP>(g, run, W, tau_f, ebar_f, red);
         __syncthreads();
-        warp_chains<P, float>(starts, red, nsep, work, red.Wt, lane, true, true);
+        block_chains<P, float>(s_lead, nlead, s_ns, my_lead, lead, nsep, work, lane_area, red.Wt, wib, lpb >> 5, lane,
+                               true, true);
         __syncthreads();
         if (W.active) substitute<P, float, true, CAP>(g, run, W, tau_f, ebar_f, red);  // w += delta
         __syncthreads();
@@ -1133,7 +1157,8 @@ __global__ void __launch_bounds__(256) cn1d_kernel(StepArgs A) {
           __syncthreads();
           if (need && W.up) resolve_bwd<P, float, true, CAP>(g, run, W, tau_f, ebar_f, red);
           __syncthreads();
-          warp_chains<P, float>(starts, red, nsep, need, red.Wt, lane, false, true);
+          block_chains<P, float>(s_lead, nlead, s_ns, my_lead, lead, nsep, need, lane_area, red.Wt, wib, lpb >> 5,
+                                 lane, false, true);
           __syncthreads();
           if (need && W.active) substitute<P, float, true, CAP>(g, run, W, tau_f, ebar_f, red);
           __syncthreads();
