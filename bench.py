@@ -47,10 +47,10 @@ sys.path.insert(0, ROOT)
 import workloads as wl  # noqa: E402
 
 # DRAM bytes (read + write) per coefficient-step of the mixed 1-D kernel, from one ncu capture of the
-# current kernel (lane-packed, residual on packed f32x2 pairs) on the DQW batch: 3.2905 GB read +
-# 0.9207 GB written in the 3-step warm-up launch of 1 873 260 coefficients; the traffic of a timed
-# launch is this times its coefficient-steps.
-NCU_DRAM_BYTES_PER_COEFF_STEP = 749.4
+# current kernel (lane-packed, residual on packed f32x2 pairs, separator chains spread over the warps)
+# on the DQW batch: 3.3143 GB read + 0.9234 GB written in the 3-step warm-up launch of 1 873 260
+# coefficients; the traffic of a timed launch is this times its coefficient-steps.
+NCU_DRAM_BYTES_PER_COEFF_STEP = 754.0
 METRIC = "TDSE coefficient-updates/s: batched mixed vs plain FP64 at stated HHG/norm error"
 UNIT = "coefficient-updates/s"
 
