@@ -643,6 +643,52 @@ __global__ void k_fused_last(const C<T>* __restrict__ in, C<T>* __restrict__ out
   }
 }
 
+// ------------------------------------------------------------------------------- reductions
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  v = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+  if (w == 0) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  }
+  return v;
+}
+
+// Fixed-order grid reduction, so that repeated runs give bitwise equal sums: every block stores its block
+// sums in its own slot of `part`; the last block to arrive (ticket counter) adds the slots in block order -
+// the same order whichever block finishes last - and adds the totals to res[0..NV). Called by every thread
+// of the block, with v holding the block's sums in thread 0.
+struct GridRed {
+  double* part;      // [blocks][4]
+  unsigned* ticket;  // zero between launches (the last block resets it)
+};
+template <int NV>
+__device__ __forceinline__ void grid_reduce(const double (&v)[NV], double* res, GridRed gr, double* sh) {
+  __shared__ int s_last;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) gr.part[(size_t)blockIdx.x * 4 + k] = v[k];
+    __threadfence();
+    s_last = atomicAdd(gr.ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double t = 0.0;
+    for (unsigned q = threadIdx.x; q < gridDim.x; q += blockDim.x) t += __ldcg(gr.part + (size_t)q * 4 + k);
+    t = block_sum(t, sh);
+    if (threadIdx.x == 0) res[k] += t;
+  }
+  if (threadIdx.x == 0) *gr.ticket = 0;
+}
+
 // k_fused_last for double-float (the mixed path's residual applies): the same pass and the same
 // arithmetic, bitwise, with the real and imaginary parts of each complex double-float value carried in
 // the two lanes of packed f32x2 registers, so every double-float step serves both parts at once.
@@ -661,16 +707,26 @@ __device__ __forceinline__ pcff pcff_times_i(pcff a) {
   return pcff{f2_pack(-h.y, h.x), f2_pack(-l.y, l.x)};
 }
 
-// three blocks of 256 per SM (80 registers, some spilled to L1): measured faster than two blocks at 128
-template <int P>
+// three blocks of 256 per SM (80 registers, some spilled to L1): measured faster than two blocks at 128.
+// OBS: the pass also reduces the soft-core observables of its input, whose pencils are those of the
+// state c (the first residual apply of a step takes c^n, the state whose observables the previous step
+// left open): res[a] += sum_q gtab(q) x_a(q) |psi(q)|^2 for a < dim, i.e. c^H G_a c of Eq.
+// pdm_acceleration with gtab = w m^-1 Z (r^2 + eps)^(-3/2) (constant mass). psi(q) is the value the pass
+// interpolates for the potential term anyway; along a pencil only x_L varies, so the pencil keeps
+// sum_q gtab |psi|^2 and sum_q gtab x_L |psi|^2 and scales the first by the pencil's fixed x_a, a < L.
+template <int P, bool OBS>
 __global__ void __launch_bounds__(256, 3) k_fused_last_fx(const C<fx>* __restrict__ in, C<fx>* __restrict__ out, C<fx>* __restrict__ side,
                                 const fx* __restrict__ Bl, int nq, int nL, int EL, long long inner, int echunk,
                                 QGrid<fx> g, MediumT<fx> M, int kind, int axis, double cr, double ci,
-                                const fx* __restrict__ ftab) {
+                                const fx* __restrict__ ftab, const fx* __restrict__ gtab, double* ores, GridRed gr) {
   const int nchunks = (EL + echunk - 1) / echunk;
   const long long total = inner * nchunks;
   const int L = g.dim - 1;
   const fx tcr = fx(cr), tci = fx(ci);
+  const bool imag_only = cr == 0.0;  // the potential term i tau V: no real part to scale
+  ffacc oacc[OBS ? 3 : 1];
+  if constexpr (OBS)
+    for (int a = 0; a < 3; ++a) acc_zero(oacc[a]);
   for (long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x; tid < total;
        tid += (long long)gridDim.x * blockDim.x) {
     const long long i = tid % inner;
@@ -685,6 +741,9 @@ __global__ void __launch_bounds__(256, 3) k_fused_last_fx(const C<fx>* __restric
       r[a] = g.x[a][q];
       wp *= g.w[a][q];
     }
+    ffacc s0, s1;  // OBS: sum gtab |psi|^2 and sum gtab x_L |psi|^2 along this pencil chunk
+    acc_zero(s0);
+    acc_zero(s1);
     pcff win[P + 1];  // coefficient e + k - 1 of the current element
     pacc acc[P + 1];  // partial projections onto coefficient e + k - 1
 #pragma unroll
@@ -715,6 +774,17 @@ __global__ void __launch_bounds__(256, 3) k_fused_last_fx(const C<fx>* __restric
 #pragma unroll
         for (int k = 0; k <= P; ++k) pacc_mul((k & 1) ? m1 : m0, pfac_of(b[k].h, b[k].l), win[k]);
         const pcff pv = pcff_add(pacc_get(m0), pacc_get(m1));
+        if constexpr (OBS) {
+          const float2 vh = f2_unpack(pv.h), vl = f2_unpack(pv.l);
+          const ff psr = ff{vh.x, vl.x}, psi = ff{vh.y, vl.y};
+          ffacc m2;
+          acc_zero(m2);
+          acc_mul(m2, psr, psr);
+          acc_mul(m2, psi, psi);
+          const ff wq = ff_mul(acc_get(m2), to_ff(gtab[(long long)q * inner + i]));
+          acc_add(s0, wq);
+          acc_mul(s1, wq, to_ff(g.x[L][q]));
+        }
         fx f;
         if (ftab) {
           f = fpre[0];
@@ -726,9 +796,13 @@ __global__ void __launch_bounds__(256, 3) k_fused_last_fx(const C<fx>* __restric
           r[L] = g.x[L][q];
           f = wp * g.w[L][q] * medium_f<fx>(M, kind, axis, r, g.dim);
         }
-        const fx fr = f * tcr, fi = f * tci;
+        const fx fi = f * tci;
         // g = (fr + i fi) p: fr p + fi (i p), lane by lane the scalar fr pr - fi pi, fr pi + fi pr
-        const pcff gv = pcff_add(pcff_scale(pfac_of(fr.h, fr.l), pv), pcff_scale(pfac_of(fi.h, fi.l), pcff_times_i(pv)));
+        pcff gv = pcff_scale(pfac_of(fi.h, fi.l), pcff_times_i(pv));
+        if (!imag_only) {
+          const fx fr = f * tcr;
+          gv = pcff_add(pcff_scale(pfac_of(fr.h, fr.l), pv), gv);
+        }
 #pragma unroll
         for (int k = 0; k <= P; ++k) pacc_mul(acc[k], pfac_of(b[k].h, b[k].l), gv);
       }
@@ -754,6 +828,20 @@ __global__ void __launch_bounds__(256, 3) k_fused_last_fx(const C<fx>* __restric
         pcff_store(out + (long long)j * inner + i, a);
       }
     }
+    if constexpr (OBS) {
+      const ff t0 = acc_get(s0);
+      for (int a = 0; a < L; ++a) acc_mul(oacc[a], t0, to_ff(r[a]));
+      acc_add(oacc[L], acc_get(s1));
+    }
+  }
+  if constexpr (OBS) {
+    __shared__ double sh[32];
+    double v[3];
+    for (int a = 0; a < 3; ++a) {
+      const ff t = acc_get(oacc[a]);
+      v[a] = block_sum((double)t.h + (double)t.l, sh);
+    }
+    grid_reduce<3>(v, ores, gr, sh);
   }
 }
 
@@ -809,52 +897,6 @@ __global__ void k_fused_fixup(C<T>* __restrict__ out, const C<T>* __restrict__ s
       *o = C<T>{v.r + a.r, v.i + a.i};
     }
   }
-}
-
-// ------------------------------------------------------------------------------- reductions
-__device__ __forceinline__ double block_sum(double v, double* sh) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __syncthreads();
-  if (l == 0) sh[w] = v;
-  __syncthreads();
-  v = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
-  if (w == 0) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  }
-  return v;
-}
-
-// Fixed-order grid reduction, so that repeated runs give bitwise equal sums: every block stores its block
-// sums in its own slot of `part`; the last block to arrive (ticket counter) adds the slots in block order -
-// the same order whichever block finishes last - and adds the totals to res[0..NV). Called by every thread
-// of the block, with v holding the block's sums in thread 0.
-struct GridRed {
-  double* part;      // [blocks][4]
-  unsigned* ticket;  // zero between launches (the last block resets it)
-};
-template <int NV>
-__device__ __forceinline__ void grid_reduce(const double (&v)[NV], double* res, GridRed gr, double* sh) {
-  __shared__ int s_last;
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) gr.part[(size_t)blockIdx.x * 4 + k] = v[k];
-    __threadfence();
-    s_last = atomicAdd(gr.ticket, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-#pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    double t = 0.0;
-    for (unsigned q = threadIdx.x; q < gridDim.x; q += blockDim.x) t += __ldcg(gr.part + (size_t)q * 4 + k);
-    t = block_sum(t, sh);
-    if (threadIdx.x == 0) res[k] += t;
-  }
-  if (threadIdx.x == 0) *gr.ticket = 0;
 }
 
 // Medium constants as double-float numbers (prepared on the host once per launch).
@@ -2095,6 +2137,10 @@ struct Apply {
   C<T>* qb;
   const T* Wm = nullptr;  // assembled 2-D stencil of the non-separable terms, or null (quadrature)
   const T* Vtab = nullptr;  // w V at the Gauss points (3-D), or null (evaluated per point)
+  // double-float only: when set, the next potential-term pass also reduces c^H G_a c of its input into
+  // obs_res[0..3) (k_fused_last_fx<P, true>; obs_gtab = the soft-core point factor); cleared by that pass
+  const fx* obs_gtab = nullptr;
+  double* obs_res = nullptr;
 
   // shape helpers: lengths of axes with the first `k` axes already in quadrature space
   void shape(int axis, const int* len, long long& outer, long long& inner) const {
@@ -2260,11 +2306,18 @@ struct Apply {
       cudaFuncSetAttribute(k_fused_last<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedStageMax);
       attr_set = true;
     }
-    if constexpr (std::is_same<T, fx>::value)
-      k_fused_last_fx<P><<<grid_for(inner * nch), TPB, 0, b->st>>>(in, U, side, tab<T>(AL, L == dax ? TDB : TB), AL.nq,
-                                                                   AL.n, AL.E, inner, echunk, grid(),
-                                                                   medium_t<T>(r->med), kind, faxis, cr, ci, ftab);
-    else
+    if constexpr (std::is_same<T, fx>::value) {
+      const bool obs = obs_res && kind == 0 && dax < 0;
+      if (obs)
+        k_fused_last_fx<P, true><<<grid_for(inner * nch), TPB, 0, b->st>>>(
+            in, U, side, tab<T>(AL, TB), AL.nq, AL.n, AL.E, inner, echunk, grid(), medium_t<T>(r->med), kind, faxis,
+            cr, ci, ftab, obs_gtab, obs_res, b->gr);
+      else
+        k_fused_last_fx<P, false><<<grid_for(inner * nch), TPB, 0, b->st>>>(
+            in, U, side, tab<T>(AL, L == dax ? TDB : TB), AL.nq, AL.n, AL.E, inner, echunk, grid(),
+            medium_t<T>(r->med), kind, faxis, cr, ci, ftab, nullptr, nullptr, b->gr);
+      if (obs) obs_res = nullptr, obs_gtab = nullptr;
+    } else
       k_fused_last<T, P><<<grid_for(inner * nch), TPB, stage ? tab_bytes : 0, b->st>>>(
           in, U, side, tab<T>(AL, L == dax ? TDB : TB), AL.nq, AL.n, AL.E, inner, echunk, grid(),
           medium_t<T>(r->med), kind, faxis, cr, ci, ftab, stage ? 1 : 0);
@@ -2634,12 +2687,16 @@ MediumFF medium_ff(const MediumDev& d) {
 
 // observables of the state c (given in the operator's arithmetic T: binary64 or double-float):
 // [d_a, a_a, norm]; y is scratch of the state's size
+// The observables of a state row (Sec. "Dipoles"): out[a] = c^H D_a c, out[D + a] = the acceleration
+// -c^H G_a c - E_a(t) c^H K c (Eq. pdm_acceleration), out[2D] = c^H S c. observe_kron forms the
+// Kronecker-product ones (norm, dipoles), observe_quad the Gauss-point ones (G_a, and K with a
+// variable mass), observe_finish the accelerations from them.
 template <class T, int P>
-void observe(NdBatch* b, NdRun* r, Apply<T, P>& op, const C<T>* c, C<T>* y, const double* Et, double* out) {
+void observe_kron(NdBatch* b, NdRun* r, Apply<T, P>& op, const C<T>* c, C<T>* y, double* out) {
   const long long N = r->N;
   double h[4];
   double zero3[3] = {0, 0, 0};
-  double norm = 0.0, dvals[3] = {0, 0, 0}, gvals[3];
+  double norm = 0.0, dvals[3] = {0, 0, 0};
   if (r->dim == 2) {
     // x-passes t = S_x c, u = D_x c, then the three forms in one y-pass
     const AxisDev& A0 = r->ax[0];
@@ -2671,7 +2728,12 @@ void observe(NdBatch* b, NdRun* r, Apply<T, P>& op, const C<T>* c, C<T>* y, cons
       dvals[a] = red_get(b, 2, h)[0];
     }
   }
-  // c^H G_a c and (variable mass) c^H K c at the Gauss points, fused along the last axis
+  for (int a = 0; a < r->dim; ++a) out[a] = dvals[a];
+  out[2 * r->dim] = norm;
+}
+// q4[a] = c^H G_a c (a < dim), q4[3] = c^H K c (variable mass), by one double-float Gauss-point pass
+template <class T, int P>
+void observe_quad(NdBatch* b, NdRun* r, Apply<T, P>& op, const C<T>* c, double* q4) {
   const C<T>* X = op.to_pencils(c, -1);
   const int L = r->dim - 1;
   long long inner = 1;
@@ -2684,16 +2746,19 @@ void observe(NdBatch* b, NdRun* r, Apply<T, P>& op, const C<T>* c, C<T>* y, cons
                                                                          echunk, medium_ff(r->med),
                                                                          r->const_mass ? 0 : 1, b->geo[r->geo].Gq,
                                                                          b->d_red, b->gr);
-  double q4[4];
   red_get(b, 4, q4);
-  const double kq = r->const_mass ? r->cm * norm : q4[3];
-  for (int a = 0; a < r->dim; ++a) gvals[a] = q4[a];
+}
+void observe_finish(const NdRun* r, const double* q4, const double* Et, double* out) {
   const int D = r->dim;
-  for (int a = 0; a < D; ++a) {
-    out[a] = dvals[a];
-    out[D + a] = -gvals[a] - Et[a] * kq;
-  }
-  out[2 * D] = norm;
+  const double kq = r->const_mass ? r->cm * out[2 * D] : q4[3];
+  for (int a = 0; a < D; ++a) out[D + a] = -q4[a] - Et[a] * kq;
+}
+template <class T, int P>
+void observe(NdBatch* b, NdRun* r, Apply<T, P>& op, const C<T>* c, C<T>* y, const double* Et, double* out) {
+  double q4[4];
+  observe_kron<T, P>(b, r, op, c, y, out);
+  observe_quad<T, P>(b, r, op, c, q4);
+  observe_finish(r, q4, Et, out);
 }
 
 template <int P>
@@ -2770,6 +2835,17 @@ int propagate_run(NdBatch* b, NdRun* r, const tdz::Ops& o, const double* field, 
     C<fx>* rc = reinterpret_cast<C<fx>*>(b->d_rc);    // current residual
     C<float>* rf = static_cast<C<float>*>(b->w_r);
     C<float>* xf = static_cast<C<float>*>(b->w_x);
+    // Where the residual apply runs the double-float potential pass at the Gauss points (quadrature
+    // operator, soft-core point factor tabulated, constant mass), the Gauss-point observables of a step's
+    // new state are reduced inside the next step's first residual apply, whose input is that state: the
+    // row stays open until then (the last row of the call is closed by the standalone pass).
+    const bool defer_obs = !stencil && r->const_mass && r->med.pot_kind == TDZ_POT_SOFTCORE && G.Gq != nullptr;
+    double* open_row = nullptr;  // the row whose c^H G_a c is pending (reduction slots 8..10)
+    auto close_row = [&](const double* g3) {
+      double q4[4] = {g3[0], g3[1], g3[2], 0.0};
+      observe_finish(r, q4, open_row + 1, open_row + 1 + D);
+      open_row = nullptr;
+    };
     for (long long s = 0; s < nsteps && r->status == TDZ_OK && !b->wait_failed; ++s) {
       double ebar[3] = {0, 0, 0}, Et[3] = {0, 0, 0};
       for (int a = 0; a < D; ++a) {
@@ -2778,11 +2854,18 @@ int propagate_run(NdBatch* b, NdRun* r, const tdz::Ops& o, const double* field, 
       }
       double zero3[3] = {0, 0, 0};
       k_axby<double, fx><<<grid_for(N), TPB, 0, b->st>>>(c, cx_, N, 1.0, 0.0);
+      if (open_row) {
+        cudaMemsetAsync(b->d_red + 8, 0, sizeof(double) * 3, b->st);
+        opx.obs_gtab = G.Gq;
+        opx.obs_res = b->d_red + 8;
+      }
       opx.apply(cx_, y, tau, ebar);
       opx.kron(cx_, r0, 1, 0.0, zero3);
       red_zero(b, 1);
       k_nrm<fx><<<grid_for(N), TPB, 0, b->st>>>(r0, N, b->d_red, b->gr);
-      const double bb = red_get(b, 1, h)[0];
+      double h16[16];
+      const double bb = red_get(b, 16, h16)[0];
+      if (open_row) close_row(h16 + 8);
       const double tol2 = b->tol * b->tol * bb;
       k_axby<fx, fx><<<grid_for(N), TPB, 0, b->st>>>(y, r0, N, -2.0, 2.0);
       cudaMemsetAsync(y, 0, sizeof(C<fx>) * N, b->st);  // y is delta from here on
@@ -2825,8 +2908,18 @@ int propagate_run(NdBatch* b, NdRun* r, const tdz::Ops& o, const double* field, 
       row[0] = (double)(step0 + s + 1) * dt;
       for (int a = 0; a < D; ++a) row[1 + a] = Et[a];
       k_axby<double, fx><<<grid_for(N), TPB, 0, b->st>>>(c, cx_, N, 1.0, 0.0);
-      observe<fx, P>(b, r, opx, cx_, y, Et, row + 1 + D);
+      if (defer_obs) {
+        observe_kron<fx, P>(b, r, opx, cx_, y, row + 1 + D);
+        open_row = row;
+      } else {
+        observe<fx, P>(b, r, opx, cx_, y, Et, row + 1 + D);
+      }
       if (!std::isfinite(row[1 + 3 * D]) || !std::isfinite(row[1 + D])) r->status = TDZ_ENONFINITE;
+    }
+    if (open_row) {  // cx_ still holds the last step's state
+      double q4[4];
+      observe_quad<fx, P>(b, r, opx, cx_, q4);
+      close_row(q4);
     }
   }
   cudaError_t e = cudaStreamSynchronize(b->st);

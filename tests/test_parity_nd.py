@@ -406,3 +406,45 @@ def test_repeat_runs_are_bitwise_equal(tdz, name):
         assert np.array_equal(out[0][0], out[1][0]), prec
         assert np.array_equal(out[0][1], out[1][1]), prec
         assert out[0][2] == out[1][2]
+
+
+@pytest.mark.parametrize("name", ["softcore2d", "softcore3d"])
+def test_deferred_gauss_point_observables(tdz, name):
+    """Mixed precision with the Gauss-point operator: the Gauss-point observables c^H G_a c of each new
+    state are reduced inside the next step's first double-float residual apply, whose input is that
+    state, and the last step of a call by the standalone observables pass. One call of n steps against n
+    calls of one step (every row from the standalone pass): the states and the Kronecker-form
+    observables (time, field, dipoles, norm) are bitwise equal, the accelerations agree to double-float
+    rounding (the two passes interpolate psi in a different order)."""
+    knots, p, med, dt, nsteps, e0 = _case(name)
+    m, c0, field, c, obs = _reference(name)
+    dim = len(knots)
+    ops = tdz.Ops([tdz.Basis(k, p, p + 1) for k in knots], med)
+    n = 6
+    one = tdz.Batch([ops], [0], tdz.MIXED)
+    _configure(tdz, one, "quadrature", "lines")
+    one.set_state(0, c0)
+    one.propagate(np.ascontiguousarray(field[:n + 1]).reshape(1, n + 1, dim), dt, 0, n)
+    o_one, st = one.observe(0)
+    assert st == tdz.TDZ_OK
+    per = tdz.Batch([ops], [0], tdz.MIXED)
+    _configure(tdz, per, "quadrature", "lines")
+    per.set_state(0, c0)
+    rows = []
+    for s in range(n):
+        per.propagate(np.ascontiguousarray(field[s:s + 2]).reshape(1, 2, dim), dt, s, 1)
+        o, st = per.observe(0)
+        assert st == tdz.TDZ_OK
+        rows.append(o[0])
+    o_per = np.array(rows)
+    assert np.array_equal(one.get_state(0), per.get_state(0))
+    acc = list(range(1 + 2 * dim, 1 + 3 * dim))
+    other = [k for k in range(o_one.shape[1]) if k not in acc]
+    assert np.array_equal(o_one[:, other], o_per[:, other])
+    for k in acc:
+        scale = max(1.0, np.max(np.abs(o_per[:, k])))
+        assert np.max(np.abs(o_one[:, k] - o_per[:, k])) < 1e-12 * scale, k
+    # and both against the oracle's accelerations over the same steps
+    for k in acc:
+        scale = max(1e-3, np.max(np.abs(obs[:n, k])))
+        assert np.max(np.abs(o_one[:, k] - obs[:n, k])) < 1e-7 * scale, k
