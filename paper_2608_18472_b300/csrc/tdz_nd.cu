@@ -195,12 +195,22 @@ __global__ void k_axis_band(BandTerms<T> bt, const C<T>* __restrict__ in0, const
   bool need0 = false, need1 = false;  // input streams some term reads
 #pragma unroll
   for (int t = 0; t < NT; ++t) (bt.sel[t] ? need1 : need0) = true;
+  const bool narrow = total < (1LL << 31);  // 32-bit index arithmetic (the divisions below) when it fits
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
-    const long long i = idx % inner;
-    const long long oj = idx / inner;
-    const int j = (int)(oj % L);
-    const long long o = oj / L;
+    long long i, o;
+    int j;
+    if (narrow) {
+      const unsigned u = (unsigned)idx, in32 = (unsigned)inner, oj = u / in32;
+      i = u - oj * in32;
+      o = oj / (unsigned)L;
+      j = (int)(oj - (unsigned)o * (unsigned)L);
+    } else {
+      i = idx % inner;
+      const long long oj = idx / inner;
+      j = (int)(oj % L);
+      o = oj / L;
+    }
     Mac<T> mr[NT], mi[NT];
 #pragma unroll
     for (int d = -P; d <= P; ++d) {
@@ -983,6 +993,9 @@ __global__ void __launch_bounds__(256, 3) k_fused_last_reduce_ff(const C<T>* __r
         wp = ff_mul(wp, ff{A.fw[q], A.lw[q]});
       }
     }
+    ffacc s0, s1;  // tabulated factor: sum gtab |psi|^2 and sum gtab x_L |psi|^2 along this pencil chunk
+    acc_zero(s0);
+    acc_zero(s1);
     // coefficient e + k - 1 of the current element, real and imaginary parts in the lanes of packed pairs
     auto packed = [](const cff& c) { return pcff{f2_pack(c.r.h, c.i.h), f2_pack(c.r.l, c.i.l)}; };
     pcff win[P + 1];
@@ -1010,7 +1023,8 @@ __global__ void __launch_bounds__(256, 3) k_fused_last_reduce_ff(const C<T>* __r
         r[L] = ff{AL.fx[q], AL.lx[q]};
         if (gtab) {  // w m^-1 Z (r^2 + eps)^(-3/2) tabulated: the soft-core gradient is that times r_a
           const ff wq = ff_mul(acc_get(m2), to_ff(gtab[(long long)q * inner + i]));
-          for (int a = 0; a < dim; ++a) acc_mul(acc[a], wq, r[a]);
+          acc_add(s0, wq);        // r_a, a < L, is fixed along the pencil: applied once, below
+          acc_mul(s1, wq, r[L]);
         } else {
           const ff wq = ff_mul(ff_mul(wp, ff{AL.fw[q], AL.lw[q]}), acc_get(m2));
           ff g[3], minv;
@@ -1024,6 +1038,11 @@ __global__ void __launch_bounds__(256, 3) k_fused_last_reduce_ff(const C<T>* __r
       const int jn = e + P;
       win[P] = packed((jn >= 0 && jn < nL && e + 1 < e1) ? to_cff(in[(long long)jn * inner + i])
                                                          : cff{{0.f, 0.f}, {0.f, 0.f}});
+    }
+    if (gtab) {
+      const ff t0 = acc_get(s0);
+      for (int a = 0; a < L; ++a) acc_mul(acc[a], t0, r[a]);
+      acc_add(acc[L], acc_get(s1));
     }
   }
   double v[4];
@@ -1376,7 +1395,8 @@ __global__ void k_wapply(const T* __restrict__ Wm, const C<T>* __restrict__ x, C
   const long long N = (long long)nx * ny;
   for (long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x; row < N;
        row += (long long)gridDim.x * blockDim.x) {
-    const int ix = (int)(row % nx), iy = (int)(row / nx);
+    const int iy = N < (1LL << 32) ? (int)((unsigned)row / (unsigned)nx) : (int)(row / nx);
+    const int ix = (int)(row - (long long)iy * nx);
     Mac<T> mr, mi;
 #pragma unroll 1
     for (int dy = 0; dy <= P; ++dy) {
@@ -1886,6 +1906,28 @@ inline long long fused_nchunks(int E, long long inner, int P, int* echunk) {
   return (E + ec - 1) / ec;
 }
 
+// element chunks of the observables pass: as many blocks of 256 as fill one to three whole waves of
+// its three resident blocks per SM (the fewest idle slots in the last wave), each chunk at least 2P+2
+// elements long
+inline long long reduce_nchunks(int E, long long inner, int P, int* echunk) {
+  const long long wave = 148LL * 3 * 256, nmax = std::max(1, E / (2 * P + 2));
+  long long best = 1;
+  double best_fill = -1.0;
+  for (int m = 1; m <= 3; ++m) {
+    const long long nch = std::max<long long>(1, std::min<long long>(nmax, m * wave / inner));
+    const int ec = (int)((E + nch - 1) / nch);
+    const long long n = (E + ec - 1) / ec;
+    const long long thr = ((inner * n + 255) / 256) * 256;
+    const double fill = (double)thr / (double)(((thr + wave - 1) / wave) * wave);
+    if (fill >= best_fill) {
+      best_fill = fill;
+      best = n;
+    }
+  }
+  *echunk = (int)((E + best - 1) / best);
+  return (E + *echunk - 1) / *echunk;
+}
+
 struct NdRun {
   int ops = 0;
   int dim = 0, P = 0;
@@ -2301,11 +2343,10 @@ struct Apply {
     const size_t QL = (size_t)AL.E * AL.nq;
     const size_t tab_bytes = sizeof(T) * QL * (P + 1 + (ftab ? 0 : 2));
     const bool stage = tab_bytes <= kFusedStageMax;
-    static bool attr_set = false;
-    if (stage && !attr_set) {
-      cudaFuncSetAttribute(k_fused_last<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedStageMax);
-      attr_set = true;
-    }
+    // raised once per instantiation (thread-safe static initialisation: the batch's workers share it)
+    static const cudaError_t attr_set =
+        cudaFuncSetAttribute(k_fused_last<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedStageMax);
+    (void)attr_set;
     if constexpr (std::is_same<T, fx>::value) {
       const bool obs = obs_res && kind == 0 && dax < 0;
       if (obs)
@@ -2740,7 +2781,7 @@ void observe_quad(NdBatch* b, NdRun* r, Apply<T, P>& op, const C<T>* c, double* 
   for (int a = 0; a < L; ++a) inner *= r->Q[a];
   const AxisDev& AL = r->ax[L];
   int echunk = 1;
-  const long long nch = fused_nchunks(AL.E, inner, P, &echunk);
+  const long long nch = reduce_nchunks(AL.E, inner, P, &echunk);
   red_zero(b, 4);
   k_fused_last_reduce_ff<P, T><<<grid_for(inner * nch), TPB, 0, b->st>>>(X, r->ax[0], r->ax[1], AL, r->dim, inner,
                                                                          echunk, medium_ff(r->med),
