@@ -76,6 +76,7 @@ _sig = {
     "tdz_batch_tuning": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int), _dp]),
     "tdz_batch_precond_tuning": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int), _dp]),
     "tdz_batch_time_operator": (C.c_int, [_vp, C.c_int, C.c_int, _dp]),
+    "tdz_batch_ground_state": (C.c_int, [_vp, C.c_int, C.c_double, C.c_double, C.c_int, _dp, C.POINTER(C.c_int), _dp]),
     "tdz_batch_destroy": (None, [_vp]),
     "tdz_observe_current": (C.c_int, [_vp, C.c_int, _vp]),
     "tdz_lowest_states": (C.c_int, [C.POINTER(_vp), C.c_int, C.c_int, _dp, _dp, _dp, C.POINTER(C.c_int), _vp]),
@@ -436,6 +437,15 @@ class Batch:
         ms = C.c_double()
         _check(_lib.tdz_batch_time_operator(self._h, int(geometry), int(reps), C.byref(ms)), "tdz_batch_time_operator")
         return ms.value
+
+    def ground_state(self, run: int, sigma: float, tol: float = 1e-10, max_outer: int = 200):
+        """Ground state of a 2-D/3-D run of a binary64 batch by shifted inverse iteration on the GPU
+        (tdz_batch_ground_state), started from the run's current state, which it replaces (S-normalised).
+        Returns (energy, outer iterations, relative eigen-residual)."""
+        e, it, res = C.c_double(), C.c_int(), C.c_double()
+        _check(_lib.tdz_batch_ground_state(self._h, int(run), float(sigma), float(tol), int(max_outer), C.byref(e),
+                                           C.byref(it), C.byref(res)), "tdz_batch_ground_state")
+        return e.value, it.value, res.value
 
     def krylov_stats(self) -> float:
         """Total Krylov iterations of all runs since creation (0 for 1-D batches)."""

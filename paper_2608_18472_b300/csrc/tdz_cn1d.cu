@@ -2091,6 +2091,13 @@ int tdz_batch_time_operator(tdz_batch* b, int geometry, int reps, double* ms) {
   return tdz::nd_time_operator(b->nd, geometry, reps, ms);
 }
 
+int tdz_batch_ground_state(tdz_batch* b, int run, double sigma, double tol, int max_outer, double* energy,
+                           int* iterations, double* residual) {
+  if (!b) return TDZ_EINVAL;
+  if (!b->nd) return TDZ_EUNSUPPORTED;
+  return tdz::nd_ground_state(b->nd, run, sigma, tol, max_outer, energy, iterations, residual);
+}
+
 int tdz_krylov_stats(const tdz_batch* b, double* iterations) {
   if (!b || !iterations) return TDZ_EINVAL;
   *iterations = 0.0;

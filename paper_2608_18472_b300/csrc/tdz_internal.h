@@ -77,6 +77,8 @@ int nd_set_option(NdBatch* b, int option, int value);
 int nd_tuning(const NdBatch* b, int geometry, int* groups, double* ms);
 int nd_precond_tuning(const NdBatch* b, int geometry, int* variant, double* ms);
 int nd_time_operator(NdBatch* b, int geometry, int reps, double* ms);
+int nd_ground_state(NdBatch* b, int run, double sigma, double tol, int max_outer, double* energy, int* outer,
+                    double* resid);
 int nd_dim(const NdBatch* b);
 size_t nd_device_bytes(const NdBatch* b);
 

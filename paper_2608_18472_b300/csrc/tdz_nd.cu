@@ -1197,6 +1197,16 @@ __global__ void k_axby(const C<Tx>* __restrict__ x, C<Ty>* __restrict__ y, long 
   }
 }
 
+// y = (ar + i ai) x + (br + i bi) y; x may alias y (each element is read and written by one thread)
+template <class T>
+__global__ void k_caxpby(const C<T>* x, C<T>* y, long long n, double ar, double ai, double br, double bi) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const C<T> u = x[i], v = y[i];
+    const T xr = u.r, xi = u.i, yr = v.r, yi = v.i;
+    y[i] = C<T>{(T)(ar * xr - ai * xi + br * yr - bi * yi), (T)(ar * xi + ai * xr + br * yi + bi * yr)};
+  }
+}
+
 template <class T>
 __global__ void k_nrm(const C<T>* __restrict__ a, long long n, double* res, GridRed gr) {
   __shared__ double sh[32];
@@ -1815,8 +1825,11 @@ __global__ void k_split_tf32(const C<float>* __restrict__ v, float* __restrict__
 
 // in the eigenbasis (index j0 fastest): u /= 1 + i tm (lam0[j0] + lam1[j1] + lam2[j2]); binary64
 template <class Tp>
+// shifted = 1 (ground-state inverse iteration): 1 / (i (tm lam - ts)) instead, the inverse of the
+// separable operator i tau (mbar K - sigma S) with ts = tau sigma
 __global__ void k_fd_scale(Tp* __restrict__ w, long long n, int dim, int n0, int n1, const double* __restrict__ l0,
-                           const double* __restrict__ l1, const double* __restrict__ l2, double tm) {
+                           const double* __restrict__ l1, const double* __restrict__ l2, double tm, int shifted,
+                           double ts) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const int j0 = (int)(i % n0);
     const long long t = i / n0;
@@ -1824,10 +1837,16 @@ __global__ void k_fd_scale(Tp* __restrict__ w, long long n, int dim, int n0, int
     if (dim > 1) lam += l1[(int)(t % n1)];
     if (dim > 2) lam += l2[(int)(t / n1)];
     const double th = tm * lam;
-    const double g = 1.0 / (1.0 + th * th);
     const double a = (double)w[i], b = (double)w[n + i];
-    w[i] = (Tp)((a + th * b) * g);
-    w[n + i] = (Tp)((b - th * a) * g);
+    if (shifted) {  // (a + i b) / (i d) = (b - i a) / d; a zero d (a padding entry at sigma = 0) gives 0
+      const double d = th - ts, id = d != 0.0 ? 1.0 / d : 0.0;
+      w[i] = (Tp)(b * id);
+      w[n + i] = (Tp)(-a * id);
+    } else {
+      const double g = 1.0 / (1.0 + th * th);
+      w[i] = (Tp)((a + th * b) * g);
+      w[n + i] = (Tp)((b - th * a) * g);
+    }
   }
 }
 
@@ -2030,6 +2049,10 @@ struct NdBatch {
   double tol = 1e-12;
   int max_it = 400;
   double inner_tol = 1e-6;
+  // ground-state inverse iteration (binary64 batches): the operator and the preconditioner of the
+  // worker's Krylov solves become those of A - (1 + i tau sigma) S = i tau (H0 - sigma S)
+  bool eig = false;
+  double eig_sigma = 0.0;
   size_t dev_bytes = 0;
 
   void* alloc(size_t bytes) {
@@ -2378,8 +2401,19 @@ struct Apply {
     }
   }
 
-  // y = A_n x
+  // y = A_n x, or in a ground-state solve (binary64) y = A x - (1 + i tau sigma) S x = i tau (H0 - sigma S) x
   void apply(const C<T>* x, C<T>* y, double tau, const double* ebar) {
+    apply_a(x, y, tau, ebar);
+    if constexpr (std::is_same<T, double>::value) {
+      if (b->eig) {
+        double zero3[3] = {0, 0, 0};
+        C<T>* s = reinterpret_cast<C<T>*>(b->d_rc);
+        kron(x, s, 1, 0.0, zero3);
+        k_caxpby<T><<<grid_for(r->N), TPB, 0, b->st>>>(s, y, r->N, -1.0, -tau * b->eig_sigma, 1.0, 0.0);
+      }
+    }
+  }
+  void apply_a(const C<T>* x, C<T>* y, double tau, const double* ebar) {
     if constexpr (std::is_same<T, float>::value) {
       if (Wm && r->dim == 2 && !r->cap) {  // FP32 2-D with the stencil: one fused pass (Kronecker terms + W)
         apply2d_fused<P>(b, r, Wm, x, y, tau, ebar);
@@ -2456,7 +2490,8 @@ void fd_apply64(NdBatch* b, const NdRun* r, const C<double>* src, C<double>* dst
     }
     if (pass == 0)
       k_fd_scale<double><<<grid_for(d.Np), TPB, 0, b->st>>>(cur, d.Np, r->dim, d.np[0], d.np[1], G.lam[0], G.lam[1],
-                                                            G.lam[2], tau * r->mbar);
+                                                            G.lam[2], tau * r->mbar, b->eig ? 1 : 0,
+                                                            tau * b->eig_sigma);
   }
   if (dot)
     k_merge_dot<double, double><<<grid_for(r->N), TPB, 0, b->st>>>(cur, dst, d, r->N, src, dot, b->gr);
@@ -2977,6 +3012,92 @@ int propagate_run(NdBatch* b, NdRun* r, const tdz::Ops& o, const double* field, 
     return TDZ_ECUDA;
   }
   return TDZ_OK;
+}
+
+// Ground state of H0 c = eps S c (Eq. gen_ev) for one 2-D/3-D run of a binary64 batch, by inverse
+// iteration with a fixed shift sigma below the spectrum: x = (H0 - sigma S)^-1 S c solved by the
+// batch's preconditioned COCG on i tau (H0 - sigma S) (the operator A - (1 + i tau sigma) S, tau = 1,
+// no field, fast-diagonalisation preconditioner with the shifted eigenvalue scaling), then
+// eps = sigma + c^H S x / x^H S x (the Rayleigh quotient of x, since (H0 - sigma S) x = S c) and
+// c <- x / |x|_S. It stops when the eigen-residual |H0 c - eps S c|_{S^-1}, formed from the solve as
+// S (c_old / |x|_S - (eps - sigma) c_new), is at most tol |eps|. The run's state is the start vector and
+// is replaced by the result (S-normalised).
+template <int P>
+int ground_state_run(NdBatch* b, NdRun* r, double sigma, double tol, int max_outer, double* energy, int* outer_out,
+                     double* resid_out) {
+  const long long N = r->N;
+  const double tau = 1.0;
+  double zero3[3] = {0, 0, 0};
+  Apply<double, P> op{b, r, reinterpret_cast<C<double>*>(b->d_t1), reinterpret_cast<C<double>*>(b->d_t2),
+                      reinterpret_cast<C<double>*>(b->d_t3), reinterpret_cast<C<double>*>(b->d_t4),
+                      reinterpret_cast<C<double>*>(b->d_qa), reinterpret_cast<C<double>*>(b->d_qb)};
+  const NdGeo& G = b->geo[r->geo];
+  if (G.has_stencil() && b->opt_operator != TDZ_OPERATOR_QUADRATURE) op.Wm = G.W64;
+  C<double>* c = reinterpret_cast<C<double>*>(r->c);
+  C<double>* rhs = reinterpret_cast<C<double>*>(b->d_r0);
+  C<double>* x = reinterpret_cast<C<double>*>(b->d_y);
+  C<double>* s = reinterpret_cast<C<double>*>(b->d_rc);
+  double h[16];
+  auto hdot = [&](const C<double>* u, const C<double>* v) {
+    red_zero(b, 2);
+    k_hdot<double><<<grid_for(N), TPB, 0, b->st>>>(u, v, N, b->d_red, b->gr);
+    return red_get(b, 2, h)[0];
+  };
+  b->eig = true;
+  b->eig_sigma = sigma;
+  int rc = TDZ_ENOCONV, k = 0;
+  double eps = 0.0, rel = 1e300;
+  // S-normalise the start vector
+  op.kron(c, rhs, 1, 0.0, zero3);
+  const double n0 = hdot(c, rhs);
+  if (!(n0 > 0.0) || !std::isfinite(n0)) {
+    b->eig = false;
+    set_error("tdz_batch_ground_state: the start vector has no S-norm");
+    return TDZ_EINVAL;
+  }
+  k_caxpby<double><<<grid_for(N), TPB, 0, b->st>>>(c, c, N, 1.0 / std::sqrt(n0), 0.0, 0.0, 0.0);
+  for (k = 1; k <= max_outer && !b->wait_failed; ++k) {
+    op.kron(c, rhs, 1, 0.0, zero3);                                                         // S c
+    k_caxpby<double><<<grid_for(N), TPB, 0, b->st>>>(rhs, rhs, N, 0.0, tau, 0.0, 0.0);      // i tau S c
+    red_zero(b, 1);
+    k_nrm<double><<<grid_for(N), TPB, 0, b->st>>>(rhs, N, b->d_red, b->gr);
+    const double bb = red_get(b, 1, h)[0];
+    double rr = 0.0;
+    const double tin = std::max(0.1 * tol, 1e-13);
+    const int its = cocg<double, P>(b, r, op, x, rhs, reinterpret_cast<C<double>*>(b->d_z),
+                                    reinterpret_cast<C<double>*>(b->d_p), reinterpret_cast<C<double>*>(b->d_q), tau,
+                                    zero3, tin * tin * bb, b->max_it, &rr);
+    r->iters += its;
+    r->nsolve++;
+    op.kron(x, s, 1, 0.0, zero3);  // S x
+    const double xsx = hdot(x, s), csx = hdot(c, s);
+    if (!(xsx > 0.0) || !std::isfinite(xsx)) {
+      rc = TDZ_ENONFINITE;
+      break;
+    }
+    eps = sigma + csx / xsx;
+    const double ix = 1.0 / std::sqrt(xsx);
+    // w = c_old / |x|_S - (eps - sigma) x / |x|_S in rhs, then |w|_S
+    cudaMemcpyAsync(rhs, c, sizeof(C<double>) * N, cudaMemcpyDeviceToDevice, b->st);
+    k_caxpby<double><<<grid_for(N), TPB, 0, b->st>>>(x, rhs, N, -(eps - sigma) * ix, 0.0, ix, 0.0);
+    op.kron(rhs, s, 1, 0.0, zero3);
+    const double ww = hdot(rhs, s);
+    k_caxpby<double><<<grid_for(N), TPB, 0, b->st>>>(x, c, N, ix, 0.0, 0.0, 0.0);  // c = x / |x|_S
+    rel = std::sqrt(std::max(ww, 0.0)) / std::max(std::fabs(eps), 1e-300);
+    if (rel <= tol) {
+      rc = TDZ_OK;
+      break;
+    }
+  }
+  b->eig = false;
+  if (b->wait_failed) rc = TDZ_ECUDA;
+  cudaError_t e = cudaStreamSynchronize(b->st);
+  if (e != cudaSuccess) return nd_cuda_fail(e, "tdz_batch_ground_state");
+  if (energy) *energy = eps;
+  if (outer_out) *outer_out = std::min(k, max_outer);
+  if (resid_out) *resid_out = rel;
+  if (rc == TDZ_ENOCONV) set_error("tdz_batch_ground_state: the eigen-residual did not reach the tolerance");
+  return rc;
 }
 
 // work buffers of one worker, sized for the largest run of the batch (maxN, maxQ, maxSide, maxn set)
@@ -3597,6 +3718,32 @@ int time_operator_p(NdBatch* b, NdRun* r, int reps, double* ms_out) {
   if (cudaMemcpy(&werr, b->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess || werr != 0) return TDZ_ECUDA;
   *ms_out = best;
   return TDZ_OK;
+}
+
+int nd_ground_state(NdBatch* b, int run, double sigma, double tol, int max_outer, double* energy, int* outer,
+                    double* resid) {
+  if (!b || run < 0 || run >= b->nruns || !(tol > 0.0) || max_outer < 1) return TDZ_EINVAL;
+  if (b->prec != TDZ_FP64) {
+    set_error("tdz_batch_ground_state: needs a binary64 batch");
+    return TDZ_EUNSUPPORTED;
+  }
+  NdRun* r = &b->runs[run];
+  if (r->cap || !use_fd(b, r)) {
+    set_error("tdz_batch_ground_state: needs the fast-diagonalisation preconditioner and no absorbing layer");
+    return TDZ_EUNSUPPORTED;
+  }
+  cudaError_t e = cudaStreamSynchronize(b->st);
+  if (e != cudaSuccess) return nd_cuda_fail(e, "tdz_batch_ground_state");
+  switch (b->P) {
+    case 1: return ground_state_run<1>(b, r, sigma, tol, max_outer, energy, outer, resid);
+    case 2: return ground_state_run<2>(b, r, sigma, tol, max_outer, energy, outer, resid);
+    case 3: return ground_state_run<3>(b, r, sigma, tol, max_outer, energy, outer, resid);
+    case 4: return ground_state_run<4>(b, r, sigma, tol, max_outer, energy, outer, resid);
+    case 5: return ground_state_run<5>(b, r, sigma, tol, max_outer, energy, outer, resid);
+    case 6: return ground_state_run<6>(b, r, sigma, tol, max_outer, energy, outer, resid);
+    case 7: return ground_state_run<7>(b, r, sigma, tol, max_outer, energy, outer, resid);
+    default: return ground_state_run<8>(b, r, sigma, tol, max_outer, energy, outer, resid);
+  }
 }
 
 int nd_time_operator(NdBatch* b, int geometry, int reps, double* ms) {
