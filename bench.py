@@ -437,20 +437,38 @@ def _gauss_state(knots, p, dim):
     return (c / np.linalg.norm(c)).astype(complex)
 
 
-def _nd_ground_state(tdz, ops, c_start, v_min):
-    """The library's own ground state of a 2-D/3-D geometry (tdz_batch_ground_state on a binary64 batch),
-    from `c_start`: a coarse pass with the shift just below the potential's minimum, then the shift 0.05
-    below that estimate to a 1e-10 eigen-residual. Returns the state and a summary."""
+def _nd_ground_state(tdz, ops, c_starts, v_mins, prec, tol):
+    """The library's own ground states of 2-D/3-D geometries (tdz_batch_ground_state; one batch of all
+    `ops`, run i from c_starts[i]): a coarse pass with the shift just below the potential's minimum v_min
+    (residual 1e-3), then the shift min(0.05, a tenth of the coarse level's height above that shift) below
+    the coarse level, to the eigen-residual `tol`. Returns the states and a summary."""
     t0 = time.perf_counter()
-    b = tdz.Batch([ops], [0], tdz.FP64)
-    b.set_state(0, c_start)
-    e1, o1, _ = b.ground_state(0, v_min - 0.01, tol=1e-4, max_outer=100)
-    e, o2, res = b.ground_state(0, e1 - 0.05, tol=1e-10, max_outer=100)
-    c0 = b.get_state(0)
-    info = {"energy": e, "outer_iterations": o1 + o2, "krylov_iterations": b.krylov_stats(),
-            "eigen_residual": res, "seconds": time.perf_counter() - t0}
+    b = tdz.Batch(ops, list(range(len(ops))), prec)
+    energies, outer, res = [], 0, 0.0
+    for i, (c, vm) in enumerate(zip(c_starts, v_mins)):
+        b.set_state(i, c)
+        s1 = vm - 0.01 * max(1e-3, abs(vm))
+        e1, o1, _ = b.ground_state(i, s1, tol=1e-3, max_outer=200)
+        e, o2, r = b.ground_state(i, e1 - min(0.05, 0.1 * (e1 - s1)), tol=tol, max_outer=200)
+        energies.append(e)
+        outer += o1 + o2
+        res = max(res, r)
+    c0s = [b.get_state(i) for i in range(len(ops))]
+    info = {"precision": "binary64" if prec == tdz.FP64 else "mixed (FP32 solves)", "eigen_residual_max": res,
+            "energy_min": min(energies), "energy_max": max(energies), "outer_iterations": outer,
+            "krylov_iterations": b.krylov_stats(), "seconds": time.perf_counter() - t0}
     del b
-    return c0, info
+    return c0s, info
+
+
+def _v_min(medium):
+    """The potential's minimum (a lower bound of every level)."""
+    v = medium["potential"]
+    if v["kind"] == "softcore":
+        return -v["z"] / np.sqrt(v["eps"])
+    if v["kind"] == "ellipse":
+        return min(v["v_in"], v["v_out"])
+    raise KeyError(v["kind"])
 
 
 # timed steps (mixed, binary64) of the 2-D/3-D legs by default
@@ -461,8 +479,9 @@ def nd_legs(tdz, nsteps, which, n2d=1024, n3d=256):
     """2-D/3-D workloads beside the 1-D batch, timed over ND_WINDOWS (mixed, binary64) steps unless
     `nsteps` (> 0) sets both windows:
     softcore_atom_2d: V = -1/sqrt(r^2+0.5) on [-150,150]^2, 1024 order-7 splines per axis (1.04 M
-      coefficients), 800 nm 1e14 W/cm^2 sin^2 pulse, dt = 0.05, from the library's ground state (the other
-      legs start from Gaussians: a binary64 ground-state solve of 64 dots or of the 3-D grid takes minutes);
+      coefficients), 800 nm 1e14 W/cm^2 sin^2 pulse, dt = 0.05, from the library's ground state (binary64,
+      eigen-residual 1e-10; the dots and the 3-D atom from ground states of the mixed batches' FP32 solves,
+      eigen-residual 1e-5: a binary64 solve of 64 dots or of the 3-D grid takes minutes);
     dot_batch_2d: 64 elliptical GaAs dots (16 M coefficients), 10 um, 8 intensities x 8 CEPs, dt = 0.5;
     softcore_atom_3d: [-100,100]^3, 256 order-6 splines per axis (16.4 M coefficients), elliptical
       (0.3) 800 nm pulse, dt = 0.05."""
@@ -477,8 +496,9 @@ def nd_legs(tdz, nsteps, which, n2d=1024, n3d=256):
         dt = 0.05
         f = wl.sin2_pulse(wl.time_grid(dt, max(km, kd) + 1), wl.e0_from_intensity(1e14), wl.omega_from_nm(800.0), 4.0,
                           dim=2)
-        c0, gs = _nd_ground_state(tdz, ops, _gauss_state(t, p, 2), -1.0 / np.sqrt(0.5))
-        out["config_2d"] = _nd_time(tdz, "softcore_atom_2d", [ops], [0], [c0], f[None], dt, km,
+        med = wl.softcore_medium(0.5)
+        c0s, gs = _nd_ground_state(tdz, [ops], [_gauss_state(t, p, 2)], [_v_min(med)], tdz.FP64, 1e-10)
+        out["config_2d"] = _nd_time(tdz, "softcore_atom_2d", [ops], [0], c0s, f[None], dt, km,
                                     {"operator": "assembled (2p+1)^2 stencil",
                                      "preconditioner": "fast diagonalisation (tcgen05 TF32 axis transforms)",
                                      "initial_state": "ground state (tdz_batch_ground_state)", "ground_state": gs}, kd)
@@ -486,11 +506,14 @@ def nd_legs(tdz, nsteps, which, n2d=1024, n3d=256):
         km, kd = win("dots")
         wk = wl.dot_batch(nsteps=max(km, kd) + 1)
         ops = [tdz.Ops([tdz.Basis(k, r.degree, r.nquad) for k in r.knots], r.medium) for r in wk.runs]
-        c0s = [_gauss_state(r.knots[0], r.degree, 2) for r in wk.runs]
+        c0s, gs = _nd_ground_state(tdz, ops, [_gauss_state(r.knots[0], r.degree, 2) for r in wk.runs],
+                                   [_v_min(r.medium) for r in wk.runs], tdz.MIXED, 1e-5)
         fields = np.stack([r.field for r in wk.runs])
         out["config_dots_2d"] = _nd_time(tdz, "dot_batch_2d", ops, list(range(len(ops))), c0s, fields, wk.dt, km,
                                          {"operator": "assembled stencil (variable mass + step potential)",
-                                          "preconditioner": "fast diagonalisation, mean 1/m"}, kd)
+                                          "preconditioner": "fast diagonalisation, mean 1/m",
+                                          "initial_state": "ground states (tdz_batch_ground_state)",
+                                          "ground_state": gs}, kd)
     if "3d" in which:
         km, kd = win("3d")
         p, t = 6, wl.knots_for_nsplines(-100.0, 100.0, n3d, 6)
@@ -498,9 +521,13 @@ def nd_legs(tdz, nsteps, which, n2d=1024, n3d=256):
         dt = 0.05
         f = wl.sin2_pulse(wl.time_grid(dt, max(km, kd) + 1), 0.05, wl.omega_from_nm(800.0), 4.0, ellipticity=0.3,
                           dim=3)
-        out["config_3d"] = _nd_time(tdz, "softcore_atom_3d", [ops], [0], [_gauss_state(t, p, 3)], f[None], dt, km,
+        med = wl.softcore_medium(0.5)
+        c0s, gs = _nd_ground_state(tdz, [ops], [_gauss_state(t, p, 3)], [_v_min(med)], tdz.MIXED, 1e-5)
+        out["config_3d"] = _nd_time(tdz, "softcore_atom_3d", [ops], [0], c0s, f[None], dt, km,
                                     {"operator": "Gauss-point sum factorisation",
-                                     "preconditioner": "fast diagonalisation (tcgen05 TF32 axis transforms)"}, kd)
+                                     "preconditioner": "fast diagonalisation (tcgen05 TF32 axis transforms)",
+                                     "initial_state": "ground state (tdz_batch_ground_state)", "ground_state": gs},
+                                    kd)
     return out
 
 

@@ -280,10 +280,12 @@ int  tdz_batch_precond_tuning(const tdz_batch* b, int geometry, int* variant, do
  * best of `reps` applies after one warm-up. Run states are not touched. Synchronises the stream.
  * Errors: TDZ_EINVAL (bad handle, geometry or reps), TDZ_EUNSUPPORTED (1-D batch), TDZ_ECUDA. */
 int  tdz_batch_time_operator(tdz_batch* b, int geometry, int reps, double* ms);
-/* tdz_batch_ground_state (2-D/3-D, binary64 batch): the ground state of H0 c = eps S c (Eq. gen_ev, no
- * field) of run `run`, on the GPU, by inverse iteration with the fixed shift sigma: every outer iteration
- * solves (H0 - sigma S) x = S c with the batch's preconditioned COCG (operator i tau (H0 - sigma S), fast
- * diagonalisation with the shifted eigenvalue scaling, inner tolerance tol / 10), takes the Rayleigh
+/* tdz_batch_ground_state (2-D/3-D): the ground state of H0 c = eps S c (Eq. gen_ev, no field) of run `run`,
+ * on the GPU, by inverse iteration with the fixed shift sigma: every outer iteration solves
+ * (H0 - sigma S) x = S c with the batch's preconditioned COCG (operator i tau (H0 - sigma S), fast
+ * diagonalisation with the shifted eigenvalue scaling, inner tolerance tol / 10), in binary64 in a binary64
+ * batch and with the FP32 operator and tensor-core preconditioner of the inner solves in a mixed batch
+ * (FP32 accuracy: tol of about 1e-5 or more, inner tolerance at least 1e-6), takes the Rayleigh
  * quotient eps = sigma + c^H S x / x^H S x and sets c = x / |x|_S; it stops when the eigen-residual
  * |H0 c - eps S c|_{S^-1} <= tol |eps|. sigma must lie below the lowest eigenvalue, close enough that
  * (eps_0 - sigma) / (eps_1 - sigma) is small (the contraction per outer iteration). The run's current state
@@ -291,7 +293,7 @@ int  tdz_batch_time_operator(tdz_batch* b, int geometry, int reps, double* ms);
  * S-normalised. energy, iterations (outer iterations), residual (the final relative eigen-residual): host
  * outputs, each may be NULL. Synchronises the batch stream.
  * Errors: TDZ_EINVAL (bad handle, run, tol <= 0, max_outer < 1, a start vector with no S-norm),
- * TDZ_EUNSUPPORTED (1-D batch, mixed batch, an absorbing layer, or the line preconditioner selected),
+ * TDZ_EUNSUPPORTED (1-D batch, an absorbing layer, or the line preconditioner selected),
  * TDZ_ENOCONV (not converged within max_outer; the last iterate and its residual are returned),
  * TDZ_ENONFINITE, TDZ_ECUDA. */
 int  tdz_batch_ground_state(tdz_batch* b, int run, double sigma, double tol, int max_outer, double* energy,

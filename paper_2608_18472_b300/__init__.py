@@ -439,9 +439,9 @@ class Batch:
         return ms.value
 
     def ground_state(self, run: int, sigma: float, tol: float = 1e-10, max_outer: int = 200):
-        """Ground state of a 2-D/3-D run of a binary64 batch by shifted inverse iteration on the GPU
-        (tdz_batch_ground_state), started from the run's current state, which it replaces (S-normalised).
-        Returns (energy, outer iterations, relative eigen-residual)."""
+        """Ground state of a 2-D/3-D run by shifted inverse iteration on the GPU (tdz_batch_ground_state;
+        binary64 in a binary64 batch, FP32 accuracy in a mixed one), started from the run's current state,
+        which it replaces (S-normalised). Returns (energy, outer iterations, relative eigen-residual)."""
         e, it, res = C.c_double(), C.c_int(), C.c_double()
         _check(_lib.tdz_batch_ground_state(self._h, int(run), float(sigma), float(tol), int(max_outer), C.byref(e),
                                            C.byref(it), C.byref(res)), "tdz_batch_ground_state")

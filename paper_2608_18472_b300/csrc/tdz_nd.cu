@@ -1851,8 +1851,10 @@ __global__ void k_fd_scale(Tp* __restrict__ w, long long n, int dim, int n0, int
 }
 
 // the same scaling in FP32 (eigenvalues in FP32), in place; the mixed preconditioner runs in FP32
+// (shifted, ts: the ground-state scaling 1 / (i (tm lam - ts)), as in k_fd_scale)
 __global__ void k_fd_scale32(float* __restrict__ w, PadDims d, const float* __restrict__ l0,
-                             const float* __restrict__ l1, const float* __restrict__ l2, float tm) {
+                             const float* __restrict__ l1, const float* __restrict__ l2, float tm, int shifted,
+                             float ts) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < d.Np; i += (long long)gridDim.x * blockDim.x) {
     int j0, j1, j2;
     pad_index(d, (unsigned)i, j0, j1, j2);
@@ -1860,10 +1862,16 @@ __global__ void k_fd_scale32(float* __restrict__ w, PadDims d, const float* __re
     if (d.dim > 1) lam += l1[j1];
     if (d.dim > 2) lam += l2[j2];
     const float th = tm * lam;
-    const float g = 1.0f / fmaf(th, th, 1.0f);
     const float a = w[i], b = w[d.Np + i];
-    w[i] = fmaf(th, b, a) * g;
-    w[d.Np + i] = fmaf(-th, a, b) * g;
+    if (shifted) {
+      const float dd = th - ts, id = dd != 0.0f ? 1.0f / dd : 0.0f;
+      w[i] = b * id;
+      w[d.Np + i] = -a * id;
+    } else {
+      const float g = 1.0f / fmaf(th, th, 1.0f);
+      w[i] = fmaf(th, b, a) * g;
+      w[d.Np + i] = fmaf(-th, a, b) * g;
+    }
   }
 }
 
@@ -1871,7 +1879,7 @@ __global__ void k_fd_scale32(float* __restrict__ w, PadDims d, const float* __re
 // TF32 pairs (planes of hi in whi, of lo in wlo)
 __global__ void k_fd_scale_tf32(const float* __restrict__ w, float* __restrict__ whi, float* __restrict__ wlo,
                                 PadDims d, const float* __restrict__ l0, const float* __restrict__ l1,
-                                const float* __restrict__ l2, float tm) {
+                                const float* __restrict__ l2, float tm, int shifted, float ts) {
   const long long n = d.Np;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     int j0, j1, j2;
@@ -1880,9 +1888,17 @@ __global__ void k_fd_scale_tf32(const float* __restrict__ w, float* __restrict__
     if (d.dim > 1) lam += l1[j1];
     if (d.dim > 2) lam += l2[j2];
     const float th = tm * lam;
-    const float g = 1.0f / fmaf(th, th, 1.0f);
     const float a = w[i], b = w[n + i];
-    const float xr = fmaf(th, b, a) * g, xi = fmaf(-th, a, b) * g;
+    float xr, xi;
+    if (shifted) {
+      const float dd = th - ts, id = dd != 0.0f ? 1.0f / dd : 0.0f;
+      xr = b * id;
+      xi = -a * id;
+    } else {
+      const float g = 1.0f / fmaf(th, th, 1.0f);
+      xr = fmaf(th, b, a) * g;
+      xi = fmaf(-th, a, b) * g;
+    }
     const float hr = tf32_hi(xr), hi = tf32_hi(xi);
     whi[i] = hr;
     whi[n + i] = hi;
@@ -2404,8 +2420,8 @@ struct Apply {
   // y = A_n x, or in a ground-state solve (binary64) y = A x - (1 + i tau sigma) S x = i tau (H0 - sigma S) x
   void apply(const C<T>* x, C<T>* y, double tau, const double* ebar) {
     apply_a(x, y, tau, ebar);
-    if constexpr (std::is_same<T, double>::value) {
-      if (b->eig) {
+    if constexpr (!std::is_same<T, fx>::value) {
+      if (b->eig) {  // (binary64 batch, or the FP32 solve of a mixed batch)
         double zero3[3] = {0, 0, 0};
         C<T>* s = reinterpret_cast<C<T>*>(b->d_rc);
         kron(x, s, 1, 0.0, zero3);
@@ -2530,7 +2546,8 @@ int fd_apply32(NdBatch* b, const NdRun* r, const C<float>* src, C<float>* dst, f
       }
       if (pass == 0)
         k_fd_scale32<<<grid_for(d.Np), TPB, 0, b->st>>>(cur, d, G.lam32[0], G.lam32[1], G.lam32[2],
-                                                        (float)(tau * r->mbar));
+                                                        (float)(tau * r->mbar), b->eig ? 1 : 0,
+                                                        (float)(tau * b->eig_sigma));
     }
     out = cur;
   } else {
@@ -2550,7 +2567,8 @@ int fd_apply32(NdBatch* b, const NdRun* r, const C<float>* src, C<float>* dst, f
       // hi holds the FP32 result of the pass
       if (pass == 0) {
         k_fd_scale_tf32<<<grid_for(d.Np), TPB, 0, b->st>>>(hi, ohi, olo, d, G.lam32[0], G.lam32[1], G.lam32[2],
-                                                           (float)(tau * r->mbar));
+                                                           (float)(tau * r->mbar), b->eig ? 1 : 0,
+                                                           (float)(tau * b->eig_sigma));
         std::swap(hi, ohi);
         std::swap(lo, olo);
       }
@@ -3014,59 +3032,69 @@ int propagate_run(NdBatch* b, NdRun* r, const tdz::Ops& o, const double* field, 
   return TDZ_OK;
 }
 
-// Ground state of H0 c = eps S c (Eq. gen_ev) for one 2-D/3-D run of a binary64 batch, by inverse
-// iteration with a fixed shift sigma below the spectrum: x = (H0 - sigma S)^-1 S c solved by the
-// batch's preconditioned COCG on i tau (H0 - sigma S) (the operator A - (1 + i tau sigma) S, tau = 1,
-// no field, fast-diagonalisation preconditioner with the shifted eigenvalue scaling), then
-// eps = sigma + c^H S x / x^H S x (the Rayleigh quotient of x, since (H0 - sigma S) x = S c) and
-// c <- x / |x|_S. It stops when the eigen-residual |H0 c - eps S c|_{S^-1}, formed from the solve as
-// S (c_old / |x|_S - (eps - sigma) c_new), is at most tol |eps|. The run's state is the start vector and
-// is replaced by the result (S-normalised).
-template <int P>
+// Ground state of H0 c = eps S c (Eq. gen_ev) for one 2-D/3-D run, by inverse iteration with a fixed
+// shift sigma below the spectrum: x = (H0 - sigma S)^-1 S c solved by the batch's preconditioned COCG on
+// i tau (H0 - sigma S) (the operator A - (1 + i tau sigma) S, tau = 1, no field, fast-diagonalisation
+// preconditioner with the shifted eigenvalue scaling), then eps = sigma + c^H S x / x^H S x (the
+// Rayleigh quotient of x, since (H0 - sigma S) x = S c) and c <- x / |x|_S. It stops when the
+// eigen-residual |H0 c - eps S c|_{S^-1}, formed from the solve as S (c_old / |x|_S - (eps - sigma) c_new),
+// is at most tol |eps|. T = double in a binary64 batch; T = float in a mixed batch (the FP32 operator and
+// preconditioner of its inner solves, residuals to FP32 accuracy). The run's state is the start vector
+// and is replaced by the result (S-normalised).
+template <class T, int P>
 int ground_state_run(NdBatch* b, NdRun* r, double sigma, double tol, int max_outer, double* energy, int* outer_out,
                      double* resid_out) {
   const long long N = r->N;
   const double tau = 1.0;
   double zero3[3] = {0, 0, 0};
-  Apply<double, P> op{b, r, reinterpret_cast<C<double>*>(b->d_t1), reinterpret_cast<C<double>*>(b->d_t2),
-                      reinterpret_cast<C<double>*>(b->d_t3), reinterpret_cast<C<double>*>(b->d_t4),
-                      reinterpret_cast<C<double>*>(b->d_qa), reinterpret_cast<C<double>*>(b->d_qb)};
+  const bool f32 = std::is_same<T, float>::value;
   const NdGeo& G = b->geo[r->geo];
-  if (G.has_stencil() && b->opt_operator != TDZ_OPERATOR_QUADRATURE) op.Wm = G.W64;
-  C<double>* c = reinterpret_cast<C<double>*>(r->c);
-  C<double>* rhs = reinterpret_cast<C<double>*>(b->d_r0);
-  C<double>* x = reinterpret_cast<C<double>*>(b->d_y);
-  C<double>* s = reinterpret_cast<C<double>*>(b->d_rc);
+  const bool stencil = G.has_stencil() && b->opt_operator != TDZ_OPERATOR_QUADRATURE;
+  auto vec = [&](void* d64, void* w32) { return static_cast<C<T>*>(f32 ? w32 : d64); };
+  Apply<T, P> op{b, r, vec(b->d_t1, b->w_t1), vec(b->d_t2, b->w_t2), vec(b->d_t3, b->w_t3), vec(b->d_t4, b->w_t4),
+                 vec(b->d_qa, b->w_qa), vec(b->d_qb, b->w_qb)};
+  if (stencil) {
+    if constexpr (std::is_same<T, float>::value) op.Wm = G.W32;
+    else op.Wm = G.W64;
+  }
+  // binary64: the run state itself, then the propagator's binary64 work vectors; FP32: the iterate in the
+  // (unused) binary64 residual buffer, the FP32 solve's vectors; S products in d_rc either way
+  C<double>* c64 = reinterpret_cast<C<double>*>(r->c);
+  C<T>* c = f32 ? reinterpret_cast<C<T>*>(b->d_r0) : reinterpret_cast<C<T>*>(r->c);
+  C<T>* rhs = f32 ? static_cast<C<T>*>(b->w_r) : reinterpret_cast<C<T>*>(b->d_r0);
+  C<T>* x = vec(b->d_y, b->w_x);
+  C<T>* s = reinterpret_cast<C<T>*>(b->d_rc);
+  C<T>* z = vec(b->d_z, b->w_z);
+  C<T>* pp = vec(b->d_p, b->w_p);
+  C<T>* qq = vec(b->d_q, b->w_q);
   double h[16];
-  auto hdot = [&](const C<double>* u, const C<double>* v) {
+  auto hdot = [&](const C<T>* u, const C<T>* v) {
     red_zero(b, 2);
-    k_hdot<double><<<grid_for(N), TPB, 0, b->st>>>(u, v, N, b->d_red, b->gr);
+    k_hdot<T><<<grid_for(N), TPB, 0, b->st>>>(u, v, N, b->d_red, b->gr);
     return red_get(b, 2, h)[0];
   };
+  if (f32) k_axby<double, T><<<grid_for(N), TPB, 0, b->st>>>(c64, c, N, 1.0, 0.0);
   b->eig = true;
   b->eig_sigma = sigma;
   int rc = TDZ_ENOCONV, k = 0;
   double eps = 0.0, rel = 1e300;
-  // S-normalise the start vector
-  op.kron(c, rhs, 1, 0.0, zero3);
+  op.kron(c, rhs, 1, 0.0, zero3);  // S-normalise the start vector
   const double n0 = hdot(c, rhs);
   if (!(n0 > 0.0) || !std::isfinite(n0)) {
     b->eig = false;
     set_error("tdz_batch_ground_state: the start vector has no S-norm");
     return TDZ_EINVAL;
   }
-  k_caxpby<double><<<grid_for(N), TPB, 0, b->st>>>(c, c, N, 1.0 / std::sqrt(n0), 0.0, 0.0, 0.0);
+  k_caxpby<T><<<grid_for(N), TPB, 0, b->st>>>(c, c, N, 1.0 / std::sqrt(n0), 0.0, 0.0, 0.0);
   for (k = 1; k <= max_outer && !b->wait_failed; ++k) {
-    op.kron(c, rhs, 1, 0.0, zero3);                                                         // S c
-    k_caxpby<double><<<grid_for(N), TPB, 0, b->st>>>(rhs, rhs, N, 0.0, tau, 0.0, 0.0);      // i tau S c
+    op.kron(c, rhs, 1, 0.0, zero3);                                                    // S c
+    k_caxpby<T><<<grid_for(N), TPB, 0, b->st>>>(rhs, rhs, N, 0.0, tau, 0.0, 0.0);      // i tau S c
     red_zero(b, 1);
-    k_nrm<double><<<grid_for(N), TPB, 0, b->st>>>(rhs, N, b->d_red, b->gr);
+    k_nrm<T><<<grid_for(N), TPB, 0, b->st>>>(rhs, N, b->d_red, b->gr);
     const double bb = red_get(b, 1, h)[0];
     double rr = 0.0;
-    const double tin = std::max(0.1 * tol, 1e-13);
-    const int its = cocg<double, P>(b, r, op, x, rhs, reinterpret_cast<C<double>*>(b->d_z),
-                                    reinterpret_cast<C<double>*>(b->d_p), reinterpret_cast<C<double>*>(b->d_q), tau,
-                                    zero3, tin * tin * bb, b->max_it, &rr);
+    const double tin = std::max(0.1 * tol, f32 ? 1e-6 : 1e-13);
+    const int its = cocg<T, P>(b, r, op, x, rhs, z, pp, qq, tau, zero3, tin * tin * bb, b->max_it, &rr);
     r->iters += its;
     r->nsolve++;
     op.kron(x, s, 1, 0.0, zero3);  // S x
@@ -3078,11 +3106,11 @@ int ground_state_run(NdBatch* b, NdRun* r, double sigma, double tol, int max_out
     eps = sigma + csx / xsx;
     const double ix = 1.0 / std::sqrt(xsx);
     // w = c_old / |x|_S - (eps - sigma) x / |x|_S in rhs, then |w|_S
-    cudaMemcpyAsync(rhs, c, sizeof(C<double>) * N, cudaMemcpyDeviceToDevice, b->st);
-    k_caxpby<double><<<grid_for(N), TPB, 0, b->st>>>(x, rhs, N, -(eps - sigma) * ix, 0.0, ix, 0.0);
+    cudaMemcpyAsync(rhs, c, sizeof(C<T>) * N, cudaMemcpyDeviceToDevice, b->st);
+    k_caxpby<T><<<grid_for(N), TPB, 0, b->st>>>(x, rhs, N, -(eps - sigma) * ix, 0.0, ix, 0.0);
     op.kron(rhs, s, 1, 0.0, zero3);
     const double ww = hdot(rhs, s);
-    k_caxpby<double><<<grid_for(N), TPB, 0, b->st>>>(x, c, N, ix, 0.0, 0.0, 0.0);  // c = x / |x|_S
+    k_caxpby<T><<<grid_for(N), TPB, 0, b->st>>>(x, c, N, ix, 0.0, 0.0, 0.0);  // c = x / |x|_S
     rel = std::sqrt(std::max(ww, 0.0)) / std::max(std::fabs(eps), 1e-300);
     if (rel <= tol) {
       rc = TDZ_OK;
@@ -3090,6 +3118,7 @@ int ground_state_run(NdBatch* b, NdRun* r, double sigma, double tol, int max_out
     }
   }
   b->eig = false;
+  if (f32) k_axby<T, double><<<grid_for(N), TPB, 0, b->st>>>(c, c64, N, 1.0, 0.0);
   if (b->wait_failed) rc = TDZ_ECUDA;
   cudaError_t e = cudaStreamSynchronize(b->st);
   if (e != cudaSuccess) return nd_cuda_fail(e, "tdz_batch_ground_state");
@@ -3723,10 +3752,6 @@ int time_operator_p(NdBatch* b, NdRun* r, int reps, double* ms_out) {
 int nd_ground_state(NdBatch* b, int run, double sigma, double tol, int max_outer, double* energy, int* outer,
                     double* resid) {
   if (!b || run < 0 || run >= b->nruns || !(tol > 0.0) || max_outer < 1) return TDZ_EINVAL;
-  if (b->prec != TDZ_FP64) {
-    set_error("tdz_batch_ground_state: needs a binary64 batch");
-    return TDZ_EUNSUPPORTED;
-  }
   NdRun* r = &b->runs[run];
   if (r->cap || !use_fd(b, r)) {
     set_error("tdz_batch_ground_state: needs the fast-diagonalisation preconditioner and no absorbing layer");
@@ -3734,15 +3759,27 @@ int nd_ground_state(NdBatch* b, int run, double sigma, double tol, int max_outer
   }
   cudaError_t e = cudaStreamSynchronize(b->st);
   if (e != cudaSuccess) return nd_cuda_fail(e, "tdz_batch_ground_state");
+  if (b->prec == TDZ_MIXED) {
+    switch (b->P) {
+      case 1: return ground_state_run<float, 1>(b, r, sigma, tol, max_outer, energy, outer, resid);
+      case 2: return ground_state_run<float, 2>(b, r, sigma, tol, max_outer, energy, outer, resid);
+      case 3: return ground_state_run<float, 3>(b, r, sigma, tol, max_outer, energy, outer, resid);
+      case 4: return ground_state_run<float, 4>(b, r, sigma, tol, max_outer, energy, outer, resid);
+      case 5: return ground_state_run<float, 5>(b, r, sigma, tol, max_outer, energy, outer, resid);
+      case 6: return ground_state_run<float, 6>(b, r, sigma, tol, max_outer, energy, outer, resid);
+      case 7: return ground_state_run<float, 7>(b, r, sigma, tol, max_outer, energy, outer, resid);
+      default: return ground_state_run<float, 8>(b, r, sigma, tol, max_outer, energy, outer, resid);
+    }
+  }
   switch (b->P) {
-    case 1: return ground_state_run<1>(b, r, sigma, tol, max_outer, energy, outer, resid);
-    case 2: return ground_state_run<2>(b, r, sigma, tol, max_outer, energy, outer, resid);
-    case 3: return ground_state_run<3>(b, r, sigma, tol, max_outer, energy, outer, resid);
-    case 4: return ground_state_run<4>(b, r, sigma, tol, max_outer, energy, outer, resid);
-    case 5: return ground_state_run<5>(b, r, sigma, tol, max_outer, energy, outer, resid);
-    case 6: return ground_state_run<6>(b, r, sigma, tol, max_outer, energy, outer, resid);
-    case 7: return ground_state_run<7>(b, r, sigma, tol, max_outer, energy, outer, resid);
-    default: return ground_state_run<8>(b, r, sigma, tol, max_outer, energy, outer, resid);
+    case 1: return ground_state_run<double, 1>(b, r, sigma, tol, max_outer, energy, outer, resid);
+    case 2: return ground_state_run<double, 2>(b, r, sigma, tol, max_outer, energy, outer, resid);
+    case 3: return ground_state_run<double, 3>(b, r, sigma, tol, max_outer, energy, outer, resid);
+    case 4: return ground_state_run<double, 4>(b, r, sigma, tol, max_outer, energy, outer, resid);
+    case 5: return ground_state_run<double, 5>(b, r, sigma, tol, max_outer, energy, outer, resid);
+    case 6: return ground_state_run<double, 6>(b, r, sigma, tol, max_outer, energy, outer, resid);
+    case 7: return ground_state_run<double, 7>(b, r, sigma, tol, max_outer, energy, outer, resid);
+    default: return ground_state_run<double, 8>(b, r, sigma, tol, max_outer, energy, outer, resid);
   }
 }
 
