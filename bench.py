@@ -404,7 +404,7 @@ TF32_PER_BF16 = 1.1 / 2.25
 def _precond_roofline(tdz, b, ops, run_ops):
     """Tensor roofline of the mixed fast-diagonalisation preconditioner for the largest geometry, from the
     autotuner's CUDA-event timing of one whole apply (split, 2 dim tcgen05 axis transforms, scaling, merge;
-    batch creation, best of three, four variants). Tensor work per apply: for each axis a and each of the
+    batch creation, best of three, six variants). Tensor work per apply: for each axis a and each of the
     two passes, 2 TF32 products x 2 flops x (2 Np / np_a rows) x np_a columns x np_a (k) = 8 Np np_a, i.e.
     16 Np sum_a np_a; the algorithmic (one FP32 product) flops are half of that. Peak: the measured BF16
     rate x the nominal TF32/BF16 ratio."""
@@ -419,13 +419,13 @@ def _precond_roofline(tdz, b, ops, run_ops):
     t = ms[v] * 1e-3
     peak = peaks["bf16_tflops"] * TF32_PER_BF16
     names = [f"{128 << (c & 1)}-column tiles, " + ("split in shared memory" if c & 2 else "TF32 pairs in memory")
-             for c in range(4)]
+             for c in range(4)] + ["64-column tiles, TF32 pairs in memory", "64-column tiles, split in shared memory"]
     return {"kernel": f"k_tc_axis<{128 << (v & 1)}, false, {'true' if v & 2 else 'false'}> x {2 * len(npad)}"
                       " + split/scale/merge", "padded_shape": npad, "variant": names[v],
             "bound": "tensor", "achieved": tflop / t, "peak": peak, "unit": "TFLOP/s", "frac": tflop / t / peak,
             "peak_source": peaks["source"] + " bf16 x nominal tf32/bf16", "tensor_tflop_per_apply": tflop,
             "algorithmic_fp32_tflop_per_apply": tflop / 2, "ms_per_apply": ms[v],
-            "variants_ms": {names[c]: ms[c] for c in range(4)}}
+            "variants_ms": {names[c]: ms[c] for c in range(len(ms))}}
 
 
 def _gauss_state(knots, p, dim):

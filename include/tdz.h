@@ -263,12 +263,13 @@ int  tdz_batch_tuning(const tdz_batch* b, int geometry, int* groups, double* ms)
 /* Autotuner result for the fast-diagonalisation preconditioner of geometry `geometry` of a 2-D/3-D
  * mixed batch: at creation one whole preconditioner apply (the tensor-core axis transforms of
  * tdz_tc_axis_transform with the split, eigenvalue scaling and merge around them) is timed on the
- * batch's own buffers (CUDA events, best of three) in four variants and the fastest is kept:
- * variant v uses 256-column transform tiles if bit 0 is set (else 128) and splits the data into TF32
- * pairs inside the transform, in shared memory, if bit 1 is set (else the kernels around the
- * transforms write the pairs to memory). variant (host, optional): the chosen v (-1 when the geometry
- * has no fast diagonalisation or the batch is not mixed); ms (host, optional, 4 doubles): ms per
- * preconditioner apply of variants 0..3. Errors: TDZ_EINVAL (bad handle or geometry index).
+ * batch's own buffers (CUDA events, best of three) in six variants and the fastest is kept: variants
+ * 0-3 use 256-column transform tiles if bit 0 of v is set (else 128) and split the data into TF32 pairs
+ * inside the transform, in shared memory, if bit 1 is set (else the kernels around the transforms write
+ * the pairs to memory); variants 4 and 5 use 64-column tiles (more blocks on small planes) with the
+ * pairs in memory and in shared memory respectively. variant (host, optional): the chosen v (-1 when
+ * the geometry has no fast diagonalisation or the batch is not mixed); ms (host, optional, 6 doubles):
+ * ms per preconditioner apply of variants 0..5. Errors: TDZ_EINVAL (bad handle or geometry index).
  * Autotuner cache (both autotuners): with the environment variable TDZ_TUNE_CACHE naming a file, each
  * result is appended to it as one JSON object per line, {"key": ..., "values": [...]}, keyed by what
  * was tuned, the sizes, the precision and the device name; a later batch creation with the same key
@@ -378,7 +379,7 @@ int  tdz_device_rates(double* fp32_flops, double* fp64_flops);
  * out_hi = D in FP32. The hi arrays should hold TF32 values and the lo arrays the FP32 remainders
  * (every operand is read as TF32: the low 13 bits of each FP32 pattern are ignored). With a_lo NULL,
  * a_hi holds the data in FP32 and each block splits its tiles into the pair in shared memory. tile_n: 0 (the
- * library's choice), 128 or 256 columns per block. All pointers are device memory owned by the caller,
+ * library's choice: 128 or 256), 64, 128 or 256 columns per block. All pointers are device memory owned by the caller,
  * the operands 16-byte aligned; k must be a multiple of 4. Synchronises the stream. Errors:
  * TDZ_EINVAL (sizes, alignment, tile_n), TDZ_ECUDA (launch failure, or a pipeline wait that ran out
  * of time). */

@@ -423,10 +423,11 @@ class Batch:
 
     def precond_tuning(self, geometry: int = 0):
         """Autotuner result of the tensor-core fast-diagonalisation preconditioner of a 2-D/3-D mixed batch
-        for one geometry: (chosen variant, [ms per preconditioner apply of variants 0..3]); variant bit 0 =
-        256-column tiles, bit 1 = TF32 split in shared memory. (-1, []) where it does not apply."""
+        for one geometry: (chosen variant, [ms per preconditioner apply of variants 0..5]); variants 0-3:
+        bit 0 = 256-column tiles (else 128), bit 1 = TF32 split in shared memory; variants 4, 5: 64-column
+        tiles, split in memory / in shared memory. (-1, []) where it does not apply."""
         v = C.c_int()
-        ms = np.zeros(4)
+        ms = np.zeros(6)
         _check(_lib.tdz_batch_precond_tuning(self._h, int(geometry), C.byref(v), ms.ctypes.data_as(_dp)),
                "tdz_batch_precond_tuning")
         return v.value, ([float(x) for x in ms] if v.value >= 0 else [])

@@ -2002,7 +2002,7 @@ struct NdGeo {
   // split into TF32 pairs in shared memory by the transform (else by the producing kernels, as pairs
   // in memory); -1 = not tuned
   int tc_variant = -1;
-  float tc_ms[4] = {0.f, 0.f, 0.f, 0.f};  // the autotuner's ms per preconditioner apply of variants 0..3
+  float tc_ms[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // the autotuner's ms per preconditioner apply of variants 0..5
   double* lam[3] = {nullptr, nullptr, nullptr};
   double* W64 = nullptr;  // binary64 batches
   float* W32 = nullptr;   // mixed: inner FP32 solve
@@ -2529,8 +2529,8 @@ int fd_apply32(NdBatch* b, const NdRun* r, const C<float>* src, C<float>* dst, f
   const NdGeo& G = b->geo[r->geo];
   const PadDims d = pad_dims(G, r);
   const int v = G.tc_variant < 0 ? 0 : G.tc_variant;
-  const int tile = (v & 1) ? 256 : 128;
-  const bool smem_split = (v & 2) != 0;
+  const int tile = v >= 4 ? 64 : (v & 1) ? 256 : 128;  // variants 4, 5: 64-column tiles
+  const bool smem_split = v >= 4 ? v == 5 : (v & 2) != 0;
   float* out = nullptr;  // the FP32 result of the last transform
   if (smem_split) {
     k_split<float, float><<<grid_for(d.Np), TPB, 0, b->st>>>(src, w0, d);
@@ -2610,16 +2610,16 @@ int autotune_fd(NdBatch* b) {
     for (int a = 0; a < r->dim; ++a) key += (a ? "," : "") + std::to_string(G.np[a]);
     key += " mixed dev=" + b->dev_name;
     std::vector<double> hit;
-    if (tune_cache_get(key, hit) && hit.size() == 5 && hit[0] >= 0 && hit[0] <= 3) {
+    if (tune_cache_get(key, hit) && hit.size() == 7 && hit[0] >= 0 && hit[0] <= 5) {
       G.tc_variant = (int)hit[0];
-      for (int c = 0; c < 4; ++c) G.tc_ms[c] = (float)hit[1 + c];
+      for (int c = 0; c < 6; ++c) G.tc_ms[c] = (float)hit[1 + c];
       continue;
     }
     const C<float>* x = static_cast<const C<float>*>(b->w_p);
     C<float>* y = static_cast<C<float>*>(b->w_q);
     float* w[4] = {static_cast<float*>(b->w_qa), static_cast<float*>(b->w_qb), static_cast<float*>(b->w_qc),
                    static_cast<float*>(b->w_qd)};
-    for (int c = 0; c < 4 && rc == TDZ_OK; ++c) {
+    for (int c = 0; c < 6 && rc == TDZ_OK; ++c) {
       G.tc_variant = c;
       rc = fd_apply32(b, r, x, y, w[0], w[1], w[2], w[3], 0.025, nullptr);
       float tmin = 0.f;
@@ -2636,11 +2636,14 @@ int autotune_fd(NdBatch* b) {
       G.tc_ms[c] = tmin;
     }
     int best = 0;
-    for (int c = 1; c < 4; ++c)
+    for (int c = 1; c < 6; ++c)
       if (G.tc_ms[c] < G.tc_ms[best]) best = c;
     G.tc_variant = best;
-    if (rc == TDZ_OK)
-      tune_cache_put(key, {(double)best, (double)G.tc_ms[0], (double)G.tc_ms[1], (double)G.tc_ms[2], (double)G.tc_ms[3]});
+    if (rc == TDZ_OK) {
+      std::vector<double> vals{(double)best};
+      for (int c = 0; c < 6; ++c) vals.push_back((double)G.tc_ms[c]);
+      tune_cache_put(key, vals);
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -3946,7 +3949,7 @@ int nd_precond_tuning(const NdBatch* b, int geometry, int* variant, double* ms) 
   const bool tuned = G.fd && G.Vt[0] && G.tc_variant >= 0;
   if (variant) *variant = tuned ? G.tc_variant : -1;
   if (ms)
-    for (int c = 0; c < 4; ++c) ms[c] = tuned ? G.tc_ms[c] : 0.0;
+    for (int c = 0; c < 6; ++c) ms[c] = tuned ? G.tc_ms[c] : 0.0;
   return TDZ_OK;
 }
 

@@ -410,14 +410,15 @@ int tc_axis_transform(const float* a_hi, const float* a_lo, long long rows, int 
                       int tile_n, cudaStream_t st) {
   using namespace tc;
   if (!a_hi || !b || !out_hi || !err || rows < 1 || K < 4 || K % 4 != 0 || ncols < 1 || plane_rows < 1 ||
-      plane_stride < 0 || rows > INT_MAX - BM || ncols > INT_MAX - 256 || (tile_n != 0 && tile_n != 128 && tile_n != 256))
+      plane_stride < 0 || rows > INT_MAX - BM || ncols > INT_MAX - 256 ||
+      (tile_n != 0 && tile_n != 64 && tile_n != 128 && tile_n != 256))
     return TDZ_EINVAL;
   if (!aligned16(a_hi) || (a_lo && !aligned16(a_lo)) || !aligned16(b) || (b_lo && !aligned16(b_lo)))
     return TDZ_EINVAL;
   const long long tiles_m = (rows + BM - 1) / BM;
   // default: 256-column tiles where there are enough of them to fill the device twice, else 128
   const bool wide = tile_n ? tile_n == 256 : tiles_m * ((ncols + 255) / 256) >= 2 * 148;
-  const int bn = wide ? 256 : 128;
+  const int bn = tile_n == 64 ? 64 : wide ? 256 : 128;
   const long long blocks = tiles_m * ((ncols + bn - 1) / bn);
   if (blocks > INT_MAX) return TDZ_EINVAL;
   CUtensorMap mah, mal, mb, mbl;
@@ -426,10 +427,13 @@ int tc_axis_transform(const float* a_hi, const float* a_lo, long long rows, int 
       !make_map(&mbl, b_lo ? b_lo : b, ncols, K, bn))
     return TDZ_ECUDA;
   const bool asplit = a_lo == nullptr;
-  const cudaError_t e = wide ? launch_any<256>(b_lo != nullptr, asplit, mah, mal, mb, mbl, rows, K, ncols, plane_rows,
-                                               plane_stride, out_hi, out_lo, err, blocks, st)
-                             : launch_any<128>(b_lo != nullptr, asplit, mah, mal, mb, mbl, rows, K, ncols, plane_rows,
-                                               plane_stride, out_hi, out_lo, err, blocks, st);
+  const cudaError_t e =
+      bn == 64    ? launch_any<64>(b_lo != nullptr, asplit, mah, mal, mb, mbl, rows, K, ncols, plane_rows, plane_stride,
+                                   out_hi, out_lo, err, blocks, st)
+      : bn == 256 ? launch_any<256>(b_lo != nullptr, asplit, mah, mal, mb, mbl, rows, K, ncols, plane_rows,
+                                    plane_stride, out_hi, out_lo, err, blocks, st)
+                  : launch_any<128>(b_lo != nullptr, asplit, mah, mal, mb, mbl, rows, K, ncols, plane_rows,
+                                    plane_stride, out_hi, out_lo, err, blocks, st);
   if (e != cudaSuccess) {
     set_error(std::string("tensor-core axis transform: ") + cudaGetErrorString(e));
     return TDZ_ECUDA;

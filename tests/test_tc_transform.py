@@ -23,11 +23,13 @@ def _tf32(x):
 
 
 # (planes, plane_rows, k, ncols, tile_n): tile_n 0 = the library's choice (128-column tiles unless
-# tiles_m * ceil(ncols / 256) >= 296)
+# tiles_m * ceil(ncols / 256) >= 296); 64 = the autotuner's narrow tiles for small planes
 CASES = [
     (2, 128, 64, 128, 0),       # one k-block ring pass, two row tiles
     (2, 200, 200, 200, 0),      # ragged k (7 blocks, the stage ring wraps), ragged columns, plane edge in a tile
     (2, 200, 200, 200, 256),    # the same with 256-column tiles
+    (2, 200, 200, 200, 64),     # and with 64-column tiles (4 column tiles, the last one ragged)
+    (2, 728, 728, 728, 64),     # the largest dot grid's padded plane in 64-column tiles
     (2, 1024, 1024, 1024, 0),   # the 2-D fast-diagonalisation shape, 128 blocks
     (2, 32768, 256, 256, 0),    # 512 row tiles: 256-column tiles
     (2, 20000, 200, 200, 128),  # ragged rows, k and columns, forced 128-column tiles
@@ -93,11 +95,11 @@ def test_tc_axis_transform_rejects_bad_sizes(tdz):
     with pytest.raises(tdz.TDZError):
         tdz.tc_axis_transform(x[1:], x, x, 64, 64, 64, 64, 64 * 64, x)  # a_hi not 16-byte aligned
     with pytest.raises(tdz.TDZError):
-        tdz.tc_axis_transform(x, x, x, 64, 64, 64, 64, 64 * 64, x, tile_n=64)  # no such tile width
+        tdz.tc_axis_transform(x, x, x, 64, 64, 64, 64, 64 * 64, x, tile_n=96)  # no such tile width
 
 
 def test_preconditioner_autotuner(tdz):
-    """A mixed 2-D batch times its preconditioner in the four transform variants at creation and keeps
+    """A mixed 2-D batch times its preconditioner in the six transform variants at creation and keeps
     the fastest; a binary64 batch (cuBLAS DGEMM transforms) reports nothing."""
     import workloads as wl
     p = 6
@@ -105,8 +107,8 @@ def test_preconditioner_autotuner(tdz):
     ops = tdz.Ops([tdz.Basis(t, p, p + 1) for _ in range(2)], wl.softcore_medium(0.5))
     b = tdz.Batch([ops], [0], tdz.MIXED)
     v, ms = b.precond_tuning(0)
-    assert v in (0, 1, 2, 3)
-    assert len(ms) == 4 and min(ms) > 0
+    assert v in range(6)
+    assert len(ms) == 6 and min(ms) > 0
     assert ms[v] == min(ms)
     b64 = tdz.Batch([ops], [0], tdz.FP64)
     assert b64.precond_tuning(0) == (-1, [])
