@@ -22,9 +22,12 @@ numpy/scipy double precision:
 * ``hhg``       - windowed spectrum S(w) and per-harmonic yields (Sec. "Dipoles").
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test against what
-the paper or the mathematics fixes, except the non-separable 2-D/3-D potential
-and mass terms (soft-core, elliptical dot) whose values have no closed form:
-those are "parity unpinned" beyond the separable special cases that reduce to
-the pinned 1-D factors.
+the paper or the mathematics fixes. The non-separable 2-D/3-D potential and mass
+terms (soft core, elliptical dot), whose matrix elements have no closed form, are
+pinned by the cases that reduce to something independent: an ellipse covering or
+missing the domain is the constant medium, a dot stretched into a stripe is the
+Kronecker product of the layered 1-D assembly, exchange symmetries of circular
+and soft-core media, and soft-core gradients against finite differences of the
+assembled potential.
 """
 from . import bspline, assemble, propagate, eigen, hhg  # noqa: F401
