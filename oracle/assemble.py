@@ -190,11 +190,13 @@ def assemble_1d(knots, p, nq, med, trim=True):
 
 
 # ------------------------------------------------------------------ 2-D / 3-D
-def assemble_nd(knots_list, p_list, nq_list, med, trim=True):
+def assemble_nd(knots_list, p_list, nq_list, med, trim=True, elements=None):
     """Tensor-product matrices by full tensor quadrature on every element (CSR).
 
     Returns {S, T, V, H0, D[axis], G[axis], K, dim, shape} with shape the per-axis
-    number of (trimmed) functions; linear index x fastest."""
+    number of (trimmed) functions; linear index x fastest. `elements` (optional): the
+    tensor elements (tuples of per-axis element indices) to integrate over instead of all;
+    the rows of functions whose support lies in them are then complete (assemble_nd_rows)."""
     dim = len(knots_list)
     qs = [quadrature_1d(np.asarray(k, dtype=np.float64), p, nq) for k, p, nq in zip(knots_list, p_list, nq_list)]
     nfun = [len(k) - p - 1 for k, p in zip(knots_list, p_list)]
@@ -207,7 +209,7 @@ def assemble_nd(knots_list, p_list, nq_list, med, trim=True):
     rows_all, cols_all = [], []
     # loop over tensor elements (one numpy block per element row along the slowest axis)
     E = [len(q["span"]) for q in qs]
-    for idx in product(*[range(e) for e in E]):
+    for idx in (product(*[range(e) for e in E]) if elements is None else elements):
         # local points: meshgrid over axes (axis 0 fastest in linear index; here arrays indexed [q0,q1,...])
         pts = np.meshgrid(*[qs[a]["x"][idx[a]] for a in range(dim)], indexing="ij")
         wts = np.ones_like(pts[0])
@@ -288,6 +290,28 @@ def assemble_nd(knots_list, p_list, nq_list, med, trim=True):
     out["dim"] = dim
     out["shape"] = shape
     return out
+
+
+def assemble_nd_rows(knots_list, p_list, nq_list, med, rows):
+    """The matrices of assemble_nd (trimmed) with the given rows complete: the same element
+    quadrature, restricted to the elements in the support of those rows' functions, so that
+    single rows of a system too large to assemble can be checked. rows: trimmed linear indices
+    (x fastest). The other rows hold partial sums and must not be used."""
+    dim = len(knots_list)
+    firsts = [quadrature_1d(np.asarray(k, dtype=np.float64), p, nq)["first"]
+              for k, p, nq in zip(knots_list, p_list, nq_list)]
+    ntrim = [len(k) - p - 1 - 2 for k, p in zip(knots_list, p_list)]
+    elements = set()
+    for j in rows:
+        per_axis = []
+        rest = int(j)
+        for a in range(dim):
+            i = rest % ntrim[a] + 1            # untrimmed index on axis a
+            rest //= ntrim[a]
+            f = firsts[a]
+            per_axis.append(np.nonzero((f <= i) & (i <= f + p_list[a]))[0].tolist())
+        elements.update(product(*per_axis))
+    return assemble_nd(knots_list, p_list, nq_list, med, trim=True, elements=sorted(elements))
 
 
 def to_band(A, p):

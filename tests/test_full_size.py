@@ -12,6 +12,9 @@
   preconditioner (per-axis line solves); plus norm conservation.
 * 3-D soft-core atom (254^3 = 16.4 M coefficients): mixed against binary64 (1e-8: both stop at a
   1e-12 residual and A_n is ill-conditioned at this size), norm conservation.
+* The 2-D atom and the largest dot at full size against the oracle on sampled outputs: one mixed CN
+  step, and the CN equation's residual on a dozen rows formed with the oracle's own quadrature of
+  those rows (assemble_nd_rows), held to the refinement's stopping rule.
 """
 import numpy as np
 import pytest
@@ -156,3 +159,52 @@ def test_softcore_atom_3d_full_size_mixed_vs_binary64(tdz):
     # agreement limited by the conditioning of A_n at the 1e-12 residual tolerance of both paths
     assert _rel(res["mixed"][0], res["fp64"][0]) < 1e-8
     assert np.max(np.abs(res["mixed"][1] - res["fp64"][1])) < 1e-8 * max(1.0, np.max(np.abs(res["fp64"][1])))
+
+
+def _cn_rows_full_size(tdz, knots, p, med, c0, field2, dt, nrand, seed):
+    """One mixed-precision CN step of a full-size 2-D run on the GPU (the benchmark's launch path: fused
+    FP32 stencil apply, tensor-core preconditioner, double-float refinement), checked on sampled rows
+    against the oracle: r_j = [(S + i tau H) c1 - (S - i tau H) c0]_j with H = H0 + Ebar . D from the
+    oracle's own quadrature of those rows (assemble_nd_rows). Rows where the state is large (the
+    informative ones) and random rows; the bound is the refinement's stopping rule, |r| <= 1e-12 |S c0|,
+    with a factor 10 (an FP32-only solve leaves about 1e-7)."""
+    ops = tdz.Ops([tdz.Basis(k, p, p + 1) for k in knots], med)
+    b = tdz.Batch([ops], [0], tdz.MIXED)
+    b.set_state(0, c0)
+    b.propagate(np.ascontiguousarray(field2.reshape(1, 2, 2)), dt, 0, 1)
+    c1 = b.get_state(0)
+    assert b.observe(0)[1] == tdz.TDZ_OK
+    del b
+    rng = np.random.default_rng(seed)
+    big = np.argsort(np.abs(c0))[-2000:]
+    rows = sorted(set(rng.choice(big, 8, replace=False).tolist()) | set(rng.integers(0, len(c0), nrand).tolist()))
+    m = assemble.assemble_nd_rows(knots, [p, p], [p + 1, p + 1], med, rows)
+    eb = 0.5 * (field2[0] + field2[1])
+    tau = 0.5 * dt
+    S = m["S"][rows]
+    H = (m["H0"] + eb[0] * m["D"][0] + eb[1] * m["D"][1])[rows]
+    r = (S @ c1 + 1j * tau * (H @ c1)) - (S @ c0 - 1j * tau * (H @ c0))
+    # |S c0| through the separable overlap S = S_y (x) S_x of the oracle's 1-D assembly (the overlap does
+    # not depend on the medium)
+    Sx = assemble.assemble_1d(knots[0], p, p + 1, wl.softcore_medium(0.5))["S"]
+    Sy = assemble.assemble_1d(knots[1], p, p + 1, wl.softcore_medium(0.5))["S"]
+    C0 = c0.reshape(Sy.shape[0], Sx.shape[0])
+    sc0 = np.linalg.norm(Sy @ (Sx @ C0.T).T)
+    assert np.max(np.abs(r)) <= 1e-11 * sc0, (np.max(np.abs(r)) / sc0)
+    return np.max(np.abs(r)) / sc0
+
+
+def test_softcore_atom_2d_full_size_cn_rows_against_oracle(tdz):
+    p, t = 7, wl.knots_for_nsplines(-150.0, 150.0, 1024, 7)
+    dt = 0.05
+    f = wl.sin2_pulse(wl.time_grid(dt, 40), wl.e0_from_intensity(1e14), wl.omega_from_nm(800.0), 4.0,
+                      ellipticity=0.3, dim=2)
+    _cn_rows_full_size(tdz, [t, t], p, wl.softcore_medium(0.5), bench._gauss_state(t, p, 2), f[20:22], dt, 4, 11)
+
+
+def test_dot_full_size_cn_rows_against_oracle(tdz):
+    wk = wl.dot_batch(nsteps=2)
+    r = max(wk.runs, key=lambda x: len(x.knots[0]) * len(x.knots[1]))
+    f = np.array([[2e-5, 1e-5], [2.5e-5, 1.5e-5]])   # a field that couples both axes (the run's own is along x)
+    _cn_rows_full_size(tdz, list(r.knots), r.degree, r.medium, bench._gauss_state(r.knots[0], r.degree, 2),
+                       f, wk.dt, 4, 12)

@@ -447,3 +447,37 @@ def test_softcore_3d_exchange_symmetry_and_acceleration_matrices():
                 assemble.potential = orig
         fd = (vs[0] - vs[1]) / (2 * h)
         assert _maxdiff(fd, m["G"][a]) < 1e-7 * abs(m["G"][a]).max(), a
+
+
+@pytest.mark.parametrize("case", ["softcore2d", "dot2d", "softcore3d"])
+def test_assemble_nd_rows_equal_full_assembly(case):
+    """assemble_nd_rows (the same element quadrature restricted to the support of chosen rows, for rows of
+    systems too large to assemble) reproduces those rows of the full assemble_nd: interior, edge and
+    corner rows, every matrix."""
+    if case == "softcore2d":
+        knots = [wl.knots_for_nsplines(-6.0, 6.0, 14, 3)] * 2
+        med, p = wl.softcore_medium(0.5), 3
+    elif case == "dot2d":
+        knots = [wl.knots_for_nsplines(-6.0, 6.0, 13, 3), wl.knots_for_nsplines(-5.0, 5.0, 15, 3)]
+        med = wl.medium({"kind": "ellipse", "a": 3.0, "b": 2.0, "m_in": 0.5, "m_out": 1.0},
+                        {"kind": "ellipse", "a": 3.0, "b": 2.0, "v_in": -1.0, "v_out": 0.0})
+        p = 3
+    else:
+        knots = [wl.knots_for_nsplines(-5.0, 5.0, 8, 2)] * 3
+        med, p = wl.softcore_medium(0.5), 2
+    dim = len(knots)
+    full = assemble.assemble_nd(knots, [p] * dim, [p + 1] * dim, med)
+    N = full["S"].shape[0]
+    rows = sorted({0, N - 1, N // 2, N // 3 + 1, full["shape"][0] - 1, full["shape"][0]})
+    part = assemble.assemble_nd_rows(knots, [p] * dim, [p + 1] * dim, med, rows)
+    for key in ("S", "T", "V", "K", "H0"):
+        a, b = full[key][rows].toarray(), part[key][rows].toarray()
+        assert np.allclose(a, b, rtol=1e-14, atol=1e-15 * np.abs(a).max()), key
+    for key in ("D", "G"):
+        for ax in range(dim):
+            a, b = full[key][ax][rows].toarray(), part[key][ax][rows].toarray()
+            assert np.allclose(a, b, rtol=1e-14, atol=1e-15 * max(np.abs(a).max(), 1e-300)), (key, ax)
+    # a row outside the chosen ones is incomplete (the restriction is real)
+    others = [j for j in range(N) if j not in rows]
+    assert part["S"].nnz < full["S"].nnz and any(
+        not np.allclose(full["S"][j].toarray(), part["S"][j].toarray()) for j in others)
