@@ -1004,6 +1004,16 @@ __global__ void __launch_bounds__(256, 3) k_fused_last_reduce_ff(const C<T>* __r
       const int j = e0 + k - 1;
       win[k] = packed((j >= 0 && j < nL) ? to_cff(in[(long long)j * inner + i]) : cff{{0.f, 0.f}, {0.f, 0.f}});
     }
+    constexpr int kGPre = 4;  // the tabulated factor a few points ahead (the table streams from memory)
+    const int gend = e1 * nq;
+    fx gpre[kGPre];
+    if (gtab) {
+#pragma unroll
+      for (int u = 0; u < kGPre; ++u) {
+        const int qp = e0 * nq + u;
+        gpre[u] = qp < gend ? gtab[(long long)qp * inner + i] : fx(0);
+      }
+    }
     for (int e = e0; e < e1; ++e) {
       for (int qq = 0; qq < nq; ++qq) {
         const int q = e * nq + qq;
@@ -1022,7 +1032,10 @@ __global__ void __launch_bounds__(256, 3) k_fused_last_reduce_ff(const C<T>* __r
         acc_mul(m2, psi, psi);
         r[L] = ff{AL.fx[q], AL.lx[q]};
         if (gtab) {  // w m^-1 Z (r^2 + eps)^(-3/2) tabulated: the soft-core gradient is that times r_a
-          const ff wq = ff_mul(acc_get(m2), to_ff(gtab[(long long)q * inner + i]));
+          const ff wq = ff_mul(acc_get(m2), to_ff(gpre[0]));
+#pragma unroll
+          for (int u = 0; u + 1 < kGPre; ++u) gpre[u] = gpre[u + 1];
+          gpre[kGPre - 1] = q + kGPre < gend ? gtab[(long long)(q + kGPre) * inner + i] : fx(0);
           acc_add(s0, wq);        // r_a, a < L, is fixed along the pencil: applied once, below
           acc_mul(s1, wq, r[L]);
         } else {
