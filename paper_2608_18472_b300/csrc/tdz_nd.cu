@@ -1015,6 +1015,10 @@ __global__ void __launch_bounds__(256, 3) k_fused_last_reduce_ff(const C<T>* __r
       }
     }
     for (int e = e0; e < e1; ++e) {
+      // the next element's new coefficient, loaded now so that its latency overlaps this element's points
+      const int jn = e + P;
+      const cff nxt = (jn >= 0 && jn < nL && e + 1 < e1) ? to_cff(in[(long long)jn * inner + i])
+                                                          : cff{{0.f, 0.f}, {0.f, 0.f}};
       for (int qq = 0; qq < nq; ++qq) {
         const int q = e * nq + qq;
         const float* bh = AL.fB + (size_t)q * (P + 1);
@@ -1048,9 +1052,7 @@ __global__ void __launch_bounds__(256, 3) k_fused_last_reduce_ff(const C<T>* __r
       }
 #pragma unroll
       for (int k = 0; k < P; ++k) win[k] = win[k + 1];
-      const int jn = e + P;
-      win[P] = packed((jn >= 0 && jn < nL && e + 1 < e1) ? to_cff(in[(long long)jn * inner + i])
-                                                         : cff{{0.f, 0.f}, {0.f, 0.f}});
+      win[P] = packed(nxt);
     }
     if (gtab) {
       const ff t0 = acc_get(s0);
