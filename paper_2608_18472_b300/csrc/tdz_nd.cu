@@ -195,22 +195,12 @@ __global__ void k_axis_band(BandTerms<T> bt, const C<T>* __restrict__ in0, const
   bool need0 = false, need1 = false;  // input streams some term reads
 #pragma unroll
   for (int t = 0; t < NT; ++t) (bt.sel[t] ? need1 : need0) = true;
-  const bool narrow = total < (1LL << 31);  // 32-bit index arithmetic (the divisions below) when it fits
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
-    long long i, o;
-    int j;
-    if (narrow) {
-      const unsigned u = (unsigned)idx, in32 = (unsigned)inner, oj = u / in32;
-      i = u - oj * in32;
-      o = oj / (unsigned)L;
-      j = (int)(oj - (unsigned)o * (unsigned)L);
-    } else {
-      i = idx % inner;
-      const long long oj = idx / inner;
-      j = (int)(oj % L);
-      o = oj / L;
-    }
+    const long long i = idx % inner;
+    const long long oj = idx / inner;
+    const int j = (int)(oj % L);
+    const long long o = oj / L;
     Mac<T> mr[NT], mi[NT];
 #pragma unroll
     for (int d = -P; d <= P; ++d) {
@@ -1420,8 +1410,7 @@ __global__ void k_wapply(const T* __restrict__ Wm, const C<T>* __restrict__ x, C
   const long long N = (long long)nx * ny;
   for (long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x; row < N;
        row += (long long)gridDim.x * blockDim.x) {
-    const int iy = N < (1LL << 32) ? (int)((unsigned)row / (unsigned)nx) : (int)(row / nx);
-    const int ix = (int)(row - (long long)iy * nx);
+    const int ix = (int)(row % nx), iy = (int)(row / nx);
     Mac<T> mr, mi;
 #pragma unroll 1
     for (int dy = 0; dy <= P; ++dy) {
